@@ -1,0 +1,149 @@
+"""Pins of the oracle's Restore / Langevin logic against closed forms.
+
+P1  LocalDynamics (Alg. 4) on a Gaussian far from the torus edges is the
+    linear map x' = A (x - c) + c + stddev xi with
+    A = (1 - a / s^2) I - (gamma_tilde / s^2) J, a = stddev^2 / 2 and
+    J (v1, v2) = (v2, -v1): one-step mean and covariance, and the stationary
+    covariance of the discrete chain from the Lyapunov equation
+    Sigma = A Sigma A^T + stddev^2 I (Sec. 5.1 Euler-Maruyama, Sec. 5.3).
+P2  Constant target: the kill probability per step is
+    k / (h + k) = p_lambda / (m p + p_lambda) = 1 / (m + 1) and Resolve
+    (Alg. 3) returns the constant (Eq. killing-rate-constant).
+P3  pi-invariance: on a 4-D Gaussian mixture the time average of g over the
+    Restore process matches the target's moments (Sec. 4, Def. 1 with the
+    modified killing rate; ergodic average of Sec. 3).
+"""
+import numpy as np
+import pytest
+
+from paper_2605_08916_gb300 import scenes as S
+
+
+def test_local_dynamics_one_step_moments(oracle):
+    O = oracle
+    s = 0.05
+    c = np.array([0.5, 0.5])
+    x = np.array([0.52, 0.47])
+    stddev, gt = 0.01, 5e-4
+    score = -(x - c) / s ** 2
+    n = 40000
+    xs = np.stack([O.local_dynamics(x, score, stddev, gt, seed=123, frame=0, step=1, chain=j) for j in range(n)])
+    a = 0.5 * stddev ** 2
+    J = np.array([[0.0, 1.0], [-1.0, 0.0]])
+    mean_exp = x + a * score + gt * (J @ score)
+    se = stddev / np.sqrt(n)
+    assert np.all(np.abs(xs.mean(0) - mean_exp) < 4 * se), (xs.mean(0), mean_exp)
+    # the rotation term is 20 SE away from zero: a sign error fails
+    assert abs(gt * (J @ score))[0] > 20 * se
+    cov = np.cov((xs - mean_exp).T)
+    assert np.allclose(cov, stddev ** 2 * np.eye(2), atol=4 * stddev ** 2 * np.sqrt(2.0 / n))
+
+
+@pytest.mark.parametrize("gt_factor", [0.0, 1.0])
+def test_stationary_covariance_closed_form(oracle, gt_factor):
+    O = oracle
+    # s = 0.1 keeps g above the density floor eps everywhere on the torus, so
+    # the drift pulls every uniform start into the mode (with s = 0.05 the
+    # far field has g < eps and chains random-walk there, as the method says)
+    s = 0.1
+    mix = S.single_gaussian([0.5, 0.5], s)
+    tgt = O.target(mix)
+    stddev = 0.04
+    gt = gt_factor * 0.5 * stddev ** 2
+    prm = O.make_params(L=1, drift="exact", rb=True, stddev=stddev, gamma_tilde=gt, k0=1e-12)
+    M, T, burn = 2048, 400, 150
+    r = O.restore_run(tgt, prm, seed=7, chain_ids=np.arange(M), n_steps=T, accum=False)
+    assert r["tour_count"] == 0
+    x = r["x"][burn:] - 0.5
+    per_chain = np.einsum("tmi,tmj->mij", x, x) / x.shape[0]
+    est = per_chain.mean(0)
+    se = per_chain.std(0) / np.sqrt(M)
+    a = 0.5 * stddev ** 2 / s ** 2
+    b = gt / s ** 2
+    var_exp = stddev ** 2 / (1.0 - (1.0 - a) ** 2 - b ** 2)
+    for i in range(2):
+        assert abs(est[i, i] - var_exp) < 3.5 * se[i, i], (est, var_exp, se)
+    assert abs(est[0, 1]) < 3.5 * se[0, 1]
+    # the discretisation is visible: the continuous-time variance s^2 is rejected
+    assert abs(est[0, 0] - s ** 2) > 3 * se[0, 0]
+
+
+@pytest.mark.parametrize("rb", [True, False])
+def test_constant_target_kill_rate_and_resolve(oracle, rb):
+    O = oracle
+    c = 2.0
+    mix = S.constant_target(d=4, value=c, width=4, height=4)
+    tgt = O.target(mix)
+    m, dt = 64.0, 1e-5
+    k0 = c / (m * dt)
+    prm = O.make_params(L=1, drift="exact", rb=rb, k0=k0, m=m, dt=dt)
+    M, T = 4096, 200
+    r = O.restore_run(tgt, prm, seed=11, chain_ids=np.arange(M), n_steps=T, record=False)
+    n = M * (T + 1)
+    p_kill = k0 / ((c + 1e-8) / dt + k0)
+    assert abs(p_kill - 1.0 / (m + 1.0)) < 1e-6
+    frac = r["tour_count"] / n
+    assert abs(frac - p_kill) < 4 * np.sqrt(p_kill * (1 - p_kill) / n)
+    img = O.resolve(r["accum"], k0, r["tour_count"])
+    # each channel's image sums (over pixels) to lambda(f) = c
+    tot = img.sum(0)
+    assert np.allclose(tot, c, rtol=4 / np.sqrt(r["tour_count"])), tot
+    # uniform target: every pixel gets c / (W H) up to noise
+    assert np.allclose(img[:, 0], c / 16, rtol=0.1)
+
+
+def _wrapped_moments_1d(mu, s, n=200001):
+    """E[x], E[x^2] on [0,1) of the nearest-image Gaussian (normalised
+    numerically), by quadrature."""
+    x = (np.arange(n) + 0.5) / n
+    dd = x - mu
+    dd -= np.round(dd)
+    w = np.exp(-0.5 * dd ** 2 / s ** 2)
+    w /= w.sum()
+    return (w * x).sum(), (w * x * x).sum()
+
+
+def test_mixture_invariance_moments(oracle):
+    O = oracle
+    d, K = 4, 3
+    rng = np.random.default_rng(5)
+    w = rng.uniform(0.5, 1.5, K)
+    w /= w.sum()
+    mu = rng.uniform(0.3, 0.7, (K, d))
+    sig = rng.uniform(0.10, 0.14, K)
+    mix = S.Mixture(d, w, mu, sig, 8, 8)
+    tgt = O.target(mix)
+    # closed-form moments of the mixture (per coordinate quadrature, product form)
+    m1 = np.zeros(d)
+    m2 = np.zeros((d, d))
+    for k in range(K):
+        e1 = np.zeros(d)
+        e2 = np.zeros(d)
+        for i in range(d):
+            e1[i], e2[i] = _wrapped_moments_1d(mu[k, i], sig[k])
+        mk2 = np.outer(e1, e1)
+        np.fill_diagonal(mk2, e2)
+        m1 += w[k] * e1
+        m2 += w[k] * mk2
+    prm = O.make_params(L=1, drift="exact", rb=True, stddev=5e-3, m=64.0)
+    # p_lambda = 1 (normalised mixture) -> k0 = p_lambda / (m dt)
+    prm.k0 = 1.0 / (64.0 * 1e-5)
+    # complete tours are i.i.d.; renewal-reward: pi(g) = E[int g] / E[int 1]
+    M = 60000
+    r = O.restore_tours(tgt, prm, seed=3, chain_ids=np.arange(M), max_steps=1 << 22)
+    assert r["truncated"].sum() == 0
+    # E[tour length] = p_lambda / k0 = m dt, i.e. m steps on average (Sec. 6)
+    assert abs(r["steps"].mean() / 64.0 - 1.0) < 0.25
+    A1, Ag, Agg = r["I1"], r["Ix"], r["Ixx"]
+    est1 = Ag.sum(0) / A1.sum()
+    est2 = Agg.sum(0) / A1.sum()
+    # ratio-estimator standard errors across independent tours
+    mA = A1.mean()
+    se1 = np.sqrt(np.var(Ag - est1[None, :] * A1[:, None], axis=0) / M) / mA
+    se2 = np.sqrt(np.var(Agg - est2[None] * A1[:, None, None], axis=0) / M) / mA
+    z1 = np.abs(est1 - m1) / se1
+    z2 = np.abs(est2 - m2) / se2
+    assert z1.max() < 3.5, (est1, m1, z1)
+    assert z2.max() < 3.5, (est2, m2, z2)
+    # the check has power: the uniform distribution's moments are rejected
+    assert np.max(np.abs(est2 - (np.full((d, d), 0.25) + np.eye(d) / 12.0)) / se2) > 10
