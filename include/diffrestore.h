@@ -1,0 +1,225 @@
+/* diffrestore.h — C ABI of libdiffrestore (GB300, sm_103a).
+ *
+ * The data-parallel hot path of Diffusion Restore (arxiv 2605.08916): many
+ * independent Jump Restore chains ("tours") in primary sample space, each
+ * step evaluating the path contribution f(x), p(x) = lum(f) + eps and
+ * grad log p, taking one Euler-Maruyama step of the nonreversible Langevin
+ * local dynamics, running the hold/kill clock, regenerating killed chains
+ * from the uniform distribution, and splatting dt * f / p into an FP64 image.
+ *
+ * Conventions for every entry point:
+ *  - Return value: DR_OK (0) or a negative DR_ERR_* code; dr_last_error()
+ *    gives a thread-local message for the most recent failure.  No call
+ *    aborts, throws or traps.
+ *  - The library owns all device memory it allocates; buffers passed in are
+ *    only read (or written where stated) during the call or, for device
+ *    pointers, in stream order on the context's stream.
+ *  - "host" pointers are read / written synchronously; "device" pointers must
+ *    point to memory of the context's device.
+ *  - Work is issued on the CUDA stream given to dr_create (0 = legacy
+ *    default stream) and is stream-ordered unless a call says it synchronises.
+ *  - Array layouts are row-major and tightly packed.
+ */
+#ifndef DIFFRESTORE_H_
+#define DIFFRESTORE_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  DR_OK = 0,
+  DR_ERR_INVALID_ARG = -1,   /* bad pointer, size or value */
+  DR_ERR_STATE = -2,         /* call out of order (e.g. step before init) or empty estimate */
+  DR_ERR_CUDA = -3,          /* a CUDA runtime call failed */
+  DR_ERR_OOM = -4,           /* device allocation failed */
+  DR_ERR_DEVICE_CHECK = -5,  /* a kernel reported a checked condition (stack overflow, non-finite value) */
+  DR_ERR_TIMEOUT = -6        /* a bounded device wait gave up */
+};
+
+enum { DR_DRIFT_NONE = 0, DR_DRIFT_FD = 1, DR_DRIFT_ADJOINT = 2 };
+
+enum { DR_MAX_PATH_LEN = 16 }; /* L <= 16, so d = 2 + 4 (L - 1) <= 62 */
+
+typedef struct dr_ctx dr_ctx;
+
+/* Parameters of the Diffusion Restore process (Def. 2, Sec. 5.3; Sec. 6
+ * "Parameter choices").
+ *   max_path_len    L, number of path segments from the camera (1..16);
+ *                   the PSS dimension is d = 2 + 4 (L - 1).
+ *   drift_mode      DR_DRIFT_NONE (score 0), DR_DRIFT_FD (central finite
+ *                   differences of log p with step fd_h), DR_DRIFT_ADJOINT
+ *                   (hand-written reverse-mode gradient of log p).
+ *   rb_weight       0: the paper's exponential race of Alg. 1 (hold time
+ *                   ~ Exp(h), kill time ~ Exp(k), splat weight = the smaller);
+ *                   1: its Rao-Blackwellisation (weight 1 / (h + k), killed
+ *                   with probability k / (h + k)).
+ *   steps_per_splat records buffered before an automatic splat (>= 1).
+ *   stddev          sqrt(dt) * sigma, the per-step noise scale (paper: 5e-3).
+ *   dt              Euler-Maruyama step; holding rate h = 1 / dt (paper 1e-5).
+ *   gamma_tilde     dt * gamma / 2, the rotation scale of Alg. 4.
+ *   eps             density floor, p = lum(f) + eps (paper 1e-8).
+ *   fd_h            finite-difference step for DR_DRIFT_FD.
+ *   m               mean tour length target in k0 = p_lambda / (m dt)
+ *                   (Eq. killing-rate-constant; paper m = 64).
+ *   k0              killing constant; if <= 0, dr_chains_init estimates
+ *                   p_lambda as the mean of p over the initial uniform
+ *                   samples and sets k0 = p_lambda / (m dt). */
+typedef struct {
+  int32_t max_path_len;
+  int32_t drift_mode;
+  int32_t rb_weight;
+  int32_t steps_per_splat;
+  float stddev;
+  float dt;
+  float gamma_tilde;
+  float eps;
+  float fd_h;
+  float m;
+  double k0;
+} dr_params;
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int dr_version(void);
+
+/* Message for the most recent failing call on this thread ("" if none).
+ * The returned pointer stays valid until the thread's next failing call. */
+const char* dr_last_error(void);
+
+/* Creates a context on CUDA device `device` issuing work on `cuda_stream`
+ * (a cudaStream_t, or NULL for the legacy default stream).  *out receives
+ * the handle.  Errors: INVALID_ARG (out NULL, bad device), CUDA. */
+int dr_create(dr_ctx** out, int device, void* cuda_stream);
+
+/* Synchronises the context's stream and frees everything it owns. NULL is OK. */
+int dr_destroy(dr_ctx* ctx);
+
+/* Uploads a triangle scene and builds its BVH on the device (Sec. 4.3: the
+ * scene the tours trace; a change invalidates the chains, which must be
+ * re-initialised).  All pointers are HOST pointers, copied before return.
+ *   verts      float [nv * 3] vertex positions
+ *   tris       int32 [nt * 3] vertex indices (counter-clockwise = front)
+ *   normals    float [nv * 3] per-vertex shading normals, or NULL (flat);
+ *              a triangle is smooth-shaded only if its three vertex
+ *              normals are all non-zero (zero rows mark flat meshes)
+ *   tri_mat    int32 [nt] material index per triangle
+ *   mats       float [nm * 12] materials: type (0 diffuse, 1 glossy GGX coat
+ *              over Lambertian, 2 smooth dielectric, 3 black emitter),
+ *              albedo rgb, roughness, ior, emission rgb, f0, 0, 0.  Emission
+ *              is one-sided along cross(v1 - v0, v2 - v0); emitting
+ *              triangles form the light set used by next-event estimation.
+ *   camera     float [10]: eye xyz, look-at xyz, up xyz, vertical fov (deg)
+ *   width, height  image size in pixels (>= 1; width * height < 2^31)
+ * Synchronises the stream.  Errors: INVALID_ARG, OOM, CUDA. */
+int dr_scene_upload(dr_ctx* ctx, const float* verts, int32_t nv, const int32_t* tris, const float* normals,
+                    int32_t nt, const int32_t* tri_mat, const float* mats, int32_t nm, const float* camera,
+                    int32_t width, int32_t height);
+
+/* Uses an analytic target instead of a scene: an isotropic Gaussian mixture
+ * on the torus T^d, p = g + eps with g(x) = sum_k w[k] N(x; mu[k],
+ * sig[k]^2 I) (differences to the nearest image), or the constant `cval`
+ * when K = 0.  f = (g, g, g); the pixel comes from (x0, x1) on a
+ * width x height grid.  HOST pointers w [K], mu [K * d], sig [K].
+ * d must be even, 2..62.  Errors: INVALID_ARG, OOM, CUDA. */
+int dr_target_mixture(dr_ctx* ctx, int32_t d, int32_t K, const float* w, const float* mu, const float* sig,
+                      float cval, int32_t width, int32_t height);
+
+/* Initialize (Alg. 1) for n_chains chains: each chain j draws x ~ U(T^d)
+ * from its Philox4x32-10 stream (key = seed, counter = (step, j, block,
+ * frame << 4 | purpose)), evaluates f and p, runs the clock and records its
+ * splat.  Clears the image accumulator and tourCount.  If prm->k0 <= 0,
+ * k0 = p_lambda / (m dt) with p_lambda estimated from the same initial
+ * samples (Eq. killing-rate-constant), computed before the init clock runs.
+ * prm is a HOST pointer, copied.  Synchronises when k0 is estimated.
+ * Errors: STATE (no scene/target), INVALID_ARG, OOM, CUDA, DEVICE_CHECK. */
+int dr_chains_init(dr_ctx* ctx, uint64_t n_chains, uint64_t seed, uint32_t frame, const dr_params* prm);
+
+/* Evolve (Alg. 2 with LocalDynamics, Alg. 4) n_steps times: killed chains
+ * regenerate from U(T^d), the others move with the drift of the score
+ * stored at their current point; then each chain accumulates at its new
+ * point.  Records are splatted automatically when the buffer of
+ * steps_per_splat steps is full (before the step that would overflow it),
+ * so after the call the last step's records are still readable.
+ * Asynchronous.  Errors: STATE, CUDA. */
+int dr_step(dr_ctx* ctx, uint32_t n_steps);
+
+/* Splats all buffered records into the FP64 accumulator (the accumulation
+ * of Alg. 1, without atomics, deterministic).  Asynchronous. */
+int dr_splat(dr_ctx* ctx);
+
+/* Resolve (Alg. 3): out_rgb[i] = k0 / tourCount * accum[i] for the W*H*3
+ * FP32 DEVICE buffer out_rgb (row-major pixels, row 0 at the top, RGB).
+ * Splats pending records first.  Zero image when tourCount = 0, and then
+ * returns DR_ERR_STATE (checked with a synchronisation unless the stream is
+ * being captured). */
+int dr_resolve(dr_ctx* ctx, float* out_rgb);
+
+/* Copies the chain state to HOST buffers (any may be NULL): x and score
+ * [N * d] row-major per chain (score = grad log p at x, valid for chains
+ * that are not killed), killed [N], logp [N] of the last step, pix [N] and
+ * val [N * 3] (the last step's splat record).  Synchronises. */
+int dr_readback_state(dr_ctx* ctx, float* x, float* score, uint8_t* killed, float* logp, int32_t* pix, float* val);
+
+/* Copies the FP64 accumulator (W * H * 3, after splatting pending records)
+ * into a HOST buffer.  Synchronises. */
+int dr_readback_accum(dr_ctx* ctx, double* accum);
+
+/* Counters (HOST outputs, any may be NULL): completed tours (tourCount of
+ * Sec. 4.3), k0 in use, steps taken since init (init = step 0), rays traced
+ * since init, and the estimated p_lambda (0 if k0 was given).  Synchronises. */
+int dr_get_counters(dr_ctx* ctx, uint64_t* tour_count, double* k0, uint64_t* steps, uint64_t* rays,
+                    double* p_lambda);
+
+/* Batched evaluation at M points, DEVICE buffers: x [M * d] row-major,
+ * logp [M] = log(lum f + eps), grad [M * d] = grad log p (hand-written
+ * adjoint, or NULL), pix [M] or NULL, f [M * 3] or NULL.  Uses the uploaded
+ * scene (L from max_path_len) or mixture target.  Asynchronous. */
+int dr_eval_logp(dr_ctx* ctx, int32_t max_path_len, const float* x, int64_t M, float* logp, float* grad,
+                 int32_t* pix, float* f);
+
+/* Closest-hit queries through the BVH: rays [n * 6] (origin, direction;
+ * DEVICE), tri [n] original triangle id or -1, t [n] distance (inf on miss).
+ * `exclude` is a triangle id to skip (-1: none).  Asynchronous. */
+int dr_trace_closest(dr_ctx* ctx, const float* rays, int64_t n, int32_t exclude, int32_t* tri, float* t);
+
+/* Philox4x32-10 (Salmon et al. 2011, cited in Sec. 4.3) on DEVICE buffers:
+ * ctr [n * 4], key [n * 2] -> out [n * 4].  cuda_stream may be NULL.
+ * Asynchronous. */
+int dr_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int64_t n, void* cuda_stream);
+
+/* Splats M caller-made records (DEVICE, 16 bytes each: uint32 pixel index,
+ * float r, g, b) into the accumulator with the same sort + reduce as the
+ * chain records.  Pixel indices must be < W * H (checked on the host side
+ * only by the caller).  Asynchronous. */
+int dr_splat_records(dr_ctx* ctx, const void* recs, int64_t M);
+
+/* Resets the accumulator and tourCount without touching the chains (a new
+ * accumulation window over the same tours).  Asynchronous. */
+int dr_clear_image(dr_ctx* ctx);
+
+/* Checkpoint: serialises the chain state, counters, k0 and the FP64
+ * accumulator into a HOST buffer.  With host_buf NULL, *bytes receives the
+ * size needed.  A run resumed with dr_state_load continues bit-for-bit like
+ * an uninterrupted one (the RNG is counter-based).  Synchronises. */
+int dr_state_save(dr_ctx* ctx, void* host_buf, size_t* bytes);
+int dr_state_load(dr_ctx* ctx, const void* host_buf, size_t bytes);
+
+/* Traversal statistics mode: when enabled, steps also count BVH node
+ * visits and triangle tests (a separate kernel instantiation; the default
+ * kernels carry no counters).  dr_get_traversal_stats returns the totals
+ * since the last enable. */
+int dr_set_stats(dr_ctx* ctx, int enable);
+int dr_get_traversal_stats(dr_ctx* ctx, uint64_t* node_visits, uint64_t* tri_tests, uint64_t* rays);
+
+/* BVH summary: number of inner nodes, triangles, maximum depth (root = 1).
+ * Synchronises. */
+int dr_bvh_info(dr_ctx* ctx, int32_t* n_nodes, int32_t* n_tris, int32_t* max_depth);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DIFFRESTORE_H_ */

@@ -1,0 +1,107 @@
+"""ctypes binding of ``libdiffrestore.so`` (declared in ``include/diffrestore.h``).
+
+Argument marshalling only: every function here forwards to the C ABI function
+of the same name.  There is no CPU fallback: if the library cannot be built or
+loaded, importing it raises."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdiffrestore.so")
+
+DR_OK = 0
+DR_ERR_INVALID_ARG = -1
+DR_ERR_STATE = -2
+DR_ERR_CUDA = -3
+DR_ERR_OOM = -4
+DR_ERR_DEVICE_CHECK = -5
+DR_ERR_TIMEOUT = -6
+ERR_NAMES = {0: "DR_OK", -1: "DR_ERR_INVALID_ARG", -2: "DR_ERR_STATE", -3: "DR_ERR_CUDA", -4: "DR_ERR_OOM",
+             -5: "DR_ERR_DEVICE_CHECK", -6: "DR_ERR_TIMEOUT"}
+DR_DRIFT_NONE, DR_DRIFT_FD, DR_DRIFT_ADJOINT = 0, 1, 2
+
+# every entry point declared in include/diffrestore.h
+EXPORTS = ["dr_version", "dr_last_error", "dr_create", "dr_destroy", "dr_scene_upload", "dr_target_mixture",
+           "dr_chains_init", "dr_step", "dr_splat", "dr_resolve", "dr_readback_state", "dr_readback_accum",
+           "dr_get_counters", "dr_eval_logp", "dr_trace_closest", "dr_philox", "dr_splat_records",
+           "dr_clear_image", "dr_state_save", "dr_state_load", "dr_set_stats", "dr_get_traversal_stats",
+           "dr_bvh_info"]
+
+
+class dr_params(C.Structure):
+    _fields_ = [("max_path_len", C.c_int32), ("drift_mode", C.c_int32), ("rb_weight", C.c_int32),
+                ("steps_per_splat", C.c_int32), ("stddev", C.c_float), ("dt", C.c_float),
+                ("gamma_tilde", C.c_float), ("eps", C.c_float), ("fd_h", C.c_float), ("m", C.c_float),
+                ("k0", C.c_double)]
+
+
+class DRError(RuntimeError):
+    def __init__(self, code, fn, msg):
+        super().__init__(f"{fn} -> {ERR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load(build_if_missing=True):
+    """Loads the in-tree library (building it first if it is missing or out of
+    date when ``build_if_missing``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing:
+        from . import build as _b
+        _b.build()
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libdiffrestore.so not found at {LIB_PATH}; run paper_2605_08916_gb300.build")
+    L = C.CDLL(LIB_PATH)
+    P, I32, I64, U32, U64 = C.c_void_p, C.c_int32, C.c_int64, C.c_uint32, C.c_uint64
+    sig = {
+        "dr_version": ([], C.c_int),
+        "dr_last_error": ([], C.c_char_p),
+        "dr_create": ([C.POINTER(P), C.c_int, P], C.c_int),
+        "dr_destroy": ([P], C.c_int),
+        "dr_scene_upload": ([P, P, I32, P, P, I32, P, P, I32, P, I32, I32], C.c_int),
+        "dr_target_mixture": ([P, I32, I32, P, P, P, C.c_float, I32, I32], C.c_int),
+        "dr_chains_init": ([P, U64, U64, U32, C.POINTER(dr_params)], C.c_int),
+        "dr_step": ([P, U32], C.c_int),
+        "dr_splat": ([P], C.c_int),
+        "dr_resolve": ([P, P], C.c_int),
+        "dr_readback_state": ([P, P, P, P, P, P, P], C.c_int),
+        "dr_readback_accum": ([P, P], C.c_int),
+        "dr_get_counters": ([P, P, P, P, P, P], C.c_int),
+        "dr_eval_logp": ([P, I32, P, I64, P, P, P, P], C.c_int),
+        "dr_trace_closest": ([P, P, I64, I32, P, P], C.c_int),
+        "dr_philox": ([P, P, P, I64, P], C.c_int),
+        "dr_splat_records": ([P, P, I64], C.c_int),
+        "dr_clear_image": ([P], C.c_int),
+        "dr_state_save": ([P, P, C.POINTER(C.c_size_t)], C.c_int),
+        "dr_state_load": ([P, P, C.c_size_t], C.c_int),
+        "dr_set_stats": ([P, C.c_int], C.c_int),
+        "dr_get_traversal_stats": ([P, P, P, P], C.c_int),
+        "dr_bvh_info": ([P, P, P, P], C.c_int),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return L
+
+
+def last_error():
+    return load().dr_last_error().decode()
+
+
+def check(code, fn):
+    if code != DR_OK:
+        raise DRError(code, fn, last_error())
+    return code
+
+
+def call(name, *args):
+    """Calls a C-ABI function and raises DRError on a non-zero status."""
+    return check(getattr(load(), name)(*args), name)

@@ -1,0 +1,874 @@
+// libdiffrestore C ABI: context, device memory, scene upload and the host
+// orchestration of Alg. 1 - 3 (see include/diffrestore.h for the contract).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/diffrestore.h"
+#include "dr_internal.h"
+
+using namespace dr;
+
+namespace {
+float hbits_f(int v) { float f; std::memcpy(&f, &v, 4); return f; }
+int hbits_i(float f) { int v; std::memcpy(&v, &f, 4); return v; }
+}  // namespace
+
+struct dr_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  // target
+  int target = -1;  // -1 none, 0 scene, 1 mixture
+  int W = 0, H = 0;
+  int nt = 0, n_nodes = 0, n_lights = 0;
+  float tmin = 0.f;
+  Camera cam{};
+  float4* nodes = nullptr;
+  float4* tris = nullptr;
+  float4* surf = nullptr;
+  float4* lights = nullptr;
+  float* nrm = nullptr;
+  float* mats = nullptr;
+  float* mw = nullptr;
+  float* mmu = nullptr;
+  float* msig = nullptr;
+  int mK = 0, md = 0;
+  float mcval = 0.f;
+  // chains
+  unsigned long long N = 0;
+  int d = 0;
+  dr_params prm{};
+  uint32_t step = 0;
+  uint64_t seed = 0;
+  uint32_t frame = 0;
+  bool inited = false;
+  float* x = nullptr;
+  float* score = nullptr;
+  float* logp = nullptr;
+  uint8_t* killed = nullptr;
+  SplatRec* rec = nullptr;
+  SplatRec* rec_alt = nullptr;
+  size_t rec_cap = 0;  // steps
+  uint32_t rec_count = 0;
+  void* sort_scratch = nullptr;
+  size_t state_cap = 0;  // N * d allocated
+  size_t chains_cap = 0;
+  size_t rec_cap_records = 0;
+  double* accum = nullptr;
+  size_t accum_n = 0;
+  unsigned long long* counters = nullptr;  // tour_count, rays, node visits, tri tests
+  double* p_partial = nullptr;
+  size_t p_partial_cap = 0;
+  double* p_sum = nullptr;
+  uint32_t* err = nullptr;
+  double k0 = 0.0;
+  double p_lambda = 0.0;
+  bool stats = false;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+#define DR_CUDA(call)                                                                              \
+  do {                                                                                             \
+    cudaError_t e_ = (call);                                                                       \
+    if (e_ != cudaSuccess) {                                                                       \
+      return fail(e_ == cudaErrorMemoryAllocation ? DR_ERR_OOM : DR_ERR_CUDA,                      \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                             \
+    }                                                                                              \
+  } while (0)
+
+template <class T>
+int dalloc(T** p, size_t count) {
+  if (*p) {
+    cudaFree(*p);
+    *p = nullptr;
+  }
+  if (count == 0) return DR_OK;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return fail(DR_ERR_OOM, std::string("cudaMalloc of ") + std::to_string(count * sizeof(T)) + " bytes: " +
+                                cudaGetErrorString(e));
+  }
+  return DR_OK;
+}
+
+template <class T>
+void dfree(T** p) {
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+}
+
+#define DR_TRY(expr)             \
+  do {                           \
+    int r_ = (expr);             \
+    if (r_ != DR_OK) return r_;  \
+  } while (0)
+
+DevScene dev_scene(const dr_ctx* c) {
+  DevScene S;
+  S.nodes = c->nodes;
+  S.tris = c->tris;
+  S.surf = c->surf;
+  S.nrm = c->nrm;
+  S.mats = c->mats;
+  S.lights = c->lights;
+  S.n_lights = c->n_lights;
+  S.n_tris = c->nt;
+  S.n_nodes = std::max(1, c->n_nodes);
+  S.W = c->W;
+  S.H = c->H;
+  S.tmin = c->tmin;
+  S.cam = c->cam;
+  return S;
+}
+
+DevMixture dev_mixture(const dr_ctx* c) {
+  DevMixture M;
+  M.w = c->mw;
+  M.mu = c->mmu;
+  M.sig = c->msig;
+  M.K = c->mK;
+  M.d = c->md;
+  M.W = c->W;
+  M.H = c->H;
+  M.cval = c->mcval;
+  return M;
+}
+
+int check_launch(const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(DR_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  return DR_OK;
+}
+
+int key_bits(long long n_pix) {
+  int b = 0;
+  while (b < 32 && (1ll << b) < n_pix) ++b;
+  return std::max(b, 1);
+}
+
+int check_device_error(dr_ctx* c) {
+  uint32_t e = 0;
+  DR_CUDA(cudaMemcpyAsync(&e, c->err, sizeof(e), cudaMemcpyDeviceToHost, c->stream));
+  DR_CUDA(cudaStreamSynchronize(c->stream));
+  if (e) {
+    std::string m = "device check failed:";
+    if (e & kErrStackOverflow) m += " traversal stack overflow;";
+    if (e & kErrNonFinite) m += " non-finite f or p;";
+    if (e & kErrBadIndex) m += " index out of range;";
+    if (e & kErrTimeout) m += " bounded wait timed out;";
+    return fail(e & kErrTimeout ? DR_ERR_TIMEOUT : DR_ERR_DEVICE_CHECK, m);
+  }
+  return DR_OK;
+}
+
+int flush(dr_ctx* c) {
+  if (c->rec_count == 0) return DR_OK;
+  const size_t n = (size_t)c->rec_count * c->N;
+  SplatRec* sorted =
+      sort_splat_records(c->rec, c->rec_alt, n, key_bits((long long)c->W * c->H), c->sort_scratch, c->stream);
+  launch_segment_reduce(sorted, n, c->accum, (uint32_t)((size_t)c->W * c->H), c->err, c->stream);
+  c->rec_count = 0;
+  return check_launch("splat");
+}
+
+StepArgs step_args(dr_ctx* c) {
+  StepArgs a{};
+  a.S = dev_scene(c);
+  a.M = dev_mixture(c);
+  a.target = c->target;
+  a.x = c->x;
+  a.score = c->score;
+  a.killed = c->killed;
+  a.logp = c->logp;
+  a.N = c->N;
+  a.d = c->d;
+  a.L = c->prm.max_path_len;
+  a.rng = Rng{(uint32_t)c->seed, (uint32_t)(c->seed >> 32), c->frame};
+  a.stddev = c->prm.stddev;
+  a.gamma_tilde = c->prm.gamma_tilde;
+  a.h = 1.0f / c->prm.dt;
+  a.eps = c->prm.eps;
+  a.k0 = c->k0;
+  a.rb = c->prm.rb_weight;
+  a.drift = c->prm.drift_mode;
+  a.tour_count = c->counters + 0;
+  a.rays = c->counters + 1;
+  a.node_visits = c->counters + 2;
+  a.tri_tests = c->counters + 3;
+  a.err = c->err;
+  return a;
+}
+
+int run_fd(dr_ctx* c) {
+  FdArgs f{};
+  f.S = dev_scene(c);
+  f.M = dev_mixture(c);
+  f.target = c->target;
+  f.x = c->x;
+  f.score = c->score;
+  f.killed = c->killed;
+  f.N = c->N;
+  f.d = c->d;
+  f.L = c->prm.max_path_len;
+  f.eps = c->prm.eps;
+  f.fd_h = c->prm.fd_h;
+  f.rays = c->counters + 1;
+  f.err = c->err;
+  launch_fd_score(f, c->stream);
+  return check_launch("fd_score");
+}
+
+// one chain step (init = Alg. 1, else Alg. 2); records into the next slot
+int one_step(dr_ctx* c, bool init) {
+  if (!init && c->rec_count >= c->rec_cap) DR_TRY(flush(c));
+  StepArgs a = step_args(c);
+  a.init = init ? 1 : 0;
+  a.step = c->step;
+  a.rec = c->rec + (size_t)c->rec_count * c->N;
+  a.p_partial = init ? c->p_partial : nullptr;
+  launch_step(a, c->stats, c->stream);
+  DR_TRY(check_launch("restore_step"));
+  c->rec_count++;
+  if (c->prm.drift_mode == DR_DRIFT_FD) DR_TRY(run_fd(c));
+  return DR_OK;
+}
+
+bool capturing(cudaStream_t s) {
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &st) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return st != cudaStreamCaptureStatusNone;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dr_version(void) { return 100; }
+
+const char* dr_last_error(void) { return g_err.c_str(); }
+
+int dr_create(dr_ctx** out, int device, void* cuda_stream) {
+  if (!out) return fail(DR_ERR_INVALID_ARG, "dr_create: out is NULL");
+  *out = nullptr;
+  int n = 0;
+  DR_CUDA(cudaGetDeviceCount(&n));
+  if (device < 0 || device >= n) return fail(DR_ERR_INVALID_ARG, "dr_create: bad device index");
+  DR_CUDA(cudaSetDevice(device));
+  dr_ctx* c = new dr_ctx();
+  c->device = device;
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  int r = dalloc(&c->counters, 4);
+  if (r == DR_OK) r = dalloc(&c->err, 1);
+  if (r == DR_OK) r = dalloc(&c->p_sum, 1);
+  if (r != DR_OK) {
+    dr_destroy(c);
+    return r;
+  }
+  cudaMemsetAsync(c->counters, 0, 4 * sizeof(unsigned long long), c->stream);
+  cudaMemsetAsync(c->err, 0, sizeof(uint32_t), c->stream);
+  *out = c;
+  return check_launch("dr_create");
+}
+
+int dr_destroy(dr_ctx* c) {
+  if (!c) return DR_OK;
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  dfree(&c->nodes); dfree(&c->tris); dfree(&c->surf); dfree(&c->lights); dfree(&c->nrm); dfree(&c->mats);
+  dfree(&c->mw); dfree(&c->mmu); dfree(&c->msig);
+  dfree(&c->x); dfree(&c->score); dfree(&c->logp); dfree(&c->killed); dfree(&c->rec); dfree(&c->rec_alt);
+  if (c->sort_scratch) cudaFree(c->sort_scratch);
+  dfree(&c->accum); dfree(&c->counters); dfree(&c->p_partial); dfree(&c->p_sum); dfree(&c->err);
+  delete c;
+  return DR_OK;
+}
+
+int dr_scene_upload(dr_ctx* c, const float* verts, int32_t nv, const int32_t* tris, const float* normals, int32_t nt,
+                    const int32_t* tri_mat, const float* mats, int32_t nm, const float* camera, int32_t width,
+                    int32_t height) {
+  if (!c || !verts || !tris || !tri_mat || !mats || !camera)
+    return fail(DR_ERR_INVALID_ARG, "dr_scene_upload: NULL argument");
+  if (nv < 1 || nt < 1 || nm < 1 || width < 1 || height < 1 || (long long)width * height >= (1ll << 31))
+    return fail(DR_ERR_INVALID_ARG, "dr_scene_upload: bad size");
+  for (int i = 0; i < 3 * nt; ++i)
+    if (tris[i] < 0 || tris[i] >= nv) return fail(DR_ERR_INVALID_ARG, "dr_scene_upload: vertex index out of range");
+  for (int i = 0; i < nt; ++i)
+    if (tri_mat[i] < 0 || tri_mat[i] >= nm) return fail(DR_ERR_INVALID_ARG, "dr_scene_upload: material out of range");
+  for (int i = 0; i < nm; ++i) {
+    const float t = mats[12 * i];
+    if (!(t == 0.f || t == 1.f || t == 2.f || t == 3.f)) return fail(DR_ERR_INVALID_ARG, "dr_scene_upload: bad material type");
+    if (t == 1.f && !(mats[12 * i + 4] > 0.f)) return fail(DR_ERR_INVALID_ARG, "dr_scene_upload: glossy roughness must be > 0");
+    if (t == 2.f && !(mats[12 * i + 5] > 0.f)) return fail(DR_ERR_INVALID_ARG, "dr_scene_upload: dielectric ior must be > 0");
+  }
+  for (long long i = 0; i < 3ll * nv; ++i)
+    if (!std::isfinite(verts[i])) return fail(DR_ERR_INVALID_ARG, "dr_scene_upload: non-finite vertex");
+  DR_CUDA(cudaSetDevice(c->device));
+  DR_CUDA(cudaStreamSynchronize(c->stream));
+  // host-side scene constants: extent -> tmin, light table, camera basis
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  for (int i = 0; i < nv; ++i)
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = std::min(lo[a], (double)verts[3 * i + a]);
+      hi[a] = std::max(hi[a], (double)verts[3 * i + a]);
+    }
+  const double ext = std::max(hi[0] - lo[0], std::max(hi[1] - lo[1], hi[2] - lo[2]));
+  auto V = [&](int i) { return f3(verts[3 * i], verts[3 * i + 1], verts[3 * i + 2]); };
+  std::vector<int> lt;
+  std::vector<double> pw;
+  double tot = 0.0;
+  for (int i = 0; i < nt; ++i) {
+    const float* m = mats + 12 * tri_mat[i];
+    if (!(m[6] > 0.f || m[7] > 0.f || m[8] > 0.f)) continue;
+    const float3 a = V(tris[3 * i]), b = V(tris[3 * i + 1]), cc = V(tris[3 * i + 2]);
+    const float3 e1 = b - a, e2 = cc - a;
+    const float3 N = cross(e1, e2);
+    const double area = 0.5 * std::sqrt((double)dot(N, N));
+    const double p = area * (0.2126 * m[6] + 0.7152 * m[7] + 0.0722 * m[8]);
+    if (!(p > 0.0)) continue;
+    lt.push_back(i);
+    pw.push_back(p);
+    tot += p;
+  }
+  std::vector<float> sel(nt, 0.f);
+  std::vector<float4> lrec(4 * lt.size());
+  double acc = 0.0;
+  for (size_t k = 0; k < lt.size(); ++k) {
+    const int i = lt[k];
+    acc += pw[k];
+    const float3 a = V(tris[3 * i]), b = V(tris[3 * i + 1]), cc = V(tris[3 * i + 2]);
+    const float3 N = cross(b - a, cc - a);
+    const float area = 0.5f * sqrtf(dot(N, N));
+    sel[i] = (float)(pw[k] / tot);
+    lrec[4 * k + 0] = make_float4(a.x, a.y, a.z, hbits_f(i));
+    lrec[4 * k + 1] = make_float4(b.x, b.y, b.z, sel[i]);
+    lrec[4 * k + 2] = make_float4(cc.x, cc.y, cc.z, area);
+    lrec[4 * k + 3] = make_float4(k + 1 == lt.size() ? 1.0f : (float)(acc / tot), 0.f, 0.f, 0.f);
+  }
+  {
+    const double eye[3] = {camera[0], camera[1], camera[2]}, look[3] = {camera[3], camera[4], camera[5]},
+                 up[3] = {camera[6], camera[7], camera[8]};
+    double fw[3] = {look[0] - eye[0], look[1] - eye[1], look[2] - eye[2]};
+    double l = std::sqrt(fw[0] * fw[0] + fw[1] * fw[1] + fw[2] * fw[2]);
+    if (!(l > 0.0) || !(camera[9] > 0.f && camera[9] < 180.f))
+      return fail(DR_ERR_INVALID_ARG, "dr_scene_upload: degenerate camera");
+    for (double& v : fw) v /= l;
+    double rt[3] = {fw[1] * up[2] - fw[2] * up[1], fw[2] * up[0] - fw[0] * up[2], fw[0] * up[1] - fw[1] * up[0]};
+    l = std::sqrt(rt[0] * rt[0] + rt[1] * rt[1] + rt[2] * rt[2]);
+    if (!(l > 0.0)) return fail(DR_ERR_INVALID_ARG, "dr_scene_upload: camera up parallel to view");
+    for (double& v : rt) v /= l;
+    const double u2[3] = {rt[1] * fw[2] - rt[2] * fw[1], rt[2] * fw[0] - rt[0] * fw[2], rt[0] * fw[1] - rt[1] * fw[0]};
+    const double th = std::tan(0.5 * camera[9] * 3.14159265358979323846 / 180.0);
+    c->cam.eye = f3(camera[0], camera[1], camera[2]);
+    c->cam.fwd = f3((float)fw[0], (float)fw[1], (float)fw[2]);
+    c->cam.right = f3((float)rt[0], (float)rt[1], (float)rt[2]);
+    c->cam.up = f3((float)u2[0], (float)u2[1], (float)u2[2]);
+    c->cam.ty = (float)th;
+    c->cam.tx = (float)(th * width / height);
+  }
+  // device arrays
+  float* dverts = nullptr;
+  int* dtris = nullptr;
+  int* dmat = nullptr;
+  float* dsel = nullptr;
+  float* dvn = nullptr;
+  void* scratch = nullptr;
+  int r = DR_OK;
+  const int n_nodes = std::max(1, nt - 1);
+  r = dalloc(&dverts, 3 * (size_t)nv);
+  if (r == DR_OK) r = dalloc(&dtris, 3 * (size_t)nt);
+  if (r == DR_OK) r = dalloc(&dmat, (size_t)nt);
+  if (r == DR_OK) r = dalloc(&dsel, (size_t)nt);
+  if (r == DR_OK && normals) r = dalloc(&dvn, 3 * (size_t)nv);
+  if (r == DR_OK) r = dalloc(&c->nodes, 4 * (size_t)n_nodes);
+  if (r == DR_OK) r = dalloc(&c->tris, 3 * (size_t)nt);
+  if (r == DR_OK) r = dalloc(&c->surf, 5 * (size_t)nt);
+  if (r == DR_OK) r = dalloc(&c->mats, 12 * (size_t)nm);
+  if (r == DR_OK) r = dalloc(&c->lights, std::max<size_t>(4, lrec.size()));
+  if (r == DR_OK) r = normals ? dalloc(&c->nrm, 9 * (size_t)nt) : (dfree(&c->nrm), DR_OK);
+  if (r == DR_OK) {
+    cudaError_t e = cudaMalloc(&scratch, bvh_scratch_bytes(nt));
+    if (e != cudaSuccess) { cudaGetLastError(); r = fail(DR_ERR_OOM, "dr_scene_upload: BVH scratch"); }
+  }
+  if (r == DR_OK) {
+    cudaStream_t s = c->stream;
+    cudaMemcpyAsync(dverts, verts, 12 * (size_t)nv, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(dtris, tris, 12 * (size_t)nt, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(dmat, tri_mat, 4 * (size_t)nt, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(dsel, sel.data(), 4 * (size_t)nt, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(c->mats, mats, 48 * (size_t)nm, cudaMemcpyHostToDevice, s);
+    if (!lrec.empty()) cudaMemcpyAsync(c->lights, lrec.data(), 16 * lrec.size(), cudaMemcpyHostToDevice, s);
+    if (normals) {
+      cudaMemcpyAsync(dvn, normals, 12 * (size_t)nv, cudaMemcpyHostToDevice, s);
+      launch_gather_normals(dvn, dtris, nt, c->nrm, s);
+    }
+    launch_surface_records(dverts, dtris, dmat, dsel, dvn, nt, c->surf, s);
+    c->n_nodes = build_lbvh(dverts, dtris, nt, c->nodes, c->tris, scratch, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) r = fail(DR_ERR_CUDA, std::string("dr_scene_upload: ") + cudaGetErrorString(e));
+  }
+  dfree(&dverts); dfree(&dtris); dfree(&dmat); dfree(&dsel); dfree(&dvn);
+  if (scratch) cudaFree(scratch);
+  if (r != DR_OK) return r;
+  c->target = 0;
+  c->W = width;
+  c->H = height;
+  c->nt = nt;
+  c->n_lights = (int)lt.size();
+  c->tmin = (float)(1e-5 * ext);
+  c->inited = false;
+  return DR_OK;
+}
+
+int dr_target_mixture(dr_ctx* c, int32_t d, int32_t K, const float* w, const float* mu, const float* sig, float cval,
+                      int32_t width, int32_t height) {
+  if (!c) return fail(DR_ERR_INVALID_ARG, "dr_target_mixture: NULL ctx");
+  if (d < 2 || d > kMaxDim || (d & 1) || K < 0 || width < 1 || height < 1)
+    return fail(DR_ERR_INVALID_ARG, "dr_target_mixture: bad size");
+  if (K > 0 && (!w || !mu || !sig)) return fail(DR_ERR_INVALID_ARG, "dr_target_mixture: NULL arrays");
+  for (int k = 0; k < K; ++k)
+    if (!(sig[k] > 0.f)) return fail(DR_ERR_INVALID_ARG, "dr_target_mixture: sigma must be > 0");
+  DR_CUDA(cudaSetDevice(c->device));
+  DR_TRY(dalloc(&c->mw, std::max(1, K)));
+  DR_TRY(dalloc(&c->mmu, std::max(1, K * d)));
+  DR_TRY(dalloc(&c->msig, std::max(1, K)));
+  if (K > 0) {
+    DR_CUDA(cudaMemcpyAsync(c->mw, w, 4 * (size_t)K, cudaMemcpyHostToDevice, c->stream));
+    DR_CUDA(cudaMemcpyAsync(c->mmu, mu, 4 * (size_t)K * d, cudaMemcpyHostToDevice, c->stream));
+    DR_CUDA(cudaMemcpyAsync(c->msig, sig, 4 * (size_t)K, cudaMemcpyHostToDevice, c->stream));
+  }
+  DR_CUDA(cudaStreamSynchronize(c->stream));
+  c->target = 1;
+  c->mK = K;
+  c->md = d;
+  c->mcval = cval;
+  c->W = width;
+  c->H = height;
+  c->inited = false;
+  return DR_OK;
+}
+
+static int validate_params(const dr_params* p) {
+  if (!p) return fail(DR_ERR_INVALID_ARG, "params: NULL");
+  if (p->max_path_len < 1 || p->max_path_len > DR_MAX_PATH_LEN) return fail(DR_ERR_INVALID_ARG, "params: max_path_len");
+  if (p->drift_mode < 0 || p->drift_mode > 2) return fail(DR_ERR_INVALID_ARG, "params: drift_mode");
+  if (!(p->stddev > 0.f) || !(p->dt > 0.f) || !(p->eps > 0.f) || !(p->m > 0.f))
+    return fail(DR_ERR_INVALID_ARG, "params: stddev, dt, eps and m must be > 0");
+  if (!std::isfinite(p->gamma_tilde)) return fail(DR_ERR_INVALID_ARG, "params: gamma_tilde");
+  if (p->drift_mode == DR_DRIFT_FD && !(p->fd_h > 0.f && p->fd_h < 0.5f)) return fail(DR_ERR_INVALID_ARG, "params: fd_h");
+  if (p->steps_per_splat < 1 || p->steps_per_splat > 4096) return fail(DR_ERR_INVALID_ARG, "params: steps_per_splat");
+  return DR_OK;
+}
+
+static int alloc_chains(dr_ctx* c, unsigned long long N, int d, int spp) {
+  const size_t nd = (size_t)N * d;
+  if (nd > c->state_cap) {
+    DR_TRY(dalloc(&c->x, nd));
+    DR_TRY(dalloc(&c->score, nd));
+    c->state_cap = nd;
+  }
+  if (N > c->chains_cap) {
+    DR_TRY(dalloc(&c->logp, N));
+    DR_TRY(dalloc(&c->killed, N));
+    c->chains_cap = N;
+  }
+  const size_t nrec = (size_t)N * spp;
+  if (nrec > c->rec_cap_records) {
+    DR_TRY(dalloc(&c->rec, nrec));
+    DR_TRY(dalloc(&c->rec_alt, nrec));
+    if (c->sort_scratch) cudaFree(c->sort_scratch);
+    c->sort_scratch = nullptr;
+    cudaError_t e = cudaMalloc(&c->sort_scratch, sort_scratch_bytes(nrec));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      c->rec_cap_records = 0;
+      return fail(DR_ERR_OOM, "sort scratch");
+    }
+    c->rec_cap_records = nrec;
+  }
+  const size_t npart = (N + step_block_size() - 1) / step_block_size();
+  if (npart > c->p_partial_cap) {
+    DR_TRY(dalloc(&c->p_partial, npart));
+    c->p_partial_cap = npart;
+  }
+  const size_t na = (size_t)c->W * c->H * 3;
+  if (na != c->accum_n) {
+    DR_TRY(dalloc(&c->accum, na));
+    c->accum_n = na;
+  }
+  return DR_OK;
+}
+
+int dr_chains_init(dr_ctx* c, uint64_t n_chains, uint64_t seed, uint32_t frame, const dr_params* prm) {
+  if (!c) return fail(DR_ERR_INVALID_ARG, "dr_chains_init: NULL ctx");
+  DR_TRY(validate_params(prm));
+  if (c->target < 0) return fail(DR_ERR_STATE, "dr_chains_init: no scene or target uploaded");
+  if (n_chains < 1 || n_chains > (1ull << 31)) return fail(DR_ERR_INVALID_ARG, "dr_chains_init: n_chains");
+  if (frame >= (1u << 28)) return fail(DR_ERR_INVALID_ARG, "dr_chains_init: frame must be < 2^28");
+  const int d = c->target == 0 ? 2 + 4 * (prm->max_path_len - 1) : c->md;
+  DR_CUDA(cudaSetDevice(c->device));
+  DR_TRY(alloc_chains(c, n_chains, d, prm->steps_per_splat));
+  c->N = n_chains;
+  c->d = d;
+  c->prm = *prm;
+  c->seed = seed;
+  c->frame = frame;
+  c->step = 0;
+  c->rec_cap = prm->steps_per_splat;
+  c->rec_count = 0;
+  cudaStream_t s = c->stream;
+  DR_CUDA(cudaMemsetAsync(c->score, 0, (size_t)n_chains * d * 4, s));
+  DR_CUDA(cudaMemsetAsync(c->killed, 0, (size_t)n_chains, s));
+  DR_CUDA(cudaMemsetAsync(c->accum, 0, c->accum_n * 8, s));
+  DR_CUDA(cudaMemsetAsync(c->counters, 0, 4 * 8, s));
+  DR_CUDA(cudaMemsetAsync(c->err, 0, 4, s));
+  c->p_lambda = 0.0;
+  if (prm->k0 > 0.0) {
+    c->k0 = prm->k0;
+  } else {
+    StepArgs a = step_args(c);
+    a.init = 1;
+    a.estimate_only = 1;
+    a.step = 0;
+    a.rec = nullptr;
+    a.tour_count = nullptr;
+    a.p_partial = c->p_partial;
+    launch_step(a, false, s);
+    DR_TRY(check_launch("init estimate"));
+    const int nb = (int)((n_chains + step_block_size() - 1) / step_block_size());
+    launch_sum_doubles(c->p_partial, nb, c->p_sum, s);
+    double sum = 0.0;
+    DR_CUDA(cudaMemcpyAsync(&sum, c->p_sum, 8, cudaMemcpyDeviceToHost, s));
+    DR_CUDA(cudaStreamSynchronize(s));
+    c->p_lambda = sum / (double)n_chains;
+    if (!(c->p_lambda > 0.0) || !std::isfinite(c->p_lambda))
+      return fail(DR_ERR_STATE, "dr_chains_init: estimated p_lambda is not positive");
+    c->k0 = c->p_lambda / ((double)prm->m * (double)prm->dt);
+    DR_CUDA(cudaMemsetAsync(c->counters, 0, 4 * 8, s));
+  }
+  c->inited = true;
+  DR_TRY(one_step(c, true));
+  return DR_OK;
+}
+
+int dr_step(dr_ctx* c, uint32_t n_steps) {
+  if (!c) return fail(DR_ERR_INVALID_ARG, "dr_step: NULL ctx");
+  if (!c->inited) return fail(DR_ERR_STATE, "dr_step: chains not initialised");
+  DR_CUDA(cudaSetDevice(c->device));
+  for (uint32_t i = 0; i < n_steps; ++i) {
+    c->step++;
+    DR_TRY(one_step(c, false));
+  }
+  return DR_OK;
+}
+
+int dr_splat(dr_ctx* c) {
+  if (!c) return fail(DR_ERR_INVALID_ARG, "dr_splat: NULL ctx");
+  if (!c->inited) return fail(DR_ERR_STATE, "dr_splat: chains not initialised");
+  DR_CUDA(cudaSetDevice(c->device));
+  return flush(c);
+}
+
+int dr_resolve(dr_ctx* c, float* out_rgb) {
+  if (!c || !out_rgb) return fail(DR_ERR_INVALID_ARG, "dr_resolve: NULL argument");
+  if (!c->inited) return fail(DR_ERR_STATE, "dr_resolve: chains not initialised");
+  DR_CUDA(cudaSetDevice(c->device));
+  DR_TRY(flush(c));
+  launch_resolve(c->accum, c->accum_n, c->counters, c->k0, out_rgb, c->stream);
+  DR_TRY(check_launch("resolve"));
+  if (!capturing(c->stream)) {
+    unsigned long long tc = 0;
+    DR_CUDA(cudaMemcpyAsync(&tc, c->counters, 8, cudaMemcpyDeviceToHost, c->stream));
+    DR_CUDA(cudaStreamSynchronize(c->stream));
+    if (tc == 0) return fail(DR_ERR_STATE, "dr_resolve: tourCount is 0 (no completed tour yet)");
+  }
+  return DR_OK;
+}
+
+int dr_readback_state(dr_ctx* c, float* x, float* score, uint8_t* killed, float* logp, int32_t* pix, float* val) {
+  if (!c) return fail(DR_ERR_INVALID_ARG, "dr_readback_state: NULL ctx");
+  if (!c->inited) return fail(DR_ERR_STATE, "dr_readback_state: chains not initialised");
+  if ((pix || val) && c->rec_count == 0)
+    return fail(DR_ERR_STATE, "dr_readback_state: last records were already splatted");
+  DR_CUDA(cudaSetDevice(c->device));
+  const size_t N = c->N, d = c->d;
+  std::vector<float> tmp;
+  auto soa = [&](const float* src, float* dst) -> int {
+    tmp.resize(N * d);
+    DR_CUDA(cudaMemcpyAsync(tmp.data(), src, N * d * 4, cudaMemcpyDeviceToHost, c->stream));
+    DR_CUDA(cudaStreamSynchronize(c->stream));
+    for (size_t i = 0; i < d; ++i)
+      for (size_t j = 0; j < N; ++j) dst[j * d + i] = tmp[i * N + j];
+    return DR_OK;
+  };
+  if (x) DR_TRY(soa(c->x, x));
+  if (score) DR_TRY(soa(c->score, score));
+  if (killed) DR_CUDA(cudaMemcpyAsync(killed, c->killed, N, cudaMemcpyDeviceToHost, c->stream));
+  if (logp) DR_CUDA(cudaMemcpyAsync(logp, c->logp, N * 4, cudaMemcpyDeviceToHost, c->stream));
+  if (pix || val) {
+    std::vector<SplatRec> r(N);
+    DR_CUDA(cudaMemcpyAsync(r.data(), c->rec + (size_t)(c->rec_count - 1) * N, N * sizeof(SplatRec),
+                            cudaMemcpyDeviceToHost, c->stream));
+    DR_CUDA(cudaStreamSynchronize(c->stream));
+    for (size_t j = 0; j < N; ++j) {
+      if (pix) pix[j] = (int32_t)r[j].pix;
+      if (val) { val[3 * j] = r[j].r; val[3 * j + 1] = r[j].g; val[3 * j + 2] = r[j].b; }
+    }
+  }
+  DR_CUDA(cudaStreamSynchronize(c->stream));
+  return check_device_error(c);
+}
+
+int dr_readback_accum(dr_ctx* c, double* accum) {
+  if (!c || !accum) return fail(DR_ERR_INVALID_ARG, "dr_readback_accum: NULL argument");
+  if (!c->inited) return fail(DR_ERR_STATE, "dr_readback_accum: chains not initialised");
+  DR_CUDA(cudaSetDevice(c->device));
+  DR_TRY(flush(c));
+  DR_CUDA(cudaMemcpyAsync(accum, c->accum, c->accum_n * 8, cudaMemcpyDeviceToHost, c->stream));
+  DR_CUDA(cudaStreamSynchronize(c->stream));
+  return check_device_error(c);
+}
+
+int dr_get_counters(dr_ctx* c, uint64_t* tour_count, double* k0, uint64_t* steps, uint64_t* rays, double* p_lambda) {
+  if (!c) return fail(DR_ERR_INVALID_ARG, "dr_get_counters: NULL ctx");
+  DR_CUDA(cudaSetDevice(c->device));
+  unsigned long long h[4] = {0, 0, 0, 0};
+  DR_CUDA(cudaMemcpyAsync(h, c->counters, 32, cudaMemcpyDeviceToHost, c->stream));
+  DR_CUDA(cudaStreamSynchronize(c->stream));
+  if (tour_count) *tour_count = h[0];
+  if (rays) *rays = h[1];
+  if (k0) *k0 = c->k0;
+  if (steps) *steps = c->step;
+  if (p_lambda) *p_lambda = c->p_lambda;
+  return check_device_error(c);
+}
+
+int dr_eval_logp(dr_ctx* c, int32_t L, const float* x, int64_t M, float* logp, float* grad, int32_t* pix, float* f) {
+  if (!c || !x || !logp) return fail(DR_ERR_INVALID_ARG, "dr_eval_logp: NULL argument");
+  if (c->target < 0) return fail(DR_ERR_STATE, "dr_eval_logp: no scene or target");
+  if (M < 0) return fail(DR_ERR_INVALID_ARG, "dr_eval_logp: M < 0");
+  if (c->target == 0 && (L < 1 || L > DR_MAX_PATH_LEN)) return fail(DR_ERR_INVALID_ARG, "dr_eval_logp: L");
+  DR_CUDA(cudaSetDevice(c->device));
+  EvalArgs a{};
+  a.S = dev_scene(c);
+  a.M = dev_mixture(c);
+  a.target = c->target;
+  a.x = x;
+  a.logp = logp;
+  a.grad = grad;
+  a.pix = pix;
+  a.f = f;
+  a.Mpts = M;
+  a.d = c->target == 0 ? 2 + 4 * (L - 1) : c->md;
+  a.L = L;
+  a.eps = c->inited ? c->prm.eps : 1e-8f;
+  a.err = c->err;
+  launch_eval(a, c->stream);
+  return check_launch("eval_logp");
+}
+
+int dr_trace_closest(dr_ctx* c, const float* rays, int64_t n, int32_t exclude, int32_t* tri, float* t) {
+  if (!c || !rays || !tri || !t) return fail(DR_ERR_INVALID_ARG, "dr_trace_closest: NULL argument");
+  if (c->target != 0) return fail(DR_ERR_STATE, "dr_trace_closest: no scene");
+  DR_CUDA(cudaSetDevice(c->device));
+  launch_trace(dev_scene(c), rays, n, exclude, tri, t, c->err, c->stream);
+  return check_launch("trace_closest");
+}
+
+int dr_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int64_t n, void* stream) {
+  if (!ctr || !key || !out || n < 0) return fail(DR_ERR_INVALID_ARG, "dr_philox: bad argument");
+  launch_philox(ctr, key, out, n, static_cast<cudaStream_t>(stream));
+  return check_launch("philox");
+}
+
+int dr_splat_records(dr_ctx* c, const void* recs, int64_t M) {
+  if (!c || (!recs && M > 0) || M < 0) return fail(DR_ERR_INVALID_ARG, "dr_splat_records: bad argument");
+  if (c->accum_n == 0) return fail(DR_ERR_STATE, "dr_splat_records: no image (init chains first)");
+  if (M == 0) return DR_OK;
+  DR_CUDA(cudaSetDevice(c->device));
+  SplatRec* a = nullptr;
+  SplatRec* b = nullptr;
+  void* scratch = nullptr;
+  int r = dalloc(&a, (size_t)M);
+  if (r == DR_OK) r = dalloc(&b, (size_t)M);
+  if (r == DR_OK && cudaMalloc(&scratch, sort_scratch_bytes((size_t)M)) != cudaSuccess) {
+    cudaGetLastError();
+    scratch = nullptr;
+    r = fail(DR_ERR_OOM, "dr_splat_records: scratch");
+  }
+  if (r == DR_OK) {
+    cudaMemcpyAsync(a, recs, (size_t)M * sizeof(SplatRec), cudaMemcpyDeviceToDevice, c->stream);
+    SplatRec* sorted = sort_splat_records(a, b, (size_t)M, key_bits((long long)c->W * c->H), scratch, c->stream);
+    launch_segment_reduce(sorted, (size_t)M, c->accum, (uint32_t)((size_t)c->W * c->H), c->err, c->stream);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) r = fail(DR_ERR_CUDA, std::string("dr_splat_records: ") + cudaGetErrorString(e));
+  }
+  dfree(&a);
+  dfree(&b);
+  if (scratch) cudaFree(scratch);
+  return r;
+}
+
+int dr_clear_image(dr_ctx* c) {
+  if (!c) return fail(DR_ERR_INVALID_ARG, "dr_clear_image: NULL ctx");
+  if (!c->inited) return fail(DR_ERR_STATE, "dr_clear_image: chains not initialised");
+  DR_CUDA(cudaSetDevice(c->device));
+  c->rec_count = 0;
+  DR_CUDA(cudaMemsetAsync(c->accum, 0, c->accum_n * 8, c->stream));
+  DR_CUDA(cudaMemsetAsync(c->counters, 0, 8, c->stream));
+  return DR_OK;
+}
+
+namespace {
+struct SaveHeader {
+  uint64_t magic, version, N, seed, step;
+  int32_t d, W, H, frame;
+  dr_params prm;
+  double k0, p_lambda;
+  uint64_t counters[4];
+};
+constexpr uint64_t kMagic = 0x3152545345524644ull;  // "DFRESTR1"
+}  // namespace
+
+int dr_state_save(dr_ctx* c, void* host_buf, size_t* bytes) {
+  if (!c || !bytes) return fail(DR_ERR_INVALID_ARG, "dr_state_save: NULL argument");
+  if (!c->inited) return fail(DR_ERR_STATE, "dr_state_save: chains not initialised");
+  const size_t nd = (size_t)c->N * c->d;
+  const size_t need = sizeof(SaveHeader) + nd * 8 + c->N * 5 + c->accum_n * 8;
+  if (!host_buf) {
+    *bytes = need;
+    return DR_OK;
+  }
+  if (*bytes < need) return fail(DR_ERR_INVALID_ARG, "dr_state_save: buffer too small");
+  DR_CUDA(cudaSetDevice(c->device));
+  DR_TRY(flush(c));
+  SaveHeader h{};
+  h.magic = kMagic;
+  h.version = 1;
+  h.N = c->N;
+  h.seed = c->seed;
+  h.step = c->step;
+  h.d = c->d;
+  h.W = c->W;
+  h.H = c->H;
+  h.frame = (int32_t)c->frame;
+  h.prm = c->prm;
+  h.k0 = c->k0;
+  h.p_lambda = c->p_lambda;
+  DR_CUDA(cudaMemcpyAsync(h.counters, c->counters, 32, cudaMemcpyDeviceToHost, c->stream));
+  char* p = static_cast<char*>(host_buf) + sizeof(SaveHeader);
+  DR_CUDA(cudaMemcpyAsync(p, c->x, nd * 4, cudaMemcpyDeviceToHost, c->stream)); p += nd * 4;
+  DR_CUDA(cudaMemcpyAsync(p, c->score, nd * 4, cudaMemcpyDeviceToHost, c->stream)); p += nd * 4;
+  DR_CUDA(cudaMemcpyAsync(p, c->logp, c->N * 4, cudaMemcpyDeviceToHost, c->stream)); p += c->N * 4;
+  DR_CUDA(cudaMemcpyAsync(p, c->killed, c->N, cudaMemcpyDeviceToHost, c->stream)); p += c->N;
+  DR_CUDA(cudaMemcpyAsync(p, c->accum, c->accum_n * 8, cudaMemcpyDeviceToHost, c->stream));
+  DR_CUDA(cudaStreamSynchronize(c->stream));
+  std::memcpy(host_buf, &h, sizeof(h));
+  *bytes = need;
+  return DR_OK;
+}
+
+int dr_state_load(dr_ctx* c, const void* host_buf, size_t bytes) {
+  if (!c || !host_buf) return fail(DR_ERR_INVALID_ARG, "dr_state_load: NULL argument");
+  if (bytes < sizeof(SaveHeader)) return fail(DR_ERR_INVALID_ARG, "dr_state_load: buffer too small");
+  SaveHeader h;
+  std::memcpy(&h, host_buf, sizeof(h));
+  if (h.magic != kMagic || h.version != 1) return fail(DR_ERR_INVALID_ARG, "dr_state_load: not a checkpoint");
+  if (c->target < 0) return fail(DR_ERR_STATE, "dr_state_load: upload the scene or target first");
+  const int d = c->target == 0 ? 2 + 4 * (h.prm.max_path_len - 1) : c->md;
+  if (d != h.d || h.W != c->W || h.H != c->H) return fail(DR_ERR_INVALID_ARG, "dr_state_load: shape mismatch");
+  DR_TRY(validate_params(&h.prm));
+  const size_t nd = (size_t)h.N * h.d;
+  const size_t need = sizeof(SaveHeader) + nd * 8 + h.N * 5 + (size_t)h.W * h.H * 3 * 8;
+  if (bytes < need) return fail(DR_ERR_INVALID_ARG, "dr_state_load: truncated checkpoint");
+  DR_CUDA(cudaSetDevice(c->device));
+  DR_TRY(alloc_chains(c, h.N, h.d, h.prm.steps_per_splat));
+  c->N = h.N;
+  c->d = h.d;
+  c->prm = h.prm;
+  c->seed = h.seed;
+  c->frame = (uint32_t)h.frame;
+  c->step = (uint32_t)h.step;
+  c->k0 = h.k0;
+  c->p_lambda = h.p_lambda;
+  c->rec_cap = h.prm.steps_per_splat;
+  c->rec_count = 0;
+  const char* p = static_cast<const char*>(host_buf) + sizeof(SaveHeader);
+  DR_CUDA(cudaMemcpyAsync(c->x, p, nd * 4, cudaMemcpyHostToDevice, c->stream)); p += nd * 4;
+  DR_CUDA(cudaMemcpyAsync(c->score, p, nd * 4, cudaMemcpyHostToDevice, c->stream)); p += nd * 4;
+  DR_CUDA(cudaMemcpyAsync(c->logp, p, h.N * 4, cudaMemcpyHostToDevice, c->stream)); p += h.N * 4;
+  DR_CUDA(cudaMemcpyAsync(c->killed, p, h.N, cudaMemcpyHostToDevice, c->stream)); p += h.N;
+  DR_CUDA(cudaMemcpyAsync(c->accum, p, c->accum_n * 8, cudaMemcpyHostToDevice, c->stream));
+  DR_CUDA(cudaMemcpyAsync(c->counters, h.counters, 32, cudaMemcpyHostToDevice, c->stream));
+  DR_CUDA(cudaMemsetAsync(c->err, 0, 4, c->stream));
+  DR_CUDA(cudaStreamSynchronize(c->stream));
+  c->inited = true;
+  return DR_OK;
+}
+
+int dr_set_stats(dr_ctx* c, int enable) {
+  if (!c) return fail(DR_ERR_INVALID_ARG, "dr_set_stats: NULL ctx");
+  DR_CUDA(cudaSetDevice(c->device));
+  c->stats = enable != 0;
+  if (c->stats) {
+    DR_CUDA(cudaMemsetAsync(c->counters + 1, 0, 24, c->stream));
+  }
+  return DR_OK;
+}
+
+int dr_get_traversal_stats(dr_ctx* c, uint64_t* node_visits, uint64_t* tri_tests, uint64_t* rays) {
+  if (!c) return fail(DR_ERR_INVALID_ARG, "dr_get_traversal_stats: NULL ctx");
+  DR_CUDA(cudaSetDevice(c->device));
+  unsigned long long h[4];
+  DR_CUDA(cudaMemcpyAsync(h, c->counters, 32, cudaMemcpyDeviceToHost, c->stream));
+  DR_CUDA(cudaStreamSynchronize(c->stream));
+  if (rays) *rays = h[1];
+  if (node_visits) *node_visits = h[2];
+  if (tri_tests) *tri_tests = h[3];
+  return DR_OK;
+}
+
+int dr_bvh_info(dr_ctx* c, int32_t* n_nodes, int32_t* n_tris, int32_t* max_depth) {
+  if (!c) return fail(DR_ERR_INVALID_ARG, "dr_bvh_info: NULL ctx");
+  if (c->target != 0) return fail(DR_ERR_STATE, "dr_bvh_info: no scene");
+  DR_CUDA(cudaSetDevice(c->device));
+  const int nn = std::max(1, c->n_nodes);
+  std::vector<float4> nodes((size_t)nn * 4);
+  DR_CUDA(cudaMemcpyAsync(nodes.data(), c->nodes, nodes.size() * 16, cudaMemcpyDeviceToHost, c->stream));
+  DR_CUDA(cudaStreamSynchronize(c->stream));
+  int depth = 0;
+  std::vector<std::pair<int, int>> st{{0, 1}};
+  while (!st.empty()) {
+    auto [n, dd] = st.back();
+    st.pop_back();
+    if (n < 0 || n >= nn) return fail(DR_ERR_DEVICE_CHECK, "dr_bvh_info: corrupt node index");
+    depth = std::max(depth, dd);
+    const int c0 = hbits_i(nodes[4 * n + 3].x), c1 = hbits_i(nodes[4 * n + 3].y);
+    if (c0 >= 0) st.push_back({c0, dd + 1});
+    if (c1 >= 0) st.push_back({c1, dd + 1});
+    if ((int)st.size() > 4 * nn + 8) return fail(DR_ERR_DEVICE_CHECK, "dr_bvh_info: cycle in BVH");
+  }
+  if (n_nodes) *n_nodes = c->n_nodes;
+  if (n_tris) *n_tris = c->nt;
+  if (max_depth) *max_depth = depth;
+  return DR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,297 @@
+// BVH construction on the GPU (linear BVH: Morton codes of triangle
+// centroids, radix sort, Karras 2012 "Maximizing Parallelism in the
+// Construction of BVHs, Octrees, and k-d Trees" hierarchy emission, then a
+// bottom-up box pass).  The paper uses the graphics API's hardware
+// acceleration structure (Sec. 4.3); this replaces it for software traversal.
+#include "dr_internal.h"
+
+namespace dr {
+
+namespace {
+
+constexpr int kB = 256;
+
+size_t a256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+struct BvhScratch {
+  uint2* keys0;     // (morton, tri)
+  uint2* keys1;
+  float* cbox;      // per block centroid bounds partials: 6 floats
+  float* gbox;      // 6 floats: global centroid bounds
+  int* parent;      // 2n - 1 (internal 0..n-2, leaves n-1..2n-2)
+  int* child;       // 2 per internal node (encoded: >= 0 internal, leaf -> n - 1 + k)
+  float* box;       // 6 floats per node (internal + leaf), [2n - 1][6]
+  unsigned* flag;   // n - 1
+  void* sort_scratch;
+};
+
+BvhScratch carve(void* p, int n) {
+  BvhScratch s;
+  char* c = static_cast<char*>(p);
+  const size_t nn = (size_t)n;
+  const int nblk = (n + kB - 1) / kB;
+  s.keys0 = reinterpret_cast<uint2*>(c); c += a256(nn * 8);
+  s.keys1 = reinterpret_cast<uint2*>(c); c += a256(nn * 8);
+  s.cbox = reinterpret_cast<float*>(c); c += a256((size_t)nblk * 6 * 4);
+  s.gbox = reinterpret_cast<float*>(c); c += a256(6 * 4);
+  s.parent = reinterpret_cast<int*>(c); c += a256((2 * nn) * 4);
+  s.child = reinterpret_cast<int*>(c); c += a256((2 * nn) * 4);
+  s.box = reinterpret_cast<float*>(c); c += a256((2 * nn) * 6 * 4);
+  s.flag = reinterpret_cast<unsigned*>(c); c += a256(nn * 4);
+  s.sort_scratch = c;
+  return s;
+}
+
+DR_D float3 vtx(const float* v, int i) { return f3(v[3 * i], v[3 * i + 1], v[3 * i + 2]); }
+
+__global__ void centroid_bounds_kernel(const float* __restrict__ verts, const int* __restrict__ tris, int n,
+                                       float* __restrict__ partial) {
+  __shared__ float sh[6][kB];
+  const int i = blockIdx.x * kB + threadIdx.x;
+  float lo[3] = {3.4e38f, 3.4e38f, 3.4e38f}, hi[3] = {-3.4e38f, -3.4e38f, -3.4e38f};
+  if (i < n) {
+    const float3 c = (vtx(verts, tris[3 * i]) + vtx(verts, tris[3 * i + 1]) + vtx(verts, tris[3 * i + 2])) * (1.0f / 3.0f);
+    lo[0] = hi[0] = c.x; lo[1] = hi[1] = c.y; lo[2] = hi[2] = c.z;
+  }
+  for (int a = 0; a < 3; ++a) { sh[a][threadIdx.x] = lo[a]; sh[3 + a][threadIdx.x] = hi[a]; }
+  __syncthreads();
+  for (int o = kB / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      for (int a = 0; a < 3; ++a) {
+        sh[a][threadIdx.x] = fminf(sh[a][threadIdx.x], sh[a][threadIdx.x + o]);
+        sh[3 + a][threadIdx.x] = fmaxf(sh[3 + a][threadIdx.x], sh[3 + a][threadIdx.x + o]);
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x < 6) partial[blockIdx.x * 6 + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+__global__ void bounds_final_kernel(const float* __restrict__ partial, int nblk, float* __restrict__ out) {
+  if (threadIdx.x >= 6) return;
+  const int a = threadIdx.x;
+  float v = a < 3 ? 3.4e38f : -3.4e38f;
+  for (int b = 0; b < nblk; ++b) v = a < 3 ? fminf(v, partial[b * 6 + a]) : fmaxf(v, partial[b * 6 + a]);
+  out[a] = v;
+}
+
+DR_D uint32_t expand10(uint32_t v) {
+  v = (v * 0x00010001u) & 0xFF0000FFu;
+  v = (v * 0x00000101u) & 0x0F00F00Fu;
+  v = (v * 0x00000011u) & 0xC30C30C3u;
+  v = (v * 0x00000005u) & 0x49249249u;
+  return v;
+}
+
+__global__ void morton_kernel(const float* __restrict__ verts, const int* __restrict__ tris, int n,
+                              const float* __restrict__ gbox, uint2* __restrict__ keys) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float3 c = (vtx(verts, tris[3 * i]) + vtx(verts, tris[3 * i + 1]) + vtx(verts, tris[3 * i + 2])) * (1.0f / 3.0f);
+  const float lo[3] = {gbox[0], gbox[1], gbox[2]}, hi[3] = {gbox[3], gbox[4], gbox[5]};
+  const float cc[3] = {c.x, c.y, c.z};
+  uint32_t q[3];
+  for (int a = 0; a < 3; ++a) {
+    const float ext = hi[a] - lo[a];
+    float u = ext > 0.0f ? (cc[a] - lo[a]) / ext : 0.5f;
+    u = fminf(fmaxf(u, 0.0f), 1.0f);
+    q[a] = (uint32_t)fminf(u * 1024.0f, 1023.0f);
+  }
+  keys[i] = make_uint2((expand10(q[0]) << 2) | (expand10(q[1]) << 1) | expand10(q[2]), (uint32_t)i);
+}
+
+// common-prefix length of sorted keys i, j (ties broken by index)
+DR_D int delta(const uint2* __restrict__ k, int n, int i, int j) {
+  if (j < 0 || j >= n) return -1;
+  const uint32_t a = k[i].x, b = k[j].x;
+  if (a != b) return __clz(a ^ b);
+  return 32 + __clz((uint32_t)i ^ (uint32_t)j);
+}
+
+__global__ void hierarchy_kernel(const uint2* __restrict__ k, int n, int* __restrict__ child, int* __restrict__ parent) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n - 1) return;
+  const int dirn = (delta(k, n, i, i + 1) - delta(k, n, i, i - 1)) >= 0 ? 1 : -1;
+  const int dmin = delta(k, n, i, i - dirn);
+  int lmax = 2;
+  while (delta(k, n, i, i + lmax * dirn) > dmin) lmax <<= 1;
+  int l = 0;
+  for (int t = lmax >> 1; t >= 1; t >>= 1)
+    if (delta(k, n, i, i + (l + t) * dirn) > dmin) l += t;
+  const int j = i + l * dirn;
+  const int dnode = delta(k, n, i, j);
+  // binary search for the split; t halves (rounding up) until it reaches 1,
+  // and a degenerate l = 0 exits after one pass
+  int s = 0;
+  int t = l;
+  do {
+    t = (t + 1) >> 1;
+    if (delta(k, n, i, i + (s + t) * dirn) > dnode) s += t;
+  } while (t > 1);
+  const int g = i + s * dirn + min(dirn, 0);
+  const int lo = min(i, j), hi = max(i, j);
+  const int left = lo == g ? (n - 1) + g : g;
+  const int right = hi == g + 1 ? (n - 1) + g + 1 : g + 1;
+  child[2 * i] = left;
+  child[2 * i + 1] = right;
+  parent[left] = i;
+  parent[right] = i;
+}
+
+__global__ void leaf_boxes_kernel(const float* __restrict__ verts, const int* __restrict__ tris,
+                                  const uint2* __restrict__ k, int n, float* __restrict__ box,
+                                  float4* __restrict__ tri_out, unsigned* __restrict__ flag) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n - 1) flag[i] = 0u;
+  if (i >= n) return;
+  const int t = (int)k[i].y;
+  const float3 v0 = vtx(verts, tris[3 * t]), v1 = vtx(verts, tris[3 * t + 1]), v2 = vtx(verts, tris[3 * t + 2]);
+  float* b = box + (size_t)(n - 1 + i) * 6;
+  b[0] = fminf(v0.x, fminf(v1.x, v2.x)); b[1] = fminf(v0.y, fminf(v1.y, v2.y)); b[2] = fminf(v0.z, fminf(v1.z, v2.z));
+  b[3] = fmaxf(v0.x, fmaxf(v1.x, v2.x)); b[4] = fmaxf(v0.y, fmaxf(v1.y, v2.y)); b[5] = fmaxf(v0.z, fmaxf(v1.z, v2.z));
+  const float3 e1 = v1 - v0, e2 = v2 - v0;
+  tri_out[3 * i + 0] = make_float4(v0.x, v0.y, v0.z, __int_as_float(t));
+  tri_out[3 * i + 1] = make_float4(e1.x, e1.y, e1.z, 0.0f);
+  tri_out[3 * i + 2] = make_float4(e2.x, e2.y, e2.z, 0.0f);
+}
+
+// Bottom-up boxes: the second child to arrive at a node computes its box.
+__global__ void internal_boxes_kernel(int n, const int* __restrict__ child, const int* __restrict__ parent,
+                                      float* box, unsigned* flag) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int node = n - 1 + i;
+  // a leaf is at most n - 1 levels deep; the cap only guards a corrupt tree
+  for (int guard = 0; node != 0 && guard < n; ++guard) {
+    const int p = parent[node];
+    if (p < 0 || p >= n - 1) return;
+    __threadfence();
+    if (atomicAdd(&flag[p], 1u) == 0u) return;
+    __threadfence();
+    const int a = child[2 * p], b = child[2 * p + 1];
+    volatile float* ba = box + (size_t)a * 6;
+    volatile float* bb = box + (size_t)b * 6;
+    float* bp = box + (size_t)p * 6;
+    for (int q = 0; q < 3; ++q) {
+      bp[q] = fminf(ba[q], bb[q]);
+      bp[3 + q] = fmaxf(ba[3 + q], bb[3 + q]);
+    }
+    node = p;
+  }
+}
+
+__global__ void emit_nodes_kernel(int n, const int* __restrict__ child, const float* __restrict__ box,
+                                  float4* __restrict__ nodes) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n - 1) return;
+  const int a = child[2 * i], b = child[2 * i + 1];
+  const float* ba = box + (size_t)a * 6;
+  const float* bb = box + (size_t)b * 6;
+  const int ca = a >= n - 1 ? leaf_code(a - (n - 1), 1) : a;
+  const int cb = b >= n - 1 ? leaf_code(b - (n - 1), 1) : b;
+  nodes[4 * i + 0] = make_float4(ba[0], ba[1], ba[2], ba[3]);
+  nodes[4 * i + 1] = make_float4(ba[4], ba[5], bb[0], bb[1]);
+  nodes[4 * i + 2] = make_float4(bb[2], bb[3], bb[4], bb[5]);
+  nodes[4 * i + 3] = make_float4(__int_as_float(ca), __int_as_float(cb), 0.0f, 0.0f);
+}
+
+// single triangle: root with one leaf child and one empty box
+__global__ void single_root_kernel(const float* __restrict__ verts, const int* __restrict__ tris,
+                                   float4* __restrict__ nodes, float4* __restrict__ tri_out) {
+  const float3 v0 = vtx(verts, tris[0]), v1 = vtx(verts, tris[1]), v2 = vtx(verts, tris[2]);
+  const float3 lo = f3(fminf(v0.x, fminf(v1.x, v2.x)), fminf(v0.y, fminf(v1.y, v2.y)), fminf(v0.z, fminf(v1.z, v2.z)));
+  const float3 hi = f3(fmaxf(v0.x, fmaxf(v1.x, v2.x)), fmaxf(v0.y, fmaxf(v1.y, v2.y)), fmaxf(v0.z, fmaxf(v1.z, v2.z)));
+  const float inf = __int_as_float(0x7f800000);
+  nodes[0] = make_float4(lo.x, lo.y, lo.z, hi.x);
+  nodes[1] = make_float4(hi.y, hi.z, inf, inf);
+  nodes[2] = make_float4(inf, -inf, -inf, -inf);
+  nodes[3] = make_float4(__int_as_float(leaf_code(0, 1)), __int_as_float(leaf_code(0, 1)), 0.0f, 0.0f);
+  const float3 e1 = v1 - v0, e2 = v2 - v0;
+  tri_out[0] = make_float4(v0.x, v0.y, v0.z, __int_as_float(0));
+  tri_out[1] = make_float4(e1.x, e1.y, e1.z, 0.0f);
+  tri_out[2] = make_float4(e2.x, e2.y, e2.z, 0.0f);
+}
+
+// Surface record of each triangle; flag bit 0 of s2.w = shading normals
+// (all three vertex normals non-zero).
+__global__ void surface_kernel(const float* __restrict__ verts, const int* __restrict__ tris,
+                               const int* __restrict__ tri_mat, const float* __restrict__ sel,
+                               const float* __restrict__ vn, int n, float4* __restrict__ surf) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float3 v0 = vtx(verts, tris[3 * i]), v1 = vtx(verts, tris[3 * i + 1]), v2 = vtx(verts, tris[3 * i + 2]);
+  const float3 e1 = v1 - v0, e2 = v2 - v0;
+  const float3 N = cross(e1, e2);
+  const float nn = dot(N, N);
+  const float3 ng = N * rsqrtf(nn);
+  const float3 au = cross(e2, N) * (1.0f / nn);
+  const float3 av = cross(N, e1) * (1.0f / nn);
+  surf[5 * i + 0] = make_float4(v0.x, v0.y, v0.z, __int_as_float(tri_mat[i]));
+  surf[5 * i + 1] = make_float4(N.x, N.y, N.z, 0.5f * sqrtf(nn));
+  int flags = 0;
+  if (vn) {
+    bool ok = true;
+    for (int k = 0; k < 3; ++k) {
+      const int v = tris[3 * i + k];
+      ok = ok && (vn[3 * v] != 0.0f || vn[3 * v + 1] != 0.0f || vn[3 * v + 2] != 0.0f);
+    }
+    flags |= ok ? 1 : 0;
+  }
+  surf[5 * i + 2] = make_float4(ng.x, ng.y, ng.z, __int_as_float(flags));
+  surf[5 * i + 3] = make_float4(au.x, au.y, au.z, sel ? sel[i] : 0.0f);
+  surf[5 * i + 4] = make_float4(av.x, av.y, av.z, 0.0f);
+}
+
+__global__ void gather_normals_kernel(const float* __restrict__ vn, const int* __restrict__ tris, int n,
+                                      float* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int k = 0; k < 3; ++k) {
+    const int v = tris[3 * i + k];
+    out[9 * i + 3 * k + 0] = vn[3 * v + 0];
+    out[9 * i + 3 * k + 1] = vn[3 * v + 1];
+    out[9 * i + 3 * k + 2] = vn[3 * v + 2];
+  }
+}
+
+}  // namespace
+
+size_t bvh_scratch_bytes(int nt) {
+  const size_t n = (size_t)(nt < 2 ? 2 : nt);
+  const int nblk = (int)((n + kB - 1) / kB);
+  return a256(n * 8) * 2 + a256((size_t)nblk * 24) + a256(24) + a256(2 * n * 4) * 2 + a256(2 * n * 24) +
+         a256(n * 4) + sort_scratch_bytes(n);
+}
+
+int build_lbvh(const float* d_verts, const int* d_tris, int n, float4* d_nodes, float4* d_tris_out, void* scratch,
+               cudaStream_t st) {
+  if (n <= 0) return 0;
+  if (n == 1) {
+    single_root_kernel<<<1, 1, 0, st>>>(d_verts, d_tris, d_nodes, d_tris_out);
+    return 1;
+  }
+  BvhScratch s = carve(scratch, n);
+  const int nblk = (n + kB - 1) / kB;
+  centroid_bounds_kernel<<<nblk, kB, 0, st>>>(d_verts, d_tris, n, s.cbox);
+  bounds_final_kernel<<<1, 32, 0, st>>>(s.cbox, nblk, s.gbox);
+  morton_kernel<<<nblk, kB, 0, st>>>(d_verts, d_tris, n, s.gbox, s.keys0);
+  uint2* sorted = sort_pairs(s.keys0, s.keys1, (size_t)n, 32, s.sort_scratch, st);
+  hierarchy_kernel<<<nblk, kB, 0, st>>>(sorted, n, s.child, s.parent);
+  leaf_boxes_kernel<<<nblk, kB, 0, st>>>(d_verts, d_tris, sorted, n, s.box, d_tris_out, s.flag);
+  internal_boxes_kernel<<<nblk, kB, 0, st>>>(n, s.child, s.parent, s.box, s.flag);
+  emit_nodes_kernel<<<nblk, kB, 0, st>>>(n, s.child, s.box, d_nodes);
+  return n - 1;
+}
+
+void launch_surface_records(const float* d_verts, const int* d_tris, const int* d_tri_mat, const float* d_sel,
+                            const float* d_vnormals, int nt, float4* d_surf, cudaStream_t s) {
+  if (nt <= 0) return;
+  surface_kernel<<<(nt + kB - 1) / kB, kB, 0, s>>>(d_verts, d_tris, d_tri_mat, d_sel, d_vnormals, nt, d_surf);
+}
+
+void launch_gather_normals(const float* d_vnormals, const int* d_tris, int nt, float* d_tri_normals, cudaStream_t s) {
+  if (nt <= 0) return;
+  gather_normals_kernel<<<(nt + kB - 1) / kB, kB, 0, s>>>(d_vnormals, d_tris, nt, d_tri_normals);
+}
+
+}  // namespace dr

@@ -1,0 +1,115 @@
+// Internal launchers shared by the translation units of libdiffrestore.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "dr_common.cuh"
+
+namespace dr {
+
+// ---------------------------------------------------------------- sorting
+// Stable LSD radix sort (8-bit digits) of 16-B splat records by pixel, or of
+// 8-B (key, value) pairs by key.  `bits` = number of significant key bits.
+// Scratch from sort_scratch_bytes(); no allocation inside.
+size_t sort_scratch_bytes(size_t n);
+// Sorts in[0..n) into out (in is used as the ping-pong buffer and is
+// clobbered).  Returns a pointer to whichever buffer holds the result.
+SplatRec* sort_splat_records(SplatRec* in, SplatRec* out, size_t n, int bits, void* scratch, cudaStream_t s);
+uint2* sort_pairs(uint2* in, uint2* out, size_t n, int bits, void* scratch, cudaStream_t s);
+
+// accum[pix * 3 + c] += sum of the sorted records' values (FP64, in sorted
+// order), one writer per pixel.  Records with pix >= n_pix are skipped and
+// flagged in *err.
+void launch_segment_reduce(const SplatRec* sorted, size_t n, double* accum, uint32_t n_pix, uint32_t* err,
+                           cudaStream_t s);
+// out[i] = k0 / tourCount * accum[i] (0 when tourCount == 0).
+void launch_resolve(const double* accum, size_t n, const unsigned long long* tour_count, double k0, float* out,
+                    cudaStream_t s);
+
+// ---------------------------------------------------------------- BVH
+struct BvhBuildOut {
+  int n_nodes;
+};
+// Builds the LBVH for nt triangles (verts [nv*3], tris [nt*3] on device)
+// into nodes (4 float4 per node, nt - 1 nodes, at least 1) and leaf-ordered
+// triangle records (3 float4 per triangle).  scratch: bvh_scratch_bytes(nt).
+size_t bvh_scratch_bytes(int nt);
+int build_lbvh(const float* d_verts, const int* d_tris, int nt, float4* d_nodes, float4* d_tris_out, void* scratch,
+               cudaStream_t s);
+// Per-triangle surface records (5 float4) from the device arrays; sel is
+// the light-selection probability per triangle (device, may be null).
+void launch_surface_records(const float* d_verts, const int* d_tris, const int* d_tri_mat, const float* d_sel,
+                            const float* d_vnormals, int nt, float4* d_surf, cudaStream_t s);
+void launch_gather_normals(const float* d_vnormals, const int* d_tris, int nt, float* d_tri_normals,
+                           cudaStream_t s);
+
+// ---------------------------------------------------------------- chains
+enum Drift { kDriftNone = 0, kDriftFD = 1, kDriftAdjoint = 2 };
+
+struct StepArgs {
+  DevScene S;
+  DevMixture M;
+  int target;  // 0 scene, 1 mixture
+  float* x;          // [d][N]
+  float* score;      // [d][N]
+  uint8_t* killed;   // [N]
+  float* logp;       // [N]
+  SplatRec* rec;     // [N] slice for this step (null: no records)
+  unsigned long long N;
+  int d, L;
+  uint32_t step;
+  Rng rng;
+  float stddev, gamma_tilde, h, eps;
+  double k0;
+  int rb, drift, init;
+  int estimate_only;  // init pass that only sums p (k0 unknown yet)
+  unsigned long long* tour_count;
+  unsigned long long* rays;
+  unsigned long long* node_visits;  // stats mode only
+  unsigned long long* tri_tests;    // stats mode only
+  double* p_partial;  // [gridDim.x] init only
+  uint32_t* err;
+};
+
+int step_block_size();
+size_t step_smem_bytes();
+void launch_step(const StepArgs& a, bool stats, cudaStream_t s);
+
+struct FdArgs {
+  DevScene S;
+  DevMixture M;
+  int target;
+  const float* x;
+  float* score;
+  const uint8_t* killed;
+  unsigned long long N;
+  int d, L;
+  float eps, fd_h;
+  unsigned long long* rays;
+  uint32_t* err;
+};
+void launch_fd_score(const FdArgs& a, cudaStream_t s);
+
+struct EvalArgs {
+  DevScene S;
+  DevMixture M;
+  int target;
+  const float* x;  // [M][d]
+  float* logp;     // [M]
+  float* grad;     // [M][d] or null
+  int* pix;        // [M] or null
+  float* f;        // [M][3] or null
+  long long Mpts;
+  int d, L;
+  float eps;
+  uint32_t* err;
+};
+void launch_eval(const EvalArgs& a, cudaStream_t s);
+
+void launch_trace(const DevScene& S, const float* rays, long long n, int exclude, int* tri, float* t, uint32_t* err,
+                  cudaStream_t s);
+void launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, long long n, cudaStream_t s);
+void launch_sum_doubles(const double* in, int n, double* out, cudaStream_t s);
+
+}  // namespace dr

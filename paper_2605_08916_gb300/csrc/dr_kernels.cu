@@ -1,0 +1,350 @@
+// Restore chain kernels: one thread per chain, structure-of-arrays state.
+//
+// step_kernel fuses, per chain and step (Alg. 2 with Alg. 4 and the
+// Accumulate procedure of Alg. 1):
+//   a1 load state / Philox draws,
+//   a2 regeneration from mu = U(T^d) if the chain was killed,
+//   a3 LocalDynamics: x += (stddev^2/2) s + gamma_tilde (s_2, -s_1)
+//      + stddev xi per coordinate pair, then the torus wrap,
+//   a4 the path contribution f(x), p = lum(f) + eps and the pixel,
+//   a6 the hold/kill clock with h = 1 / dt and k = k0 / p
+//      (Eq. modified-killing-rate with uniform mu), or its Rao-Blackwellised
+//      form (weight 1 / (h + k), killed with probability k / (h + k)),
+//   a7 the splat record dt * f / p,
+//   a5 (adjoint drift) grad log p at the new x for the next step, computed
+//      only for chains that survived.
+// Kill counts and ray counts are reduced per block (warp shuffles, then one
+// integer atomic per block); no per-lane global atomics.
+#include "dr_internal.h"
+#include "dr_path.cuh"
+
+namespace dr {
+
+namespace {
+
+constexpr int kStepThreads = 128;
+constexpr int kStack = 48;
+
+struct XSoA {
+  const float* x;
+  unsigned long long N, j;
+  DR_D float operator()(int i) const { return x[(size_t)i * N + j]; }
+};
+
+struct XPerturbed {
+  const float* x;
+  unsigned long long N, j;
+  int k;
+  float v;
+  DR_D float operator()(int i) const { return i == k ? v : x[(size_t)i * N + j]; }
+};
+
+struct XRow {
+  const float* x;
+  int d;
+  long long j;
+  DR_D float operator()(int i) const { return x[(size_t)j * d + i]; }
+};
+
+struct GSoA {
+  float* g;
+  unsigned long long N, j;
+  DR_D void operator()(int i, float v) const { g[(size_t)i * N + j] = v; }
+};
+
+struct GRow {
+  float* g;
+  int d;
+  long long j;
+  DR_D void operator()(int i, float v) const { g[(size_t)j * d + i] = v; }
+};
+
+struct GNone {
+  DR_D void operator()(int, float) const {}
+};
+
+DR_D unsigned long long warp_sum_u64(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+DR_D double warp_sum_f64(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Evaluates f, p and (optionally) grad log p through GW.
+template <bool TAPE, bool STATS, class XA, class GW>
+DR_D float3 evaluate(const DevScene& S, const DevMixture& M, int target, int L, float eps, const XA& xa, int* pix,
+                     float* p_out, bool want_grad, const GW& gw, TraceStack<kStack> st, uint32_t* err,
+                     TraceStats* stats, uint32_t* rays) {
+  if (target == 1) {
+    const float g = mixture_eval(M, xa, eps, want_grad, gw);
+    *pix = pixel_of(xa(0), xa(1), M.W, M.H);
+    *p_out = g + eps;
+    return f3(g, g, g);
+  }
+  Tape<kMaxPathLen> tape;
+  const PathResult r = path_forward<kStack, STATS, TAPE>(S, xa, L, &tape, st, err, stats);
+  *rays += r.rays;
+  *pix = r.pix;
+  const float p = lum(r.f) + eps;
+  *p_out = p;
+  if (TAPE && want_grad) path_adjoint(S, xa, L, p, tape, r.nseg, gw);
+  return r.f;
+}
+
+template <int DRIFT, bool STATS>
+__global__ void __launch_bounds__(kStepThreads) step_kernel(StepArgs a) {
+  extern __shared__ int smem[];
+  TraceStack<kStack> st{smem + threadIdx.x, (int)blockDim.x};
+  const unsigned long long j = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool active = j < a.N;
+  uint32_t err = 0, rays = 0;
+  TraceStats stats{0u, 0u};
+  unsigned long long kill = 0;
+  double pval = 0.0;
+  if (active) {
+    const uint32_t cj = (uint32_t)j;
+    const bool regen = a.init || a.killed[j];
+    if (regen) {
+      for (int i = 0; i < a.d; i += 4) {
+        const U4 r = a.rng.draw(a.step, cj, (uint32_t)(i >> 2), kRegen);
+        const uint32_t w[4] = {r.a, r.b, r.c, r.d};
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (i + k < a.d) a.x[(size_t)(i + k) * a.N + j] = u01(w[k]);
+      }
+    } else {
+      const float c2 = 0.5f * a.stddev * a.stddev;
+      for (int q = 0; q < a.d / 2; ++q) {
+        const U4 r = a.rng.draw(a.step, cj, (uint32_t)(q >> 1), kNormal);
+        const float ua = u01((q & 1) ? r.c : r.a), ub = u01((q & 1) ? r.d : r.b);
+        const float2 xi = box_muller(ua, ub);
+        const size_t i0 = (size_t)(2 * q) * a.N + j, i1 = (size_t)(2 * q + 1) * a.N + j;
+        const float s0 = a.score[i0], s1 = a.score[i1];
+        a.x[i0] = wrap01(a.x[i0] + c2 * s0 + a.gamma_tilde * s1 + a.stddev * xi.x);
+        a.x[i1] = wrap01(a.x[i1] + c2 * s1 - a.gamma_tilde * s0 + a.stddev * xi.y);
+      }
+    }
+    const XSoA xa{a.x, a.N, j};
+    int pix;
+    float p;
+    float3 f;
+    const U4 rc = a.rng.draw(a.step, cj, 0u, kClock);
+    const float u1 = u01(rc.a), u2 = u01(rc.b);
+    if (DRIFT == kDriftAdjoint && !a.estimate_only) {
+      // forward with tape; kill decision; adjoint only if the chain survives
+      if (a.target == 1) {
+        f = evaluate<false, STATS>(a.S, a.M, 1, a.L, a.eps, xa, &pix, &p, false, GNone{}, st, &err, &stats, &rays);
+      } else {
+        Tape<kMaxPathLen> tape;
+        const PathResult r = path_forward<kStack, STATS, true>(a.S, xa, a.L, &tape, st, &err, &stats);
+        rays += r.rays;
+        pix = r.pix;
+        f = r.f;
+        p = lum(f) + a.eps;
+        bool killed_now;
+        if (a.rb) killed_now = (double)u2 * ((double)a.h * p + a.k0) < a.k0;
+        else killed_now = !(-logf(1.0f - u1) / a.h < -logf(1.0f - u2) * p / (float)a.k0);
+        if (!killed_now) path_adjoint(a.S, xa, a.L, p, tape, r.nseg, GSoA{a.score, a.N, j});
+      }
+    } else {
+      f = evaluate<false, STATS>(a.S, a.M, a.target, a.L, a.eps, xa, &pix, &p, false, GNone{}, st, &err, &stats,
+                                 &rays);
+    }
+    if (a.estimate_only) {
+      pval = (double)p;
+    } else {
+      bool killed;
+      float wt;
+      if (a.rb) {
+        killed = (double)u2 * ((double)a.h * p + a.k0) < a.k0;
+        wt = (float)((double)p / ((double)a.h * p + a.k0));
+      } else {
+        const float t1 = -logf(1.0f - u1) / a.h;
+        const float t2 = -logf(1.0f - u2) * p / (float)a.k0;
+        killed = !(t1 < t2);
+        wt = killed ? t2 : t1;
+      }
+      if (DRIFT == kDriftAdjoint && a.target == 1 && !killed) {
+        mixture_eval(a.M, xa, a.eps, true, GSoA{a.score, a.N, j});
+      }
+      a.killed[j] = killed ? 1 : 0;
+      a.logp[j] = logf(p);
+      kill = killed ? 1ull : 0ull;
+      if (a.init) pval = (double)p;
+      if (a.rec) {
+        const float s = wt / p;
+        SplatRec rr;
+        rr.pix = (uint32_t)pix;
+        rr.r = f.x * s;
+        rr.g = f.y * s;
+        rr.b = f.z * s;
+        a.rec[j] = rr;
+      }
+      if (!(isfinite(p) && isfinite(f.x) && isfinite(f.y) && isfinite(f.z))) err |= kErrNonFinite;
+    }
+  }
+  // block reductions
+  __shared__ unsigned long long sk[kStepThreads / 32], sr[kStepThreads / 32], sn[kStepThreads / 32],
+      stt[kStepThreads / 32];
+  __shared__ double sp[kStepThreads / 32];
+  __shared__ uint32_t serr;
+  if (threadIdx.x == 0) serr = 0;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned long long wk = warp_sum_u64(kill), wr = warp_sum_u64(rays);
+  const unsigned long long wn = STATS ? warp_sum_u64(stats.nodes) : 0ull, wt = STATS ? warp_sum_u64(stats.tris) : 0ull;
+  const double wp = warp_sum_f64(pval);
+  __syncthreads();
+  if (err) atomicOr(&serr, err);
+  if (lane == 0) { sk[warp] = wk; sr[warp] = wr; sp[warp] = wp; sn[warp] = wn; stt[warp] = wt; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long K = 0, R = 0, Nn = 0, Tt = 0;
+    double P = 0.0;
+    for (int w = 0; w < kStepThreads / 32; ++w) { K += sk[w]; R += sr[w]; P += sp[w]; Nn += sn[w]; Tt += stt[w]; }
+    if (K && a.tour_count) atomicAdd(a.tour_count, K);
+    if (R && a.rays) atomicAdd(a.rays, R);
+    if (STATS && a.node_visits) atomicAdd(a.node_visits, Nn);
+    if (STATS && a.tri_tests) atomicAdd(a.tri_tests, Tt);
+    if (a.p_partial) a.p_partial[blockIdx.x] = P;
+    if (serr) atomicOr(a.err, serr);
+  }
+}
+
+// Central finite differences of log p for every (coordinate, surviving
+// chain): thread t -> coordinate t / N, chain t % N.
+__global__ void __launch_bounds__(kStepThreads) fd_kernel(FdArgs a) {
+  extern __shared__ int smem[];
+  TraceStack<kStack> st{smem + threadIdx.x, (int)blockDim.x};
+  const unsigned long long t = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned long long total = a.N * (unsigned long long)a.d;
+  uint32_t err = 0, rays = 0;
+  if (t < total) {
+    const unsigned long long j = t % a.N;
+    const int i = (int)(t / a.N);
+    if (!a.killed[j]) {
+      const float xi = a.x[(size_t)i * a.N + j];
+      TraceStats stats{0u, 0u};
+      int pix;
+      float pp, pm;
+      evaluate<false, false>(a.S, a.M, a.target, a.L, a.eps, XPerturbed{a.x, a.N, j, i, wrap01(xi + a.fd_h)}, &pix,
+                             &pp, false, GNone{}, st, &err, &stats, &rays);
+      evaluate<false, false>(a.S, a.M, a.target, a.L, a.eps, XPerturbed{a.x, a.N, j, i, wrap01(xi - a.fd_h)}, &pix,
+                             &pm, false, GNone{}, st, &err, &stats, &rays);
+      a.score[(size_t)i * a.N + j] = (logf(pp) - logf(pm)) / (2.0f * a.fd_h);
+    }
+  }
+  const unsigned long long wr = warp_sum_u64(rays);
+  if ((threadIdx.x & 31) == 0 && wr && a.rays) atomicAdd(a.rays, wr);
+  if (err) atomicOr(a.err, err);
+}
+
+__global__ void __launch_bounds__(kStepThreads) eval_kernel(EvalArgs a) {
+  extern __shared__ int smem[];
+  TraceStack<kStack> st{smem + threadIdx.x, (int)blockDim.x};
+  const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= a.Mpts) return;
+  uint32_t err = 0, rays = 0;
+  TraceStats stats{0u, 0u};
+  int pix;
+  float p;
+  const XRow xa{a.x, a.d, j};
+  float3 f;
+  if (a.grad) f = evaluate<true, false>(a.S, a.M, a.target, a.L, a.eps, xa, &pix, &p, true, GRow{a.grad, a.d, j}, st,
+                                        &err, &stats, &rays);
+  else f = evaluate<false, false>(a.S, a.M, a.target, a.L, a.eps, xa, &pix, &p, false, GNone{}, st, &err, &stats,
+                                  &rays);
+  a.logp[j] = logf(p);
+  if (a.pix) a.pix[j] = pix;
+  if (a.f) { a.f[3 * j] = f.x; a.f[3 * j + 1] = f.y; a.f[3 * j + 2] = f.z; }
+  if (err) atomicOr(a.err, err);
+}
+
+__global__ void __launch_bounds__(kStepThreads) trace_kernel(DevScene S, const float* __restrict__ rays, long long n,
+                                                             int exclude, int* __restrict__ tri, float* __restrict__ t,
+                                                             uint32_t* errp) {
+  extern __shared__ int smem[];
+  TraceStack<kStack> st{smem + threadIdx.x, (int)blockDim.x};
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float* r = rays + 6 * i;
+  uint32_t err = 0;
+  float th;
+  const int h = trace_closest<kStack, false>(S, make_ray(f3(r[0], r[1], r[2]), f3(r[3], r[4], r[5])), exclude, &th, st,
+                                             &err, nullptr);
+  tri[i] = h;
+  t[i] = h >= 0 ? th : __int_as_float(0x7f800000);
+  if (err) atomicOr(errp, err);
+}
+
+__global__ void philox_kernel(const uint32_t* __restrict__ ctr, const uint32_t* __restrict__ key,
+                              uint32_t* __restrict__ out, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const U4 r = philox4x32_10(ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3], key[2 * i], key[2 * i + 1]);
+  out[4 * i] = r.a;
+  out[4 * i + 1] = r.b;
+  out[4 * i + 2] = r.c;
+  out[4 * i + 3] = r.d;
+}
+
+__global__ void sum_doubles_kernel(const double* __restrict__ in, int n, double* __restrict__ out) {
+  // one thread, fixed order: deterministic
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double s = 0.0;
+  for (int i = 0; i < n; ++i) s += in[i];
+  *out = s;
+}
+
+template <int DRIFT, bool STATS>
+void launch_step_t(const StepArgs& a, cudaStream_t s) {
+  const unsigned grid = (unsigned)((a.N + kStepThreads - 1) / kStepThreads);
+  step_kernel<DRIFT, STATS><<<grid, kStepThreads, step_smem_bytes(), s>>>(a);
+}
+
+}  // namespace
+
+int step_block_size() { return kStepThreads; }
+size_t step_smem_bytes() { return (size_t)kStack * kStepThreads * sizeof(int); }
+
+void launch_step(const StepArgs& a, bool stats, cudaStream_t s) {
+  if (a.N == 0) return;
+  if (a.drift == kDriftAdjoint) {
+    if (stats) launch_step_t<kDriftAdjoint, true>(a, s); else launch_step_t<kDriftAdjoint, false>(a, s);
+  } else {
+    if (stats) launch_step_t<kDriftNone, true>(a, s); else launch_step_t<kDriftNone, false>(a, s);
+  }
+}
+
+void launch_fd_score(const FdArgs& a, cudaStream_t s) {
+  const unsigned long long total = a.N * (unsigned long long)a.d;
+  if (total == 0) return;
+  fd_kernel<<<(unsigned)((total + kStepThreads - 1) / kStepThreads), kStepThreads, step_smem_bytes(), s>>>(a);
+}
+
+void launch_eval(const EvalArgs& a, cudaStream_t s) {
+  if (a.Mpts <= 0) return;
+  eval_kernel<<<(unsigned)((a.Mpts + kStepThreads - 1) / kStepThreads), kStepThreads, step_smem_bytes(), s>>>(a);
+}
+
+void launch_trace(const DevScene& S, const float* rays, long long n, int exclude, int* tri, float* t, uint32_t* err,
+                  cudaStream_t s) {
+  if (n <= 0) return;
+  trace_kernel<<<(unsigned)((n + kStepThreads - 1) / kStepThreads), kStepThreads, step_smem_bytes(), s>>>(
+      S, rays, n, exclude, tri, t, err);
+}
+
+void launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, long long n, cudaStream_t s) {
+  if (n <= 0) return;
+  philox_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(ctr, key, out, n);
+}
+
+void launch_sum_doubles(const double* in, int n, double* out, cudaStream_t s) {
+  sum_doubles_kernel<<<1, 32, 0, s>>>(in, n, out);
+}
+
+}  // namespace dr

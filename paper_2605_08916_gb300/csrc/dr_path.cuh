@@ -1,0 +1,753 @@
+// Path contribution f(x) in primary sample space, its log-density
+// p = lum(f) + eps, and a hand-written reverse-mode adjoint for grad log p.
+//
+// The paper samples paths with routines shared by all its methods (Sec. 6,
+// "Setup") and differentiates them with Slang's autodiff (Sec. 6); it runs
+// MCMC on the full PSS, direct and indirect light together (Sec. 6,
+// "Parameter choices").  The sampler here is unidirectional path tracing
+// with next-event estimation (one point on one emitting triangle per vertex)
+// and balance-heuristic MIS, fixed maximum length L, no Russian roulette.
+// PSS layout, d = 2 + 4 (L - 1): x0, x1 = film position (pixel =
+// floor(x0 W), floor(x1 H), row 0 at the top); scattering vertex v
+// (1 .. L-1) uses base b = 2 + 4 (v - 1): x[b], x[b+1] BSDF sample (first
+// coordinate also picks the lobe by rescaling), x[b+2], x[b+3] light sample
+// (first coordinate also picks the emitting triangle by rescaling).  f
+// carries the pixel importance W H.
+//
+// The adjoint differentiates the smooth piece containing x: triangle ids,
+// lobe choices and visibility are held fixed (what automatic differentiation
+// of the sampler gives).  The forward pass records per segment the ray, the
+// throughput, the previous BSDF pdf, the hit triangle and the discrete
+// choices; the backward pass walks the segments in reverse, recomputes each
+// vertex from its ray and triangle (no traversal), and applies the
+// vector-Jacobian products of each step.
+#pragma once
+#include "dr_trace.cuh"
+
+namespace dr {
+
+// ---------------------------------------------------------------- records
+struct MatP {
+  int type;
+  float3 albedo, emit;
+  float rough, ior, f0;
+  bool emissive;
+};
+
+DR_D MatP load_mat(const float* __restrict__ mats, int id) {
+  const float* m = mats + kMatFloats * id;
+  MatP r;
+  r.type = (int)__ldg(m + 0);
+  r.albedo = f3(__ldg(m + 1), __ldg(m + 2), __ldg(m + 3));
+  r.rough = __ldg(m + 4);
+  r.ior = __ldg(m + 5);
+  r.emit = f3(__ldg(m + 6), __ldg(m + 7), __ldg(m + 8));
+  r.f0 = __ldg(m + 9);
+  r.emissive = r.emit.x > 0.f || r.emit.y > 0.f || r.emit.z > 0.f;
+  return r;
+}
+
+struct Surf {
+  float3 v0, N, ng, au, av;
+  float area, sel;
+  int mat;
+  bool has_n;
+};
+
+DR_D Surf load_surf(const DevScene& S, int tri) {
+  const float4 a = __ldg(S.surf + kSurfF4 * tri + 0);
+  const float4 b = __ldg(S.surf + kSurfF4 * tri + 1);
+  const float4 c = __ldg(S.surf + kSurfF4 * tri + 2);
+  const float4 d = __ldg(S.surf + kSurfF4 * tri + 3);
+  const float4 e = __ldg(S.surf + kSurfF4 * tri + 4);
+  Surf s;
+  s.v0 = xyz(a);
+  s.mat = __float_as_int(a.w);
+  s.N = xyz(b);
+  s.area = b.w;
+  s.ng = xyz(c);
+  s.au = xyz(d);
+  s.sel = d.w;
+  s.av = xyz(e);
+  s.has_n = S.nrm != nullptr && (__float_as_int(c.w) & 1);
+  return s;
+}
+
+DR_D void load_vnormals(const DevScene& S, int tri, float3& n0, float3& n1, float3& n2) {
+  const float* p = S.nrm + 9 * tri;
+  n0 = f3(__ldg(p + 0), __ldg(p + 1), __ldg(p + 2));
+  n1 = f3(__ldg(p + 3), __ldg(p + 4), __ldg(p + 5));
+  n2 = f3(__ldg(p + 6), __ldg(p + 7), __ldg(p + 8));
+}
+
+// Interpolated, normalised shading normal at P (un-flipped) and its raw sum.
+DR_D float3 shading_normal(const DevScene& S, int tri, const Surf& sf, float3 P, float3* raw_out) {
+  if (!sf.has_n) {
+    *raw_out = sf.ng;
+    return sf.ng;
+  }
+  float3 n0, n1, n2;
+  load_vnormals(S, tri, n0, n1, n2);
+  const float3 q = P - sf.v0;
+  const float bu = dot(q, sf.au), bv = dot(q, sf.av);
+  const float3 raw = n0 * (1.0f - bu - bv) + n1 * bu + n2 * bv;
+  *raw_out = raw;
+  return normalize(raw);
+}
+
+DR_D float3 shading_normal_bwd(const DevScene& S, int tri, const Surf& sf, float3 raw, float3 nsn, float3 gnsn) {
+  if (!sf.has_n) return f3(0.f, 0.f, 0.f);
+  float3 n0, n1, n2;
+  load_vnormals(S, tri, n0, n1, n2);
+  const float3 graw = normalize_bwd(raw, nsn, gnsn);
+  const float gbu = dot(graw, n1 - n0), gbv = dot(graw, n2 - n0);
+  return sf.au * gbu + sf.av * gbv;
+}
+
+// ---------------------------------------------------------------- basis
+// Orthonormal basis around unit n (Duff et al. 2017, branchless form).
+DR_D void onb(float3 n, float3& t, float3& b) {
+  const float s = n.z >= 0.0f ? 1.0f : -1.0f;
+  const float a = -1.0f / (s + n.z);
+  const float c = n.x * n.y * a;
+  t = f3(1.0f + s * n.x * n.x * a, s * c, -s * n.x);
+  b = f3(c, s + n.y * n.y * a, -n.y);
+}
+
+DR_D float3 onb_bwd(float3 n, float3 gt, float3 gb) {
+  const float s = n.z >= 0.0f ? 1.0f : -1.0f;
+  const float a = -1.0f / (s + n.z);
+  const float gc = gt.y * s + gb.x;
+  const float ga = gt.x * s * n.x * n.x + gb.y * n.y * n.y + gc * n.x * n.y;
+  float3 g;
+  g.x = gt.x * 2.0f * s * n.x * a - gt.z * s + gc * n.y * a;
+  g.y = gb.y * 2.0f * n.y * a - gb.z + gc * n.x * a;
+  g.z = ga * a * a;
+  return g;
+}
+
+// ---------------------------------------------------------------- BSDFs
+// GGX (Trowbridge-Reitz) D, Smith height-correlated G2, Schlick F; the
+// glossy BSDF is a GGX coat over a Lambertian base, sampled by picking the
+// specular lobe with probability 1/2 (D cos(theta_h) half-vector sampling)
+// or the cosine-weighted diffuse lobe; its pdf is the two-lobe mixture.
+struct GlossyFwd {
+  float co, ci, hl, nh, oh, ih, k, D, lo, li, ro, ri, G, om, F, spec, pdf;
+  float3 h, hv;
+};
+
+DR_D GlossyFwd glossy_fwd(const MatP& m, float3 n, float3 wo, float3 wi) {
+  GlossyFwd g;
+  const float a2 = m.rough * m.rough;
+  g.co = dot(n, wo);
+  g.ci = dot(n, wi);
+  g.hv = wo + wi;
+  g.hl = sqrtf(dot(g.hv, g.hv));
+  g.h = g.hv * (1.0f / g.hl);
+  g.nh = dot(n, g.h);
+  g.oh = dot(wo, g.h);
+  g.ih = dot(wi, g.h);
+  g.k = g.nh * g.nh * (a2 - 1.0f) + 1.0f;
+  g.D = a2 / (kPi * g.k * g.k);
+  g.ro = sqrtf(1.0f + a2 * (1.0f - g.co * g.co) / (g.co * g.co));
+  g.ri = sqrtf(1.0f + a2 * (1.0f - g.ci * g.ci) / (g.ci * g.ci));
+  g.lo = 0.5f * (g.ro - 1.0f);
+  g.li = 0.5f * (g.ri - 1.0f);
+  g.G = 1.0f / (1.0f + g.lo + g.li);
+  g.om = 1.0f - g.ih;
+  const float om2 = g.om * g.om;
+  g.F = m.f0 + (1.0f - m.f0) * (om2 * om2 * g.om);
+  g.spec = g.D * g.G * g.F / (4.0f * g.co * g.ci);
+  g.pdf = kGlossySpecProb * g.D * g.nh / (4.0f * fabsf(g.oh)) + (1.0f - kGlossySpecProb) * g.ci * kInvPi;
+  return g;
+}
+
+// BSDF value (RGB) and sampling pdf (solid angle) of an opaque material.
+DR_D float3 bsdf_eval(const MatP& m, float3 n, float3 wo, float3 wi, float* pdf) {
+  if (m.type == kGlossy) {
+    const GlossyFwd g = glossy_fwd(m, n, wo, wi);
+    *pdf = g.pdf;
+    const float kd = (1.0f - m.f0) * kInvPi;
+    return m.albedo * kd + f3(g.spec, g.spec, g.spec);
+  }
+  *pdf = dot(n, wi) * kInvPi;
+  return m.albedo * kInvPi;
+}
+
+// Backward of bsdf_eval: given d(fs) (RGB) and d(pdf), accumulates into
+// d(n), d(wo), d(wi).
+DR_D void bsdf_eval_bwd(const MatP& m, float3 n, float3 wo, float3 wi, float3 gfs, float gpdf, float3& gn,
+                        float3& gwo, float3& gwi) {
+  if (m.type != kGlossy) {
+    gn += wi * (gpdf * kInvPi);
+    gwi += n * (gpdf * kInvPi);
+    return;
+  }
+  const GlossyFwd g = glossy_fwd(m, n, wo, wi);
+  const float a2 = m.rough * m.rough;
+  const float gspec = gfs.x + gfs.y + gfs.z;
+  const float den = 4.0f * g.co * g.ci;
+  const float aoh = fabsf(g.oh);
+  const float gD = gspec * g.G * g.F / den + gpdf * kGlossySpecProb * g.nh / (4.0f * aoh);
+  const float gG = gspec * g.D * g.F / den;
+  const float gF = gspec * g.D * g.G / den;
+  // Lambda'(c) = -a2 / (2 r c^3), dG/dLambda = -G^2
+  const float dlo = -a2 / (2.0f * g.ro * g.co * g.co * g.co);
+  const float dli = -a2 / (2.0f * g.ri * g.ci * g.ci * g.ci);
+  const float gco = -gspec * g.spec / g.co - gG * g.G * g.G * dlo;
+  const float gci = -gspec * g.spec / g.ci - gG * g.G * g.G * dli + gpdf * (1.0f - kGlossySpecProb) * kInvPi;
+  const float dD = g.D * (-4.0f * g.nh * (a2 - 1.0f) / g.k);
+  const float gnh = gD * dD + gpdf * kGlossySpecProb * g.D / (4.0f * aoh);
+  const float goh = -gpdf * kGlossySpecProb * g.D * g.nh * (g.oh >= 0.0f ? 1.0f : -1.0f) / (4.0f * g.oh * g.oh);
+  const float om2 = g.om * g.om;
+  const float gih = gF * (-5.0f * (1.0f - m.f0) * om2 * om2);
+  const float3 gh = n * gnh + wo * goh + wi * gih;
+  gn += g.h * gnh;
+  gwo += g.h * goh;
+  gwi += g.h * gih;
+  const float3 ghv = (gh - g.h * dot(g.h, gh)) * (1.0f / g.hl);
+  gwo += ghv;
+  gwi += ghv;
+  gn += wo * gco + wi * gci;
+  gwo += n * gco;
+  gwi += n * gci;
+}
+
+// Cosine-weighted direction (local frame) and its backward.
+DR_D float3 cosine_local(float u, float u2, float* r, float* cph, float* sph) {
+  *r = sqrtf(u);
+  sincospif(2.0f * u2, sph, cph);
+  return f3(*r * *cph, *r * *sph, sqrtf(1.0f - u));
+}
+
+struct SampleRec {
+  float3 wi;
+  float3 w;
+  float pdf;
+  int lobe;
+};
+
+// BSDF sampling of an opaque material at a vertex with shading normal n,
+// geometric normal ngf (same side as wo).  Returns false if wi is not above
+// both normals.
+DR_D bool opaque_sample(const MatP& m, float3 n, float3 ngf, float3 wo, float u1, float u2, SampleRec& s) {
+  float3 t, b;
+  onb(n, t, b);
+  if (m.type == kGlossy && u1 < kGlossySpecProb) {
+    s.lobe = 1;
+    const float v = u1 * (1.0f / kGlossySpecProb);
+    const float a2 = m.rough * m.rough;
+    const float den = 1.0f + (a2 - 1.0f) * v;
+    const float ch = sqrtf((1.0f - v) / den);
+    const float sh = m.rough * sqrtf(v / den);
+    float sp, cp;
+    sincospif(2.0f * u2, &sp, &cp);
+    const float3 h = t * (sh * cp) + b * (sh * sp) + n * ch;
+    s.wi = h * (2.0f * dot(wo, h)) - wo;
+  } else {
+    s.lobe = 0;
+    const float v = m.type == kGlossy ? (u1 - kGlossySpecProb) * (1.0f / (1.0f - kGlossySpecProb)) : u1;
+    float r, cp, sp;
+    const float3 l = cosine_local(v, u2, &r, &cp, &sp);
+    s.wi = t * l.x + b * l.y + n * l.z;
+  }
+  const float ci = dot(n, s.wi);
+  if (!(ci > 0.0f) || !(dot(ngf, s.wi) > 0.0f)) return false;
+  const float3 fs = bsdf_eval(m, n, wo, s.wi, &s.pdf);
+  s.w = fs * (ci / s.pdf);
+  return true;
+}
+
+// Backward of the sampled direction wi(n, wo, u1, u2) for the recorded lobe.
+DR_D void opaque_sample_dir_bwd(const MatP& m, int lobe, float3 n, float3 wo, float u1, float u2, float3 gwi,
+                                float3& gn, float3& gwo, float& gu1, float& gu2) {
+  float3 t, b;
+  onb(n, t, b);
+  float3 gt, gb;
+  if (lobe == 1) {
+    const float v = u1 * (1.0f / kGlossySpecProb);
+    const float a2 = m.rough * m.rough;
+    const float den = 1.0f + (a2 - 1.0f) * v;
+    const float ch = sqrtf((1.0f - v) / den);
+    const float sh = m.rough * sqrtf(v / den);
+    float sp, cp;
+    sincospif(2.0f * u2, &sp, &cp);
+    const float3 h = t * (sh * cp) + b * (sh * sp) + n * ch;
+    const float oh = dot(wo, h);
+    const float wh = dot(gwi, h);
+    const float3 gh = gwi * (2.0f * oh) + wo * (2.0f * wh);
+    gwo += h * (2.0f * wh) - gwi;
+    gt = gh * (sh * cp);
+    gb = gh * (sh * sp);
+    gn += gh * ch;
+    const float ght = dot(gh, t), ghb = dot(gh, b);
+    const float gsh = ght * cp + ghb * sp;
+    const float gch = dot(gh, n);
+    const float gph = sh * (-sp * ght + cp * ghb);
+    const float den2 = den * den;
+    float gv = 0.0f;
+    if (sh > 0.0f) gv += gsh * a2 / (2.0f * sh * den2);
+    if (ch > 0.0f) gv -= gch * a2 / (2.0f * ch * den2);
+    gu1 = gv * (1.0f / kGlossySpecProb);
+    gu2 = gph * 2.0f * kPi;
+  } else {
+    const float dvdu = m.type == kGlossy ? 1.0f / (1.0f - kGlossySpecProb) : 1.0f;
+    const float v = m.type == kGlossy ? (u1 - kGlossySpecProb) * dvdu : u1;
+    float r, cp, sp;
+    const float3 l = cosine_local(v, u2, &r, &cp, &sp);
+    const float glx = dot(gwi, t), gly = dot(gwi, b), glz = dot(gwi, n);
+    gt = gwi * l.x;
+    gb = gwi * l.y;
+    gn += gwi * l.z;
+    float gv = 0.0f;
+    if (r > 0.0f) gv += (glx * cp + gly * sp) / (2.0f * r);
+    if (l.z > 0.0f) gv -= glz / (2.0f * l.z);
+    gu1 = gv * dvdu;
+    gu2 = r * (-glx * sp + gly * cp) * 2.0f * kPi;
+  }
+  gn += onb_bwd(n, gt, gb);
+}
+
+// Exact dielectric Fresnel reflectance, eta = n_t / n_i.
+DR_D float fresnel_dielectric(float ci, float ct, float eta) {
+  const float rs = (ci - eta * ct) / (ci + eta * ct);
+  const float rp = (eta * ci - ct) / (eta * ci + ct);
+  return 0.5f * (rs * rs + rp * rp);
+}
+
+// ---------------------------------------------------------------- tape
+enum : int {
+  kFPrevDelta = 1 << 0,
+  kFNeeVis = 1 << 1,
+  kFScatter = 1 << 2,   // BSDF sample succeeded (next segment traced)
+  kFLobeShift = 3,      // 2 bits: 0 diffuse, 1 glossy spec, 2 reflect, 3 refract
+  kFLightShift = 8,
+};
+
+template <int LMAX>
+struct Tape {
+  float4 a[LMAX];  // (o, prev pdf)
+  float4 b[LMAX];  // (d, tri bits)
+  float4 c[LMAX];  // (beta, flags bits)
+};
+
+struct PathResult {
+  float3 f;
+  int pix;
+  int nseg;
+  uint32_t rays;
+};
+
+DR_D int pixel_of(float x0, float x1, int W, int H) {
+  int col = (int)floorf(x0 * (float)W), row = (int)floorf(x1 * (float)H);
+  col = min(max(col, 0), W - 1);
+  row = min(max(row, 0), H - 1);
+  return row * W + col;
+}
+
+DR_D float3 camera_dir(const Camera& C, float x0, float x1, float3* raw) {
+  const float sx = (2.0f * x0 - 1.0f) * C.tx, sy = (1.0f - 2.0f * x1) * C.ty;
+  *raw = C.fwd + C.right * sx + C.up * sy;
+  return normalize(*raw);
+}
+
+// Light pick by the first light coordinate (CDF over emitting triangles,
+// prefix of area * lum(emission)), rescaled to [0, 1).
+DR_D int pick_light(const DevScene& S, float ul, float* lo, float* pk) {
+  int a = 0, b = S.n_lights - 1;
+  while (a < b) {  // first k with ul < cdf[k]
+    const int mid = (a + b) >> 1;
+    if (ul < __ldg(&S.lights[kLightF4 * mid + 3].x)) b = mid; else a = mid + 1;
+  }
+  *lo = a == 0 ? 0.0f : __ldg(&S.lights[kLightF4 * (a - 1) + 3].x);
+  *pk = __ldg(&S.lights[kLightF4 * a + 3].x) - *lo;
+  return a;
+}
+
+struct LightSample {
+  float3 V0, V1, V2, nl, y, Le;
+  float v1, v2, su, sel, area, pk;
+  int tri;
+  bool clamped;
+};
+
+DR_D LightSample light_sample(const DevScene& S, int k, float ul, float ul2, float lo, float pk) {
+  LightSample ls;
+  const float4 l0 = __ldg(S.lights + kLightF4 * k + 0);
+  const float4 l1 = __ldg(S.lights + kLightF4 * k + 1);
+  const float4 l2 = __ldg(S.lights + kLightF4 * k + 2);
+  ls.V0 = xyz(l0);
+  ls.V1 = xyz(l1);
+  ls.V2 = xyz(l2);
+  ls.tri = __float_as_int(l0.w);
+  ls.sel = l1.w;
+  ls.area = l2.w;
+  ls.pk = pk;
+  float v1 = (ul - lo) / pk;
+  ls.clamped = false;
+  if (v1 >= 1.0f) { v1 = 0.99999994f; ls.clamped = true; }
+  if (v1 < 0.0f) { v1 = 0.0f; ls.clamped = true; }
+  ls.v1 = v1;
+  ls.v2 = ul2;
+  ls.su = sqrtf(v1);
+  ls.y = ls.V0 * (1.0f - ls.su) + ls.V1 * (ls.su * (1.0f - ul2)) + ls.V2 * (ls.su * ul2);
+  ls.nl = normalize(cross(ls.V1 - ls.V0, ls.V2 - ls.V0));
+  const Surf lsf = load_surf(S, ls.tri);
+  ls.Le = load_mat(S.mats, lsf.mat).emit;
+  return ls;
+}
+
+// Forward path evaluation.  XA: functor x(i) -> float.  With TAPE the
+// per-segment record for the adjoint is written.
+template <int STACK, bool STATS, bool TAPE, int LMAX, class XA>
+DR_D PathResult path_forward(const DevScene& S, const XA& xa, int L, Tape<LMAX>* tape, TraceStack<STACK> st,
+                             uint32_t* err, TraceStats* stats) {
+  PathResult res;
+  res.rays = 0;
+  res.nseg = 0;
+  const float WH = (float)S.W * (float)S.H;
+  float3 beta = f3(WH, WH, WH);
+  float3 f = f3(0.f, 0.f, 0.f);
+  const float x0 = xa(0), x1 = xa(1);
+  res.pix = pixel_of(x0, x1, S.W, S.H);
+  float3 raw;
+  float3 d = camera_dir(S.cam, x0, x1, &raw);
+  float3 o = S.cam.eye;
+  int prev_tri = -1;
+  bool prev_delta = true;
+  float ppdf = 0.0f;
+  for (int seg = 1; seg <= L; ++seg) {
+    const Ray r = make_ray(o, d);
+    ++res.rays;
+    float th;
+    const int tri = trace_closest<STACK, STATS>(S, r, prev_tri, &th, st, err, stats);
+    if (tri < 0) break;
+    res.nseg = seg;
+    int flags = prev_delta ? kFPrevDelta : 0;
+    if (TAPE) {
+      tape->a[seg - 1] = make_float4(o.x, o.y, o.z, ppdf);
+      tape->b[seg - 1] = make_float4(d.x, d.y, d.z, __int_as_float(tri));
+      tape->c[seg - 1] = make_float4(beta.x, beta.y, beta.z, __int_as_float(flags));
+    }
+    const Surf sf = load_surf(S, tri);
+    const MatP m = load_mat(S.mats, sf.mat);
+    const float t = dot(sf.v0 - o, sf.N) / dot(d, sf.N);
+    const float3 P = o + d * t;
+    if (m.emissive) {
+      const float cl = -dot(sf.ng, d);
+      if (cl > 0.0f) {
+        float w = 1.0f;
+        if (!prev_delta) {
+          const float pl = sf.sel / sf.area * t * t / cl;
+          w = ppdf / (ppdf + pl);
+        }
+        f += beta * m.emit * w;
+      }
+    }
+    if (m.type == kEmitter || seg == L) break;
+    const float3 wo = -d;
+    float3 nraw;
+    float3 ns = shading_normal(S, tri, sf, P, &nraw);
+    const int b = 2 + 4 * (seg - 1);
+    if (m.type == kDielectric) {
+      const bool entering = dot(sf.ng, wo) > 0.0f;
+      const float3 nn = entering ? ns : -ns;
+      const float c = dot(nn, wo);
+      if (!(c > 0.0f)) break;
+      const float eta = entering ? m.ior : 1.0f / m.ior;
+      const float s2 = (1.0f - c * c) / (eta * eta);
+      float F = 1.0f, ct = 0.0f;
+      if (s2 < 1.0f) {
+        ct = sqrtf(1.0f - s2);
+        F = fresnel_dielectric(c, ct, eta);
+      }
+      float3 wi;
+      float wgt;
+      int lobe;
+      if (xa(b) < F) {
+        wi = nn * (2.0f * c) - wo;
+        wgt = 1.0f;
+        lobe = 2;
+      } else {
+        wi = wo * (-1.0f / eta) + nn * (c / eta - ct);
+        wgt = 1.0f / (eta * eta);
+        lobe = 3;
+      }
+      beta = beta * wgt;
+      flags |= kFScatter | (lobe << kFLobeShift);
+      if (TAPE) tape->c[seg - 1].w = __int_as_float(flags);
+      prev_delta = true;
+      ppdf = 0.0f;
+      o = P;
+      d = wi;
+      prev_tri = tri;
+      continue;
+    }
+    float3 ngf = sf.ng;
+    if (dot(ngf, wo) < 0.0f) {
+      ngf = -ngf;
+      ns = -ns;
+    }
+    if (!(dot(ns, wo) > 0.0f)) break;
+    if (S.n_lights > 0) {
+      float lo, pk;
+      const int k = pick_light(S, xa(b + 2), &lo, &pk);
+      flags |= k << kFLightShift;
+      const LightSample ls = light_sample(S, k, xa(b + 2), xa(b + 3), lo, pk);
+      const float3 wv = ls.y - P;
+      const float dist2 = dot(wv, wv);
+      const float dist = sqrtf(dist2);
+      const float3 wi = wv * (1.0f / dist);
+      const float ci = dot(ns, wi);
+      const float cl = -dot(ls.nl, wi);
+      if (ci > 0.0f && cl > 0.0f && dot(ngf, wi) > 0.0f) {
+        ++res.rays;
+        if (!trace_any<STACK, STATS>(S, make_ray(P, wi), dist - S.tmin, tri, ls.tri, st, err, stats)) {
+          flags |= kFNeeVis;
+          float pb;
+          const float3 fs = bsdf_eval(m, ns, wo, wi, &pb);
+          const float pl = ls.sel / ls.area * dist2 / cl;
+          const float g = ci / (pl + pb);
+          f += beta * fs * ls.Le * g;
+        }
+      }
+    }
+    SampleRec s;
+    const bool ok = opaque_sample(m, ns, ngf, wo, xa(b), xa(b + 1), s);
+    if (ok) flags |= kFScatter | (s.lobe << kFLobeShift);
+    if (TAPE) tape->c[seg - 1].w = __int_as_float(flags);
+    if (!ok) break;
+    beta = beta * s.w;
+    prev_delta = false;
+    ppdf = s.pdf;
+    o = P;
+    d = s.wi;
+    prev_tri = tri;
+  }
+  res.f = f;
+  return res;
+}
+
+// Reverse-mode adjoint of p = lum(f) + eps with respect to x, using the tape
+// of a forward pass with the same x.  GW: functor gw(i, value) receiving
+// d log p / d x_i = (d p / d x_i) / p; every i < d is written exactly once.
+template <int LMAX, class XA, class GW>
+DR_D void path_adjoint(const DevScene& S, const XA& xa, int L, float p, const Tape<LMAX>& tape, int nseg,
+                       const GW& gw) {
+  const float inv_p = 1.0f / p;
+  const float3 lw = lum_weights();
+  float3 go = f3(0.f, 0.f, 0.f), gd = f3(0.f, 0.f, 0.f), gbeta = f3(0.f, 0.f, 0.f);
+  float gpp = 0.0f;
+  // vertices that were never reached have zero gradient
+  for (int v = L - 1; v > nseg; --v) {
+    const int b = 2 + 4 * (v - 1);
+    gw(b, 0.f); gw(b + 1, 0.f); gw(b + 2, 0.f); gw(b + 3, 0.f);
+  }
+  for (int seg = nseg; seg >= 1; --seg) {
+    const float4 ta = tape.a[seg - 1], tb = tape.b[seg - 1], tc = tape.c[seg - 1];
+    const float3 o = xyz(ta), d = xyz(tb), beta = xyz(tc);
+    const float ppdf = ta.w;
+    const int tri = __float_as_int(tb.w);
+    const int flags = __float_as_int(tc.w);
+    const bool prev_delta = flags & kFPrevDelta;
+    const Surf sf = load_surf(S, tri);
+    const MatP m = load_mat(S.mats, sf.mat);
+    const float dn = dot(d, sf.N);
+    const float t = dot(sf.v0 - o, sf.N) / dn;
+    const float3 P = o + d * t;
+    float3 gP = f3(0.f, 0.f, 0.f), gdd = f3(0.f, 0.f, 0.f), gbb = f3(0.f, 0.f, 0.f);
+    float gt = 0.0f, gppd = 0.0f;
+    // emission at this hit
+    if (m.emissive) {
+      const float cl = -dot(sf.ng, d);
+      if (cl > 0.0f) {
+        float w = 1.0f;
+        if (!prev_delta) {
+          const float pl = sf.sel / sf.area * t * t / cl;
+          const float den = ppdf + pl;
+          w = ppdf / den;
+          const float gw_ = dot(lw * beta, m.emit);
+          gppd += gw_ * pl / (den * den);
+          const float gpl = -gw_ * ppdf / (den * den);
+          gt += gpl * 2.0f * pl / t;
+          const float gcl = -gpl * pl / cl;
+          gdd += sf.ng * (-gcl);
+        }
+        gbb += lw * m.emit * w;
+      }
+    }
+    const int b = 2 + 4 * (seg - 1);
+    const bool vertex = !(m.type == kEmitter || seg == L);
+    if (vertex) {
+      const float3 wo = -d;
+      float3 gwo = f3(0.f, 0.f, 0.f), gns = f3(0.f, 0.f, 0.f);
+      float3 nraw;
+      const float3 nsn = shading_normal(S, tri, sf, P, &nraw);
+      float sgn = 1.0f;
+      float g0 = 0.f, g1 = 0.f, g2 = 0.f, g3 = 0.f;
+      const int lobe = (flags >> kFLobeShift) & 3;
+      if (m.type == kDielectric) {
+        const bool entering = dot(sf.ng, wo) > 0.0f;
+        sgn = entering ? 1.0f : -1.0f;
+        const float3 nn = nsn * sgn;
+        if (flags & kFScatter) {
+          const float c = dot(nn, wo);
+          const float eta = entering ? m.ior : 1.0f / m.ior;
+          const float wgt = lobe == 2 ? 1.0f : 1.0f / (eta * eta);
+          gbb += gbeta * wgt;
+          gP += go;
+          float3 gnn = f3(0.f, 0.f, 0.f);
+          float gc;
+          if (lobe == 2) {
+            gc = 2.0f * dot(gd, nn);
+            gnn += gd * (2.0f * c);
+            gwo -= gd;
+          } else {
+            const float ct = sqrtf(fmaxf(0.0f, 1.0f - (1.0f - c * c) / (eta * eta)));
+            const float k = c / eta - ct;
+            const float gk = dot(gd, nn);
+            gnn += gd * k;
+            gwo += gd * (-1.0f / eta);
+            gc = gk * (1.0f / eta - (ct > 0.0f ? c / (eta * eta * ct) : 0.0f));
+          }
+          gnn += wo * gc;
+          gwo += nn * gc;
+          gns += gnn;  // in the frame of nn; mapped to nsn below via sgn
+        }
+      } else {
+        float3 ngf = sf.ng;
+        if (dot(ngf, wo) < 0.0f) {
+          ngf = -ngf;
+          sgn = -1.0f;
+        }
+        const float3 ns = nsn * sgn;
+        if (flags & kFNeeVis) {
+          const int k = flags >> kFLightShift;
+          float lo = k == 0 ? 0.0f : __ldg(&S.lights[kLightF4 * (k - 1) + 3].x);
+          const float pk = __ldg(&S.lights[kLightF4 * k + 3].x) - lo;
+          const LightSample ls = light_sample(S, k, xa(b + 2), xa(b + 3), lo, pk);
+          const float3 wv = ls.y - P;
+          const float dist2 = dot(wv, wv);
+          const float dist = sqrtf(dist2);
+          const float3 wi = wv * (1.0f / dist);
+          const float ci = dot(ns, wi);
+          const float cl = -dot(ls.nl, wi);
+          float pb;
+          const float3 fs = bsdf_eval(m, ns, wo, wi, &pb);
+          const float pl = ls.sel / ls.area * dist2 / cl;
+          const float den = pl + pb;
+          const float g = ci / den;
+          gbb += lw * fs * ls.Le * g;
+          const float3 gfs = lw * beta * ls.Le * g;
+          const float gg = dot(lw * beta * fs, ls.Le);
+          const float gci = gg / den;
+          const float gpl = -gg * ci / (den * den);
+          const float gpb = gpl;
+          float3 gwi = f3(0.f, 0.f, 0.f);
+          bsdf_eval_bwd(m, ns, wo, wi, gfs, gpb, gns, gwo, gwi);
+          const float gdist2 = gpl * pl / dist2;
+          const float gcl = -gpl * pl / cl;
+          gwi += ns * gci - ls.nl * gcl;
+          gns += wi * gci;
+          const float3 gwv = (gwi - wi * dot(wi, gwi)) * (1.0f / dist) + wv * (2.0f * gdist2);
+          gP -= gwv;
+          const float3 dy_dsu = -ls.V0 + ls.V1 * (1.0f - ls.v2) + ls.V2 * ls.v2;
+          const float gsu = dot(gwv, dy_dsu);
+          g3 = dot(gwv, (ls.V2 - ls.V1) * ls.su);
+          if (!ls.clamped && ls.su > 0.0f) g2 = gsu / (2.0f * ls.su) / ls.pk;
+        }
+        if (flags & kFScatter) {
+          SampleRec s;
+          opaque_sample(m, ns, ngf, wo, xa(b), xa(b + 1), s);
+          const float ci = dot(ns, s.wi);
+          float pdf;
+          const float3 fs = bsdf_eval(m, ns, wo, s.wi, &pdf);
+          // beta' = beta * fs * ci / pdf
+          gbb += gbeta * s.w;
+          const float3 gwv = gbeta * beta;
+          const float3 gfs = gwv * (ci / pdf);
+          const float gci = dot(gwv, fs) / pdf;
+          const float gpdf = -dot(gwv, fs) * ci / (pdf * pdf) + gpp;
+          float3 gwi = gd;
+          bsdf_eval_bwd(m, ns, wo, s.wi, gfs, gpdf, gns, gwo, gwi);
+          gwi += ns * gci;
+          gns += s.wi * gci;
+          opaque_sample_dir_bwd(m, s.lobe, ns, wo, xa(b), xa(b + 1), gwi, gns, gwo, g0, g1);
+          gP += go;
+        }
+      }
+      // d(ns) -> d(nsn) -> d(P)
+      gP += shading_normal_bwd(S, tri, sf, nraw, nsn, gns * sgn);
+      gdd -= gwo;
+      gw(b, g0 * inv_p);
+      gw(b + 1, g1 * inv_p);
+      gw(b + 2, g2 * inv_p);
+      gw(b + 3, g3 * inv_p);
+    } else if (seg <= L - 1) {
+      gw(b, 0.f); gw(b + 1, 0.f); gw(b + 2, 0.f); gw(b + 3, 0.f);
+    }
+    // hit point P = o + t d, t = ((v0 - o) . N) / (d . N)
+    const float gtt = gt + dot(gP, d);
+    go = gP - sf.N * (gtt / dn);
+    gdd += gP * t - sf.N * (gtt * t / dn);
+    gd = gdd;
+    gbeta = gbb;
+    gpp = gppd;
+  }
+  // camera
+  float g0 = 0.f, g1 = 0.f;
+  if (nseg >= 1) {
+    float3 raw;
+    const float3 d = camera_dir(S.cam, xa(0), xa(1), &raw);
+    const float3 graw = normalize_bwd(raw, d, gd);
+    g0 = 2.0f * S.cam.tx * dot(graw, S.cam.right);
+    g1 = -2.0f * S.cam.ty * dot(graw, S.cam.up);
+  }
+  gw(0, g0 * inv_p);
+  gw(1, g1 * inv_p);
+}
+
+// ---------------------------------------------------------------- mixture
+// Isotropic Gaussian mixture on the torus: g(x) and (optionally) grad g.
+template <class XA, class GW>
+DR_D float mixture_eval(const DevMixture& M, const XA& xa, float eps, bool want_grad, const GW& gw) {
+  if (M.K == 0) {
+    if (want_grad) for (int i = 0; i < M.d; ++i) gw(i, 0.0f);
+    return M.cval;
+  }
+  // pass 1: density
+  float g = 0.0f;
+  for (int k = 0; k < M.K; ++k) {
+    const float s = __ldg(M.sig + k), s2 = s * s;
+    float q = 0.0f;
+    for (int i = 0; i < M.d; ++i) {
+      float dd = xa(i) - __ldg(M.mu + k * M.d + i);
+      dd -= rintf(dd);
+      q += dd * dd;
+    }
+    g += __ldg(M.w + k) * expf(-0.5f * q / s2) * powf(2.0f * kPi * s2, -0.5f * (float)M.d);
+  }
+  if (want_grad) {
+    const float inv = 1.0f / (g + eps);
+    for (int i = 0; i < M.d; ++i) {
+      float gi = 0.0f;
+      for (int k = 0; k < M.K; ++k) {
+        const float s = __ldg(M.sig + k), s2 = s * s;
+        float q = 0.0f;
+        for (int j = 0; j < M.d; ++j) {
+          float dd = xa(j) - __ldg(M.mu + k * M.d + j);
+          dd -= rintf(dd);
+          q += dd * dd;
+        }
+        float di = xa(i) - __ldg(M.mu + k * M.d + i);
+        di -= rintf(di);
+        const float c = __ldg(M.w + k) * expf(-0.5f * q / s2) * powf(2.0f * kPi * s2, -0.5f * (float)M.d);
+        gi -= c * di / s2;
+      }
+      gw(i, gi * inv);
+    }
+  }
+  return g;
+}
+
+}  // namespace dr

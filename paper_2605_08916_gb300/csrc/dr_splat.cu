@@ -1,0 +1,262 @@
+// Atomic-free, deterministic splatting of the ergodic-average contributions
+// into the FP64 image, and Resolve (Alg. 3).
+//
+// The paper atomically adds dt * f / p into an accumulation buffer per chain
+// (Alg. 1, Accumulate).  Here every chain-step emits a 16-B record
+// (pixel, rgb); a batch of records is sorted by pixel with a stable LSD radix
+// sort (8-bit digits; per-tile digit histograms in shared memory, a
+// device-wide exclusive scan, and a stable scatter that ranks equal digits
+// with warp match-any) and then reduced per pixel in FP64 by one writer per
+// pixel.  The sum order is the records' (step, chain) order, so the image is
+// bit-reproducible and equals a sequential FP64 sum of the same records.
+#include "dr_internal.h"
+
+namespace dr {
+
+namespace {
+
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 8;
+constexpr int kSortTile = kSortThreads * kSortItems;
+constexpr int kScanThreads = 1024;
+constexpr int kScanChunk = 2048;
+
+DR_D uint32_t rec_key(const SplatRec& r) { return r.pix; }
+DR_D uint32_t rec_key(const uint2& r) { return r.x; }
+
+template <class R>
+__global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(const R* __restrict__ in, size_t n, int shift,
+                                                                  uint32_t* __restrict__ hist, int ntiles) {
+  __shared__ uint32_t cnt[256];
+  cnt[threadIdx.x] = 0;
+  __syncthreads();
+  const size_t base = (size_t)blockIdx.x * kSortTile;
+#pragma unroll
+  for (int r = 0; r < kSortItems; ++r) {
+    const size_t i = base + (size_t)r * kSortThreads + threadIdx.x;
+    if (i < n) atomicAdd(&cnt[(rec_key(in[i]) >> shift) & 255u], 1u);
+  }
+  __syncthreads();
+  hist[(size_t)threadIdx.x * ntiles + blockIdx.x] = cnt[threadIdx.x];
+}
+
+template <class R>
+__global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(const R* __restrict__ in, R* __restrict__ out,
+                                                                     size_t n, int shift,
+                                                                     const uint32_t* __restrict__ offs, int ntiles) {
+  __shared__ uint32_t run[256];
+  __shared__ uint32_t whist[kSortThreads / 32][256];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  run[threadIdx.x] = offs[(size_t)threadIdx.x * ntiles + blockIdx.x];
+  const size_t base = (size_t)blockIdx.x * kSortTile;
+  const uint32_t lt_mask = (1u << lane) - 1u;
+  for (int r = 0; r < kSortItems; ++r) {
+    const size_t i = base + (size_t)r * kSortThreads + threadIdx.x;
+    const bool valid = i < n;
+    R v;
+    uint32_t digit = 256;
+    if (valid) {
+      v = in[i];
+      digit = (rec_key(v) >> shift) & 255u;
+    }
+#pragma unroll
+    for (int w = 0; w < kSortThreads / 32; ++w) whist[w][threadIdx.x] = 0;
+    __syncthreads();
+    const uint32_t peers = __match_any_sync(0xffffffffu, digit);
+    const uint32_t rank = __popc(peers & lt_mask);
+    if (valid && lane == __ffs(peers) - 1) whist[warp][digit] = __popc(peers);
+    __syncthreads();
+    {
+      uint32_t acc = run[threadIdx.x];
+#pragma unroll
+      for (int w = 0; w < kSortThreads / 32; ++w) {
+        const uint32_t c = whist[w][threadIdx.x];
+        whist[w][threadIdx.x] = acc;
+        acc += c;
+      }
+      run[threadIdx.x] = acc;
+    }
+    __syncthreads();
+    if (valid) out[whist[warp][digit] + rank] = v;
+    __syncthreads();
+  }
+}
+
+// ---------------- device-wide exclusive scan of uint32 (reduce, scan sums, scan chunks)
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* sh, uint32_t* total) {
+  // kScanThreads threads; sh has kScanThreads / 32 entries
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sh[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t s = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += y;
+    }
+    sh[lane] = s;
+  }
+  __syncthreads();
+  const uint32_t warp_off = warp == 0 ? 0u : sh[warp - 1];
+  *total = sh[(blockDim.x >> 5) - 1];
+  __syncthreads();
+  return warp_off + x - v;
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const uint32_t* __restrict__ in, size_t n,
+                                                                   uint32_t* __restrict__ sums) {
+  __shared__ uint32_t sh[32];
+  const size_t base = (size_t)blockIdx.x * kScanChunk;
+  uint32_t v = 0;
+  for (int k = 0; k < kScanChunk / kScanThreads; ++k) {
+    const size_t i = base + (size_t)k * kScanThreads + threadIdx.x;
+    if (i < n) v += in[i];
+  }
+  uint32_t total;
+  block_exclusive_scan(v, sh, &total);
+  if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_sums_kernel(uint32_t* __restrict__ sums, int nchunks) {
+  __shared__ uint32_t sh[32];
+  uint32_t carry = 0;
+  for (int base = 0; base < nchunks; base += kScanThreads) {
+    const int i = base + threadIdx.x;
+    const uint32_t v = i < nchunks ? sums[i] : 0u;
+    uint32_t total;
+    const uint32_t ex = block_exclusive_scan(v, sh, &total);
+    if (i < nchunks) sums[i] = carry + ex;
+    carry += total;
+  }
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_chunks_kernel(const uint32_t* __restrict__ in, size_t n,
+                                                                   const uint32_t* __restrict__ sums,
+                                                                   uint32_t* __restrict__ out) {
+  __shared__ uint32_t sh[32];
+  const size_t base = (size_t)blockIdx.x * kScanChunk;
+  uint32_t carry = sums[blockIdx.x];
+  for (int k = 0; k < kScanChunk / kScanThreads; ++k) {
+    const size_t i = base + (size_t)k * kScanThreads + threadIdx.x;
+    const uint32_t v = i < n ? in[i] : 0u;
+    uint32_t total;
+    const uint32_t ex = block_exclusive_scan(v, sh, &total);
+    if (i < n) out[i] = carry + ex;
+    carry += total;
+  }
+}
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+struct SortScratch {
+  uint32_t* hist;
+  uint32_t* offs;
+  uint32_t* sums;
+  int ntiles;
+  size_t nhist;
+  int nchunks;
+};
+
+SortScratch carve(void* scratch, size_t n) {
+  SortScratch s;
+  s.ntiles = (int)((n + kSortTile - 1) / kSortTile);
+  if (s.ntiles < 1) s.ntiles = 1;
+  s.nhist = (size_t)256 * s.ntiles;
+  s.nchunks = (int)((s.nhist + kScanChunk - 1) / kScanChunk);
+  char* p = static_cast<char*>(scratch);
+  s.hist = reinterpret_cast<uint32_t*>(p);
+  p += align256(s.nhist * 4);
+  s.offs = reinterpret_cast<uint32_t*>(p);
+  p += align256(s.nhist * 4);
+  s.sums = reinterpret_cast<uint32_t*>(p);
+  return s;
+}
+
+template <class R>
+R* radix_sort(R* in, R* out, size_t n, int bits, void* scratch, cudaStream_t st) {
+  if (n == 0) return in;
+  SortScratch s = carve(scratch, n);
+  R* src = in;
+  R* dst = out;
+  for (int shift = 0; shift < bits; shift += 8) {
+    radix_hist_kernel<R><<<s.ntiles, kSortThreads, 0, st>>>(src, n, shift, s.hist, s.ntiles);
+    scan_reduce_kernel<<<s.nchunks, kScanThreads, 0, st>>>(s.hist, s.nhist, s.sums);
+    scan_sums_kernel<<<1, kScanThreads, 0, st>>>(s.sums, s.nchunks);
+    scan_chunks_kernel<<<s.nchunks, kScanThreads, 0, st>>>(s.hist, s.nhist, s.sums, s.offs);
+    radix_scatter_kernel<R><<<s.ntiles, kSortThreads, 0, st>>>(src, dst, n, shift, s.offs, s.ntiles);
+    R* t = src;
+    src = dst;
+    dst = t;
+  }
+  return src;
+}
+
+__global__ void segment_reduce_kernel(const SplatRec* __restrict__ s, size_t n, double* __restrict__ accum,
+                                      uint32_t n_pix, uint32_t* err) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t pix = s[i].pix;
+  if (i > 0 && s[i - 1].pix == pix) return;
+  if (pix >= n_pix) {
+    atomicOr(err, kErrBadIndex);
+    return;
+  }
+  double r = 0.0, g = 0.0, b = 0.0;
+  for (size_t k = i; k < n; ++k) {
+    const SplatRec q = s[k];
+    if (q.pix != pix) break;
+    r += (double)q.r;
+    g += (double)q.g;
+    b += (double)q.b;
+  }
+  accum[(size_t)pix * 3 + 0] += r;
+  accum[(size_t)pix * 3 + 1] += g;
+  accum[(size_t)pix * 3 + 2] += b;
+}
+
+__global__ void resolve_kernel(const double* __restrict__ accum, size_t n,
+                               const unsigned long long* __restrict__ tour_count, double k0, float* __restrict__ out) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const unsigned long long tc = *tour_count;
+  out[i] = tc == 0ull ? 0.0f : (float)(k0 / (double)tc * accum[i]);
+}
+
+}  // namespace
+
+size_t sort_scratch_bytes(size_t n) {
+  size_t ntiles = (n + kSortTile - 1) / kSortTile;
+  if (ntiles < 1) ntiles = 1;
+  const size_t nhist = 256 * ntiles;
+  const size_t nchunks = (nhist + kScanChunk - 1) / kScanChunk;
+  return 2 * align256(nhist * 4) + align256(nchunks * 4);
+}
+
+SplatRec* sort_splat_records(SplatRec* in, SplatRec* out, size_t n, int bits, void* scratch, cudaStream_t s) {
+  return radix_sort<SplatRec>(in, out, n, bits, scratch, s);
+}
+
+uint2* sort_pairs(uint2* in, uint2* out, size_t n, int bits, void* scratch, cudaStream_t s) {
+  return radix_sort<uint2>(in, out, n, bits, scratch, s);
+}
+
+void launch_segment_reduce(const SplatRec* sorted, size_t n, double* accum, uint32_t n_pix, uint32_t* err,
+                           cudaStream_t s) {
+  if (n == 0) return;
+  segment_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(sorted, n, accum, n_pix, err);
+}
+
+void launch_resolve(const double* accum, size_t n, const unsigned long long* tour_count, double k0, float* out,
+                    cudaStream_t s) {
+  if (n == 0) return;
+  resolve_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(accum, n, tour_count, k0, out);
+}
+
+}  // namespace dr

@@ -1,0 +1,213 @@
+// BVH traversal for the path-contribution kernels.
+//
+// The paper traces rays with hardware RT cores through a graphics API
+// (Sec. 4.3, "ray tracing and compute shaders"); GB300 has no RT cores, so
+// traversal is software: a binary BVH whose nodes hold both children's boxes
+// (one 64-B node = four 16-B vector loads), leaf triangles in 48-B records
+// (three 16-B loads), read through the read-only path, and a per-thread
+// traversal stack staged in shared memory (layout [depth][thread], so a warp's
+// pushes and pops hit 32 distinct banks).
+#pragma once
+#include "dr_common.cuh"
+
+namespace dr {
+
+struct Ray {
+  float3 o, d, inv;
+};
+
+DR_D Ray make_ray(float3 o, float3 d) {
+  Ray r;
+  r.o = o;
+  r.d = d;
+  r.inv = f3(1.0f / d.x, 1.0f / d.y, 1.0f / d.z);
+  return r;
+}
+
+// Slab test of one box against [0, tmax]; returns entry distance or +inf.
+DR_D float box_entry(float3 lo, float3 hi, const Ray& r, float tmax) {
+  const float tx0 = (lo.x - r.o.x) * r.inv.x, tx1 = (hi.x - r.o.x) * r.inv.x;
+  const float ty0 = (lo.y - r.o.y) * r.inv.y, ty1 = (hi.y - r.o.y) * r.inv.y;
+  const float tz0 = (lo.z - r.o.z) * r.inv.z, tz1 = (hi.z - r.o.z) * r.inv.z;
+  const float tn = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), 0.0f));
+  const float tf = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), tmax));
+  // a small relative slack keeps boxes of hits at exactly tmax
+  return tn <= tf * 1.0000002f ? tn : __int_as_float(0x7f800000);
+}
+
+// Moller-Trumbore; hit iff det != 0, u >= 0, v >= 0, u + v <= 1, tmin < t < tmax.
+DR_D bool tri_test(float3 v0, float3 e1, float3 e2, const Ray& r, float tmin, float tmax, float* t_out) {
+  const float3 p = cross(r.d, e2);
+  const float det = dot(e1, p);
+  if (det == 0.0f) return false;
+  const float inv = 1.0f / det;
+  const float3 tv = r.o - v0;
+  const float u = dot(tv, p) * inv;
+  if (u < 0.0f || u > 1.0f) return false;
+  const float3 q = cross(tv, e1);
+  const float v = dot(r.d, q) * inv;
+  if (v < 0.0f || u + v > 1.0f) return false;
+  const float t = dot(e2, q) * inv;
+  if (!(t > tmin && t < tmax)) return false;
+  *t_out = t;
+  return true;
+}
+
+struct TraceStats {
+  uint32_t nodes, tris;
+};
+
+template <int STACK>
+struct TraceStack {
+  int* base;  // shared memory, [STACK][blockDim.x]
+  int stride;
+  DR_D int& at(int i) { return base[i * stride]; }
+};
+
+DR_D void load_node(const float4* __restrict__ nodes, int n, float3& lo0, float3& hi0, float3& lo1, float3& hi1,
+                    int& c0, int& c1) {
+  const float4 a = __ldg(nodes + 4 * n + 0);
+  const float4 b = __ldg(nodes + 4 * n + 1);
+  const float4 c = __ldg(nodes + 4 * n + 2);
+  const int4 e = __ldg(reinterpret_cast<const int4*>(nodes) + 4 * n + 3);
+  lo0 = f3(a.x, a.y, a.z);
+  hi0 = f3(a.w, b.x, b.y);
+  lo1 = f3(b.z, b.w, c.x);
+  hi1 = f3(c.y, c.z, c.w);
+  c0 = e.x;
+  c1 = e.y;
+}
+
+// Closest hit with t in (tmin, inf), skipping triangle `exclude` (original
+// id).  Equal distances resolve to the smaller original triangle id.
+// Returns the original triangle id or -1.
+template <int STACK, bool STATS>
+DR_D int trace_closest(const DevScene& S, const Ray& r, int exclude, float* t_hit, TraceStack<STACK> st,
+                       uint32_t* err, TraceStats* stats) {
+  float tbest = __int_as_float(0x7f800000);
+  int best = -1;
+  int sp = 0;
+  int node = 0;
+  // a tree traversal visits every inner node at most once: more visits mean
+  // a corrupt hierarchy, reported instead of looping
+  int budget = 2 * S.n_nodes + 64;
+  while (true) {
+    if (--budget < 0 || node < 0 || node >= S.n_nodes) {
+      *err |= kErrBadIndex;
+      break;
+    }
+    float3 lo0, hi0, lo1, hi1;
+    int c0, c1;
+    load_node(S.nodes, node, lo0, hi0, lo1, hi1, c0, c1);
+    if (STATS) ++stats->nodes;
+    float e0 = box_entry(lo0, hi0, r, tbest);
+    float e1 = box_entry(lo1, hi1, r, tbest);
+    // leaves are processed on the spot, inner children are descended into
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int c = k == 0 ? c0 : c1;
+      const float e = k == 0 ? e0 : e1;
+      if (c < 0 && e <= tbest) {
+        const int first = leaf_first(c);
+        int cnt = leaf_count(c);
+        if (first + cnt > S.n_tris) {
+          *err |= kErrBadIndex;
+          cnt = 0;
+        }
+        for (int i = 0; i < cnt; ++i) {
+          const float4 t0 = __ldg(S.tris + 3 * (first + i) + 0);
+          const float4 t1 = __ldg(S.tris + 3 * (first + i) + 1);
+          const float4 t2 = __ldg(S.tris + 3 * (first + i) + 2);
+          const int id = __float_as_int(t0.w);
+          if (STATS) ++stats->tris;
+          float th;
+          if (id != exclude && tri_test(xyz(t0), xyz(t1), xyz(t2), r, S.tmin, tbest * 1.0000001f + 1e-30f, &th)) {
+            if (th < tbest || (th == tbest && id < best)) {
+              tbest = th;
+              best = id;
+            }
+          }
+        }
+      }
+    }
+    const bool in0 = c0 >= 0 && e0 <= tbest, in1 = c1 >= 0 && e1 <= tbest;
+    if (in0 && in1) {
+      const int nearc = e0 <= e1 ? c0 : c1, farc = e0 <= e1 ? c1 : c0;
+      if (sp < STACK) {
+        st.at(sp++) = farc;
+      } else {
+        *err |= kErrStackOverflow;
+      }
+      node = nearc;
+      continue;
+    }
+    if (in0) { node = c0; continue; }
+    if (in1) { node = c1; continue; }
+    // pop, skipping nothing (boxes are re-tested against the shrunken tbest
+    // when the popped node's children are examined)
+    if (sp == 0) break;
+    node = st.at(--sp);
+  }
+  *t_hit = tbest;
+  return best;
+}
+
+// Any hit with t in (tmin, tmax), skipping two triangle ids.
+template <int STACK, bool STATS>
+DR_D bool trace_any(const DevScene& S, const Ray& r, float tmax, int ex0, int ex1, TraceStack<STACK> st,
+                    uint32_t* err, TraceStats* stats) {
+  int sp = 0;
+  int node = 0;
+  int budget = 2 * S.n_nodes + 64;
+  while (true) {
+    if (--budget < 0 || node < 0 || node >= S.n_nodes) {
+      *err |= kErrBadIndex;
+      break;
+    }
+    float3 lo0, hi0, lo1, hi1;
+    int c0, c1;
+    load_node(S.nodes, node, lo0, hi0, lo1, hi1, c0, c1);
+    if (STATS) ++stats->nodes;
+    const float e0 = box_entry(lo0, hi0, r, tmax);
+    const float e1 = box_entry(lo1, hi1, r, tmax);
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int c = k == 0 ? c0 : c1;
+      const float e = k == 0 ? e0 : e1;
+      if (c < 0 && e <= tmax) {
+        const int first = leaf_first(c);
+        int cnt = leaf_count(c);
+        if (first + cnt > S.n_tris) {
+          *err |= kErrBadIndex;
+          cnt = 0;
+        }
+        for (int i = 0; i < cnt; ++i) {
+          const float4 t0 = __ldg(S.tris + 3 * (first + i) + 0);
+          const float4 t1 = __ldg(S.tris + 3 * (first + i) + 1);
+          const float4 t2 = __ldg(S.tris + 3 * (first + i) + 2);
+          const int id = __float_as_int(t0.w);
+          if (STATS) ++stats->tris;
+          float th;
+          if (id != ex0 && id != ex1 && tri_test(xyz(t0), xyz(t1), xyz(t2), r, S.tmin, tmax, &th)) return true;
+        }
+      }
+    }
+    const bool in0 = c0 >= 0 && e0 <= tmax, in1 = c1 >= 0 && e1 <= tmax;
+    if (in0 && in1) {
+      if (sp < STACK) {
+        st.at(sp++) = e0 <= e1 ? c1 : c0;
+      } else {
+        *err |= kErrStackOverflow;
+      }
+      node = e0 <= e1 ? c0 : c1;
+      continue;
+    }
+    if (in0) { node = c0; continue; }
+    if (in1) { node = c1; continue; }
+    if (sp == 0) break;
+    node = st.at(--sp);
+  }
+  return false;
+}
+
+}  // namespace dr

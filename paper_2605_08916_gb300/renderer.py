@@ -1,0 +1,225 @@
+"""Torch-facing wrapper of the C ABI: device tensors in, device tensors out.
+
+PyTorch provides device memory and the CUDA stream; all computation runs in
+``libdiffrestore.so``.  ``LogPFunction`` exposes x -> log p as an autograd
+function whose backward uses the library's hand-written adjoint kernel.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import call, dr_params
+
+DRIFT = {"none": _lib.DR_DRIFT_NONE, "fd": _lib.DR_DRIFT_FD, "adjoint": _lib.DR_DRIFT_ADJOINT}
+
+
+def make_params(L=4, drift="adjoint", rb=True, stddev=5e-3, dt=1e-5, gamma_tilde=None, eps=1e-8, fd_h=1e-3, m=64.0,
+                k0=0.0, steps_per_splat=16):
+    """Diffusion Restore parameters (Sec. 5.3 and Sec. 6).  gamma_tilde
+    defaults to stddev^2 / 2 (gamma = sigma^2); k0 <= 0 means estimate
+    p_lambda from the initial samples and set k0 = p_lambda / (m dt)."""
+    if gamma_tilde is None:
+        gamma_tilde = 0.5 * stddev * stddev
+    return dr_params(int(L), DRIFT[drift] if isinstance(drift, str) else int(drift), int(bool(rb)),
+                     int(steps_per_splat), float(stddev), float(dt), float(gamma_tilde), float(eps), float(fd_h),
+                     float(m), float(k0))
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        assert t.flags["C_CONTIGUOUS"]
+        return t.ctypes.data_as(C.c_void_p)
+    assert t.is_contiguous()
+    return C.c_void_p(t.data_ptr())
+
+
+class Renderer:
+    """One library context on one CUDA device."""
+
+    def __init__(self, device=0, stream=None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("Renderer needs a CUDA device (the library has no CPU path)")
+        self.device = torch.device("cuda", device)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        self.stream = stream
+        h = C.c_void_p()
+        call("dr_create", C.byref(h), int(device), C.c_void_p(stream.cuda_stream))
+        self.h = h
+        self.width = self.height = 0
+        self.d = 0
+        self.N = 0
+        self.L = 0
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.load().dr_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---------------------------------------------------------------- inputs
+    def upload_scene(self, scene):
+        v = np.ascontiguousarray(scene.verts, np.float32)
+        t = np.ascontiguousarray(scene.tris, np.int32)
+        n = None if scene.normals is None else np.ascontiguousarray(scene.normals, np.float32)
+        tm = np.ascontiguousarray(scene.tri_mat, np.int32)
+        m = np.ascontiguousarray(scene.materials, np.float32)
+        cam = np.ascontiguousarray(scene.camera, np.float32)
+        call("dr_scene_upload", self.h, _ptr(v), v.shape[0], _ptr(t), _ptr(n), t.shape[0], _ptr(tm), _ptr(m),
+             m.shape[0], _ptr(cam), int(scene.width), int(scene.height))
+        self.width, self.height = int(scene.width), int(scene.height)
+        self.kind = 0
+
+    def set_mixture(self, mix):
+        w = np.ascontiguousarray(mix.w, np.float32).reshape(-1)
+        mu = np.ascontiguousarray(mix.mu, np.float32).reshape(-1)
+        sig = np.ascontiguousarray(mix.sig, np.float32).reshape(-1)
+        call("dr_target_mixture", self.h, int(mix.d), int(mix.K), _ptr(w) if w.size else None,
+             _ptr(mu) if mu.size else None, _ptr(sig) if sig.size else None, float(mix.const), int(mix.width),
+             int(mix.height))
+        self.width, self.height = int(mix.width), int(mix.height)
+        self.kind = 1
+        self.mix_d = int(mix.d)
+
+    # ---------------------------------------------------------------- chains
+    def init_chains(self, n_chains, seed, params, frame=0):
+        self.params = params
+        call("dr_chains_init", self.h, int(n_chains), int(seed), int(frame), C.byref(params))
+        self.N = int(n_chains)
+        self.L = int(params.max_path_len)
+        self.d = 2 + 4 * (self.L - 1) if self.kind == 0 else self.mix_d
+
+    def step(self, n=1):
+        call("dr_step", self.h, int(n))
+
+    def splat(self):
+        call("dr_splat", self.h)
+
+    def resolve(self, out=None):
+        if out is None:
+            out = torch.empty((self.height, self.width, 3), dtype=torch.float32, device=self.device)
+        call("dr_resolve", self.h, _ptr(out))
+        return out
+
+    def clear_image(self):
+        call("dr_clear_image", self.h)
+
+    def readback_state(self, fields=("x", "score", "killed", "logp", "pix", "val")):
+        N, d = self.N, self.d
+        out = {}
+        bufs = {
+            "x": np.zeros((N, d), np.float32) if "x" in fields else None,
+            "score": np.zeros((N, d), np.float32) if "score" in fields else None,
+            "killed": np.zeros(N, np.uint8) if "killed" in fields else None,
+            "logp": np.zeros(N, np.float32) if "logp" in fields else None,
+            "pix": np.zeros(N, np.int32) if "pix" in fields else None,
+            "val": np.zeros((N, 3), np.float32) if "val" in fields else None,
+        }
+        call("dr_readback_state", self.h, *[_ptr(bufs[k]) for k in ("x", "score", "killed", "logp", "pix", "val")])
+        for k, v in bufs.items():
+            if v is not None:
+                out[k] = v
+        return out
+
+    def readback_accum(self):
+        a = np.zeros((self.width * self.height, 3), np.float64)
+        call("dr_readback_accum", self.h, _ptr(a))
+        return a
+
+    def counters(self):
+        tc, st, rays = C.c_uint64(), C.c_uint64(), C.c_uint64()
+        k0, pl = C.c_double(), C.c_double()
+        call("dr_get_counters", self.h, C.byref(tc), C.byref(k0), C.byref(st), C.byref(rays), C.byref(pl))
+        return {"tour_count": tc.value, "k0": k0.value, "steps": st.value, "rays": rays.value, "p_lambda": pl.value}
+
+    def set_stats(self, enable=True):
+        call("dr_set_stats", self.h, int(bool(enable)))
+
+    def traversal_stats(self):
+        a, b, c = C.c_uint64(), C.c_uint64(), C.c_uint64()
+        call("dr_get_traversal_stats", self.h, C.byref(a), C.byref(b), C.byref(c))
+        return {"node_visits": a.value, "tri_tests": b.value, "rays": c.value}
+
+    def bvh_info(self):
+        a, b, c = C.c_int32(), C.c_int32(), C.c_int32()
+        call("dr_bvh_info", self.h, C.byref(a), C.byref(b), C.byref(c))
+        return {"n_nodes": a.value, "n_tris": b.value, "max_depth": c.value}
+
+    def state_save(self):
+        n = C.c_size_t(0)
+        call("dr_state_save", self.h, None, C.byref(n))
+        buf = np.zeros(n.value, np.uint8)
+        call("dr_state_save", self.h, _ptr(buf), C.byref(n))
+        return buf
+
+    def state_load(self, buf):
+        buf = np.ascontiguousarray(buf, np.uint8)
+        call("dr_state_load", self.h, _ptr(buf), buf.size)
+
+    # ---------------------------------------------------------------- queries
+    def eval_logp(self, x, L=None, grad=False, want_f=False):
+        """x: float32 CUDA tensor [M, d]. Returns (logp [M], grad [M, d] or
+        None, pix [M], f [M, 3] or None)."""
+        L = self.L if L is None else int(L)
+        x = x.contiguous()
+        M = x.shape[0]
+        logp = torch.empty(M, dtype=torch.float32, device=x.device)
+        g = torch.empty_like(x) if grad else None
+        pix = torch.empty(M, dtype=torch.int32, device=x.device)
+        f = torch.empty((M, 3), dtype=torch.float32, device=x.device) if want_f else None
+        call("dr_eval_logp", self.h, int(L), _ptr(x), int(M), _ptr(logp), _ptr(g), _ptr(pix), _ptr(f))
+        return logp, g, pix, f
+
+    def trace_closest(self, rays, exclude=-1):
+        rays = rays.contiguous()
+        n = rays.shape[0]
+        tri = torch.empty(n, dtype=torch.int32, device=rays.device)
+        t = torch.empty(n, dtype=torch.float32, device=rays.device)
+        call("dr_trace_closest", self.h, _ptr(rays), int(n), int(exclude), _ptr(tri), _ptr(t))
+        return tri, t
+
+    def splat_records(self, recs):
+        """recs: CUDA tensor of 16-byte records viewed as int32 [M, 4] (pixel
+        index, then float bits of r, g, b)."""
+        recs = recs.contiguous()
+        call("dr_splat_records", self.h, _ptr(recs), int(recs.shape[0]))
+
+
+def philox(ctr, key, stream=None):
+    """ctr uint32 [n, 4], key uint32 [n, 2] as int32 CUDA tensors -> [n, 4]."""
+    out = torch.empty_like(ctr)
+    s = stream if stream is not None else torch.cuda.current_stream(ctr.device)
+    call("dr_philox", _ptr(ctr.contiguous()), _ptr(key.contiguous()), _ptr(out), int(ctr.shape[0]),
+         C.c_void_p(s.cuda_stream))
+    return out
+
+
+class LogPFunction(torch.autograd.Function):
+    """x [M, d] (CUDA float32) -> log p(x) [M] through the library; the
+    backward recomputes the paths and applies the hand-written adjoint
+    (grad log p), scaled by the incoming gradient."""
+
+    @staticmethod
+    def forward(ctx, x, renderer, L):
+        logp, _, _, _ = renderer.eval_logp(x.detach(), L=L, grad=False)
+        ctx.save_for_backward(x)
+        ctx.renderer = renderer
+        ctx.L = L
+        return logp
+
+    @staticmethod
+    def backward(ctx, g):
+        (x,) = ctx.saved_tensors
+        _, grad, _, _ = ctx.renderer.eval_logp(x.detach(), L=ctx.L, grad=True)
+        return grad * g.unsqueeze(1), None, None

@@ -1,0 +1,307 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 oracle
+on the same seeded inputs and the same Philox4x32-10 streams.
+
+Tolerances (FP32 kernels vs FP64 oracle):
+* Philox, splat reduction (same records): bit-exact.
+* Closest-hit triangle ids: identical except on edge/tie cases, where the
+  two distances must agree to 1e-4 relative.
+* Chain state over 16-step horizons: torus distance of x <= 1e-4,
+  |log p difference| <= 1e-4 max(1, |log p|), splat values within 1e-4
+  relative, kill flags and pixels identical.  A chain whose discrete choices
+  differ (kill, pixel, or an x jump beyond tolerance after an edge crossing)
+  is counted as divergent from that step on; the divergent fraction is
+  bounded.
+* grad log p (hand-written adjoint, FP32) vs the oracle's dual-number
+  gradient: relative L2 error <= 1e-3 on >= 97% of points with f > 0.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2605_08916_gb300 import scenes as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as T
+    assert T.cuda.is_available(), "GPU tests need a CUDA device"
+    return T
+
+
+@pytest.fixture(scope="module")
+def R(torch):
+    from paper_2605_08916_gb300 import renderer
+    return renderer
+
+
+def torus_dist(a, b):
+    d = np.asarray(a, np.float64) - np.asarray(b, np.float64)
+    return np.abs(d - np.round(d))
+
+
+def test_philox_bit_exact(torch, R, oracle):
+    rng = np.random.default_rng(1)
+    n = 8192
+    ctr = rng.integers(0, 2 ** 32, (n, 4), dtype=np.uint64).astype(np.uint32)
+    key = rng.integers(0, 2 ** 32, (n, 2), dtype=np.uint64).astype(np.uint32)
+    g = R.philox(torch.from_numpy(ctr.view(np.int32)).cuda(), torch.from_numpy(key.view(np.int32)).cuda())
+    torch.cuda.synchronize()
+    mine = g.cpu().numpy().view(np.uint32)
+    assert np.array_equal(mine, oracle.philox4x32_10(ctr, key))
+
+
+@pytest.mark.parametrize("which", ["cornell", "caustic", "procedural"])
+def test_closest_hit_matches_oracle(torch, R, oracle, which):
+    if which == "cornell":
+        scene = S.cornell_box(1, 16, 16)
+    elif which == "caustic":
+        scene = S.caustic_scene(1, 16, 16, n_theta=40, n_phi=40)
+    else:
+        scene = S.procedural_scene(1, 32, 18, target_tris=30000, n_objects=40)
+    r = R.Renderer()
+    r.upload_scene(scene)
+    info = r.bvh_info()
+    assert info["n_tris"] == scene.n_tris and info["max_depth"] < 48
+    tgt = oracle.OracleScene(scene)
+    lo, hi = scene.verts.min(0), scene.verts.max(0)
+    rng = np.random.default_rng(2)
+    n = 20000
+    o = (lo + (hi - lo) * rng.uniform(0.05, 0.95, (n, 3))).astype(np.float32)
+    d = rng.normal(size=(n, 3)).astype(np.float32)
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    rays = torch.from_numpy(np.concatenate([o, d], 1)).cuda()
+    tri_g, t_g = r.trace_closest(rays)
+    torch.cuda.synchronize()
+    tri_g, t_g = tri_g.cpu().numpy(), t_g.cpu().numpy()
+    tri_o, t_o = tgt.trace(o.astype(np.float64), d.astype(np.float64))
+    same = tri_g == tri_o
+    assert same.mean() > 0.999, same.mean()
+    bad = ~same
+    both = bad & (tri_g >= 0) & (tri_o >= 0)
+    assert np.all(np.abs(t_g[both] - t_o[both]) <= 1e-4 * np.maximum(1.0, t_o[both]))
+    hit = same & (tri_o >= 0)
+    assert np.allclose(t_g[hit], t_o[hit], rtol=1e-4, atol=1e-5)
+    r.close()
+
+
+EVAL_CASES = {
+    "cornell-L4": (lambda: S.cornell_box(1, 64, 64), 4),
+    "glossy-L8": (lambda: S.cornell_box(1, 256, 256, glossy=True), 8),
+    "caustic-L6": (lambda: S.caustic_scene(1, 64, 64, n_theta=24, n_phi=24), 6),
+}
+
+
+@pytest.mark.parametrize("case", list(EVAL_CASES))
+def test_eval_logp_and_adjoint_match_oracle(torch, R, oracle, case):
+    make, L = EVAL_CASES[case]
+    scene = make()
+    d = S.pss_dim(L)
+    r = R.Renderer()
+    r.upload_scene(scene)
+    rng = np.random.default_rng(3)
+    M = 3000
+    x = rng.random((M, d)).astype(np.float32)
+    lp, g, pix, f = r.eval_logp(torch.from_numpy(x).cuda(), L=L, grad=True, want_f=True)
+    torch.cuda.synchronize()
+    lp, g, pix, f = lp.cpu().numpy(), g.cpu().numpy(), pix.cpu().numpy(), f.cpu().numpy()
+    ro = oracle.evaluate(oracle.OracleScene(scene), x.astype(np.float64), L, grad=True)
+    assert np.array_equal(pix, ro["pix"])
+    lit = ro["f"].sum(1) > 0
+    assert lit.mean() > 0.03
+    ok_lp = np.abs(lp - ro["logp"]) <= 1e-4 * np.maximum(1.0, np.abs(ro["logp"]))
+    assert ok_lp.mean() > 0.995, ok_lp.mean()
+    go = ro["grad"]
+    rel = np.linalg.norm(g - go, axis=1) / np.maximum(np.linalg.norm(go, axis=1), 1e-6)
+    good = rel[lit & ok_lp] <= 1e-3
+    print(f"{case}: median rel grad err {np.median(rel[lit]):.2e}, frac<=1e-3 {good.mean():.4f}")
+    assert good.mean() >= 0.97, good.mean()
+    r.close()
+
+
+def _chain_parity(torch, R, oracle, target_obj, params_gpu, params_orc, N, M, T, seed, x_tol=1e-4):
+    r = R.Renderer()
+    if isinstance(target_obj, S.Scene):
+        r.upload_scene(target_obj)
+    else:
+        r.set_mixture(target_obj)
+    r.init_chains(N, seed, params_gpu)
+    tgt = oracle.target(target_obj)
+    ro = oracle.restore_run(tgt, params_orc, seed=seed, chain_ids=np.arange(M), n_steps=T)
+    alive = np.ones(M, bool)
+    first_div = np.full(M, -1)
+    n_cmp = 0
+    for s in range(T + 1):
+        if s > 0:
+            r.step(1)
+        st = r.readback_state()
+        xg, lg, kg, pg, vg = st["x"][:M], st["logp"][:M], st["killed"][:M], st["pix"][:M], st["val"][:M]
+        xo, lo_, ko, po, vo = ro["x"][s], ro["logp"][s], ro["killed"][s], ro["pix"][s], ro["val"][s]
+        xerr = torus_dist(xg, xo).max(1)
+        ok = (kg == ko) & (pg == po) & (xerr <= x_tol)
+        ok &= np.abs(lg - lo_) <= 1e-4 * np.maximum(1.0, np.abs(lo_))
+        vn = np.linalg.norm(vo, axis=1)
+        ok &= np.linalg.norm(vg - vo, axis=1) <= 1e-4 * vn + 1e-12
+        newly = alive & ~ok
+        first_div[newly] = s
+        alive &= ok
+        n_cmp += alive.sum()
+    frac_div = 1.0 - alive.mean()
+    r.close()
+    return frac_div, first_div, n_cmp
+
+
+def test_chain_parity_mixture_target(torch, R, oracle):
+    mix = S.gaussian_mixture(seed=4, d=4, K=3, sig_range=(0.08, 0.12), width=16, height=16)
+    k0 = 1.0 / (64 * 1e-5)
+    pg = R.make_params(L=1, drift="adjoint", rb=True, k0=k0, steps_per_splat=4)
+    po = oracle.make_params(L=1, drift="exact", rb=True, k0=k0)
+    frac, first, n = _chain_parity(torch, R, oracle, mix, pg, po, N=8192, M=2048, T=16, seed=21)
+    print("mixture divergent fraction", frac, "compared", n)
+    assert frac <= 0.002
+
+
+def test_chain_parity_cornell_fd(torch, R, oracle):
+    scene = S.cornell_box(1, 64, 64)
+    k0 = 5000.0
+    pg = R.make_params(L=4, drift="fd", rb=True, k0=k0, fd_h=1e-3, steps_per_splat=8)
+    po = oracle.make_params(L=4, drift="fd", rb=True, k0=k0, fd_h=1e-3)
+    frac, first, n = _chain_parity(torch, R, oracle, scene, pg, po, N=4096, M=512, T=16, seed=5)
+    print("cornell fd divergent fraction", frac, "compared", n)
+    assert frac <= 0.01
+
+
+def test_chain_parity_glossy_adjoint(torch, R, oracle):
+    scene = S.cornell_box(1, 256, 256, glossy=True)
+    k0 = 1e6
+    pg = R.make_params(L=8, drift="adjoint", rb=True, k0=k0, steps_per_splat=16)
+    po = oracle.make_params(L=8, drift="exact", rb=True, k0=k0)
+    frac, first, n = _chain_parity(torch, R, oracle, scene, pg, po, N=65536, M=512, T=16, seed=6)
+    print("glossy adjoint divergent fraction", frac, "compared", n)
+    assert frac <= 0.01
+
+
+def test_chain_parity_race_clock(torch, R, oracle):
+    scene = S.cornell_box(2, 32, 32)
+    k0 = 2000.0
+    pg = R.make_params(L=4, drift="adjoint", rb=False, k0=k0, steps_per_splat=4)
+    po = oracle.make_params(L=4, drift="exact", rb=False, k0=k0)
+    frac, first, n = _chain_parity(torch, R, oracle, scene, pg, po, N=1024, M=512, T=16, seed=8)
+    print("race-clock divergent fraction", frac)
+    assert frac <= 0.01
+
+
+def test_k0_estimate_matches_oracle(torch, R, oracle):
+    scene = S.cornell_box(1, 64, 64)
+    N = 4096
+    r = R.Renderer()
+    r.upload_scene(scene)
+    r.init_chains(N, 17, R.make_params(L=4, drift="adjoint", k0=0.0))
+    c = r.counters()
+    ro = oracle.restore_run(oracle.OracleScene(scene), oracle.make_params(L=4, drift="none", k0=1.0), seed=17,
+                            chain_ids=np.arange(N), n_steps=0, record=False)
+    p_lambda = ro["p_init_sum"] / N
+    assert abs(c["p_lambda"] / p_lambda - 1.0) < 1e-4
+    assert abs(c["k0"] - p_lambda / (64 * 1e-5)) < 1e-4 * c["k0"]
+    r.close()
+
+
+def test_splat_is_bit_exact_sequential_sum(torch, R):
+    r = R.Renderer()
+    W, H = 64, 48
+    r.set_mixture(S.constant_target(d=2, value=1.0, width=W, height=H))
+    r.init_chains(16, 1, R.make_params(L=1, drift="none", k0=1.0))
+    r.clear_image()
+    rng = np.random.default_rng(7)
+    M = 300000
+    pix = (rng.zipf(1.3, M) % (W * H)).astype(np.uint32)   # heavy duplicates
+    val = rng.normal(size=(M, 3)).astype(np.float32) * np.float32(1e-3)
+    rec = np.zeros((M, 4), np.int32)
+    rec[:, 0] = pix.view(np.int32)
+    rec[:, 1:] = val.view(np.int32)
+    r.splat_records(torch.from_numpy(rec).cuda())
+    acc = r.readback_accum()
+    ref = np.zeros((W * H, 3))
+    for c in range(3):
+        ref[:, c] = np.bincount(pix, weights=val[:, c].astype(np.float64), minlength=W * H)
+    assert np.array_equal(acc, ref)
+    r.close()
+
+
+def test_resolve_is_k0_over_tourcount_times_accum(torch, R):
+    r = R.Renderer()
+    scene = S.cornell_box(1, 32, 32)
+    r.upload_scene(scene)
+    r.init_chains(2048, 3, R.make_params(L=4, drift="adjoint", k0=0.0, steps_per_splat=4))
+    r.step(10)
+    img = r.resolve().cpu().numpy().reshape(-1, 3)
+    acc = r.readback_accum()
+    c = r.counters()
+    assert c["tour_count"] > 0 and c["steps"] == 10
+    ref = (acc * (c["k0"] / c["tour_count"])).astype(np.float32)
+    assert np.allclose(img, ref, rtol=1e-6, atol=0)
+    r.close()
+
+
+def test_constant_target_kill_fraction_and_image(torch, R):
+    c = 2.0
+    m, dt = 64.0, 1e-5
+    k0 = c / (m * dt)
+    r = R.Renderer()
+    r.set_mixture(S.constant_target(d=4, value=c, width=4, height=4))
+    N, T = 65536, 64
+    r.init_chains(N, 9, R.make_params(L=1, drift="adjoint", rb=True, k0=k0, m=m, dt=dt, steps_per_splat=16))
+    r.step(T)
+    cnt = r.counters()
+    n = N * (T + 1)
+    p = 1.0 / (m + 1.0)
+    assert abs(cnt["tour_count"] / n - p) < 4 * math.sqrt(p * (1 - p) / n)
+    img = r.resolve().cpu().numpy().reshape(-1, 3)
+    assert np.allclose(img.sum(0), c, rtol=4 / math.sqrt(cnt["tour_count"]))
+    r.close()
+
+
+def test_checkpoint_resume_is_bit_identical(torch, R):
+    scene = S.cornell_box(1, 32, 32, glossy=True)
+    prm = R.make_params(L=5, drift="adjoint", k0=0.0, steps_per_splat=3)
+    a = R.Renderer()
+    a.upload_scene(scene)
+    a.init_chains(4096, 12, prm)
+    a.step(7)
+    blob = a.state_save()
+    a.step(9)
+    img_a = a.readback_accum()
+    st_a = a.readback_state(fields=("x", "killed"))
+    b = R.Renderer()
+    b.upload_scene(scene)
+    b.state_load(blob)
+    b.step(9)
+    img_b = b.readback_accum()
+    st_b = b.readback_state(fields=("x", "killed"))
+    assert np.array_equal(st_a["x"], st_b["x"]) and np.array_equal(st_a["killed"], st_b["killed"])
+    assert np.array_equal(img_a, img_b)
+    a.close()
+    b.close()
+
+
+def test_errors_are_reported_not_raised_on_device(torch, R):
+    from paper_2605_08916_gb300 import _lib
+    r = R.Renderer()
+    L = _lib.load()
+    assert L.dr_step(r.h, 1) == _lib.DR_ERR_STATE
+    bad = R.make_params(L=0)
+    import ctypes
+    assert L.dr_chains_init(r.h, 16, 1, 0, ctypes.byref(bad)) in (_lib.DR_ERR_INVALID_ARG, _lib.DR_ERR_STATE)
+    scene = S.cornell_box(1, 8, 8)
+    tris = scene.tris.copy()
+    tris[0, 0] = 10 ** 6
+    with pytest.raises(_lib.DRError) as e:
+        r.upload_scene(S.Scene(scene.verts, tris, scene.tri_mat, scene.materials, scene.camera, 8, 8))
+    assert e.value.code == _lib.DR_ERR_INVALID_ARG
+    r.upload_scene(scene)
+    r.init_chains(64, 1, R.make_params(L=3, drift="adjoint", k0=100.0))
+    r.step(2)
+    assert r.counters()["steps"] == 2
+    r.close()
