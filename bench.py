@@ -1,0 +1,329 @@
+#!/usr/bin/env python
+"""Benchmark of the Diffusion Restore hot path: Restore chain-steps/s (and
+rays/s) on one or more GB300s, one process per GPU.
+
+A timed "step" advances every chain of the workload by one Restore step
+(regenerate or LocalDynamics, path contribution with NEE, hold/kill clock,
+splat record, adjoint drift for survivors); the records are splatted into the
+FP64 image and resolved once at the end of the timed region (inside it).
+
+Default workload: the large procedural scene (fBm terrain + 200 tessellated
+spheres/boxes, ~1M triangles, mixed Lambertian / GGX / dielectric), 1280x720,
+L = 12 (d = 46), 2^20 chains, adjoint drift; inputs are larger than L2 and
+L2 is also flushed between timed steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+    python bench.py --impl reference ...   # the FP64 CPU oracle, timed on host cores
+
+Under torchrun each rank runs an independent replica (disjoint seeds, weak
+scaling); the per-rank FP64 images and tour counts are merged with one
+all-reduce at the end (the only exchange of the method).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2605_08916_gb300 import scenes as S  # noqa: E402
+
+METRIC = "Restore chain-steps/s"
+UNIT = "chain-steps/s"
+
+WORKLOADS = {
+    "procedural-1m-720p": dict(scene=lambda: S.procedural_scene(1, 1280, 720), L=12, chains=1 << 20,
+                               drift="adjoint", spp=8, cpu_chains=64),
+    "cornell-glossy-256": dict(scene=lambda: S.cornell_box(1, 256, 256, glossy=True), L=8, chains=65536,
+                               drift="adjoint", spp=16, cpu_chains=256),
+    "caustic-20k-512": dict(scene=lambda: S.caustic_scene(1, 512, 512), L=10, chains=262144, drift="adjoint",
+                            spp=16, cpu_chains=128),
+    "cornell-64-fd": dict(scene=lambda: S.cornell_box(1, 64, 64), L=4, chains=4096, drift="fd", spp=16,
+                          cpu_chains=128),
+}
+DEFAULT = "procedural-1m-720p"
+SEED = 0x5EED
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def cpu_baseline(wl, scene, steps=3, target_s=15.0):
+    """The FP64 oracle, as it stands, on this host's cores: a bounded sample
+    of the same workload (a subset of the chains, a few steps)."""
+    from oracle import oracle as O
+    tgt = O.OracleScene(scene)
+    cores = O.num_threads()
+    prm = O.make_params(L=wl["L"], drift="exact" if wl["drift"] == "adjoint" else wl["drift"], rb=True, k0=1.0)
+    # p_lambda estimate on a small uniform sample sets k0 as the GPU run does
+    est = O.restore_run(tgt, prm, seed=SEED, chain_ids=np.arange(256), n_steps=0, record=False)
+    prm.k0 = est["p_init_sum"] / 256 / (64.0 * 1e-5)
+    m = 16
+    t0 = time.perf_counter()
+    O.restore_run(tgt, prm, seed=SEED, chain_ids=np.arange(m), n_steps=steps, record=False, accum=False)
+    dt = time.perf_counter() - t0
+    m = int(max(16, min(wl["cpu_chains"] * 64, m * target_s / max(dt, 1e-3))))
+    t0 = time.perf_counter()
+    O.restore_run(tgt, prm, seed=SEED, chain_ids=np.arange(m), n_steps=steps, record=False, accum=False)
+    dt = time.perf_counter() - t0
+    units = m * (steps + 1)
+    return {"value": units / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{m} chains x {steps + 1} steps (init + {steps}) of the workload, FP64, OpenMP",
+            "seconds": dt}
+
+
+def run_reference(args, wl, rank, world):
+    if rank != 0:
+        return 0
+    scene = wl["scene"]()
+    from oracle import oracle as O
+    tgt = O.OracleScene(scene)
+    prm = O.make_params(L=wl["L"], drift="exact" if wl["drift"] == "adjoint" else wl["drift"], rb=True, k0=1.0)
+    est = O.restore_run(tgt, prm, seed=SEED, chain_ids=np.arange(256), n_steps=0, record=False)
+    prm.k0 = est["p_init_sum"] / 256 / (64.0 * 1e-5)
+    m = max(16, wl["cpu_chains"] // 2)
+    for _ in range(args.warmup):
+        O.restore_run(tgt, prm, seed=SEED, chain_ids=np.arange(16), n_steps=1, record=False, accum=False)
+    t0 = time.perf_counter()
+    O.restore_run(tgt, prm, seed=SEED, chain_ids=np.arange(m), n_steps=args.steps, record=False, accum=False)
+    dt = time.perf_counter() - t0
+    value = m * (args.steps + 1) / dt
+    sample = f"{m} chains x {args.steps + 1} steps of the workload, FP64 oracle"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / (args.steps + 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "chains": m, "max_path_len": wl["L"], "triangles": scene.n_tris,
+                       "image": [scene.width, scene.height], "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args, wl, rank, world, local):
+    import torch
+    from paper_2605_08916_gb300 import renderer as R
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    scene = wl["scene"]()
+    N = wl["chains"]
+    params = R.make_params(L=wl["L"], drift=wl["drift"], rb=True, k0=0.0, steps_per_splat=wl["spp"])
+    seed = SEED ^ (rank * 0x9E3779B97F4A7C15 & 0xFFFFFFFFFFFFFFFF)
+    stream = torch.cuda.current_stream(dev)
+    r = R.Renderer(local, stream)
+    r.upload_scene(scene)
+    r.init_chains(N, seed, params)
+    # traversal statistics pass (separate kernel instantiation, untimed)
+    r.set_stats(True)
+    r.step(2)
+    ts = r.traversal_stats()
+    r.set_stats(False)
+    chain_steps_stats = 2 * N
+    node_b, tri_b = 64, 48
+    d = 2 + 4 * (wl["L"] - 1)
+    state_b = 4 * d * 4 + 1 + 1 + 4 + 16   # x and score read+write, killed r+w, logp, record
+    bytes_per_cs = (ts["node_visits"] * node_b + ts["tri_tests"] * tri_b) / chain_steps_stats + state_b
+    for _ in range(args.warmup):
+        r.step(1)
+    torch.cuda.synchronize()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
+    c0 = r.counters()
+    l0 = r.launch_count()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps + 1)]
+    step_launches = []
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            la = r.launch_count()
+            ev[k][0].record(stream)
+            r.step(1)
+            ev[k][1].record(stream)
+            step_launches.append(r.launch_count() - la)
+        flush.zero_()
+        img = torch.empty((scene.height, scene.width, 3), dtype=torch.float32, device=dev)
+        ev[-1][0].record(stream)
+        r.splat()
+        r.resolve(img)
+        ev[-1][1].record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    times = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(times)
+    launches = r.launch_count() - l0
+    c1 = r.counters()
+    rays = c1["rays"] - c0["rays"]
+    t_max = total_ms
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(t.item())
+        # the method's one exchange: merge the FP64 images and tour counts
+        acc = torch.from_numpy(r.readback_accum()).to(dev)
+        tc = torch.tensor([c1["tour_count"]], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(acc)
+        torch.distributed.all_reduce(tc)
+    value = N * args.steps * world / (t_max / 1e3)
+    rays_s = rays * world / (t_max / 1e3)
+    pure = [t for t, nl in zip(times[:-1], step_launches) if nl == 1]
+    k_ms = statistics.mean(pure) if pure else statistics.mean(times[:-1])
+    peak, peak_kind = measured_peaks()
+    achieved = bytes_per_cs * N / (k_ms / 1e3) / 1e9
+    clocks = clk.summary()
+
+    line = None
+    if rank == 0:
+        e2e = run_e2e(R, scene, wl, N, args.steps, local, stream)
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": args.workload, "scene": scene.name, "triangles": scene.n_tris,
+                           "image": [scene.width, scene.height], "chains_per_gpu": N, "max_path_len": wl["L"],
+                           "pss_dim": d, "drift": wl["drift"], "rb_weight": True, "steps_per_splat": wl["spp"],
+                           "l2": "inputs > L2 (BVH + chain state) and a 512 MB L2 flush between timed steps",
+                           "parallelism": f"replicas{world}"},
+                "rays_per_s": rays_s, "rays_per_chain_step": rays / max(1, N * args.steps),
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                             "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                             "kernel": "step_kernel (fused Restore step)", "kernel_ms": k_ms,
+                             "algorithmic_bytes_per_chain_step": bytes_per_cs,
+                             "node_visits_per_chain_step": ts["node_visits"] / chain_steps_stats,
+                             "tri_tests_per_chain_step": ts["tri_tests"] / chain_steps_stats},
+                "clocks": clocks, "gpu_launches": launches, "e2e": e2e}
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(wl, scene)
+        print(json.dumps(line), flush=True)
+    r.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def run_e2e(R, scene, wl, N, steps, local, stream):
+    """Same metric through the public API with host buffers: scene arrays
+    copied host -> device (upload + BVH build), chain init with the p_lambda
+    estimate, the steps, resolve, and the image copied device -> host."""
+    import torch
+    h2d = sum(a.nbytes for a in (scene.verts, scene.tris, scene.tri_mat, scene.materials, scene.camera))
+    if scene.normals is not None:
+        h2d += scene.normals.nbytes
+    out = torch.empty((scene.height, scene.width, 3), dtype=torch.float32, device=torch.device("cuda", local))
+    host = torch.empty(out.shape, dtype=torch.float32, pin_memory=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r = R.Renderer(local, stream)
+    r.upload_scene(scene)
+    r.init_chains(N, SEED + 1, R.make_params(L=wl["L"], drift=wl["drift"], rb=True, k0=0.0,
+                                            steps_per_splat=wl["spp"]))
+    r.step(steps)
+    r.resolve(out)
+    host.copy_(out, non_blocking=True)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    r.close()
+    d2h = out.numel() * 4
+    return {"value": N * steps / dt, "unit": UNIT, "h2d_bytes_per_step": h2d / steps, "d2h_bytes_per_step": d2h / steps,
+            "seconds": dt, "includes": "scene upload + BVH build + init (p_lambda estimate) + steps + resolve + image D2H"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=24)
+    ap.add_argument("--warmup", type=int, default=4)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    rank, world, local = dist_env()
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, wl, rank, world)
+    return run_ours(args, wl, rank, world, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -218,6 +218,16 @@ int dr_get_traversal_stats(dr_ctx* ctx, uint64_t* node_visits, uint64_t* tri_tes
  * Synchronises. */
 int dr_bvh_info(dr_ctx* ctx, int32_t* n_nodes, int32_t* n_tris, int32_t* max_depth);
 
+/* Number of kernels this context has launched since creation (a host-side
+ * count kept at every launch site; HOST output). */
+int dr_get_launch_count(dr_ctx* ctx, uint64_t* launches);
+
+/* Shape of the current chain state (HOST outputs, any may be NULL): number
+ * of chains N, PSS dimension d and max path length L; the sizes callers of
+ * dr_readback_state must allocate for (e.g. after dr_state_load).
+ * Errors: STATE when no chains exist. */
+int dr_get_chain_shape(dr_ctx* ctx, uint64_t* n_chains, int32_t* dim, int32_t* max_path_len);
+
 #ifdef __cplusplus
 }
 #endif

@@ -64,6 +64,7 @@ struct dr_ctx {
   size_t p_partial_cap = 0;
   double* p_sum = nullptr;
   uint32_t* err = nullptr;
+  unsigned long long launches = 0;  // kernels launched by this context
   double k0 = 0.0;
   double p_lambda = 0.0;
   bool stats = false;
@@ -180,6 +181,7 @@ int flush(dr_ctx* c) {
   SplatRec* sorted =
       sort_splat_records(c->rec, c->rec_alt, n, key_bits((long long)c->W * c->H), c->sort_scratch, c->stream);
   launch_segment_reduce(sorted, n, c->accum, (uint32_t)((size_t)c->W * c->H), c->err, c->stream);
+  c->launches += 5 * ((key_bits((long long)c->W * c->H) + 7) / 8) + 1;
   c->rec_count = 0;
   return check_launch("splat");
 }
@@ -228,6 +230,7 @@ int run_fd(dr_ctx* c) {
   f.rays = c->counters + 1;
   f.err = c->err;
   launch_fd_score(f, c->stream);
+  c->launches += 1;
   return check_launch("fd_score");
 }
 
@@ -240,6 +243,7 @@ int one_step(dr_ctx* c, bool init) {
   a.rec = c->rec + (size_t)c->rec_count * c->N;
   a.p_partial = init ? c->p_partial : nullptr;
   launch_step(a, c->stats, c->stream);
+  c->launches += 1;
   DR_TRY(check_launch("restore_step"));
   c->rec_count++;
   if (c->prm.drift_mode == DR_DRIFT_FD) DR_TRY(run_fd(c));
@@ -591,6 +595,7 @@ int dr_resolve(dr_ctx* c, float* out_rgb) {
   DR_CUDA(cudaSetDevice(c->device));
   DR_TRY(flush(c));
   launch_resolve(c->accum, c->accum_n, c->counters, c->k0, out_rgb, c->stream);
+  c->launches += 1;
   DR_TRY(check_launch("resolve"));
   if (!capturing(c->stream)) {
     unsigned long long tc = 0;
@@ -842,6 +847,21 @@ int dr_get_traversal_stats(dr_ctx* c, uint64_t* node_visits, uint64_t* tri_tests
   if (rays) *rays = h[1];
   if (node_visits) *node_visits = h[2];
   if (tri_tests) *tri_tests = h[3];
+  return DR_OK;
+}
+
+int dr_get_chain_shape(dr_ctx* c, uint64_t* n_chains, int32_t* dim, int32_t* max_path_len) {
+  if (!c) return fail(DR_ERR_INVALID_ARG, "dr_get_chain_shape: NULL ctx");
+  if (!c->inited) return fail(DR_ERR_STATE, "dr_get_chain_shape: no chains");
+  if (n_chains) *n_chains = c->N;
+  if (dim) *dim = c->d;
+  if (max_path_len) *max_path_len = c->prm.max_path_len;
+  return DR_OK;
+}
+
+int dr_get_launch_count(dr_ctx* c, uint64_t* launches) {
+  if (!c || !launches) return fail(DR_ERR_INVALID_ARG, "dr_get_launch_count: NULL argument");
+  *launches = c->launches;
   return DR_OK;
 }
 

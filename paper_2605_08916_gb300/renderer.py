@@ -96,9 +96,7 @@ class Renderer:
     def init_chains(self, n_chains, seed, params, frame=0):
         self.params = params
         call("dr_chains_init", self.h, int(n_chains), int(seed), int(frame), C.byref(params))
-        self.N = int(n_chains)
-        self.L = int(params.max_path_len)
-        self.d = 2 + 4 * (self.L - 1) if self.kind == 0 else self.mix_d
+        self._sync_shape()
 
     def step(self, n=1):
         call("dr_step", self.h, int(n))
@@ -156,6 +154,11 @@ class Renderer:
         call("dr_bvh_info", self.h, C.byref(a), C.byref(b), C.byref(c))
         return {"n_nodes": a.value, "n_tris": b.value, "max_depth": c.value}
 
+    def launch_count(self):
+        n = C.c_uint64()
+        call("dr_get_launch_count", self.h, C.byref(n))
+        return n.value
+
     def state_save(self):
         n = C.c_size_t(0)
         call("dr_state_save", self.h, None, C.byref(n))
@@ -166,6 +169,12 @@ class Renderer:
     def state_load(self, buf):
         buf = np.ascontiguousarray(buf, np.uint8)
         call("dr_state_load", self.h, _ptr(buf), buf.size)
+        self._sync_shape()
+
+    def _sync_shape(self):
+        n, d, L = C.c_uint64(), C.c_int32(), C.c_int32()
+        call("dr_get_chain_shape", self.h, C.byref(n), C.byref(d), C.byref(L))
+        self.N, self.d, self.L = n.value, d.value, L.value
 
     # ---------------------------------------------------------------- queries
     def eval_logp(self, x, L=None, grad=False, want_f=False):

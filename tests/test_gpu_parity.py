@@ -133,6 +133,7 @@ def _chain_parity(torch, R, oracle, target_obj, params_gpu, params_orc, N, M, T,
     alive = np.ones(M, bool)
     first_div = np.full(M, -1)
     n_cmp = 0
+    causes = {}
     for s in range(T + 1):
         if s > 0:
             r.step(1)
@@ -140,15 +141,22 @@ def _chain_parity(torch, R, oracle, target_obj, params_gpu, params_orc, N, M, T,
         xg, lg, kg, pg, vg = st["x"][:M], st["logp"][:M], st["killed"][:M], st["pix"][:M], st["val"][:M]
         xo, lo_, ko, po, vo = ro["x"][s], ro["logp"][s], ro["killed"][s], ro["pix"][s], ro["val"][s]
         xerr = torus_dist(xg, xo).max(1)
-        ok = (kg == ko) & (pg == po) & (xerr <= x_tol)
-        ok &= np.abs(lg - lo_) <= 1e-4 * np.maximum(1.0, np.abs(lo_))
-        vn = np.linalg.norm(vo, axis=1)
-        ok &= np.linalg.norm(vg - vo, axis=1) <= 1e-4 * vn + 1e-12
+        checks = {"killed": kg == ko, "pix": pg == po, "x": xerr <= x_tol,
+                  "logp": np.abs(lg - lo_) <= 1e-4 * np.maximum(1.0, np.abs(lo_)),
+                  "val": np.linalg.norm(vg - vo, axis=1) <= 1e-4 * np.linalg.norm(vo, axis=1) + 1e-12}
+        ok = np.logical_and.reduce(list(checks.values()))
         newly = alive & ~ok
+        for j in np.nonzero(newly)[0]:
+            failed = ",".join(k for k, v in checks.items() if not v[j])
+            causes[failed] = causes.get(failed, 0) + 1
+            if len(causes) <= 6:
+                print(f"  chain {j} step {s}: {failed}; xerr {xerr[j]:.2e} logp {lg[j]:.6g}/{lo_[j]:.6g} "
+                      f"killed {kg[j]}/{ko[j]} pix {pg[j]}/{po[j]}")
         first_div[newly] = s
         alive &= ok
         n_cmp += alive.sum()
     frac_div = 1.0 - alive.mean()
+    print("  divergence causes:", causes)
     r.close()
     return frac_div, first_div, n_cmp
 
