@@ -114,6 +114,14 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+_T0 = time.perf_counter()
+
+
+def log(msg):
+    """Progress on stderr (the JSON line is the only stdout output)."""
+    print(f"[bench {time.perf_counter() - _T0:8.1f}s] {msg}", file=sys.stderr, flush=True)
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -184,18 +192,23 @@ def run_ours(args, wl, rank, world, local):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     scene = wl["scene"]()
+    log(f"scene {scene.name}: {scene.n_tris} triangles")
     N = wl["chains"]
     params = R.make_params(L=wl["L"], drift=wl["drift"], rb=True, k0=0.0, steps_per_splat=wl["spp"])
-    seed = SEED ^ (rank * 0x9E3779B97F4A7C15 & 0xFFFFFFFFFFFFFFFF)
+    from paper_2605_08916_gb300.replicas import replica_seed
+    seed = replica_seed(SEED, rank)
     stream = torch.cuda.current_stream(dev)
     r = R.Renderer(local, stream)
     r.upload_scene(scene)
     r.init_chains(N, seed, params)
+    torch.cuda.synchronize()
+    log(f"uploaded + init {N} chains; bvh {r.bvh_info()}")
     # traversal statistics pass (separate kernel instantiation, untimed)
     r.set_stats(True)
     r.step(2)
     ts = r.traversal_stats()
     r.set_stats(False)
+    log(f"stats pass: {ts}")
     chain_steps_stats = 2 * N
     node_b, tri_b = 64, 48
     d = 2 + 4 * (wl["L"] - 1)
@@ -240,10 +253,8 @@ def run_ours(args, wl, rank, world, local):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         t_max = float(t.item())
         # the method's one exchange: merge the FP64 images and tour counts
-        acc = torch.from_numpy(r.readback_accum()).to(dev)
-        tc = torch.tensor([c1["tour_count"]], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(acc)
-        torch.distributed.all_reduce(tc)
+        from paper_2605_08916_gb300.replicas import merge_and_resolve
+        merge_and_resolve(torch.from_numpy(r.readback_accum()).to(dev), c1["tour_count"], c1["k0"])
     value = N * args.steps * world / (t_max / 1e3)
     rays_s = rays * world / (t_max / 1e3)
     pure = [t for t, nl in zip(times[:-1], step_launches) if nl == 1]
@@ -254,7 +265,9 @@ def run_ours(args, wl, rank, world, local):
 
     line = None
     if rank == 0:
+        log(f"timed {args.steps} steps: {total_ms:.1f} ms")
         e2e = run_e2e(R, scene, wl, N, args.steps, local, stream)
+        log("e2e done")
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -273,6 +286,7 @@ def run_ours(args, wl, rank, world, local):
                 "clocks": clocks, "gpu_launches": launches, "e2e": e2e}
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(wl, scene)
+            log("cpu baseline done")
         print(json.dumps(line), flush=True)
     r.close()
     if world > 1:

@@ -222,6 +222,23 @@ int dr_bvh_info(dr_ctx* ctx, int32_t* n_nodes, int32_t* n_tris, int32_t* max_dep
  * count kept at every launch site; HOST output). */
 int dr_get_launch_count(dr_ctx* ctx, uint64_t* launches);
 
+/* Ordinary Monte Carlo (path tracing, the paper's PT method, Sec. 6) over
+ * the same f: per pixel, spp samples with the film pair stratified to the
+ * pixel and the other coordinates uniform from Philox (key = seed, counter
+ * = (sample, pixel, block, 3)).  out_mean: DEVICE FP64 [W * H * 3], the
+ * per-pixel mean of f / (W H), i.e. the pixel radiance estimate in the same
+ * units as dr_resolve.  Allocates temporary device memory; synchronises.
+ * Errors: STATE (no scene), INVALID_ARG, OOM, CUDA, DEVICE_CHECK. */
+int dr_pt_render(dr_ctx* ctx, int32_t max_path_len, uint32_t spp, uint64_t seed, double* out_mean);
+
+/* BVH construction used by later dr_scene_upload calls:
+ * DR_BVH_PLOC (default; parallel locally-ordered clustering of the
+ * Morton-ordered triangles with search radius `radius`, 1..256, default 16)
+ * or DR_BVH_LBVH (linear BVH, Karras 2012; radius ignored).  Both produce
+ * the same node layout.  Errors: INVALID_ARG. */
+enum { DR_BVH_LBVH = 0, DR_BVH_PLOC = 1 };
+int dr_set_bvh_builder(dr_ctx* ctx, int32_t builder, int32_t radius);
+
 /* Shape of the current chain state (HOST outputs, any may be NULL): number
  * of chains N, PSS dimension d and max path length L; the sizes callers of
  * dr_readback_state must allocate for (e.g. after dr_state_load).

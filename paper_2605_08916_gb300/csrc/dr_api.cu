@@ -68,6 +68,8 @@ struct dr_ctx {
   double k0 = 0.0;
   double p_lambda = 0.0;
   bool stats = false;
+  int builder = DR_BVH_PLOC;
+  int ploc_radius = 16;
 };
 
 namespace {
@@ -405,8 +407,10 @@ int dr_scene_upload(dr_ctx* c, const float* verts, int32_t nv, const int32_t* tr
   if (r == DR_OK) r = dalloc(&c->mats, 12 * (size_t)nm);
   if (r == DR_OK) r = dalloc(&c->lights, std::max<size_t>(4, lrec.size()));
   if (r == DR_OK) r = normals ? dalloc(&c->nrm, 9 * (size_t)nt) : (dfree(&c->nrm), DR_OK);
+  void* ploc_scratch = nullptr;
   if (r == DR_OK) {
     cudaError_t e = cudaMalloc(&scratch, bvh_scratch_bytes(nt));
+    if (e == cudaSuccess && c->builder == DR_BVH_PLOC) e = cudaMalloc(&ploc_scratch, ploc_scratch_bytes(nt));
     if (e != cudaSuccess) { cudaGetLastError(); r = fail(DR_ERR_OOM, "dr_scene_upload: BVH scratch"); }
   }
   if (r == DR_OK) {
@@ -422,13 +426,17 @@ int dr_scene_upload(dr_ctx* c, const float* verts, int32_t nv, const int32_t* tr
       launch_gather_normals(dvn, dtris, nt, c->nrm, s);
     }
     launch_surface_records(dverts, dtris, dmat, dsel, dvn, nt, c->surf, s);
-    c->n_nodes = build_lbvh(dverts, dtris, nt, c->nodes, c->tris, scratch, s);
+    c->n_nodes = c->builder == DR_BVH_PLOC
+                     ? build_ploc(dverts, dtris, nt, c->nodes, c->tris, scratch, ploc_scratch, c->ploc_radius, s)
+                     : build_lbvh(dverts, dtris, nt, c->nodes, c->tris, scratch, s);
     cudaError_t e = cudaStreamSynchronize(s);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) r = fail(DR_ERR_CUDA, std::string("dr_scene_upload: ") + cudaGetErrorString(e));
+    else if (c->n_nodes < 0) r = fail(DR_ERR_CUDA, "dr_scene_upload: BVH construction failed");
   }
   dfree(&dverts); dfree(&dtris); dfree(&dmat); dfree(&dsel); dfree(&dvn);
   if (scratch) cudaFree(scratch);
+  if (ploc_scratch) cudaFree(ploc_scratch);
   if (r != DR_OK) return r;
   c->target = 0;
   c->W = width;
@@ -847,6 +855,37 @@ int dr_get_traversal_stats(dr_ctx* c, uint64_t* node_visits, uint64_t* tri_tests
   if (rays) *rays = h[1];
   if (node_visits) *node_visits = h[2];
   if (tri_tests) *tri_tests = h[3];
+  return DR_OK;
+}
+
+int dr_pt_render(dr_ctx* c, int32_t L, uint32_t spp, uint64_t seed, double* out_mean) {
+  if (!c || !out_mean) return fail(DR_ERR_INVALID_ARG, "dr_pt_render: NULL argument");
+  if (c->target != 0) return fail(DR_ERR_STATE, "dr_pt_render: no scene");
+  if (L < 1 || L > DR_MAX_PATH_LEN || spp < 1) return fail(DR_ERR_INVALID_ARG, "dr_pt_render: bad L or spp");
+  DR_CUDA(cudaSetDevice(c->device));
+  const long long n_pix = (long long)c->W * c->H;
+  // enough threads to fill the GPU, at most spp chunks
+  long long want = (1ll << 20) / std::max(1ll, n_pix);
+  const int n_chunks = (int)std::max(1ll, std::min<long long>(want, (long long)spp));
+  double* part = nullptr;
+  DR_TRY(dalloc(&part, (size_t)n_chunks * n_pix * 3));
+  Rng rng{(uint32_t)seed, (uint32_t)(seed >> 32), 0u};
+  launch_pt(dev_scene(c), L, spp, n_chunks, rng, part, out_mean, c->counters + 1, c->err, c->stream);
+  c->launches += 2;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  dfree(&part);
+  if (e != cudaSuccess) return fail(DR_ERR_CUDA, std::string("dr_pt_render: ") + cudaGetErrorString(e));
+  return check_device_error(c);
+}
+
+int dr_set_bvh_builder(dr_ctx* c, int32_t builder, int32_t radius) {
+  if (!c) return fail(DR_ERR_INVALID_ARG, "dr_set_bvh_builder: NULL ctx");
+  if (builder != DR_BVH_LBVH && builder != DR_BVH_PLOC) return fail(DR_ERR_INVALID_ARG, "dr_set_bvh_builder: builder");
+  if (builder == DR_BVH_PLOC && (radius < 1 || radius > 256))
+    return fail(DR_ERR_INVALID_ARG, "dr_set_bvh_builder: radius must be 1..256");
+  c->builder = builder;
+  c->ploc_radius = radius;
   return DR_OK;
 }
 

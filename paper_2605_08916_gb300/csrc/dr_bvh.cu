@@ -254,7 +254,166 @@ __global__ void gather_normals_kernel(const float* __restrict__ vn, const int* _
   }
 }
 
+// ---------------------------------------------------------------- PLOC
+// Parallel locally-ordered clustering (Meister and Bittner 2018): clusters
+// kept in Morton order; each finds the neighbour within +-r whose merged box
+// has the smallest surface area; mutual nearest neighbours merge; the
+// cluster list is compacted; repeat until one cluster remains.  Inner nodes
+// are numbered from the top (the last merge is node 0, the root), so the
+// hierarchy has the same layout as the linear build.
+
+DR_D float box_area(const float* a, const float* b) {
+  const float dx = fmaxf(a[3], b[3]) - fminf(a[0], b[0]);
+  const float dy = fmaxf(a[4], b[4]) - fminf(a[1], b[1]);
+  const float dz = fmaxf(a[5], b[5]) - fminf(a[2], b[2]);
+  return dx * dy + dy * dz + dz * dx;
+}
+
+__global__ void ploc_init_kernel(int n, const float* __restrict__ box, int* __restrict__ cl_node,
+                                 float* __restrict__ cl_box) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  cl_node[i] = n - 1 + i;
+  for (int q = 0; q < 6; ++q) cl_box[6 * i + q] = box[(size_t)(n - 1 + i) * 6 + q];
+}
+
+__global__ void ploc_nn_kernel(int m, int r, const float* __restrict__ cl_box, int* __restrict__ nn) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  float bi[6];
+  for (int q = 0; q < 6; ++q) bi[q] = cl_box[6 * i + q];
+  float best = __int_as_float(0x7f800000);
+  int bj = i == 0 ? 1 : i - 1;
+  const int lo = max(0, i - r), hi = min(m - 1, i + r);
+  for (int j = lo; j <= hi; ++j) {
+    if (j == i) continue;
+    float bb[6];
+    for (int q = 0; q < 6; ++q) bb[q] = cl_box[6 * j + q];
+    const float a = box_area(bi, bb);
+    if (a < best) {  // first minimum wins: ties go to the smaller index
+      best = a;
+      bj = j;
+    }
+  }
+  nn[i] = bj;
+}
+
+__global__ void ploc_flag_kernel(int m, const int* __restrict__ nn, uint32_t* __restrict__ flag) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  const int j = nn[i];
+  flag[i] = (j >= 0 && j < m && nn[j] == i && i < j) ? 1u : 0u;
+}
+
+// Merges the flagged pairs: the k-th merge (k = exclusive scan of the flags)
+// creates inner node base - k.  Writes the surviving cluster list's keep
+// flags (1 = keep) into keep.
+__global__ void ploc_merge_kernel(int m, int base, const int* __restrict__ nn, const uint32_t* __restrict__ flag,
+                                  const uint32_t* __restrict__ pos, int* __restrict__ cl_node,
+                                  float* __restrict__ cl_box, int* __restrict__ child, float* __restrict__ box,
+                                  uint32_t* __restrict__ keep) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  const int j = nn[i];
+  const bool merging_left = flag[i] != 0u;
+  const bool merged_away = j >= 0 && j < m && flag[j] != 0u && nn[j] == i;  // i is the right partner of j
+  keep[i] = merged_away ? 0u : 1u;
+  if (!merging_left) return;
+  const int idx = base - (int)pos[i];
+  const int a = cl_node[i], b = cl_node[j];
+  child[2 * idx] = a;
+  child[2 * idx + 1] = b;
+  float u[6];
+  for (int q = 0; q < 3; ++q) {
+    u[q] = fminf(cl_box[6 * i + q], cl_box[6 * j + q]);
+    u[3 + q] = fmaxf(cl_box[6 * i + 3 + q], cl_box[6 * j + 3 + q]);
+  }
+  for (int q = 0; q < 6; ++q) {
+    box[(size_t)idx * 6 + q] = u[q];
+    cl_box[6 * i + q] = u[q];
+  }
+  cl_node[i] = idx;
+}
+
+__global__ void ploc_compact_kernel(int m, const uint32_t* __restrict__ keep, const uint32_t* __restrict__ pos,
+                                    const int* __restrict__ cl_node, const float* __restrict__ cl_box,
+                                    int* __restrict__ out_node, float* __restrict__ out_box) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m || !keep[i]) return;
+  const int o = (int)pos[i];
+  out_node[o] = cl_node[i];
+  for (int q = 0; q < 6; ++q) out_box[6 * o + q] = cl_box[6 * i + q];
+}
+
+// fallback when no mutual pair exists (degenerate ties): merge clusters 0, 1
+__global__ void ploc_force_pair_kernel(int* nn, uint32_t* flag) {
+  nn[0] = 1;
+  nn[1] = 0;
+  flag[0] = 1u;
+  flag[1] = 0u;
+}
+
 }  // namespace
+
+size_t ploc_scratch_bytes(int nt) {
+  const size_t n = (size_t)(nt < 2 ? 2 : nt);
+  return a256(n * 4) * 2 + a256(n * 24) * 2 + a256(n * 4) * 4 + scan_scratch_bytes(n) + 256;
+}
+
+int build_ploc(const float* d_verts, const int* d_tris, int n, float4* d_nodes, float4* d_tris_out, void* scratch,
+               void* ploc_scratch, int radius, cudaStream_t st) {
+  if (n <= 1) return build_lbvh(d_verts, d_tris, n, d_nodes, d_tris_out, scratch, st);
+  BvhScratch s = carve(scratch, n);
+  const int nblk = (n + kB - 1) / kB;
+  centroid_bounds_kernel<<<nblk, kB, 0, st>>>(d_verts, d_tris, n, s.cbox);
+  bounds_final_kernel<<<1, 32, 0, st>>>(s.cbox, nblk, s.gbox);
+  morton_kernel<<<nblk, kB, 0, st>>>(d_verts, d_tris, n, s.gbox, s.keys0);
+  uint2* sorted = sort_pairs(s.keys0, s.keys1, (size_t)n, 32, s.sort_scratch, st);
+  leaf_boxes_kernel<<<nblk, kB, 0, st>>>(d_verts, d_tris, sorted, n, s.box, d_tris_out, s.flag);
+  // carve the clustering buffers
+  char* p = static_cast<char*>(ploc_scratch);
+  const size_t nn_ = (size_t)n;
+  int* node_a = reinterpret_cast<int*>(p); p += a256(nn_ * 4);
+  int* node_b = reinterpret_cast<int*>(p); p += a256(nn_ * 4);
+  float* box_a = reinterpret_cast<float*>(p); p += a256(nn_ * 24);
+  float* box_b = reinterpret_cast<float*>(p); p += a256(nn_ * 24);
+  int* nn = reinterpret_cast<int*>(p); p += a256(nn_ * 4);
+  uint32_t* flag = reinterpret_cast<uint32_t*>(p); p += a256(nn_ * 4);
+  uint32_t* pos = reinterpret_cast<uint32_t*>(p); p += a256(nn_ * 4);
+  uint32_t* keep = reinterpret_cast<uint32_t*>(p); p += a256(nn_ * 4);
+  void* scan_tmp = p;
+  ploc_init_kernel<<<nblk, kB, 0, st>>>(n, s.box, node_a, box_a);
+  int m = n;
+  int created = 0;
+  uint32_t host[2];
+  // every pass merges at least one pair, so at most n - 1 passes
+  for (int pass = 0; m > 1 && pass < n; ++pass) {
+    const int mb = (m + kB - 1) / kB;
+    ploc_nn_kernel<<<mb, kB, 0, st>>>(m, radius, box_a, nn);
+    ploc_flag_kernel<<<mb, kB, 0, st>>>(m, nn, flag);
+    launch_exclusive_scan(flag, pos, (size_t)m, scan_tmp, st);
+    if (cudaMemcpyAsync(host, pos + (m - 1), 4, cudaMemcpyDeviceToHost, st) != cudaSuccess) return -1;
+    if (cudaMemcpyAsync(host + 1, flag + (m - 1), 4, cudaMemcpyDeviceToHost, st) != cudaSuccess) return -1;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return -1;
+    int merges = (int)(host[0] + host[1]);
+    if (merges == 0) {
+      ploc_force_pair_kernel<<<1, 1, 0, st>>>(nn, flag);
+      launch_exclusive_scan(flag, pos, (size_t)m, scan_tmp, st);
+      merges = 1;
+    }
+    const int base = (n - 2) - created;
+    ploc_merge_kernel<<<mb, kB, 0, st>>>(m, base, nn, flag, pos, node_a, box_a, s.child, s.box, keep);
+    launch_exclusive_scan(keep, pos, (size_t)m, scan_tmp, st);
+    ploc_compact_kernel<<<mb, kB, 0, st>>>(m, keep, pos, node_a, box_a, node_b, box_b);
+    std::swap(node_a, node_b);
+    std::swap(box_a, box_b);
+    created += merges;
+    m -= merges;
+  }
+  if (m != 1 || created != n - 1) return -1;
+  emit_nodes_kernel<<<nblk, kB, 0, st>>>(n, s.child, s.box, d_nodes);
+  return n - 1;
+}
 
 size_t bvh_scratch_bytes(int nt) {
   const size_t n = (size_t)(nt < 2 ? 2 : nt);

@@ -16,6 +16,9 @@ size_t sort_scratch_bytes(size_t n);
 // Sorts in[0..n) into out (in is used as the ping-pong buffer and is
 // clobbered).  Returns a pointer to whichever buffer holds the result.
 SplatRec* sort_splat_records(SplatRec* in, SplatRec* out, size_t n, int bits, void* scratch, cudaStream_t s);
+// Device-wide exclusive scan of uint32 (out may alias in only if n <= one chunk).
+size_t scan_scratch_bytes(size_t n);
+void launch_exclusive_scan(const uint32_t* in, uint32_t* out, size_t n, void* scratch, cudaStream_t s);
 uint2* sort_pairs(uint2* in, uint2* out, size_t n, int bits, void* scratch, cudaStream_t s);
 
 // accum[pix * 3 + c] += sum of the sorted records' values (FP64, in sorted
@@ -37,6 +40,12 @@ struct BvhBuildOut {
 size_t bvh_scratch_bytes(int nt);
 int build_lbvh(const float* d_verts, const int* d_tris, int nt, float4* d_nodes, float4* d_tris_out, void* scratch,
                cudaStream_t s);
+// Same output layout, clustered by PLOC with search radius `radius`
+// (second scratch of ploc_scratch_bytes(nt)).  Synchronises once per pass.
+// Returns the node count, or -1 on failure.
+size_t ploc_scratch_bytes(int nt);
+int build_ploc(const float* d_verts, const int* d_tris, int nt, float4* d_nodes, float4* d_tris_out, void* scratch,
+               void* ploc_scratch, int radius, cudaStream_t s);
 // Per-triangle surface records (5 float4) from the device arrays; sel is
 // the light-selection probability per triangle (device, may be null).
 void launch_surface_records(const float* d_verts, const int* d_tris, const int* d_tri_mat, const float* d_sel,
@@ -111,5 +120,9 @@ void launch_trace(const DevScene& S, const float* rays, long long n, int exclude
                   cudaStream_t s);
 void launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, long long n, cudaStream_t s);
 void launch_sum_doubles(const double* in, int n, double* out, cudaStream_t s);
+// Stratified path tracing of the same f: part [n_chunks][W*H][3] FP64
+// scratch, mean [W*H][3] = per-pixel mean of f / (W H) over spp samples.
+void launch_pt(const DevScene& S, int L, uint32_t spp, int n_chunks, Rng rng, double* part, double* mean,
+               unsigned long long* rays, uint32_t* err, cudaStream_t s);
 
 }  // namespace dr

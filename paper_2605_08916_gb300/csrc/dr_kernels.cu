@@ -292,6 +292,65 @@ __global__ void philox_kernel(const uint32_t* __restrict__ ctr, const uint32_t* 
   out[4 * i + 3] = r.d;
 }
 
+// Ordinary Monte Carlo over the same f (the paper's PT method, Sec. 6):
+// thread t handles pixel t % n_pix and samples [c * spc, (c + 1) * spc) of
+// chunk c = t / n_pix; film pair stratified to the pixel, other coordinates
+// uniform from Philox (counter = (sample, pixel, block, frame<<4 | 3)).
+// part[c][pix][3] receives the chunk's FP64 sum of f / (W H).
+__global__ void __launch_bounds__(kStepThreads) pt_kernel(DevScene S, int L, int d, uint32_t spp, uint32_t spc,
+                                                          int n_chunks, Rng rng, double* __restrict__ part,
+                                                          unsigned long long* rays_out, uint32_t* errp) {
+  extern __shared__ int smem[];
+  TraceStack<kStack> st{smem + threadIdx.x, (int)blockDim.x};
+  const long long n_pix = (long long)S.W * S.H;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t err = 0, rays = 0;
+  if (t < n_pix * n_chunks) {
+    const int pix = (int)(t % n_pix), c = (int)(t / n_pix);
+    const int row = pix / S.W, col = pix % S.W;
+    const uint32_t s0 = (uint32_t)c * spc, s1 = min(spp, s0 + spc);
+    const double inv_wh = 1.0 / (double)n_pix;
+    double acc[3] = {0.0, 0.0, 0.0};
+    float xs[kMaxDim];
+    for (uint32_t s = s0; s < s1; ++s) {
+      for (int i = 0; i < d; i += 4) {
+        const U4 r = rng.draw(s, (uint32_t)pix, (uint32_t)(i >> 2), kPT);
+        const uint32_t w[4] = {r.a, r.b, r.c, r.d};
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (i + k < d) xs[i + k] = u01(w[k]);
+      }
+      xs[0] = ((float)col + xs[0]) / (float)S.W;
+      xs[1] = ((float)row + xs[1]) / (float)S.H;
+      TraceStats stats{0u, 0u};
+      Tape<kMaxPathLen> tape;
+      const PathResult pr =
+          path_forward<kStack, false, false>(S, [&](int i) { return xs[i]; }, L, &tape, st, &err, &stats);
+      rays += pr.rays;
+      acc[0] += (double)pr.f.x * inv_wh;
+      acc[1] += (double)pr.f.y * inv_wh;
+      acc[2] += (double)pr.f.z * inv_wh;
+    }
+    double* o = part + ((size_t)c * n_pix + pix) * 3;
+    o[0] = acc[0];
+    o[1] = acc[1];
+    o[2] = acc[2];
+  }
+  const unsigned long long wr = warp_sum_u64(rays);
+  if ((threadIdx.x & 31) == 0 && wr && rays_out) atomicAdd(rays_out, wr);
+  if (err) atomicOr(errp, err);
+}
+
+// mean[pix][c] = sum over chunks of part[chunk][pix][c] / spp (fixed order)
+__global__ void pt_reduce_kernel(const double* __restrict__ part, long long n, int n_chunks, double inv_spp,
+                                 double* __restrict__ mean) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double s = 0.0;
+  for (int c = 0; c < n_chunks; ++c) s += part[(size_t)c * n + i];
+  mean[i] = s * inv_spp;
+}
+
 __global__ void sum_doubles_kernel(const double* __restrict__ in, int n, double* __restrict__ out) {
   // one thread, fixed order: deterministic
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
@@ -341,6 +400,17 @@ void launch_trace(const DevScene& S, const float* rays, long long n, int exclude
 void launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, long long n, cudaStream_t s) {
   if (n <= 0) return;
   philox_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(ctr, key, out, n);
+}
+
+void launch_pt(const DevScene& S, int L, uint32_t spp, int n_chunks, Rng rng, double* part, double* mean,
+               unsigned long long* rays, uint32_t* err, cudaStream_t s) {
+  const long long n_pix = (long long)S.W * S.H;
+  const uint32_t spc = (spp + n_chunks - 1) / n_chunks;
+  const long long threads = n_pix * n_chunks;
+  const int d = 2 + 4 * (L - 1);
+  pt_kernel<<<(unsigned)((threads + kStepThreads - 1) / kStepThreads), kStepThreads, step_smem_bytes(), s>>>(
+      S, L, d, spp, spc, n_chunks, rng, part, rays, err);
+  pt_reduce_kernel<<<(unsigned)((n_pix * 3 + 255) / 256), 256, 0, s>>>(part, n_pix * 3, n_chunks, 1.0 / spp, mean);
 }
 
 void launch_sum_doubles(const double* in, int n, double* out, cudaStream_t s) {

@@ -239,6 +239,17 @@ size_t sort_scratch_bytes(size_t n) {
   return 2 * align256(nhist * 4) + align256(nchunks * 4);
 }
 
+size_t scan_scratch_bytes(size_t n) { return align256(((n + kScanChunk - 1) / kScanChunk + 1) * 4); }
+
+void launch_exclusive_scan(const uint32_t* in, uint32_t* out, size_t n, void* scratch, cudaStream_t s) {
+  if (n == 0) return;
+  const int nchunks = (int)((n + kScanChunk - 1) / kScanChunk);
+  uint32_t* sums = static_cast<uint32_t*>(scratch);
+  scan_reduce_kernel<<<nchunks, kScanThreads, 0, s>>>(in, n, sums);
+  scan_sums_kernel<<<1, kScanThreads, 0, s>>>(sums, nchunks);
+  scan_chunks_kernel<<<nchunks, kScanThreads, 0, s>>>(in, n, sums, out);
+}
+
 SplatRec* sort_splat_records(SplatRec* in, SplatRec* out, size_t n, int bits, void* scratch, cudaStream_t s) {
   return radix_sort<SplatRec>(in, out, n, bits, scratch, s);
 }

@@ -12,6 +12,11 @@
 
 namespace dr {
 
+// Per-ray bound on inner-node visits: far above any legitimate traversal of
+// the scenes here, it caps the time a corrupt hierarchy could take; hitting
+// it sets kErrBadIndex.
+constexpr int kMaxNodeVisits = 1 << 15;
+
 struct Ray {
   float3 o, d, inv;
 };
@@ -90,7 +95,7 @@ DR_D int trace_closest(const DevScene& S, const Ray& r, int exclude, float* t_hi
   int node = 0;
   // a tree traversal visits every inner node at most once: more visits mean
   // a corrupt hierarchy, reported instead of looping
-  int budget = 2 * S.n_nodes + 64;
+  int budget = min(2 * S.n_nodes + 64, kMaxNodeVisits);
   while (true) {
     if (--budget < 0 || node < 0 || node >= S.n_nodes) {
       *err |= kErrBadIndex;
@@ -158,7 +163,7 @@ DR_D bool trace_any(const DevScene& S, const Ray& r, float tmax, int ex0, int ex
                     uint32_t* err, TraceStats* stats) {
   int sp = 0;
   int node = 0;
-  int budget = 2 * S.n_nodes + 64;
+  int budget = min(2 * S.n_nodes + 64, kMaxNodeVisits);
   while (true) {
     if (--budget < 0 || node < 0 || node >= S.n_nodes) {
       *err |= kErrBadIndex;

@@ -69,6 +69,9 @@ class Renderer:
             pass
 
     # ---------------------------------------------------------------- inputs
+    def set_bvh_builder(self, builder="ploc", radius=16):
+        call("dr_set_bvh_builder", self.h, _lib.DR_BVH_PLOC if builder == "ploc" else _lib.DR_BVH_LBVH, int(radius))
+
     def upload_scene(self, scene):
         v = np.ascontiguousarray(scene.verts, np.float32)
         t = np.ascontiguousarray(scene.tris, np.int32)
@@ -189,6 +192,13 @@ class Renderer:
         f = torch.empty((M, 3), dtype=torch.float32, device=x.device) if want_f else None
         call("dr_eval_logp", self.h, int(L), _ptr(x), int(M), _ptr(logp), _ptr(g), _ptr(pix), _ptr(f))
         return logp, g, pix, f
+
+    def pt_render(self, L, spp, seed=7):
+        """Stratified path-traced image [H, W, 3] (FP64 CUDA tensor) of the
+        uploaded scene, in the units of resolve()."""
+        out = torch.empty((self.height, self.width, 3), dtype=torch.float64, device=self.device)
+        call("dr_pt_render", self.h, int(L), int(spp), int(seed), _ptr(out))
+        return out
 
     def trace_closest(self, rays, exclude=-1):
         rays = rays.contiguous()

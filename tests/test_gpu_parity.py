@@ -53,8 +53,9 @@ def test_philox_bit_exact(torch, R, oracle):
     assert np.array_equal(mine, oracle.philox4x32_10(ctr, key))
 
 
+@pytest.mark.parametrize("builder", ["ploc", "lbvh"])
 @pytest.mark.parametrize("which", ["cornell", "caustic", "procedural"])
-def test_closest_hit_matches_oracle(torch, R, oracle, which):
+def test_closest_hit_matches_oracle(torch, R, oracle, which, builder):
     if which == "cornell":
         scene = S.cornell_box(1, 16, 16)
     elif which == "caustic":
@@ -62,6 +63,7 @@ def test_closest_hit_matches_oracle(torch, R, oracle, which):
     else:
         scene = S.procedural_scene(1, 32, 18, target_tris=30000, n_objects=40)
     r = R.Renderer()
+    r.set_bvh_builder(builder)
     r.upload_scene(scene)
     info = r.bvh_info()
     assert info["n_tris"] == scene.n_tris and info["max_depth"] < 48
@@ -199,6 +201,22 @@ def test_chain_parity_race_clock(torch, R, oracle):
     frac, first, n = _chain_parity(torch, R, oracle, scene, pg, po, N=1024, M=512, T=16, seed=8)
     print("race-clock divergent fraction", frac)
     assert frac <= 0.01
+
+
+def test_pt_reference_image_matches_oracle(torch, R, oracle):
+    """Stratified path tracing on the GPU and in the oracle draw the same
+    Philox numbers, so their per-pixel means agree sample for sample."""
+    scene = S.cornell_box(3, 16, 16, glossy=True)
+    L, spp = 5, 256
+    r = R.Renderer()
+    r.upload_scene(scene)
+    img = r.pt_render(L, spp, seed=99).cpu().numpy().reshape(-1, 3)
+    mean, var = oracle.pt_image(oracle.OracleScene(scene), L, spp, seed=99)
+    err = np.abs(img - mean)
+    close = err <= 1e-3 * np.maximum(mean, 1e-3) + 3e-3 * np.sqrt(var)
+    assert close.mean() > 0.98, close.mean()
+    assert abs(img.mean() / mean.mean() - 1) < 1e-3
+    r.close()
 
 
 def test_k0_estimate_matches_oracle(torch, R, oracle):
