@@ -129,21 +129,26 @@ def dist_env():
     return rank, world, local
 
 
-def cpu_baseline(wl, scene, steps=3, target_s=15.0):
+def cpu_baseline(wl, scene, steps=8, target_s=15.0):
     """The FP64 oracle, as it stands, on this host's cores: a bounded sample
-    of the same workload (a subset of the chains, a few steps)."""
+    of the same workload (the first m of its chains for init + `steps`
+    steps), sized by a calibration run to about target_s seconds."""
     from oracle import oracle as O
     tgt = O.OracleScene(scene)
     cores = O.num_threads()
     prm = O.make_params(L=wl["L"], drift="exact" if wl["drift"] == "adjoint" else wl["drift"], rb=True, k0=1.0)
-    # p_lambda estimate on a small uniform sample sets k0 as the GPU run does
-    est = O.restore_run(tgt, prm, seed=SEED, chain_ids=np.arange(256), n_steps=0, record=False)
-    prm.k0 = est["p_init_sum"] / 256 / (64.0 * 1e-5)
-    m = 16
-    t0 = time.perf_counter()
-    O.restore_run(tgt, prm, seed=SEED, chain_ids=np.arange(m), n_steps=steps, record=False, accum=False)
-    dt = time.perf_counter() - t0
-    m = int(max(16, min(wl["cpu_chains"] * 64, m * target_s / max(dt, 1e-3))))
+    # p_lambda estimate on a uniform sample sets k0 as the GPU run does
+    est = O.restore_run(tgt, prm, seed=SEED, chain_ids=np.arange(4096), n_steps=0, record=False)
+    prm.k0 = est["p_init_sum"] / 4096 / (64.0 * 1e-5)
+    m = 1024
+    while True:
+        t0 = time.perf_counter()
+        O.restore_run(tgt, prm, seed=SEED, chain_ids=np.arange(m), n_steps=steps, record=False, accum=False)
+        dt = time.perf_counter() - t0
+        if dt > 1.0 or m >= wl["chains"]:
+            break
+        m = min(wl["chains"], m * 4)
+    m = int(max(16, min(wl["chains"], m * target_s / max(dt, 1e-3))))
     t0 = time.perf_counter()
     O.restore_run(tgt, prm, seed=SEED, chain_ids=np.arange(m), n_steps=steps, record=False, accum=False)
     dt = time.perf_counter() - t0

@@ -251,9 +251,15 @@ void build_bvh(Scene& S) {
 }
 
 // Closest hit: smallest t; ties broken by the smallest triangle id.
+inline bool finite_ray(const D3& o, const D3& d) {
+  return std::isfinite(o.x) && std::isfinite(o.y) && std::isfinite(o.z) && std::isfinite(d.x) &&
+         std::isfinite(d.y) && std::isfinite(d.z);
+}
+
 bool closest(const Scene& S, const D3& o, const D3& d, int exclude, int* tri, double* t, long* tests = nullptr) {
   int best = -1;
   double bt = INFINITY;
+  if (!finite_ray(o, d)) return false;
   auto consider = [&](int i) {
     if (i == exclude) return;
     double th;
@@ -290,6 +296,7 @@ bool closest(const Scene& S, const D3& o, const D3& d, int exclude, int* tri, do
 
 // Any hit in (tmin, tmax), ignoring two triangle ids.
 bool occluded(const Scene& S, const D3& o, const D3& d, double tmax, int ex0, int ex1) {
+  if (!finite_ray(o, d)) return true;
   auto test = [&](int i) {
     if (i == ex0 || i == ex1) return false;
     double th;
@@ -475,9 +482,12 @@ void eval_path(const Scene& S, const T* x, int L, PathOut<T>& out) {
     double th;
     ++info.rays;
     if (!closest(S, vval(o), vval(d), prev_tri, &tri, &th)) break;
+    const Tri& tr = S.tris[tri];
+    // a hit within 1e-6 (cosine) of grazing ends the path: the hit distance
+    // as a function of the ray is ill-conditioned there
+    if (!(std::fabs(dot(vval(d), tr.ng)) >= 1e-6)) break;
     info.nseg = seg;
     info.tri[seg - 1] = tri;
-    const Tri& tr = S.tris[tri];
     const Mat& m = S.mats[tr.mat];
     // differentiable hit point on the (fixed) plane of the hit triangle
     V3<T> N = lift<T>(tr.N);

@@ -912,18 +912,34 @@ int dr_bvh_info(dr_ctx* c, int32_t* n_nodes, int32_t* n_tris, int32_t* max_depth
   std::vector<float4> nodes((size_t)nn * 4);
   DR_CUDA(cudaMemcpyAsync(nodes.data(), c->nodes, nodes.size() * 16, cudaMemcpyDeviceToHost, c->stream));
   DR_CUDA(cudaStreamSynchronize(c->stream));
+  // walk the hierarchy once, checking that it is a tree: every inner node is
+  // reached exactly once and every triangle lies in exactly one leaf
   int depth = 0;
+  std::vector<uint8_t> seen_node((size_t)nn, 0), seen_tri((size_t)std::max(1, c->nt), 0);
   std::vector<std::pair<int, int>> st{{0, 1}};
+  long long leaves_tris = 0;
   while (!st.empty()) {
     auto [n, dd] = st.back();
     st.pop_back();
     if (n < 0 || n >= nn) return fail(DR_ERR_DEVICE_CHECK, "dr_bvh_info: corrupt node index");
+    if (seen_node[n]++) return fail(DR_ERR_DEVICE_CHECK, "dr_bvh_info: node reached twice (not a tree)");
     depth = std::max(depth, dd);
-    const int c0 = hbits_i(nodes[4 * n + 3].x), c1 = hbits_i(nodes[4 * n + 3].y);
-    if (c0 >= 0) st.push_back({c0, dd + 1});
-    if (c1 >= 0) st.push_back({c1, dd + 1});
-    if ((int)st.size() > 4 * nn + 8) return fail(DR_ERR_DEVICE_CHECK, "dr_bvh_info: cycle in BVH");
+    const int ch[2] = {hbits_i(nodes[4 * n + 3].x), hbits_i(nodes[4 * n + 3].y)};
+    for (int k = 0; k < 2; ++k) {
+      if (ch[k] >= 0) {
+        st.push_back({ch[k], dd + 1});
+      } else if (!(c->nt == 1 && k == 1)) {  // a one-triangle scene repeats its leaf
+        const int first = leaf_first(ch[k]), cnt = leaf_count(ch[k]);
+        for (int i = first; i < first + cnt; ++i) {
+          if (i >= c->nt || seen_tri[i]++) return fail(DR_ERR_DEVICE_CHECK, "dr_bvh_info: bad or repeated leaf");
+          ++leaves_tris;
+        }
+      }
+    }
   }
+  if (leaves_tris != c->nt) return fail(DR_ERR_DEVICE_CHECK, "dr_bvh_info: triangles missing from the leaves");
+  for (int i = 0; i < c->n_nodes; ++i)
+    if (!seen_node[i]) return fail(DR_ERR_DEVICE_CHECK, "dr_bvh_info: unreachable inner node");
   if (n_nodes) *n_nodes = c->n_nodes;
   if (n_tris) *n_tris = c->nt;
   if (max_depth) *max_depth = depth;

@@ -345,6 +345,10 @@ DR_D int pixel_of(float x0, float x1, int W, int H) {
   return row * W + col;
 }
 
+// A hit is kept when the unit ray direction is not within 1e-6 (cosine) of
+// the triangle's plane.
+DR_D bool grazing_ok(float3 d, float3 ng) { return fabsf(dot(d, ng)) >= 1e-6f; }
+
 DR_D float3 camera_dir(const Camera& C, float x0, float x1, float3* raw) {
   const float sx = (2.0f * x0 - 1.0f) * C.tx, sy = (1.0f - 2.0f * x1) * C.ty;
   *raw = C.fwd + C.right * sx + C.up * sy;
@@ -422,6 +426,10 @@ DR_D PathResult path_forward(const DevScene& S, const XA& xa, int L, Tape<LMAX>*
     float th;
     const int tri = trace_closest<STACK, STATS>(S, r, prev_tri, &th, st, err, stats);
     if (tri < 0) break;
+    const Surf sf = load_surf(S, tri);
+    // grazing hits (|cos| < 1e-6) end the path: the differentiable hit
+    // distance (v0 - o).N / d.N is ill-conditioned there
+    if (!grazing_ok(d, sf.ng)) break;
     res.nseg = seg;
     int flags = prev_delta ? kFPrevDelta : 0;
     if (TAPE) {
@@ -429,7 +437,6 @@ DR_D PathResult path_forward(const DevScene& S, const XA& xa, int L, Tape<LMAX>*
       tape->b[seg - 1] = make_float4(d.x, d.y, d.z, __int_as_float(tri));
       tape->c[seg - 1] = make_float4(beta.x, beta.y, beta.z, __int_as_float(flags));
     }
-    const Surf sf = load_surf(S, tri);
     const MatP m = load_mat(S.mats, sf.mat);
     const float t = dot(sf.v0 - o, sf.N) / dot(d, sf.N);
     const float3 P = o + d * t;

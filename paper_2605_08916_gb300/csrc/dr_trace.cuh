@@ -21,6 +21,12 @@ struct Ray {
   float3 o, d, inv;
 };
 
+// A NaN in the ray makes every slab test pass (fminf / fmaxf drop NaNs), so
+// such a ray would walk the whole tree: it is refused up front.
+DR_D bool ray_finite(float3 o, float3 d) {
+  return isfinite(o.x) && isfinite(o.y) && isfinite(o.z) && isfinite(d.x) && isfinite(d.y) && isfinite(d.z);
+}
+
 DR_D Ray make_ray(float3 o, float3 d) {
   Ray r;
   r.o = o;
@@ -29,7 +35,9 @@ DR_D Ray make_ray(float3 o, float3 d) {
   return r;
 }
 
-// Slab test of one box against [0, tmax]; returns entry distance or +inf.
+// Slab test of one box against [0, tmax]: the entry distance (>= 0) of a
+// hit box, or -1 for a miss.  (A miss must not compare below an infinite
+// tmax, so it is negative rather than +inf.)
 DR_D float box_entry(float3 lo, float3 hi, const Ray& r, float tmax) {
   const float tx0 = (lo.x - r.o.x) * r.inv.x, tx1 = (hi.x - r.o.x) * r.inv.x;
   const float ty0 = (lo.y - r.o.y) * r.inv.y, ty1 = (hi.y - r.o.y) * r.inv.y;
@@ -37,7 +45,7 @@ DR_D float box_entry(float3 lo, float3 hi, const Ray& r, float tmax) {
   const float tn = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), 0.0f));
   const float tf = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), tmax));
   // a small relative slack keeps boxes of hits at exactly tmax
-  return tn <= tf * 1.0000002f ? tn : __int_as_float(0x7f800000);
+  return tn <= tf * 1.0000002f ? tn : -1.0f;
 }
 
 // Moller-Trumbore; hit iff det != 0, u >= 0, v >= 0, u + v <= 1, tmin < t < tmax.
@@ -93,6 +101,11 @@ DR_D int trace_closest(const DevScene& S, const Ray& r, int exclude, float* t_hi
   int best = -1;
   int sp = 0;
   int node = 0;
+  if (!ray_finite(r.o, r.d)) {
+    *err |= kErrNonFinite;
+    *t_hit = tbest;
+    return -1;
+  }
   // a tree traversal visits every inner node at most once: more visits mean
   // a corrupt hierarchy, reported instead of looping
   int budget = min(2 * S.n_nodes + 64, kMaxNodeVisits);
@@ -112,7 +125,7 @@ DR_D int trace_closest(const DevScene& S, const Ray& r, int exclude, float* t_hi
     for (int k = 0; k < 2; ++k) {
       const int c = k == 0 ? c0 : c1;
       const float e = k == 0 ? e0 : e1;
-      if (c < 0 && e <= tbest) {
+      if (c < 0 && e >= 0.0f && e <= tbest) {
         const int first = leaf_first(c);
         int cnt = leaf_count(c);
         if (first + cnt > S.n_tris) {
@@ -135,7 +148,7 @@ DR_D int trace_closest(const DevScene& S, const Ray& r, int exclude, float* t_hi
         }
       }
     }
-    const bool in0 = c0 >= 0 && e0 <= tbest, in1 = c1 >= 0 && e1 <= tbest;
+    const bool in0 = c0 >= 0 && e0 >= 0.0f && e0 <= tbest, in1 = c1 >= 0 && e1 >= 0.0f && e1 <= tbest;
     if (in0 && in1) {
       const int nearc = e0 <= e1 ? c0 : c1, farc = e0 <= e1 ? c1 : c0;
       if (sp < STACK) {
@@ -163,6 +176,10 @@ DR_D bool trace_any(const DevScene& S, const Ray& r, float tmax, int ex0, int ex
                     uint32_t* err, TraceStats* stats) {
   int sp = 0;
   int node = 0;
+  if (!ray_finite(r.o, r.d)) {
+    *err |= kErrNonFinite;
+    return true;  // treated as occluded: no contribution from a broken ray
+  }
   int budget = min(2 * S.n_nodes + 64, kMaxNodeVisits);
   while (true) {
     if (--budget < 0 || node < 0 || node >= S.n_nodes) {
@@ -179,7 +196,7 @@ DR_D bool trace_any(const DevScene& S, const Ray& r, float tmax, int ex0, int ex
     for (int k = 0; k < 2; ++k) {
       const int c = k == 0 ? c0 : c1;
       const float e = k == 0 ? e0 : e1;
-      if (c < 0 && e <= tmax) {
+      if (c < 0 && e >= 0.0f) {
         const int first = leaf_first(c);
         int cnt = leaf_count(c);
         if (first + cnt > S.n_tris) {
@@ -197,7 +214,7 @@ DR_D bool trace_any(const DevScene& S, const Ray& r, float tmax, int ex0, int ex
         }
       }
     }
-    const bool in0 = c0 >= 0 && e0 <= tmax, in1 = c1 >= 0 && e1 <= tmax;
+    const bool in0 = c0 >= 0 && e0 >= 0.0f, in1 = c1 >= 0 && e1 >= 0.0f;
     if (in0 && in1) {
       if (sp < STACK) {
         st.at(sp++) = e0 <= e1 ? c1 : c0;
