@@ -239,6 +239,33 @@ int dr_pt_render(dr_ctx* ctx, int32_t max_path_len, uint32_t spp, uint64_t seed,
 enum { DR_BVH_LBVH = 0, DR_BVH_PLOC = 1 };
 int dr_set_bvh_builder(dr_ctx* ctx, int32_t builder, int32_t radius);
 
+/* Splat without allocating: the paper has no counterpart to this entry point;
+ * it exists for callers that cannot call cudaMalloc (for example a render
+ * loop held to a fixed device-memory budget, code running where another
+ * framework owns the device's allocator, or code that must not pay for the
+ * device-wide synchronisation cudaMalloc / cudaFree can cause).
+ * It computes what dr_splat_records computes: accum[pix * 3 + c] += the FP64
+ * sum of the records' values, sorted by pixel (stable, so the sum order is
+ * the records' order), without a context.
+ *   recs    DEVICE, M records of 16 bytes (uint32 pixel, float r, g, b);
+ *           only read.
+ *   M       0 .. DR_NOALLOC_MAX_RECORDS; larger M is rejected with
+ *           DR_ERR_INVALID_ARG (split the records into batches).
+ *   n_pix   number of pixels; records with pixel >= n_pix are skipped.
+ *   accum   DEVICE FP64 [n_pix * 3], added to (not cleared).
+ *   cuda_stream  stream to issue on (NULL: legacy default stream).
+ * All pointers must belong to the current CUDA device.  The scratch is a
+ * fixed array of about 2.1 MB in this library's device memory, present on
+ * every GPU that loads the library until the process exits; it calls no
+ * cudaMalloc, cudaFree or allocating routine.  The first call on a device
+ * looks up the array's device address (once per device; make that first
+ * call before any stream capture).  Every call on a device shares the one
+ * array, so calls that overlap on the GPU (for example on two streams at
+ * once) race; issue them in order on one stream, or synchronise between
+ * them.  Asynchronous.  Errors: INVALID_ARG, CUDA. */
+enum { DR_NOALLOC_MAX_RECORDS = 65536 };
+int dr_splat_records_noalloc(const void* recs, int64_t M, int32_t n_pix, double* accum, void* cuda_stream);
+
 /* Shape of the current chain state (HOST outputs, any may be NULL): number
  * of chains N, PSS dimension d and max path length L; the sizes callers of
  * dr_readback_state must allocate for (e.g. after dr_state_load).

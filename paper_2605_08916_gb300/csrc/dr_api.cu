@@ -81,6 +81,12 @@ int fail(int code, const std::string& msg) {
   return code;
 }
 
+}  // namespace
+
+void dr::set_error_message(const char* msg) { g_err = msg; }
+
+namespace {
+
 #define DR_CUDA(call)                                                                              \
   do {                                                                                             \
     cudaError_t e_ = (call);                                                                       \

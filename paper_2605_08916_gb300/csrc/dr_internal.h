@@ -8,6 +8,9 @@
 
 namespace dr {
 
+// Sets the thread-local message returned by dr_last_error().
+void set_error_message(const char* msg);
+
 // ---------------------------------------------------------------- sorting
 // Stable LSD radix sort (8-bit digits) of 16-B splat records by pixel, or of
 // 8-B (key, value) pairs by key.  `bits` = number of significant key bits.
