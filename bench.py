@@ -198,7 +198,7 @@ def run_ours(args, wl, rank, world, local):
         dist.init_process_group("nccl", device_id=dev)
     scene = wl["scene"]()
     log(f"scene {scene.name}: {scene.n_tris} triangles")
-    N = wl["chains"]
+    N = args.chains or wl["chains"]
     params = R.make_params(L=wl["L"], drift=wl["drift"], rb=True, k0=0.0, steps_per_splat=wl["spp"])
     from paper_2605_08916_gb300.replicas import replica_seed
     seed = replica_seed(SEED, rank)
@@ -271,7 +271,7 @@ def run_ours(args, wl, rank, world, local):
     line = None
     if rank == 0:
         log(f"timed {args.steps} steps: {total_ms:.1f} ms")
-        e2e = run_e2e(R, scene, wl, N, args.steps, local, stream)
+        e2e = None if args.no_e2e else run_e2e(R, scene, wl, N, args.steps, local, stream)
         log("e2e done")
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
@@ -334,6 +334,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end run (profiling cases)")
+    ap.add_argument("--chains", type=int, default=0, help="override the workload's chain count (profiling cases)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
