@@ -204,6 +204,8 @@ def run_ours(args, wl, rank, world, local):
     seed = replica_seed(SEED, rank)
     stream = torch.cuda.current_stream(dev)
     r = R.Renderer(local, stream)
+    r.set_option("work_order", args.work_order)
+    r.set_option("wavefront", args.wavefront)
     r.upload_scene(scene)
     r.init_chains(N, seed, params)
     torch.cuda.synchronize()
@@ -336,6 +338,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end run (profiling cases)")
     ap.add_argument("--chains", type=int, default=0, help="override the workload's chain count (profiling cases)")
+    ap.add_argument("--wavefront", type=int, default=-1, choices=[-1, 0, 1],
+                    help="bounce-by-bounce execution over compacted path queues: 1 on, 0 fused kernel, "
+                         "-1 (default) by chain count")
+    ap.add_argument("--work-order", type=int, default=0, choices=[0, 1],
+                    help="fused kernel only: order chains by expected path cost (default 0)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -231,6 +231,23 @@ int dr_get_launch_count(dr_ctx* ctx, uint64_t* launches);
  * Errors: STATE (no scene), INVALID_ARG, OOM, CUDA, DEVICE_CHECK. */
 int dr_pt_render(dr_ctx* ctx, int32_t max_path_len, uint32_t spp, uint64_t seed, double* out_mean);
 
+/* Execution options (they change speed only, never results):
+ *   DR_OPT_WAVEFRONT   1: adjoint-drift steps on a scene run bounce by
+ *                      bounce over compacted queues of live paths (trace /
+ *                      shade / shadow kernels per bounce, the per-segment
+ *                      tape in device memory, the adjoint pass over
+ *                      surviving chains only); 0: one fused kernel, one
+ *                      thread per chain-step; -1 (default): wavefront from
+ *                      2^17 chains up, fused below.  The two agree to
+ *                      floating-point contraction order (last-bit level).
+ *   DR_OPT_WORK_ORDER  for the fused kernel only: 1 orders chains by
+ *                      (killed last step, previous path length) with one
+ *                      stable radix pass before each step so that warps
+ *                      trace paths of similar cost; 0 (default): chain order.
+ * Errors: INVALID_ARG (unknown option or value). */
+enum { DR_OPT_WORK_ORDER = 1, DR_OPT_WAVEFRONT = 2 };
+int dr_set_option(dr_ctx* ctx, int32_t option, int32_t value);
+
 /* BVH construction used by later dr_scene_upload calls:
  * DR_BVH_PLOC (default; parallel locally-ordered clustering of the
  * Morton-ordered triangles with search radius `radius`, 1..256, default 16)

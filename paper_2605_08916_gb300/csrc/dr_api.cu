@@ -49,6 +49,9 @@ struct dr_ctx {
   float* score = nullptr;
   float* logp = nullptr;
   uint8_t* killed = nullptr;
+  uint8_t* plen = nullptr;      // [N] last path length (work-order key)
+  uint2* order_a = nullptr;     // [N] (key, chain) pairs and the sort's ping-pong buffer
+  uint2* order_b = nullptr;
   SplatRec* rec = nullptr;
   SplatRec* rec_alt = nullptr;
   size_t rec_cap = 0;  // steps
@@ -70,6 +73,11 @@ struct dr_ctx {
   bool stats = false;
   int builder = DR_BVH_PLOC;
   int ploc_radius = 16;
+  int work_order = 0;  // DR_OPT_WORK_ORDER
+  int wavefront = -1;  // DR_OPT_WAVEFRONT: -1 auto (N >= 2^17), 0 fused, 1 wavefront
+  void* wf_mem = nullptr;
+  size_t wf_cap = 0;
+  int n_sm = 152;
 };
 
 namespace {
@@ -250,6 +258,34 @@ int one_step(dr_ctx* c, bool init) {
   a.step = c->step;
   a.rec = c->rec + (size_t)c->rec_count * c->N;
   a.p_partial = init ? c->p_partial : nullptr;
+  a.plen = c->plen;
+  const bool adjoint_scene = c->prm.drift_mode == DR_DRIFT_ADJOINT && c->target == 0;
+  const bool use_wf = c->wavefront == 1 || (c->wavefront == -1 && c->N >= (1ull << 17));
+  if (!init && adjoint_scene && use_wf) {
+    const size_t need = wf_bytes(c->N, c->prm.max_path_len);
+    if (need > c->wf_cap) {
+      if (c->wf_mem) cudaFree(c->wf_mem);
+      c->wf_mem = nullptr;
+      c->wf_cap = 0;
+      cudaError_t e = cudaMalloc(&c->wf_mem, need);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        c->wf_mem = nullptr;
+        return fail(DR_ERR_OOM, "wavefront buffers");
+      }
+      c->wf_cap = need;
+    }
+    const WfBuffers w = wf_carve(c->wf_mem, c->N, c->prm.max_path_len);
+    c->launches += launch_wavefront_step(a, w, c->stats, c->n_sm, c->stream);
+    DR_TRY(check_launch("wavefront step"));
+    c->rec_count++;
+    return DR_OK;
+  }
+  if (!init && c->work_order && adjoint_scene) {
+    launch_order_keys(c->killed, c->plen, c->N, c->order_a, c->stream);
+    a.order = sort_pairs(c->order_a, c->order_b, c->N, 6, c->sort_scratch, c->stream);
+    c->launches += 6;
+  }
   launch_step(a, c->stats, c->stream);
   c->launches += 1;
   DR_TRY(check_launch("restore_step"));
@@ -285,6 +321,10 @@ int dr_create(dr_ctx** out, int device, void* cuda_stream) {
   dr_ctx* c = new dr_ctx();
   c->device = device;
   c->stream = static_cast<cudaStream_t>(cuda_stream);
+  int n_sm = 0;
+  if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, device) == cudaSuccess && n_sm > 0)
+    c->n_sm = n_sm;
+  cudaGetLastError();
   int r = dalloc(&c->counters, 4);
   if (r == DR_OK) r = dalloc(&c->err, 1);
   if (r == DR_OK) r = dalloc(&c->p_sum, 1);
@@ -304,7 +344,9 @@ int dr_destroy(dr_ctx* c) {
   cudaStreamSynchronize(c->stream);
   dfree(&c->nodes); dfree(&c->tris); dfree(&c->surf); dfree(&c->lights); dfree(&c->nrm); dfree(&c->mats);
   dfree(&c->mw); dfree(&c->mmu); dfree(&c->msig);
-  dfree(&c->x); dfree(&c->score); dfree(&c->logp); dfree(&c->killed); dfree(&c->rec); dfree(&c->rec_alt);
+  dfree(&c->x); dfree(&c->score); dfree(&c->logp); dfree(&c->killed);
+  dfree(&c->plen); dfree(&c->order_a); dfree(&c->order_b);
+  if (c->wf_mem) cudaFree(c->wf_mem); dfree(&c->rec); dfree(&c->rec_alt);
   if (c->sort_scratch) cudaFree(c->sort_scratch);
   dfree(&c->accum); dfree(&c->counters); dfree(&c->p_partial); dfree(&c->p_sum); dfree(&c->err);
   delete c;
@@ -504,6 +546,9 @@ static int alloc_chains(dr_ctx* c, unsigned long long N, int d, int spp) {
   if (N > c->chains_cap) {
     DR_TRY(dalloc(&c->logp, N));
     DR_TRY(dalloc(&c->killed, N));
+    DR_TRY(dalloc(&c->plen, N));
+    DR_TRY(dalloc(&c->order_a, N));
+    DR_TRY(dalloc(&c->order_b, N));
     c->chains_cap = N;
   }
   const size_t nrec = (size_t)N * spp;
@@ -553,6 +598,7 @@ int dr_chains_init(dr_ctx* c, uint64_t n_chains, uint64_t seed, uint32_t frame, 
   cudaStream_t s = c->stream;
   DR_CUDA(cudaMemsetAsync(c->score, 0, (size_t)n_chains * d * 4, s));
   DR_CUDA(cudaMemsetAsync(c->killed, 0, (size_t)n_chains, s));
+  DR_CUDA(cudaMemsetAsync(c->plen, 0, (size_t)n_chains, s));
   DR_CUDA(cudaMemsetAsync(c->accum, 0, c->accum_n * 8, s));
   DR_CUDA(cudaMemsetAsync(c->counters, 0, 4 * 8, s));
   DR_CUDA(cudaMemsetAsync(c->err, 0, 4, s));
@@ -883,6 +929,22 @@ int dr_pt_render(dr_ctx* c, int32_t L, uint32_t spp, uint64_t seed, double* out_
   dfree(&part);
   if (e != cudaSuccess) return fail(DR_ERR_CUDA, std::string("dr_pt_render: ") + cudaGetErrorString(e));
   return check_device_error(c);
+}
+
+int dr_set_option(dr_ctx* c, int32_t option, int32_t value) {
+  if (!c) return fail(DR_ERR_INVALID_ARG, "dr_set_option: NULL ctx");
+  switch (option) {
+    case DR_OPT_WAVEFRONT:
+      if (value < -1 || value > 1) return fail(DR_ERR_INVALID_ARG, "dr_set_option: wavefront is -1, 0 or 1");
+      c->wavefront = value;
+      return DR_OK;
+    case DR_OPT_WORK_ORDER:
+      if (value != 0 && value != 1) return fail(DR_ERR_INVALID_ARG, "dr_set_option: work order is 0 or 1");
+      c->work_order = value;
+      return DR_OK;
+    default:
+      return fail(DR_ERR_INVALID_ARG, "dr_set_option: unknown option");
+  }
 }
 
 int dr_set_bvh_builder(dr_ctx* c, int32_t builder, int32_t radius) {

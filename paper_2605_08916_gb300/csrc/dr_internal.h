@@ -76,6 +76,8 @@ struct StepArgs {
   double k0;
   int rb, drift, init;
   int estimate_only;  // init pass that only sums p (k0 unknown yet)
+  const uint2* order;  // [N] (key, chain) pairs: thread t works on chain order[t].y; null = identity
+  uint8_t* plen;       // [N] path length of the chain's last evaluation (null: not recorded)
   unsigned long long* tour_count;
   unsigned long long* rays;
   unsigned long long* node_visits;  // stats mode only
@@ -83,6 +85,37 @@ struct StepArgs {
   double* p_partial;  // [gridDim.x] init only
   uint32_t* err;
 };
+
+// (key, chain) pairs for the work order of the next step
+void launch_order_keys(const uint8_t* killed, const uint8_t* plen, unsigned long long N, uint2* keys,
+                       cudaStream_t s);
+
+// ---------------------------------------------------------------- wavefront
+// NEE shadow ray of one vertex: origin + tmax, direction + chain id bits,
+// pending contribution + excluded triangle, second excluded triangle.
+struct __align__(16) ShadowRec {
+  float4 o_tmax, wi_chain, contrib_ex;
+  int ex1, pad0, pad1, pad2;
+};
+// counters: [k] = rays of bounce k (1..16), [17 + k] = shadow rays of bounce
+// k, [34] = surviving chains for the adjoint pass
+constexpr int kWfShadowCount0 = 17;
+constexpr int kWfAdjointCount = 34;
+constexpr int kWfCounts = 36;
+struct WfBuffers {
+  float4* slot;        // [N][4] path state
+  int* hit;            // [N] closest-hit triangle of the current ray
+  uint32_t* queue[2];  // ray queues (ping-pong), chain ids
+  ShadowRec* shadow;   // [N] shadow queue of the current bounce
+  uint32_t* adj;       // [N] chains for the adjoint pass
+  uint32_t* counts;    // [kWfCounts]
+  float4* tape;        // [L][3][N]
+};
+size_t wf_bytes(unsigned long long N, int L);
+WfBuffers wf_carve(void* base, unsigned long long N, int L);
+// One adjoint-drift Restore step on a scene, bounce by bounce; returns the
+// number of kernels (and memsets) issued.
+int launch_wavefront_step(const StepArgs& a, const WfBuffers& w, bool stats, int n_sm, cudaStream_t s);
 
 int step_block_size();
 size_t step_smem_bytes();

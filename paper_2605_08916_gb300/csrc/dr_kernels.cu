@@ -15,8 +15,7 @@
 //      only for chains that survived.
 // Kill counts and ray counts are reduced per block (warp shuffles, then one
 // integer atomic per block); no per-lane global atomics.
-#include "dr_internal.h"
-#include "dr_path.cuh"
+#include "dr_step.cuh"
 
 namespace dr {
 
@@ -24,12 +23,6 @@ namespace {
 
 constexpr int kStepThreads = 128;
 constexpr int kStack = 48;
-
-struct XSoA {
-  const float* x;
-  unsigned long long N, j;
-  DR_D float operator()(int i) const { return x[(size_t)i * N + j]; }
-};
 
 struct XPerturbed {
   const float* x;
@@ -46,12 +39,6 @@ struct XRow {
   DR_D float operator()(int i) const { return x[(size_t)j * d + i]; }
 };
 
-struct GSoA {
-  float* g;
-  unsigned long long N, j;
-  DR_D void operator()(int i, float v) const { g[(size_t)i * N + j] = v; }
-};
-
 struct GRow {
   float* g;
   int d;
@@ -62,12 +49,6 @@ struct GRow {
 struct GNone {
   DR_D void operator()(int, float) const {}
 };
-
-DR_D unsigned long long warp_sum_u64(unsigned long long v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  return v;
-}
 
 DR_D double warp_sum_f64(double v) {
 #pragma unroll
@@ -92,7 +73,7 @@ DR_D float3 evaluate(const DevScene& S, const DevMixture& M, int target, int L, 
   *pix = r.pix;
   const float p = lum(r.f) + eps;
   *p_out = p;
-  if (TAPE && want_grad) path_adjoint(S, xa, L, p, tape, r.nseg, gw);
+  if (TAPE && want_grad) path_adjoint(S, xa, L, p, LocalTape<kMaxPathLen>{&tape}, r.nseg, gw);
   return r.f;
 }
 
@@ -100,75 +81,44 @@ template <int DRIFT, bool STATS>
 __global__ void __launch_bounds__(kStepThreads) step_kernel(StepArgs a) {
   extern __shared__ int smem[];
   TraceStack<kStack> st{smem + threadIdx.x, (int)blockDim.x};
-  const unsigned long long j = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const bool active = j < a.N;
+  // thread t works on chain order[t] (or t); all state is indexed by chain
+  const unsigned long long t = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool active = t < a.N;
+  const unsigned long long j = active && a.order ? (unsigned long long)a.order[t].y : t;
   uint32_t err = 0, rays = 0;
   TraceStats stats{0u, 0u};
   unsigned long long kill = 0;
   double pval = 0.0;
   if (active) {
     const uint32_t cj = (uint32_t)j;
-    const bool regen = a.init || a.killed[j];
-    if (regen) {
-      for (int i = 0; i < a.d; i += 4) {
-        const U4 r = a.rng.draw(a.step, cj, (uint32_t)(i >> 2), kRegen);
-        const uint32_t w[4] = {r.a, r.b, r.c, r.d};
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-          if (i + k < a.d) a.x[(size_t)(i + k) * a.N + j] = u01(w[k]);
-      }
-    } else {
-      const float c2 = 0.5f * a.stddev * a.stddev;
-      for (int q = 0; q < a.d / 2; ++q) {
-        const U4 r = a.rng.draw(a.step, cj, (uint32_t)(q >> 1), kNormal);
-        const float ua = u01((q & 1) ? r.c : r.a), ub = u01((q & 1) ? r.d : r.b);
-        const float2 xi = box_muller(ua, ub);
-        const size_t i0 = (size_t)(2 * q) * a.N + j, i1 = (size_t)(2 * q + 1) * a.N + j;
-        const float s0 = a.score[i0], s1 = a.score[i1];
-        a.x[i0] = wrap01(a.x[i0] + c2 * s0 + a.gamma_tilde * s1 + a.stddev * xi.x);
-        a.x[i1] = wrap01(a.x[i1] + c2 * s1 - a.gamma_tilde * s0 + a.stddev * xi.y);
-      }
-    }
+    evolve_x(a, j, a.init || a.killed[j]);
     const XSoA xa{a.x, a.N, j};
     int pix;
     float p;
     float3 f;
     const U4 rc = a.rng.draw(a.step, cj, 0u, kClock);
     const float u1 = u01(rc.a), u2 = u01(rc.b);
-    if (DRIFT == kDriftAdjoint && !a.estimate_only) {
+    bool killed = false;
+    float wt = 0.0f;
+    if (DRIFT == kDriftAdjoint && !a.estimate_only && a.target == 0) {
       // forward with tape; kill decision; adjoint only if the chain survives
-      if (a.target == 1) {
-        f = evaluate<false, STATS>(a.S, a.M, 1, a.L, a.eps, xa, &pix, &p, false, GNone{}, st, &err, &stats, &rays);
-      } else {
-        Tape<kMaxPathLen> tape;
-        const PathResult r = path_forward<kStack, STATS, true>(a.S, xa, a.L, &tape, st, &err, &stats);
-        rays += r.rays;
-        pix = r.pix;
-        f = r.f;
-        p = lum(f) + a.eps;
-        bool killed_now;
-        if (a.rb) killed_now = (double)u2 * ((double)a.h * p + a.k0) < a.k0;
-        else killed_now = !(-logf(1.0f - u1) / a.h < -logf(1.0f - u2) * p / (float)a.k0);
-        if (!killed_now) path_adjoint(a.S, xa, a.L, p, tape, r.nseg, GSoA{a.score, a.N, j});
-      }
+      Tape<kMaxPathLen> tape;
+      const PathResult r = path_forward<kStack, STATS, true>(a.S, xa, a.L, &tape, st, &err, &stats);
+      rays += r.rays;
+      pix = r.pix;
+      f = r.f;
+      if (a.plen) a.plen[j] = (uint8_t)r.nseg;
+      p = lum(f) + a.eps;
+      kill_clock(a.rb, u1, u2, p, a.h, a.k0, &killed, &wt);
+      if (!killed) path_adjoint(a.S, xa, a.L, p, LocalTape<kMaxPathLen>{&tape}, r.nseg, GSoA{a.score, a.N, j});
     } else {
       f = evaluate<false, STATS>(a.S, a.M, a.target, a.L, a.eps, xa, &pix, &p, false, GNone{}, st, &err, &stats,
                                  &rays);
+      if (!a.estimate_only) kill_clock(a.rb, u1, u2, p, a.h, a.k0, &killed, &wt);
     }
     if (a.estimate_only) {
       pval = (double)p;
     } else {
-      bool killed;
-      float wt;
-      if (a.rb) {
-        killed = (double)u2 * ((double)a.h * p + a.k0) < a.k0;
-        wt = (float)((double)p / ((double)a.h * p + a.k0));
-      } else {
-        const float t1 = -logf(1.0f - u1) / a.h;
-        const float t2 = -logf(1.0f - u2) * p / (float)a.k0;
-        killed = !(t1 < t2);
-        wt = killed ? t2 : t1;
-      }
       if (DRIFT == kDriftAdjoint && a.target == 1 && !killed) {
         mixture_eval(a.M, xa, a.eps, true, GSoA{a.score, a.N, j});
       }
@@ -188,31 +138,42 @@ __global__ void __launch_bounds__(kStepThreads) step_kernel(StepArgs a) {
       if (!(isfinite(p) && isfinite(f.x) && isfinite(f.y) && isfinite(f.z))) err |= kErrNonFinite;
     }
   }
-  // block reductions
-  __shared__ unsigned long long sk[kStepThreads / 32], sr[kStepThreads / 32], sn[kStepThreads / 32],
-      stt[kStepThreads / 32];
-  __shared__ double sp[kStepThreads / 32];
-  __shared__ uint32_t serr;
-  if (threadIdx.x == 0) serr = 0;
+  // counters: warp sums, then one integer atomic per warp (no block barrier,
+  // so warps that finish early do not wait for the block's slowest warp)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned long long wk = warp_sum_u64(kill), wr = warp_sum_u64(rays);
-  const unsigned long long wn = STATS ? warp_sum_u64(stats.nodes) : 0ull, wt = STATS ? warp_sum_u64(stats.tris) : 0ull;
-  const double wp = warp_sum_f64(pval);
-  __syncthreads();
-  if (err) atomicOr(&serr, err);
-  if (lane == 0) { sk[warp] = wk; sr[warp] = wr; sp[warp] = wp; sn[warp] = wn; stt[warp] = wt; }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned long long K = 0, R = 0, Nn = 0, Tt = 0;
-    double P = 0.0;
-    for (int w = 0; w < kStepThreads / 32; ++w) { K += sk[w]; R += sr[w]; P += sp[w]; Nn += sn[w]; Tt += stt[w]; }
-    if (K && a.tour_count) atomicAdd(a.tour_count, K);
-    if (R && a.rays) atomicAdd(a.rays, R);
-    if (STATS && a.node_visits) atomicAdd(a.node_visits, Nn);
-    if (STATS && a.tri_tests) atomicAdd(a.tri_tests, Tt);
-    if (a.p_partial) a.p_partial[blockIdx.x] = P;
-    if (serr) atomicOr(a.err, serr);
+  if (err) atomicOr(a.err, err);
+  if (lane == 0) {
+    if (wk && a.tour_count) atomicAdd(a.tour_count, wk);
+    if (wr && a.rays) atomicAdd(a.rays, wr);
   }
+  if (STATS) {
+    const unsigned long long wn = warp_sum_u64(stats.nodes), wt = warp_sum_u64(stats.tris);
+    if (lane == 0 && a.node_visits) atomicAdd(a.node_visits, wn);
+    if (lane == 0 && a.tri_tests) atomicAdd(a.tri_tests, wt);
+  }
+  if (a.p_partial) {
+    // init only: FP64 sum of p in a fixed order (deterministic p_lambda)
+    __shared__ double sp[kStepThreads / 32];
+    const double wp = warp_sum_f64(pval);
+    if (lane == 0) sp[warp] = wp;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double P = 0.0;
+      for (int w = 0; w < kStepThreads / 32; ++w) P += sp[w];
+      a.p_partial[blockIdx.x] = P;
+    }
+  }
+}
+
+// Work order for the next step: key = (killed last step, previous path
+// length), so that warps get chains of similar cost; pairs (key, chain).
+__global__ void order_keys_kernel(const uint8_t* __restrict__ killed, const uint8_t* __restrict__ plen,
+                                  unsigned long long N, uint2* __restrict__ keys) {
+  const unsigned long long j = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= N) return;
+  const uint32_t k = ((uint32_t)killed[j] << 5) | min((uint32_t)plen[j], 31u);
+  keys[j] = make_uint2(k, (uint32_t)j);
 }
 
 // Central finite differences of log p for every (coordinate, surviving
@@ -369,6 +330,12 @@ void launch_step_t(const StepArgs& a, cudaStream_t s) {
 
 int step_block_size() { return kStepThreads; }
 size_t step_smem_bytes() { return (size_t)kStack * kStepThreads * sizeof(int); }
+
+void launch_order_keys(const uint8_t* killed, const uint8_t* plen, unsigned long long N, uint2* keys,
+                       cudaStream_t s) {
+  if (N == 0) return;
+  order_keys_kernel<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(killed, plen, N, keys);
+}
 
 void launch_step(const StepArgs& a, bool stats, cudaStream_t s) {
   if (a.N == 0) return;

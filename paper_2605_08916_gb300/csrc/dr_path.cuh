@@ -401,146 +401,221 @@ DR_D LightSample light_sample(const DevScene& S, int k, float ul, float ul2, flo
   return ls;
 }
 
-// Forward path evaluation.  XA: functor x(i) -> float.  With TAPE the
-// per-segment record for the adjoint is written.
+// Tape accessors: a per-thread array, or a [segment][3][N] float4 array in
+// global memory (wavefront execution), or nothing.
+template <int LMAX>
+struct LocalTape {
+  Tape<LMAX>* t;
+  DR_D void put(int s, float4 a, float4 b, float4 c) const { t->a[s] = a; t->b[s] = b; t->c[s] = c; }
+  DR_D void set_flags(int s, int f) const { t->c[s].w = __int_as_float(f); }
+  DR_D void or_flags(int s, int f) const { t->c[s].w = __int_as_float(__float_as_int(t->c[s].w) | f); }
+  DR_D void get(int s, float4& a, float4& b, float4& c) const { a = t->a[s]; b = t->b[s]; c = t->c[s]; }
+};
+
+struct GlobalTape {
+  float4* base;
+  unsigned long long N, j;
+  DR_D float4* at(int s, int k) const { return base + ((size_t)s * 3 + k) * N + j; }
+  DR_D void put(int s, float4 a, float4 b, float4 c) const { *at(s, 0) = a; *at(s, 1) = b; *at(s, 2) = c; }
+  DR_D void set_flags(int s, int f) const { at(s, 2)->w = __int_as_float(f); }
+  DR_D void or_flags(int s, int f) const { at(s, 2)->w = __int_as_float(__float_as_int(at(s, 2)->w) | f); }
+  DR_D void get(int s, float4& a, float4& b, float4& c) const { a = *at(s, 0); b = *at(s, 1); c = *at(s, 2); }
+};
+
+struct NoTape {
+  DR_D void put(int, float4, float4, float4) const {}
+  DR_D void set_flags(int, int) const {}
+  DR_D void or_flags(int, int) const {}
+};
+
+// State of one path between segments.
+struct PathState {
+  float3 o, d, beta, f;
+  float ppdf;
+  int prev_tri, prev_delta, nseg;
+};
+
+// Next-event estimation request of one vertex: the shadow ray and the
+// contribution that is added to f if the ray is unoccluded.
+struct NeeReq {
+  float3 o, wi, contrib;
+  float tmax;
+  int ex0, ex1, seg;
+  bool valid;
+};
+
+// Camera ray from the film pair; returns the pixel.
+template <class XA>
+DR_D int path_begin(const DevScene& S, const XA& xa, PathState& ps) {
+  const float WH = (float)S.W * (float)S.H;
+  ps.beta = f3(WH, WH, WH);
+  ps.f = f3(0.f, 0.f, 0.f);
+  const float x0 = xa(0), x1 = xa(1);
+  float3 raw;
+  ps.d = camera_dir(S.cam, x0, x1, &raw);
+  ps.o = S.cam.eye;
+  ps.prev_tri = -1;
+  ps.prev_delta = 1;
+  ps.ppdf = 0.0f;
+  ps.nseg = 0;
+  return pixel_of(x0, x1, S.W, S.H);
+}
+
+// Processes the closest hit `tri` of segment `seg` (1-based): records the
+// tape entry, adds the hit's emission (MIS-weighted after a non-delta
+// vertex), prepares the NEE request of the vertex and samples the next
+// direction.  Returns whether the path continues (ps then holds the next
+// ray).  The NEE contribution is added by the caller once the shadow ray
+// is found unoccluded, before the next vertex.
+template <class XA, class TP>
+DR_D bool path_vertex(const DevScene& S, const XA& xa, int L, int seg, int tri, PathState& ps, const TP& tape,
+                      NeeReq& nee) {
+  nee.valid = false;
+  const Surf sf = load_surf(S, tri);
+  // grazing hits (|cos| < 1e-6) end the path: the differentiable hit
+  // distance (v0 - o).N / d.N is ill-conditioned there
+  if (!grazing_ok(ps.d, sf.ng)) return false;
+  ps.nseg = seg;
+  int flags = ps.prev_delta ? kFPrevDelta : 0;
+  tape.put(seg - 1, make_float4(ps.o.x, ps.o.y, ps.o.z, ps.ppdf), make_float4(ps.d.x, ps.d.y, ps.d.z, __int_as_float(tri)),
+           make_float4(ps.beta.x, ps.beta.y, ps.beta.z, __int_as_float(flags)));
+  const MatP m = load_mat(S.mats, sf.mat);
+  const float t = dot(sf.v0 - ps.o, sf.N) / dot(ps.d, sf.N);
+  const float3 P = ps.o + ps.d * t;
+  if (m.emissive) {
+    const float cl = -dot(sf.ng, ps.d);
+    if (cl > 0.0f) {
+      float w = 1.0f;
+      if (!ps.prev_delta) {
+        const float pl = sf.sel / sf.area * t * t / cl;
+        w = ps.ppdf / (ps.ppdf + pl);
+      }
+      ps.f += ps.beta * m.emit * w;
+    }
+  }
+  if (m.type == kEmitter || seg == L) return false;
+  const float3 wo = -ps.d;
+  float3 nraw;
+  float3 ns = shading_normal(S, tri, sf, P, &nraw);
+  const int b = 2 + 4 * (seg - 1);
+  if (m.type == kDielectric) {
+    const bool entering = dot(sf.ng, wo) > 0.0f;
+    const float3 nn = entering ? ns : -ns;
+    const float c = dot(nn, wo);
+    if (!(c > 0.0f)) return false;
+    const float eta = entering ? m.ior : 1.0f / m.ior;
+    const float s2 = (1.0f - c * c) / (eta * eta);
+    float F = 1.0f, ct = 0.0f;
+    if (s2 < 1.0f) {
+      ct = sqrtf(1.0f - s2);
+      F = fresnel_dielectric(c, ct, eta);
+    }
+    float3 wi;
+    float wgt;
+    int lobe;
+    if (xa(b) < F) {
+      wi = nn * (2.0f * c) - wo;
+      wgt = 1.0f;
+      lobe = 2;
+    } else {
+      wi = wo * (-1.0f / eta) + nn * (c / eta - ct);
+      wgt = 1.0f / (eta * eta);
+      lobe = 3;
+    }
+    ps.beta = ps.beta * wgt;
+    flags |= kFScatter | (lobe << kFLobeShift);
+    tape.set_flags(seg - 1, flags);
+    ps.prev_delta = 1;
+    ps.ppdf = 0.0f;
+    ps.o = P;
+    ps.d = wi;
+    ps.prev_tri = tri;
+    return true;
+  }
+  float3 ngf = sf.ng;
+  if (dot(ngf, wo) < 0.0f) {
+    ngf = -ngf;
+    ns = -ns;
+  }
+  if (!(dot(ns, wo) > 0.0f)) return false;
+  if (S.n_lights > 0) {
+    float lo, pk;
+    const int k = pick_light(S, xa(b + 2), &lo, &pk);
+    flags |= k << kFLightShift;
+    const LightSample ls = light_sample(S, k, xa(b + 2), xa(b + 3), lo, pk);
+    const float3 wv = ls.y - P;
+    const float dist2 = dot(wv, wv);
+    const float dist = sqrtf(dist2);
+    const float3 wi = wv * (1.0f / dist);
+    const float ci = dot(ns, wi);
+    const float cl = -dot(ls.nl, wi);
+    if (ci > 0.0f && cl > 0.0f && dot(ngf, wi) > 0.0f) {
+      float pb;
+      const float3 fs = bsdf_eval(m, ns, wo, wi, &pb);
+      const float pl = ls.sel / ls.area * dist2 / cl;
+      const float g = ci / (pl + pb);
+      nee.valid = true;
+      nee.o = P;
+      nee.wi = wi;
+      nee.tmax = dist - S.tmin;
+      nee.ex0 = tri;
+      nee.ex1 = ls.tri;
+      nee.seg = seg;
+      nee.contrib = ps.beta * fs * ls.Le * g;
+    }
+  }
+  SampleRec s;
+  const bool ok = opaque_sample(m, ns, ngf, wo, xa(b), xa(b + 1), s);
+  if (ok) flags |= kFScatter | (s.lobe << kFLobeShift);
+  tape.set_flags(seg - 1, flags);
+  if (!ok) return false;
+  ps.beta = ps.beta * s.w;
+  ps.prev_delta = 0;
+  ps.ppdf = s.pdf;
+  ps.o = P;
+  ps.d = s.wi;
+  ps.prev_tri = tri;
+  return true;
+}
+
+// Forward path evaluation in one thread (traversal inline).  XA: functor
+// x(i) -> float.  With TAPE the per-segment record for the adjoint is
+// written to *tape.
 template <int STACK, bool STATS, bool TAPE, int LMAX, class XA>
 DR_D PathResult path_forward(const DevScene& S, const XA& xa, int L, Tape<LMAX>* tape, TraceStack<STACK> st,
                              uint32_t* err, TraceStats* stats) {
   PathResult res;
   res.rays = 0;
-  res.nseg = 0;
-  const float WH = (float)S.W * (float)S.H;
-  float3 beta = f3(WH, WH, WH);
-  float3 f = f3(0.f, 0.f, 0.f);
-  const float x0 = xa(0), x1 = xa(1);
-  res.pix = pixel_of(x0, x1, S.W, S.H);
-  float3 raw;
-  float3 d = camera_dir(S.cam, x0, x1, &raw);
-  float3 o = S.cam.eye;
-  int prev_tri = -1;
-  bool prev_delta = true;
-  float ppdf = 0.0f;
+  PathState ps;
+  res.pix = path_begin(S, xa, ps);
   for (int seg = 1; seg <= L; ++seg) {
-    const Ray r = make_ray(o, d);
     ++res.rays;
     float th;
-    const int tri = trace_closest<STACK, STATS>(S, r, prev_tri, &th, st, err, stats);
+    const int tri = trace_closest<STACK, STATS>(S, make_ray(ps.o, ps.d), ps.prev_tri, &th, st, err, stats);
     if (tri < 0) break;
-    const Surf sf = load_surf(S, tri);
-    // grazing hits (|cos| < 1e-6) end the path: the differentiable hit
-    // distance (v0 - o).N / d.N is ill-conditioned there
-    if (!grazing_ok(d, sf.ng)) break;
-    res.nseg = seg;
-    int flags = prev_delta ? kFPrevDelta : 0;
-    if (TAPE) {
-      tape->a[seg - 1] = make_float4(o.x, o.y, o.z, ppdf);
-      tape->b[seg - 1] = make_float4(d.x, d.y, d.z, __int_as_float(tri));
-      tape->c[seg - 1] = make_float4(beta.x, beta.y, beta.z, __int_as_float(flags));
-    }
-    const MatP m = load_mat(S.mats, sf.mat);
-    const float t = dot(sf.v0 - o, sf.N) / dot(d, sf.N);
-    const float3 P = o + d * t;
-    if (m.emissive) {
-      const float cl = -dot(sf.ng, d);
-      if (cl > 0.0f) {
-        float w = 1.0f;
-        if (!prev_delta) {
-          const float pl = sf.sel / sf.area * t * t / cl;
-          w = ppdf / (ppdf + pl);
-        }
-        f += beta * m.emit * w;
+    NeeReq nee;
+    bool cont;
+    if (TAPE) cont = path_vertex(S, xa, L, seg, tri, ps, LocalTape<LMAX>{tape}, nee);
+    else cont = path_vertex(S, xa, L, seg, tri, ps, NoTape{}, nee);
+    if (nee.valid) {
+      ++res.rays;
+      if (!trace_any<STACK, STATS>(S, make_ray(nee.o, nee.wi), nee.tmax, nee.ex0, nee.ex1, st, err, stats)) {
+        ps.f += nee.contrib;
+        if (TAPE) LocalTape<LMAX>{tape}.or_flags(seg - 1, kFNeeVis);
       }
     }
-    if (m.type == kEmitter || seg == L) break;
-    const float3 wo = -d;
-    float3 nraw;
-    float3 ns = shading_normal(S, tri, sf, P, &nraw);
-    const int b = 2 + 4 * (seg - 1);
-    if (m.type == kDielectric) {
-      const bool entering = dot(sf.ng, wo) > 0.0f;
-      const float3 nn = entering ? ns : -ns;
-      const float c = dot(nn, wo);
-      if (!(c > 0.0f)) break;
-      const float eta = entering ? m.ior : 1.0f / m.ior;
-      const float s2 = (1.0f - c * c) / (eta * eta);
-      float F = 1.0f, ct = 0.0f;
-      if (s2 < 1.0f) {
-        ct = sqrtf(1.0f - s2);
-        F = fresnel_dielectric(c, ct, eta);
-      }
-      float3 wi;
-      float wgt;
-      int lobe;
-      if (xa(b) < F) {
-        wi = nn * (2.0f * c) - wo;
-        wgt = 1.0f;
-        lobe = 2;
-      } else {
-        wi = wo * (-1.0f / eta) + nn * (c / eta - ct);
-        wgt = 1.0f / (eta * eta);
-        lobe = 3;
-      }
-      beta = beta * wgt;
-      flags |= kFScatter | (lobe << kFLobeShift);
-      if (TAPE) tape->c[seg - 1].w = __int_as_float(flags);
-      prev_delta = true;
-      ppdf = 0.0f;
-      o = P;
-      d = wi;
-      prev_tri = tri;
-      continue;
-    }
-    float3 ngf = sf.ng;
-    if (dot(ngf, wo) < 0.0f) {
-      ngf = -ngf;
-      ns = -ns;
-    }
-    if (!(dot(ns, wo) > 0.0f)) break;
-    if (S.n_lights > 0) {
-      float lo, pk;
-      const int k = pick_light(S, xa(b + 2), &lo, &pk);
-      flags |= k << kFLightShift;
-      const LightSample ls = light_sample(S, k, xa(b + 2), xa(b + 3), lo, pk);
-      const float3 wv = ls.y - P;
-      const float dist2 = dot(wv, wv);
-      const float dist = sqrtf(dist2);
-      const float3 wi = wv * (1.0f / dist);
-      const float ci = dot(ns, wi);
-      const float cl = -dot(ls.nl, wi);
-      if (ci > 0.0f && cl > 0.0f && dot(ngf, wi) > 0.0f) {
-        ++res.rays;
-        if (!trace_any<STACK, STATS>(S, make_ray(P, wi), dist - S.tmin, tri, ls.tri, st, err, stats)) {
-          flags |= kFNeeVis;
-          float pb;
-          const float3 fs = bsdf_eval(m, ns, wo, wi, &pb);
-          const float pl = ls.sel / ls.area * dist2 / cl;
-          const float g = ci / (pl + pb);
-          f += beta * fs * ls.Le * g;
-        }
-      }
-    }
-    SampleRec s;
-    const bool ok = opaque_sample(m, ns, ngf, wo, xa(b), xa(b + 1), s);
-    if (ok) flags |= kFScatter | (s.lobe << kFLobeShift);
-    if (TAPE) tape->c[seg - 1].w = __int_as_float(flags);
-    if (!ok) break;
-    beta = beta * s.w;
-    prev_delta = false;
-    ppdf = s.pdf;
-    o = P;
-    d = s.wi;
-    prev_tri = tri;
+    if (!cont) break;
   }
-  res.f = f;
+  res.f = ps.f;
+  res.nseg = ps.nseg;
   return res;
 }
 
 // Reverse-mode adjoint of p = lum(f) + eps with respect to x, using the tape
 // of a forward pass with the same x.  GW: functor gw(i, value) receiving
 // d log p / d x_i = (d p / d x_i) / p; every i < d is written exactly once.
-template <int LMAX, class XA, class GW>
-DR_D void path_adjoint(const DevScene& S, const XA& xa, int L, float p, const Tape<LMAX>& tape, int nseg,
-                       const GW& gw) {
+template <class TP, class XA, class GW>
+DR_D void path_adjoint(const DevScene& S, const XA& xa, int L, float p, const TP& tape, int nseg, const GW& gw) {
   const float inv_p = 1.0f / p;
   const float3 lw = lum_weights();
   float3 go = f3(0.f, 0.f, 0.f), gd = f3(0.f, 0.f, 0.f), gbeta = f3(0.f, 0.f, 0.f);
@@ -551,7 +626,8 @@ DR_D void path_adjoint(const DevScene& S, const XA& xa, int L, float p, const Ta
     gw(b, 0.f); gw(b + 1, 0.f); gw(b + 2, 0.f); gw(b + 3, 0.f);
   }
   for (int seg = nseg; seg >= 1; --seg) {
-    const float4 ta = tape.a[seg - 1], tb = tape.b[seg - 1], tc = tape.c[seg - 1];
+    float4 ta, tb, tc;
+    tape.get(seg - 1, ta, tb, tc);
     const float3 o = xyz(ta), d = xyz(tb), beta = xyz(tc);
     const float ppdf = ta.w;
     const int tri = __float_as_int(tb.w);

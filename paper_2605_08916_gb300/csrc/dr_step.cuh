@@ -1,0 +1,73 @@
+// Per-chain pieces of one Restore step shared by the fused (one thread per
+// chain-step) and the wavefront (one kernel per bounce) executions, so both
+// perform the same floating-point operations.
+#pragma once
+#include "dr_internal.h"
+#include "dr_path.cuh"
+
+namespace dr {
+
+// x[i] of chain j in the [d][N] state arrays
+struct XSoA {
+  const float* x;
+  unsigned long long N, j;
+  DR_D float operator()(int i) const { return x[(size_t)i * N + j]; }
+};
+
+// writes d log p / d x_i of chain j into the [d][N] score array
+struct GSoA {
+  float* g;
+  unsigned long long N, j;
+  DR_D void operator()(int i, float v) const { g[(size_t)i * N + j] = v; }
+};
+
+// Evolve (Alg. 2): regeneration x ~ U(T^d) for a killed (or initialising)
+// chain, else LocalDynamics (Alg. 4): for each coordinate pair
+// x += (stddev^2 / 2) s + gamma_tilde (s_2, -s_1) + stddev xi, then wrap.
+DR_D void evolve_x(const StepArgs& a, unsigned long long j, bool regen) {
+  const uint32_t cj = (uint32_t)j;
+  if (regen) {
+    for (int i = 0; i < a.d; i += 4) {
+      const U4 r = a.rng.draw(a.step, cj, (uint32_t)(i >> 2), kRegen);
+      const uint32_t w[4] = {r.a, r.b, r.c, r.d};
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (i + k < a.d) a.x[(size_t)(i + k) * a.N + j] = u01(w[k]);
+    }
+    return;
+  }
+  const float c2 = 0.5f * a.stddev * a.stddev;
+  for (int q = 0; q < a.d / 2; ++q) {
+    const U4 r = a.rng.draw(a.step, cj, (uint32_t)(q >> 1), kNormal);
+    const float ua = u01((q & 1) ? r.c : r.a), ub = u01((q & 1) ? r.d : r.b);
+    const float2 xi = box_muller(ua, ub);
+    const size_t i0 = (size_t)(2 * q) * a.N + j, i1 = (size_t)(2 * q + 1) * a.N + j;
+    const float s0 = a.score[i0], s1 = a.score[i1];
+    a.x[i0] = wrap01(a.x[i0] + c2 * s0 + a.gamma_tilde * s1 + a.stddev * xi.x);
+    a.x[i1] = wrap01(a.x[i1] + c2 * s1 - a.gamma_tilde * s0 + a.stddev * xi.y);
+  }
+}
+
+// The hold/kill clock (Accumulate of Alg. 1) with h = 1 / dt and k = k0 / p:
+// the exponential race, or its Rao-Blackwellised form (weight 1 / (h + k),
+// killed with probability k / (h + k)); the kill test and the RB weight are
+// evaluated in FP64.
+DR_D void kill_clock(int rb, float u1, float u2, float p, float h, double k0, bool* killed, float* wt) {
+  if (rb) {
+    *killed = (double)u2 * ((double)h * p + k0) < k0;
+    *wt = (float)((double)p / ((double)h * p + k0));
+  } else {
+    const float t1 = -logf(1.0f - u1) / h;
+    const float t2 = -logf(1.0f - u2) * p / (float)k0;
+    *killed = !(t1 < t2);
+    *wt = *killed ? t2 : t1;
+  }
+}
+
+DR_D unsigned long long warp_sum_u64(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+}  // namespace dr

@@ -1,0 +1,281 @@
+// Wavefront execution of one Restore step with the adjoint drift: instead
+// of one thread tracing a whole path (plus NEE and the reverse sweep), each
+// bounce is a separate pass over a compacted queue of the paths still alive:
+//
+//   wf_begin      Evolve (regenerate / LocalDynamics) and the camera ray
+//   per bounce k  wf_trace   closest hit of every queued ray
+//                 wf_shade   path_vertex: tape entry, emission, NEE request,
+//                            BSDF sample; survivors go to the next queue,
+//                            NEE requests to the shadow queue
+//                 wf_shadow  any-hit test of each NEE ray, contribution add
+//   wf_finish     p = lum(f) + eps, hold/kill clock, splat record; chains
+//                 that survive go to the adjoint queue
+//   wf_adjoint    reverse sweep over the tape kept in HBM
+//
+// Queues are compacted with one atomic per warp (ballot + popcount), so
+// warps never carry finished paths; the traversal passes are small kernels
+// that run at full occupancy.  Every path accumulates its contributions in
+// the same order as the fused kernel (emission of hit k, NEE of vertex k,
+// emission of hit k + 1, ...), so both executions give identical results.
+#include "dr_step.cuh"
+
+namespace dr {
+
+namespace {
+
+constexpr int kWfThreads = 128;
+constexpr int kWfStack = 48;
+
+// 64-B path slot per chain: (o, ppdf), (d, prev tri), (beta, prev_delta |
+// nseg << 8), (f, pixel)
+DR_D void load_slot(const float4* __restrict__ slot, unsigned long long j, PathState& ps, int& pix) {
+  const float4 a = slot[4 * j + 0], b = slot[4 * j + 1], c = slot[4 * j + 2], d = slot[4 * j + 3];
+  ps.o = xyz(a);
+  ps.ppdf = a.w;
+  ps.d = xyz(b);
+  ps.prev_tri = __float_as_int(b.w);
+  ps.beta = xyz(c);
+  const int fl = __float_as_int(c.w);
+  ps.prev_delta = fl & 1;
+  ps.nseg = fl >> 8;
+  ps.f = xyz(d);
+  pix = __float_as_int(d.w);
+}
+
+DR_D void store_slot(float4* __restrict__ slot, unsigned long long j, const PathState& ps, int pix) {
+  slot[4 * j + 0] = make_float4(ps.o.x, ps.o.y, ps.o.z, ps.ppdf);
+  slot[4 * j + 1] = make_float4(ps.d.x, ps.d.y, ps.d.z, __int_as_float(ps.prev_tri));
+  slot[4 * j + 2] = make_float4(ps.beta.x, ps.beta.y, ps.beta.z, __int_as_float((ps.prev_delta & 1) | (ps.nseg << 8)));
+  slot[4 * j + 3] = make_float4(ps.f.x, ps.f.y, ps.f.z, __int_as_float(pix));
+}
+
+// Warp-aggregated queue append: lanes with `take` get consecutive slots.
+DR_D uint32_t warp_append(uint32_t* count, bool take) {
+  const uint32_t mask = __activemask();
+  const uint32_t want = __ballot_sync(mask, take);
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(mask) - 1;
+  uint32_t base = 0;
+  if (lane == leader && want) base = atomicAdd(count, (uint32_t)__popc(want));
+  base = __shfl_sync(mask, base, leader);
+  return base + __popc(want & ((1u << lane) - 1u));
+}
+
+DR_D void add_counts(unsigned long long* target, unsigned long long v) {
+  const unsigned long long w = warp_sum_u64(v);
+  if ((threadIdx.x & 31) == 0 && w && target) atomicAdd(target, w);
+}
+
+__global__ void __launch_bounds__(kWfThreads) wf_begin(StepArgs a, WfBuffers w) {
+  for (unsigned long long j = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; j < a.N;
+       j += (unsigned long long)gridDim.x * blockDim.x) {
+    evolve_x(a, j, a.killed[j] != 0);
+    PathState ps;
+    const int pix = path_begin(a.S, XSoA{a.x, a.N, j}, ps);
+    store_slot(w.slot, j, ps, pix);
+    w.hit[j] = -1;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) w.counts[1] = (uint32_t)a.N;  // bounce 1: every chain
+}
+
+template <bool STATS>
+__global__ void __launch_bounds__(kWfThreads) wf_trace(StepArgs a, WfBuffers w, int k) {
+  extern __shared__ int smem[];
+  TraceStack<kWfStack> st{smem + threadIdx.x, (int)blockDim.x};
+  const uint32_t n = w.counts[k];
+  const uint32_t* q = k == 1 ? nullptr : w.queue[k & 1];
+  uint32_t err = 0;
+  TraceStats stats{0u, 0u};
+  unsigned long long rays = 0;
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    const unsigned long long j = q ? q[t] : t;
+    const float4 o = w.slot[4 * j + 0], d = w.slot[4 * j + 1];
+    float th;
+    w.hit[j] = trace_closest<kWfStack, STATS>(a.S, make_ray(xyz(o), xyz(d)), __float_as_int(d.w), &th, st, &err,
+                                              &stats);
+    ++rays;
+  }
+  add_counts(a.rays, rays);
+  if (STATS) {
+    add_counts(a.node_visits, stats.nodes);
+    add_counts(a.tri_tests, stats.tris);
+  }
+  if (err) atomicOr(a.err, err);
+}
+
+__global__ void __launch_bounds__(kWfThreads) wf_shade(StepArgs a, WfBuffers w, int k) {
+  const uint32_t n = w.counts[k];
+  const uint32_t* q = k == 1 ? nullptr : w.queue[k & 1];
+  uint32_t* qn = w.queue[(k + 1) & 1];
+  const uint32_t n_iter = (n + gridDim.x * blockDim.x - 1) / (gridDim.x * blockDim.x);
+  // every lane runs the same number of iterations so the queue appends see
+  // whole warps
+  for (uint32_t it = 0; it < n_iter; ++it) {
+    const uint32_t t = it * gridDim.x * blockDim.x + blockIdx.x * blockDim.x + threadIdx.x;
+    bool cont = false;
+    NeeReq nee;
+    nee.valid = false;
+    unsigned long long j = 0;
+    if (t < n) {
+      j = q ? q[t] : t;
+      const int tri = w.hit[j];
+      if (tri >= 0) {
+        PathState ps;
+        int pix;
+        load_slot(w.slot, j, ps, pix);
+        cont = path_vertex(a.S, XSoA{a.x, a.N, j}, a.L, k, tri, ps, GlobalTape{w.tape, a.N, j}, nee);
+        store_slot(w.slot, j, ps, pix);
+      }
+    }
+    const uint32_t si = warp_append(&w.counts[kWfShadowCount0 + k], nee.valid);
+    if (nee.valid) {
+      ShadowRec r;
+      r.o_tmax = make_float4(nee.o.x, nee.o.y, nee.o.z, nee.tmax);
+      r.wi_chain = make_float4(nee.wi.x, nee.wi.y, nee.wi.z, __int_as_float((int)j));
+      r.contrib_ex = make_float4(nee.contrib.x, nee.contrib.y, nee.contrib.z, __int_as_float(nee.ex0));
+      r.ex1 = nee.ex1;
+      w.shadow[si] = r;
+    }
+    const bool next = cont && k < a.L;
+    const uint32_t ni = warp_append(&w.counts[k + 1], next);
+    if (next) {
+      qn[ni] = (uint32_t)j;
+      w.hit[j] = -1;
+    }
+  }
+}
+
+template <bool STATS>
+__global__ void __launch_bounds__(kWfThreads) wf_shadow(StepArgs a, WfBuffers w, int k) {
+  extern __shared__ int smem[];
+  TraceStack<kWfStack> st{smem + threadIdx.x, (int)blockDim.x};
+  const uint32_t n = w.counts[kWfShadowCount0 + k];
+  uint32_t err = 0;
+  TraceStats stats{0u, 0u};
+  unsigned long long rays = 0;
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    const ShadowRec r = w.shadow[t];
+    const unsigned long long j = (unsigned long long)__float_as_int(r.wi_chain.w);
+    ++rays;
+    if (!trace_any<kWfStack, STATS>(a.S, make_ray(xyz(r.o_tmax), xyz(r.wi_chain)), r.o_tmax.w,
+                                    __float_as_int(r.contrib_ex.w), r.ex1, st, &err, &stats)) {
+      float4 f = w.slot[4 * j + 3];
+      f.x += r.contrib_ex.x;
+      f.y += r.contrib_ex.y;
+      f.z += r.contrib_ex.z;
+      w.slot[4 * j + 3] = f;
+      GlobalTape{w.tape, a.N, j}.or_flags(k - 1, kFNeeVis);
+    }
+  }
+  add_counts(a.rays, rays);
+  if (STATS) {
+    add_counts(a.node_visits, stats.nodes);
+    add_counts(a.tri_tests, stats.tris);
+  }
+  if (err) atomicOr(a.err, err);
+}
+
+__global__ void __launch_bounds__(kWfThreads) wf_finish(StepArgs a, WfBuffers w) {
+  const unsigned long long n_iter = (a.N + (unsigned long long)gridDim.x * blockDim.x - 1) /
+                                    ((unsigned long long)gridDim.x * blockDim.x);
+  uint32_t err = 0;
+  unsigned long long kills = 0;
+  for (unsigned long long it = 0; it < n_iter; ++it) {
+    const unsigned long long j = it * gridDim.x * blockDim.x + (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    bool survive = false;
+    if (j < a.N) {
+      PathState ps;
+      int pix;
+      load_slot(w.slot, j, ps, pix);
+      const float3 f = ps.f;
+      const float p = lum(f) + a.eps;
+      const U4 rc = a.rng.draw(a.step, (uint32_t)j, 0u, kClock);
+      bool killed;
+      float wt;
+      kill_clock(a.rb, u01(rc.a), u01(rc.b), p, a.h, a.k0, &killed, &wt);
+      a.killed[j] = killed ? 1 : 0;
+      a.logp[j] = logf(p);
+      if (a.plen) a.plen[j] = (uint8_t)ps.nseg;
+      kills += killed ? 1ull : 0ull;
+      if (a.rec) {
+        const float s = wt / p;
+        SplatRec rr;
+        rr.pix = (uint32_t)pix;
+        rr.r = f.x * s;
+        rr.g = f.y * s;
+        rr.b = f.z * s;
+        a.rec[j] = rr;
+      }
+      if (!(isfinite(p) && isfinite(f.x) && isfinite(f.y) && isfinite(f.z))) err |= kErrNonFinite;
+      survive = !killed;
+    }
+    const uint32_t ai = warp_append(&w.counts[kWfAdjointCount], survive);
+    if (survive) w.adj[ai] = (uint32_t)j;
+  }
+  add_counts(a.tour_count, kills);
+  if (err) atomicOr(a.err, err);
+}
+
+__global__ void __launch_bounds__(kWfThreads) wf_adjoint(StepArgs a, WfBuffers w) {
+  const uint32_t n = w.counts[kWfAdjointCount];
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    const unsigned long long j = w.adj[t];
+    PathState ps;
+    int pix;
+    load_slot(w.slot, j, ps, pix);
+    const float p = lum(ps.f) + a.eps;
+    path_adjoint(a.S, XSoA{a.x, a.N, j}, a.L, p, GlobalTape{w.tape, a.N, j}, ps.nseg, GSoA{a.score, a.N, j});
+  }
+}
+
+unsigned grid_for(unsigned long long n, int max_blocks) {
+  const unsigned long long b = (n + kWfThreads - 1) / kWfThreads;
+  return (unsigned)std::max<unsigned long long>(1, std::min<unsigned long long>(b, (unsigned long long)max_blocks));
+}
+
+}  // namespace
+
+size_t wf_bytes(unsigned long long N, int L) {
+  auto a = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  return a(N * 64) + a(N * 4) + 2 * a(N * 4) + a(N * sizeof(ShadowRec)) + a(N * 4) + a(kWfCounts * 4) +
+         a((size_t)L * 3 * N * 16);
+}
+
+WfBuffers wf_carve(void* base, unsigned long long N, int L) {
+  auto a = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  char* p = static_cast<char*>(base);
+  WfBuffers w;
+  w.slot = reinterpret_cast<float4*>(p); p += a(N * 64);
+  w.hit = reinterpret_cast<int*>(p); p += a(N * 4);
+  w.queue[0] = reinterpret_cast<uint32_t*>(p); p += a(N * 4);
+  w.queue[1] = reinterpret_cast<uint32_t*>(p); p += a(N * 4);
+  w.shadow = reinterpret_cast<ShadowRec*>(p); p += a(N * sizeof(ShadowRec));
+  w.adj = reinterpret_cast<uint32_t*>(p); p += a(N * 4);
+  w.counts = reinterpret_cast<uint32_t*>(p); p += a(kWfCounts * 4);
+  w.tape = reinterpret_cast<float4*>(p);
+  return w;
+}
+
+int launch_wavefront_step(const StepArgs& a, const WfBuffers& w, bool stats, int n_sm, cudaStream_t s) {
+  if (a.N == 0) return 0;
+  const int max_blocks = n_sm * 16;
+  const unsigned g = grid_for(a.N, max_blocks);
+  const size_t smem = (size_t)kWfStack * kWfThreads * sizeof(int);
+  int launches = 0;
+  cudaMemsetAsync(w.counts, 0, kWfCounts * sizeof(uint32_t), s);
+  wf_begin<<<g, kWfThreads, 0, s>>>(a, w);
+  launches += 2;
+  for (int k = 1; k <= a.L; ++k) {
+    if (stats) wf_trace<true><<<g, kWfThreads, smem, s>>>(a, w, k);
+    else wf_trace<false><<<g, kWfThreads, smem, s>>>(a, w, k);
+    wf_shade<<<g, kWfThreads, 0, s>>>(a, w, k);
+    if (stats) wf_shadow<true><<<g, kWfThreads, smem, s>>>(a, w, k);
+    else wf_shadow<false><<<g, kWfThreads, smem, s>>>(a, w, k);
+    launches += 3;
+  }
+  wf_finish<<<g, kWfThreads, 0, s>>>(a, w);
+  wf_adjoint<<<g, kWfThreads, 0, s>>>(a, w);
+  return launches + 2;
+}
+
+}  // namespace dr

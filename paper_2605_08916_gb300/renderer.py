@@ -69,6 +69,11 @@ class Renderer:
             pass
 
     # ---------------------------------------------------------------- inputs
+    def set_option(self, option, value):
+        """option: "wavefront" (0/1) or "work_order" (0/1)."""
+        code = {"work_order": _lib.DR_OPT_WORK_ORDER, "wavefront": _lib.DR_OPT_WAVEFRONT}[option]
+        call("dr_set_option", self.h, code, int(value))
+
     def set_bvh_builder(self, builder="ploc", radius=16):
         call("dr_set_bvh_builder", self.h, _lib.DR_BVH_PLOC if builder == "ploc" else _lib.DR_BVH_LBVH, int(radius))
 

@@ -219,6 +219,43 @@ def test_pt_reference_image_matches_oracle(torch, R, oracle):
     r.close()
 
 
+@pytest.mark.parametrize("which", ["glossy", "procedural"])
+def test_wavefront_matches_fused(torch, R, which):
+    """The bounce-by-bounce execution performs the same operations per path
+    as the fused kernel; the compiler may contract multiply-adds
+    differently in the two, so values agree to the last bit or two (chains
+    whose discrete choices flip on such a difference are counted)."""
+    if which == "glossy":
+        scene, L = S.cornell_box(1, 64, 64, glossy=True), 8
+    else:
+        scene, L = S.procedural_scene(1, 64, 36, target_tris=60000, n_objects=40), 12
+    out = []
+    for wf in (0, 1):
+        r = R.Renderer()
+        r.set_option("wavefront", wf)
+        r.upload_scene(scene)
+        r.init_chains(16384, 33, R.make_params(L=L, drift="adjoint", k0=0.0, steps_per_splat=4))
+        r.step(9)
+        st = r.readback_state()
+        acc = r.readback_accum()
+        c = r.counters()
+        r.close()
+        out.append((st, acc, c))
+    (a, acc_a, c_a), (b, acc_b, c_b) = out
+    same = (a["killed"] == b["killed"]) & (a["pix"] == b["pix"])
+    same &= torus_dist(a["x"], b["x"]).max(1) <= 1e-6
+    same &= np.abs(a["logp"] - b["logp"]) <= 1e-5 * np.maximum(1.0, np.abs(a["logp"]))
+    same &= np.linalg.norm(a["val"] - b["val"], axis=1) <= 1e-5 * np.linalg.norm(a["val"], axis=1) + 1e-30
+    print(f"{which}: bit-identical x {np.mean(np.all(a['x'] == b['x'], 1)):.4f}, agreeing chains {same.mean():.5f}")
+    assert same.mean() >= 0.999
+    alive = (a["killed"] == 0) & same
+    ga, gb = a["score"][alive], b["score"][alive]
+    rel = np.linalg.norm(ga - gb, axis=1) / np.maximum(np.linalg.norm(ga, axis=1), 1e-6)
+    assert np.mean(rel <= 1e-4) >= 0.999
+    assert np.allclose(acc_a, acc_b, rtol=1e-3, atol=1e-9 * np.abs(acc_a).max())
+    assert abs(c_a["tour_count"] - c_b["tour_count"]) <= 1e-3 * c_a["tour_count"] + 5
+
+
 def test_k0_estimate_matches_oracle(torch, R, oracle):
     scene = S.cornell_box(1, 64, 64)
     N = 4096
