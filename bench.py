@@ -190,6 +190,7 @@ def run_reference(args, wl, rank, world):
 def run_ours(args, wl, rank, world, local):
     import torch
     from paper_2605_08916_gb300 import renderer as R
+    from paper_2605_08916_gb300.replicas import merge_and_resolve, replica_seed
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -199,53 +200,69 @@ def run_ours(args, wl, rank, world, local):
     scene = wl["scene"]()
     log(f"scene {scene.name}: {scene.n_tris} triangles")
     N = args.chains or wl["chains"]
-    params = R.make_params(L=wl["L"], drift=wl["drift"], rb=True, k0=0.0, steps_per_splat=wl["spp"])
-    from paper_2605_08916_gb300.replicas import replica_seed
+    F = wl["spp"]                                   # steps per frame (one graph replay)
+    params = R.make_params(L=wl["L"], drift=wl["drift"], rb=True, k0=0.0, steps_per_splat=F)
     seed = replica_seed(SEED, rank)
-    stream = torch.cuda.current_stream(dev)
+    stream = torch.cuda.Stream(device=dev)          # graph capture needs a created stream
     r = R.Renderer(local, stream)
     r.set_option("work_order", args.work_order)
     r.set_option("wavefront", args.wavefront)
     r.upload_scene(scene)
     r.init_chains(N, seed, params)
-    torch.cuda.synchronize()
+    stream.synchronize()
     log(f"uploaded + init {N} chains; bvh {r.bvh_info()}")
-    # traversal statistics pass (separate kernel instantiation, untimed)
+    # traversal statistics (separate kernel instantiation, untimed)
     r.set_stats(True)
     r.step(2)
     ts = r.traversal_stats()
     r.set_stats(False)
-    log(f"stats pass: {ts}")
     chain_steps_stats = 2 * N
-    node_b, tri_b = 64, 48
     d = 2 + 4 * (wl["L"] - 1)
-    state_b = 4 * d * 4 + 1 + 1 + 4 + 16   # x and score read+write, killed r+w, logp, record
-    bytes_per_cs = (ts["node_visits"] * node_b + ts["tri_tests"] * tri_b) / chain_steps_stats + state_b
-    for _ in range(args.warmup):
-        r.step(1)
-    torch.cuda.synchronize()
+    trav_bytes = (ts["node_visits"] * 64 + ts["tri_tests"] * 48) / chain_steps_stats
+    state_bytes = 4 * d * 4 + 1 + 1 + 4 + 16   # x and score read+write, killed r+w, logp, record
+    log(f"stats pass: {ts}")
+    # per-phase device time (events around each pass; untimed) for the roofline
+    r.set_option("profile", 1)
+    r.profile()
+    prof_steps = 4
+    r.step(prof_steps)
+    prof = r.profile()
+    r.set_option("profile", 0)
+    wavefront = prof["trace"][1] > 0
+    if wavefront:
+        k_name = "wf_trace + wf_shadow (BVH traversal passes)"
+        k_ms = (prof["trace"][0] + prof["shadow"][0]) / prof_steps
+        k_bytes = trav_bytes
+    else:
+        k_name = "step_kernel (fused Restore step)"
+        k_ms = (prof["fused_step"][0] + prof["fd_score"][0]) / prof_steps
+        k_bytes = trav_bytes + state_bytes
+    log(f"profile per step: " + ", ".join(f"{k} {v[0] / prof_steps:.3f} ms" for k, v in prof.items() if v[1]))
+    # warm-up frames (also captures the frame graph)
+    n_frames = max(1, (args.steps + F - 1) // F)
+    steps = n_frames * F
+    for _ in range(max(1, (args.warmup + F - 1) // F)):
+        r.frame(F)
+    stream.synchronize()
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
     c0 = r.counters()
     l0 = r.launch_count()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps + 1)]
-    step_launches = []
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_frames + 1)]
+    img = torch.empty((scene.height, scene.width, 3), dtype=torch.float32, device=dev)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
-        for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            for k in range(n_frames):
+                flush.zero_()
+                ev[k][0].record(stream)
+                r.frame(F)
+                ev[k][1].record(stream)
             flush.zero_()
-            la = r.launch_count()
-            ev[k][0].record(stream)
-            r.step(1)
-            ev[k][1].record(stream)
-            step_launches.append(r.launch_count() - la)
-        flush.zero_()
-        img = torch.empty((scene.height, scene.width, 3), dtype=torch.float32, device=dev)
-        ev[-1][0].record(stream)
-        r.splat()
-        r.resolve(img)
-        ev[-1][1].record(stream)
+            ev[-1][0].record(stream)
+            r.resolve(img)
+            ev[-1][1].record(stream)
         torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
@@ -260,36 +277,33 @@ def run_ours(args, wl, rank, world, local):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         t_max = float(t.item())
         # the method's one exchange: merge the FP64 images and tour counts
-        from paper_2605_08916_gb300.replicas import merge_and_resolve
         merge_and_resolve(torch.from_numpy(r.readback_accum()).to(dev), c1["tour_count"], c1["k0"])
-    value = N * args.steps * world / (t_max / 1e3)
+    value = N * steps * world / (t_max / 1e3)
     rays_s = rays * world / (t_max / 1e3)
-    pure = [t for t, nl in zip(times[:-1], step_launches) if nl == 1]
-    k_ms = statistics.mean(pure) if pure else statistics.mean(times[:-1])
     peak, peak_kind = measured_peaks()
-    achieved = bytes_per_cs * N / (k_ms / 1e3) / 1e9
+    achieved = k_bytes * N / (k_ms / 1e3) / 1e9
     clocks = clk.summary()
-
-    line = None
     if rank == 0:
-        log(f"timed {args.steps} steps: {total_ms:.1f} ms")
-        e2e = None if args.no_e2e else run_e2e(R, scene, wl, N, args.steps, local, stream)
-        log("e2e done")
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+        log(f"timed {steps} steps in {n_frames} frames: {total_ms:.1f} ms")
+        e2e = None if args.no_e2e else run_e2e(R, scene, wl, N, steps, local, stream)
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
+                "warmup": args.warmup, "ms_per_step": t_max / steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": args.workload, "scene": scene.name, "triangles": scene.n_tris,
                            "image": [scene.width, scene.height], "chains_per_gpu": N, "max_path_len": wl["L"],
-                           "pss_dim": d, "drift": wl["drift"], "rb_weight": True, "steps_per_splat": wl["spp"],
-                           "l2": "inputs > L2 (BVH + chain state) and a 512 MB L2 flush between timed steps",
+                           "pss_dim": d, "drift": wl["drift"], "rb_weight": True, "steps_per_frame": F,
+                           "execution": "wavefront" if wavefront else "fused",
+                           "frame": "CUDA graph of steps_per_frame steps + splat, replayed",
+                           "l2": "inputs > L2 (BVH + chain state) and a 512 MB L2 flush between timed frames",
                            "parallelism": f"replicas{world}"},
-                "rays_per_s": rays_s, "rays_per_chain_step": rays / max(1, N * args.steps),
+                "rays_per_s": rays_s, "rays_per_chain_step": rays / max(1, N * steps),
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                              "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
-                             "kernel": "step_kernel (fused Restore step)", "kernel_ms": k_ms,
-                             "algorithmic_bytes_per_chain_step": bytes_per_cs,
+                             "kernel": k_name, "kernel_ms_per_step": k_ms,
+                             "algorithmic_bytes_per_chain_step": k_bytes,
                              "node_visits_per_chain_step": ts["node_visits"] / chain_steps_stats,
                              "tri_tests_per_chain_step": ts["tri_tests"] / chain_steps_stats},
+                "phase_ms_per_step": {k: v[0] / prof_steps for k, v in prof.items() if v[1]},
                 "clocks": clocks, "gpu_launches": launches, "e2e": e2e}
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(wl, scene)
@@ -317,9 +331,12 @@ def run_e2e(R, scene, wl, N, steps, local, stream):
     r.upload_scene(scene)
     r.init_chains(N, SEED + 1, R.make_params(L=wl["L"], drift=wl["drift"], rb=True, k0=0.0,
                                             steps_per_splat=wl["spp"]))
-    r.step(steps)
+    F = wl["spp"]
+    for _ in range(steps // F):
+        r.frame(F)
     r.resolve(out)
-    host.copy_(out, non_blocking=True)
+    with torch.cuda.stream(stream):
+        host.copy_(out, non_blocking=True)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     r.close()

@@ -244,9 +244,32 @@ int dr_pt_render(dr_ctx* ctx, int32_t max_path_len, uint32_t spp, uint64_t seed,
  *                      (killed last step, previous path length) with one
  *                      stable radix pass before each step so that warps
  *                      trace paths of similar cost; 0 (default): chain order.
+ *   DR_OPT_PROFILE     1: record CUDA events around each pass of dr_step /
+ *                      dr_splat (not inside dr_frame graphs) and accumulate
+ *                      their durations per phase (see dr_get_profile).
  * Errors: INVALID_ARG (unknown option or value). */
-enum { DR_OPT_WORK_ORDER = 1, DR_OPT_WAVEFRONT = 2 };
+enum { DR_OPT_WORK_ORDER = 1, DR_OPT_WAVEFRONT = 2, DR_OPT_PROFILE = 3 };
 int dr_set_option(dr_ctx* ctx, int32_t option, int32_t value);
+
+/* Per-phase device time accumulated since the last call while DR_OPT_PROFILE
+ * is on (synchronises, then resets the totals).  HOST outputs ms[i] and
+ * counts[i] (launches timed; may be NULL) for i < n, phases in order:
+ * 0 wavefront begin (Evolve + camera rays), 1 closest-hit traversal,
+ * 2 shading / NEE / BSDF sampling, 3 shadow-ray traversal, 4 clock and
+ * records, 5 adjoint, 6 fused step kernel, 7 finite-difference score,
+ * 8 splat (sort + reduce), 9 work-order sort. */
+enum { DR_PHASES = 10 };
+int dr_get_profile(dr_ctx* ctx, double* ms, uint64_t* counts, int32_t n);
+
+/* One frame of the per-frame loop: n_steps Evolve steps (Alg. 2, as
+ * dr_step) followed by the splat of their records (as dr_splat), issued as
+ * one CUDA graph that is captured on the first call and replayed by later
+ * calls with the same configuration (recaptured automatically when the
+ * chains, scene, parameters or options change).  The step index is kept in
+ * device memory so every replay draws new Philox numbers.  Requires that
+ * the context was created on a created (non-default) stream.  Asynchronous.
+ * Errors: STATE (no chains; default stream), CUDA, OOM. */
+int dr_frame(dr_ctx* ctx, uint32_t n_steps);
 
 /* BVH construction used by later dr_scene_upload calls:
  * DR_BVH_PLOC (default; parallel locally-ordered clustering of the

@@ -28,8 +28,11 @@ EXPORTS = ["dr_version", "dr_last_error", "dr_create", "dr_destroy", "dr_scene_u
            "dr_get_counters", "dr_eval_logp", "dr_trace_closest", "dr_philox", "dr_splat_records",
            "dr_clear_image", "dr_state_save", "dr_state_load", "dr_set_stats", "dr_get_traversal_stats",
            "dr_bvh_info", "dr_get_launch_count", "dr_get_chain_shape", "dr_pt_render", "dr_set_bvh_builder",
-           "dr_splat_records_noalloc", "dr_set_option"]
-DR_OPT_WORK_ORDER, DR_OPT_WAVEFRONT = 1, 2
+           "dr_splat_records_noalloc", "dr_set_option", "dr_get_profile", "dr_frame"]
+DR_OPT_WORK_ORDER, DR_OPT_WAVEFRONT, DR_OPT_PROFILE = 1, 2, 3
+DR_PHASES = 10
+PHASE_NAMES = ["wf_begin", "trace", "shade", "shadow", "finish", "adjoint", "fused_step", "fd_score", "splat",
+               "work_order"]
 DR_NOALLOC_MAX_RECORDS = 65536
 DR_BVH_LBVH, DR_BVH_PLOC = 0, 1
 
@@ -93,6 +96,8 @@ def load(build_if_missing=True):
         "dr_set_bvh_builder": ([P, I32, I32], C.c_int),
         "dr_splat_records_noalloc": ([P, I64, I32, P, P], C.c_int),
         "dr_set_option": ([P, I32, I32], C.c_int),
+        "dr_get_profile": ([P, P, P, I32], C.c_int),
+        "dr_frame": ([P, U32], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)

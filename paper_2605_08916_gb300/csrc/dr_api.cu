@@ -78,7 +78,73 @@ struct dr_ctx {
   void* wf_mem = nullptr;
   size_t wf_cap = 0;
   int n_sm = 152;
+  // graph-captured frames (dr_frame)
+  uint32_t* step_dev = nullptr;  // device copy of the step index while replaying
+  bool capturing = false;
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<unsigned long long> graph_key;  // what the captured launches depend on
+  unsigned long long graph_launches = 0;
+  uint32_t step_host = 0;
+  // optional per-phase timing (DR_OPT_PROFILE)
+  bool profile = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> marks;
+  cudaEvent_t open_ev[kPhCount] = {};
+  double phase_ms[kPhCount] = {};
+  unsigned long long phase_n[kPhCount] = {};
 };
+
+namespace {
+
+cudaEvent_t pooled_event(dr_ctx* c) {
+  if (!c->ev_pool.empty()) {
+    cudaEvent_t e = c->ev_pool.back();
+    c->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+// Records an event at the start / end of a phase on the context's stream.
+void phase_mark(void* user, int phase, bool begin) {
+  dr_ctx* c = static_cast<dr_ctx*>(user);
+  if (!c->profile || c->capturing) return;
+  cudaEvent_t e = pooled_event(c);
+  if (!e) return;
+  cudaEventRecord(e, c->stream);
+  if (begin) {
+    c->open_ev[phase] = e;
+  } else if (c->open_ev[phase]) {
+    c->marks.push_back({phase, {c->open_ev[phase], e}});
+    c->open_ev[phase] = nullptr;
+  } else {
+    c->ev_pool.push_back(e);
+  }
+}
+
+// Folds finished event pairs into the per-phase totals (synchronises).
+void phase_collect(dr_ctx* c) {
+  if (c->marks.empty()) return;
+  cudaStreamSynchronize(c->stream);
+  for (auto& m : c->marks) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, m.second.first, m.second.second) == cudaSuccess) {
+      c->phase_ms[m.first] += ms;
+      c->phase_n[m.first] += 1;
+    }
+    c->ev_pool.push_back(m.second.first);
+    c->ev_pool.push_back(m.second.second);
+  }
+  cudaGetLastError();
+  c->marks.clear();
+}
+
+}  // namespace
 
 namespace {
 
@@ -194,9 +260,11 @@ int check_device_error(dr_ctx* c) {
 int flush(dr_ctx* c) {
   if (c->rec_count == 0) return DR_OK;
   const size_t n = (size_t)c->rec_count * c->N;
+  phase_mark(c, kPhSplat, true);
   SplatRec* sorted =
       sort_splat_records(c->rec, c->rec_alt, n, key_bits((long long)c->W * c->H), c->sort_scratch, c->stream);
   launch_segment_reduce(sorted, n, c->accum, (uint32_t)((size_t)c->W * c->H), c->err, c->stream);
+  phase_mark(c, kPhSplat, false);
   c->launches += 5 * ((key_bits((long long)c->W * c->H) + 7) / 8) + 1;
   c->rec_count = 0;
   return check_launch("splat");
@@ -250,47 +318,67 @@ int run_fd(dr_ctx* c) {
   return check_launch("fd_score");
 }
 
+bool use_wavefront(const dr_ctx* c) {
+  const bool adjoint_scene = c->prm.drift_mode == DR_DRIFT_ADJOINT && c->target == 0;
+  return adjoint_scene && (c->wavefront == 1 || (c->wavefront == -1 && c->N >= (1ull << 17)));
+}
+
+int ensure_wavefront_buffers(dr_ctx* c) {
+  const size_t need = wf_bytes(c->N, c->prm.max_path_len);
+  if (need <= c->wf_cap) return DR_OK;
+  if (c->wf_mem) cudaFree(c->wf_mem);
+  c->wf_mem = nullptr;
+  c->wf_cap = 0;
+  cudaError_t e = cudaMalloc(&c->wf_mem, need);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    c->wf_mem = nullptr;
+    return fail(DR_ERR_OOM, "wavefront buffers");
+  }
+  c->wf_cap = need;
+  return DR_OK;
+}
+
 // one chain step (init = Alg. 1, else Alg. 2); records into the next slot
 int one_step(dr_ctx* c, bool init) {
   if (!init && c->rec_count >= c->rec_cap) DR_TRY(flush(c));
   StepArgs a = step_args(c);
   a.init = init ? 1 : 0;
   a.step = c->step;
+  a.step_ptr = c->capturing ? c->step_dev : nullptr;
   a.rec = c->rec + (size_t)c->rec_count * c->N;
   a.p_partial = init ? c->p_partial : nullptr;
   a.plen = c->plen;
-  const bool adjoint_scene = c->prm.drift_mode == DR_DRIFT_ADJOINT && c->target == 0;
-  const bool use_wf = c->wavefront == 1 || (c->wavefront == -1 && c->N >= (1ull << 17));
-  if (!init && adjoint_scene && use_wf) {
-    const size_t need = wf_bytes(c->N, c->prm.max_path_len);
-    if (need > c->wf_cap) {
-      if (c->wf_mem) cudaFree(c->wf_mem);
-      c->wf_mem = nullptr;
-      c->wf_cap = 0;
-      cudaError_t e = cudaMalloc(&c->wf_mem, need);
-      if (e != cudaSuccess) {
-        cudaGetLastError();
-        c->wf_mem = nullptr;
-        return fail(DR_ERR_OOM, "wavefront buffers");
-      }
-      c->wf_cap = need;
-    }
+  const PhaseHook hook{phase_mark, c};
+  if (!init && use_wavefront(c)) {
+    DR_TRY(ensure_wavefront_buffers(c));
     const WfBuffers w = wf_carve(c->wf_mem, c->N, c->prm.max_path_len);
-    c->launches += launch_wavefront_step(a, w, c->stats, c->n_sm, c->stream);
+    c->launches += launch_wavefront_step(a, w, c->stats, c->n_sm, hook, c->stream);
     DR_TRY(check_launch("wavefront step"));
-    c->rec_count++;
-    return DR_OK;
+  } else {
+    if (!init && c->work_order && c->prm.drift_mode == DR_DRIFT_ADJOINT && c->target == 0) {
+      hook(kPhOrder, true);
+      launch_order_keys(c->killed, c->plen, c->N, c->order_a, c->stream);
+      a.order = sort_pairs(c->order_a, c->order_b, c->N, 6, c->sort_scratch, c->stream);
+      hook(kPhOrder, false);
+      c->launches += 6;
+    }
+    hook(kPhFused, true);
+    launch_step(a, c->stats, c->stream);
+    hook(kPhFused, false);
+    c->launches += 1;
+    DR_TRY(check_launch("restore_step"));
+    if (c->prm.drift_mode == DR_DRIFT_FD) {
+      hook(kPhFd, true);
+      DR_TRY(run_fd(c));
+      hook(kPhFd, false);
+    }
   }
-  if (!init && c->work_order && adjoint_scene) {
-    launch_order_keys(c->killed, c->plen, c->N, c->order_a, c->stream);
-    a.order = sort_pairs(c->order_a, c->order_b, c->N, 6, c->sort_scratch, c->stream);
-    c->launches += 6;
-  }
-  launch_step(a, c->stats, c->stream);
-  c->launches += 1;
-  DR_TRY(check_launch("restore_step"));
   c->rec_count++;
-  if (c->prm.drift_mode == DR_DRIFT_FD) DR_TRY(run_fd(c));
+  if (c->capturing) {
+    launch_advance_step(c->step_dev, c->stream);
+    c->launches += 1;
+  }
   return DR_OK;
 }
 
@@ -328,6 +416,7 @@ int dr_create(dr_ctx** out, int device, void* cuda_stream) {
   int r = dalloc(&c->counters, 4);
   if (r == DR_OK) r = dalloc(&c->err, 1);
   if (r == DR_OK) r = dalloc(&c->p_sum, 1);
+  if (r == DR_OK) r = dalloc(&c->step_dev, 1);
   if (r != DR_OK) {
     dr_destroy(c);
     return r;
@@ -349,6 +438,15 @@ int dr_destroy(dr_ctx* c) {
   if (c->wf_mem) cudaFree(c->wf_mem); dfree(&c->rec); dfree(&c->rec_alt);
   if (c->sort_scratch) cudaFree(c->sort_scratch);
   dfree(&c->accum); dfree(&c->counters); dfree(&c->p_partial); dfree(&c->p_sum); dfree(&c->err);
+  dfree(&c->step_dev);
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  for (auto& m : c->marks) {
+    cudaEventDestroy(m.second.first);
+    cudaEventDestroy(m.second.second);
+  }
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  for (cudaEvent_t e : c->open_ev)
+    if (e) cudaEventDestroy(e);
   delete c;
   return DR_OK;
 }
@@ -493,7 +591,14 @@ int dr_scene_upload(dr_ctx* c, const float* verts, int32_t nv, const int32_t* tr
   c->n_lights = (int)lt.size();
   c->tmin = (float)(1e-5 * ext);
   c->inited = false;
-  return DR_OK;
+  // the hierarchy must be a tree that the traversal stack can hold
+  int32_t depth = 0;
+  r = dr_bvh_info(c, nullptr, nullptr, &depth);
+  if (r == DR_OK && depth - 1 > kTraversalStack)
+    r = fail(DR_ERR_DEVICE_CHECK, "dr_scene_upload: BVH depth " + std::to_string(depth) +
+                                      " exceeds the traversal stack (" + std::to_string(kTraversalStack + 1) + ")");
+  if (r != DR_OK) c->target = -1;
+  return r;
 }
 
 int dr_target_mixture(dr_ctx* c, int32_t d, int32_t K, const float* w, const float* mu, const float* sig, float cval,
@@ -888,6 +993,99 @@ int dr_state_load(dr_ctx* c, const void* host_buf, size_t bytes) {
   return DR_OK;
 }
 
+namespace {
+
+// Everything a captured frame's launches depend on: buffers, sizes,
+// parameters and options.  A frame is recaptured when any of it changes.
+std::vector<unsigned long long> frame_key(const dr_ctx* c, uint32_t n_steps) {
+  auto P = [](const void* p) { return (unsigned long long)(uintptr_t)p; };
+  double k0 = c->k0;
+  unsigned long long k0b;
+  std::memcpy(&k0b, &k0, 8);
+  unsigned long long prm[6];
+  std::memset(prm, 0, sizeof(prm));
+  std::memcpy(prm, &c->prm, std::min(sizeof(prm), sizeof(c->prm)));
+  std::vector<unsigned long long> k = {n_steps, c->N, (unsigned long long)c->d, (unsigned long long)c->target,
+                                       P(c->x), P(c->score), P(c->killed), P(c->logp), P(c->plen), P(c->rec),
+                                       P(c->rec_alt), P(c->sort_scratch), P(c->accum), P(c->wf_mem), P(c->nodes),
+                                       P(c->tris), P(c->surf), P(c->mats), P(c->lights), P(c->nrm), P(c->mw),
+                                       c->seed, c->frame, k0b, c->rec_cap, (unsigned long long)c->wavefront,
+                                       (unsigned long long)c->work_order, (unsigned long long)c->stats,
+                                       (unsigned long long)c->nt, (unsigned long long)c->n_lights, P(c->stream)};
+  for (unsigned long long v : prm) k.push_back(v);
+  return k;
+}
+
+}  // namespace
+
+int dr_frame(dr_ctx* c, uint32_t n_steps) {
+  if (!c) return fail(DR_ERR_INVALID_ARG, "dr_frame: NULL ctx");
+  if (!c->inited) return fail(DR_ERR_STATE, "dr_frame: chains not initialised");
+  if (n_steps == 0) return DR_OK;
+  if (c->stream == nullptr || c->stream == cudaStreamLegacy || c->stream == cudaStreamPerThread)
+    return fail(DR_ERR_STATE, "dr_frame: needs a created (non-default) CUDA stream for graph capture");
+  DR_CUDA(cudaSetDevice(c->device));
+  DR_TRY(flush(c));  // a frame starts with an empty record buffer
+  if (use_wavefront(c)) DR_TRY(ensure_wavefront_buffers(c));
+  const std::vector<unsigned long long> key = frame_key(c, n_steps);
+  if (!c->gexec || key != c->graph_key) {
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+    const uint32_t saved_step = c->step;
+    const unsigned long long saved_launches = c->launches;
+    DR_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    c->capturing = true;
+    int r = DR_OK;
+    for (uint32_t i = 0; i < n_steps && r == DR_OK; ++i) {
+      c->step++;
+      r = one_step(c, false);
+    }
+    if (r == DR_OK) r = flush(c);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    c->capturing = false;
+    c->step = saved_step;
+    c->rec_count = 0;
+    c->graph_launches = c->launches - saved_launches;
+    c->launches = saved_launches;
+    if (r != DR_OK) {
+      if (g) cudaGraphDestroy(g);
+      return r;
+    }
+    if (e != cudaSuccess) return fail(DR_ERR_CUDA, std::string("dr_frame: capture failed: ") + cudaGetErrorString(e));
+    const cudaError_t ei = cudaGraphInstantiate(&c->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+      c->gexec = nullptr;
+      return fail(DR_ERR_CUDA, std::string("dr_frame: instantiate: ") + cudaGetErrorString(ei));
+    }
+    c->graph_key = key;
+  }
+  // the graph reads the step index from device memory and advances it
+  c->step_host = c->step + 1;
+  DR_CUDA(cudaMemcpyAsync(c->step_dev, &c->step_host, 4, cudaMemcpyHostToDevice, c->stream));
+  DR_CUDA(cudaGraphLaunch(c->gexec, c->stream));
+  c->step += n_steps;
+  c->launches += c->graph_launches;
+  c->rec_count = 0;
+  return DR_OK;
+}
+
+int dr_get_profile(dr_ctx* c, double* ms, uint64_t* counts, int32_t n) {
+  if (!c || !ms || n < 1) return fail(DR_ERR_INVALID_ARG, "dr_get_profile: bad argument");
+  DR_CUDA(cudaSetDevice(c->device));
+  phase_collect(c);
+  for (int i = 0; i < n; ++i) {
+    ms[i] = i < kPhCount ? c->phase_ms[i] : 0.0;
+    if (counts) counts[i] = i < kPhCount ? c->phase_n[i] : 0;
+  }
+  for (int i = 0; i < kPhCount; ++i) {
+    c->phase_ms[i] = 0.0;
+    c->phase_n[i] = 0;
+  }
+  return DR_OK;
+}
+
 int dr_set_stats(dr_ctx* c, int enable) {
   if (!c) return fail(DR_ERR_INVALID_ARG, "dr_set_stats: NULL ctx");
   DR_CUDA(cudaSetDevice(c->device));
@@ -934,6 +1132,10 @@ int dr_pt_render(dr_ctx* c, int32_t L, uint32_t spp, uint64_t seed, double* out_
 int dr_set_option(dr_ctx* c, int32_t option, int32_t value) {
   if (!c) return fail(DR_ERR_INVALID_ARG, "dr_set_option: NULL ctx");
   switch (option) {
+    case DR_OPT_PROFILE:
+      if (value != 0 && value != 1) return fail(DR_ERR_INVALID_ARG, "dr_set_option: profile is 0 or 1");
+      c->profile = value != 0;
+      return DR_OK;
     case DR_OPT_WAVEFRONT:
       if (value < -1 || value > 1) return fail(DR_ERR_INVALID_ARG, "dr_set_option: wavefront is -1, 0 or 1");
       c->wavefront = value;

@@ -14,6 +14,9 @@ constexpr float kPi = 3.14159265358979323846f;
 constexpr float kInvPi = 0.318309886183790671538f;
 constexpr float kLumR = 0.2126f, kLumG = 0.7152f, kLumB = 0.0722f;
 constexpr int kMaxPathLen = 16;               // L <= 16  ->  d <= 62
+// Entries of the per-thread traversal stack; a BVH deeper than this + 1 is
+// rejected at scene upload.
+constexpr int kTraversalStack = 40;
 constexpr int kMaxDim = 2 + 4 * (kMaxPathLen - 1);
 
 // device error word bits (read back by the host after each call)

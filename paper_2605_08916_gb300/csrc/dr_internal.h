@@ -71,6 +71,7 @@ struct StepArgs {
   unsigned long long N;
   int d, L;
   uint32_t step;
+  const uint32_t* step_ptr;  // non-null: read the step index from device memory (graph replay)
   Rng rng;
   float stddev, gamma_tilde, h, eps;
   double k0;
@@ -113,9 +114,24 @@ struct WfBuffers {
 };
 size_t wf_bytes(unsigned long long N, int L);
 WfBuffers wf_carve(void* base, unsigned long long N, int L);
+
+// Phases timed by the optional profiler (events recorded around launches).
+enum Phase { kPhBegin = 0, kPhTrace, kPhShade, kPhShadow, kPhFinish, kPhAdjoint, kPhFused, kPhFd, kPhSplat,
+             kPhOrder, kPhCount };
+struct PhaseHook {
+  void (*mark)(void* user, int phase, bool begin);
+  void* user;
+  void operator()(int phase, bool begin) const {
+    if (mark) mark(user, phase, begin);
+  }
+};
+
 // One adjoint-drift Restore step on a scene, bounce by bounce; returns the
 // number of kernels (and memsets) issued.
-int launch_wavefront_step(const StepArgs& a, const WfBuffers& w, bool stats, int n_sm, cudaStream_t s);
+int launch_wavefront_step(const StepArgs& a, const WfBuffers& w, bool stats, int n_sm, const PhaseHook& hook,
+                          cudaStream_t s);
+// step index += 1 on the device (graph replay)
+void launch_advance_step(uint32_t* step, cudaStream_t s);
 
 int step_block_size();
 size_t step_smem_bytes();

@@ -22,7 +22,7 @@ namespace dr {
 namespace {
 
 constexpr int kStepThreads = 128;
-constexpr int kStack = 48;
+constexpr int kStack = kTraversalStack;
 
 struct XPerturbed {
   const float* x;
@@ -91,12 +91,13 @@ __global__ void __launch_bounds__(kStepThreads) step_kernel(StepArgs a) {
   double pval = 0.0;
   if (active) {
     const uint32_t cj = (uint32_t)j;
-    evolve_x(a, j, a.init || a.killed[j]);
+    const uint32_t step = step_index(a);
+    evolve_x(a, step, j, a.init || a.killed[j]);
     const XSoA xa{a.x, a.N, j};
     int pix;
     float p;
     float3 f;
-    const U4 rc = a.rng.draw(a.step, cj, 0u, kClock);
+    const U4 rc = a.rng.draw(step, cj, 0u, kClock);
     const float u1 = u01(rc.a), u2 = u01(rc.b);
     bool killed = false;
     float wt = 0.0f;
@@ -330,6 +331,10 @@ void launch_step_t(const StepArgs& a, cudaStream_t s) {
 
 int step_block_size() { return kStepThreads; }
 size_t step_smem_bytes() { return (size_t)kStack * kStepThreads * sizeof(int); }
+
+__global__ void advance_step_kernel(uint32_t* step) { *step += 1u; }
+
+void launch_advance_step(uint32_t* step, cudaStream_t s) { advance_step_kernel<<<1, 1, 0, s>>>(step); }
 
 void launch_order_keys(const uint8_t* killed, const uint8_t* plen, unsigned long long N, uint2* keys,
                        cudaStream_t s) {

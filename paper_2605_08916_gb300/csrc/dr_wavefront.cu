@@ -14,9 +14,10 @@
 //
 // Queues are compacted with one atomic per warp (ballot + popcount), so
 // warps never carry finished paths; the traversal passes are small kernels
-// that run at full occupancy.  Every path accumulates its contributions in
-// the same order as the fused kernel (emission of hit k, NEE of vertex k,
-// emission of hit k + 1, ...), so both executions give identical results.
+// with few registers.  Every path accumulates its contributions in the same
+// order as the fused kernel (emission of hit k, NEE of vertex k, emission of
+// hit k + 1, ...); the two executions differ only where the compiler
+// contracts multiply-adds differently (last-bit differences).
 #include "dr_step.cuh"
 
 namespace dr {
@@ -24,7 +25,9 @@ namespace dr {
 namespace {
 
 constexpr int kWfThreads = 128;
-constexpr int kWfStack = 48;
+constexpr int kWfStack = kTraversalStack;
+// resident blocks per SM the traversal passes are compiled for (register cap)
+constexpr int kWfTraceMinBlocks = 10;
 
 // 64-B path slot per chain: (o, ppdf), (d, prev tri), (beta, prev_delta |
 // nseg << 8), (f, pixel)
@@ -69,7 +72,7 @@ DR_D void add_counts(unsigned long long* target, unsigned long long v) {
 __global__ void __launch_bounds__(kWfThreads) wf_begin(StepArgs a, WfBuffers w) {
   for (unsigned long long j = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; j < a.N;
        j += (unsigned long long)gridDim.x * blockDim.x) {
-    evolve_x(a, j, a.killed[j] != 0);
+    evolve_x(a, step_index(a), j, a.killed[j] != 0);
     PathState ps;
     const int pix = path_begin(a.S, XSoA{a.x, a.N, j}, ps);
     store_slot(w.slot, j, ps, pix);
@@ -79,7 +82,7 @@ __global__ void __launch_bounds__(kWfThreads) wf_begin(StepArgs a, WfBuffers w) 
 }
 
 template <bool STATS>
-__global__ void __launch_bounds__(kWfThreads) wf_trace(StepArgs a, WfBuffers w, int k) {
+__global__ void __launch_bounds__(kWfThreads, kWfTraceMinBlocks) wf_trace(StepArgs a, WfBuffers w, int k) {
   extern __shared__ int smem[];
   TraceStack<kWfStack> st{smem + threadIdx.x, (int)blockDim.x};
   const uint32_t n = w.counts[k];
@@ -146,7 +149,7 @@ __global__ void __launch_bounds__(kWfThreads) wf_shade(StepArgs a, WfBuffers w, 
 }
 
 template <bool STATS>
-__global__ void __launch_bounds__(kWfThreads) wf_shadow(StepArgs a, WfBuffers w, int k) {
+__global__ void __launch_bounds__(kWfThreads, kWfTraceMinBlocks) wf_shadow(StepArgs a, WfBuffers w, int k) {
   extern __shared__ int smem[];
   TraceStack<kWfStack> st{smem + threadIdx.x, (int)blockDim.x};
   const uint32_t n = w.counts[kWfShadowCount0 + k];
@@ -189,7 +192,7 @@ __global__ void __launch_bounds__(kWfThreads) wf_finish(StepArgs a, WfBuffers w)
       load_slot(w.slot, j, ps, pix);
       const float3 f = ps.f;
       const float p = lum(f) + a.eps;
-      const U4 rc = a.rng.draw(a.step, (uint32_t)j, 0u, kClock);
+      const U4 rc = a.rng.draw(step_index(a), (uint32_t)j, 0u, kClock);
       bool killed;
       float wt;
       kill_clock(a.rb, u01(rc.a), u01(rc.b), p, a.h, a.k0, &killed, &wt);
@@ -216,7 +219,7 @@ __global__ void __launch_bounds__(kWfThreads) wf_finish(StepArgs a, WfBuffers w)
   if (err) atomicOr(a.err, err);
 }
 
-__global__ void __launch_bounds__(kWfThreads) wf_adjoint(StepArgs a, WfBuffers w) {
+__global__ void __launch_bounds__(kWfThreads, 4) wf_adjoint(StepArgs a, WfBuffers w) {
   const uint32_t n = w.counts[kWfAdjointCount];
   for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
     const unsigned long long j = w.adj[t];
@@ -256,25 +259,38 @@ WfBuffers wf_carve(void* base, unsigned long long N, int L) {
   return w;
 }
 
-int launch_wavefront_step(const StepArgs& a, const WfBuffers& w, bool stats, int n_sm, cudaStream_t s) {
+int launch_wavefront_step(const StepArgs& a, const WfBuffers& w, bool stats, int n_sm, const PhaseHook& hook,
+                          cudaStream_t s) {
   if (a.N == 0) return 0;
   const int max_blocks = n_sm * 16;
   const unsigned g = grid_for(a.N, max_blocks);
   const size_t smem = (size_t)kWfStack * kWfThreads * sizeof(int);
   int launches = 0;
   cudaMemsetAsync(w.counts, 0, kWfCounts * sizeof(uint32_t), s);
+  hook(kPhBegin, true);
   wf_begin<<<g, kWfThreads, 0, s>>>(a, w);
+  hook(kPhBegin, false);
   launches += 2;
   for (int k = 1; k <= a.L; ++k) {
+    hook(kPhTrace, true);
     if (stats) wf_trace<true><<<g, kWfThreads, smem, s>>>(a, w, k);
     else wf_trace<false><<<g, kWfThreads, smem, s>>>(a, w, k);
+    hook(kPhTrace, false);
+    hook(kPhShade, true);
     wf_shade<<<g, kWfThreads, 0, s>>>(a, w, k);
+    hook(kPhShade, false);
+    hook(kPhShadow, true);
     if (stats) wf_shadow<true><<<g, kWfThreads, smem, s>>>(a, w, k);
     else wf_shadow<false><<<g, kWfThreads, smem, s>>>(a, w, k);
+    hook(kPhShadow, false);
     launches += 3;
   }
+  hook(kPhFinish, true);
   wf_finish<<<g, kWfThreads, 0, s>>>(a, w);
+  hook(kPhFinish, false);
+  hook(kPhAdjoint, true);
   wf_adjoint<<<g, kWfThreads, 0, s>>>(a, w);
+  hook(kPhAdjoint, false);
   return launches + 2;
 }
 

@@ -70,8 +70,9 @@ class Renderer:
 
     # ---------------------------------------------------------------- inputs
     def set_option(self, option, value):
-        """option: "wavefront" (0/1) or "work_order" (0/1)."""
-        code = {"work_order": _lib.DR_OPT_WORK_ORDER, "wavefront": _lib.DR_OPT_WAVEFRONT}[option]
+        """option: "wavefront" (-1 auto / 0 / 1), "work_order" (0/1) or "profile" (0/1)."""
+        code = {"work_order": _lib.DR_OPT_WORK_ORDER, "wavefront": _lib.DR_OPT_WAVEFRONT,
+                "profile": _lib.DR_OPT_PROFILE}[option]
         call("dr_set_option", self.h, code, int(value))
 
     def set_bvh_builder(self, builder="ploc", radius=16):
@@ -111,6 +112,18 @@ class Renderer:
 
     def splat(self):
         call("dr_splat", self.h)
+
+    def frame(self, n_steps):
+        """n_steps steps + splat as one replayed CUDA graph (needs a renderer
+        created on a non-default torch stream)."""
+        call("dr_frame", self.h, int(n_steps))
+
+    def profile(self):
+        """Per-phase device milliseconds since the last call (DR_OPT_PROFILE)."""
+        ms = (C.c_double * _lib.DR_PHASES)()
+        cnt = (C.c_uint64 * _lib.DR_PHASES)()
+        call("dr_get_profile", self.h, ms, cnt, _lib.DR_PHASES)
+        return {n: (ms[i], cnt[i]) for i, n in enumerate(_lib.PHASE_NAMES)}
 
     def resolve(self, out=None):
         if out is None:

@@ -256,6 +256,52 @@ def test_wavefront_matches_fused(torch, R, which):
     assert abs(c_a["tour_count"] - c_b["tour_count"]) <= 1e-3 * c_a["tour_count"] + 5
 
 
+@pytest.mark.parametrize("chains", [8192, 1 << 17])
+def test_graph_frames_match_plain_steps(torch, R, chains):
+    """dr_frame (captured once, replayed with the step index in device
+    memory) draws the same Philox numbers and runs the same kernels as
+    dr_step + dr_splat: identical chains and image."""
+    scene = S.cornell_box(1, 64, 64, glossy=True)
+    F = 5
+    res = []
+    for graph in (False, True):
+        s = torch.cuda.Stream()
+        r = R.Renderer(0, s)
+        r.upload_scene(scene)
+        r.init_chains(chains, 44, R.make_params(L=6, drift="adjoint", k0=0.0, steps_per_splat=F))
+        for _ in range(3):
+            if graph:
+                r.frame(F)
+            else:
+                r.step(F)
+                r.splat()
+        s.synchronize()
+        st = r.readback_state(fields=("x", "killed", "score"))
+        acc = r.readback_accum()
+        c = r.counters()
+        res.append((st, acc, c))
+        r.close()
+    (a, acc_a, c_a), (b, acc_b, c_b) = res
+    assert c_a["steps"] == c_b["steps"] == 3 * F
+    assert np.array_equal(a["x"], b["x"]) and np.array_equal(a["killed"], b["killed"])
+    assert np.array_equal(acc_a, acc_b)
+    assert c_a["tour_count"] == c_b["tour_count"]
+
+
+def test_profile_reports_phases(torch, R):
+    r = R.Renderer()
+    r.upload_scene(S.cornell_box(1, 32, 32, glossy=True))
+    r.init_chains(1 << 17, 5, R.make_params(L=6, drift="adjoint", k0=0.0, steps_per_splat=2))
+    r.set_option("profile", 1)
+    r.profile()
+    r.step(3)
+    r.splat()
+    p = r.profile()
+    assert p["trace"][1] == 3 * 6 and p["trace"][0] > 0
+    assert p["adjoint"][1] == 3 and p["splat"][1] >= 1
+    r.close()
+
+
 def test_k0_estimate_matches_oracle(torch, R, oracle):
     scene = S.cornell_box(1, 64, 64)
     N = 4096
