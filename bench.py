@@ -207,10 +207,12 @@ def run_ours(args, wl, rank, world, local):
     r = R.Renderer(local, stream)
     r.set_option("work_order", args.work_order)
     r.set_option("wavefront", args.wavefront)
+    r.set_option("bvh_width", args.bvh_width)
     r.upload_scene(scene)
     r.init_chains(N, seed, params)
     stream.synchronize()
-    log(f"uploaded + init {N} chains; bvh {r.bvh_info()}")
+    bvh4 = r.bvh4_info() if args.bvh_width != 2 else None
+    log(f"uploaded + init {N} chains; bvh {r.bvh_info()}; 4-wide {bvh4}")
     # traversal statistics (separate kernel instantiation, untimed)
     r.set_stats(True)
     r.step(2)
@@ -218,7 +220,13 @@ def run_ours(args, wl, rank, world, local):
     r.set_stats(False)
     chain_steps_stats = 2 * N
     d = 2 + 4 * (wl["L"] - 1)
-    trav_bytes = (ts["node_visits"] * 64 + ts["tri_tests"] * 48) / chain_steps_stats
+    # node size of the BVH the stats pass traversed: 4-wide in the
+    # bounce-by-bounce passes unless disabled; the fused kernel (automatic
+    # width) walks the binary one
+    wf_expected = wl["drift"] == "adjoint" and (args.wavefront == 1 or (args.wavefront == -1 and N >= 1 << 17))
+    wide = bool(bvh4) and (args.bvh_width == 4 or wf_expected)
+    node_bytes = 112 if wide else 64
+    trav_bytes = (ts["node_visits"] * node_bytes + ts["tri_tests"] * 48) / chain_steps_stats
     state_bytes = 4 * d * 4 + 1 + 1 + 4 + 16   # x and score read+write, killed r+w, logp, record
     log(f"stats pass: {ts}")
     # per-phase device time (events around each pass; untimed) for the roofline
@@ -229,6 +237,7 @@ def run_ours(args, wl, rank, world, local):
     prof = r.profile()
     r.set_option("profile", 0)
     wavefront = prof["trace"][1] > 0
+    assert wavefront == wf_expected, "execution mode differs from the one the roofline bytes assume"
     if wavefront:
         k_name = "wf_trace + wf_shadow (BVH traversal passes)"
         k_ms = (prof["trace"][0] + prof["shadow"][0]) / prof_steps
@@ -293,6 +302,7 @@ def run_ours(args, wl, rank, world, local):
                            "image": [scene.width, scene.height], "chains_per_gpu": N, "max_path_len": wl["L"],
                            "pss_dim": d, "drift": wl["drift"], "rb_weight": True, "steps_per_frame": F,
                            "execution": "wavefront" if wavefront else "fused",
+                           "bvh": "4-wide" if wide else "binary",
                            "frame": "CUDA graph of steps_per_frame steps + splat, replayed",
                            "l2": "inputs > L2 (BVH + chain state) and a 512 MB L2 flush between timed frames",
                            "parallelism": f"replicas{world}"},
@@ -358,6 +368,9 @@ def main():
     ap.add_argument("--wavefront", type=int, default=-1, choices=[-1, 0, 1],
                     help="bounce-by-bounce execution over compacted path queues: 1 on, 0 fused kernel, "
                          "-1 (default) by chain count")
+    ap.add_argument("--bvh-width", type=int, default=0, choices=[0, 2, 4],
+                    help="BVH the rays traverse: 4-wide, binary, or 0 (default) 4-wide in the bounce-by-bounce "
+                         "passes and binary in the fused kernel")
     ap.add_argument("--work-order", type=int, default=0, choices=[0, 1],
                     help="fused kernel only: order chains by expected path cost (default 0)")
     args = ap.parse_args()

@@ -218,6 +218,17 @@ int dr_get_traversal_stats(dr_ctx* ctx, uint64_t* node_visits, uint64_t* tri_tes
  * Synchronises. */
 int dr_bvh_info(dr_ctx* ctx, int32_t* n_nodes, int32_t* n_tris, int32_t* max_depth);
 
+/* The 4-wide BVH that dr_scene_upload collapses from the binary one on the
+ * host (a subtree of at most 4 triangles becomes a leaf where the surface-
+ * area heuristic favours it; each inner node takes up to 4 children by
+ * opening its largest inner grandchildren).  Node: 112 B = lo.x[4], hi.x[4],
+ * lo.y[4], hi.y[4], lo.z[4], hi.z[4], links[4].  HOST outputs (each may be
+ * NULL): node count, depth (root = 1), and the most traversal-stack entries
+ * a traversal can hold.  Errors: STATE (no scene, or none was built: a
+ * one-triangle scene, or a tree whose traversal would need more stack than
+ * the kernels hold; rays then use the binary BVH). */
+int dr_bvh4_info(dr_ctx* ctx, int32_t* n_nodes, int32_t* max_depth, int32_t* stack_need);
+
 /* Number of kernels this context has launched since creation (a host-side
  * count kept at every launch site; HOST output). */
 int dr_get_launch_count(dr_ctx* ctx, uint64_t* launches);
@@ -247,8 +258,13 @@ int dr_pt_render(dr_ctx* ctx, int32_t max_path_len, uint32_t spp, uint64_t seed,
  *   DR_OPT_PROFILE     1: record CUDA events around each pass of dr_step /
  *                      dr_splat (not inside dr_frame graphs) and accumulate
  *                      their durations per phase (see dr_get_profile).
+ *   DR_OPT_BVH_WIDTH   4: rays traverse the 4-wide BVH collapsed from the
+ *                      binary one at scene upload (when it was built, see
+ *                      dr_bvh4_info); 2: the binary BVH; 0 (default): the
+ *                      4-wide one everywhere but in the fused step kernel.
+ *                      Both return the same closest hit (ties: smaller id).
  * Errors: INVALID_ARG (unknown option or value). */
-enum { DR_OPT_WORK_ORDER = 1, DR_OPT_WAVEFRONT = 2, DR_OPT_PROFILE = 3 };
+enum { DR_OPT_WORK_ORDER = 1, DR_OPT_WAVEFRONT = 2, DR_OPT_PROFILE = 3, DR_OPT_BVH_WIDTH = 4 };
 int dr_set_option(dr_ctx* ctx, int32_t option, int32_t value);
 
 /* Per-phase device time accumulated since the last call while DR_OPT_PROFILE

@@ -28,6 +28,11 @@ struct dr_ctx {
   Camera cam{};
   float4* nodes = nullptr;
   float4* tris = nullptr;
+  float4* nodes4 = nullptr;  // 4-wide collapse of `nodes` (null when not built)
+  float4* tris4 = nullptr;
+  int n_nodes4 = 0, bvh4_depth = 0, bvh4_stack = 0;
+  int bvh_width = 0;  // DR_OPT_BVH_WIDTH (0 automatic)
+  unsigned long long target_gen = 0;  // bumped by every scene / mixture upload
   float4* surf = nullptr;
   float4* lights = nullptr;
   float* nrm = nullptr;
@@ -199,7 +204,11 @@ void dfree(T** p) {
     if (r_ != DR_OK) return r_;  \
   } while (0)
 
-DevScene dev_scene(const dr_ctx* c) {
+// wide_ok: under the automatic BVH choice, whether the caller's kernels take
+// the 4-wide BVH (the bounce-by-bounce passes and the single-purpose
+// kernels do; the fused step kernel, which holds a whole path's state while
+// it traverses, keeps the binary one)
+DevScene dev_scene(const dr_ctx* c, bool wide_ok = true) {
   DevScene S;
   S.nodes = c->nodes;
   S.tris = c->tris;
@@ -210,6 +219,10 @@ DevScene dev_scene(const dr_ctx* c) {
   S.n_lights = c->n_lights;
   S.n_tris = c->nt;
   S.n_nodes = std::max(1, c->n_nodes);
+  const bool wide = c->nodes4 != nullptr && (c->bvh_width == 4 || (c->bvh_width == 0 && wide_ok));
+  S.nodes4 = wide ? c->nodes4 : nullptr;
+  S.tris4 = wide ? c->tris4 : nullptr;
+  S.n_nodes4 = wide ? c->n_nodes4 : 0;
   S.W = c->W;
   S.H = c->H;
   S.tmin = c->tmin;
@@ -270,9 +283,11 @@ int flush(dr_ctx* c) {
   return check_launch("splat");
 }
 
+bool use_wavefront(const dr_ctx* c);
+
 StepArgs step_args(dr_ctx* c) {
   StepArgs a{};
-  a.S = dev_scene(c);
+  a.S = dev_scene(c, use_wavefront(c));
   a.M = dev_mixture(c);
   a.target = c->target;
   a.x = c->x;
@@ -300,7 +315,7 @@ StepArgs step_args(dr_ctx* c) {
 
 int run_fd(dr_ctx* c) {
   FdArgs f{};
-  f.S = dev_scene(c);
+  f.S = dev_scene(c, false);
   f.M = dev_mixture(c);
   f.target = c->target;
   f.x = c->x;
@@ -391,6 +406,46 @@ bool capturing(cudaStream_t s) {
   return st != cudaStreamCaptureStatusNone;
 }
 
+// Collapses the freshly built binary BVH into the 4-wide layout (on the
+// device).  Scenes of one triangle (whose binary tree repeats its leaf) and
+// trees whose 4-wide traversal could need more stack than the kernels hold
+// keep the binary BVH only.
+int build_bvh4(dr_ctx* c) {
+  dfree(&c->nodes4);
+  dfree(&c->tris4);
+  c->n_nodes4 = c->bvh4_depth = c->bvh4_stack = 0;
+  if (c->nt < 2) return DR_OK;
+  const int nn = std::max(1, c->n_nodes);
+  void* scratch = nullptr;
+  if (cudaMalloc(&scratch, bvh4_scratch_bytes(nn)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(DR_ERR_OOM, "dr_scene_upload: 4-wide BVH scratch");
+  }
+  Bvh4Plan plan{};
+  int r = DR_OK;
+  const int n4 = bvh4_plan(c->nodes, nn, c->nt, scratch, &plan, c->stream);
+  c->launches += plan.launches;
+  if (n4 >= 1 && plan.stack_need <= kTraversalStack) {
+    r = dalloc(&c->nodes4, (size_t)kNode4F4 * n4);
+    if (r == DR_OK) r = dalloc(&c->tris4, (size_t)kTriF4 * c->nt);
+    if (r == DR_OK && bvh4_emit(c->nodes, c->tris, nn, c->nt, scratch, c->nodes4, c->tris4, c->stream) < 0)
+      r = fail(DR_ERR_DEVICE_CHECK, "dr_scene_upload: 4-wide BVH emission failed");
+    c->launches += 1;
+    if (r == DR_OK) {
+      c->n_nodes4 = n4;
+      c->bvh4_depth = plan.depth;
+      c->bvh4_stack = plan.stack_need;
+    } else {
+      dfree(&c->nodes4);
+      dfree(&c->tris4);
+    }
+  }
+  cudaFree(scratch);
+  const cudaError_t e = cudaGetLastError();
+  if (r == DR_OK && e != cudaSuccess) r = fail(DR_ERR_CUDA, std::string("dr_scene_upload: ") + cudaGetErrorString(e));
+  return r;
+}
+
 }  // namespace
 
 extern "C" {
@@ -431,6 +486,7 @@ int dr_destroy(dr_ctx* c) {
   if (!c) return DR_OK;
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
+  dfree(&c->nodes4); dfree(&c->tris4);
   dfree(&c->nodes); dfree(&c->tris); dfree(&c->surf); dfree(&c->lights); dfree(&c->nrm); dfree(&c->mats);
   dfree(&c->mw); dfree(&c->mmu); dfree(&c->msig);
   dfree(&c->x); dfree(&c->score); dfree(&c->logp); dfree(&c->killed);
@@ -597,7 +653,9 @@ int dr_scene_upload(dr_ctx* c, const float* verts, int32_t nv, const int32_t* tr
   if (r == DR_OK && depth - 1 > kTraversalStack)
     r = fail(DR_ERR_DEVICE_CHECK, "dr_scene_upload: BVH depth " + std::to_string(depth) +
                                       " exceeds the traversal stack (" + std::to_string(kTraversalStack + 1) + ")");
+  if (r == DR_OK) r = build_bvh4(c);
   if (r != DR_OK) c->target = -1;
+  c->target_gen++;
   return r;
 }
 
@@ -626,6 +684,7 @@ int dr_target_mixture(dr_ctx* c, int32_t d, int32_t K, const float* w, const flo
   c->W = width;
   c->H = height;
   c->inited = false;
+  c->target_gen++;
   return DR_OK;
 }
 
@@ -1008,10 +1067,11 @@ std::vector<unsigned long long> frame_key(const dr_ctx* c, uint32_t n_steps) {
   std::vector<unsigned long long> k = {n_steps, c->N, (unsigned long long)c->d, (unsigned long long)c->target,
                                        P(c->x), P(c->score), P(c->killed), P(c->logp), P(c->plen), P(c->rec),
                                        P(c->rec_alt), P(c->sort_scratch), P(c->accum), P(c->wf_mem), P(c->nodes),
-                                       P(c->tris), P(c->surf), P(c->mats), P(c->lights), P(c->nrm), P(c->mw),
+                                       P(c->nodes4), (unsigned long long)c->bvh_width, P(c->tris), P(c->surf), P(c->mats), P(c->lights), P(c->nrm), P(c->mw),
                                        c->seed, c->frame, k0b, c->rec_cap, (unsigned long long)c->wavefront,
                                        (unsigned long long)c->work_order, (unsigned long long)c->stats,
-                                       (unsigned long long)c->nt, (unsigned long long)c->n_lights, P(c->stream)};
+                                       (unsigned long long)c->nt, (unsigned long long)c->n_lights, P(c->stream),
+                                       c->target_gen};
   for (unsigned long long v : prm) k.push_back(v);
   return k;
 }
@@ -1144,6 +1204,11 @@ int dr_set_option(dr_ctx* c, int32_t option, int32_t value) {
       if (value != 0 && value != 1) return fail(DR_ERR_INVALID_ARG, "dr_set_option: work order is 0 or 1");
       c->work_order = value;
       return DR_OK;
+    case DR_OPT_BVH_WIDTH:
+      if (value != 0 && value != 2 && value != 4)
+        return fail(DR_ERR_INVALID_ARG, "dr_set_option: BVH width is 0, 2 or 4");
+      c->bvh_width = value;
+      return DR_OK;
     default:
       return fail(DR_ERR_INVALID_ARG, "dr_set_option: unknown option");
   }
@@ -1171,6 +1236,16 @@ int dr_get_chain_shape(dr_ctx* c, uint64_t* n_chains, int32_t* dim, int32_t* max
 int dr_get_launch_count(dr_ctx* c, uint64_t* launches) {
   if (!c || !launches) return fail(DR_ERR_INVALID_ARG, "dr_get_launch_count: NULL argument");
   *launches = c->launches;
+  return DR_OK;
+}
+
+int dr_bvh4_info(dr_ctx* c, int32_t* n_nodes, int32_t* max_depth, int32_t* stack_need) {
+  if (!c) return fail(DR_ERR_INVALID_ARG, "dr_bvh4_info: NULL ctx");
+  if (c->target != 0) return fail(DR_ERR_STATE, "dr_bvh4_info: no scene");
+  if (!c->nodes4) return fail(DR_ERR_STATE, "dr_bvh4_info: the scene has no 4-wide BVH");
+  if (n_nodes) *n_nodes = c->n_nodes4;
+  if (max_depth) *max_depth = c->bvh4_depth;
+  if (stack_need) *stack_need = c->bvh4_stack;
   return DR_OK;
 }
 

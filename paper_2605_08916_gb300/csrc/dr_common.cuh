@@ -123,6 +123,13 @@ constexpr int kNodeF4 = 4, kTriF4 = 3, kSurfF4 = 5, kLightF4 = 4, kMatFloats = 1
 enum MatType { kDiffuse = 0, kGlossy = 1, kDielectric = 2, kEmitter = 3 };
 constexpr float kGlossySpecProb = 0.5f;
 
+// 4-wide BVH node (112 B, 7 x float4): lo.x[4], hi.x[4], lo.y[4], hi.y[4],
+// lo.z[4], hi.z[4], then the four child links (inner index, leaf code, or
+// kBvh4Empty); leaves hold up to kBvh4MaxLeaf triangles.
+constexpr int kNode4F4 = 7;
+constexpr int kBvh4MaxLeaf = 4;
+constexpr int kBvh4Empty = 0x7fffffff;
+
 DR_HD int leaf_code(int first, int count) { return (int)(0x80000000u | ((uint32_t)first << 3) | (uint32_t)(count - 1)); }
 DR_HD int leaf_first(int c) { return (int)(((uint32_t)c & 0x7fffffffu) >> 3); }
 DR_HD int leaf_count(int c) { return (int)((uint32_t)c & 7u) + 1; }
@@ -140,12 +147,14 @@ struct Camera {
 
 struct DevScene {
   const float4* __restrict__ nodes;
+  const float4* __restrict__ nodes4;  // 4-wide BVH (null: use the binary one)
+  const float4* __restrict__ tris4;   // triangles in the 4-wide BVH's leaf order
   const float4* __restrict__ tris;
   const float4* __restrict__ surf;
   const float* __restrict__ nrm;     // 9 floats per original triangle, or null
   const float* __restrict__ mats;
   const float4* __restrict__ lights;
-  int n_lights, n_tris, n_nodes, W, H;
+  int n_lights, n_tris, n_nodes, n_nodes4, W, H;
   float tmin;
   Camera cam;
 };

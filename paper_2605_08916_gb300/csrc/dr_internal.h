@@ -55,6 +55,20 @@ void launch_surface_records(const float* d_verts, const int* d_tris, const int* 
                             const float* d_vnormals, int nt, float4* d_surf, cudaStream_t s);
 void launch_gather_normals(const float* d_vnormals, const int* d_tris, int nt, float* d_tri_normals,
                            cudaStream_t s);
+// Device-side collapse of the binary BVH (4 float4 per node, n_inner nodes;
+// triangles 3 float4 each) into the 4-wide layout, triangles re-laid in
+// depth-first order.  bvh4_plan runs every pass but the output (one
+// synchronisation per 4-wide level) and returns the 4-wide node count, or -1
+// (bad tree, fewer than 2 triangles, CUDA error); bvh4_emit then writes
+// nodes4 [count * 7] and tris4 [n_tris * 3] (returns 1, or -1).  Both use
+// the same scratch of bvh4_scratch_bytes(n_inner).
+struct Bvh4Plan {
+  int n_nodes4, depth, stack_need, launches;
+};
+size_t bvh4_scratch_bytes(int n_inner);
+int bvh4_plan(const float4* d_nodes2, int n_inner, int n_tris, void* scratch, Bvh4Plan* plan, cudaStream_t s);
+int bvh4_emit(const float4* d_nodes2, const float4* d_tris2, int n_inner, int n_tris, void* scratch,
+              float4* d_nodes4, float4* d_tris4, cudaStream_t s);
 
 // ---------------------------------------------------------------- chains
 enum Drift { kDriftNone = 0, kDriftFD = 1, kDriftAdjoint = 2 };

@@ -91,12 +91,172 @@ DR_D void load_node(const float4* __restrict__ nodes, int n, float3& lo0, float3
   c1 = e.y;
 }
 
-// Closest hit with t in (tmin, inf), skipping triangle `exclude` (original
-// id).  Equal distances resolve to the smaller original triangle id.
-// Returns the original triangle id or -1.
+DR_D float f4c(float4 v, int k) { return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w; }
+DR_D int i4c(int4 v, int k) { return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w; }
+
+// Tests the triangles of one leaf against [tmin, tbest]; keeps the closest
+// (ties: smaller original id).
+template <bool STATS>
+DR_D void leaf_closest(const DevScene& S, int code, const Ray& r, int exclude, float& tbest, int& best, uint32_t* err,
+                       TraceStats* stats) {
+  const int first = leaf_first(code);
+  int cnt = leaf_count(code);
+  if (first + cnt > S.n_tris) {
+    *err |= kErrBadIndex;
+    cnt = 0;
+  }
+  for (int i = 0; i < cnt; ++i) {
+    const float4 t0 = __ldg(S.tris4 + 3 * (first + i) + 0);
+    const float4 t1 = __ldg(S.tris4 + 3 * (first + i) + 1);
+    const float4 t2 = __ldg(S.tris4 + 3 * (first + i) + 2);
+    const int id = __float_as_int(t0.w);
+    if (STATS) ++stats->tris;
+    float th;
+    if (id != exclude && tri_test(xyz(t0), xyz(t1), xyz(t2), r, S.tmin, tbest * 1.0000001f + 1e-30f, &th)) {
+      if (th < tbest || (th == tbest && id < best)) {
+        tbest = th;
+        best = id;
+      }
+    }
+  }
+}
+
+// 4-wide closest hit: the four child boxes of a node are tested together;
+// leaves are tested on the spot, hit inner children are visited nearest
+// first (the others pushed far-to-near).
 template <int STACK, bool STATS>
-DR_D int trace_closest(const DevScene& S, const Ray& r, int exclude, float* t_hit, TraceStack<STACK> st,
-                       uint32_t* err, TraceStats* stats) {
+DR_D int trace_closest4(const DevScene& S, const Ray& r, int exclude, float* t_hit, TraceStack<STACK> st,
+                        uint32_t* err, TraceStats* stats) {
+  float tbest = __int_as_float(0x7f800000);
+  int best = -1;
+  int sp = 0;
+  int node = 0;
+  if (!ray_finite(r.o, r.d)) {
+    *err |= kErrNonFinite;
+    *t_hit = tbest;
+    return -1;
+  }
+  int budget = min(2 * S.n_nodes4 + 64, kMaxNodeVisits);
+  while (true) {
+    if (--budget < 0 || node < 0 || node >= S.n_nodes4) {
+      *err |= kErrBadIndex;
+      break;
+    }
+    const float4* nb = S.nodes4 + (size_t)kNode4F4 * node;
+    const float4 bx0 = __ldg(nb + 0), bx1 = __ldg(nb + 1), by0 = __ldg(nb + 2), by1 = __ldg(nb + 3);
+    const float4 bz0 = __ldg(nb + 4), bz1 = __ldg(nb + 5);
+    const int4 ch = __ldg(reinterpret_cast<const int4*>(nb + 6));
+    if (STATS) ++stats->nodes;
+    float e[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      e[k] = box_entry(f3(f4c(bx0, k), f4c(by0, k), f4c(bz0, k)), f3(f4c(bx1, k), f4c(by1, k), f4c(bz1, k)), r,
+                       tbest);
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (i4c(ch, k) < 0 && e[k] >= 0.0f && e[k] <= tbest) leaf_closest<STATS>(S, i4c(ch, k), r, exclude, tbest, best, err, stats);
+    bool ok[4];
+    int nc = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int c = i4c(ch, k);
+      ok[k] = c >= 0 && c != kBvh4Empty && e[k] >= 0.0f && e[k] <= tbest;
+      nc += ok[k] ? 1 : 0;
+    }
+    if (nc == 0) {
+      if (sp == 0) break;
+      node = st.at(--sp);
+      continue;
+    }
+    if (sp + nc - 1 > STACK) {
+      *err |= kErrStackOverflow;
+      nc = STACK - sp + 1;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (!ok[k]) continue;
+      int rank = 0;
+#pragma unroll
+      for (int m = 0; m < 4; ++m)
+        if (m != k && ok[m] && (e[m] < e[k] || (e[m] == e[k] && m < k))) ++rank;
+      if (rank == 0) node = i4c(ch, k);
+      else if (rank < nc) st.at(sp + nc - 1 - rank) = i4c(ch, k);
+    }
+    sp += nc - 1;
+  }
+  *t_hit = tbest;
+  return best;
+}
+
+// 4-wide any hit in (tmin, tmax), skipping two triangle ids.
+template <int STACK, bool STATS>
+DR_D bool trace_any4(const DevScene& S, const Ray& r, float tmax, int ex0, int ex1, TraceStack<STACK> st,
+                     uint32_t* err, TraceStats* stats) {
+  int sp = 0;
+  int node = 0;
+  if (!ray_finite(r.o, r.d)) {
+    *err |= kErrNonFinite;
+    return true;  // treated as occluded
+  }
+  int budget = min(2 * S.n_nodes4 + 64, kMaxNodeVisits);
+  while (true) {
+    if (--budget < 0 || node < 0 || node >= S.n_nodes4) {
+      *err |= kErrBadIndex;
+      break;
+    }
+    const float4* nb = S.nodes4 + (size_t)kNode4F4 * node;
+    const float4 bx0 = __ldg(nb + 0), bx1 = __ldg(nb + 1), by0 = __ldg(nb + 2), by1 = __ldg(nb + 3);
+    const float4 bz0 = __ldg(nb + 4), bz1 = __ldg(nb + 5);
+    const int4 ch = __ldg(reinterpret_cast<const int4*>(nb + 6));
+    if (STATS) ++stats->nodes;
+    int next = -1;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int c = i4c(ch, k);
+      if (c == kBvh4Empty) continue;
+      const float e = box_entry(f3(f4c(bx0, k), f4c(by0, k), f4c(bz0, k)), f3(f4c(bx1, k), f4c(by1, k), f4c(bz1, k)),
+                                r, tmax);
+      if (!(e >= 0.0f)) continue;
+      if (c < 0) {
+        const int first = leaf_first(c);
+        int cnt = leaf_count(c);
+        if (first + cnt > S.n_tris) {
+          *err |= kErrBadIndex;
+          cnt = 0;
+        }
+        for (int i = 0; i < cnt; ++i) {
+          const float4 t0 = __ldg(S.tris4 + 3 * (first + i) + 0);
+          const float4 t1 = __ldg(S.tris4 + 3 * (first + i) + 1);
+          const float4 t2 = __ldg(S.tris4 + 3 * (first + i) + 2);
+          const int id = __float_as_int(t0.w);
+          if (STATS) ++stats->tris;
+          float th;
+          if (id != ex0 && id != ex1 && tri_test(xyz(t0), xyz(t1), xyz(t2), r, S.tmin, tmax, &th)) return true;
+        }
+      } else if (next < 0) {
+        next = c;
+      } else if (sp < STACK) {
+        st.at(sp++) = c;
+      } else {
+        *err |= kErrStackOverflow;
+      }
+    }
+    if (next >= 0) {
+      node = next;
+      continue;
+    }
+    if (sp == 0) break;
+    node = st.at(--sp);
+  }
+  return false;
+}
+
+// Binary-BVH closest hit with t in (tmin, inf), skipping triangle `exclude`
+// (original id).  Equal distances resolve to the smaller original triangle
+// id.  Returns the original triangle id or -1.
+template <int STACK, bool STATS>
+DR_D int trace_closest2(const DevScene& S, const Ray& r, int exclude, float* t_hit, TraceStack<STACK> st,
+                        uint32_t* err, TraceStats* stats) {
   float tbest = __int_as_float(0x7f800000);
   int best = -1;
   int sp = 0;
@@ -170,10 +330,10 @@ DR_D int trace_closest(const DevScene& S, const Ray& r, int exclude, float* t_hi
   return best;
 }
 
-// Any hit with t in (tmin, tmax), skipping two triangle ids.
+// Binary-BVH any hit with t in (tmin, tmax), skipping two triangle ids.
 template <int STACK, bool STATS>
-DR_D bool trace_any(const DevScene& S, const Ray& r, float tmax, int ex0, int ex1, TraceStack<STACK> st,
-                    uint32_t* err, TraceStats* stats) {
+DR_D bool trace_any2(const DevScene& S, const Ray& r, float tmax, int ex0, int ex1, TraceStack<STACK> st,
+                     uint32_t* err, TraceStats* stats) {
   int sp = 0;
   int node = 0;
   if (!ray_finite(r.o, r.d)) {
@@ -230,6 +390,25 @@ DR_D bool trace_any(const DevScene& S, const Ray& r, float tmax, int ex0, int ex
     node = st.at(--sp);
   }
   return false;
+}
+
+// Closest hit / any hit through whichever BVH the scene selects (WIDTH 0:
+// decided per call from S.nodes4; 2 or 4: fixed at compile time, for
+// kernels specialised per width).
+template <int STACK, bool STATS, int WIDTH = 0>
+DR_D int trace_closest(const DevScene& S, const Ray& r, int exclude, float* t_hit, TraceStack<STACK> st,
+                       uint32_t* err, TraceStats* stats) {
+  if (WIDTH == 4 || (WIDTH == 0 && S.nodes4 != nullptr))
+    return trace_closest4<STACK, STATS>(S, r, exclude, t_hit, st, err, stats);
+  return trace_closest2<STACK, STATS>(S, r, exclude, t_hit, st, err, stats);
+}
+
+template <int STACK, bool STATS, int WIDTH = 0>
+DR_D bool trace_any(const DevScene& S, const Ray& r, float tmax, int ex0, int ex1, TraceStack<STACK> st,
+                    uint32_t* err, TraceStats* stats) {
+  if (WIDTH == 4 || (WIDTH == 0 && S.nodes4 != nullptr))
+    return trace_any4<STACK, STATS>(S, r, tmax, ex0, ex1, st, err, stats);
+  return trace_any2<STACK, STATS>(S, r, tmax, ex0, ex1, st, err, stats);
 }
 
 }  // namespace dr

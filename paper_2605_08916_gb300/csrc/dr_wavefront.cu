@@ -28,6 +28,13 @@ constexpr int kWfThreads = 128;
 constexpr int kWfStack = kTraversalStack;
 // resident blocks per SM the traversal passes are compiled for (register cap)
 constexpr int kWfTraceMinBlocks = 10;
+// the 4-wide traversal holds four child boxes at once: fewer resident
+// blocks, more registers per thread
+#ifndef DR_WF_TRACE4_MIN_BLOCKS
+#define DR_WF_TRACE4_MIN_BLOCKS 6
+#endif
+constexpr int kWfTrace4MinBlocks = DR_WF_TRACE4_MIN_BLOCKS;
+constexpr int trace_min_blocks(int width) { return width == 4 ? kWfTrace4MinBlocks : kWfTraceMinBlocks; }
 
 // 64-B path slot per chain: (o, ppdf), (d, prev tri), (beta, prev_delta |
 // nseg << 8), (f, pixel)
@@ -81,8 +88,8 @@ __global__ void __launch_bounds__(kWfThreads) wf_begin(StepArgs a, WfBuffers w) 
   if (blockIdx.x == 0 && threadIdx.x == 0) w.counts[1] = (uint32_t)a.N;  // bounce 1: every chain
 }
 
-template <bool STATS>
-__global__ void __launch_bounds__(kWfThreads, kWfTraceMinBlocks) wf_trace(StepArgs a, WfBuffers w, int k) {
+template <bool STATS, int WIDTH>
+__global__ void __launch_bounds__(kWfThreads, trace_min_blocks(WIDTH)) wf_trace(StepArgs a, WfBuffers w, int k) {
   extern __shared__ int smem[];
   TraceStack<kWfStack> st{smem + threadIdx.x, (int)blockDim.x};
   const uint32_t n = w.counts[k];
@@ -94,8 +101,8 @@ __global__ void __launch_bounds__(kWfThreads, kWfTraceMinBlocks) wf_trace(StepAr
     const unsigned long long j = q ? q[t] : t;
     const float4 o = w.slot[4 * j + 0], d = w.slot[4 * j + 1];
     float th;
-    w.hit[j] = trace_closest<kWfStack, STATS>(a.S, make_ray(xyz(o), xyz(d)), __float_as_int(d.w), &th, st, &err,
-                                              &stats);
+    w.hit[j] = trace_closest<kWfStack, STATS, WIDTH>(a.S, make_ray(xyz(o), xyz(d)), __float_as_int(d.w), &th, st,
+                                                     &err, &stats);
     ++rays;
   }
   add_counts(a.rays, rays);
@@ -148,8 +155,8 @@ __global__ void __launch_bounds__(kWfThreads) wf_shade(StepArgs a, WfBuffers w, 
   }
 }
 
-template <bool STATS>
-__global__ void __launch_bounds__(kWfThreads, kWfTraceMinBlocks) wf_shadow(StepArgs a, WfBuffers w, int k) {
+template <bool STATS, int WIDTH>
+__global__ void __launch_bounds__(kWfThreads, trace_min_blocks(WIDTH)) wf_shadow(StepArgs a, WfBuffers w, int k) {
   extern __shared__ int smem[];
   TraceStack<kWfStack> st{smem + threadIdx.x, (int)blockDim.x};
   const uint32_t n = w.counts[kWfShadowCount0 + k];
@@ -160,8 +167,8 @@ __global__ void __launch_bounds__(kWfThreads, kWfTraceMinBlocks) wf_shadow(StepA
     const ShadowRec r = w.shadow[t];
     const unsigned long long j = (unsigned long long)__float_as_int(r.wi_chain.w);
     ++rays;
-    if (!trace_any<kWfStack, STATS>(a.S, make_ray(xyz(r.o_tmax), xyz(r.wi_chain)), r.o_tmax.w,
-                                    __float_as_int(r.contrib_ex.w), r.ex1, st, &err, &stats)) {
+    if (!trace_any<kWfStack, STATS, WIDTH>(a.S, make_ray(xyz(r.o_tmax), xyz(r.wi_chain)), r.o_tmax.w,
+                                           __float_as_int(r.contrib_ex.w), r.ex1, st, &err, &stats)) {
       float4 f = w.slot[4 * j + 3];
       f.x += r.contrib_ex.x;
       f.y += r.contrib_ex.y;
@@ -265,6 +272,7 @@ int launch_wavefront_step(const StepArgs& a, const WfBuffers& w, bool stats, int
   const int max_blocks = n_sm * 16;
   const unsigned g = grid_for(a.N, max_blocks);
   const size_t smem = (size_t)kWfStack * kWfThreads * sizeof(int);
+  const bool wide = a.S.nodes4 != nullptr;
   int launches = 0;
   cudaMemsetAsync(w.counts, 0, kWfCounts * sizeof(uint32_t), s);
   hook(kPhBegin, true);
@@ -273,15 +281,25 @@ int launch_wavefront_step(const StepArgs& a, const WfBuffers& w, bool stats, int
   launches += 2;
   for (int k = 1; k <= a.L; ++k) {
     hook(kPhTrace, true);
-    if (stats) wf_trace<true><<<g, kWfThreads, smem, s>>>(a, w, k);
-    else wf_trace<false><<<g, kWfThreads, smem, s>>>(a, w, k);
+    if (wide) {
+      if (stats) wf_trace<true, 4><<<g, kWfThreads, smem, s>>>(a, w, k);
+      else wf_trace<false, 4><<<g, kWfThreads, smem, s>>>(a, w, k);
+    } else {
+      if (stats) wf_trace<true, 2><<<g, kWfThreads, smem, s>>>(a, w, k);
+      else wf_trace<false, 2><<<g, kWfThreads, smem, s>>>(a, w, k);
+    }
     hook(kPhTrace, false);
     hook(kPhShade, true);
     wf_shade<<<g, kWfThreads, 0, s>>>(a, w, k);
     hook(kPhShade, false);
     hook(kPhShadow, true);
-    if (stats) wf_shadow<true><<<g, kWfThreads, smem, s>>>(a, w, k);
-    else wf_shadow<false><<<g, kWfThreads, smem, s>>>(a, w, k);
+    if (wide) {
+      if (stats) wf_shadow<true, 4><<<g, kWfThreads, smem, s>>>(a, w, k);
+      else wf_shadow<false, 4><<<g, kWfThreads, smem, s>>>(a, w, k);
+    } else {
+      if (stats) wf_shadow<true, 2><<<g, kWfThreads, smem, s>>>(a, w, k);
+      else wf_shadow<false, 2><<<g, kWfThreads, smem, s>>>(a, w, k);
+    }
     hook(kPhShadow, false);
     launches += 3;
   }

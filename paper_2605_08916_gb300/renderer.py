@@ -70,9 +70,10 @@ class Renderer:
 
     # ---------------------------------------------------------------- inputs
     def set_option(self, option, value):
-        """option: "wavefront" (-1 auto / 0 / 1), "work_order" (0/1) or "profile" (0/1)."""
+        """option: "wavefront" (-1 auto / 0 / 1), "work_order" (0/1), "profile" (0/1) or
+        "bvh_width" (0 automatic / 2 / 4)."""
         code = {"work_order": _lib.DR_OPT_WORK_ORDER, "wavefront": _lib.DR_OPT_WAVEFRONT,
-                "profile": _lib.DR_OPT_PROFILE}[option]
+                "profile": _lib.DR_OPT_PROFILE, "bvh_width": _lib.DR_OPT_BVH_WIDTH}[option]
         call("dr_set_option", self.h, code, int(value))
 
     def set_bvh_builder(self, builder="ploc", radius=16):
@@ -174,6 +175,15 @@ class Renderer:
         a, b, c = C.c_int32(), C.c_int32(), C.c_int32()
         call("dr_bvh_info", self.h, C.byref(a), C.byref(b), C.byref(c))
         return {"n_nodes": a.value, "n_tris": b.value, "max_depth": c.value}
+
+    def bvh4_info(self):
+        """The 4-wide BVH's node count, depth and traversal-stack need, or None when the scene has none."""
+        a, b, c = C.c_int32(), C.c_int32(), C.c_int32()
+        r = _lib.load().dr_bvh4_info(self.h, C.byref(a), C.byref(b), C.byref(c))
+        if r == _lib.DR_ERR_STATE:
+            return None
+        _lib.check(r, "dr_bvh4_info")
+        return {"n_nodes": a.value, "max_depth": b.value, "stack_need": c.value}
 
     def launch_count(self):
         n = C.c_uint64()

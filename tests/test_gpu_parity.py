@@ -53,27 +53,40 @@ def test_philox_bit_exact(torch, R, oracle):
     assert np.array_equal(mine, oracle.philox4x32_10(ctr, key))
 
 
-@pytest.mark.parametrize("builder", ["ploc", "lbvh"])
-@pytest.mark.parametrize("which", ["cornell", "caustic", "procedural"])
-def test_closest_hit_matches_oracle(torch, R, oracle, which, builder):
+def hit_scene(which):
     if which == "cornell":
-        scene = S.cornell_box(1, 16, 16)
-    elif which == "caustic":
-        scene = S.caustic_scene(1, 16, 16, n_theta=40, n_phi=40)
-    else:
-        scene = S.procedural_scene(1, 32, 18, target_tris=30000, n_objects=40)
-    r = R.Renderer()
-    r.set_bvh_builder(builder)
-    r.upload_scene(scene)
-    info = r.bvh_info()
-    assert info["n_tris"] == scene.n_tris and info["max_depth"] < 48
-    tgt = oracle.OracleScene(scene)
+        return S.cornell_box(1, 16, 16)
+    if which == "caustic":
+        return S.caustic_scene(1, 16, 16, n_theta=40, n_phi=40)
+    return S.procedural_scene(1, 32, 18, target_tris=30000, n_objects=40)
+
+
+def random_rays(scene, n, seed):
     lo, hi = scene.verts.min(0), scene.verts.max(0)
-    rng = np.random.default_rng(2)
-    n = 20000
+    rng = np.random.default_rng(seed)
     o = (lo + (hi - lo) * rng.uniform(0.05, 0.95, (n, 3))).astype(np.float32)
     d = rng.normal(size=(n, 3)).astype(np.float32)
     d /= np.linalg.norm(d, axis=1, keepdims=True)
+    return o, d
+
+
+@pytest.mark.parametrize("width", [2, 4])
+@pytest.mark.parametrize("builder", ["ploc", "lbvh"])
+@pytest.mark.parametrize("which", ["cornell", "caustic", "procedural"])
+def test_closest_hit_matches_oracle(torch, R, oracle, which, builder, width):
+    scene = hit_scene(which)
+    r = R.Renderer()
+    r.set_bvh_builder(builder)
+    r.set_option("bvh_width", width)
+    r.upload_scene(scene)
+    info = r.bvh_info()
+    assert info["n_tris"] == scene.n_tris and info["max_depth"] < 48
+    info4 = r.bvh4_info()
+    assert info4 is not None and info4["stack_need"] <= 40
+    assert info4["n_nodes"] < info["n_nodes"] and info4["max_depth"] < info["max_depth"]
+    tgt = oracle.OracleScene(scene)
+    n = 20000
+    o, d = random_rays(scene, n, 2)
     rays = torch.from_numpy(np.concatenate([o, d], 1)).cuda()
     tri_g, t_g = r.trace_closest(rays)
     torch.cuda.synchronize()
@@ -86,6 +99,52 @@ def test_closest_hit_matches_oracle(torch, R, oracle, which, builder):
     assert np.all(np.abs(t_g[both] - t_o[both]) <= 1e-4 * np.maximum(1.0, t_o[both]))
     hit = same & (tri_o >= 0)
     assert np.allclose(t_g[hit], t_o[hit], rtol=1e-4, atol=1e-5)
+    r.close()
+
+
+@pytest.mark.parametrize("which", ["cornell", "caustic", "procedural"])
+def test_bvh_widths_return_the_same_hits(torch, R, which):
+    """The 4-wide BVH is a regrouping of the binary one's boxes and
+    triangles: the closest hit (ties to the smaller id) and its distance
+    come from the same triangle test on the same data, so they agree
+    bitwise."""
+    scene = hit_scene(which)
+    o, d = random_rays(scene, 50000, 3)
+    rays = torch.from_numpy(np.concatenate([o, d], 1)).cuda()
+    out = []
+    for width in (2, 4):
+        r = R.Renderer()
+        r.set_option("bvh_width", width)
+        r.upload_scene(scene)
+        tri, t = r.trace_closest(rays)
+        torch.cuda.synchronize()
+        out.append((tri.cpu().numpy(), t.cpu().numpy()))
+        r.close()
+    (a, ta), (b, tb) = out
+    assert (a == b).mean() >= 0.9999
+    same = a == b
+    assert np.array_equal(ta[same], tb[same])
+
+
+def test_one_triangle_scene_keeps_the_binary_bvh(torch, R):
+    scene = S.cornell_box(1, 8, 8)
+    keep = np.zeros(scene.n_tris, bool)
+    keep[0] = True
+    one = S.Scene(verts=scene.verts, tris=np.ascontiguousarray(scene.tris[keep]),
+                  tri_mat=np.ascontiguousarray(scene.tri_mat[keep]), materials=scene.materials,
+                  camera=scene.camera, width=8, height=8, normals=scene.normals).check()
+    r = R.Renderer()
+    r.upload_scene(one)
+    assert r.bvh4_info() is None
+    v = scene.verts[scene.tris[0]].astype(np.float64)
+    centre = v.mean(0)
+    nrm = np.cross(v[1] - v[0], v[2] - v[0])
+    nrm /= np.linalg.norm(nrm)
+    o = centre + nrm
+    rays = torch.tensor([np.concatenate([o, -nrm])], dtype=torch.float32).cuda()
+    tri, t = r.trace_closest(rays)
+    torch.cuda.synchronize()
+    assert int(tri.cpu()[0]) == 0 and abs(float(t.cpu()[0]) - 1.0) < 1e-4
     r.close()
 
 
@@ -254,6 +313,28 @@ def test_wavefront_matches_fused(torch, R, which):
     assert np.mean(rel <= 1e-4) >= 0.999
     assert np.allclose(acc_a, acc_b, rtol=1e-3, atol=1e-9 * np.abs(acc_a).max())
     assert abs(c_a["tour_count"] - c_b["tour_count"]) <= 1e-3 * c_a["tour_count"] + 5
+
+
+def test_bvh_widths_give_the_same_chains(torch, R):
+    """Restore steps (wavefront, adjoint drift) through the binary and the
+    4-wide BVH: both return the same hits, so the chains agree."""
+    scene, L = S.procedural_scene(1, 64, 36, target_tris=60000, n_objects=40), 12
+    out = []
+    for width in (2, 4):
+        r = R.Renderer()
+        r.set_option("wavefront", 1)
+        r.set_option("bvh_width", width)
+        r.upload_scene(scene)
+        r.init_chains(16384, 35, R.make_params(L=L, drift="adjoint", k0=0.0, steps_per_splat=4))
+        r.step(9)
+        out.append((r.readback_state(), r.readback_accum()))
+        r.close()
+    (a, acc_a), (b, acc_b) = out
+    same = (a["killed"] == b["killed"]) & (a["pix"] == b["pix"]) & np.all(a["x"] == b["x"], 1)
+    same &= a["logp"] == b["logp"]
+    print(f"bit-identical chains {same.mean():.5f}")
+    assert same.mean() >= 0.999
+    assert np.allclose(acc_a, acc_b, rtol=1e-3, atol=1e-9 * np.abs(acc_a).max())
 
 
 @pytest.mark.parametrize("chains", [8192, 1 << 17])
