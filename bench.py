@@ -234,6 +234,7 @@ def run_ours(args, wl, rank, world, local):
     r.profile()
     prof_steps = 4
     r.step(prof_steps)
+    bprof = r.bounce_profile(wl["L"])
     prof = r.profile()
     r.set_option("profile", 0)
     wavefront = prof["trace"][1] > 0
@@ -314,6 +315,8 @@ def run_ours(args, wl, rank, world, local):
                              "node_visits_per_chain_step": ts["node_visits"] / chain_steps_stats,
                              "tri_tests_per_chain_step": ts["tri_tests"] / chain_steps_stats},
                 "phase_ms_per_step": {k: v[0] / prof_steps for k, v in prof.items() if v[1]},
+                "bounce_ms_per_step": {k: [round(x / prof_steps, 4) for x in v] for k, v in bprof.items()}
+                if wavefront else None,
                 "clocks": clocks, "gpu_launches": launches, "e2e": e2e}
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(wl, scene)

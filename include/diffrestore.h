@@ -277,6 +277,13 @@ int dr_set_option(dr_ctx* ctx, int32_t option, int32_t value);
 enum { DR_PHASES = 10 };
 int dr_get_profile(dr_ctx* ctx, double* ms, uint64_t* counts, int32_t n);
 
+/* The bounce-by-bounce part of the same profile: HOST output ms[3 *
+ * n_bounces], rows closest-hit traversal, shading, shadow-ray traversal,
+ * column k - 1 = bounce k, accumulated since the last dr_get_profile (which
+ * also clears these; this call clears nothing).  Synchronises.
+ * Errors: INVALID_ARG (n_bounces outside 1..16). */
+int dr_get_bounce_profile(dr_ctx* ctx, double* ms, int32_t n_bounces);
+
 /* One frame of the per-frame loop: n_steps Evolve steps (Alg. 2, as
  * dr_step) followed by the splat of their records (as dr_splat), issued as
  * one CUDA graph that is captured on the first call and replayed by later

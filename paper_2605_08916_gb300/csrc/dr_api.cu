@@ -93,10 +93,15 @@ struct dr_ctx {
   // optional per-phase timing (DR_OPT_PROFILE)
   bool profile = false;
   std::vector<cudaEvent_t> ev_pool;
-  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> marks;
+  struct Mark {
+    int phase, bounce;
+    cudaEvent_t begin, end;
+  };
+  std::vector<Mark> marks;
   cudaEvent_t open_ev[kPhCount] = {};
   double phase_ms[kPhCount] = {};
   unsigned long long phase_n[kPhCount] = {};
+  double bounce_ms[3][kMaxPathLen + 1] = {};  // trace, shade, shadow per bounce
 };
 
 namespace {
@@ -116,7 +121,7 @@ cudaEvent_t pooled_event(dr_ctx* c) {
 }
 
 // Records an event at the start / end of a phase on the context's stream.
-void phase_mark(void* user, int phase, bool begin) {
+void phase_mark(void* user, int phase, bool begin, int bounce) {
   dr_ctx* c = static_cast<dr_ctx*>(user);
   if (!c->profile || c->capturing) return;
   cudaEvent_t e = pooled_event(c);
@@ -125,7 +130,7 @@ void phase_mark(void* user, int phase, bool begin) {
   if (begin) {
     c->open_ev[phase] = e;
   } else if (c->open_ev[phase]) {
-    c->marks.push_back({phase, {c->open_ev[phase], e}});
+    c->marks.push_back({phase, bounce, c->open_ev[phase], e});
     c->open_ev[phase] = nullptr;
   } else {
     c->ev_pool.push_back(e);
@@ -138,12 +143,14 @@ void phase_collect(dr_ctx* c) {
   cudaStreamSynchronize(c->stream);
   for (auto& m : c->marks) {
     float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, m.second.first, m.second.second) == cudaSuccess) {
-      c->phase_ms[m.first] += ms;
-      c->phase_n[m.first] += 1;
+    if (cudaEventElapsedTime(&ms, m.begin, m.end) == cudaSuccess) {
+      c->phase_ms[m.phase] += ms;
+      c->phase_n[m.phase] += 1;
+      const int row = m.phase == kPhTrace ? 0 : m.phase == kPhShade ? 1 : m.phase == kPhShadow ? 2 : -1;
+      if (row >= 0 && m.bounce >= 1 && m.bounce <= kMaxPathLen) c->bounce_ms[row][m.bounce] += ms;
     }
-    c->ev_pool.push_back(m.second.first);
-    c->ev_pool.push_back(m.second.second);
+    c->ev_pool.push_back(m.begin);
+    c->ev_pool.push_back(m.end);
   }
   cudaGetLastError();
   c->marks.clear();
@@ -273,11 +280,11 @@ int check_device_error(dr_ctx* c) {
 int flush(dr_ctx* c) {
   if (c->rec_count == 0) return DR_OK;
   const size_t n = (size_t)c->rec_count * c->N;
-  phase_mark(c, kPhSplat, true);
+  phase_mark(c, kPhSplat, true, 0);
   SplatRec* sorted =
       sort_splat_records(c->rec, c->rec_alt, n, key_bits((long long)c->W * c->H), c->sort_scratch, c->stream);
   launch_segment_reduce(sorted, n, c->accum, (uint32_t)((size_t)c->W * c->H), c->err, c->stream);
-  phase_mark(c, kPhSplat, false);
+  phase_mark(c, kPhSplat, false, 0);
   c->launches += 5 * ((key_bits((long long)c->W * c->H) + 7) / 8) + 1;
   c->rec_count = 0;
   return check_launch("splat");
@@ -497,8 +504,8 @@ int dr_destroy(dr_ctx* c) {
   dfree(&c->step_dev);
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
   for (auto& m : c->marks) {
-    cudaEventDestroy(m.second.first);
-    cudaEventDestroy(m.second.second);
+    cudaEventDestroy(m.begin);
+    cudaEventDestroy(m.end);
   }
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   for (cudaEvent_t e : c->open_ev)
@@ -1143,6 +1150,17 @@ int dr_get_profile(dr_ctx* c, double* ms, uint64_t* counts, int32_t n) {
     c->phase_ms[i] = 0.0;
     c->phase_n[i] = 0;
   }
+  std::memset(c->bounce_ms, 0, sizeof(c->bounce_ms));
+  return DR_OK;
+}
+
+int dr_get_bounce_profile(dr_ctx* c, double* ms, int32_t n_bounces) {
+  if (!c || !ms || n_bounces < 1 || n_bounces > kMaxPathLen)
+    return fail(DR_ERR_INVALID_ARG, "dr_get_bounce_profile: bad argument");
+  DR_CUDA(cudaSetDevice(c->device));
+  phase_collect(c);
+  for (int row = 0; row < 3; ++row)
+    for (int k = 1; k <= n_bounces; ++k) ms[row * n_bounces + k - 1] = c->bounce_ms[row][k];
   return DR_OK;
 }
 

@@ -113,10 +113,13 @@ struct __align__(16) ShadowRec {
   int ex1, pad0, pad1, pad2;
 };
 // counters: [k] = rays of bounce k (1..16), [17 + k] = shadow rays of bounce
-// k, [34] = surviving chains for the adjoint pass
+// k, [34] = surviving chains for the adjoint pass, [35 + k] / [52 + k] =
+// fetch positions of the persistent trace / shadow passes of bounce k
 constexpr int kWfShadowCount0 = 17;
 constexpr int kWfAdjointCount = 34;
-constexpr int kWfCounts = 36;
+constexpr int kWfFetch0 = 35;
+constexpr int kWfShadowFetch0 = 52;
+constexpr int kWfCounts = 69;
 struct WfBuffers {
   float4* slot;        // [N][4] path state
   int* hit;            // [N] closest-hit triangle of the current ray
@@ -133,10 +136,11 @@ WfBuffers wf_carve(void* base, unsigned long long N, int L);
 enum Phase { kPhBegin = 0, kPhTrace, kPhShade, kPhShadow, kPhFinish, kPhAdjoint, kPhFused, kPhFd, kPhSplat,
              kPhOrder, kPhCount };
 struct PhaseHook {
-  void (*mark)(void* user, int phase, bool begin);
+  void (*mark)(void* user, int phase, bool begin, int bounce);
   void* user;
-  void operator()(int phase, bool begin) const {
-    if (mark) mark(user, phase, begin);
+  // bounce: 1..L for the per-bounce passes, 0 otherwise
+  void operator()(int phase, bool begin, int bounce = 0) const {
+    if (mark) mark(user, phase, begin, bounce);
   }
 };
 

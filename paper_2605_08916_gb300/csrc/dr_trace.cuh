@@ -31,13 +31,19 @@ DR_D Ray make_ray(float3 o, float3 d) {
   Ray r;
   r.o = o;
   r.d = d;
-  r.inv = f3(1.0f / d.x, 1.0f / d.y, 1.0f / d.z);
+  // a zero (or tiny) direction component gets a huge finite inverse rather
+  // than an infinite one, so that no slab product is 0 * inf = NaN
+  auto safe_inv = [](float v) { return 1.0f / (fabsf(v) > 1e-20f ? v : copysignf(1e-20f, v)); };
+  r.inv = f3(safe_inv(d.x), safe_inv(d.y), safe_inv(d.z));
   return r;
 }
 
 // Slab test of one box against [0, tmax]: the entry distance (>= 0) of a
 // hit box, or -1 for a miss.  (A miss must not compare below an infinite
 // tmax, so it is negative rather than +inf.)
+// The differences lo - o are taken before scaling (not lo / d - o / d),
+// which keeps the distances accurate when the origin lies far from the
+// scene origin; the inverse is finite (see make_ray).
 DR_D float box_entry(float3 lo, float3 hi, const Ray& r, float tmax) {
   const float tx0 = (lo.x - r.o.x) * r.inv.x, tx1 = (hi.x - r.o.x) * r.inv.x;
   const float ty0 = (lo.y - r.o.y) * r.inv.y, ty1 = (hi.y - r.o.y) * r.inv.y;
@@ -53,12 +59,20 @@ DR_D bool tri_test(float3 v0, float3 e1, float3 e2, const Ray& r, float tmin, fl
   const float3 p = cross(r.d, e2);
   const float det = dot(e1, p);
   if (det == 0.0f) return false;
-  const float inv = 1.0f / det;
+  // most candidates fail the barycentric bounds: they are rejected before
+  // the division, on the numerators scaled by |det|; the survivors take the
+  // exact test on the divided values
+  const float sg = det < 0.0f ? -1.0f : 1.0f, adet = fabsf(det);
   const float3 tv = r.o - v0;
-  const float u = dot(tv, p) * inv;
-  if (u < 0.0f || u > 1.0f) return false;
+  const float du = dot(tv, p);
+  if (du * sg < 0.0f || du * sg > adet) return false;
   const float3 q = cross(tv, e1);
-  const float v = dot(r.d, q) * inv;
+  const float dv = dot(r.d, q);
+  if (dv * sg < 0.0f || (du + dv) * sg > adet) return false;
+  const float inv = 1.0f / det;
+  const float u = du * inv;
+  if (u < 0.0f || u > 1.0f) return false;
+  const float v = dv * inv;
   if (v < 0.0f || u + v > 1.0f) return false;
   const float t = dot(e2, q) * inv;
   if (!(t > tmin && t < tmax)) return false;
@@ -121,134 +135,175 @@ DR_D void leaf_closest(const DevScene& S, int code, const Ray& r, int exclude, f
   }
 }
 
-// 4-wide closest hit: the four child boxes of a node are tested together;
-// leaves are tested on the spot, hit inner children are visited nearest
-// first (the others pushed far-to-near).
+// 4-wide traversal, one node per call so that a caller can interleave rays
+// (the persistent trace passes refill finished lanes between steps).  The
+// four child boxes of a node are tested together; leaves are tested on the
+// spot, hit inner children are visited nearest first (the others pushed
+// far-to-near).
+struct Walk4 {
+  int node, sp, budget;
+};
+
+DR_D Walk4 walk4_begin(const DevScene& S) { return Walk4{0, 0, min(2 * S.n_nodes4 + 64, kMaxNodeVisits)}; }
+
+DR_D void load_node4(const DevScene& S, int node, float3 lo[4], float3 hi[4], int4& ch) {
+  const float4* nb = S.nodes4 + (size_t)kNode4F4 * node;
+  const float4 bx0 = __ldg(nb + 0), bx1 = __ldg(nb + 1), by0 = __ldg(nb + 2), by1 = __ldg(nb + 3);
+  const float4 bz0 = __ldg(nb + 4), bz1 = __ldg(nb + 5);
+  ch = __ldg(reinterpret_cast<const int4*>(nb + 6));
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    lo[k] = f3(f4c(bx0, k), f4c(by0, k), f4c(bz0, k));
+    hi[k] = f3(f4c(bx1, k), f4c(by1, k), f4c(bz1, k));
+  }
+}
+
+// One node of a closest-hit walk; returns true when the walk is over
+// (tbest / best then hold the result).
+template <int STACK, bool STATS>
+DR_D bool closest4_step(const DevScene& S, const Ray& r, int exclude, Walk4& w, float& tbest, int& best,
+                        TraceStack<STACK> st, uint32_t* err, TraceStats* stats) {
+  if (--w.budget < 0 || w.node < 0 || w.node >= S.n_nodes4) {
+    *err |= kErrBadIndex;
+    return true;
+  }
+  float3 lo[4], hi[4];
+  int4 ch;
+  load_node4(S, w.node, lo, hi, ch);
+  if (STATS) ++stats->nodes;
+  float e[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) e[k] = box_entry(lo[k], hi[k], r, tbest);
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    if (i4c(ch, k) < 0 && e[k] >= 0.0f && e[k] <= tbest)
+      leaf_closest<STATS>(S, i4c(ch, k), r, exclude, tbest, best, err, stats);
+  bool ok[4];
+  int nc = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int c = i4c(ch, k);
+    ok[k] = c >= 0 && c != kBvh4Empty && e[k] >= 0.0f && e[k] <= tbest;
+    nc += ok[k] ? 1 : 0;
+  }
+  if (nc == 0) {
+    if (w.sp == 0) return true;
+    w.node = st.at(--w.sp);
+    return false;
+  }
+  if (w.sp + nc - 1 > STACK) {
+    *err |= kErrStackOverflow;
+    nc = STACK - w.sp + 1;
+  }
+  // near-to-far order by a five-exchange sorting network on (entry distance
+  // bits, slot) keys; entries are >= 0 so their bit patterns sort like them
+  uint32_t key[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) key[k] = ok[k] ? ((__float_as_uint(e[k]) & ~3u) | (uint32_t)k) : 0xffffffffu;
+  auto cx = [](uint32_t& x, uint32_t& y) {
+    const uint32_t lo = min(x, y), hi = max(x, y);
+    x = lo;
+    y = hi;
+  };
+  cx(key[0], key[1]);
+  cx(key[2], key[3]);
+  cx(key[0], key[2]);
+  cx(key[1], key[3]);
+  cx(key[1], key[2]);
+  w.node = i4c(ch, (int)(key[0] & 3u));
+#pragma unroll
+  for (int i = 1; i < 4; ++i)
+    if (i < nc) st.at(w.sp + nc - 1 - i) = i4c(ch, (int)(key[i] & 3u));
+  w.sp += nc - 1;
+  return false;
+}
+
+// One node of an any-hit walk in (tmin, tmax) skipping two triangle ids;
+// returns true when the walk is over, with *occluded set.
+template <int STACK, bool STATS>
+DR_D bool any4_step(const DevScene& S, const Ray& r, float tmax, int ex0, int ex1, Walk4& w, bool* occluded,
+                    TraceStack<STACK> st, uint32_t* err, TraceStats* stats) {
+  *occluded = false;
+  if (--w.budget < 0 || w.node < 0 || w.node >= S.n_nodes4) {
+    *err |= kErrBadIndex;
+    return true;
+  }
+  float3 lo[4], hi[4];
+  int4 ch;
+  load_node4(S, w.node, lo, hi, ch);
+  if (STATS) ++stats->nodes;
+  int next = -1;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int c = i4c(ch, k);
+    if (c == kBvh4Empty) continue;
+    const float e = box_entry(lo[k], hi[k], r, tmax);
+    if (!(e >= 0.0f)) continue;
+    if (c < 0) {
+      const int first = leaf_first(c);
+      int cnt = leaf_count(c);
+      if (first + cnt > S.n_tris) {
+        *err |= kErrBadIndex;
+        cnt = 0;
+      }
+      for (int i = 0; i < cnt; ++i) {
+        const float4 t0 = __ldg(S.tris4 + 3 * (first + i) + 0);
+        const float4 t1 = __ldg(S.tris4 + 3 * (first + i) + 1);
+        const float4 t2 = __ldg(S.tris4 + 3 * (first + i) + 2);
+        const int id = __float_as_int(t0.w);
+        if (STATS) ++stats->tris;
+        float th;
+        if (id != ex0 && id != ex1 && tri_test(xyz(t0), xyz(t1), xyz(t2), r, S.tmin, tmax, &th)) {
+          *occluded = true;
+          return true;
+        }
+      }
+    } else if (next < 0) {
+      next = c;
+    } else if (w.sp < STACK) {
+      st.at(w.sp++) = c;
+    } else {
+      *err |= kErrStackOverflow;
+    }
+  }
+  if (next >= 0) {
+    w.node = next;
+    return false;
+  }
+  if (w.sp == 0) return true;
+  w.node = st.at(--w.sp);
+  return false;
+}
+
 template <int STACK, bool STATS>
 DR_D int trace_closest4(const DevScene& S, const Ray& r, int exclude, float* t_hit, TraceStack<STACK> st,
                         uint32_t* err, TraceStats* stats) {
   float tbest = __int_as_float(0x7f800000);
   int best = -1;
-  int sp = 0;
-  int node = 0;
   if (!ray_finite(r.o, r.d)) {
     *err |= kErrNonFinite;
     *t_hit = tbest;
     return -1;
   }
-  int budget = min(2 * S.n_nodes4 + 64, kMaxNodeVisits);
-  while (true) {
-    if (--budget < 0 || node < 0 || node >= S.n_nodes4) {
-      *err |= kErrBadIndex;
-      break;
-    }
-    const float4* nb = S.nodes4 + (size_t)kNode4F4 * node;
-    const float4 bx0 = __ldg(nb + 0), bx1 = __ldg(nb + 1), by0 = __ldg(nb + 2), by1 = __ldg(nb + 3);
-    const float4 bz0 = __ldg(nb + 4), bz1 = __ldg(nb + 5);
-    const int4 ch = __ldg(reinterpret_cast<const int4*>(nb + 6));
-    if (STATS) ++stats->nodes;
-    float e[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-      e[k] = box_entry(f3(f4c(bx0, k), f4c(by0, k), f4c(bz0, k)), f3(f4c(bx1, k), f4c(by1, k), f4c(bz1, k)), r,
-                       tbest);
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-      if (i4c(ch, k) < 0 && e[k] >= 0.0f && e[k] <= tbest) leaf_closest<STATS>(S, i4c(ch, k), r, exclude, tbest, best, err, stats);
-    bool ok[4];
-    int nc = 0;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const int c = i4c(ch, k);
-      ok[k] = c >= 0 && c != kBvh4Empty && e[k] >= 0.0f && e[k] <= tbest;
-      nc += ok[k] ? 1 : 0;
-    }
-    if (nc == 0) {
-      if (sp == 0) break;
-      node = st.at(--sp);
-      continue;
-    }
-    if (sp + nc - 1 > STACK) {
-      *err |= kErrStackOverflow;
-      nc = STACK - sp + 1;
-    }
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      if (!ok[k]) continue;
-      int rank = 0;
-#pragma unroll
-      for (int m = 0; m < 4; ++m)
-        if (m != k && ok[m] && (e[m] < e[k] || (e[m] == e[k] && m < k))) ++rank;
-      if (rank == 0) node = i4c(ch, k);
-      else if (rank < nc) st.at(sp + nc - 1 - rank) = i4c(ch, k);
-    }
-    sp += nc - 1;
+  Walk4 w = walk4_begin(S);
+  while (!closest4_step<STACK, STATS>(S, r, exclude, w, tbest, best, st, err, stats)) {
   }
   *t_hit = tbest;
   return best;
 }
 
-// 4-wide any hit in (tmin, tmax), skipping two triangle ids.
 template <int STACK, bool STATS>
 DR_D bool trace_any4(const DevScene& S, const Ray& r, float tmax, int ex0, int ex1, TraceStack<STACK> st,
                      uint32_t* err, TraceStats* stats) {
-  int sp = 0;
-  int node = 0;
   if (!ray_finite(r.o, r.d)) {
     *err |= kErrNonFinite;
     return true;  // treated as occluded
   }
-  int budget = min(2 * S.n_nodes4 + 64, kMaxNodeVisits);
-  while (true) {
-    if (--budget < 0 || node < 0 || node >= S.n_nodes4) {
-      *err |= kErrBadIndex;
-      break;
-    }
-    const float4* nb = S.nodes4 + (size_t)kNode4F4 * node;
-    const float4 bx0 = __ldg(nb + 0), bx1 = __ldg(nb + 1), by0 = __ldg(nb + 2), by1 = __ldg(nb + 3);
-    const float4 bz0 = __ldg(nb + 4), bz1 = __ldg(nb + 5);
-    const int4 ch = __ldg(reinterpret_cast<const int4*>(nb + 6));
-    if (STATS) ++stats->nodes;
-    int next = -1;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const int c = i4c(ch, k);
-      if (c == kBvh4Empty) continue;
-      const float e = box_entry(f3(f4c(bx0, k), f4c(by0, k), f4c(bz0, k)), f3(f4c(bx1, k), f4c(by1, k), f4c(bz1, k)),
-                                r, tmax);
-      if (!(e >= 0.0f)) continue;
-      if (c < 0) {
-        const int first = leaf_first(c);
-        int cnt = leaf_count(c);
-        if (first + cnt > S.n_tris) {
-          *err |= kErrBadIndex;
-          cnt = 0;
-        }
-        for (int i = 0; i < cnt; ++i) {
-          const float4 t0 = __ldg(S.tris4 + 3 * (first + i) + 0);
-          const float4 t1 = __ldg(S.tris4 + 3 * (first + i) + 1);
-          const float4 t2 = __ldg(S.tris4 + 3 * (first + i) + 2);
-          const int id = __float_as_int(t0.w);
-          if (STATS) ++stats->tris;
-          float th;
-          if (id != ex0 && id != ex1 && tri_test(xyz(t0), xyz(t1), xyz(t2), r, S.tmin, tmax, &th)) return true;
-        }
-      } else if (next < 0) {
-        next = c;
-      } else if (sp < STACK) {
-        st.at(sp++) = c;
-      } else {
-        *err |= kErrStackOverflow;
-      }
-    }
-    if (next >= 0) {
-      node = next;
-      continue;
-    }
-    if (sp == 0) break;
-    node = st.at(--sp);
+  Walk4 w = walk4_begin(S);
+  bool occ = false;
+  while (!any4_step<STACK, STATS>(S, r, tmax, ex0, ex1, w, &occ, st, err, stats)) {
   }
-  return false;
+  return occ;
 }
 
 // Binary-BVH closest hit with t in (tmin, inf), skipping triangle `exclude`

@@ -29,12 +29,8 @@ constexpr int kWfStack = kTraversalStack;
 // resident blocks per SM the traversal passes are compiled for (register cap)
 constexpr int kWfTraceMinBlocks = 10;
 // the 4-wide traversal holds four child boxes at once: fewer resident
-// blocks, more registers per thread
-#ifndef DR_WF_TRACE4_MIN_BLOCKS
-#define DR_WF_TRACE4_MIN_BLOCKS 6
-#endif
-constexpr int kWfTrace4MinBlocks = DR_WF_TRACE4_MIN_BLOCKS;
-constexpr int trace_min_blocks(int width) { return width == 4 ? kWfTrace4MinBlocks : kWfTraceMinBlocks; }
+// blocks, more registers per thread (measured: 7 beats 6 and 8)
+constexpr int kWfTrace4MinBlocks = 7;
 
 // 64-B path slot per chain: (o, ppdf), (d, prev tri), (beta, prev_delta |
 // nseg << 8), (f, pixel)
@@ -88,8 +84,9 @@ __global__ void __launch_bounds__(kWfThreads) wf_begin(StepArgs a, WfBuffers w) 
   if (blockIdx.x == 0 && threadIdx.x == 0) w.counts[1] = (uint32_t)a.N;  // bounce 1: every chain
 }
 
-template <bool STATS, int WIDTH>
-__global__ void __launch_bounds__(kWfThreads, trace_min_blocks(WIDTH)) wf_trace(StepArgs a, WfBuffers w, int k) {
+// binary-BVH trace pass: one closest-hit ray per thread, grid-stride
+template <bool STATS>
+__global__ void __launch_bounds__(kWfThreads, kWfTraceMinBlocks) wf_trace(StepArgs a, WfBuffers w, int k) {
   extern __shared__ int smem[];
   TraceStack<kWfStack> st{smem + threadIdx.x, (int)blockDim.x};
   const uint32_t n = w.counts[k];
@@ -101,9 +98,128 @@ __global__ void __launch_bounds__(kWfThreads, trace_min_blocks(WIDTH)) wf_trace(
     const unsigned long long j = q ? q[t] : t;
     const float4 o = w.slot[4 * j + 0], d = w.slot[4 * j + 1];
     float th;
-    w.hit[j] = trace_closest<kWfStack, STATS, WIDTH>(a.S, make_ray(xyz(o), xyz(d)), __float_as_int(d.w), &th, st,
+    w.hit[j] = trace_closest<kWfStack, STATS, 2>(a.S, make_ray(xyz(o), xyz(d)), __float_as_int(d.w), &th, st,
                                                      &err, &stats);
     ++rays;
+  }
+  add_counts(a.rays, rays);
+  if (STATS) {
+    add_counts(a.node_visits, stats.nodes);
+    add_counts(a.tri_tests, stats.tris);
+  }
+  if (err) atomicOr(a.err, err);
+}
+
+// Persistent 4-wide trace passes with dynamic ray fetch: a warp keeps
+// stepping its lanes' walks one node at a time and, whenever fewer than
+// kRefillBelow lanes still hold a ray, refills the idle lanes from the queue
+// with one atomic per warp.  A warp's time is then set by its total work
+// rather than by its slowest ray.
+constexpr int kRefillBelow = 24;  // measured: 24-28 of 32 beat 12 and 20
+constexpr unsigned kFull = 0xffffffffu;
+
+// Hands the idle lanes of a warp (mask `idle`) consecutive queue positions;
+// returns this lane's position (valid for idle lanes) and whether the queue
+// of n entries is now drained.  All 32 lanes call it together.
+DR_D uint32_t warp_fetch(uint32_t* ctr, unsigned idle, uint32_t n, bool& drained) {
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(idle) - 1;
+  uint32_t base = 0;
+  if (lane == leader) base = atomicAdd(ctr, (uint32_t)__popc(idle));
+  base = __shfl_sync(kFull, base, leader);
+  if (base + (uint32_t)__popc(idle) >= n) drained = true;
+  return base + __popc(idle & ((1u << lane) - 1u));
+}
+
+// One traversal pass of the 4-wide path: the closest-hit rays of bounce k
+// (n_ray of them; none when k > L) and the shadow rays of bounce k - 1
+// (n_shadow; none when k = 1) share one fetch counter, closest-hit rays
+// first.  The two sets touch disjoint data (hit[] and the ray state vs. the
+// path's f and the shadow-visibility tape flag), so one launch replaces two
+// and each bounce pays the latency of its slowest ray once.
+template <bool STATS>
+__global__ void __launch_bounds__(kWfThreads, kWfTrace4MinBlocks) wf_traverse(StepArgs a, WfBuffers w, int k) {
+  extern __shared__ int smem[];
+  TraceStack<kWfStack> st{smem + threadIdx.x, (int)blockDim.x};
+  const uint32_t n_ray = k <= a.L ? w.counts[k] : 0u;
+  const uint32_t n_shadow = k >= 2 ? w.counts[kWfShadowCount0 + k - 1] : 0u;
+  const uint32_t n = n_ray + n_shadow;
+  const uint32_t* q = k == 1 ? nullptr : w.queue[k & 1];
+  uint32_t* ctr = &w.counts[kWfFetch0 + k];
+  uint32_t err = 0;
+  TraceStats stats{0u, 0u};
+  unsigned long long rays = 0;
+  bool has = false, drained = false, shadow = false;
+  uint32_t j = 0, t = 0;
+  int ex0 = -1, ex1 = -1, best = -1;
+  float tlim = 0.0f;  // closest hit so far, or the shadow ray's tmax
+  Ray r;
+  Walk4 wk{0, 0, 0};
+  while (true) {
+    if (!drained) {
+      const unsigned idle = __ballot_sync(kFull, !has);
+      if (idle) {
+        const uint32_t tn = warp_fetch(ctr, idle, n, drained);
+        if (!has && tn < n) {
+          shadow = tn >= n_ray;
+          if (shadow) {
+            t = tn - n_ray;
+            const ShadowRec& sr = w.shadow[t];
+            const float4 o = sr.o_tmax, d = sr.wi_chain;
+            r = make_ray(xyz(o), xyz(d));
+            tlim = o.w;
+            ex0 = __float_as_int(sr.contrib_ex.w);
+            ex1 = sr.ex1;
+          } else {
+            j = q ? q[tn] : tn;
+            const float4 o = w.slot[4 * (size_t)j + 0], d = w.slot[4 * (size_t)j + 1];
+            r = make_ray(xyz(o), xyz(d));
+            ex0 = __float_as_int(d.w);
+            tlim = __int_as_float(0x7f800000);
+            best = -1;
+          }
+          wk = walk4_begin(a.S);
+          ++rays;
+          if (ray_finite(r.o, r.d)) {
+            has = true;
+          } else {
+            err |= kErrNonFinite;  // no hit; a shadow ray counts as occluded
+            if (!shadow) w.hit[j] = -1;
+          }
+        }
+      }
+    }
+    if (__ballot_sync(kFull, has) == 0) {
+      if (drained) break;
+      continue;
+    }
+    while (true) {
+      if (has) {
+        if (!shadow) {
+          if (closest4_step<kWfStack, STATS>(a.S, r, ex0, wk, tlim, best, st, &err, &stats)) {
+            w.hit[j] = best;
+            has = false;
+          }
+        } else {
+          bool occ;
+          if (any4_step<kWfStack, STATS>(a.S, r, tlim, ex0, ex1, wk, &occ, st, &err, &stats)) {
+            has = false;
+            if (!occ) {
+              const ShadowRec& sr = w.shadow[t];
+              const unsigned long long c = (unsigned long long)__float_as_int(sr.wi_chain.w);
+              float4 f = w.slot[4 * c + 3];
+              f.x += sr.contrib_ex.x;
+              f.y += sr.contrib_ex.y;
+              f.z += sr.contrib_ex.z;
+              w.slot[4 * c + 3] = f;
+              GlobalTape{w.tape, a.N, c}.or_flags(k - 2, kFNeeVis);
+            }
+          }
+        }
+      }
+      const unsigned act = __ballot_sync(kFull, has);
+      if (act == 0 || (!drained && __popc(act) < kRefillBelow)) break;
+    }
   }
   add_counts(a.rays, rays);
   if (STATS) {
@@ -155,8 +271,9 @@ __global__ void __launch_bounds__(kWfThreads) wf_shade(StepArgs a, WfBuffers w, 
   }
 }
 
-template <bool STATS, int WIDTH>
-__global__ void __launch_bounds__(kWfThreads, trace_min_blocks(WIDTH)) wf_shadow(StepArgs a, WfBuffers w, int k) {
+// binary-BVH shadow pass of bounce k
+template <bool STATS>
+__global__ void __launch_bounds__(kWfThreads, kWfTraceMinBlocks) wf_shadow(StepArgs a, WfBuffers w, int k) {
   extern __shared__ int smem[];
   TraceStack<kWfStack> st{smem + threadIdx.x, (int)blockDim.x};
   const uint32_t n = w.counts[kWfShadowCount0 + k];
@@ -167,7 +284,7 @@ __global__ void __launch_bounds__(kWfThreads, trace_min_blocks(WIDTH)) wf_shadow
     const ShadowRec r = w.shadow[t];
     const unsigned long long j = (unsigned long long)__float_as_int(r.wi_chain.w);
     ++rays;
-    if (!trace_any<kWfStack, STATS, WIDTH>(a.S, make_ray(xyz(r.o_tmax), xyz(r.wi_chain)), r.o_tmax.w,
+    if (!trace_any<kWfStack, STATS, 2>(a.S, make_ray(xyz(r.o_tmax), xyz(r.wi_chain)), r.o_tmax.w,
                                            __float_as_int(r.contrib_ex.w), r.ex1, st, &err, &stats)) {
       float4 f = w.slot[4 * j + 3];
       f.x += r.contrib_ex.x;
@@ -266,6 +383,18 @@ WfBuffers wf_carve(void* base, unsigned long long N, int L) {
   return w;
 }
 
+// resident blocks per SM of the persistent trace passes (the smaller of
+// the two kernels' occupancies), computed once
+int fetch_blocks_per_sm(size_t smem) {
+  static int cached = 0;
+  if (cached == 0) {
+    int b0 = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b0, wf_traverse<false>, kWfThreads, smem);
+    cached = std::max(1, b0);
+  }
+  return cached;
+}
+
 int launch_wavefront_step(const StepArgs& a, const WfBuffers& w, bool stats, int n_sm, const PhaseHook& hook,
                           cudaStream_t s) {
   if (a.N == 0) return 0;
@@ -273,35 +402,45 @@ int launch_wavefront_step(const StepArgs& a, const WfBuffers& w, bool stats, int
   const unsigned g = grid_for(a.N, max_blocks);
   const size_t smem = (size_t)kWfStack * kWfThreads * sizeof(int);
   const bool wide = a.S.nodes4 != nullptr;
+  // persistent passes: as many blocks as stay resident
+  const unsigned g4 = (unsigned)(n_sm * fetch_blocks_per_sm(smem));
   int launches = 0;
   cudaMemsetAsync(w.counts, 0, kWfCounts * sizeof(uint32_t), s);
   hook(kPhBegin, true);
   wf_begin<<<g, kWfThreads, 0, s>>>(a, w);
   hook(kPhBegin, false);
   launches += 2;
-  for (int k = 1; k <= a.L; ++k) {
-    hook(kPhTrace, true);
-    if (wide) {
-      if (stats) wf_trace<true, 4><<<g, kWfThreads, smem, s>>>(a, w, k);
-      else wf_trace<false, 4><<<g, kWfThreads, smem, s>>>(a, w, k);
-    } else {
-      if (stats) wf_trace<true, 2><<<g, kWfThreads, smem, s>>>(a, w, k);
-      else wf_trace<false, 2><<<g, kWfThreads, smem, s>>>(a, w, k);
+  if (wide) {
+    // traverse(k) = closest-hit rays of bounce k + shadow rays of bounce
+    // k - 1; the last launch (k = L + 1) carries the final shadow rays
+    for (int k = 1; k <= a.L + 1; ++k) {
+      hook(k <= a.L ? kPhTrace : kPhShadow, true, k <= a.L ? k : a.L);
+      if (stats) wf_traverse<true><<<g4, kWfThreads, smem, s>>>(a, w, k);
+      else wf_traverse<false><<<g4, kWfThreads, smem, s>>>(a, w, k);
+      hook(k <= a.L ? kPhTrace : kPhShadow, false, k <= a.L ? k : a.L);
+      launches += 1;
+      if (k <= a.L) {
+        hook(kPhShade, true, k);
+        wf_shade<<<g, kWfThreads, 0, s>>>(a, w, k);
+        hook(kPhShade, false, k);
+        launches += 1;
+      }
     }
-    hook(kPhTrace, false);
-    hook(kPhShade, true);
-    wf_shade<<<g, kWfThreads, 0, s>>>(a, w, k);
-    hook(kPhShade, false);
-    hook(kPhShadow, true);
-    if (wide) {
-      if (stats) wf_shadow<true, 4><<<g, kWfThreads, smem, s>>>(a, w, k);
-      else wf_shadow<false, 4><<<g, kWfThreads, smem, s>>>(a, w, k);
-    } else {
-      if (stats) wf_shadow<true, 2><<<g, kWfThreads, smem, s>>>(a, w, k);
-      else wf_shadow<false, 2><<<g, kWfThreads, smem, s>>>(a, w, k);
+  } else {
+    for (int k = 1; k <= a.L; ++k) {
+      hook(kPhTrace, true, k);
+      if (stats) wf_trace<true><<<g, kWfThreads, smem, s>>>(a, w, k);
+      else wf_trace<false><<<g, kWfThreads, smem, s>>>(a, w, k);
+      hook(kPhTrace, false, k);
+      hook(kPhShade, true, k);
+      wf_shade<<<g, kWfThreads, 0, s>>>(a, w, k);
+      hook(kPhShade, false, k);
+      hook(kPhShadow, true, k);
+      if (stats) wf_shadow<true><<<g, kWfThreads, smem, s>>>(a, w, k);
+      else wf_shadow<false><<<g, kWfThreads, smem, s>>>(a, w, k);
+      hook(kPhShadow, false, k);
+      launches += 3;
     }
-    hook(kPhShadow, false);
-    launches += 3;
   }
   hook(kPhFinish, true);
   wf_finish<<<g, kWfThreads, 0, s>>>(a, w);

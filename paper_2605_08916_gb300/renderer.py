@@ -119,6 +119,14 @@ class Renderer:
         created on a non-default torch stream)."""
         call("dr_frame", self.h, int(n_steps))
 
+    def bounce_profile(self, n_bounces):
+        """Per-bounce milliseconds of the trace / shade / shadow passes since the
+        last profile() call: dict of three lists of n_bounces values."""
+        ms = (C.c_double * (3 * n_bounces))()
+        call("dr_get_bounce_profile", self.h, ms, int(n_bounces))
+        v = list(ms)
+        return {"trace": v[:n_bounces], "shade": v[n_bounces:2 * n_bounces], "shadow": v[2 * n_bounces:]}
+
     def profile(self):
         """Per-phase device milliseconds since the last call (DR_OPT_PROFILE)."""
         ms = (C.c_double * _lib.DR_PHASES)()

@@ -377,9 +377,18 @@ def test_profile_reports_phases(torch, R):
     r.profile()
     r.step(3)
     r.splat()
+    b = r.bounce_profile(6)
     p = r.profile()
     assert p["trace"][1] == 3 * 6 and p["trace"][0] > 0
     assert p["adjoint"][1] == 3 and p["splat"][1] >= 1
+    # 4-wide BVH: the trace row holds the combined passes (closest-hit rays
+    # of bounce k and shadow rays of bounce k - 1), the shadow row the last
+    # bounce's shadow rays
+    assert min(b["trace"]) > 0 and min(b["shade"]) > 0 and b["shadow"][-1] > 0
+    for name in ("trace", "shade", "shadow"):
+        assert len(b[name]) == 6
+        assert abs(sum(b[name]) - p[name][0]) <= 1e-6 * p[name][0] + 1e-9
+    assert sum(r.bounce_profile(6)["trace"]) == 0.0  # cleared by profile()
     r.close()
 
 
