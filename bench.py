@@ -240,7 +240,8 @@ def run_ours(args, wl, rank, world, local):
     wavefront = prof["trace"][1] > 0
     assert wavefront == wf_expected, "execution mode differs from the one the roofline bytes assume"
     if wavefront:
-        k_name = "wf_trace + wf_shadow (BVH traversal passes)"
+        k_name = ("wf_traverse (4-wide BVH traversal passes)" if wide
+                  else "wf_trace + wf_shadow (binary BVH traversal passes)")
         k_ms = (prof["trace"][0] + prof["shadow"][0]) / prof_steps
         k_bytes = trav_bytes
     else:
