@@ -41,7 +41,7 @@ UNIT = "chain-steps/s"
 
 WORKLOADS = {
     "procedural-1m-720p": dict(scene=lambda: S.procedural_scene(1, 1280, 720), L=12, chains=1 << 20,
-                               drift="adjoint", spp=8, cpu_chains=64),
+                               drift="adjoint", spp=4, cpu_chains=64),
     "cornell-glossy-256": dict(scene=lambda: S.cornell_box(1, 256, 256, glossy=True), L=8, chains=65536,
                                drift="adjoint", spp=16, cpu_chains=256),
     "caustic-20k-512": dict(scene=lambda: S.caustic_scene(1, 512, 512), L=10, chains=262144, drift="adjoint",
@@ -209,8 +209,12 @@ def run_ours(args, wl, rank, world, local):
     r.set_option("wavefront", args.wavefront)
     r.set_option("bvh_width", args.bvh_width)
     r.upload_scene(scene)
+    stream.synchronize()
+    t_init = time.perf_counter()
     r.init_chains(N, seed, params)
     stream.synchronize()
+    t_init = time.perf_counter() - t_init
+    log(f"init (evaluation + p_lambda estimate + clock) {t_init * 1e3:.1f} ms")
     bvh4 = r.bvh4_info() if args.bvh_width != 2 else None
     log(f"uploaded + init {N} chains; bvh {r.bvh_info()}; 4-wide {bvh4}")
     # traversal statistics (separate kernel instantiation, untimed)
@@ -297,6 +301,7 @@ def run_ours(args, wl, rank, world, local):
     if rank == 0:
         log(f"timed {steps} steps in {n_frames} frames: {total_ms:.1f} ms")
         e2e = None if args.no_e2e else run_e2e(R, scene, wl, N, steps, local, stream)
+        rel = None if args.no_relmse else run_relmse33(R, scene, wl, local)
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
                 "warmup": args.warmup, "ms_per_step": t_max / steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -318,7 +323,7 @@ def run_ours(args, wl, rank, world, local):
                 "phase_ms_per_step": {k: v[0] / prof_steps for k, v in prof.items() if v[1]},
                 "bounce_ms_per_step": {k: [round(x / prof_steps, 4) for x in v] for k, v in bprof.items()}
                 if wavefront else None,
-                "clocks": clocks, "gpu_launches": launches, "e2e": e2e}
+                "clocks": clocks, "gpu_launches": launches, "e2e": e2e, "relmse_33ms": rel}
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(wl, scene)
             log("cpu baseline done")
@@ -327,6 +332,89 @@ def run_ours(args, wl, rank, world, local):
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+BUDGET_MS = 1000.0 / 30.0
+
+
+def relmse(img, ref):
+    """mean over pixels and channels of (I - R)^2 / (R^2 + 1e-2)"""
+    return float(np.mean((img - ref) ** 2 / (ref ** 2 + 1e-2)))
+
+
+def run_relmse33(R, scene, wl, local, seeds=16):
+    """Image relMSE after one 33.3 ms frame budget, from scratch (chain init
+    with the p_lambda estimate, the steps, the splat and the resolve all
+    inside the budget), for the plain form (finite-difference drift, one
+    launch sequence per step) and the batched form (adjoint drift,
+    bounce-by-bounce passes, all steps of the frame in one CUDA graph).
+    Each form takes the largest chain count (halving from the workload's)
+    that fits at least two steps; the steps are calibrated to the budget.
+    Reference: stratified path tracing of the same f."""
+    import torch
+    stream = torch.cuda.Stream(device=torch.device("cuda", local))
+    rr = R.Renderer(local, stream)
+    rr.upload_scene(scene)
+    t0 = time.perf_counter()
+    rr.pt_render(wl["L"], 4, seed=99)
+    stream.synchronize()
+    per_spp = (time.perf_counter() - t0) / 4
+    spp_ref = int(max(64, min(4096, 2 ** int(np.log2(max(1.0, 20.0 / max(per_spp, 1e-6)))))))
+    t0 = time.perf_counter()
+    ref = rr.pt_render(wl["L"], spp_ref, seed=12345).cpu().numpy()
+    t_ref = time.perf_counter() - t0
+    rr.close()
+    log(f"relmse: reference PT {spp_ref} spp in {t_ref:.1f} s")
+    out = {"budget_ms": BUDGET_MS, "seeds": seeds, "reference": f"path tracing, {spp_ref} spp, same f",
+           "metric": "mean over pixels and channels of (I-R)^2/(R^2+1e-2)"}
+    img = torch.empty((scene.height, scene.width, 3), dtype=torch.float32, device=torch.device("cuda", local))
+    for form in ("plain_fd", "batched_adjoint"):
+        drift = "fd" if form == "plain_fd" else "adjoint"
+        r = R.Renderer(local, stream)
+        r.upload_scene(scene)
+        if form == "plain_fd":
+            r.set_option("wavefront", 0)
+        F = wl["spp"]
+        prm = R.make_params(L=wl["L"], drift=drift, rb=True, k0=0.0, steps_per_splat=F)
+
+        def run(n, steps, seed):
+            stream.synchronize()
+            t0 = time.perf_counter()
+            r.init_chains(n, seed, prm)
+            if form == "plain_fd":
+                r.step(steps)
+            else:
+                r.frame(steps)
+            r.resolve(img)
+            stream.synchronize()
+            return (time.perf_counter() - t0) * 1e3
+
+        n = wl["chains"]
+        while True:
+            for steps in (2, 4):            # warm-up (graph capture), then calibration
+                run(n, steps, 7)
+            ta = min(run(n, 2, 8 + k) for k in range(2))
+            tb = min(run(n, 4, 10 + k) for k in range(2))
+            t_step = max((tb - ta) / 2, 1e-3)
+            t_fixed = ta - 2 * t_step
+            steps = int((0.97 * BUDGET_MS - t_fixed) / t_step)
+            if steps >= 2 or n <= 4096:
+                break
+            n //= 2
+        steps = max(1, steps)
+        run(n, steps, 9)                    # capture at the final step count
+        errs, times = [], []
+        for k in range(seeds):
+            times.append(run(n, steps, 1000 + k))
+            errs.append(relmse(img.cpu().numpy().astype(np.float64), ref))
+        r.close()
+        out[form] = {"chains": n, "steps": steps, "ms_per_step": t_step, "ms_fixed": t_fixed,
+                     "frame_ms_mean": statistics.mean(times), "frame_ms_max": max(times),
+                     "relmse_mean": statistics.mean(errs), "relmse_sd": statistics.stdev(errs)}
+        log(f"relmse {form}: {n} chains x {steps} steps, frame {statistics.mean(times):.1f} ms, "
+            f"relMSE {statistics.mean(errs):.4g} +- {statistics.stdev(errs):.2g}")
+    out["ratio_plain_over_batched"] = out["plain_fd"]["relmse_mean"] / out["batched_adjoint"]["relmse_mean"]
+    return out
 
 
 def run_e2e(R, scene, wl, N, steps, local, stream):
@@ -368,6 +456,7 @@ def main():
     ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end run (profiling cases)")
+    ap.add_argument("--no-relmse", action="store_true", help="skip the 33 ms image relMSE comparison")
     ap.add_argument("--chains", type=int, default=0, help="override the workload's chain count (profiling cases)")
     ap.add_argument("--wavefront", type=int, default=-1, choices=[-1, 0, 1],
                     help="bounce-by-bounce execution over compacted path queues: 1 on, 0 fused kernel, "

@@ -84,12 +84,12 @@ struct dr_ctx {
   size_t wf_cap = 0;
   int n_sm = 152;
   // graph-captured frames (dr_frame)
-  uint32_t* step_dev = nullptr;  // device copy of the step index while replaying
+  FrameParams* frame_dev = nullptr;  // what a replayed frame graph reads (step, RNG key, k0)
   bool capturing = false;
   cudaGraphExec_t gexec = nullptr;
   std::vector<unsigned long long> graph_key;  // what the captured launches depend on
   unsigned long long graph_launches = 0;
-  uint32_t step_host = 0;
+  FrameParams frame_host{};  // source of the per-launch copy into frame_dev
   // optional per-phase timing (DR_OPT_PROFILE)
   bool profile = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -367,12 +367,12 @@ int one_step(dr_ctx* c, bool init) {
   StepArgs a = step_args(c);
   a.init = init ? 1 : 0;
   a.step = c->step;
-  a.step_ptr = c->capturing ? c->step_dev : nullptr;
+  a.fp = c->capturing ? c->frame_dev : nullptr;
   a.rec = c->rec + (size_t)c->rec_count * c->N;
   a.p_partial = init ? c->p_partial : nullptr;
   a.plen = c->plen;
   const PhaseHook hook{phase_mark, c};
-  if (!init && use_wavefront(c)) {
+  if (use_wavefront(c)) {
     DR_TRY(ensure_wavefront_buffers(c));
     const WfBuffers w = wf_carve(c->wf_mem, c->N, c->prm.max_path_len);
     c->launches += launch_wavefront_step(a, w, c->stats, c->n_sm, hook, c->stream);
@@ -398,7 +398,7 @@ int one_step(dr_ctx* c, bool init) {
   }
   c->rec_count++;
   if (c->capturing) {
-    launch_advance_step(c->step_dev, c->stream);
+    launch_advance_step(&c->frame_dev->step, c->stream);
     c->launches += 1;
   }
   return DR_OK;
@@ -478,7 +478,7 @@ int dr_create(dr_ctx** out, int device, void* cuda_stream) {
   int r = dalloc(&c->counters, 4);
   if (r == DR_OK) r = dalloc(&c->err, 1);
   if (r == DR_OK) r = dalloc(&c->p_sum, 1);
-  if (r == DR_OK) r = dalloc(&c->step_dev, 1);
+  if (r == DR_OK) r = dalloc(&c->frame_dev, 1);
   if (r != DR_OK) {
     dr_destroy(c);
     return r;
@@ -501,7 +501,7 @@ int dr_destroy(dr_ctx* c) {
   if (c->wf_mem) cudaFree(c->wf_mem); dfree(&c->rec); dfree(&c->rec_alt);
   if (c->sort_scratch) cudaFree(c->sort_scratch);
   dfree(&c->accum); dfree(&c->counters); dfree(&c->p_partial); dfree(&c->p_sum); dfree(&c->err);
-  dfree(&c->step_dev);
+  dfree(&c->frame_dev);
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
   for (auto& m : c->marks) {
     cudaEventDestroy(m.begin);
@@ -774,6 +774,38 @@ int dr_chains_init(dr_ctx* c, uint64_t n_chains, uint64_t seed, uint32_t frame, 
   DR_CUDA(cudaMemsetAsync(c->counters, 0, 4 * 8, s));
   DR_CUDA(cudaMemsetAsync(c->err, 0, 4, s));
   c->p_lambda = 0.0;
+  if (prm->k0 <= 0.0 && use_wavefront(c)) {
+    // one evaluation serves the p_lambda estimate and Init: evaluate (with
+    // the adjoint for every chain), reduce p, then run the clock
+    DR_TRY(ensure_wavefront_buffers(c));
+    const WfBuffers w = wf_carve(c->wf_mem, c->N, c->prm.max_path_len);
+    float* p_tmp = reinterpret_cast<float*>(w.hit);  // free once the last bounce is shaded
+    StepArgs a = step_args(c);
+    a.init = 1;
+    a.step = 0;
+    a.rec = c->rec;
+    a.plen = c->plen;
+    const PhaseHook hook{phase_mark, c};
+    c->launches += launch_wavefront_step(a, w, c->stats, c->n_sm, hook, s, kWfInitEval, p_tmp);
+    launch_block_sums(p_tmp, n_chains, c->p_partial, s);
+    const int nb = (int)((n_chains + step_block_size() - 1) / step_block_size());
+    launch_sum_doubles(c->p_partial, nb, c->p_sum, s);
+    c->launches += 2;
+    DR_TRY(check_launch("init evaluation"));
+    double sum = 0.0;
+    DR_CUDA(cudaMemcpyAsync(&sum, c->p_sum, 8, cudaMemcpyDeviceToHost, s));
+    DR_CUDA(cudaStreamSynchronize(s));
+    c->p_lambda = sum / (double)n_chains;
+    if (!(c->p_lambda > 0.0) || !std::isfinite(c->p_lambda))
+      return fail(DR_ERR_STATE, "dr_chains_init: estimated p_lambda is not positive");
+    c->k0 = c->p_lambda / ((double)prm->m * (double)prm->dt);
+    a.k0 = c->k0;
+    c->launches += launch_wavefront_step(a, w, c->stats, c->n_sm, hook, s, kWfInitClock, p_tmp);
+    DR_TRY(check_launch("init clock"));
+    c->inited = true;
+    c->rec_count = 1;
+    return check_device_error(c);
+  }
   if (prm->k0 > 0.0) {
     c->k0 = prm->k0;
   } else {
@@ -1063,11 +1095,10 @@ namespace {
 
 // Everything a captured frame's launches depend on: buffers, sizes,
 // parameters and options.  A frame is recaptured when any of it changes.
+// The step index, seed, frame number and k0 are not part of it: the graph
+// reads them from device memory, so re-initialised chains replay it.
 std::vector<unsigned long long> frame_key(const dr_ctx* c, uint32_t n_steps) {
   auto P = [](const void* p) { return (unsigned long long)(uintptr_t)p; };
-  double k0 = c->k0;
-  unsigned long long k0b;
-  std::memcpy(&k0b, &k0, 8);
   unsigned long long prm[6];
   std::memset(prm, 0, sizeof(prm));
   std::memcpy(prm, &c->prm, std::min(sizeof(prm), sizeof(c->prm)));
@@ -1075,7 +1106,7 @@ std::vector<unsigned long long> frame_key(const dr_ctx* c, uint32_t n_steps) {
                                        P(c->x), P(c->score), P(c->killed), P(c->logp), P(c->plen), P(c->rec),
                                        P(c->rec_alt), P(c->sort_scratch), P(c->accum), P(c->wf_mem), P(c->nodes),
                                        P(c->nodes4), (unsigned long long)c->bvh_width, P(c->tris), P(c->surf), P(c->mats), P(c->lights), P(c->nrm), P(c->mw),
-                                       c->seed, c->frame, k0b, c->rec_cap, (unsigned long long)c->wavefront,
+                                       c->rec_cap, (unsigned long long)c->wavefront,
                                        (unsigned long long)c->work_order, (unsigned long long)c->stats,
                                        (unsigned long long)c->nt, (unsigned long long)c->n_lights, P(c->stream),
                                        c->target_gen};
@@ -1129,8 +1160,8 @@ int dr_frame(dr_ctx* c, uint32_t n_steps) {
     c->graph_key = key;
   }
   // the graph reads the step index from device memory and advances it
-  c->step_host = c->step + 1;
-  DR_CUDA(cudaMemcpyAsync(c->step_dev, &c->step_host, 4, cudaMemcpyHostToDevice, c->stream));
+  c->frame_host = FrameParams{c->step + 1, (uint32_t)c->seed, (uint32_t)(c->seed >> 32), c->frame, c->k0};
+  DR_CUDA(cudaMemcpyAsync(c->frame_dev, &c->frame_host, sizeof(FrameParams), cudaMemcpyHostToDevice, c->stream));
   DR_CUDA(cudaGraphLaunch(c->gexec, c->stream));
   c->step += n_steps;
   c->launches += c->graph_launches;

@@ -73,6 +73,15 @@ int bvh4_emit(const float4* d_nodes2, const float4* d_tris2, int n_inner, int n_
 // ---------------------------------------------------------------- chains
 enum Drift { kDriftNone = 0, kDriftFD = 1, kDriftAdjoint = 2 };
 
+// What a replayed CUDA graph reads from device memory instead of its
+// captured launch arguments, so that one graph serves every step, seed,
+// frame and k0: the step index (advanced on the device after each step),
+// the Philox key and frame, and the killing-rate constant.
+struct FrameParams {
+  uint32_t step, seed_lo, seed_hi, frame;
+  double k0;
+};
+
 struct StepArgs {
   DevScene S;
   DevMixture M;
@@ -85,7 +94,7 @@ struct StepArgs {
   unsigned long long N;
   int d, L;
   uint32_t step;
-  const uint32_t* step_ptr;  // non-null: read the step index from device memory (graph replay)
+  const FrameParams* fp;  // non-null: step, RNG key and k0 from device memory (graph replay)
   Rng rng;
   float stddev, gamma_tilde, h, eps;
   double k0;
@@ -145,9 +154,14 @@ struct PhaseHook {
 };
 
 // One adjoint-drift Restore step on a scene, bounce by bounce; returns the
-// number of kernels (and memsets) issued.
+// number of kernels (and memsets) issued.  Modes: kWfStep (the step), and
+// the two halves of a single-pass initialisation whose k0 is estimated from
+// the same evaluation: kWfInitEval (Init's evaluation; p of every chain to
+// p_out, the adjoint for every chain, no clock) then kWfInitClock (the
+// kill clock and records from the stored path results, once k0 is known).
+enum WfMode { kWfStep = 0, kWfInitEval = 1, kWfInitClock = 2 };
 int launch_wavefront_step(const StepArgs& a, const WfBuffers& w, bool stats, int n_sm, const PhaseHook& hook,
-                          cudaStream_t s);
+                          cudaStream_t s, WfMode mode = kWfStep, float* p_out = nullptr);
 // step index += 1 on the device (graph replay)
 void launch_advance_step(uint32_t* step, cudaStream_t s);
 
@@ -190,6 +204,8 @@ void launch_trace(const DevScene& S, const float* rays, long long n, int exclude
                   cudaStream_t s);
 void launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, long long n, cudaStream_t s);
 void launch_sum_doubles(const double* in, int n, double* out, cudaStream_t s);
+// partial[b] = FP64 sum of p over the fused step kernel's block b, in its order
+void launch_block_sums(const float* p, unsigned long long N, double* partial, cudaStream_t s);
 // Stratified path tracing of the same f: part [n_chunks][W*H][3] FP64
 // scratch, mean [W*H][3] = per-pixel mean of f / (W H) over spp samples.
 void launch_pt(const DevScene& S, int L, uint32_t spp, int n_chunks, Rng rng, double* part, double* mean,

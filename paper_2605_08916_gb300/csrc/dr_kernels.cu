@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(kStepThreads) step_kernel(StepArgs a) {
     int pix;
     float p;
     float3 f;
-    const U4 rc = a.rng.draw(step, cj, 0u, kClock);
+    const U4 rc = rng_of(a).draw(step, cj, 0u, kClock);
     const float u1 = u01(rc.a), u2 = u01(rc.b);
     bool killed = false;
     float wt = 0.0f;
@@ -110,12 +110,12 @@ __global__ void __launch_bounds__(kStepThreads) step_kernel(StepArgs a) {
       f = r.f;
       if (a.plen) a.plen[j] = (uint8_t)r.nseg;
       p = lum(f) + a.eps;
-      kill_clock(a.rb, u1, u2, p, a.h, a.k0, &killed, &wt);
+      kill_clock(a.rb, u1, u2, p, a.h, k0_of(a), &killed, &wt);
       if (!killed) path_adjoint(a.S, xa, a.L, p, LocalTape<kMaxPathLen>{&tape}, r.nseg, GSoA{a.score, a.N, j});
     } else {
       f = evaluate<false, STATS>(a.S, a.M, a.target, a.L, a.eps, xa, &pix, &p, false, GNone{}, st, &err, &stats,
                                  &rays);
-      if (!a.estimate_only) kill_clock(a.rb, u1, u2, p, a.h, a.k0, &killed, &wt);
+      if (!a.estimate_only) kill_clock(a.rb, u1, u2, p, a.h, k0_of(a), &killed, &wt);
     }
     if (a.estimate_only) {
       pval = (double)p;
@@ -383,6 +383,29 @@ void launch_pt(const DevScene& S, int L, uint32_t spp, int n_chunks, Rng rng, do
   pt_kernel<<<(unsigned)((threads + kStepThreads - 1) / kStepThreads), kStepThreads, step_smem_bytes(), s>>>(
       S, L, d, spp, spc, n_chunks, rng, part, rays, err);
   pt_reduce_kernel<<<(unsigned)((n_pix * 3 + 255) / 256), 256, 0, s>>>(part, n_pix * 3, n_chunks, 1.0 / spp, mean);
+}
+
+// FP64 block sums of p[0..N) over blocks of the fused kernel's size, in the
+// fused kernel's order (lanes by shuffle tree, then warps in order), so a p
+// estimate from stored values equals the one the fused kernel reduces.
+__global__ void __launch_bounds__(kStepThreads) block_sums_kernel(const float* __restrict__ p, unsigned long long N,
+                                                                  double* __restrict__ partial) {
+  const unsigned long long t = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const double v = t < N ? (double)p[t] : 0.0;
+  __shared__ double sp[kStepThreads / 32];
+  const double wp = warp_sum_f64(v);
+  if ((threadIdx.x & 31) == 0) sp[threadIdx.x >> 5] = wp;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double P = 0.0;
+    for (int w = 0; w < kStepThreads / 32; ++w) P += sp[w];
+    partial[blockIdx.x] = P;
+  }
+}
+
+void launch_block_sums(const float* p, unsigned long long N, double* partial, cudaStream_t s) {
+  const unsigned grid = (unsigned)((N + kStepThreads - 1) / kStepThreads);
+  block_sums_kernel<<<grid, kStepThreads, 0, s>>>(p, N, partial);
 }
 
 void launch_sum_doubles(const double* in, int n, double* out, cudaStream_t s) {

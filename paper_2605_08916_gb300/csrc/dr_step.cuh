@@ -21,19 +21,21 @@ struct GSoA {
   DR_D void operator()(int i, float v) const { g[(size_t)i * N + j] = v; }
 };
 
-// The step index of this launch: from device memory when the step is part of
-// a replayed CUDA graph (advanced on the device after each step), else the
-// launch argument.
-DR_D uint32_t step_index(const StepArgs& a) { return a.step_ptr ? *a.step_ptr : a.step; }
+// The step index, Philox key and k0 of this launch: from device memory when
+// the step is part of a replayed CUDA graph, else the launch arguments.
+DR_D uint32_t step_index(const StepArgs& a) { return a.fp ? a.fp->step : a.step; }
+DR_D Rng rng_of(const StepArgs& a) { return a.fp ? Rng{a.fp->seed_lo, a.fp->seed_hi, a.fp->frame} : a.rng; }
+DR_D double k0_of(const StepArgs& a) { return a.fp ? a.fp->k0 : a.k0; }
 
 // Evolve (Alg. 2): regeneration x ~ U(T^d) for a killed (or initialising)
 // chain, else LocalDynamics (Alg. 4): for each coordinate pair
 // x += (stddev^2 / 2) s + gamma_tilde (s_2, -s_1) + stddev xi, then wrap.
 DR_D void evolve_x(const StepArgs& a, uint32_t step, unsigned long long j, bool regen) {
   const uint32_t cj = (uint32_t)j;
+  const Rng rng = rng_of(a);
   if (regen) {
     for (int i = 0; i < a.d; i += 4) {
-      const U4 r = a.rng.draw(step, cj, (uint32_t)(i >> 2), kRegen);
+      const U4 r = rng.draw(step, cj, (uint32_t)(i >> 2), kRegen);
       const uint32_t w[4] = {r.a, r.b, r.c, r.d};
 #pragma unroll
       for (int k = 0; k < 4; ++k)
@@ -43,7 +45,7 @@ DR_D void evolve_x(const StepArgs& a, uint32_t step, unsigned long long j, bool 
   }
   const float c2 = 0.5f * a.stddev * a.stddev;
   for (int q = 0; q < a.d / 2; ++q) {
-    const U4 r = a.rng.draw(step, cj, (uint32_t)(q >> 1), kNormal);
+    const U4 r = rng.draw(step, cj, (uint32_t)(q >> 1), kNormal);
     const float ua = u01((q & 1) ? r.c : r.a), ub = u01((q & 1) ? r.d : r.b);
     const float2 xi = box_muller(ua, ub);
     const size_t i0 = (size_t)(2 * q) * a.N + j, i1 = (size_t)(2 * q + 1) * a.N + j;

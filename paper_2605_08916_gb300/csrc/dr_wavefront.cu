@@ -75,7 +75,7 @@ DR_D void add_counts(unsigned long long* target, unsigned long long v) {
 __global__ void __launch_bounds__(kWfThreads) wf_begin(StepArgs a, WfBuffers w) {
   for (unsigned long long j = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; j < a.N;
        j += (unsigned long long)gridDim.x * blockDim.x) {
-    evolve_x(a, step_index(a), j, a.killed[j] != 0);
+    evolve_x(a, step_index(a), j, a.init || a.killed[j] != 0);
     PathState ps;
     const int pix = path_begin(a.S, XSoA{a.x, a.N, j}, ps);
     store_slot(w.slot, j, ps, pix);
@@ -302,7 +302,10 @@ __global__ void __launch_bounds__(kWfThreads, kWfTraceMinBlocks) wf_shadow(StepA
   if (err) atomicOr(a.err, err);
 }
 
-__global__ void __launch_bounds__(kWfThreads) wf_finish(StepArgs a, WfBuffers w) {
+// Accumulate: the kill clock, the state written back and the splat record
+// (mode kWfStep / kWfInitClock); the chains that survive go to the adjoint
+// queue (kWfStep).  kWfInitEval instead stores p and queues every chain.
+__global__ void __launch_bounds__(kWfThreads) wf_finish(StepArgs a, WfBuffers w, int mode, float* p_out) {
   const unsigned long long n_iter = (a.N + (unsigned long long)gridDim.x * blockDim.x - 1) /
                                     ((unsigned long long)gridDim.x * blockDim.x);
   uint32_t err = 0;
@@ -316,25 +319,30 @@ __global__ void __launch_bounds__(kWfThreads) wf_finish(StepArgs a, WfBuffers w)
       load_slot(w.slot, j, ps, pix);
       const float3 f = ps.f;
       const float p = lum(f) + a.eps;
-      const U4 rc = a.rng.draw(step_index(a), (uint32_t)j, 0u, kClock);
-      bool killed;
-      float wt;
-      kill_clock(a.rb, u01(rc.a), u01(rc.b), p, a.h, a.k0, &killed, &wt);
-      a.killed[j] = killed ? 1 : 0;
-      a.logp[j] = logf(p);
-      if (a.plen) a.plen[j] = (uint8_t)ps.nseg;
-      kills += killed ? 1ull : 0ull;
-      if (a.rec) {
-        const float s = wt / p;
-        SplatRec rr;
-        rr.pix = (uint32_t)pix;
-        rr.r = f.x * s;
-        rr.g = f.y * s;
-        rr.b = f.z * s;
-        a.rec[j] = rr;
-      }
       if (!(isfinite(p) && isfinite(f.x) && isfinite(f.y) && isfinite(f.z))) err |= kErrNonFinite;
-      survive = !killed;
+      if (a.plen) a.plen[j] = (uint8_t)ps.nseg;
+      if (mode == kWfInitEval) {
+        p_out[j] = p;
+        survive = true;
+      } else {
+        const U4 rc = rng_of(a).draw(step_index(a), (uint32_t)j, 0u, kClock);
+        bool killed;
+        float wt;
+        kill_clock(a.rb, u01(rc.a), u01(rc.b), p, a.h, k0_of(a), &killed, &wt);
+        a.killed[j] = killed ? 1 : 0;
+        a.logp[j] = logf(p);
+        kills += killed ? 1ull : 0ull;
+        if (a.rec) {
+          const float s = wt / p;
+          SplatRec rr;
+          rr.pix = (uint32_t)pix;
+          rr.r = f.x * s;
+          rr.g = f.y * s;
+          rr.b = f.z * s;
+          a.rec[j] = rr;
+        }
+        survive = !killed && mode == kWfStep;
+      }
     }
     const uint32_t ai = warp_append(&w.counts[kWfAdjointCount], survive);
     if (survive) w.adj[ai] = (uint32_t)j;
@@ -396,10 +404,16 @@ int fetch_blocks_per_sm(size_t smem) {
 }
 
 int launch_wavefront_step(const StepArgs& a, const WfBuffers& w, bool stats, int n_sm, const PhaseHook& hook,
-                          cudaStream_t s) {
+                          cudaStream_t s, WfMode mode, float* p_out) {
   if (a.N == 0) return 0;
   const int max_blocks = n_sm * 16;
   const unsigned g = grid_for(a.N, max_blocks);
+  if (mode == kWfInitClock) {
+    hook(kPhFinish, true);
+    wf_finish<<<g, kWfThreads, 0, s>>>(a, w, mode, p_out);
+    hook(kPhFinish, false);
+    return 1;
+  }
   const size_t smem = (size_t)kWfStack * kWfThreads * sizeof(int);
   const bool wide = a.S.nodes4 != nullptr;
   // persistent passes: as many blocks as stay resident
@@ -443,7 +457,7 @@ int launch_wavefront_step(const StepArgs& a, const WfBuffers& w, bool stats, int
     }
   }
   hook(kPhFinish, true);
-  wf_finish<<<g, kWfThreads, 0, s>>>(a, w);
+  wf_finish<<<g, kWfThreads, 0, s>>>(a, w, mode, p_out);
   hook(kPhFinish, false);
   hook(kPhAdjoint, true);
   wf_adjoint<<<g, kWfThreads, 0, s>>>(a, w);
