@@ -262,6 +262,41 @@ def test_chain_parity_race_clock(torch, R, oracle):
     assert frac <= 0.01
 
 
+def test_image_relmse_distribution_matches_oracle(torch, R, oracle):
+    """At equal chain-step counts, the relMSE of the GPU's Restore images over
+    16 seeds is statistically indistinguishable from the oracle's on the same
+    seeds (Welch t-test, p > 0.01), against an oracle path-traced reference."""
+    stats = pytest.importorskip("scipy.stats")
+    scene = S.cornell_box(1, 16, 16)
+    L, N, T = 4, 1024, 128
+    tgt = oracle.OracleScene(scene)
+    xs = np.random.default_rng(11).random((4096, S.pss_dim(L)))
+    p_hat = float(np.mean(np.exp(oracle.evaluate(tgt, xs, L)["logp"])))
+    k0 = p_hat / (64 * 1e-5)
+    ref, _ = oracle.pt_image(tgt, L, 1 << 14, seed=3)
+    ref = ref.reshape(16, 16, 3)
+    pg = R.make_params(L=L, drift="adjoint", rb=True, k0=k0, steps_per_splat=16)
+    po = oracle.make_params(L=L, drift="exact", rb=True, k0=k0)
+    r = R.Renderer()
+    r.upload_scene(scene)
+    e_gpu, e_orc = [], []
+    for seed in range(100, 116):
+        r.init_chains(N, seed, pg)
+        r.step(T)
+        img = r.resolve().cpu().numpy().astype(np.float64)
+        e_gpu.append(oracle.rel_mse(img, ref))
+        ro = oracle.restore_run(tgt, po, seed=seed, chain_ids=np.arange(N), n_steps=T, record=False)
+        img_o = oracle.resolve(ro["accum"], k0, ro["tour_count"]).reshape(16, 16, 3)
+        e_orc.append(oracle.rel_mse(img_o, ref))
+    r.close()
+    e_gpu, e_orc = np.array(e_gpu), np.array(e_orc)
+    t = stats.ttest_ind(e_gpu, e_orc, equal_var=False)
+    print(f"relMSE gpu {e_gpu.mean():.4g} +- {e_gpu.std(ddof=1):.2g}, oracle {e_orc.mean():.4g} +- "
+          f"{e_orc.std(ddof=1):.2g}, Welch p = {t.pvalue:.3g}")
+    assert t.pvalue > 0.01
+    assert np.all(np.abs(e_gpu - e_orc) <= 0.05 * e_orc + 1e-3)
+
+
 def test_pt_reference_image_matches_oracle(torch, R, oracle):
     """Stratified path tracing on the GPU and in the oracle draw the same
     Philox numbers, so their per-pixel means agree sample for sample."""
