@@ -118,6 +118,50 @@ int dr_scene_upload(dr_ctx* ctx, const float* verts, int32_t nv, const int32_t* 
                     int32_t nt, const int32_t* tri_mat, const float* mats, int32_t nm, const float* camera,
                     int32_t width, int32_t height);
 
+/* One scene of a multi-scene batch: the arrays and meaning of
+ * dr_scene_upload (HOST pointers, copied), plus the scene's own path length
+ * (1..16) and number of chains. */
+typedef struct {
+  const float* verts;
+  int32_t nv;
+  const int32_t* tris;
+  const float* normals;
+  int32_t nt;
+  const int32_t* tri_mat;
+  const float* mats;
+  int32_t nm;
+  const float* camera;
+  int32_t width, height;
+  int32_t max_path_len;
+  uint64_t n_chains;
+} dr_scene_desc;
+
+/* Uploads n_scenes (1..255) scenes as one batch (a workload of many views
+ * of uneven size and path length advanced together).  Each scene gets its
+ * own BVH (binary and 4-wide; every scene needs >= 2 triangles), camera,
+ * image, k0 and tourCount; their chains are laid out scene after scene in
+ * one state array (PSS dimension of the longest path), and every step of
+ * all scenes runs in one sequence of bounce-by-bounce launches whose ray
+ * queues mix the scenes.  Chain j of scene s draws from the Philox stream
+ * with key (seed_lo, seed_hi + s) and chain word j - (first chain of s), so
+ * a scene evolves exactly as it would in a context of its own with that
+ * key.  The images share one FP64 accumulator, scene after scene.  Then
+ * dr_chains_init (n_chains = the sum over scenes, prm->drift_mode must be
+ * DR_DRIFT_ADJOINT; prm->max_path_len is ignored), dr_step / dr_frame /
+ * dr_splat as usual, and dr_resolve_scene per scene.  Synchronises.
+ * Errors: INVALID_ARG, OOM, CUDA, DEVICE_CHECK. */
+int dr_scenes_upload_batch(dr_ctx* ctx, const dr_scene_desc* scenes, int32_t n_scenes);
+
+/* Resolve (Alg. 3) of scene `scene` of a batch into the FP32 DEVICE buffer
+ * out_rgb [W_s * H_s * 3] with that scene's k0 and tourCount.  Errors as
+ * dr_resolve, plus STATE when no batch is uploaded, INVALID_ARG for a bad
+ * scene index. */
+int dr_resolve_scene(dr_ctx* ctx, int32_t scene, float* out_rgb);
+
+/* Per-scene counters of a batch (HOST outputs, may be NULL): completed
+ * tours and k0.  Synchronises. */
+int dr_get_scene_counters(dr_ctx* ctx, int32_t scene, uint64_t* tour_count, double* k0);
+
 /* Uses an analytic target instead of a scene: an isotropic Gaussian mixture
  * on the torus T^d, p = g + eps with g(x) = sum_k w[k] N(x; mu[k],
  * sig[k]^2 I) (differences to the nearest image), or the constant `cval`
@@ -258,13 +302,19 @@ int dr_pt_render(dr_ctx* ctx, int32_t max_path_len, uint32_t spp, uint64_t seed,
  *   DR_OPT_PROFILE     1: record CUDA events around each pass of dr_step /
  *                      dr_splat (not inside dr_frame graphs) and accumulate
  *                      their durations per phase (see dr_get_profile).
+ *   DR_OPT_TRAVERSE_BLOCKS  blocks per SM of the persistent traversal pass
+ *                      (1..64, capped at the resident count; 0 (default):
+ *                      all resident blocks).
+ *   DR_OPT_REFILL      a traversal warp fetches new rays once fewer than
+ *                      this many of its 32 lanes are busy (1..32; default 24).
  *   DR_OPT_BVH_WIDTH   4: rays traverse the 4-wide BVH collapsed from the
  *                      binary one at scene upload (when it was built, see
  *                      dr_bvh4_info); 2: the binary BVH; 0 (default): the
  *                      4-wide one everywhere but in the fused step kernel.
  *                      Both return the same closest hit (ties: smaller id).
  * Errors: INVALID_ARG (unknown option or value). */
-enum { DR_OPT_WORK_ORDER = 1, DR_OPT_WAVEFRONT = 2, DR_OPT_PROFILE = 3, DR_OPT_BVH_WIDTH = 4 };
+enum { DR_OPT_WORK_ORDER = 1, DR_OPT_WAVEFRONT = 2, DR_OPT_PROFILE = 3, DR_OPT_BVH_WIDTH = 4,
+       DR_OPT_TRAVERSE_BLOCKS = 5, DR_OPT_REFILL = 6 };
 int dr_set_option(dr_ctx* ctx, int32_t option, int32_t value);
 
 /* Per-phase device time accumulated since the last call while DR_OPT_PROFILE

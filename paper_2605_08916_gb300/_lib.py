@@ -28,13 +28,22 @@ EXPORTS = ["dr_version", "dr_last_error", "dr_create", "dr_destroy", "dr_scene_u
            "dr_get_counters", "dr_eval_logp", "dr_trace_closest", "dr_philox", "dr_splat_records",
            "dr_clear_image", "dr_state_save", "dr_state_load", "dr_set_stats", "dr_get_traversal_stats",
            "dr_bvh_info", "dr_get_launch_count", "dr_get_chain_shape", "dr_pt_render", "dr_set_bvh_builder",
-           "dr_splat_records_noalloc", "dr_set_option", "dr_get_profile", "dr_frame", "dr_bvh4_info", "dr_get_bounce_profile"]
+           "dr_splat_records_noalloc", "dr_set_option", "dr_get_profile", "dr_frame", "dr_bvh4_info", "dr_get_bounce_profile",
+           "dr_scenes_upload_batch", "dr_resolve_scene", "dr_get_scene_counters"]
 DR_OPT_WORK_ORDER, DR_OPT_WAVEFRONT, DR_OPT_PROFILE, DR_OPT_BVH_WIDTH = 1, 2, 3, 4
+DR_OPT_TRAVERSE_BLOCKS, DR_OPT_REFILL = 5, 6
 DR_PHASES = 10
 PHASE_NAMES = ["wf_begin", "trace", "shade", "shadow", "finish", "adjoint", "fused_step", "fd_score", "splat",
                "work_order"]
 DR_NOALLOC_MAX_RECORDS = 65536
 DR_BVH_LBVH, DR_BVH_PLOC = 0, 1
+
+
+class dr_scene_desc(C.Structure):
+    _fields_ = [("verts", C.c_void_p), ("nv", C.c_int32), ("tris", C.c_void_p), ("normals", C.c_void_p),
+                ("nt", C.c_int32), ("tri_mat", C.c_void_p), ("mats", C.c_void_p), ("nm", C.c_int32),
+                ("camera", C.c_void_p), ("width", C.c_int32), ("height", C.c_int32),
+                ("max_path_len", C.c_int32), ("n_chains", C.c_uint64)]
 
 
 class dr_params(C.Structure):
@@ -100,6 +109,9 @@ def load(build_if_missing=True):
         "dr_frame": ([P, U32], C.c_int),
         "dr_bvh4_info": ([P, P, P, P], C.c_int),
         "dr_get_bounce_profile": ([P, P, I32], C.c_int),
+        "dr_scenes_upload_batch": ([P, P, I32], C.c_int),
+        "dr_resolve_scene": ([P, I32, P], C.c_int),
+        "dr_get_scene_counters": ([P, I32, P, P], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)

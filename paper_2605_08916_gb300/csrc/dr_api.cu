@@ -33,6 +33,17 @@ struct dr_ctx {
   int n_nodes4 = 0, bvh4_depth = 0, bvh4_stack = 0;
   int bvh_width = 0;  // DR_OPT_BVH_WIDTH (0 automatic)
   unsigned long long target_gen = 0;  // bumped by every scene / mixture upload
+  // multi-scene batch (target 2): one sub-context per scene owns that
+  // scene's BVH and surface data; the kernels see them through d_scenes
+  std::vector<dr_ctx*> subs;
+  std::vector<SceneChains> h_sc;   // per scene: chain range, L, d, first pixel, k0, tour counter
+  std::vector<int> batch_w, batch_h;
+  DevScene* d_scenes = nullptr;
+  SceneChains* d_sc = nullptr;
+  uint8_t* chain_scene = nullptr;  // [N]
+  unsigned long long* batch_tours = nullptr;  // [n_scenes]
+  double* batch_psum = nullptr;               // [n_scenes]
+  WfTuning tune;                              // DR_OPT_TRAVERSE_BLOCKS, DR_OPT_REFILL
   float4* surf = nullptr;
   float4* lights = nullptr;
   float* nrm = nullptr;
@@ -317,6 +328,13 @@ StepArgs step_args(dr_ctx* c) {
   a.node_visits = c->counters + 2;
   a.tri_tests = c->counters + 3;
   a.err = c->err;
+  a.refill = c->tune.refill;
+  if (c->target == 2) {
+    a.scenes = c->d_scenes;
+    a.sc = c->d_sc;
+    a.chain_scene = c->chain_scene;
+    a.target = 0;
+  }
   return a;
 }
 
@@ -341,6 +359,7 @@ int run_fd(dr_ctx* c) {
 }
 
 bool use_wavefront(const dr_ctx* c) {
+  if (c->target == 2) return true;  // a batch runs bounce by bounce only
   const bool adjoint_scene = c->prm.drift_mode == DR_DRIFT_ADJOINT && c->target == 0;
   return adjoint_scene && (c->wavefront == 1 || (c->wavefront == -1 && c->N >= (1ull << 17)));
 }
@@ -375,7 +394,7 @@ int one_step(dr_ctx* c, bool init) {
   if (use_wavefront(c)) {
     DR_TRY(ensure_wavefront_buffers(c));
     const WfBuffers w = wf_carve(c->wf_mem, c->N, c->prm.max_path_len);
-    c->launches += launch_wavefront_step(a, w, c->stats, c->n_sm, hook, c->stream);
+    c->launches += launch_wavefront_step(a, w, c->stats, c->n_sm, c->tune, hook, c->stream);
     DR_TRY(check_launch("wavefront step"));
   } else {
     if (!init && c->work_order && c->prm.drift_mode == DR_DRIFT_ADJOINT && c->target == 0) {
@@ -411,6 +430,20 @@ bool capturing(cudaStream_t s) {
     return false;
   }
   return st != cudaStreamCaptureStatusNone;
+}
+
+// Releases a multi-scene batch (its per-scene contexts and tables).
+void free_batch(dr_ctx* c) {
+  for (dr_ctx* s : c->subs) dr_destroy(s);
+  c->subs.clear();
+  c->h_sc.clear();
+  c->batch_w.clear();
+  c->batch_h.clear();
+  dfree(&c->d_scenes);
+  dfree(&c->d_sc);
+  dfree(&c->chain_scene);
+  dfree(&c->batch_tours);
+  dfree(&c->batch_psum);
 }
 
 // Collapses the freshly built binary BVH into the 4-wide layout (on the
@@ -502,6 +535,7 @@ int dr_destroy(dr_ctx* c) {
   if (c->sort_scratch) cudaFree(c->sort_scratch);
   dfree(&c->accum); dfree(&c->counters); dfree(&c->p_partial); dfree(&c->p_sum); dfree(&c->err);
   dfree(&c->frame_dev);
+  free_batch(c);
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
   for (auto& m : c->marks) {
     cudaEventDestroy(m.begin);
@@ -523,6 +557,7 @@ int dr_scene_upload(dr_ctx* c, const float* verts, int32_t nv, const int32_t* tr
     return fail(DR_ERR_INVALID_ARG, "dr_scene_upload: bad size");
   for (int i = 0; i < 3 * nt; ++i)
     if (tris[i] < 0 || tris[i] >= nv) return fail(DR_ERR_INVALID_ARG, "dr_scene_upload: vertex index out of range");
+  free_batch(c);
   for (int i = 0; i < nt; ++i)
     if (tri_mat[i] < 0 || tri_mat[i] >= nm) return fail(DR_ERR_INVALID_ARG, "dr_scene_upload: material out of range");
   for (int i = 0; i < nm; ++i) {
@@ -675,6 +710,7 @@ int dr_target_mixture(dr_ctx* c, int32_t d, int32_t K, const float* w, const flo
   for (int k = 0; k < K; ++k)
     if (!(sig[k] > 0.f)) return fail(DR_ERR_INVALID_ARG, "dr_target_mixture: sigma must be > 0");
   DR_CUDA(cudaSetDevice(c->device));
+  free_batch(c);
   DR_TRY(dalloc(&c->mw, std::max(1, K)));
   DR_TRY(dalloc(&c->mmu, std::max(1, K * d)));
   DR_TRY(dalloc(&c->msig, std::max(1, K)));
@@ -749,10 +785,222 @@ static int alloc_chains(dr_ctx* c, unsigned long long N, int d, int spp) {
   return DR_OK;
 }
 
+int dr_scenes_upload_batch(dr_ctx* c, const dr_scene_desc* sd, int32_t n) {
+  if (!c || !sd) return fail(DR_ERR_INVALID_ARG, "dr_scenes_upload_batch: NULL argument");
+  if (n < 1 || n > 255) return fail(DR_ERR_INVALID_ARG, "dr_scenes_upload_batch: n_scenes must be 1..255");
+  for (int i = 0; i < n; ++i)
+    if (sd[i].max_path_len < 1 || sd[i].max_path_len > DR_MAX_PATH_LEN || sd[i].n_chains < 1 ||
+        sd[i].n_chains > (1ull << 31))
+      return fail(DR_ERR_INVALID_ARG, "dr_scenes_upload_batch: scene " + std::to_string(i) +
+                                          ": max_path_len 1..16 and n_chains 1..2^31");
+  DR_CUDA(cudaSetDevice(c->device));
+  free_batch(c);
+  c->target = -1;
+  c->inited = false;
+  c->target_gen++;
+  std::vector<DevScene> ds((size_t)n);
+  unsigned long long pix = 0, chains = 0;
+  long long tris = 0;
+  for (int i = 0; i < n; ++i) {
+    const dr_scene_desc& q = sd[i];
+    dr_ctx* sub = nullptr;
+    int r = dr_create(&sub, c->device, c->stream);
+    if (r != DR_OK) {
+      free_batch(c);
+      return r;
+    }
+    sub->builder = c->builder;
+    sub->ploc_radius = c->ploc_radius;
+    sub->bvh_width = 4;
+    c->subs.push_back(sub);
+    r = dr_scene_upload(sub, q.verts, q.nv, q.tris, q.normals, q.nt, q.tri_mat, q.mats, q.nm, q.camera, q.width,
+                        q.height);
+    if (r == DR_OK && !sub->nodes4)
+      r = fail(DR_ERR_INVALID_ARG, "no 4-wide BVH (a batch scene needs at least 2 triangles)");
+    if (r == DR_OK && pix + (unsigned long long)q.width * q.height >= (1ull << 31))
+      r = fail(DR_ERR_INVALID_ARG, "the batch's images exceed 2^31 pixels");
+    if (r != DR_OK) {
+      const std::string msg = "dr_scenes_upload_batch: scene " + std::to_string(i) + ": " + g_err;
+      free_batch(c);
+      return fail(r, msg);
+    }
+    ds[(size_t)i] = dev_scene(sub, true);
+    SceneChains sc{};
+    sc.chain0 = chains;
+    sc.n = q.n_chains;
+    sc.L = q.max_path_len;
+    sc.d = 2 + 4 * (q.max_path_len - 1);
+    sc.pix0 = (uint32_t)pix;
+    c->h_sc.push_back(sc);
+    c->batch_w.push_back(q.width);
+    c->batch_h.push_back(q.height);
+    pix += (unsigned long long)q.width * q.height;
+    chains += q.n_chains;
+    tris += q.nt;
+  }
+  int r = dalloc(&c->d_scenes, (size_t)n);
+  if (r == DR_OK && cudaMemcpyAsync(c->d_scenes, ds.data(), ds.size() * sizeof(DevScene), cudaMemcpyHostToDevice,
+                                    c->stream) != cudaSuccess)
+    r = fail(DR_ERR_CUDA, "dr_scenes_upload_batch: scene table copy");
+  if (r == DR_OK && cudaStreamSynchronize(c->stream) != cudaSuccess)
+    r = fail(DR_ERR_CUDA, "dr_scenes_upload_batch: synchronise");
+  if (r != DR_OK) {
+    free_batch(c);
+    return r;
+  }
+  c->target = 2;
+  c->W = (int)pix;  // the shared accumulator is one row of all scenes' pixels
+  c->H = 1;
+  c->nt = (int)std::min<long long>(tris, 1ll << 30);
+  c->n_lights = 0;
+  return DR_OK;
+}
+
+namespace {
+
+// Initialize (Alg. 1) for a batch: as for one scene, with p_lambda and k0
+// per scene (each scene's p summed over its own chains, in the fused
+// kernel's block order from the scene's first chain).
+int init_batch(dr_ctx* c, uint64_t n_chains, uint64_t seed, uint32_t frame, const dr_params* prm) {
+  if (prm->drift_mode != DR_DRIFT_ADJOINT)
+    return fail(DR_ERR_INVALID_ARG, "dr_chains_init: a batch runs with the adjoint drift (DR_DRIFT_ADJOINT)");
+  const int ns = (int)c->h_sc.size();
+  unsigned long long total = 0;
+  int Lmax = 1;
+  for (const SceneChains& q : c->h_sc) {
+    total += q.n;
+    Lmax = std::max(Lmax, q.L);
+  }
+  if (n_chains != total)
+    return fail(DR_ERR_INVALID_ARG, "dr_chains_init: n_chains must equal the batch's total (" +
+                                        std::to_string(total) + ")");
+  const int d = 2 + 4 * (Lmax - 1);
+  dr_params p = *prm;
+  p.max_path_len = Lmax;
+  DR_TRY(alloc_chains(c, total, d, p.steps_per_splat));
+  c->N = total;
+  c->d = d;
+  c->prm = p;
+  c->seed = seed;
+  c->frame = frame;
+  c->step = 0;
+  c->rec_cap = p.steps_per_splat;
+  c->rec_count = 0;
+  c->k0 = 0.0;
+  c->p_lambda = 0.0;
+  cudaStream_t s = c->stream;
+  std::vector<uint8_t> cs((size_t)total);
+  for (int q = 0; q < ns; ++q)
+    std::fill(cs.begin() + (long long)c->h_sc[q].chain0, cs.begin() + (long long)(c->h_sc[q].chain0 + c->h_sc[q].n),
+              (uint8_t)q);
+  dfree(&c->chain_scene);
+  dfree(&c->batch_tours);
+  dfree(&c->batch_psum);
+  dfree(&c->d_sc);
+  DR_TRY(dalloc(&c->chain_scene, (size_t)total));
+  DR_TRY(dalloc(&c->batch_tours, (size_t)ns));
+  DR_TRY(dalloc(&c->batch_psum, (size_t)ns));
+  DR_TRY(dalloc(&c->d_sc, (size_t)ns));
+  for (int q = 0; q < ns; ++q) {
+    c->h_sc[q].tour_count = c->batch_tours + q;
+    c->h_sc[q].k0 = prm->k0 > 0.0 ? prm->k0 : 0.0;
+  }
+  DR_CUDA(cudaMemcpyAsync(c->chain_scene, cs.data(), cs.size(), cudaMemcpyHostToDevice, s));
+  DR_CUDA(cudaMemcpyAsync(c->d_sc, c->h_sc.data(), ns * sizeof(SceneChains), cudaMemcpyHostToDevice, s));
+  DR_CUDA(cudaMemsetAsync(c->batch_tours, 0, ns * sizeof(unsigned long long), s));
+  DR_CUDA(cudaMemsetAsync(c->score, 0, (size_t)total * d * 4, s));
+  DR_CUDA(cudaMemsetAsync(c->killed, 0, (size_t)total, s));
+  DR_CUDA(cudaMemsetAsync(c->plen, 0, (size_t)total, s));
+  DR_CUDA(cudaMemsetAsync(c->accum, 0, c->accum_n * 8, s));
+  DR_CUDA(cudaMemsetAsync(c->counters, 0, 4 * 8, s));
+  DR_CUDA(cudaMemsetAsync(c->err, 0, 4, s));
+  DR_CUDA(cudaStreamSynchronize(s));  // the host copies above are of stack memory
+  DR_TRY(ensure_wavefront_buffers(c));
+  c->inited = true;
+  if (prm->k0 > 0.0) return one_step(c, true);
+  const WfBuffers w = wf_carve(c->wf_mem, c->N, c->prm.max_path_len);
+  float* p_tmp = reinterpret_cast<float*>(w.hit);  // free once the last bounce is shaded
+  StepArgs a = step_args(c);
+  a.init = 1;
+  a.step = 0;
+  a.rec = c->rec;
+  a.plen = c->plen;
+  const PhaseHook hook{phase_mark, c};
+  c->launches += launch_wavefront_step(a, w, c->stats, c->n_sm, c->tune, hook, s, kWfInitEval, p_tmp);
+  for (int q = 0; q < ns; ++q) {
+    const SceneChains& sc = c->h_sc[q];
+    launch_block_sums(p_tmp + sc.chain0, sc.n, c->p_partial, s);
+    const int nb = (int)((sc.n + step_block_size() - 1) / step_block_size());
+    launch_sum_doubles(c->p_partial, nb, c->batch_psum + q, s);
+    c->launches += 2;
+  }
+  DR_TRY(check_launch("batch init evaluation"));
+  std::vector<double> psum((size_t)ns);
+  DR_CUDA(cudaMemcpyAsync(psum.data(), c->batch_psum, ns * sizeof(double), cudaMemcpyDeviceToHost, s));
+  DR_CUDA(cudaStreamSynchronize(s));
+  for (int q = 0; q < ns; ++q) {
+    const double pl = psum[q] / (double)c->h_sc[q].n;
+    if (!(pl > 0.0) || !std::isfinite(pl)) {
+      c->inited = false;
+      return fail(DR_ERR_STATE, "dr_chains_init: estimated p_lambda of scene " + std::to_string(q) +
+                                    " is not positive");
+    }
+    c->h_sc[q].k0 = pl / ((double)prm->m * (double)prm->dt);
+  }
+  DR_CUDA(cudaMemcpyAsync(c->d_sc, c->h_sc.data(), ns * sizeof(SceneChains), cudaMemcpyHostToDevice, s));
+  c->launches += launch_wavefront_step(a, w, c->stats, c->n_sm, c->tune, hook, s, kWfInitClock, p_tmp);
+  DR_TRY(check_launch("batch init clock"));
+  DR_CUDA(cudaStreamSynchronize(s));
+  c->rec_count = 1;
+  return check_device_error(c);
+}
+
+}  // namespace
+
+int dr_resolve_scene(dr_ctx* c, int32_t scene, float* out_rgb) {
+  if (!c || !out_rgb) return fail(DR_ERR_INVALID_ARG, "dr_resolve_scene: NULL argument");
+  if (c->target != 2) return fail(DR_ERR_STATE, "dr_resolve_scene: no batch uploaded");
+  if (scene < 0 || scene >= (int)c->h_sc.size()) return fail(DR_ERR_INVALID_ARG, "dr_resolve_scene: scene index");
+  if (!c->inited) return fail(DR_ERR_STATE, "dr_resolve_scene: chains not initialised");
+  DR_CUDA(cudaSetDevice(c->device));
+  DR_TRY(flush(c));
+  const SceneChains& q = c->h_sc[scene];
+  launch_resolve(c->accum + 3 * (size_t)q.pix0, 3 * (size_t)c->batch_w[scene] * c->batch_h[scene],
+                 c->batch_tours + scene, q.k0, out_rgb, c->stream);
+  c->launches += 1;
+  DR_TRY(check_launch("resolve"));
+  if (!capturing(c->stream)) {
+    unsigned long long tc = 0;
+    DR_CUDA(cudaMemcpyAsync(&tc, c->batch_tours + scene, 8, cudaMemcpyDeviceToHost, c->stream));
+    DR_CUDA(cudaStreamSynchronize(c->stream));
+    if (tc == 0) return fail(DR_ERR_STATE, "dr_resolve_scene: tourCount is 0 (no completed tour yet)");
+  }
+  return DR_OK;
+}
+
+int dr_get_scene_counters(dr_ctx* c, int32_t scene, uint64_t* tour_count, double* k0) {
+  if (!c) return fail(DR_ERR_INVALID_ARG, "dr_get_scene_counters: NULL ctx");
+  if (c->target != 2) return fail(DR_ERR_STATE, "dr_get_scene_counters: no batch uploaded");
+  if (scene < 0 || scene >= (int)c->h_sc.size()) return fail(DR_ERR_INVALID_ARG, "dr_get_scene_counters: scene");
+  DR_CUDA(cudaSetDevice(c->device));
+  unsigned long long tc = 0;
+  if (c->batch_tours) {
+    DR_CUDA(cudaMemcpyAsync(&tc, c->batch_tours + scene, 8, cudaMemcpyDeviceToHost, c->stream));
+    DR_CUDA(cudaStreamSynchronize(c->stream));
+  }
+  if (tour_count) *tour_count = tc;
+  if (k0) *k0 = c->h_sc[scene].k0;
+  return check_device_error(c);
+}
+
 int dr_chains_init(dr_ctx* c, uint64_t n_chains, uint64_t seed, uint32_t frame, const dr_params* prm) {
   if (!c) return fail(DR_ERR_INVALID_ARG, "dr_chains_init: NULL ctx");
   DR_TRY(validate_params(prm));
   if (c->target < 0) return fail(DR_ERR_STATE, "dr_chains_init: no scene or target uploaded");
+  if (c->target == 2) {
+    DR_CUDA(cudaSetDevice(c->device));
+    return init_batch(c, n_chains, seed, frame, prm);
+  }
   if (n_chains < 1 || n_chains > (1ull << 31)) return fail(DR_ERR_INVALID_ARG, "dr_chains_init: n_chains");
   if (frame >= (1u << 28)) return fail(DR_ERR_INVALID_ARG, "dr_chains_init: frame must be < 2^28");
   const int d = c->target == 0 ? 2 + 4 * (prm->max_path_len - 1) : c->md;
@@ -786,7 +1034,7 @@ int dr_chains_init(dr_ctx* c, uint64_t n_chains, uint64_t seed, uint32_t frame, 
     a.rec = c->rec;
     a.plen = c->plen;
     const PhaseHook hook{phase_mark, c};
-    c->launches += launch_wavefront_step(a, w, c->stats, c->n_sm, hook, s, kWfInitEval, p_tmp);
+    c->launches += launch_wavefront_step(a, w, c->stats, c->n_sm, c->tune, hook, s, kWfInitEval, p_tmp);
     launch_block_sums(p_tmp, n_chains, c->p_partial, s);
     const int nb = (int)((n_chains + step_block_size() - 1) / step_block_size());
     launch_sum_doubles(c->p_partial, nb, c->p_sum, s);
@@ -800,7 +1048,7 @@ int dr_chains_init(dr_ctx* c, uint64_t n_chains, uint64_t seed, uint32_t frame, 
       return fail(DR_ERR_STATE, "dr_chains_init: estimated p_lambda is not positive");
     c->k0 = c->p_lambda / ((double)prm->m * (double)prm->dt);
     a.k0 = c->k0;
-    c->launches += launch_wavefront_step(a, w, c->stats, c->n_sm, hook, s, kWfInitClock, p_tmp);
+    c->launches += launch_wavefront_step(a, w, c->stats, c->n_sm, c->tune, hook, s, kWfInitClock, p_tmp);
     DR_TRY(check_launch("init clock"));
     c->inited = true;
     c->rec_count = 1;
@@ -854,6 +1102,7 @@ int dr_splat(dr_ctx* c) {
 
 int dr_resolve(dr_ctx* c, float* out_rgb) {
   if (!c || !out_rgb) return fail(DR_ERR_INVALID_ARG, "dr_resolve: NULL argument");
+  if (c->target == 2) return fail(DR_ERR_STATE, "dr_resolve: a batch resolves per scene (dr_resolve_scene)");
   if (!c->inited) return fail(DR_ERR_STATE, "dr_resolve: chains not initialised");
   DR_CUDA(cudaSetDevice(c->device));
   DR_TRY(flush(c));
@@ -929,7 +1178,7 @@ int dr_get_counters(dr_ctx* c, uint64_t* tour_count, double* k0, uint64_t* steps
 
 int dr_eval_logp(dr_ctx* c, int32_t L, const float* x, int64_t M, float* logp, float* grad, int32_t* pix, float* f) {
   if (!c || !x || !logp) return fail(DR_ERR_INVALID_ARG, "dr_eval_logp: NULL argument");
-  if (c->target < 0) return fail(DR_ERR_STATE, "dr_eval_logp: no scene or target");
+  if (c->target < 0 || c->target == 2) return fail(DR_ERR_STATE, "dr_eval_logp: no single scene or target");
   if (M < 0) return fail(DR_ERR_INVALID_ARG, "dr_eval_logp: M < 0");
   if (c->target == 0 && (L < 1 || L > DR_MAX_PATH_LEN)) return fail(DR_ERR_INVALID_ARG, "dr_eval_logp: L");
   DR_CUDA(cudaSetDevice(c->device));
@@ -1018,6 +1267,7 @@ constexpr uint64_t kMagic = 0x3152545345524644ull;  // "DFRESTR1"
 int dr_state_save(dr_ctx* c, void* host_buf, size_t* bytes) {
   if (!c || !bytes) return fail(DR_ERR_INVALID_ARG, "dr_state_save: NULL argument");
   if (!c->inited) return fail(DR_ERR_STATE, "dr_state_save: chains not initialised");
+  if (c->target == 2) return fail(DR_ERR_STATE, "dr_state_save: not available for a batch");
   const size_t nd = (size_t)c->N * c->d;
   const size_t need = sizeof(SaveHeader) + nd * 8 + c->N * 5 + c->accum_n * 8;
   if (!host_buf) {
@@ -1056,6 +1306,7 @@ int dr_state_save(dr_ctx* c, void* host_buf, size_t* bytes) {
 int dr_state_load(dr_ctx* c, const void* host_buf, size_t bytes) {
   if (!c || !host_buf) return fail(DR_ERR_INVALID_ARG, "dr_state_load: NULL argument");
   if (bytes < sizeof(SaveHeader)) return fail(DR_ERR_INVALID_ARG, "dr_state_load: buffer too small");
+  if (c->target == 2) return fail(DR_ERR_STATE, "dr_state_load: not available for a batch");
   SaveHeader h;
   std::memcpy(&h, host_buf, sizeof(h));
   if (h.magic != kMagic || h.version != 1) return fail(DR_ERR_INVALID_ARG, "dr_state_load: not a checkpoint");
@@ -1109,7 +1360,9 @@ std::vector<unsigned long long> frame_key(const dr_ctx* c, uint32_t n_steps) {
                                        c->rec_cap, (unsigned long long)c->wavefront,
                                        (unsigned long long)c->work_order, (unsigned long long)c->stats,
                                        (unsigned long long)c->nt, (unsigned long long)c->n_lights, P(c->stream),
-                                       c->target_gen};
+                                       c->target_gen, P(c->d_scenes), P(c->d_sc), P(c->chain_scene),
+                                       (unsigned long long)c->tune.blocks_per_sm,
+                                       (unsigned long long)c->tune.refill};
   for (unsigned long long v : prm) k.push_back(v);
   return k;
 }
@@ -1252,6 +1505,14 @@ int dr_set_option(dr_ctx* c, int32_t option, int32_t value) {
     case DR_OPT_WORK_ORDER:
       if (value != 0 && value != 1) return fail(DR_ERR_INVALID_ARG, "dr_set_option: work order is 0 or 1");
       c->work_order = value;
+      return DR_OK;
+    case DR_OPT_TRAVERSE_BLOCKS:
+      if (value < 0 || value > 64) return fail(DR_ERR_INVALID_ARG, "dr_set_option: traverse blocks is 0..64");
+      c->tune.blocks_per_sm = value;
+      return DR_OK;
+    case DR_OPT_REFILL:
+      if (value < 1 || value > 32) return fail(DR_ERR_INVALID_ARG, "dr_set_option: refill is 1..32");
+      c->tune.refill = value;
       return DR_OK;
     case DR_OPT_BVH_WIDTH:
       if (value != 0 && value != 2 && value != 4)

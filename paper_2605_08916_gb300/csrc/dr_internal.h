@@ -82,8 +82,25 @@ struct FrameParams {
   double k0;
 };
 
+// One scene of a multi-scene batch as its chains see it: their index range,
+// path length L and PSS dimension d, the scene's first pixel in the shared
+// accumulation image, its k0 and its tour counter.  Device memory, so a
+// replayed graph picks up k0 estimated after capture.
+struct SceneChains {
+  unsigned long long chain0, n;
+  int L, d;
+  uint32_t pix0, pad;
+  double k0;
+  unsigned long long* tour_count;
+};
+
 struct StepArgs {
   DevScene S;
+  // multi-scene batch (null: the single scene S): per-scene BVH and camera,
+  // per-scene chain table, and the scene of every chain
+  const DevScene* scenes;
+  const SceneChains* sc;
+  const uint8_t* chain_scene;
   DevMixture M;
   int target;  // 0 scene, 1 mixture
   float* x;          // [d][N]
@@ -108,6 +125,7 @@ struct StepArgs {
   unsigned long long* tri_tests;    // stats mode only
   double* p_partial;  // [gridDim.x] init only
   uint32_t* err;
+  int refill;  // persistent traversal: refill a warp below this many busy lanes
 };
 
 // (key, chain) pairs for the work order of the next step
@@ -160,8 +178,14 @@ struct PhaseHook {
 // p_out, the adjoint for every chain, no clock) then kWfInitClock (the
 // kill clock and records from the stored path results, once k0 is known).
 enum WfMode { kWfStep = 0, kWfInitEval = 1, kWfInitClock = 2 };
-int launch_wavefront_step(const StepArgs& a, const WfBuffers& w, bool stats, int n_sm, const PhaseHook& hook,
-                          cudaStream_t s, WfMode mode = kWfStep, float* p_out = nullptr);
+// Launch shape of the persistent traversal pass: blocks per SM (0: as many
+// as stay resident) and the lane count below which a warp refills.
+struct WfTuning {
+  int blocks_per_sm = 0;
+  int refill = 24;
+};
+int launch_wavefront_step(const StepArgs& a, const WfBuffers& w, bool stats, int n_sm, const WfTuning& tune,
+                          const PhaseHook& hook, cudaStream_t s, WfMode mode = kWfStep, float* p_out = nullptr);
 // step index += 1 on the device (graph replay)
 void launch_advance_step(uint32_t* step, cudaStream_t s);
 

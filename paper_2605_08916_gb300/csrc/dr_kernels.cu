@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(kStepThreads) step_kernel(StepArgs a) {
   if (active) {
     const uint32_t cj = (uint32_t)j;
     const uint32_t step = step_index(a);
-    evolve_x(a, step, j, a.init || a.killed[j]);
+    evolve_x(a, rng_of(a), step, j, cj, a.d, a.init || a.killed[j]);
     const XSoA xa{a.x, a.N, j};
     int pix;
     float p;

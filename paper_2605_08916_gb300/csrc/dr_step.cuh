@@ -30,21 +30,22 @@ DR_D double k0_of(const StepArgs& a) { return a.fp ? a.fp->k0 : a.k0; }
 // Evolve (Alg. 2): regeneration x ~ U(T^d) for a killed (or initialising)
 // chain, else LocalDynamics (Alg. 4): for each coordinate pair
 // x += (stddev^2 / 2) s + gamma_tilde (s_2, -s_1) + stddev xi, then wrap.
-DR_D void evolve_x(const StepArgs& a, uint32_t step, unsigned long long j, bool regen) {
-  const uint32_t cj = (uint32_t)j;
-  const Rng rng = rng_of(a);
+// j: the chain's index in the state arrays; cj: its Philox chain word; d:
+// its PSS dimension; rng: its stream key.
+DR_D void evolve_x(const StepArgs& a, const Rng& rng, uint32_t step, unsigned long long j, uint32_t cj, int d,
+                   bool regen) {
   if (regen) {
-    for (int i = 0; i < a.d; i += 4) {
+    for (int i = 0; i < d; i += 4) {
       const U4 r = rng.draw(step, cj, (uint32_t)(i >> 2), kRegen);
       const uint32_t w[4] = {r.a, r.b, r.c, r.d};
 #pragma unroll
       for (int k = 0; k < 4; ++k)
-        if (i + k < a.d) a.x[(size_t)(i + k) * a.N + j] = u01(w[k]);
+        if (i + k < d) a.x[(size_t)(i + k) * a.N + j] = u01(w[k]);
     }
     return;
   }
   const float c2 = 0.5f * a.stddev * a.stddev;
-  for (int q = 0; q < a.d / 2; ++q) {
+  for (int q = 0; q < d / 2; ++q) {
     const U4 r = rng.draw(step, cj, (uint32_t)(q >> 1), kNormal);
     const float ua = u01((q & 1) ? r.c : r.a), ub = u01((q & 1) ? r.d : r.b);
     const float2 xi = box_muller(ua, ub);

@@ -72,12 +72,44 @@ DR_D void add_counts(unsigned long long* target, unsigned long long v) {
   if ((threadIdx.x & 31) == 0 && w && target) atomicAdd(target, w);
 }
 
+// Per-chain view of the target: the single scene, or in a multi-scene batch
+// the chain's own scene (index sid, path length, PSS dimension, first pixel
+// in the shared image).  A batch chain draws Philox numbers with its index
+// within its scene and the key (seed_lo, seed_hi + sid), so each scene of a
+// batch evolves exactly as it would in a context of its own.
+struct ChainView {
+  int sid, L, d;
+  uint32_t cj, pix0;
+};
+
+template <bool BATCH>
+DR_D ChainView chain_view(const StepArgs& a, unsigned long long j) {
+  if (!BATCH) return ChainView{0, a.L, a.d, (uint32_t)j, 0u};
+  const int s = a.chain_scene[j];
+  const SceneChains& sc = a.sc[s];
+  return ChainView{s, sc.L, sc.d, (uint32_t)(j - sc.chain0), sc.pix0};
+}
+
+template <bool BATCH>
+DR_D Rng chain_rng(const StepArgs& a, const ChainView& v) {
+  Rng r = rng_of(a);
+  if (BATCH) r.k1 += (uint32_t)v.sid;
+  return r;
+}
+
+template <bool BATCH>
+DR_D const DevScene& scene_of(const StepArgs& a, int sid) {
+  return BATCH ? a.scenes[sid] : a.S;
+}
+
+template <bool BATCH>
 __global__ void __launch_bounds__(kWfThreads) wf_begin(StepArgs a, WfBuffers w) {
   for (unsigned long long j = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; j < a.N;
        j += (unsigned long long)gridDim.x * blockDim.x) {
-    evolve_x(a, step_index(a), j, a.init || a.killed[j] != 0);
+    const ChainView v = chain_view<BATCH>(a, j);
+    evolve_x(a, chain_rng<BATCH>(a, v), step_index(a), j, v.cj, v.d, a.init || a.killed[j] != 0);
     PathState ps;
-    const int pix = path_begin(a.S, XSoA{a.x, a.N, j}, ps);
+    const int pix = path_begin(scene_of<BATCH>(a, v.sid), XSoA{a.x, a.N, j}, ps);
     store_slot(w.slot, j, ps, pix);
     w.hit[j] = -1;
   }
@@ -112,10 +144,10 @@ __global__ void __launch_bounds__(kWfThreads, kWfTraceMinBlocks) wf_trace(StepAr
 
 // Persistent 4-wide trace passes with dynamic ray fetch: a warp keeps
 // stepping its lanes' walks one node at a time and, whenever fewer than
-// kRefillBelow lanes still hold a ray, refills the idle lanes from the queue
-// with one atomic per warp.  A warp's time is then set by its total work
+// a.refill lanes (24 of 32 by default; measured better than 12 and 20)
+// still hold a ray, refills the idle lanes from the queue with one atomic
+// per warp.  A warp's time is then set by its total work
 // rather than by its slowest ray.
-constexpr int kRefillBelow = 24;  // measured: 24-28 of 32 beat 12 and 20
 constexpr unsigned kFull = 0xffffffffu;
 
 // Hands the idle lanes of a warp (mask `idle`) consecutive queue positions;
@@ -137,7 +169,7 @@ DR_D uint32_t warp_fetch(uint32_t* ctr, unsigned idle, uint32_t n, bool& drained
 // first.  The two sets touch disjoint data (hit[] and the ray state vs. the
 // path's f and the shadow-visibility tape flag), so one launch replaces two
 // and each bounce pays the latency of its slowest ray once.
-template <bool STATS>
+template <bool STATS, bool BATCH>
 __global__ void __launch_bounds__(kWfThreads, kWfTrace4MinBlocks) wf_traverse(StepArgs a, WfBuffers w, int k) {
   extern __shared__ int smem[];
   TraceStack<kWfStack> st{smem + threadIdx.x, (int)blockDim.x};
@@ -151,7 +183,7 @@ __global__ void __launch_bounds__(kWfThreads, kWfTrace4MinBlocks) wf_traverse(St
   unsigned long long rays = 0;
   bool has = false, drained = false, shadow = false;
   uint32_t j = 0, t = 0;
-  int ex0 = -1, ex1 = -1, best = -1;
+  int ex0 = -1, ex1 = -1, best = -1, sid = 0;
   float tlim = 0.0f;  // closest hit so far, or the shadow ray's tmax
   Ray r;
   Walk4 wk{0, 0, 0};
@@ -170,6 +202,7 @@ __global__ void __launch_bounds__(kWfThreads, kWfTrace4MinBlocks) wf_traverse(St
             tlim = o.w;
             ex0 = __float_as_int(sr.contrib_ex.w);
             ex1 = sr.ex1;
+            if (BATCH) sid = a.chain_scene[__float_as_int(d.w)];
           } else {
             j = q ? q[tn] : tn;
             const float4 o = w.slot[4 * (size_t)j + 0], d = w.slot[4 * (size_t)j + 1];
@@ -177,8 +210,9 @@ __global__ void __launch_bounds__(kWfThreads, kWfTrace4MinBlocks) wf_traverse(St
             ex0 = __float_as_int(d.w);
             tlim = __int_as_float(0x7f800000);
             best = -1;
+            if (BATCH) sid = a.chain_scene[j];
           }
-          wk = walk4_begin(a.S);
+          wk = walk4_begin(scene_of<BATCH>(a, sid));
           ++rays;
           if (ray_finite(r.o, r.d)) {
             has = true;
@@ -195,14 +229,15 @@ __global__ void __launch_bounds__(kWfThreads, kWfTrace4MinBlocks) wf_traverse(St
     }
     while (true) {
       if (has) {
+        const DevScene& S = scene_of<BATCH>(a, sid);
         if (!shadow) {
-          if (closest4_step<kWfStack, STATS>(a.S, r, ex0, wk, tlim, best, st, &err, &stats)) {
+          if (closest4_step<kWfStack, STATS>(S, r, ex0, wk, tlim, best, st, &err, &stats)) {
             w.hit[j] = best;
             has = false;
           }
         } else {
           bool occ;
-          if (any4_step<kWfStack, STATS>(a.S, r, tlim, ex0, ex1, wk, &occ, st, &err, &stats)) {
+          if (any4_step<kWfStack, STATS>(S, r, tlim, ex0, ex1, wk, &occ, st, &err, &stats)) {
             has = false;
             if (!occ) {
               const ShadowRec& sr = w.shadow[t];
@@ -218,7 +253,7 @@ __global__ void __launch_bounds__(kWfThreads, kWfTrace4MinBlocks) wf_traverse(St
         }
       }
       const unsigned act = __ballot_sync(kFull, has);
-      if (act == 0 || (!drained && __popc(act) < kRefillBelow)) break;
+      if (act == 0 || (!drained && __popc(act) < a.refill)) break;
     }
   }
   add_counts(a.rays, rays);
@@ -229,6 +264,7 @@ __global__ void __launch_bounds__(kWfThreads, kWfTrace4MinBlocks) wf_traverse(St
   if (err) atomicOr(a.err, err);
 }
 
+template <bool BATCH>
 __global__ void __launch_bounds__(kWfThreads) wf_shade(StepArgs a, WfBuffers w, int k) {
   const uint32_t n = w.counts[k];
   const uint32_t* q = k == 1 ? nullptr : w.queue[k & 1];
@@ -242,14 +278,18 @@ __global__ void __launch_bounds__(kWfThreads) wf_shade(StepArgs a, WfBuffers w, 
     NeeReq nee;
     nee.valid = false;
     unsigned long long j = 0;
+    int L = a.L;
     if (t < n) {
       j = q ? q[t] : t;
       const int tri = w.hit[j];
+      const ChainView v = chain_view<BATCH>(a, j);
+      L = v.L;
       if (tri >= 0) {
         PathState ps;
         int pix;
         load_slot(w.slot, j, ps, pix);
-        cont = path_vertex(a.S, XSoA{a.x, a.N, j}, a.L, k, tri, ps, GlobalTape{w.tape, a.N, j}, nee);
+        cont = path_vertex(scene_of<BATCH>(a, v.sid), XSoA{a.x, a.N, j}, L, k, tri, ps, GlobalTape{w.tape, a.N, j},
+                           nee);
         store_slot(w.slot, j, ps, pix);
       }
     }
@@ -262,7 +302,7 @@ __global__ void __launch_bounds__(kWfThreads) wf_shade(StepArgs a, WfBuffers w, 
       r.ex1 = nee.ex1;
       w.shadow[si] = r;
     }
-    const bool next = cont && k < a.L;
+    const bool next = cont && k < L;
     const uint32_t ni = warp_append(&w.counts[k + 1], next);
     if (next) {
       qn[ni] = (uint32_t)j;
@@ -305,6 +345,7 @@ __global__ void __launch_bounds__(kWfThreads, kWfTraceMinBlocks) wf_shadow(StepA
 // Accumulate: the kill clock, the state written back and the splat record
 // (mode kWfStep / kWfInitClock); the chains that survive go to the adjoint
 // queue (kWfStep).  kWfInitEval instead stores p and queues every chain.
+template <bool BATCH>
 __global__ void __launch_bounds__(kWfThreads) wf_finish(StepArgs a, WfBuffers w, int mode, float* p_out) {
   const unsigned long long n_iter = (a.N + (unsigned long long)gridDim.x * blockDim.x - 1) /
                                     ((unsigned long long)gridDim.x * blockDim.x);
@@ -325,17 +366,22 @@ __global__ void __launch_bounds__(kWfThreads) wf_finish(StepArgs a, WfBuffers w,
         p_out[j] = p;
         survive = true;
       } else {
-        const U4 rc = rng_of(a).draw(step_index(a), (uint32_t)j, 0u, kClock);
+        const ChainView v = chain_view<BATCH>(a, j);
+        const U4 rc = chain_rng<BATCH>(a, v).draw(step_index(a), v.cj, 0u, kClock);
         bool killed;
         float wt;
-        kill_clock(a.rb, u01(rc.a), u01(rc.b), p, a.h, k0_of(a), &killed, &wt);
+        kill_clock(a.rb, u01(rc.a), u01(rc.b), p, a.h, BATCH ? a.sc[v.sid].k0 : k0_of(a), &killed, &wt);
         a.killed[j] = killed ? 1 : 0;
         a.logp[j] = logf(p);
-        kills += killed ? 1ull : 0ull;
+        if (BATCH) {
+          if (killed) atomicAdd(a.sc[v.sid].tour_count, 1ull);
+        } else {
+          kills += killed ? 1ull : 0ull;
+        }
         if (a.rec) {
           const float s = wt / p;
           SplatRec rr;
-          rr.pix = (uint32_t)pix;
+          rr.pix = v.pix0 + (uint32_t)pix;
           rr.r = f.x * s;
           rr.g = f.y * s;
           rr.b = f.z * s;
@@ -351,6 +397,7 @@ __global__ void __launch_bounds__(kWfThreads) wf_finish(StepArgs a, WfBuffers w,
   if (err) atomicOr(a.err, err);
 }
 
+template <bool BATCH>
 __global__ void __launch_bounds__(kWfThreads, 4) wf_adjoint(StepArgs a, WfBuffers w) {
   const uint32_t n = w.counts[kWfAdjointCount];
   for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
@@ -359,13 +406,91 @@ __global__ void __launch_bounds__(kWfThreads, 4) wf_adjoint(StepArgs a, WfBuffer
     int pix;
     load_slot(w.slot, j, ps, pix);
     const float p = lum(ps.f) + a.eps;
-    path_adjoint(a.S, XSoA{a.x, a.N, j}, a.L, p, GlobalTape{w.tape, a.N, j}, ps.nseg, GSoA{a.score, a.N, j});
+    const ChainView v = chain_view<BATCH>(a, j);
+    path_adjoint(scene_of<BATCH>(a, v.sid), XSoA{a.x, a.N, j}, v.L, p, GlobalTape{w.tape, a.N, j}, ps.nseg,
+                 GSoA{a.score, a.N, j});
   }
 }
 
 unsigned grid_for(unsigned long long n, int max_blocks) {
   const unsigned long long b = (n + kWfThreads - 1) / kWfThreads;
   return (unsigned)std::max<unsigned long long>(1, std::min<unsigned long long>(b, (unsigned long long)max_blocks));
+}
+
+// resident blocks per SM of the persistent traversal pass, computed once
+template <bool BATCH>
+int traverse_blocks_per_sm(size_t smem) {
+  static int cached = 0;
+  if (cached == 0) {
+    int b0 = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b0, wf_traverse<false, BATCH>, kWfThreads, smem);
+    cached = std::max(1, b0);
+  }
+  return cached;
+}
+
+template <bool BATCH>
+int launch_wf(const StepArgs& a, const WfBuffers& w, bool stats, int n_sm, const WfTuning& tune,
+              const PhaseHook& hook, cudaStream_t s, WfMode mode, float* p_out) {
+  const int max_blocks = n_sm * 16;
+  const unsigned g = grid_for(a.N, max_blocks);
+  if (mode == kWfInitClock) {
+    hook(kPhFinish, true);
+    wf_finish<BATCH><<<g, kWfThreads, 0, s>>>(a, w, mode, p_out);
+    hook(kPhFinish, false);
+    return 1;
+  }
+  const size_t smem = (size_t)kWfStack * kWfThreads * sizeof(int);
+  const bool wide = a.S.nodes4 != nullptr || BATCH;
+  // persistent traversal: as many blocks as stay resident (or fewer, tuned)
+  const int resident = traverse_blocks_per_sm<BATCH>(smem);
+  const int per_sm = tune.blocks_per_sm > 0 ? std::min(tune.blocks_per_sm, resident) : resident;
+  const unsigned g4 = (unsigned)(n_sm * per_sm);
+  int launches = 0;
+  cudaMemsetAsync(w.counts, 0, kWfCounts * sizeof(uint32_t), s);
+  hook(kPhBegin, true);
+  wf_begin<BATCH><<<g, kWfThreads, 0, s>>>(a, w);
+  hook(kPhBegin, false);
+  launches += 2;
+  if (wide) {
+    // traverse(k) = closest-hit rays of bounce k + shadow rays of bounce
+    // k - 1; the last launch (k = L + 1) carries the final shadow rays
+    for (int k = 1; k <= a.L + 1; ++k) {
+      hook(k <= a.L ? kPhTrace : kPhShadow, true, k <= a.L ? k : a.L);
+      if (stats) wf_traverse<true, BATCH><<<g4, kWfThreads, smem, s>>>(a, w, k);
+      else wf_traverse<false, BATCH><<<g4, kWfThreads, smem, s>>>(a, w, k);
+      hook(k <= a.L ? kPhTrace : kPhShadow, false, k <= a.L ? k : a.L);
+      launches += 1;
+      if (k <= a.L) {
+        hook(kPhShade, true, k);
+        wf_shade<BATCH><<<g, kWfThreads, 0, s>>>(a, w, k);
+        hook(kPhShade, false, k);
+        launches += 1;
+      }
+    }
+  } else if (!BATCH) {
+    for (int k = 1; k <= a.L; ++k) {
+      hook(kPhTrace, true, k);
+      if (stats) wf_trace<true><<<g, kWfThreads, smem, s>>>(a, w, k);
+      else wf_trace<false><<<g, kWfThreads, smem, s>>>(a, w, k);
+      hook(kPhTrace, false, k);
+      hook(kPhShade, true, k);
+      wf_shade<false><<<g, kWfThreads, 0, s>>>(a, w, k);
+      hook(kPhShade, false, k);
+      hook(kPhShadow, true, k);
+      if (stats) wf_shadow<true><<<g, kWfThreads, smem, s>>>(a, w, k);
+      else wf_shadow<false><<<g, kWfThreads, smem, s>>>(a, w, k);
+      hook(kPhShadow, false, k);
+      launches += 3;
+    }
+  }
+  hook(kPhFinish, true);
+  wf_finish<BATCH><<<g, kWfThreads, 0, s>>>(a, w, mode, p_out);
+  hook(kPhFinish, false);
+  hook(kPhAdjoint, true);
+  wf_adjoint<BATCH><<<g, kWfThreads, 0, s>>>(a, w);
+  hook(kPhAdjoint, false);
+  return launches + 2;
 }
 
 }  // namespace
@@ -391,78 +516,11 @@ WfBuffers wf_carve(void* base, unsigned long long N, int L) {
   return w;
 }
 
-// resident blocks per SM of the persistent trace passes (the smaller of
-// the two kernels' occupancies), computed once
-int fetch_blocks_per_sm(size_t smem) {
-  static int cached = 0;
-  if (cached == 0) {
-    int b0 = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b0, wf_traverse<false>, kWfThreads, smem);
-    cached = std::max(1, b0);
-  }
-  return cached;
-}
-
-int launch_wavefront_step(const StepArgs& a, const WfBuffers& w, bool stats, int n_sm, const PhaseHook& hook,
-                          cudaStream_t s, WfMode mode, float* p_out) {
+int launch_wavefront_step(const StepArgs& a, const WfBuffers& w, bool stats, int n_sm, const WfTuning& tune,
+                          const PhaseHook& hook, cudaStream_t s, WfMode mode, float* p_out) {
   if (a.N == 0) return 0;
-  const int max_blocks = n_sm * 16;
-  const unsigned g = grid_for(a.N, max_blocks);
-  if (mode == kWfInitClock) {
-    hook(kPhFinish, true);
-    wf_finish<<<g, kWfThreads, 0, s>>>(a, w, mode, p_out);
-    hook(kPhFinish, false);
-    return 1;
-  }
-  const size_t smem = (size_t)kWfStack * kWfThreads * sizeof(int);
-  const bool wide = a.S.nodes4 != nullptr;
-  // persistent passes: as many blocks as stay resident
-  const unsigned g4 = (unsigned)(n_sm * fetch_blocks_per_sm(smem));
-  int launches = 0;
-  cudaMemsetAsync(w.counts, 0, kWfCounts * sizeof(uint32_t), s);
-  hook(kPhBegin, true);
-  wf_begin<<<g, kWfThreads, 0, s>>>(a, w);
-  hook(kPhBegin, false);
-  launches += 2;
-  if (wide) {
-    // traverse(k) = closest-hit rays of bounce k + shadow rays of bounce
-    // k - 1; the last launch (k = L + 1) carries the final shadow rays
-    for (int k = 1; k <= a.L + 1; ++k) {
-      hook(k <= a.L ? kPhTrace : kPhShadow, true, k <= a.L ? k : a.L);
-      if (stats) wf_traverse<true><<<g4, kWfThreads, smem, s>>>(a, w, k);
-      else wf_traverse<false><<<g4, kWfThreads, smem, s>>>(a, w, k);
-      hook(k <= a.L ? kPhTrace : kPhShadow, false, k <= a.L ? k : a.L);
-      launches += 1;
-      if (k <= a.L) {
-        hook(kPhShade, true, k);
-        wf_shade<<<g, kWfThreads, 0, s>>>(a, w, k);
-        hook(kPhShade, false, k);
-        launches += 1;
-      }
-    }
-  } else {
-    for (int k = 1; k <= a.L; ++k) {
-      hook(kPhTrace, true, k);
-      if (stats) wf_trace<true><<<g, kWfThreads, smem, s>>>(a, w, k);
-      else wf_trace<false><<<g, kWfThreads, smem, s>>>(a, w, k);
-      hook(kPhTrace, false, k);
-      hook(kPhShade, true, k);
-      wf_shade<<<g, kWfThreads, 0, s>>>(a, w, k);
-      hook(kPhShade, false, k);
-      hook(kPhShadow, true, k);
-      if (stats) wf_shadow<true><<<g, kWfThreads, smem, s>>>(a, w, k);
-      else wf_shadow<false><<<g, kWfThreads, smem, s>>>(a, w, k);
-      hook(kPhShadow, false, k);
-      launches += 3;
-    }
-  }
-  hook(kPhFinish, true);
-  wf_finish<<<g, kWfThreads, 0, s>>>(a, w, mode, p_out);
-  hook(kPhFinish, false);
-  hook(kPhAdjoint, true);
-  wf_adjoint<<<g, kWfThreads, 0, s>>>(a, w);
-  hook(kPhAdjoint, false);
-  return launches + 2;
+  return a.scenes ? launch_wf<true>(a, w, stats, n_sm, tune, hook, s, mode, p_out)
+                  : launch_wf<false>(a, w, stats, n_sm, tune, hook, s, mode, p_out);
 }
 
 }  // namespace dr

@@ -71,9 +71,10 @@ class Renderer:
     # ---------------------------------------------------------------- inputs
     def set_option(self, option, value):
         """option: "wavefront" (-1 auto / 0 / 1), "work_order" (0/1), "profile" (0/1) or
-        "bvh_width" (0 automatic / 2 / 4)."""
+        "bvh_width" (0 automatic / 2 / 4), "traverse_blocks" (0 = all resident) or "refill" (1..32)."""
         code = {"work_order": _lib.DR_OPT_WORK_ORDER, "wavefront": _lib.DR_OPT_WAVEFRONT,
-                "profile": _lib.DR_OPT_PROFILE, "bvh_width": _lib.DR_OPT_BVH_WIDTH}[option]
+                "profile": _lib.DR_OPT_PROFILE, "bvh_width": _lib.DR_OPT_BVH_WIDTH,
+                "traverse_blocks": _lib.DR_OPT_TRAVERSE_BLOCKS, "refill": _lib.DR_OPT_REFILL}[option]
         call("dr_set_option", self.h, code, int(value))
 
     def set_bvh_builder(self, builder="ploc", radius=16):
@@ -90,6 +91,42 @@ class Renderer:
              m.shape[0], _ptr(cam), int(scene.width), int(scene.height))
         self.width, self.height = int(scene.width), int(scene.height)
         self.kind = 0
+
+    def upload_scenes(self, items):
+        """A multi-scene batch: items = [(scene, max_path_len, n_chains), ...].
+        Afterwards init_chains(sum of n_chains, ...) with adjoint drift, step /
+        frame as usual, and resolve_scene(s) per scene."""
+        keep = []
+        descs = (_lib.dr_scene_desc * len(items))()
+        for i, (scene, L, n) in enumerate(items):
+            v = np.ascontiguousarray(scene.verts, np.float32)
+            t = np.ascontiguousarray(scene.tris, np.int32)
+            nr = None if scene.normals is None else np.ascontiguousarray(scene.normals, np.float32)
+            tm = np.ascontiguousarray(scene.tri_mat, np.int32)
+            m = np.ascontiguousarray(scene.materials, np.float32)
+            cam = np.ascontiguousarray(scene.camera, np.float32)
+            keep += [v, t, nr, tm, m, cam]
+            descs[i] = _lib.dr_scene_desc(v.ctypes.data, v.shape[0], t.ctypes.data,
+                                          None if nr is None else nr.ctypes.data, t.shape[0], tm.ctypes.data,
+                                          m.ctypes.data, m.shape[0], cam.ctypes.data, int(scene.width),
+                                          int(scene.height), int(L), int(n))
+        call("dr_scenes_upload_batch", self.h, descs, len(items))
+        self.batch = [(int(sc.width), int(sc.height), int(L), int(n)) for sc, L, n in items]
+        self.width, self.height = sum(w * h for w, h, _, _ in self.batch), 1  # the shared accumulator
+        self.kind = 2
+        del keep
+
+    def resolve_scene(self, s, out=None):
+        w, h = self.batch[s][0], self.batch[s][1]
+        if out is None:
+            out = torch.empty((h, w, 3), dtype=torch.float32, device=self.device)
+        call("dr_resolve_scene", self.h, int(s), _ptr(out))
+        return out
+
+    def scene_counters(self, s):
+        tc, k0 = C.c_uint64(), C.c_double()
+        call("dr_get_scene_counters", self.h, int(s), C.byref(tc), C.byref(k0))
+        return {"tour_count": tc.value, "k0": k0.value}
 
     def set_mixture(self, mix):
         w = np.ascontiguousarray(mix.w, np.float32).reshape(-1)

@@ -331,6 +331,31 @@ def procedural_scene(seed=1, width=1280, height=720, target_tris=1_000_000, n_ob
     return b.build(cam, width, height, f"procedural-{target_tris}-{width}x{height}")
 
 
+def procedural_batch(n_scenes=64, total_chains=1 << 21, seed=2605, tris_range=(1_000, 200_000),
+                     size_range=(128, 512), L_range=(4, 16)):
+    """The multi-scene workload: ``n_scenes`` variants of the procedural
+    scene (scene seed 1..n) with triangle counts log-uniform over
+    ``tris_range``, square images with sides uniform over ``size_range``
+    (multiples of 16), path lengths uniform over ``L_range``, and
+    ``total_chains`` split in proportion to the pixel counts.  Returns
+    [(scene, max_path_len, n_chains), ...]."""
+    rng = np.random.default_rng(seed)
+    specs = []
+    for i in range(n_scenes):
+        tris = int(round(math.exp(rng.uniform(math.log(tris_range[0]), math.log(tris_range[1])))))
+        side = int(rng.integers(size_range[0] // 16, size_range[1] // 16 + 1)) * 16
+        L = int(rng.integers(L_range[0], L_range[1] + 1))
+        specs.append((i + 1, tris, side, L))
+    px = np.array([side * side for _, _, side, _ in specs], np.float64)
+    chains = np.floor(total_chains * px / px.sum()).astype(np.int64)
+    chains[-1] += total_chains - chains.sum()
+    out = []
+    for (sseed, tris, side, L), n in zip(specs, chains):
+        n_obj = int(max(2, min(200, round(tris / 1000))))
+        out.append((procedural_scene(sseed, side, side, target_tris=tris, n_objects=n_obj), L, int(n)))
+    return out
+
+
 def furnace_box(albedo=0.5, emission=1.0, width=8, height=8):
     """Closed room whose walls all reflect (Lambertian, ``albedo``) and emit
     (``emission``, facing inward).  Radiance is the same everywhere: truncated

@@ -372,6 +372,86 @@ def test_bvh_widths_give_the_same_chains(torch, R):
     assert np.allclose(acc_a, acc_b, rtol=1e-3, atol=1e-9 * np.abs(acc_a).max())
 
 
+def batch_items():
+    return [(S.cornell_box(1, 32, 32), 4, 8192),
+            (S.cornell_box(2, 48, 40, glossy=True), 6, 12000),
+            (S.procedural_scene(3, 64, 36, target_tris=20000, n_objects=20), 8, 20000)]
+
+
+def test_batch_matches_separate_contexts(torch, R):
+    """A multi-scene batch advances each scene exactly as a context of its
+    own with key (seed_lo, seed_hi + scene): same chain states, k0, tour
+    counts and images, bit for bit."""
+    items = batch_items()
+    seed, T = 77, 6
+    rb = R.Renderer()
+    rb.upload_scenes(items)
+    N = sum(n for _, _, n in items)
+    rb.init_chains(N, seed, R.make_params(L=16, drift="adjoint", k0=0.0, steps_per_splat=4))
+    rb.step(T)
+    stb = rb.readback_state(("x", "killed", "logp", "score"))
+    imgs = [rb.resolve_scene(s).cpu().numpy() for s in range(len(items))]
+    cnt = [rb.scene_counters(s) for s in range(len(items))]
+    rb.close()
+    c0 = 0
+    for s, (scene, L, n) in enumerate(items):
+        r = R.Renderer()
+        r.set_option("wavefront", 1)
+        r.set_option("bvh_width", 4)
+        r.upload_scene(scene)
+        r.init_chains(n, seed + (s << 32), R.make_params(L=L, drift="adjoint", k0=0.0, steps_per_splat=4))
+        r.step(T)
+        st = r.readback_state(("x", "killed", "logp", "score"))
+        img = r.resolve().cpu().numpy()
+        c = r.counters()
+        r.close()
+        d = S.pss_dim(L)
+        assert np.array_equal(stb["x"][c0:c0 + n, :d], st["x"])
+        assert np.array_equal(stb["killed"][c0:c0 + n], st["killed"])
+        assert np.array_equal(stb["logp"][c0:c0 + n], st["logp"])
+        alive = st["killed"] == 0
+        assert np.array_equal(stb["score"][c0:c0 + n, :d][alive], st["score"][alive])
+        assert cnt[s]["k0"] == c["k0"] and cnt[s]["tour_count"] == c["tour_count"]
+        assert np.array_equal(imgs[s], img)
+        c0 += n
+
+
+def test_batch_graph_frames_and_errors(torch, R):
+    from paper_2605_08916_gb300 import _lib
+    items = batch_items()
+    N = sum(n for _, _, n in items)
+    stream = torch.cuda.Stream()
+    r = R.Renderer(0, stream)
+    r.upload_scenes(items)
+    with pytest.raises(_lib.DRError):
+        r.init_chains(N + 1, 5, R.make_params(L=8, drift="adjoint", k0=0.0))
+    with pytest.raises(_lib.DRError):
+        r.init_chains(N, 5, R.make_params(L=8, drift="fd", k0=0.0))
+    with pytest.raises(_lib.DRError):
+        r.resolve()
+    prm = R.make_params(L=8, drift="adjoint", k0=0.0, steps_per_splat=4)
+    r.init_chains(N, 5, prm)
+    r.step(8)
+    a = [r.resolve_scene(s).cpu().numpy() for s in range(3)]
+    r.init_chains(N, 5, prm)
+    r.frame(4)
+    r.frame(4)
+    b = [r.resolve_scene(s).cpu().numpy() for s in range(3)]
+    stream.synchronize()
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+        assert np.isfinite(x).all() and x.max() > 0
+    one = S.cornell_box(1, 8, 8)
+    keep = np.zeros(one.n_tris, bool)
+    keep[0] = True
+    tiny = S.Scene(verts=one.verts, tris=np.ascontiguousarray(one.tris[keep]),
+                   tri_mat=np.ascontiguousarray(one.tri_mat[keep]), materials=one.materials, camera=one.camera,
+                   width=8, height=8, normals=one.normals).check()
+    with pytest.raises(_lib.DRError):
+        r.upload_scenes([(tiny, 4, 128)])
+    r.close()
+
+
 @pytest.mark.parametrize("chains", [8192, 1 << 17])
 def test_graph_frames_match_plain_steps(torch, R, chains):
     """dr_frame (captured once, replayed with the step index in device
