@@ -159,22 +159,34 @@ def cpu_baseline(wl, scene, steps=8, target_s=15.0):
 
 
 def run_reference(args, wl, rank, world):
+    """The reference arm: the FP64 oracle, as it stands, on this host's
+    cores, timing init + args.steps steps of a bounded sample of the
+    workload's chains (sized by a calibration run so that the timed run
+    takes about ten seconds), after args.warmup untimed one-step runs."""
     if rank != 0:
         return 0
     scene = wl["scene"]()
     from oracle import oracle as O
     tgt = O.OracleScene(scene)
     prm = O.make_params(L=wl["L"], drift="exact" if wl["drift"] == "adjoint" else wl["drift"], rb=True, k0=1.0)
-    est = O.restore_run(tgt, prm, seed=SEED, chain_ids=np.arange(256), n_steps=0, record=False)
-    prm.k0 = est["p_init_sum"] / 256 / (64.0 * 1e-5)
-    m = max(16, wl["cpu_chains"] // 2)
+    est = O.restore_run(tgt, prm, seed=SEED, chain_ids=np.arange(4096), n_steps=0, record=False)
+    prm.k0 = est["p_init_sum"] / 4096 / (64.0 * 1e-5)
     for _ in range(args.warmup):
-        O.restore_run(tgt, prm, seed=SEED, chain_ids=np.arange(16), n_steps=1, record=False, accum=False)
+        O.restore_run(tgt, prm, seed=SEED, chain_ids=np.arange(256), n_steps=1, record=False, accum=False)
+    m = 1024
+    while True:
+        t0 = time.perf_counter()
+        O.restore_run(tgt, prm, seed=SEED, chain_ids=np.arange(m), n_steps=args.steps, record=False, accum=False)
+        dt = time.perf_counter() - t0
+        if dt > 1.0 or m >= wl["chains"]:
+            break
+        m = min(wl["chains"], m * 4)
+    m = int(max(256, min(wl["chains"], m * 10.0 / max(dt, 1e-3))))
     t0 = time.perf_counter()
     O.restore_run(tgt, prm, seed=SEED, chain_ids=np.arange(m), n_steps=args.steps, record=False, accum=False)
     dt = time.perf_counter() - t0
     value = m * (args.steps + 1) / dt
-    sample = f"{m} chains x {args.steps + 1} steps of the workload, FP64 oracle"
+    sample = f"{m} chains x {args.steps + 1} steps (init + {args.steps}) of the workload, FP64 oracle, OpenMP"
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / (args.steps + 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
