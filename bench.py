@@ -220,6 +220,7 @@ def run_ours(args, wl, rank, world, local):
     r.set_option("work_order", args.work_order)
     r.set_option("wavefront", args.wavefront)
     r.set_option("bvh_width", args.bvh_width)
+    r.set_option("ray_order", args.ray_order)
     r.upload_scene(scene)
     stream.synchronize()
     t_init = time.perf_counter()
@@ -482,6 +483,7 @@ def run_batched(args, rank, world, local):
     log(f"batch: {len(items)} scenes, {tris} triangles, {pixels} pixels, {N} chains")
     stream = torch.cuda.Stream(device=dev)
     r = R.Renderer(local, stream)
+    r.set_option("ray_order", args.ray_order)
     r.upload_scenes(items)
     seed = replica_seed(SEED, rank)
     prm = R.make_params(L=16, drift="adjoint", rb=True, k0=0.0, steps_per_splat=8)
@@ -597,6 +599,8 @@ def main():
     ap.add_argument("--wavefront", type=int, default=-1, choices=[-1, 0, 1],
                     help="bounce-by-bounce execution over compacted path queues: 1 on, 0 fused kernel, "
                          "-1 (default) by chain count")
+    ap.add_argument("--ray-order", type=int, default=-1, choices=[-1, 0, 1],
+                    help="sort camera rays by pixel before the first traversal (-1: by triangle count)")
     ap.add_argument("--bvh-width", type=int, default=0, choices=[0, 2, 4],
                     help="BVH the rays traverse: 4-wide, binary, or 0 (default) 4-wide in the bounce-by-bounce "
                          "passes and binary in the fused kernel")

@@ -307,6 +307,12 @@ int dr_pt_render(dr_ctx* ctx, int32_t max_path_len, uint32_t spp, uint64_t seed,
  *                      all resident blocks).
  *   DR_OPT_REFILL      a traversal warp fetches new rays once fewer than
  *                      this many of its 32 lanes are busy (1..32; default 24).
+ *   DR_OPT_RAY_ORDER   1: before the first traversal of a bounce-by-bounce
+ *                      step the camera rays are sorted by pixel (Morton
+ *                      order; scene first in a batch), so that neighbouring
+ *                      lanes trace neighbouring rays; 0: chain order; -1
+ *                      (default): on from 2^17 triangles (a batch counts
+ *                      all its scenes).  Results are the same either way.
  *   DR_OPT_BVH_WIDTH   4: rays traverse the 4-wide BVH collapsed from the
  *                      binary one at scene upload (when it was built, see
  *                      dr_bvh4_info); 2: the binary BVH; 0 (default): the
@@ -314,7 +320,7 @@ int dr_pt_render(dr_ctx* ctx, int32_t max_path_len, uint32_t spp, uint64_t seed,
  *                      Both return the same closest hit (ties: smaller id).
  * Errors: INVALID_ARG (unknown option or value). */
 enum { DR_OPT_WORK_ORDER = 1, DR_OPT_WAVEFRONT = 2, DR_OPT_PROFILE = 3, DR_OPT_BVH_WIDTH = 4,
-       DR_OPT_TRAVERSE_BLOCKS = 5, DR_OPT_REFILL = 6 };
+       DR_OPT_TRAVERSE_BLOCKS = 5, DR_OPT_REFILL = 6, DR_OPT_RAY_ORDER = 7 };
 int dr_set_option(dr_ctx* ctx, int32_t option, int32_t value);
 
 /* Per-phase device time accumulated since the last call while DR_OPT_PROFILE

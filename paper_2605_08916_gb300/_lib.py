@@ -31,7 +31,7 @@ EXPORTS = ["dr_version", "dr_last_error", "dr_create", "dr_destroy", "dr_scene_u
            "dr_splat_records_noalloc", "dr_set_option", "dr_get_profile", "dr_frame", "dr_bvh4_info", "dr_get_bounce_profile",
            "dr_scenes_upload_batch", "dr_resolve_scene", "dr_get_scene_counters"]
 DR_OPT_WORK_ORDER, DR_OPT_WAVEFRONT, DR_OPT_PROFILE, DR_OPT_BVH_WIDTH = 1, 2, 3, 4
-DR_OPT_TRAVERSE_BLOCKS, DR_OPT_REFILL = 5, 6
+DR_OPT_TRAVERSE_BLOCKS, DR_OPT_REFILL, DR_OPT_RAY_ORDER = 5, 6, 7
 DR_PHASES = 10
 PHASE_NAMES = ["wf_begin", "trace", "shade", "shadow", "finish", "adjoint", "fused_step", "fd_score", "splat",
                "work_order"]

@@ -44,6 +44,7 @@ struct dr_ctx {
   unsigned long long* batch_tours = nullptr;  // [n_scenes]
   double* batch_psum = nullptr;               // [n_scenes]
   WfTuning tune;                              // DR_OPT_TRAVERSE_BLOCKS, DR_OPT_REFILL
+  int ray_order = -1;                         // DR_OPT_RAY_ORDER (-1 automatic)
   float4* surf = nullptr;
   float4* lights = nullptr;
   float* nrm = nullptr;
@@ -381,6 +382,31 @@ int ensure_wavefront_buffers(dr_ctx* c) {
 }
 
 // one chain step (init = Alg. 1, else Alg. 2); records into the next slot
+// Camera-ray ordering for the bounce-by-bounce passes (DR_OPT_RAY_ORDER):
+// Morton keys over the largest image side, above them the scene index of a
+// batch; off when the key would not fit 32 bits.
+RayOrder ray_order(dr_ctx* c, StepArgs& a) {
+  RayOrder o;
+  // automatic: on for large geometry, where coherent camera rays save more
+  // traversal time than the sort and the scattered slot accesses cost
+  // (measured: +5% at 1M triangles, +7% for a 2M-triangle batch, -5% at 20k)
+  const bool on = c->ray_order == 1 || (c->ray_order == -1 && c->nt >= (1 << 17));
+  if (!on || !c->order_a || !c->order_b || !c->sort_scratch) return o;
+  int side = c->target == 2 ? 1 : std::max(c->W, c->H);
+  for (size_t q = 0; q < c->batch_w.size(); ++q) side = std::max(side, std::max(c->batch_w[q], c->batch_h[q]));
+  int b = 0;
+  while ((1 << b) < side) ++b;
+  int sb = 0;
+  while ((1u << sb) < (unsigned)std::max<size_t>(1, c->h_sc.size())) ++sb;
+  if (b > 16 || 2 * b + (c->target == 2 ? sb : 0) > 32) return o;
+  o.keys = c->order_a;
+  o.alt = c->order_b;
+  o.scratch = c->sort_scratch;
+  o.bits = 2 * b + (c->target == 2 ? sb : 0);
+  a.key_shift = 2 * b;
+  return o;
+}
+
 int one_step(dr_ctx* c, bool init) {
   if (!init && c->rec_count >= c->rec_cap) DR_TRY(flush(c));
   StepArgs a = step_args(c);
@@ -394,7 +420,8 @@ int one_step(dr_ctx* c, bool init) {
   if (use_wavefront(c)) {
     DR_TRY(ensure_wavefront_buffers(c));
     const WfBuffers w = wf_carve(c->wf_mem, c->N, c->prm.max_path_len);
-    c->launches += launch_wavefront_step(a, w, c->stats, c->n_sm, c->tune, hook, c->stream);
+    const RayOrder ord = ray_order(c, a);
+    c->launches += launch_wavefront_step(a, w, c->stats, c->n_sm, c->tune, hook, c->stream, kWfStep, nullptr, ord);
     DR_TRY(check_launch("wavefront step"));
   } else {
     if (!init && c->work_order && c->prm.drift_mode == DR_DRIFT_ADJOINT && c->target == 0) {
@@ -1362,7 +1389,7 @@ std::vector<unsigned long long> frame_key(const dr_ctx* c, uint32_t n_steps) {
                                        (unsigned long long)c->nt, (unsigned long long)c->n_lights, P(c->stream),
                                        c->target_gen, P(c->d_scenes), P(c->d_sc), P(c->chain_scene),
                                        (unsigned long long)c->tune.blocks_per_sm,
-                                       (unsigned long long)c->tune.refill};
+                                       (unsigned long long)c->tune.refill, (unsigned long long)c->ray_order};
   for (unsigned long long v : prm) k.push_back(v);
   return k;
 }
@@ -1513,6 +1540,10 @@ int dr_set_option(dr_ctx* c, int32_t option, int32_t value) {
     case DR_OPT_REFILL:
       if (value < 1 || value > 32) return fail(DR_ERR_INVALID_ARG, "dr_set_option: refill is 1..32");
       c->tune.refill = value;
+      return DR_OK;
+    case DR_OPT_RAY_ORDER:
+      if (value < -1 || value > 1) return fail(DR_ERR_INVALID_ARG, "dr_set_option: ray order is -1, 0 or 1");
+      c->ray_order = value;
       return DR_OK;
     case DR_OPT_BVH_WIDTH:
       if (value != 0 && value != 2 && value != 4)

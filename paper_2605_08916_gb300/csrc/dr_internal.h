@@ -126,6 +126,10 @@ struct StepArgs {
   double* p_partial;  // [gridDim.x] init only
   uint32_t* err;
   int refill;  // persistent traversal: refill a warp below this many busy lanes
+  // camera-ray order (null: chain order): wf_begin writes (key, chain) with
+  // key = the pixel's Morton code (above it the scene of a batch chain)
+  uint2* ray_keys;
+  int key_shift;  // Morton bits: a batch chain's key is (scene << key_shift) | morton
 };
 
 // (key, chain) pairs for the work order of the next step
@@ -184,8 +188,18 @@ struct WfTuning {
   int blocks_per_sm = 0;
   int refill = 24;
 };
+// Sorting of the camera rays by pixel before the first traversal: the key
+// buffer (a.ray_keys), its ping-pong partner, the sort scratch and the
+// number of key bits.  keys == null: rays in chain order.
+struct RayOrder {
+  uint2* keys = nullptr;
+  uint2* alt = nullptr;
+  void* scratch = nullptr;
+  int bits = 0;
+};
 int launch_wavefront_step(const StepArgs& a, const WfBuffers& w, bool stats, int n_sm, const WfTuning& tune,
-                          const PhaseHook& hook, cudaStream_t s, WfMode mode = kWfStep, float* p_out = nullptr);
+                          const PhaseHook& hook, cudaStream_t s, WfMode mode = kWfStep, float* p_out = nullptr,
+                          const RayOrder& order = RayOrder{});
 // step index += 1 on the device (graph replay)
 void launch_advance_step(uint32_t* step, cudaStream_t s);
 

@@ -102,6 +102,23 @@ DR_D const DevScene& scene_of(const StepArgs& a, int sid) {
   return BATCH ? a.scenes[sid] : a.S;
 }
 
+// Morton (Z-order) interleave of two 16-bit coordinates
+DR_D uint32_t spread16(uint32_t v) {
+  v &= 0xffffu;
+  v = (v | (v << 8)) & 0x00ff00ffu;
+  v = (v | (v << 4)) & 0x0f0f0f0fu;
+  v = (v | (v << 2)) & 0x33333333u;
+  v = (v | (v << 1)) & 0x55555555u;
+  return v;
+}
+DR_D uint32_t morton2(uint32_t x, uint32_t y) { return spread16(x) | (spread16(y) << 1); }
+
+// queue[1] = the chains of the sorted (key, chain) pairs
+__global__ void wf_order_queue(const uint2* __restrict__ sorted, unsigned long long n, uint32_t* __restrict__ q) {
+  const unsigned long long t = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) q[t] = sorted[t].y;
+}
+
 template <bool BATCH>
 __global__ void __launch_bounds__(kWfThreads) wf_begin(StepArgs a, WfBuffers w) {
   for (unsigned long long j = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; j < a.N;
@@ -109,7 +126,14 @@ __global__ void __launch_bounds__(kWfThreads) wf_begin(StepArgs a, WfBuffers w) 
     const ChainView v = chain_view<BATCH>(a, j);
     evolve_x(a, chain_rng<BATCH>(a, v), step_index(a), j, v.cj, v.d, a.init || a.killed[j] != 0);
     PathState ps;
-    const int pix = path_begin(scene_of<BATCH>(a, v.sid), XSoA{a.x, a.N, j}, ps);
+    const DevScene& S = scene_of<BATCH>(a, v.sid);
+    const int pix = path_begin(S, XSoA{a.x, a.N, j}, ps);
+    if (a.ray_keys) {
+      const uint32_t px = (uint32_t)pix % (uint32_t)S.W, py = (uint32_t)pix / (uint32_t)S.W;
+      uint32_t key = morton2(px, py);
+      if (BATCH) key |= (uint32_t)v.sid << a.key_shift;
+      a.ray_keys[j] = make_uint2(key, (uint32_t)j);
+    }
     store_slot(w.slot, j, ps, pix);
     w.hit[j] = -1;
   }
@@ -122,7 +146,7 @@ __global__ void __launch_bounds__(kWfThreads, kWfTraceMinBlocks) wf_trace(StepAr
   extern __shared__ int smem[];
   TraceStack<kWfStack> st{smem + threadIdx.x, (int)blockDim.x};
   const uint32_t n = w.counts[k];
-  const uint32_t* q = k == 1 ? nullptr : w.queue[k & 1];
+  const uint32_t* q = k == 1 && !a.ray_keys ? nullptr : w.queue[k & 1];
   uint32_t err = 0;
   TraceStats stats{0u, 0u};
   unsigned long long rays = 0;
@@ -176,7 +200,7 @@ __global__ void __launch_bounds__(kWfThreads, kWfTrace4MinBlocks) wf_traverse(St
   const uint32_t n_ray = k <= a.L ? w.counts[k] : 0u;
   const uint32_t n_shadow = k >= 2 ? w.counts[kWfShadowCount0 + k - 1] : 0u;
   const uint32_t n = n_ray + n_shadow;
-  const uint32_t* q = k == 1 ? nullptr : w.queue[k & 1];
+  const uint32_t* q = k == 1 && !a.ray_keys ? nullptr : w.queue[k & 1];
   uint32_t* ctr = &w.counts[kWfFetch0 + k];
   uint32_t err = 0;
   TraceStats stats{0u, 0u};
@@ -267,7 +291,7 @@ __global__ void __launch_bounds__(kWfThreads, kWfTrace4MinBlocks) wf_traverse(St
 template <bool BATCH>
 __global__ void __launch_bounds__(kWfThreads) wf_shade(StepArgs a, WfBuffers w, int k) {
   const uint32_t n = w.counts[k];
-  const uint32_t* q = k == 1 ? nullptr : w.queue[k & 1];
+  const uint32_t* q = k == 1 && !a.ray_keys ? nullptr : w.queue[k & 1];
   uint32_t* qn = w.queue[(k + 1) & 1];
   const uint32_t n_iter = (n + gridDim.x * blockDim.x - 1) / (gridDim.x * blockDim.x);
   // every lane runs the same number of iterations so the queue appends see
@@ -431,7 +455,7 @@ int traverse_blocks_per_sm(size_t smem) {
 
 template <bool BATCH>
 int launch_wf(const StepArgs& a, const WfBuffers& w, bool stats, int n_sm, const WfTuning& tune,
-              const PhaseHook& hook, cudaStream_t s, WfMode mode, float* p_out) {
+              const PhaseHook& hook, cudaStream_t s, WfMode mode, float* p_out, const RayOrder& order) {
   const int max_blocks = n_sm * 16;
   const unsigned g = grid_for(a.N, max_blocks);
   if (mode == kWfInitClock) {
@@ -452,6 +476,16 @@ int launch_wf(const StepArgs& a, const WfBuffers& w, bool stats, int n_sm, const
   wf_begin<BATCH><<<g, kWfThreads, 0, s>>>(a, w);
   hook(kPhBegin, false);
   launches += 2;
+  if (a.ray_keys) {
+    // camera rays in pixel (Morton) order: neighbouring lanes trace
+    // neighbouring rays, here and, through the order-keeping queue
+    // appends, at later bounces
+    hook(kPhOrder, true);
+    const uint2* sorted = sort_pairs(order.keys, order.alt, a.N, order.bits, order.scratch, s);
+    wf_order_queue<<<(unsigned)((a.N + 255) / 256), 256, 0, s>>>(sorted, a.N, w.queue[1]);
+    hook(kPhOrder, false);
+    launches += 1 + 5 * ((order.bits + 7) / 8);
+  }
   if (wide) {
     // traverse(k) = closest-hit rays of bounce k + shadow rays of bounce
     // k - 1; the last launch (k = L + 1) carries the final shadow rays
@@ -517,10 +551,12 @@ WfBuffers wf_carve(void* base, unsigned long long N, int L) {
 }
 
 int launch_wavefront_step(const StepArgs& a, const WfBuffers& w, bool stats, int n_sm, const WfTuning& tune,
-                          const PhaseHook& hook, cudaStream_t s, WfMode mode, float* p_out) {
+                          const PhaseHook& hook, cudaStream_t s, WfMode mode, float* p_out, const RayOrder& order) {
   if (a.N == 0) return 0;
-  return a.scenes ? launch_wf<true>(a, w, stats, n_sm, tune, hook, s, mode, p_out)
-                  : launch_wf<false>(a, w, stats, n_sm, tune, hook, s, mode, p_out);
+  StepArgs b = a;
+  b.ray_keys = order.keys;
+  return a.scenes ? launch_wf<true>(b, w, stats, n_sm, tune, hook, s, mode, p_out, order)
+                  : launch_wf<false>(b, w, stats, n_sm, tune, hook, s, mode, p_out, order);
 }
 
 }  // namespace dr
