@@ -144,19 +144,18 @@ struct __align__(16) ShadowRec {
   int ex1, pad0, pad1, pad2;
 };
 // counters: [k] = rays of bounce k (1..16), [17 + k] = shadow rays of bounce
-// k, [34] = surviving chains for the adjoint pass, [35 + k] / [52 + k] =
-// fetch positions of the persistent trace / shadow passes of bounce k
+// k, [35 + k] = fetch position of the traversal pass of bounce k, [52 + s] =
+// surviving chains with s path segments (0..16), queued for the adjoint
 constexpr int kWfShadowCount0 = 17;
-constexpr int kWfAdjointCount = 34;
 constexpr int kWfFetch0 = 35;
-constexpr int kWfShadowFetch0 = 52;
+constexpr int kWfAdjBucket0 = 52;
 constexpr int kWfCounts = 69;
 struct WfBuffers {
   float4* slot;        // [N][4] path state
   int* hit;            // [N] closest-hit triangle of the current ray
   uint32_t* queue[2];  // ray queues (ping-pong), chain ids
   ShadowRec* shadow;   // [N] shadow queue of the current bounce
-  uint32_t* adj;       // [N] chains for the adjoint pass
+  uint32_t* adj;       // [17][N] chains for the adjoint pass, by path length
   uint32_t* counts;    // [kWfCounts]
   float4* tape;        // [L][3][N]
 };

@@ -67,6 +67,18 @@ DR_D uint32_t warp_append(uint32_t* count, bool take) {
   return base + __popc(want & ((1u << lane) - 1u));
 }
 
+// Appends to one of several queues (counters[key]): the lanes of `want`
+// (every lane calling, and only those) group by key, one atomic per group.
+DR_D uint32_t keyed_append(uint32_t* counters, int key, unsigned want) {
+  const int lane = threadIdx.x & 31;
+  const unsigned peers = __match_any_sync(want, key);
+  const int leader = __ffs(peers) - 1;
+  uint32_t base = 0;
+  if (lane == leader) base = atomicAdd(&counters[key], (uint32_t)__popc(peers));
+  base = __shfl_sync(peers, base, leader);
+  return base + __popc(peers & ((1u << lane) - 1u));
+}
+
 DR_D void add_counts(unsigned long long* target, unsigned long long v) {
   const unsigned long long w = warp_sum_u64(v);
   if ((threadIdx.x & 31) == 0 && w && target) atomicAdd(target, w);
@@ -378,10 +390,12 @@ __global__ void __launch_bounds__(kWfThreads) wf_finish(StepArgs a, WfBuffers w,
   for (unsigned long long it = 0; it < n_iter; ++it) {
     const unsigned long long j = it * gridDim.x * blockDim.x + (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
     bool survive = false;
+    int nseg = 0;
     if (j < a.N) {
       PathState ps;
       int pix;
       load_slot(w.slot, j, ps, pix);
+      nseg = min(max(ps.nseg, 0), kMaxPathLen);
       const float3 f = ps.f;
       const float p = lum(f) + a.eps;
       if (!(isfinite(p) && isfinite(f.x) && isfinite(f.y) && isfinite(f.z))) err |= kErrNonFinite;
@@ -414,8 +428,12 @@ __global__ void __launch_bounds__(kWfThreads) wf_finish(StepArgs a, WfBuffers w,
         survive = !killed && mode == kWfStep;
       }
     }
-    const uint32_t ai = warp_append(&w.counts[kWfAdjointCount], survive);
-    if (survive) w.adj[ai] = (uint32_t)j;
+    // survivors queue by path length, so that the adjoint's warps run
+    // loops of equal trip count
+    if (survive) {
+      const uint32_t ai = keyed_append(&w.counts[kWfAdjBucket0], nseg, __ballot_sync(__activemask(), true));
+      w.adj[(size_t)nseg * a.N + ai] = (uint32_t)j;
+    }
   }
   add_counts(a.tour_count, kills);
   if (err) atomicOr(a.err, err);
@@ -423,9 +441,22 @@ __global__ void __launch_bounds__(kWfThreads) wf_finish(StepArgs a, WfBuffers w,
 
 template <bool BATCH>
 __global__ void __launch_bounds__(kWfThreads, 4) wf_adjoint(StepArgs a, WfBuffers w) {
-  const uint32_t n = w.counts[kWfAdjointCount];
+  // the queue is the concatenation of the path-length buckets, longest first
+  __shared__ uint32_t off[kMaxPathLen + 2];
+  if (threadIdx.x == 0) {
+    uint32_t acc = 0;
+    for (int b = kMaxPathLen; b >= 0; --b) {
+      off[b + 1] = acc;
+      acc += w.counts[kWfAdjBucket0 + b];
+    }
+    off[0] = acc;  // total
+  }
+  __syncthreads();
+  const uint32_t n = off[0];
   for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
-    const unsigned long long j = w.adj[t];
+    int b = kMaxPathLen;
+    while (b > 0 && t >= off[b]) --b;  // bucket b holds positions [off[b + 1], off[b])
+    const unsigned long long j = w.adj[(size_t)b * a.N + (t - off[b + 1])];
     PathState ps;
     int pix;
     load_slot(w.slot, j, ps, pix);
@@ -531,8 +562,8 @@ int launch_wf(const StepArgs& a, const WfBuffers& w, bool stats, int n_sm, const
 
 size_t wf_bytes(unsigned long long N, int L) {
   auto a = [](size_t b) { return (b + 255) & ~(size_t)255; };
-  return a(N * 64) + a(N * 4) + 2 * a(N * 4) + a(N * sizeof(ShadowRec)) + a(N * 4) + a(kWfCounts * 4) +
-         a((size_t)L * 3 * N * 16);
+  return a(N * 64) + a(N * 4) + 2 * a(N * 4) + a(N * sizeof(ShadowRec)) + a((size_t)(kMaxPathLen + 1) * N * 4) +
+         a(kWfCounts * 4) + a((size_t)L * 3 * N * 16);
 }
 
 WfBuffers wf_carve(void* base, unsigned long long N, int L) {
@@ -544,7 +575,7 @@ WfBuffers wf_carve(void* base, unsigned long long N, int L) {
   w.queue[0] = reinterpret_cast<uint32_t*>(p); p += a(N * 4);
   w.queue[1] = reinterpret_cast<uint32_t*>(p); p += a(N * 4);
   w.shadow = reinterpret_cast<ShadowRec*>(p); p += a(N * sizeof(ShadowRec));
-  w.adj = reinterpret_cast<uint32_t*>(p); p += a(N * 4);
+  w.adj = reinterpret_cast<uint32_t*>(p); p += a((size_t)(kMaxPathLen + 1) * N * 4);
   w.counts = reinterpret_cast<uint32_t*>(p); p += a(kWfCounts * 4);
   w.tape = reinterpret_cast<float4*>(p);
   return w;
