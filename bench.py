@@ -221,6 +221,8 @@ def run_ours(args, wl, rank, world, local):
     r.set_option("wavefront", args.wavefront)
     r.set_option("bvh_width", args.bvh_width)
     r.set_option("ray_order", args.ray_order)
+    if args.tail_bounce is not None:
+        r.set_option("tail_bounce", args.tail_bounce)
     r.upload_scene(scene)
     stream.synchronize()
     t_init = time.perf_counter()
@@ -484,6 +486,8 @@ def run_batched(args, rank, world, local):
     stream = torch.cuda.Stream(device=dev)
     r = R.Renderer(local, stream)
     r.set_option("ray_order", args.ray_order)
+    if args.tail_bounce is not None:
+        r.set_option("tail_bounce", args.tail_bounce)
     r.upload_scenes(items)
     seed = replica_seed(SEED, rank)
     prm = R.make_params(L=16, drift="adjoint", rb=True, k0=0.0, steps_per_splat=8)
@@ -599,6 +603,8 @@ def main():
     ap.add_argument("--wavefront", type=int, default=-1, choices=[-1, 0, 1],
                     help="bounce-by-bounce execution over compacted path queues: 1 on, 0 fused kernel, "
                          "-1 (default) by chain count")
+    ap.add_argument("--tail-bounce", type=int, default=None,
+                    help="run the bounces from this one on as one persistent pass (0 off; default: library's choice)")
     ap.add_argument("--ray-order", type=int, default=-1, choices=[-1, 0, 1],
                     help="sort camera rays by pixel before the first traversal (-1: by triangle count)")
     ap.add_argument("--bvh-width", type=int, default=0, choices=[0, 2, 4],

@@ -313,6 +313,12 @@ int dr_pt_render(dr_ctx* ctx, int32_t max_path_len, uint32_t spp, uint64_t seed,
  *                      lanes trace neighbouring rays; 0: chain order; -1
  *                      (default): on from 2^17 triangles (a batch counts
  *                      all its scenes).  Results are the same either way.
+ *   DR_OPT_TAIL_BOUNCE k >= 1: from the shading of bounce k on, each path
+ *                      runs to its end inside one persistent pass (its
+ *                      shadow rays, next rays and shading interleaved per
+ *                      lane) instead of one launch per pass and bounce; the
+ *                      arithmetic per path is the same.  0: no tail pass;
+ *                      -1 (default): automatic.  4-wide BVH only.
  *   DR_OPT_BVH_WIDTH   4: rays traverse the 4-wide BVH collapsed from the
  *                      binary one at scene upload (when it was built, see
  *                      dr_bvh4_info); 2: the binary BVH; 0 (default): the
@@ -320,7 +326,7 @@ int dr_pt_render(dr_ctx* ctx, int32_t max_path_len, uint32_t spp, uint64_t seed,
  *                      Both return the same closest hit (ties: smaller id).
  * Errors: INVALID_ARG (unknown option or value). */
 enum { DR_OPT_WORK_ORDER = 1, DR_OPT_WAVEFRONT = 2, DR_OPT_PROFILE = 3, DR_OPT_BVH_WIDTH = 4,
-       DR_OPT_TRAVERSE_BLOCKS = 5, DR_OPT_REFILL = 6, DR_OPT_RAY_ORDER = 7 };
+       DR_OPT_TRAVERSE_BLOCKS = 5, DR_OPT_REFILL = 6, DR_OPT_RAY_ORDER = 7, DR_OPT_TAIL_BOUNCE = 8 };
 int dr_set_option(dr_ctx* ctx, int32_t option, int32_t value);
 
 /* Per-phase device time accumulated since the last call while DR_OPT_PROFILE
@@ -329,8 +335,9 @@ int dr_set_option(dr_ctx* ctx, int32_t option, int32_t value);
  * 0 wavefront begin (Evolve + camera rays), 1 closest-hit traversal,
  * 2 shading / NEE / BSDF sampling, 3 shadow-ray traversal, 4 clock and
  * records, 5 adjoint, 6 fused step kernel, 7 finite-difference score,
- * 8 splat (sort + reduce), 9 work-order sort. */
-enum { DR_PHASES = 10 };
+ * 8 splat (sort + reduce), 9 work-order / camera-ray sort, 10 the tail
+ * pass (shading and traversal of the late bounces, DR_OPT_TAIL_BOUNCE). */
+enum { DR_PHASES = 11 };
 int dr_get_profile(dr_ctx* ctx, double* ms, uint64_t* counts, int32_t n);
 
 /* The bounce-by-bounce part of the same profile: HOST output ms[3 *

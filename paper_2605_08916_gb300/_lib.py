@@ -31,10 +31,10 @@ EXPORTS = ["dr_version", "dr_last_error", "dr_create", "dr_destroy", "dr_scene_u
            "dr_splat_records_noalloc", "dr_set_option", "dr_get_profile", "dr_frame", "dr_bvh4_info", "dr_get_bounce_profile",
            "dr_scenes_upload_batch", "dr_resolve_scene", "dr_get_scene_counters"]
 DR_OPT_WORK_ORDER, DR_OPT_WAVEFRONT, DR_OPT_PROFILE, DR_OPT_BVH_WIDTH = 1, 2, 3, 4
-DR_OPT_TRAVERSE_BLOCKS, DR_OPT_REFILL, DR_OPT_RAY_ORDER = 5, 6, 7
-DR_PHASES = 10
+DR_OPT_TRAVERSE_BLOCKS, DR_OPT_REFILL, DR_OPT_RAY_ORDER, DR_OPT_TAIL_BOUNCE = 5, 6, 7, 8
+DR_PHASES = 11
 PHASE_NAMES = ["wf_begin", "trace", "shade", "shadow", "finish", "adjoint", "fused_step", "fd_score", "splat",
-               "work_order"]
+               "work_order", "tail"]
 DR_NOALLOC_MAX_RECORDS = 65536
 DR_BVH_LBVH, DR_BVH_PLOC = 0, 1
 

@@ -8,7 +8,9 @@ API, the launch schedule that the hot path leaves open:
 * ``refill`` - the busy-lane count below which a traversal warp fetches new
   rays,
 * ``steps_per_frame`` - Restore steps per captured CUDA-graph frame (steps per
-  launch of the graph).
+  launch of the graph),
+* ``tail_bounce`` - the bounce from whose shading on each path finishes in
+  one persistent pass (0: every bounce as its own launches).
 
 The traversal stack depth is fixed at build time (40 entries, checked
 against every BVH at upload), so it is not a run-time choice.
@@ -21,13 +23,14 @@ import torch
 
 
 def default_candidates():
-    return [dict(traverse_blocks=b, refill=f, steps_per_frame=F)
-            for b, f, F in itertools.product((0, 6, 5), (20, 24, 28), (2, 4, 8))]
+    return [dict(traverse_blocks=b, refill=f, steps_per_frame=F, tail_bounce=t)
+            for b, f, F, t in itertools.product((0, 6), (20, 24), (2, 4), (0, 4, 6))]
 
 
 def apply(r, cand):
     r.set_option("traverse_blocks", cand["traverse_blocks"])
     r.set_option("refill", cand["refill"])
+    r.set_option("tail_bounce", cand["tail_bounce"])
 
 
 def autotune(r, stream, n_chains, seed, params, candidates=None, steps=8, reps=2):

@@ -45,6 +45,7 @@ struct dr_ctx {
   double* batch_psum = nullptr;               // [n_scenes]
   WfTuning tune;                              // DR_OPT_TRAVERSE_BLOCKS, DR_OPT_REFILL
   int ray_order = -1;                         // DR_OPT_RAY_ORDER (-1 automatic)
+  int tail_bounce = -1;                       // DR_OPT_TAIL_BOUNCE (-1 automatic)
   float4* surf = nullptr;
   float4* lights = nullptr;
   float* nrm = nullptr;
@@ -407,6 +408,15 @@ RayOrder ray_order(dr_ctx* c, StepArgs& a) {
   return o;
 }
 
+// The bounce from whose shading on a step runs as one persistent pass
+// (DR_OPT_TAIL_BOUNCE; 0 none).  Automatic: from bounce 4 when paths reach
+// 14 segments or more, where the late bounces hold few rays each (measured:
+// +7% on the 64-scene batch with L up to 16; no gain at L = 12).
+int tail_bounce(const dr_ctx* c) {
+  if (c->tail_bounce >= 0) return c->tail_bounce;
+  return c->prm.max_path_len >= 14 ? 4 : 0;
+}
+
 int one_step(dr_ctx* c, bool init) {
   if (!init && c->rec_count >= c->rec_cap) DR_TRY(flush(c));
   StepArgs a = step_args(c);
@@ -421,7 +431,9 @@ int one_step(dr_ctx* c, bool init) {
     DR_TRY(ensure_wavefront_buffers(c));
     const WfBuffers w = wf_carve(c->wf_mem, c->N, c->prm.max_path_len);
     const RayOrder ord = ray_order(c, a);
-    c->launches += launch_wavefront_step(a, w, c->stats, c->n_sm, c->tune, hook, c->stream, kWfStep, nullptr, ord);
+    WfTuning tune = c->tune;
+    tune.tail_bounce = tail_bounce(c);
+    c->launches += launch_wavefront_step(a, w, c->stats, c->n_sm, tune, hook, c->stream, kWfStep, nullptr, ord);
     DR_TRY(check_launch("wavefront step"));
   } else {
     if (!init && c->work_order && c->prm.drift_mode == DR_DRIFT_ADJOINT && c->target == 0) {
@@ -1389,7 +1401,8 @@ std::vector<unsigned long long> frame_key(const dr_ctx* c, uint32_t n_steps) {
                                        (unsigned long long)c->nt, (unsigned long long)c->n_lights, P(c->stream),
                                        c->target_gen, P(c->d_scenes), P(c->d_sc), P(c->chain_scene),
                                        (unsigned long long)c->tune.blocks_per_sm,
-                                       (unsigned long long)c->tune.refill, (unsigned long long)c->ray_order};
+                                       (unsigned long long)c->tune.refill, (unsigned long long)c->ray_order,
+                                       (unsigned long long)(c->tail_bounce + 1)};
   for (unsigned long long v : prm) k.push_back(v);
   return k;
 }
@@ -1540,6 +1553,10 @@ int dr_set_option(dr_ctx* c, int32_t option, int32_t value) {
     case DR_OPT_REFILL:
       if (value < 1 || value > 32) return fail(DR_ERR_INVALID_ARG, "dr_set_option: refill is 1..32");
       c->tune.refill = value;
+      return DR_OK;
+    case DR_OPT_TAIL_BOUNCE:
+      if (value < -1 || value > DR_MAX_PATH_LEN) return fail(DR_ERR_INVALID_ARG, "dr_set_option: tail bounce is -1..16");
+      c->tail_bounce = value;
       return DR_OK;
     case DR_OPT_RAY_ORDER:
       if (value < -1 || value > 1) return fail(DR_ERR_INVALID_ARG, "dr_set_option: ray order is -1, 0 or 1");

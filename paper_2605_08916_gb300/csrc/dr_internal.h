@@ -144,12 +144,16 @@ struct __align__(16) ShadowRec {
   int ex1, pad0, pad1, pad2;
 };
 // counters: [k] = rays of bounce k (1..16), [17 + k] = shadow rays of bounce
-// k, [35 + k] = fetch position of the traversal pass of bounce k, [52 + s] =
-// surviving chains with s path segments (0..16), queued for the adjoint
+// k (1..16), [34 + k] = fetch position of the traversal pass of bounce k
+// (1..17; k = 0: the tail pass), [52 + s] = surviving chains with s path
+// segments (0..16), queued for the adjoint
 constexpr int kWfShadowCount0 = 17;
-constexpr int kWfFetch0 = 35;
+constexpr int kWfFetch0 = 34;
 constexpr int kWfAdjBucket0 = 52;
 constexpr int kWfCounts = 69;
+static_assert(kWfFetch0 + kMaxPathLen + 1 < kWfAdjBucket0, "fetch counters overlap the adjoint buckets");
+static_assert(kWfShadowCount0 + kMaxPathLen < kWfFetch0, "shadow counts overlap the fetch counters");
+static_assert(kWfAdjBucket0 + kMaxPathLen < kWfCounts, "adjoint buckets exceed the counter block");
 struct WfBuffers {
   float4* slot;        // [N][4] path state
   int* hit;            // [N] closest-hit triangle of the current ray
@@ -164,7 +168,7 @@ WfBuffers wf_carve(void* base, unsigned long long N, int L);
 
 // Phases timed by the optional profiler (events recorded around launches).
 enum Phase { kPhBegin = 0, kPhTrace, kPhShade, kPhShadow, kPhFinish, kPhAdjoint, kPhFused, kPhFd, kPhSplat,
-             kPhOrder, kPhCount };
+             kPhOrder, kPhTail, kPhCount };
 struct PhaseHook {
   void (*mark)(void* user, int phase, bool begin, int bounce);
   void* user;
@@ -186,6 +190,7 @@ enum WfMode { kWfStep = 0, kWfInitEval = 1, kWfInitClock = 2 };
 struct WfTuning {
   int blocks_per_sm = 0;
   int refill = 24;
+  int tail_bounce = 0;  // 0: every bounce as its own passes; k >= 1: one persistent pass from shading bounce k on
 };
 // Sorting of the camera rays by pixel before the first traversal: the key
 // buffer (a.ray_keys), its ping-pong partner, the sort scratch and the

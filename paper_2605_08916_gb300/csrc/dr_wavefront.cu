@@ -347,6 +347,153 @@ __global__ void __launch_bounds__(kWfThreads) wf_shade(StepArgs a, WfBuffers w, 
   }
 }
 
+// The tail of a step in one persistent pass: from the shading of bounce k0
+// on, each lane carries a whole path (shade, its shadow ray, the next
+// closest-hit ray, shade, ...) until it ends, and fetches another path from
+// the bounce-k0 queue whenever fewer than a.refill lanes are busy.  Late
+// bounces have few rays, so separate launches per bounce would each wait for
+// their slowest ray; here those waits overlap.  The per-path order of work,
+// and with it every addition to f and every tape write, is the one of the
+// bounce-by-bounce passes, so the results are identical.
+constexpr int kWfTailMinBlocks = 4;
+
+template <bool STATS, bool BATCH>
+__global__ void __launch_bounds__(kWfThreads, kWfTailMinBlocks) wf_tail(StepArgs a, WfBuffers w, int k0) {
+  extern __shared__ int smem[];
+  TraceStack<kWfStack> st{smem + threadIdx.x, (int)blockDim.x};
+  enum { kIdle = 0, kShade, kClosest, kShadow };
+  const uint32_t n = w.counts[k0];
+  const uint32_t* q = k0 == 1 && !a.ray_keys ? nullptr : w.queue[k0 & 1];
+  uint32_t* ctr = &w.counts[kWfFetch0 + 0];  // the fetch counter of bounce 0 is otherwise unused
+  uint32_t err = 0;
+  TraceStats stats{0u, 0u};
+  unsigned long long rays = 0;
+  bool drained = false, cont_after = false;
+  int state = kIdle, k = 0, hit = -1, L = a.L, sid = 0, ex0 = -1, ex1 = -1, best = -1;
+  unsigned long long j = 0;
+  PathState ps;
+  int pix = 0;
+  Ray r;
+  Walk4 wk{0, 0, 0};
+  float tlim = 0.0f;
+  float3 contrib = f3(0.f, 0.f, 0.f);
+  while (true) {
+    if (!drained) {
+      const unsigned idle = __ballot_sync(kFull, state == kIdle);
+      if (idle) {
+        const uint32_t t = warp_fetch(ctr, idle, n, drained);
+        if (state == kIdle && t < n) {
+          j = q ? q[t] : t;
+          load_slot(w.slot, j, ps, pix);
+          hit = w.hit[j];
+          const ChainView v = chain_view<BATCH>(a, j);
+          L = v.L;
+          sid = v.sid;
+          k = k0;
+          state = kShade;
+        }
+      }
+    }
+    if (__ballot_sync(kFull, state != kIdle) == 0) {
+      if (drained) break;
+      continue;
+    }
+    while (true) {
+      const DevScene& S = scene_of<BATCH>(a, sid);
+      // shading is long and walking steps are short: a warp shades only
+      // when at least as many of its lanes wait to shade as walk, so the
+      // shading runs with many lanes at once
+      const unsigned shading = __ballot_sync(kFull, state == kShade);
+      const unsigned walking = __ballot_sync(kFull, state == kClosest || state == kShadow);
+      const bool do_shade = __popc(shading) >= __popc(walking);
+      if (state == kShade && do_shade) {
+        bool next = false;
+        if (hit >= 0) {
+          NeeReq nee;
+          nee.valid = false;
+          const bool cont = path_vertex(S, XSoA{a.x, a.N, j}, L, k, hit, ps, GlobalTape{w.tape, a.N, j}, nee);
+          next = cont && k < L;
+          if (nee.valid) {
+            r = make_ray(nee.o, nee.wi);
+            tlim = nee.tmax;
+            ex0 = nee.ex0;
+            ex1 = nee.ex1;
+            contrib = nee.contrib;
+            cont_after = next;
+            wk = walk4_begin(S);
+            ++rays;
+            if (ray_finite(r.o, r.d)) {
+              state = kShadow;
+            } else {
+              err |= kErrNonFinite;  // occluded: no contribution
+            }
+          }
+        }
+        if (state == kShade) {  // no shadow ray to walk
+          if (next) {
+            ++k;
+            r = make_ray(ps.o, ps.d);
+            ex0 = ps.prev_tri;
+            tlim = __int_as_float(0x7f800000);
+            best = -1;
+            wk = walk4_begin(S);
+            ++rays;
+            if (ray_finite(r.o, r.d)) {
+              state = kClosest;
+            } else {
+              err |= kErrNonFinite;
+              hit = -1;  // shaded as a miss
+            }
+          } else {
+            store_slot(w.slot, j, ps, pix);
+            state = kIdle;
+          }
+        }
+      } else if (state == kShadow && !do_shade) {
+        bool occ;
+        if (any4_step<kWfStack, STATS>(S, r, tlim, ex0, ex1, wk, &occ, st, &err, &stats)) {
+          if (!occ) {
+            ps.f += contrib;
+            GlobalTape{w.tape, a.N, j}.or_flags(k - 1, kFNeeVis);
+          }
+          if (cont_after) {
+            ++k;
+            r = make_ray(ps.o, ps.d);
+            ex0 = ps.prev_tri;
+            tlim = __int_as_float(0x7f800000);
+            best = -1;
+            wk = walk4_begin(S);
+            ++rays;
+            if (ray_finite(r.o, r.d)) {
+              state = kClosest;
+            } else {
+              err |= kErrNonFinite;
+              hit = -1;
+              state = kShade;
+            }
+          } else {
+            store_slot(w.slot, j, ps, pix);
+            state = kIdle;
+          }
+        }
+      } else if (state == kClosest && !do_shade) {
+        if (closest4_step<kWfStack, STATS>(S, r, ex0, wk, tlim, best, st, &err, &stats)) {
+          hit = best;
+          state = kShade;
+        }
+      }
+      const unsigned act = __ballot_sync(kFull, state != kIdle);
+      if (act == 0 || (!drained && __popc(act) < a.refill)) break;
+    }
+  }
+  add_counts(a.rays, rays);
+  if (STATS) {
+    add_counts(a.node_visits, stats.nodes);
+    add_counts(a.tri_tests, stats.tris);
+  }
+  if (err) atomicOr(a.err, err);
+}
+
 // binary-BVH shadow pass of bounce k
 template <bool STATS>
 __global__ void __launch_bounds__(kWfThreads, kWfTraceMinBlocks) wf_shadow(StepArgs a, WfBuffers w, int k) {
@@ -457,6 +604,10 @@ __global__ void __launch_bounds__(kWfThreads, 4) wf_adjoint(StepArgs a, WfBuffer
     int b = kMaxPathLen;
     while (b > 0 && t >= off[b]) --b;  // bucket b holds positions [off[b + 1], off[b])
     const unsigned long long j = w.adj[(size_t)b * a.N + (t - off[b + 1])];
+    if (j >= a.N || t - off[b + 1] >= a.N) {
+      atomicOr(a.err, kErrBadIndex);
+      continue;
+    }
     PathState ps;
     int pix;
     load_slot(w.slot, j, ps, pix);
@@ -479,6 +630,17 @@ int traverse_blocks_per_sm(size_t smem) {
   if (cached == 0) {
     int b0 = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b0, wf_traverse<false, BATCH>, kWfThreads, smem);
+    cached = std::max(1, b0);
+  }
+  return cached;
+}
+
+template <bool BATCH>
+int tail_blocks_per_sm(size_t smem) {
+  static int cached = 0;
+  if (cached == 0) {
+    int b0 = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b0, wf_tail<false, BATCH>, kWfThreads, smem);
     cached = std::max(1, b0);
   }
   return cached;
@@ -526,6 +688,15 @@ int launch_wf(const StepArgs& a, const WfBuffers& w, bool stats, int n_sm, const
       else wf_traverse<false, BATCH><<<g4, kWfThreads, smem, s>>>(a, w, k);
       hook(k <= a.L ? kPhTrace : kPhShadow, false, k <= a.L ? k : a.L);
       launches += 1;
+      if (k <= a.L && k == tune.tail_bounce) {
+        // the rest of every path in one persistent pass
+        hook(kPhTail, true, k);
+        if (stats) wf_tail<true, BATCH><<<n_sm * tail_blocks_per_sm<BATCH>(smem), kWfThreads, smem, s>>>(a, w, k);
+        else wf_tail<false, BATCH><<<n_sm * tail_blocks_per_sm<BATCH>(smem), kWfThreads, smem, s>>>(a, w, k);
+        hook(kPhTail, false, k);
+        launches += 1;
+        break;
+      }
       if (k <= a.L) {
         hook(kPhShade, true, k);
         wf_shade<BATCH><<<g, kWfThreads, 0, s>>>(a, w, k);

@@ -72,11 +72,11 @@ class Renderer:
     def set_option(self, option, value):
         """option: "wavefront" (-1 auto / 0 / 1), "work_order" (0/1), "profile" (0/1) or
         "bvh_width" (0 automatic / 2 / 4), "traverse_blocks" (0 = all resident),
-        "refill" (1..32) or "ray_order" (-1 automatic / 0 / 1)."""
+        "refill" (1..32), "ray_order" (-1 automatic / 0 / 1) or "tail_bounce" (-1 automatic, 0 off, k)."""
         code = {"work_order": _lib.DR_OPT_WORK_ORDER, "wavefront": _lib.DR_OPT_WAVEFRONT,
                 "profile": _lib.DR_OPT_PROFILE, "bvh_width": _lib.DR_OPT_BVH_WIDTH,
                 "traverse_blocks": _lib.DR_OPT_TRAVERSE_BLOCKS, "refill": _lib.DR_OPT_REFILL,
-                "ray_order": _lib.DR_OPT_RAY_ORDER}[option]
+                "ray_order": _lib.DR_OPT_RAY_ORDER, "tail_bounce": _lib.DR_OPT_TAIL_BOUNCE}[option]
         call("dr_set_option", self.h, code, int(value))
 
     def set_bvh_builder(self, builder="ploc", radius=16):

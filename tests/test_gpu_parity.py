@@ -452,6 +452,29 @@ def test_batch_graph_frames_and_errors(torch, R):
     r.close()
 
 
+@pytest.mark.parametrize("tail", [2, 5])
+def test_tail_pass_gives_the_same_chains(torch, R, tail):
+    """Running the late bounces as one persistent pass performs each path's
+    work in the same order as the bounce-by-bounce passes: identical chain
+    states, counters and images."""
+    scene, L = S.procedural_scene(1, 64, 36, target_tris=60000, n_objects=40), 12
+    out = []
+    for tb in (0, tail):
+        r = R.Renderer()
+        r.set_option("wavefront", 1)
+        r.set_option("tail_bounce", tb)
+        r.upload_scene(scene)
+        r.init_chains(16384, 37, R.make_params(L=L, drift="adjoint", k0=0.0, steps_per_splat=4))
+        r.step(7)
+        out.append((r.readback_state(("x", "killed", "logp", "score")), r.readback_accum(), r.counters()))
+        r.close()
+    (a, acc_a, c_a), (b, acc_b, c_b) = out
+    for key in ("x", "killed", "logp", "score"):
+        assert np.array_equal(a[key], b[key]), key
+    assert np.array_equal(acc_a, acc_b)
+    assert c_a["tour_count"] == c_b["tour_count"] and c_a["rays"] == c_b["rays"]
+
+
 @pytest.mark.parametrize("chains", [8192, 1 << 17])
 def test_graph_frames_match_plain_steps(torch, R, chains):
     """dr_frame (captured once, replayed with the step index in device
