@@ -146,15 +146,25 @@ struct Walk4 {
 
 DR_D Walk4 walk4_begin(const DevScene& S) { return Walk4{0, 0, min(2 * S.n_nodes4 + 64, kMaxNodeVisits)}; }
 
-DR_D void load_node4(const DevScene& S, int node, float3 lo[4], float3 hi[4], int4& ch) {
+// Entry distances of a node's four child boxes against [0, tmax] (-1: a
+// miss), and its links.  Per axis the ray's direction sign picks which slab
+// plane is near, so each distance is one subtract and one multiply and no
+// min / max pair is needed (the same values box_entry gives).
+DR_D void node4_entries(const DevScene& S, int node, const Ray& r, float tmax, float e[4], int4& ch) {
   const float4* nb = S.nodes4 + (size_t)kNode4F4 * node;
-  const float4 bx0 = __ldg(nb + 0), bx1 = __ldg(nb + 1), by0 = __ldg(nb + 2), by1 = __ldg(nb + 3);
-  const float4 bz0 = __ldg(nb + 4), bz1 = __ldg(nb + 5);
+  const int sx = r.inv.x < 0.0f, sy = r.inv.y < 0.0f, sz = r.inv.z < 0.0f;
+  const float4 nx = __ldg(nb + sx), fx = __ldg(nb + 1 - sx);
+  const float4 ny = __ldg(nb + 2 + sy), fy = __ldg(nb + 3 - sy);
+  const float4 nz = __ldg(nb + 4 + sz), fz = __ldg(nb + 5 - sz);
   ch = __ldg(reinterpret_cast<const int4*>(nb + 6));
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    lo[k] = f3(f4c(bx0, k), f4c(by0, k), f4c(bz0, k));
-    hi[k] = f3(f4c(bx1, k), f4c(by1, k), f4c(bz1, k));
+    const float tnx = (f4c(nx, k) - r.o.x) * r.inv.x, tfx = (f4c(fx, k) - r.o.x) * r.inv.x;
+    const float tny = (f4c(ny, k) - r.o.y) * r.inv.y, tfy = (f4c(fy, k) - r.o.y) * r.inv.y;
+    const float tnz = (f4c(nz, k) - r.o.z) * r.inv.z, tfz = (f4c(fz, k) - r.o.z) * r.inv.z;
+    const float tn = fmaxf(fmaxf(tnx, tny), fmaxf(tnz, 0.0f));
+    const float tf = fminf(fminf(tfx, tfy), fminf(tfz, tmax));
+    e[k] = tn <= tf * 1.0000002f ? tn : -1.0f;
   }
 }
 
@@ -167,13 +177,10 @@ DR_D bool closest4_step(const DevScene& S, const Ray& r, int exclude, Walk4& w, 
     *err |= kErrBadIndex;
     return true;
   }
-  float3 lo[4], hi[4];
   int4 ch;
-  load_node4(S, w.node, lo, hi, ch);
-  if (STATS) ++stats->nodes;
   float e[4];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) e[k] = box_entry(lo[k], hi[k], r, tbest);
+  node4_entries(S, w.node, r, tbest, e, ch);
+  if (STATS) ++stats->nodes;
 #pragma unroll
   for (int k = 0; k < 4; ++k)
     if (i4c(ch, k) < 0 && e[k] >= 0.0f && e[k] <= tbest)
@@ -228,16 +235,16 @@ DR_D bool any4_step(const DevScene& S, const Ray& r, float tmax, int ex0, int ex
     *err |= kErrBadIndex;
     return true;
   }
-  float3 lo[4], hi[4];
   int4 ch;
-  load_node4(S, w.node, lo, hi, ch);
+  float ent[4];
+  node4_entries(S, w.node, r, tmax, ent, ch);
   if (STATS) ++stats->nodes;
   int next = -1;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     const int c = i4c(ch, k);
     if (c == kBvh4Empty) continue;
-    const float e = box_entry(lo[k], hi[k], r, tmax);
+    const float e = ent[k];
     if (!(e >= 0.0f)) continue;
     if (c < 0) {
       const int first = leaf_first(c);
