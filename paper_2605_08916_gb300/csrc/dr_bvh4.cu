@@ -236,9 +236,8 @@ __global__ void mark_kernel(const float4* __restrict__ n2, const uint8_t* as_lea
   const int n = (int)q_in[t];
   Kid kids[4];
   const int nk = expand(n2, n, as_leaf, kids);
-  int inner = 0;
-  for (int k = 0; k < nk; ++k) inner += leaf_ref(kids[k], as_leaf) ? 0 : 1;
-  const int here = need[n] + max(0, inner - 1);
+  // a closest-hit walk pushes every hit child but the nearest (leaves too)
+  const int here = need[n] + max(0, nk - 1);
   atomicMax(&maxes[0], (uint32_t)here);
   atomicMax(&maxes[1], (uint32_t)depth[n]);
   for (int k = 0; k < nk; ++k) {

@@ -16,7 +16,7 @@ constexpr float kLumR = 0.2126f, kLumG = 0.7152f, kLumB = 0.0722f;
 constexpr int kMaxPathLen = 16;               // L <= 16  ->  d <= 62
 // Entries of the per-thread traversal stack; a BVH deeper than this + 1 is
 // rejected at scene upload.
-constexpr int kTraversalStack = 40;
+constexpr int kTraversalStack = 48;
 constexpr int kMaxDim = 2 + 4 * (kMaxPathLen - 1);
 
 // device error word bits (read back by the host after each call)

@@ -144,7 +144,8 @@ struct Walk4 {
   int node, sp, budget;
 };
 
-DR_D Walk4 walk4_begin(const DevScene& S) { return Walk4{0, 0, min(2 * S.n_nodes4 + 64, kMaxNodeVisits)}; }
+// budget: every inner node and every leaf (at most four per node) once
+DR_D Walk4 walk4_begin(const DevScene& S) { return Walk4{0, 0, min(5 * S.n_nodes4 + 64, kMaxNodeVisits)}; }
 
 // Entry distances of a node's four child boxes against [0, tmax] (-1: a
 // miss), and its links.  Per axis the ray's direction sign picks which slab
@@ -168,29 +169,34 @@ DR_D void node4_entries(const DevScene& S, int node, const Ray& r, float tmax, f
   }
 }
 
-// One node of a closest-hit walk; returns true when the walk is over
-// (tbest / best then hold the result).
+// One step of a closest-hit walk: an inner node (its hit children, leaves
+// and inner nodes alike, are taken nearest first: the nearest now, the
+// others pushed far-to-near) or a leaf (its triangles tested against the
+// closest hit so far).  Returns true when the walk is over (tbest / best
+// then hold the result).
 template <int STACK, bool STATS>
 DR_D bool closest4_step(const DevScene& S, const Ray& r, int exclude, Walk4& w, float& tbest, int& best,
                         TraceStack<STACK> st, uint32_t* err, TraceStats* stats) {
-  if (--w.budget < 0 || w.node < 0 || w.node >= S.n_nodes4) {
+  if (--w.budget < 0 || w.node >= S.n_nodes4) {
     *err |= kErrBadIndex;
     return true;
+  }
+  if (w.node < 0) {
+    leaf_closest<STATS>(S, w.node, r, exclude, tbest, best, err, stats);
+    if (w.sp == 0) return true;
+    w.node = st.at(--w.sp);
+    return false;
   }
   int4 ch;
   float e[4];
   node4_entries(S, w.node, r, tbest, e, ch);
   if (STATS) ++stats->nodes;
-#pragma unroll
-  for (int k = 0; k < 4; ++k)
-    if (i4c(ch, k) < 0 && e[k] >= 0.0f && e[k] <= tbest)
-      leaf_closest<STATS>(S, i4c(ch, k), r, exclude, tbest, best, err, stats);
   bool ok[4];
   int nc = 0;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     const int c = i4c(ch, k);
-    ok[k] = c >= 0 && c != kBvh4Empty && e[k] >= 0.0f && e[k] <= tbest;
+    ok[k] = c != kBvh4Empty && e[k] >= 0.0f && e[k] <= tbest;
     nc += ok[k] ? 1 : 0;
   }
   if (nc == 0) {
