@@ -237,41 +237,46 @@ template <int STACK, bool STATS>
 DR_D bool any4_step(const DevScene& S, const Ray& r, float tmax, int ex0, int ex1, Walk4& w, bool* occluded,
                     TraceStack<STACK> st, uint32_t* err, TraceStats* stats) {
   *occluded = false;
-  if (--w.budget < 0 || w.node < 0 || w.node >= S.n_nodes4) {
+  if (--w.budget < 0 || w.node >= S.n_nodes4) {
     *err |= kErrBadIndex;
     return true;
+  }
+  if (w.node < 0) {
+    // a leaf: any hit ends the walk
+    const int first = leaf_first(w.node);
+    int cnt = leaf_count(w.node);
+    if (first + cnt > S.n_tris) {
+      *err |= kErrBadIndex;
+      cnt = 0;
+    }
+    for (int i = 0; i < cnt; ++i) {
+      const float4 t0 = __ldg(S.tris4 + 3 * (first + i) + 0);
+      const float4 t1 = __ldg(S.tris4 + 3 * (first + i) + 1);
+      const float4 t2 = __ldg(S.tris4 + 3 * (first + i) + 2);
+      const int id = __float_as_int(t0.w);
+      if (STATS) ++stats->tris;
+      float th;
+      if (id != ex0 && id != ex1 && tri_test(xyz(t0), xyz(t1), xyz(t2), r, S.tmin, tmax, &th)) {
+        *occluded = true;
+        return true;
+      }
+    }
+    if (w.sp == 0) return true;
+    w.node = st.at(--w.sp);
+    return false;
   }
   int4 ch;
   float ent[4];
   node4_entries(S, w.node, r, tmax, ent, ch);
   if (STATS) ++stats->nodes;
-  int next = -1;
+  // hit children, leaves and inner nodes alike: the first now, the others
+  // pushed (a step tests at most one leaf)
+  int next = kBvh4Empty;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     const int c = i4c(ch, k);
-    if (c == kBvh4Empty) continue;
-    const float e = ent[k];
-    if (!(e >= 0.0f)) continue;
-    if (c < 0) {
-      const int first = leaf_first(c);
-      int cnt = leaf_count(c);
-      if (first + cnt > S.n_tris) {
-        *err |= kErrBadIndex;
-        cnt = 0;
-      }
-      for (int i = 0; i < cnt; ++i) {
-        const float4 t0 = __ldg(S.tris4 + 3 * (first + i) + 0);
-        const float4 t1 = __ldg(S.tris4 + 3 * (first + i) + 1);
-        const float4 t2 = __ldg(S.tris4 + 3 * (first + i) + 2);
-        const int id = __float_as_int(t0.w);
-        if (STATS) ++stats->tris;
-        float th;
-        if (id != ex0 && id != ex1 && tri_test(xyz(t0), xyz(t1), xyz(t2), r, S.tmin, tmax, &th)) {
-          *occluded = true;
-          return true;
-        }
-      }
-    } else if (next < 0) {
+    if (c == kBvh4Empty || !(ent[k] >= 0.0f)) continue;
+    if (next == kBvh4Empty) {
       next = c;
     } else if (w.sp < STACK) {
       st.at(w.sp++) = c;
@@ -279,7 +284,7 @@ DR_D bool any4_step(const DevScene& S, const Ray& r, float tmax, int ex0, int ex
       *err |= kErrStackOverflow;
     }
   }
-  if (next >= 0) {
+  if (next != kBvh4Empty) {
     w.node = next;
     return false;
   }
