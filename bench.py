@@ -53,6 +53,32 @@ DEFAULT = "procedural-1m-720p"
 SEED = 0x5EED
 
 
+TRAFFIC_SOURCES = ["dr_common.cuh", "dr_trace.cuh", "dr_path.cuh", "dr_step.cuh", "dr_internal.h", "dr_wavefront.cu",
+                   "dr_bvh.cu", "dr_bvh4.cu"]
+
+
+def traversal_traffic(workload, n_chains):
+    """DRAM bytes per step of the traversal passes from the committed ncu
+    capture for this workload, if the traversal sources are unchanged since
+    (their sha256 matches); else None."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", f"wf_traverse_traffic_{workload}.txt")
+    if not os.path.exists(path):
+        return None
+    kv = {}
+    for line in open(path):
+        if line.strip() and not line.startswith("#") and ":" in line:
+            k, v = line.split(":", 1)
+            kv[k.strip()] = v.strip()
+    h = hashlib.sha256()
+    for f in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, "paper_2605_08916_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest() != kv.get("source_sha256") or int(kv.get("chains", 0)) != n_chains:
+        return None
+    return int(kv["dram_read_bytes_per_step"]) + int(kv["dram_write_bytes_per_step"])
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -330,8 +356,11 @@ def run_ours(args, wl, rank, world, local):
                            "parallelism": f"replicas{world}"},
                 "rays_per_s": rays_s, "rays_per_chain_step": rays / max(1, N * steps),
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                             "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
-                             "kernel": k_name, "kernel_ms_per_step": k_ms,
+                             "frac": achieved / peak,
+                             "traffic": traversal_traffic(args.workload, N) if wavefront and wide else None,
+                             "basis": "per Restore step: all traversal launches of the step (achieved = "
+                                      "algorithmic bytes per step / their time; traffic = their DRAM bytes)",
+                             "peak_kind": peak_kind, "kernel": k_name, "kernel_ms_per_step": k_ms,
                              "algorithmic_bytes_per_chain_step": k_bytes,
                              "node_visits_per_chain_step": ts["node_visits"] / chain_steps_stats,
                              "tri_tests_per_chain_step": ts["tri_tests"] / chain_steps_stats},
