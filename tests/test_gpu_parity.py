@@ -313,6 +313,69 @@ def test_pt_reference_image_matches_oracle(torch, R, oracle):
     r.close()
 
 
+def _sampled_parity(st_x, st_logp, st_killed, ro, sample, x_tol=1e-4):
+    """Fraction of sampled chains whose final state differs from the oracle's."""
+    xo, lo_, ko = ro["x"][-1], ro["logp"][-1], ro["killed"][-1]
+    ok = (st_killed[sample] == ko) & (torus_dist(st_x[sample], xo).max(1) <= x_tol)
+    ok &= np.abs(st_logp[sample] - lo_) <= 1e-4 * np.maximum(1.0, np.abs(lo_))
+    return 1.0 - ok.mean()
+
+
+def test_full_size_bench_configuration_matches_oracle_on_sampled_chains(torch, R, oracle):
+    """The bench's own workload and launch configuration (1M-triangle
+    procedural scene, 2^20 chains, L = 12, bounce-by-bounce passes with the
+    4-wide BVH, camera-ray sort and CUDA-graph frames), checked on 192
+    sampled chains that the oracle follows one by one over two frames."""
+    scene = S.procedural_scene(1, 1280, 720)
+    N, L, F, seed = 1 << 20, 12, 4, 91
+    k0 = 2.0e6
+    stream = torch.cuda.Stream()
+    r = R.Renderer(0, stream)
+    r.upload_scene(scene)
+    r.init_chains(N, seed, R.make_params(L=L, drift="adjoint", rb=True, k0=k0, steps_per_splat=F))
+    r.frame(F)
+    r.frame(F)
+    stream.synchronize()
+    st = r.readback_state(("x", "killed", "logp"))
+    r.close()
+    sample = np.sort(np.random.default_rng(5).choice(N, 192, replace=False))
+    tgt = oracle.OracleScene(scene)
+    ro = oracle.restore_run(tgt, oracle.make_params(L=L, drift="exact", rb=True, k0=k0), seed=seed,
+                            chain_ids=sample, n_steps=2 * F)
+    frac = _sampled_parity(st["x"], st["logp"], st["killed"], ro, np.arange(N)[sample])
+    print(f"full-size sampled chains: divergent fraction {frac:.4f}")
+    assert frac <= 0.02
+
+
+def test_full_size_batch_matches_oracle_on_sampled_chains(torch, R, oracle):
+    """The 64-scene batch workload (2^21 chains, L 4..16), in the bench's
+    launch configuration: sampled chains of four scenes against the oracle
+    run on each scene with the batch's key (seed_lo, seed_hi + scene)."""
+    items = S.procedural_batch()
+    N = sum(n for _, _, n in items)
+    seed, F, k0 = 93, 2, 2.0e6
+    stream = torch.cuda.Stream()
+    r = R.Renderer(0, stream)
+    r.upload_scenes(items)
+    r.init_chains(N, seed, R.make_params(L=16, drift="adjoint", rb=True, k0=k0, steps_per_splat=F))
+    r.frame(F)
+    stream.synchronize()
+    st = r.readback_state(("x", "killed", "logp"))
+    r.close()
+    starts = np.concatenate([[0], np.cumsum([n for _, _, n in items])])
+    rng = np.random.default_rng(6)
+    fracs = []
+    for s_i in (0, 17, 40, 63):
+        scene, L, n = items[s_i]
+        local = np.sort(rng.choice(n, 48, replace=False))
+        ro = oracle.restore_run(oracle.OracleScene(scene), oracle.make_params(L=L, drift="exact", rb=True, k0=k0),
+                                seed=seed + (s_i << 32), chain_ids=local, n_steps=F)
+        d = S.pss_dim(L)
+        fracs.append(_sampled_parity(st["x"][:, :d], st["logp"], st["killed"], ro, starts[s_i] + local))
+    print("batch sampled chains: divergent fractions", fracs)
+    assert max(fracs) <= 0.05 and np.mean(fracs) <= 0.02
+
+
 @pytest.mark.parametrize("which", ["glossy", "procedural"])
 def test_wavefront_matches_fused(torch, R, which):
     """The bounce-by-bounce execution performs the same operations per path
