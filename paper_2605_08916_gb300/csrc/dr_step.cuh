@@ -45,14 +45,21 @@ DR_D void evolve_x(const StepArgs& a, const Rng& rng, uint32_t step, unsigned lo
     return;
   }
   const float c2 = 0.5f * a.stddev * a.stddev;
-  for (int q = 0; q < d / 2; ++q) {
-    const U4 r = rng.draw(step, cj, (uint32_t)(q >> 1), kNormal);
-    const float ua = u01((q & 1) ? r.c : r.a), ub = u01((q & 1) ? r.d : r.b);
-    const float2 xi = box_muller(ua, ub);
-    const size_t i0 = (size_t)(2 * q) * a.N + j, i1 = (size_t)(2 * q + 1) * a.N + j;
-    const float s0 = a.score[i0], s1 = a.score[i1];
-    a.x[i0] = wrap01(a.x[i0] + c2 * s0 + a.gamma_tilde * s1 + a.stddev * xi.x);
-    a.x[i1] = wrap01(a.x[i1] + c2 * s1 - a.gamma_tilde * s0 + a.stddev * xi.y);
+  // one Philox block serves two coordinate pairs: pair q uses words
+  // (q & 1) * 2 and (q & 1) * 2 + 1 of block q >> 1
+  for (int blk = 0; 2 * blk < d / 2; ++blk) {
+    const U4 r = rng.draw(step, cj, (uint32_t)blk, kNormal);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int q = 2 * blk + h;
+      if (q >= d / 2) break;
+      const float ua = u01(h ? r.c : r.a), ub = u01(h ? r.d : r.b);
+      const float2 xi = box_muller(ua, ub);
+      const size_t i0 = (size_t)(2 * q) * a.N + j, i1 = (size_t)(2 * q + 1) * a.N + j;
+      const float s0 = a.score[i0], s1 = a.score[i1];
+      a.x[i0] = wrap01(a.x[i0] + c2 * s0 + a.gamma_tilde * s1 + a.stddev * xi.x);
+      a.x[i1] = wrap01(a.x[i1] + c2 * s1 - a.gamma_tilde * s0 + a.stddev * xi.y);
+    }
   }
 }
 

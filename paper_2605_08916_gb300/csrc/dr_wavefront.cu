@@ -31,6 +31,9 @@ constexpr int kWfTraceMinBlocks = 10;
 // the 4-wide traversal holds four child boxes at once: fewer resident
 // blocks, more registers per thread (measured: 7 beats 6 and 8)
 constexpr int kWfTrace4MinBlocks = 7;
+// shading waits on its loads: more resident warps (80 registers) hide more
+// (measured: 6 blocks beat 5 on the 1M-triangle and batch workloads)
+constexpr int kWfShadeMinBlocks = 6;
 
 // 64-B path slot per chain: (o, ppdf), (d, prev tri), (beta, prev_delta |
 // nseg << 8), (f, pixel)
@@ -301,7 +304,7 @@ __global__ void __launch_bounds__(kWfThreads, kWfTrace4MinBlocks) wf_traverse(St
 }
 
 template <bool BATCH>
-__global__ void __launch_bounds__(kWfThreads) wf_shade(StepArgs a, WfBuffers w, int k) {
+__global__ void __launch_bounds__(kWfThreads, kWfShadeMinBlocks) wf_shade(StepArgs a, WfBuffers w, int k) {
   const uint32_t n = w.counts[k];
   const uint32_t* q = k == 1 && !a.ray_keys ? nullptr : w.queue[k & 1];
   uint32_t* qn = w.queue[(k + 1) & 1];
