@@ -19,6 +19,7 @@ constexpr int kMaxNodeVisits = 1 << 15;
 
 struct Ray {
   float3 o, d, inv;
+  float3 oinv;  // o * inv (rounded), for the 4-wide slab test
 };
 
 // A NaN in the ray makes every slab test pass (fminf / fmaxf drop NaNs), so
@@ -35,6 +36,7 @@ DR_D Ray make_ray(float3 o, float3 d) {
   // than an infinite one, so that no slab product is 0 * inf = NaN
   auto safe_inv = [](float v) { return 1.0f / (fabsf(v) > 1e-20f ? v : copysignf(1e-20f, v)); };
   r.inv = f3(safe_inv(d.x), safe_inv(d.y), safe_inv(d.z));
+  r.oinv = f3(o.x * r.inv.x, o.y * r.inv.y, o.z * r.inv.z);
   return r;
 }
 
@@ -149,8 +151,12 @@ DR_D Walk4 walk4_begin(const DevScene& S) { return Walk4{0, 0, min(5 * S.n_nodes
 
 // Entry distances of a node's four child boxes against [0, tmax] (-1: a
 // miss), and its links.  Per axis the ray's direction sign picks which slab
-// plane is near, so each distance is one subtract and one multiply and no
-// min / max pair is needed (the same values box_entry gives).
+// plane is near, so no min / max pair is needed, and each distance is one
+// fused multiply-add, plane * (1/d) - o * (1/d).  That form loses accuracy
+// when the origin lies far from the scene origin (o/d is rounded), so the
+// near distances subtract, and the far ones add, a margin of 2^-22 |o/d|
+// (more than the rounding): boxes are only ever widened, never missed, and
+// the closest hit is decided by the exact triangle tests.
 DR_D void node4_entries(const DevScene& S, int node, const Ray& r, float tmax, float e[4], int4& ch) {
   const float4* nb = S.nodes4 + (size_t)kNode4F4 * node;
   const int sx = r.inv.x < 0.0f, sy = r.inv.y < 0.0f, sz = r.inv.z < 0.0f;
@@ -158,11 +164,15 @@ DR_D void node4_entries(const DevScene& S, int node, const Ray& r, float tmax, f
   const float4 ny = __ldg(nb + 2 + sy), fy = __ldg(nb + 3 - sy);
   const float4 nz = __ldg(nb + 4 + sz), fz = __ldg(nb + 5 - sz);
   ch = __ldg(reinterpret_cast<const int4*>(nb + 6));
+  constexpr float kM = 2.384185791015625e-07f;  // 2^-22
+  const float onx = fmaf(fabsf(r.oinv.x), kM, r.oinv.x), ofx = fmaf(-fabsf(r.oinv.x), kM, r.oinv.x);
+  const float ony = fmaf(fabsf(r.oinv.y), kM, r.oinv.y), ofy = fmaf(-fabsf(r.oinv.y), kM, r.oinv.y);
+  const float onz = fmaf(fabsf(r.oinv.z), kM, r.oinv.z), ofz = fmaf(-fabsf(r.oinv.z), kM, r.oinv.z);
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    const float tnx = (f4c(nx, k) - r.o.x) * r.inv.x, tfx = (f4c(fx, k) - r.o.x) * r.inv.x;
-    const float tny = (f4c(ny, k) - r.o.y) * r.inv.y, tfy = (f4c(fy, k) - r.o.y) * r.inv.y;
-    const float tnz = (f4c(nz, k) - r.o.z) * r.inv.z, tfz = (f4c(fz, k) - r.o.z) * r.inv.z;
+    const float tnx = fmaf(f4c(nx, k), r.inv.x, -onx), tfx = fmaf(f4c(fx, k), r.inv.x, -ofx);
+    const float tny = fmaf(f4c(ny, k), r.inv.y, -ony), tfy = fmaf(f4c(fy, k), r.inv.y, -ofy);
+    const float tnz = fmaf(f4c(nz, k), r.inv.z, -onz), tfz = fmaf(f4c(fz, k), r.inv.z, -ofz);
     const float tn = fmaxf(fmaxf(tnx, tny), fmaxf(tnz, 0.0f));
     const float tf = fminf(fminf(tfx, tfy), fminf(tfz, tmax));
     e[k] = tn <= tf * 1.0000002f ? tn : -1.0f;
