@@ -222,6 +222,23 @@ def _chain_parity(torch, R, oracle, target_obj, params_gpu, params_orc, N, M, T,
     return frac_div, first_div, n_cmp
 
 
+def _chain_parity_opts(torch, R, oracle, target_obj, params_gpu, params_orc, N, M, T, seed, opts, x_tol=1e-4):
+    """_chain_parity with renderer options set before the upload."""
+    orig = R.Renderer
+
+    class _R(orig):
+        def __init__(self, *args, **kw):
+            super().__init__(*args, **kw)
+            for k, v in opts.items():
+                self.set_option(k, v)
+
+    R.Renderer = _R
+    try:
+        return _chain_parity(torch, R, oracle, target_obj, params_gpu, params_orc, N, M, T, seed, x_tol)
+    finally:
+        R.Renderer = orig
+
+
 def test_chain_parity_mixture_target(torch, R, oracle):
     mix = S.gaussian_mixture(seed=4, d=4, K=3, sig_range=(0.08, 0.12), width=16, height=16)
     k0 = 1.0 / (64 * 1e-5)
@@ -704,4 +721,62 @@ def test_errors_are_reported_not_raised_on_device(torch, R):
     r.init_chains(64, 1, R.make_params(L=3, drift="adjoint", k0=100.0))
     r.step(2)
     assert r.counters()["steps"] == 2
+    r.close()
+
+
+@pytest.mark.parametrize("wavefront", [0, 1])
+def test_chain_parity_longest_paths(torch, R, oracle, wavefront):
+    """The largest PSS the library takes: L = 16 (d = 62) on the glossy Cornell
+    box, in both execution modes."""
+    scene = S.cornell_box(1, 64, 64, glossy=True)
+    k0 = 1e6
+    pg = R.make_params(L=16, drift="adjoint", rb=True, k0=k0, steps_per_splat=4)
+    po = oracle.make_params(L=16, drift="exact", rb=True, k0=k0)
+    r_opts = {"wavefront": wavefront}
+    frac, first, n = _chain_parity_opts(torch, R, oracle, scene, pg, po, N=2048, M=128, T=6, seed=61, opts=r_opts)
+    print("L = 16 divergent fraction", frac)
+    assert frac <= 0.02
+
+
+def test_chain_parity_camera_only_paths(torch, R, oracle):
+    """L = 1 (d = 2): only the emission seen directly through each pixel."""
+    scene = S.cornell_box(1, 32, 32)
+    k0 = 500.0
+    pg = R.make_params(L=1, drift="adjoint", rb=True, k0=k0, steps_per_splat=4)
+    po = oracle.make_params(L=1, drift="exact", rb=True, k0=k0)
+    frac, first, n = _chain_parity(torch, R, oracle, scene, pg, po, N=4096, M=512, T=8, seed=62)
+    assert frac <= 0.01
+
+
+@pytest.mark.parametrize("chains", [1, 33, 1000])
+def test_ragged_chain_counts(torch, R, oracle, chains):
+    """Chain counts that fill no warp or block exactly, down to a single
+    chain, through the bounce-by-bounce passes with every option on."""
+    scene = S.procedural_scene(2, 48, 32, target_tris=30000, n_objects=20)
+    k0 = 2.0e6
+    pg = R.make_params(L=6, drift="adjoint", rb=True, k0=k0, steps_per_splat=4)
+    po = oracle.make_params(L=6, drift="exact", rb=True, k0=k0)
+    opts = {"wavefront": 1, "ray_order": 1, "tail_bounce": 3}
+    frac, first, n = _chain_parity_opts(torch, R, oracle, scene, pg, po, N=chains, M=chains, T=6, seed=63,
+                                        opts=opts)
+    assert frac <= (0.0 if chains < 100 else 0.01)
+
+
+def test_zero_steps_and_size_limits(torch, R):
+    from paper_2605_08916_gb300 import _lib
+    import ctypes
+    stream = torch.cuda.Stream()
+    r = R.Renderer(0, stream)
+    r.upload_scene(S.cornell_box(1, 8, 8))
+    prm = R.make_params(L=3, drift="adjoint", k0=100.0)
+    L = _lib.load()
+    assert L.dr_chains_init(r.h, (1 << 31) + 1, 1, 0, ctypes.byref(prm)) == _lib.DR_ERR_INVALID_ARG
+    assert L.dr_chains_init(r.h, 0, 1, 0, ctypes.byref(prm)) == _lib.DR_ERR_INVALID_ARG
+    r.init_chains(256, 1, prm)
+    before = r.readback_state(("x",))["x"]
+    r.step(0)
+    r.frame(0)
+    stream.synchronize()
+    assert np.array_equal(before, r.readback_state(("x",))["x"])
+    assert r.counters()["steps"] == 0
     r.close()
