@@ -269,7 +269,7 @@ def run_ours(args, wl, rank, world, local):
     # bounce-by-bounce passes unless disabled; the fused kernel (automatic
     # width) walks the binary one
     wf_expected = wl["drift"] == "adjoint" and (args.wavefront == 1 or (args.wavefront == -1 and N >= 1 << 17))
-    wide = bool(bvh4) and (args.bvh_width == 4 or wf_expected)
+    wide = bool(bvh4)
     node_bytes = 112 if wide else 64
     trav_bytes = (ts["node_visits"] * node_bytes + ts["tri_tests"] * 48) / chain_steps_stats
     state_bytes = 4 * d * 4 + 1 + 1 + 4 + 16   # x and score read+write, killed r+w, logp, record
@@ -637,8 +637,7 @@ def main():
     ap.add_argument("--ray-order", type=int, default=-1, choices=[-1, 0, 1],
                     help="sort camera rays by pixel before the first traversal (-1: by triangle count)")
     ap.add_argument("--bvh-width", type=int, default=0, choices=[0, 2, 4],
-                    help="BVH the rays traverse: 4-wide, binary, or 0 (default) 4-wide in the bounce-by-bounce "
-                         "passes and binary in the fused kernel")
+                    help="BVH the rays traverse: 4-wide (0, the default, or 4) or binary (2)")
     ap.add_argument("--work-order", type=int, default=0, choices=[0, 1],
                     help="fused kernel only: order chains by expected path cost (default 0)")
     args = ap.parse_args()

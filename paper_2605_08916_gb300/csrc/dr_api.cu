@@ -224,11 +224,9 @@ void dfree(T** p) {
     if (r_ != DR_OK) return r_;  \
   } while (0)
 
-// wide_ok: under the automatic BVH choice, whether the caller's kernels take
-// the 4-wide BVH (the bounce-by-bounce passes and the single-purpose
-// kernels do; the fused step kernel, which holds a whole path's state while
-// it traverses, keeps the binary one)
-DevScene dev_scene(const dr_ctx* c, bool wide_ok = true) {
+// Kernel view of the uploaded scene: the 4-wide BVH unless the binary one
+// is asked for (DR_OPT_BVH_WIDTH = 2) or none was built.
+DevScene dev_scene(const dr_ctx* c) {
   DevScene S;
   S.nodes = c->nodes;
   S.tris = c->tris;
@@ -239,7 +237,7 @@ DevScene dev_scene(const dr_ctx* c, bool wide_ok = true) {
   S.n_lights = c->n_lights;
   S.n_tris = c->nt;
   S.n_nodes = std::max(1, c->n_nodes);
-  const bool wide = c->nodes4 != nullptr && (c->bvh_width == 4 || (c->bvh_width == 0 && wide_ok));
+  const bool wide = c->nodes4 != nullptr && c->bvh_width != 2;
   S.nodes4 = wide ? c->nodes4 : nullptr;
   S.tris4 = wide ? c->tris4 : nullptr;
   S.n_nodes4 = wide ? c->n_nodes4 : 0;
@@ -307,7 +305,7 @@ bool use_wavefront(const dr_ctx* c);
 
 StepArgs step_args(dr_ctx* c) {
   StepArgs a{};
-  a.S = dev_scene(c, use_wavefront(c));
+  a.S = dev_scene(c);
   a.M = dev_mixture(c);
   a.target = c->target;
   a.x = c->x;
@@ -342,7 +340,7 @@ StepArgs step_args(dr_ctx* c) {
 
 int run_fd(dr_ctx* c) {
   FdArgs f{};
-  f.S = dev_scene(c, false);
+  f.S = dev_scene(c);
   f.M = dev_mixture(c);
   f.target = c->target;
   f.x = c->x;
@@ -863,7 +861,7 @@ int dr_scenes_upload_batch(dr_ctx* c, const dr_scene_desc* sd, int32_t n) {
       free_batch(c);
       return fail(r, msg);
     }
-    ds[(size_t)i] = dev_scene(sub, true);
+    ds[(size_t)i] = dev_scene(sub);
     SceneChains sc{};
     sc.chain0 = chains;
     sc.n = q.n_chains;
