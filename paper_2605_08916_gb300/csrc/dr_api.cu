@@ -483,18 +483,21 @@ void free_batch(dr_ctx* c) {
   dfree(&c->batch_psum);
 }
 
-// Collapses the freshly built binary BVH into the 4-wide layout (on the
-// device).  Scenes of one triangle (whose binary tree repeats its leaf) and
-// trees whose 4-wide traversal could need more stack than the kernels hold
-// keep the binary BVH only.
-int build_bvh4(dr_ctx* c) {
+// Checks the freshly built binary BVH on the device (a tree: every inner
+// node but the root and every triangle referenced exactly once; its height
+// to *depth2) and collapses it into the 4-wide layout.  Scenes of one
+// triangle (whose binary tree repeats its leaf) are trivially fine and keep
+// the binary BVH only, as do trees whose 4-wide traversal could need more
+// stack than the kernels hold.
+int build_bvh4(dr_ctx* c, int* depth2) {
   dfree(&c->nodes4);
   dfree(&c->tris4);
   c->n_nodes4 = c->bvh4_depth = c->bvh4_stack = 0;
+  *depth2 = 1;
   if (c->nt < 2) return DR_OK;
   const int nn = std::max(1, c->n_nodes);
   void* scratch = nullptr;
-  if (cudaMalloc(&scratch, bvh4_scratch_bytes(nn)) != cudaSuccess) {
+  if (cudaMalloc(&scratch, bvh4_scratch_bytes(nn, c->nt)) != cudaSuccess) {
     cudaGetLastError();
     return fail(DR_ERR_OOM, "dr_scene_upload: 4-wide BVH scratch");
   }
@@ -502,20 +505,27 @@ int build_bvh4(dr_ctx* c) {
   int r = DR_OK;
   const int n4 = bvh4_plan(c->nodes, nn, c->nt, scratch, &plan, c->stream);
   c->launches += plan.launches;
-  if (n4 >= 1 && plan.stack_need <= kTraversalStack) {
-    r = dalloc(&c->nodes4, (size_t)kNode4F4 * n4);
-    if (r == DR_OK) r = dalloc(&c->tris4, (size_t)kTriF4 * c->nt);
-    if (r == DR_OK && bvh4_emit(c->nodes, c->tris, nn, c->nt, scratch, c->nodes4, c->tris4, c->stream) < 0)
-      r = fail(DR_ERR_DEVICE_CHECK, "dr_scene_upload: 4-wide BVH emission failed");
-    c->launches += 1;
-    if (r == DR_OK) {
-      c->n_nodes4 = n4;
-      c->bvh4_depth = plan.depth;
-      c->bvh4_stack = plan.stack_need;
-    } else {
-      dfree(&c->nodes4);
-      dfree(&c->tris4);
+  if (!plan.tree_ok) {
+    r = fail(DR_ERR_DEVICE_CHECK, "dr_scene_upload: the BVH is not a tree over the triangles");
+  } else if (n4 >= 1) {
+    *depth2 = plan.depth2;
+    if (plan.stack_need <= kTraversalStack) {
+      r = dalloc(&c->nodes4, (size_t)kNode4F4 * n4);
+      if (r == DR_OK) r = dalloc(&c->tris4, (size_t)kTriF4 * c->nt);
+      if (r == DR_OK && bvh4_emit(c->nodes, c->tris, nn, c->nt, scratch, c->nodes4, c->tris4, c->stream) < 0)
+        r = fail(DR_ERR_DEVICE_CHECK, "dr_scene_upload: 4-wide BVH emission failed");
+      c->launches += 1;
+      if (r == DR_OK) {
+        c->n_nodes4 = n4;
+        c->bvh4_depth = plan.depth;
+        c->bvh4_stack = plan.stack_need;
+      } else {
+        dfree(&c->nodes4);
+        dfree(&c->tris4);
+      }
     }
+  } else {
+    r = fail(DR_ERR_CUDA, "dr_scene_upload: BVH check / collapse failed");
   }
   cudaFree(scratch);
   const cudaError_t e = cudaGetLastError();
@@ -726,13 +736,13 @@ int dr_scene_upload(dr_ctx* c, const float* verts, int32_t nv, const int32_t* tr
   c->n_lights = (int)lt.size();
   c->tmin = (float)(1e-5 * ext);
   c->inited = false;
-  // the hierarchy must be a tree that the traversal stack can hold
-  int32_t depth = 0;
-  r = dr_bvh_info(c, nullptr, nullptr, &depth);
+  // the hierarchy must be a tree (checked on the device) that the
+  // traversal stack can hold
+  int depth = 1;
+  r = build_bvh4(c, &depth);
   if (r == DR_OK && depth - 1 > kTraversalStack)
     r = fail(DR_ERR_DEVICE_CHECK, "dr_scene_upload: BVH depth " + std::to_string(depth) +
                                       " exceeds the traversal stack (" + std::to_string(kTraversalStack + 1) + ")");
-  if (r == DR_OK) r = build_bvh4(c);
   if (r != DR_OK) c->target = -1;
   c->target_gen++;
   return r;

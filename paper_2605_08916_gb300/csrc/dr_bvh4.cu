@@ -11,11 +11,15 @@
 // subtree (hence every 4-wide leaf) is one contiguous range.
 //
 // Passes (deterministic: no result depends on thread arrival order):
-//   parents      parent index of every inner node
+//   parents      parent index of every inner node, and reference counts
+//                of every inner node and triangle (the tree check: each
+//                inner node but the root, and each triangle, referenced
+//                exactly once)
 //   bottom-up    triangle count and SAH cost per node (the thread that
 //                delivers a node's second finished child settles it; no
 //                thread ever waits for another)
-//   first        depth-first position of every subtree's first triangle
+//   first        depth-first position of every subtree's first triangle,
+//                and every inner node's depth (the binary tree's height)
 //   mark         top-down, one launch per 4-wide level: which binary nodes
 //                become 4-wide nodes, their depth and stack need
 //   scan         4-wide node slots in binary-node order
@@ -70,19 +74,21 @@ struct B4Scratch {
   int* depth;         // [nn] 4-wide depth (root = 1)
   uint32_t* queue[2]; // [nn] each
   uint8_t* as_leaf;   // [nn] 1: becomes one 4-wide leaf
-  uint32_t* counts;   // [4]: queue sizes (2), max need, max depth
+  uint32_t* refs;     // [nn] references to each inner node
+  uint32_t* tri_refs; // [nt] references to each triangle
+  uint32_t* counts;   // [8]: queue sizes (2), max need, max 4-wide depth, max binary depth
   uint32_t* err;      // [1]
   void* scan_tmp;
 };
 
 size_t a256(size_t b) { return (b + 255) & ~size_t(255); }
 
-size_t b4_bytes(int nn) {
+size_t b4_bytes(int nn, int nt) {
   const size_t n = (size_t)nn;
-  return a256(n * 4) * 11 + a256(n) + a256(16) + a256(4) + a256(scan_scratch_bytes(n));
+  return a256(n * 4) * 12 + a256((size_t)nt * 4) + a256(n) + a256(32) + a256(4) + a256(scan_scratch_bytes(n));
 }
 
-B4Scratch b4_carve(void* base, int nn) {
+B4Scratch b4_carve(void* base, int nn, int nt) {
   const size_t n = (size_t)nn;
   char* p = static_cast<char*>(base);
   B4Scratch s;
@@ -97,8 +103,10 @@ B4Scratch b4_carve(void* base, int nn) {
   s.depth = reinterpret_cast<int*>(p); p += a256(n * 4);
   s.queue[0] = reinterpret_cast<uint32_t*>(p); p += a256(n * 4);
   s.queue[1] = reinterpret_cast<uint32_t*>(p); p += a256(n * 4);
+  s.refs = reinterpret_cast<uint32_t*>(p); p += a256(n * 4);
+  s.tri_refs = reinterpret_cast<uint32_t*>(p); p += a256((size_t)nt * 4);
   s.as_leaf = reinterpret_cast<uint8_t*>(p); p += a256(n);
-  s.counts = reinterpret_cast<uint32_t*>(p); p += a256(16);
+  s.counts = reinterpret_cast<uint32_t*>(p); p += a256(32);
   s.err = reinterpret_cast<uint32_t*>(p); p += a256(4);
   s.scan_tmp = p;
   return s;
@@ -107,8 +115,9 @@ B4Scratch b4_carve(void* base, int nn) {
 // triangles below a binary link
 DR_D int count_of(int code, const int* cnt) { return code < 0 ? leaf_count(code) : cnt[code]; }
 
-__global__ void parents_kernel(const float4* __restrict__ n2, int nn, int* parent, uint32_t* visit, uint32_t* is4,
-                               int* need, int* depth, uint32_t* err) {
+__global__ void parents_kernel(const float4* __restrict__ n2, int nn, int nt, int* parent, uint32_t* visit,
+                               uint32_t* is4, int* need, int* depth, uint32_t* refs, uint32_t* tri_refs,
+                               uint32_t* err) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= nn) return;
   visit[n] = 0;
@@ -121,10 +130,27 @@ __global__ void parents_kernel(const float4* __restrict__ n2, int nn, int* paren
   const int c[2] = {__float_as_int(d.x), __float_as_int(d.y)};
   for (int k = 0; k < 2; ++k) {
     if (c[k] >= 0) {
-      if (c[k] == 0 || c[k] >= nn) atomicOr(err, kErrBadIndex);
-      else parent[c[k]] = n;
+      if (c[k] == 0 || c[k] >= nn) {
+        atomicOr(err, kErrBadIndex);
+      } else {
+        parent[c[k]] = n;
+        atomicAdd(&refs[c[k]], 1u);
+      }
+    } else {
+      const int first = leaf_first(c[k]), cnt = leaf_count(c[k]);
+      if (first + cnt > nt) atomicOr(err, kErrBadIndex);
+      else
+        for (int i = 0; i < cnt; ++i) atomicAdd(&tri_refs[first + i], 1u);
     }
   }
+}
+
+// the tree check: the root unreferenced, every other inner node and every
+// triangle referenced exactly once
+__global__ void verify_kernel(int nn, int nt, const uint32_t* refs, const uint32_t* tri_refs, uint32_t* err) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nn && refs[i] != (i == 0 ? 0u : 1u)) atomicOr(err, kErrBadIndex);
+  if (i < nt && tri_refs[i] != 1u) atomicOr(err, kErrBadIndex);
 }
 
 // settles node n (its inner children are settled): count, SAH cost, leaf
@@ -184,7 +210,7 @@ __global__ void bottom_up_kernel(const float4* __restrict__ n2, int nn, const in
 // depth-first position of node n's first triangle: the triangles below
 // every left sibling on the way up come before it
 __global__ void first_kernel(const float4* __restrict__ n2, int nn, const int* parent, const int* cnt, int* first,
-                             uint32_t* err) {
+                             uint32_t* max_depth, uint32_t* err) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= nn) return;
   int f = 0, cur = n;
@@ -192,6 +218,7 @@ __global__ void first_kernel(const float4* __restrict__ n2, int nn, const int* p
     const int p = parent[cur];
     if (p < 0) {
       first[n] = f;
+      atomicMax(max_depth, (uint32_t)guard + 1u);
       return;
     }
     const float4 d = n2[4 * p + 3];
@@ -303,22 +330,34 @@ unsigned blocks(long long n) { return (unsigned)((n + kB4Threads - 1) / kB4Threa
 
 }  // namespace
 
-size_t bvh4_scratch_bytes(int n_inner) { return b4_bytes(std::max(1, n_inner)); }
+size_t bvh4_scratch_bytes(int n_inner, int n_tris) { return b4_bytes(std::max(1, n_inner), std::max(1, n_tris)); }
 
 int bvh4_plan(const float4* d_nodes2, int n_inner, int n_tris, void* scratch, Bvh4Plan* plan, cudaStream_t s) {
   const int nn = n_inner;
   *plan = Bvh4Plan{};
   if (nn < 1 || n_tris < 2) return -1;
-  B4Scratch b = b4_carve(scratch, nn);
+  B4Scratch b = b4_carve(scratch, nn, n_tris);
   cudaMemsetAsync(b.parent, 0xff, (size_t)nn * 4, s);
-  cudaMemsetAsync(b.counts, 0, 16, s);
+  cudaMemsetAsync(b.refs, 0, (size_t)nn * 4, s);
+  cudaMemsetAsync(b.tri_refs, 0, (size_t)n_tris * 4, s);
+  cudaMemsetAsync(b.counts, 0, 32, s);
   cudaMemsetAsync(b.err, 0, 4, s);
   cudaMemsetAsync(b.queue[0], 0, 4, s);  // level 1: the root
-  parents_kernel<<<blocks(nn), kB4Threads, 0, s>>>(d_nodes2, nn, b.parent, b.visit, b.is4, b.need, b.depth, b.err);
+  parents_kernel<<<blocks(nn), kB4Threads, 0, s>>>(d_nodes2, nn, n_tris, b.parent, b.visit, b.is4, b.need, b.depth,
+                                                    b.refs, b.tri_refs, b.err);
+  verify_kernel<<<blocks(std::max(nn, n_tris)), kB4Threads, 0, s>>>(nn, n_tris, b.refs, b.tri_refs, b.err);
+  uint32_t err = 0;
+  cudaMemcpyAsync(&err, b.err, 4, cudaMemcpyDeviceToHost, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return -1;
+  if (err != 0) {
+    plan->tree_ok = 0;
+    return -1;
+  }
+  plan->tree_ok = 1;
   bottom_up_kernel<<<blocks(nn), kB4Threads, 0, s>>>(d_nodes2, nn, b.parent, b.cnt, b.cost, b.as_leaf, b.visit,
                                                       b.err);
-  first_kernel<<<blocks(nn), kB4Threads, 0, s>>>(d_nodes2, nn, b.parent, b.cnt, b.first, b.err);
-  int launches = 3;
+  first_kernel<<<blocks(nn), kB4Threads, 0, s>>>(d_nodes2, nn, b.parent, b.cnt, b.first, b.counts + 4, b.err);
+  int launches = 4;
   uint32_t n_in = 1;
   // one launch per 4-wide level; a tree has fewer levels than inner nodes
   for (int level = 0; n_in > 0; ++level) {
@@ -335,15 +374,19 @@ int bvh4_plan(const float4* d_nodes2, int n_inner, int n_tris, void* scratch, Bv
   }
   launch_exclusive_scan(b.is4, b.slot, (size_t)nn, b.scan_tmp, s);
   launches += 3;
-  uint32_t last[2] = {0, 0}, maxes[2] = {0, 0}, err = 0;
+  uint32_t last[2] = {0, 0}, maxes[3] = {0, 0, 0};
   int root_cnt = 0;
   cudaMemcpyAsync(&last[0], b.slot + nn - 1, 4, cudaMemcpyDeviceToHost, s);
   cudaMemcpyAsync(&last[1], b.is4 + nn - 1, 4, cudaMemcpyDeviceToHost, s);
-  cudaMemcpyAsync(maxes, b.counts + 2, 8, cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(maxes, b.counts + 2, 12, cudaMemcpyDeviceToHost, s);
   cudaMemcpyAsync(&err, b.err, 4, cudaMemcpyDeviceToHost, s);
   cudaMemcpyAsync(&root_cnt, b.cnt, 4, cudaMemcpyDeviceToHost, s);
   if (cudaStreamSynchronize(s) != cudaSuccess) return -1;
-  if (err != 0 || root_cnt != n_tris) return -1;
+  if (err != 0 || root_cnt != n_tris) {
+    plan->tree_ok = 0;
+    return -1;
+  }
+  plan->depth2 = (int)maxes[2];
   plan->n_nodes4 = (int)(last[0] + last[1]);
   plan->stack_need = (int)maxes[0];
   plan->depth = (int)maxes[1];
@@ -353,7 +396,7 @@ int bvh4_plan(const float4* d_nodes2, int n_inner, int n_tris, void* scratch, Bv
 
 int bvh4_emit(const float4* d_nodes2, const float4* d_tris2, int n_inner, int n_tris, void* scratch,
               float4* d_nodes4, float4* d_tris4, cudaStream_t s) {
-  B4Scratch b = b4_carve(scratch, n_inner);
+  B4Scratch b = b4_carve(scratch, n_inner, n_tris);
   emit_kernel<<<blocks(n_inner), kB4Threads, 0, s>>>(d_nodes2, d_tris2, n_inner, n_tris, b.as_leaf, b.cnt, b.first,
                                                       b.is4, b.slot, d_nodes4, d_tris4, b.err);
   uint32_t err = 0;

@@ -64,8 +64,10 @@ void launch_gather_normals(const float* d_vnormals, const int* d_tris, int nt, f
 // the same scratch of bvh4_scratch_bytes(n_inner).
 struct Bvh4Plan {
   int n_nodes4, depth, stack_need, launches;
+  int tree_ok;  // 1: every inner node but the root and every triangle referenced exactly once
+  int depth2;   // height of the binary tree (root = 1)
 };
-size_t bvh4_scratch_bytes(int n_inner);
+size_t bvh4_scratch_bytes(int n_inner, int n_tris);
 int bvh4_plan(const float4* d_nodes2, int n_inner, int n_tris, void* scratch, Bvh4Plan* plan, cudaStream_t s);
 int bvh4_emit(const float4* d_nodes2, const float4* d_tris2, int n_inner, int n_tris, void* scratch,
               float4* d_nodes4, float4* d_tris4, cudaStream_t s);
