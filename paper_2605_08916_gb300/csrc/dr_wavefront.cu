@@ -267,7 +267,13 @@ __global__ void __launch_bounds__(kWfThreads, kWfTrace4MinBlocks) wf_traverse(St
       continue;
     }
     while (true) {
-      if (has) {
+      // inner-node steps and leaf steps are different code: a warp takes
+      // the kind that more of its lanes are at, and the other lanes wait a
+      // step, so each kind runs with many lanes at once
+      const unsigned at_leaf = __ballot_sync(kFull, has && wk.node < 0);
+      const unsigned at_inner = __ballot_sync(kFull, has && wk.node >= 0);
+      const bool leaf_phase = __popc(at_leaf) >= __popc(at_inner);
+      if (has && (wk.node < 0) == leaf_phase) {
         const DevScene& S = scene_of<BATCH>(a, sid);
         if (!shadow) {
           if (closest4_step<kWfStack, STATS>(S, r, ex0, wk, tlim, best, st, &err, &stats)) {
