@@ -306,7 +306,7 @@ int dr_pt_render(dr_ctx* ctx, int32_t max_path_len, uint32_t spp, uint64_t seed,
  *                      (1..64, capped at the resident count; 0 (default):
  *                      all resident blocks).
  *   DR_OPT_REFILL      a traversal warp fetches new rays once fewer than
- *                      this many of its 32 lanes are busy (1..32; default 24).
+ *                      this many of its 32 lanes are busy (1..32; default 16).
  *   DR_OPT_RAY_ORDER   1: before the first traversal of a bounce-by-bounce
  *                      step the camera rays are sorted by pixel (Morton
  *                      order; scene first in a batch), so that neighbouring

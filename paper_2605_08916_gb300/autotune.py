@@ -24,7 +24,7 @@ import torch
 
 def default_candidates():
     return [dict(traverse_blocks=b, refill=f, steps_per_frame=F, tail_bounce=t)
-            for b, f, F, t in itertools.product((0, 6), (20, 24), (2, 4), (0, 4, 6))]
+            for b, f, F, t in itertools.product((0, 6), (12, 16, 20), (2, 4), (0, 4, 6))]
 
 
 def apply(r, cand):

@@ -191,7 +191,7 @@ enum WfMode { kWfStep = 0, kWfInitEval = 1, kWfInitClock = 2 };
 // as stay resident) and the lane count below which a warp refills.
 struct WfTuning {
   int blocks_per_sm = 0;
-  int refill = 24;
+  int refill = 16;
   int tail_bounce = 0;  // 0: every bounce as its own passes; k >= 1: one persistent pass from shading bounce k on
 };
 // Sorting of the camera rays by pixel before the first traversal: the key

@@ -183,7 +183,8 @@ __global__ void __launch_bounds__(kWfThreads, kWfTraceMinBlocks) wf_trace(StepAr
 
 // Persistent 4-wide trace passes with dynamic ray fetch: a warp keeps
 // stepping its lanes' walks one node at a time and, whenever fewer than
-// a.refill lanes (24 of 32 by default; measured better than 12 and 20)
+// a.refill lanes (16 of 32 by default; with inner-node and leaf steps
+// alternated by majority, measured better than 20-32)
 // still hold a ray, refills the idle lanes from the queue with one atomic
 // per warp.  A warp's time is then set by its total work
 // rather than by its slowest ray.
