@@ -107,8 +107,12 @@ int dr_destroy(dr_ctx* ctx);
  *              normals are all non-zero (zero rows mark flat meshes)
  *   tri_mat    int32 [nt] material index per triangle
  *   mats       float [nm * 12] materials: type (0 diffuse, 1 glossy GGX coat
- *              over Lambertian, 2 smooth dielectric, 3 black emitter),
- *              albedo rgb, roughness, ior, emission rgb, f0, 0, 0.  Emission
+ *              over Lambertian, 2 smooth dielectric, 3 black emitter,
+ *              4 rough GGX conductor), albedo rgb, roughness, ior, emission
+ *              rgb, f0, 0, 0.  A conductor (pbrt's conductor, Sec. 6 "Test
+ *              scenes") stores the real part eta of its complex index of
+ *              refraction (rgb, > 0) in the albedo slots and the imaginary
+ *              part k (rgb, > 0) in the last three slots.  Emission
  *              is one-sided along cross(v1 - v0, v2 - v0); emitting
  *              triangles form the light set used by next-event estimation.
  *   camera     float [10]: eye xyz, look-at xyz, up xyz, vertical fov (deg)

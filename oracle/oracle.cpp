@@ -133,10 +133,12 @@ constexpr double LUM[3] = {0.2126, 0.7152, 0.0722};
 constexpr double PI = 3.14159265358979323846;
 
 // ---------------------------------------------------------------- scene
-enum MatType { M_DIFFUSE = 0, M_GLOSSY = 1, M_DIELECTRIC = 2, M_EMITTER = 3 };
+enum MatType { M_DIFFUSE = 0, M_GLOSSY = 1, M_DIELECTRIC = 2, M_EMITTER = 3, M_CONDUCTOR = 4 };
+// Conductor records reuse the albedo slots for the real part eta of the
+// complex index of refraction (RGB) and slots 9..11 for its imaginary part k.
 struct Mat {
   int type;
-  double albedo[3], rough, ior, emit[3], f0;
+  double albedo[3], rough, ior, emit[3], f0, k[3];
   bool emissive() const { return emit[0] > 0 || emit[1] > 0 || emit[2] > 0; }
 };
 struct Tri {
@@ -370,9 +372,67 @@ void glossy_eval(const Mat& m, const V3<T>& n, const V3<T>& wo, const V3<T>& wi,
   pdf = GLOSSY_SPEC_PROB * D * nh / (4.0 * oh_abs) + (1.0 - GLOSSY_SPEC_PROB) * ci / PI;
 }
 
+// Complex numbers over the scalar type T (values or duals), enough for the
+// Fresnel equations of an absorbing interface.
+template <class T>
+struct Cx {
+  T re, im;
+  Cx(T r = T(0.0), T i = T(0.0)) : re(r), im(i) {}
+};
+template <class T> Cx<T> operator+(const Cx<T>& a, const Cx<T>& b) { return Cx<T>(a.re + b.re, a.im + b.im); }
+template <class T> Cx<T> operator-(const Cx<T>& a, const Cx<T>& b) { return Cx<T>(a.re - b.re, a.im - b.im); }
+template <class T> Cx<T> operator*(const Cx<T>& a, const Cx<T>& b) {
+  return Cx<T>(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+template <class T> Cx<T> operator/(const Cx<T>& a, const Cx<T>& b) {
+  T q = b.re * b.re + b.im * b.im;
+  return Cx<T>((a.re * b.re + a.im * b.im) / q, (a.im * b.re - a.re * b.im) / q);
+}
+template <class T> T norm2(const Cx<T>& a) { return a.re * a.re + a.im * a.im; }
+// Principal square root.
+template <class T> Cx<T> csqrt(const Cx<T>& z) {
+  T r = sqrt(norm2(z));
+  T re = sqrt((r + z.re) * 0.5);
+  T im = sqrt((r - z.re) * 0.5);
+  if (val(z.im) < 0.0) im = -im;
+  return Cx<T>(re, im);
+}
+
+// Fresnel reflectance of unpolarised light arriving from vacuum at an
+// interface of complex index eta + i k (a conductor), for the cosine ci of
+// the angle of incidence: Snell's law with the complex index gives the
+// transmitted cosine, and R = (|r_s|^2 + |r_p|^2) / 2 with the amplitude
+// coefficients of the Fresnel equations.
+template <class T>
+T fresnel_conductor(const T& ci, double eta, double k) {
+  const Cx<T> n{T(eta), T(k)};
+  Cx<T> s2(1.0 - ci * ci);
+  Cx<T> ct = csqrt(Cx<T>(T(1.0)) - s2 / (n * n));
+  Cx<T> c(ci);
+  Cx<T> rs = (c - n * ct) / (c + n * ct);
+  Cx<T> rp = (n * c - ct) / (n * c + ct);
+  return (norm2(rs) + norm2(rp)) * 0.5;
+}
+
+// Rough conductor (pbrt's conductor with a GGX distribution): a single
+// specular microfacet lobe, D G2 F / (4 cos_o cos_i) with the conductor
+// Fresnel per RGB channel, sampled by D cos(theta_h) half-vectors.
+template <class T>
+void conductor_eval(const Mat& m, const V3<T>& n, const V3<T>& wo, const V3<T>& wi, T fs[3], T& pdf) {
+  T co = dot(n, wo), ci = dot(n, wi);
+  V3<T> h = normalize(wo + wi);
+  T nh = dot(n, h), oh = dot(wo, h);
+  T D = ggx_D(nh, m.rough);
+  T G = 1.0 / (1.0 + smith_lambda(co, m.rough) + smith_lambda(ci, m.rough));
+  for (int c = 0; c < 3; ++c) fs[c] = D * G * fresnel_conductor(oh, m.albedo[c], m.k[c]) / (4.0 * co * ci);
+  T oh_abs = val(oh) >= 0 ? oh : -oh;
+  pdf = D * nh / (4.0 * oh_abs);
+}
+
 template <class T>
 void bsdf_eval(const Mat& m, const V3<T>& n, const V3<T>& wo, const V3<T>& wi, T fs[3], T& pdf) {
   if (m.type == M_GLOSSY) { glossy_eval(m, n, wo, wi, fs, pdf); return; }
+  if (m.type == M_CONDUCTOR) { conductor_eval(m, n, wo, wi, fs, pdf); return; }
   T ci = dot(n, wi);
   for (int c = 0; c < 3; ++c) fs[c] = T(m.albedo[c] / PI);
   pdf = ci / PI;
@@ -393,10 +453,11 @@ bool opaque_sample(const Mat& m, const V3<T>& n, const D3& ngf, const V3<T>& wo,
                    V3<T>& wi, T w[3], T& pdf, int& lobe) {
   V3<T> t, b;
   onb(n, t, b);
-  if (m.type == M_GLOSSY) {
-    if (val(u1) < GLOSSY_SPEC_PROB) {
+  if (m.type == M_GLOSSY || m.type == M_CONDUCTOR) {
+    const double sp = m.type == M_CONDUCTOR ? 1.0 : GLOSSY_SPEC_PROB;
+    if (val(u1) < sp) {
       lobe = 1;
-      T v = u1 / GLOSSY_SPEC_PROB;
+      T v = u1 / sp;
       double a2 = m.rough * m.rough;
       T den = 1.0 + (a2 - 1.0) * v;
       T ch = sqrt((1.0 - v) / den);
@@ -836,6 +897,7 @@ void* orc_scene_create(const float* verts, int nv, const int* tris, const float*
     q.rough = m[4];
     q.ior = m[5];
     q.f0 = m[9];
+    for (int c = 0; c < 3; ++c) q.k[c] = m[9 + c];
     S->mats.push_back(q);
   }
   double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
@@ -980,6 +1042,7 @@ int orc_bsdf_sample(const float* mat, const double* n, const double* wo, double 
   m.type = (int)mat[0];
   for (int c = 0; c < 3; ++c) { m.albedo[c] = mat[1 + c]; m.emit[c] = mat[6 + c]; }
   m.rough = mat[4]; m.ior = mat[5]; m.f0 = mat[9];
+  for (int c = 0; c < 3; ++c) m.k[c] = mat[9 + c];
   D3 N(n[0], n[1], n[2]), WO(wo[0], wo[1], wo[2]), WI;
   double ww[3], pp;
   int lb = -1;
@@ -996,11 +1059,13 @@ void orc_bsdf_eval(const float* mat, const double* n, const double* wo, const do
   m.type = (int)mat[0];
   for (int c = 0; c < 3; ++c) { m.albedo[c] = mat[1 + c]; m.emit[c] = mat[6 + c]; }
   m.rough = mat[4]; m.ior = mat[5]; m.f0 = mat[9];
+  for (int c = 0; c < 3; ++c) m.k[c] = mat[9 + c];
   D3 N(n[0], n[1], n[2]), WO(wo[0], wo[1], wo[2]), WI(wi[0], wi[1], wi[2]);
   bsdf_eval<double>(m, N, WO, WI, fs, *pdf);
 }
 
 double orc_fresnel_dielectric(double ci, double ct, double eta) { return fresnel_dielectric(ci, ct, eta); }
+double orc_fresnel_conductor(double ci, double eta, double k) { return fresnel_conductor<double>(ci, eta, k); }
 
 // One Evolve move of x (Alg. 2 / Alg. 4) for a surviving chain, given score;
 // exposes the LocalDynamics step alone for closed-form checks.

@@ -68,6 +68,8 @@ def lib():
         L.orc_bsdf_eval.argtypes = [fp, dp, dp, dp, dp, dp]
         L.orc_fresnel_dielectric.restype = C.c_double
         L.orc_fresnel_dielectric.argtypes = [C.c_double] * 3
+        L.orc_fresnel_conductor.restype = C.c_double
+        L.orc_fresnel_conductor.argtypes = [C.c_double] * 3
         L.orc_local_dynamics.argtypes = [dp, C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, C.c_int, dp, dp, dp]
         L.orc_restore_run.argtypes = [P, C.c_int, C.POINTER(Params), C.c_uint64, C.c_uint32, up, C.c_int64,
                                       C.c_int, P, P, P, P, P, P, P, P, P, P]

@@ -609,8 +609,15 @@ int dr_scene_upload(dr_ctx* c, const float* verts, int32_t nv, const int32_t* tr
     if (tri_mat[i] < 0 || tri_mat[i] >= nm) return fail(DR_ERR_INVALID_ARG, "dr_scene_upload: material out of range");
   for (int i = 0; i < nm; ++i) {
     const float t = mats[12 * i];
-    if (!(t == 0.f || t == 1.f || t == 2.f || t == 3.f)) return fail(DR_ERR_INVALID_ARG, "dr_scene_upload: bad material type");
-    if (t == 1.f && !(mats[12 * i + 4] > 0.f)) return fail(DR_ERR_INVALID_ARG, "dr_scene_upload: glossy roughness must be > 0");
+    if (!(t == 0.f || t == 1.f || t == 2.f || t == 3.f || t == 4.f))
+      return fail(DR_ERR_INVALID_ARG, "dr_scene_upload: bad material type");
+    if ((t == 1.f || t == 4.f) && !(mats[12 * i + 4] > 0.f))
+      return fail(DR_ERR_INVALID_ARG, "dr_scene_upload: glossy / conductor roughness must be > 0");
+    if (t == 4.f)
+      for (int ch = 0; ch < 3; ++ch)
+        if (!(mats[12 * i + 1 + ch] > 0.f) || !(mats[12 * i + 9 + ch] > 0.f) || !std::isfinite(mats[12 * i + 1 + ch]) ||
+            !std::isfinite(mats[12 * i + 9 + ch]))
+          return fail(DR_ERR_INVALID_ARG, "dr_scene_upload: conductor eta and k must be finite and > 0");
     if (t == 2.f && !(mats[12 * i + 5] > 0.f)) return fail(DR_ERR_INVALID_ARG, "dr_scene_upload: dielectric ior must be > 0");
   }
   for (long long i = 0; i < 3ll * nv; ++i)

@@ -118,9 +118,11 @@ DR_D float wrap01(float v) {
 // Light record (64 B, 4 x float4): l0 = (v0, tri id bits), l1 = (v1, selection
 // probability), l2 = (v2, area), l3 = (cdf upper bound, -, -, -); the emission
 // comes from the triangle's material.
-// Material: 12 floats [type, albedo rgb, roughness, ior, emission rgb, f0, -, -].
+// Material: 12 floats [type, albedo rgb, roughness, ior, emission rgb, f0, -, -];
+// a conductor keeps the real part eta of its complex index (RGB) in the
+// albedo slots and the imaginary part k (RGB) in the last three.
 constexpr int kNodeF4 = 4, kTriF4 = 3, kSurfF4 = 5, kLightF4 = 4, kMatFloats = 12;
-enum MatType { kDiffuse = 0, kGlossy = 1, kDielectric = 2, kEmitter = 3 };
+enum MatType { kDiffuse = 0, kGlossy = 1, kDielectric = 2, kEmitter = 3, kConductor = 4 };
 constexpr float kGlossySpecProb = 0.5f;
 
 // 4-wide BVH node (112 B, 7 x float4): lo.x[4], hi.x[4], lo.y[4], hi.y[4],

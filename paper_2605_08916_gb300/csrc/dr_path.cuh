@@ -29,7 +29,8 @@ namespace dr {
 // ---------------------------------------------------------------- records
 struct MatP {
   int type;
-  float3 albedo, emit;
+  float3 albedo, emit;  // conductor: albedo = eta; k at rec[9..11]
+  const float* rec;
   float rough, ior, f0;
   bool emissive;
 };
@@ -43,6 +44,7 @@ DR_D MatP load_mat(const float* __restrict__ mats, int id) {
   r.ior = __ldg(m + 5);
   r.emit = f3(__ldg(m + 6), __ldg(m + 7), __ldg(m + 8));
   r.f0 = __ldg(m + 9);
+  r.rec = m;
   r.emissive = r.emit.x > 0.f || r.emit.y > 0.f || r.emit.z > 0.f;
   return r;
 }
@@ -127,18 +129,24 @@ DR_D float3 onb_bwd(float3 n, float3 gt, float3 gb) {
 }
 
 // ---------------------------------------------------------------- BSDFs
-// GGX (Trowbridge-Reitz) D, Smith height-correlated G2, Schlick F; the
-// glossy BSDF is a GGX coat over a Lambertian base, sampled by picking the
+// GGX (Trowbridge-Reitz) D, Smith height-correlated G2.  The glossy BSDF is
+// a GGX coat (Schlick F) over a Lambertian base, sampled by picking the
 // specular lobe with probability 1/2 (D cos(theta_h) half-vector sampling)
-// or the cosine-weighted diffuse lobe; its pdf is the two-lobe mixture.
+// or the cosine-weighted diffuse lobe; its pdf is the two-lobe mixture.  The
+// rough conductor (pbrt's conductor, Sec. 6 "Test scenes") is the specular
+// lobe alone with the Fresnel reflectance of a complex index per channel,
+// always sampled by half-vectors.
 struct GlossyFwd {
-  float co, ci, hl, nh, oh, ih, k, D, lo, li, ro, ri, G, om, F, spec, pdf;
+  float co, ci, hl, nh, oh, ih, k, D, lo, li, ro, ri, G, pdf, sp;
   float3 h, hv;
 };
+
+DR_D float spec_prob(const MatP& m) { return m.type == kConductor ? 1.0f : kGlossySpecProb; }
 
 DR_D GlossyFwd glossy_fwd(const MatP& m, float3 n, float3 wo, float3 wi) {
   GlossyFwd g;
   const float a2 = m.rough * m.rough;
+  g.sp = spec_prob(m);
   g.co = dot(n, wo);
   g.ci = dot(n, wi);
   g.hv = wo + wi;
@@ -154,21 +162,83 @@ DR_D GlossyFwd glossy_fwd(const MatP& m, float3 n, float3 wo, float3 wi) {
   g.lo = 0.5f * (g.ro - 1.0f);
   g.li = 0.5f * (g.ri - 1.0f);
   g.G = 1.0f / (1.0f + g.lo + g.li);
-  g.om = 1.0f - g.ih;
-  const float om2 = g.om * g.om;
-  g.F = m.f0 + (1.0f - m.f0) * (om2 * om2 * g.om);
-  g.spec = g.D * g.G * g.F / (4.0f * g.co * g.ci);
-  g.pdf = kGlossySpecProb * g.D * g.nh / (4.0f * fabsf(g.oh)) + (1.0f - kGlossySpecProb) * g.ci * kInvPi;
+  g.pdf = g.sp * g.D * g.nh / (4.0f * fabsf(g.oh)) + (1.0f - g.sp) * g.ci * kInvPi;
   return g;
+}
+
+// Fresnel reflectance of unpolarised light from vacuum onto an interface of
+// complex index eta + i k, written in real variables: with
+// A = |(eta + i k)^2 - sin^2| and a = sqrt((A + Re) / 2),
+// R_s = (A + c^2 - 2ac) / (A + c^2 + 2ac) and
+// R_p = R_s (c^2 A + s^4 - 2ac s^2) / (c^2 A + s^4 + 2ac s^2); R = (R_s + R_p) / 2.
+// Also returns dR/dc (forward-mode, for the adjoint).
+DR_D float fresnel_conductor(float c, float eta, float k, float* dFdc) {
+  const float c2 = c * c, s2 = 1.0f - c2, ds2 = -2.0f * c;
+  const float t0 = eta * eta - k * k - s2, dt0 = -ds2;
+  const float A = sqrtf(t0 * t0 + 4.0f * eta * eta * k * k), dA = t0 * dt0 / A;
+  const float a = sqrtf(fmaxf(0.5f * (A + t0), 0.0f));
+  const float da = a > 0.0f ? (dA + dt0) / (4.0f * a) : 0.0f;
+  const float t1 = A + c2, dt1 = dA + 2.0f * c;
+  const float t2 = 2.0f * a * c, dt2 = 2.0f * (da * c + a);
+  const float q1 = 1.0f / (t1 + t2);
+  const float Rs = (t1 - t2) * q1;
+  const float dRs = 2.0f * (t2 * dt1 - t1 * dt2) * q1 * q1;
+  const float t3 = c2 * A + s2 * s2, dt3 = 2.0f * c * A + c2 * dA + 2.0f * s2 * ds2;
+  const float t4 = t2 * s2, dt4 = dt2 * s2 + t2 * ds2;
+  const float q2 = 1.0f / (t3 + t4);
+  const float Q = (t3 - t4) * q2;
+  const float dQ = 2.0f * (t4 * dt3 - t3 * dt4) * q2 * q2;
+  *dFdc = 0.5f * (dRs * (1.0f + Q) + Rs * dQ);
+  return 0.5f * Rs * (1.0f + Q);
+}
+
+// Per-channel Fresnel of the specular lobe at cos = ih.
+DR_D float3 lobe_fresnel(const MatP& m, float ih) {
+  if (m.type == kConductor) {
+    // k is read here rather than with the record: it is live only here
+    float d;
+    return f3(fresnel_conductor(ih, m.albedo.x, __ldg(m.rec + 9), &d),
+              fresnel_conductor(ih, m.albedo.y, __ldg(m.rec + 10), &d),
+              fresnel_conductor(ih, m.albedo.z, __ldg(m.rec + 11), &d));
+  }
+  const float om = 1.0f - ih, om2 = om * om;
+  const float F = m.f0 + (1.0f - m.f0) * (om2 * om2 * om);
+  return f3(F, F, F);
+}
+
+// sum_c g_c F_c and sum_c g_c dF_c/d(ih) for the adjoint, one channel at a
+// time (few live registers).
+DR_D void lobe_fresnel_dots(const MatP& m, float ih, float3 g, float* gF, float* gdF) {
+  if (m.type == kConductor) {
+    float d0, d1, d2;
+    const float F0 = fresnel_conductor(ih, m.albedo.x, __ldg(m.rec + 9), &d0);
+    float sF = g.x * F0, sd = g.x * d0;
+    const float F1 = fresnel_conductor(ih, m.albedo.y, __ldg(m.rec + 10), &d1);
+    sF += g.y * F1;
+    sd += g.y * d1;
+    const float F2 = fresnel_conductor(ih, m.albedo.z, __ldg(m.rec + 11), &d2);
+    *gF = sF + g.z * F2;
+    *gdF = sd + g.z * d2;
+    return;
+  }
+  const float om = 1.0f - ih, om2 = om * om;
+  const float F = m.f0 + (1.0f - m.f0) * (om2 * om2 * om);
+  const float gs = g.x + g.y + g.z;
+  *gF = gs * F;
+  *gdF = gs * (-5.0f * (1.0f - m.f0) * om2 * om2);
 }
 
 // BSDF value (RGB) and sampling pdf (solid angle) of an opaque material.
 DR_D float3 bsdf_eval(const MatP& m, float3 n, float3 wo, float3 wi, float* pdf) {
-  if (m.type == kGlossy) {
+  if (m.type == kGlossy || m.type == kConductor) {
     const GlossyFwd g = glossy_fwd(m, n, wo, wi);
     *pdf = g.pdf;
+    const float3 F = lobe_fresnel(m, g.ih);
+    const float DG = g.D * g.G, den = 4.0f * g.co * g.ci;
+    const float3 spec = f3(DG * F.x / den, DG * F.y / den, DG * F.z / den);
+    if (m.type == kConductor) return spec;
     const float kd = (1.0f - m.f0) * kInvPi;
-    return m.albedo * kd + f3(g.spec, g.spec, g.spec);
+    return m.albedo * kd + spec;
   }
   *pdf = dot(n, wi) * kInvPi;
   return m.albedo * kInvPi;
@@ -178,29 +248,29 @@ DR_D float3 bsdf_eval(const MatP& m, float3 n, float3 wo, float3 wi, float* pdf)
 // d(n), d(wo), d(wi).
 DR_D void bsdf_eval_bwd(const MatP& m, float3 n, float3 wo, float3 wi, float3 gfs, float gpdf, float3& gn,
                         float3& gwo, float3& gwi) {
-  if (m.type != kGlossy) {
+  if (m.type != kGlossy && m.type != kConductor) {
     gn += wi * (gpdf * kInvPi);
     gwi += n * (gpdf * kInvPi);
     return;
   }
   const GlossyFwd g = glossy_fwd(m, n, wo, wi);
+  float gFsum, gdF;  // sum_c gfs_c F_c, sum_c gfs_c dF_c / d(ih)
+  lobe_fresnel_dots(m, g.ih, gfs, &gFsum, &gdF);
   const float a2 = m.rough * m.rough;
-  const float gspec = gfs.x + gfs.y + gfs.z;
   const float den = 4.0f * g.co * g.ci;
   const float aoh = fabsf(g.oh);
-  const float gD = gspec * g.G * g.F / den + gpdf * kGlossySpecProb * g.nh / (4.0f * aoh);
-  const float gG = gspec * g.D * g.F / den;
-  const float gF = gspec * g.D * g.G / den;
+  const float gspec = gFsum * (g.D * g.G / den);  // sum_c gfs_c spec_c
+  const float gD = gFsum * g.G / den + gpdf * g.sp * g.nh / (4.0f * aoh);
+  const float gG = gFsum * g.D / den;
   // Lambda'(c) = -a2 / (2 r c^3), dG/dLambda = -G^2
   const float dlo = -a2 / (2.0f * g.ro * g.co * g.co * g.co);
   const float dli = -a2 / (2.0f * g.ri * g.ci * g.ci * g.ci);
-  const float gco = -gspec * g.spec / g.co - gG * g.G * g.G * dlo;
-  const float gci = -gspec * g.spec / g.ci - gG * g.G * g.G * dli + gpdf * (1.0f - kGlossySpecProb) * kInvPi;
+  const float gco = -gspec / g.co - gG * g.G * g.G * dlo;
+  const float gci = -gspec / g.ci - gG * g.G * g.G * dli + gpdf * (1.0f - g.sp) * kInvPi;
   const float dD = g.D * (-4.0f * g.nh * (a2 - 1.0f) / g.k);
-  const float gnh = gD * dD + gpdf * kGlossySpecProb * g.D / (4.0f * aoh);
-  const float goh = -gpdf * kGlossySpecProb * g.D * g.nh * (g.oh >= 0.0f ? 1.0f : -1.0f) / (4.0f * g.oh * g.oh);
-  const float om2 = g.om * g.om;
-  const float gih = gF * (-5.0f * (1.0f - m.f0) * om2 * om2);
+  const float gnh = gD * dD + gpdf * g.sp * g.D / (4.0f * aoh);
+  const float goh = -gpdf * g.sp * g.D * g.nh * (g.oh >= 0.0f ? 1.0f : -1.0f) / (4.0f * g.oh * g.oh);
+  const float gih = gdF * (g.D * g.G / den);
   const float3 gh = n * gnh + wo * goh + wi * gih;
   gn += g.h * gnh;
   gwo += g.h * goh;
@@ -233,9 +303,10 @@ struct SampleRec {
 DR_D bool opaque_sample(const MatP& m, float3 n, float3 ngf, float3 wo, float u1, float u2, SampleRec& s) {
   float3 t, b;
   onb(n, t, b);
-  if (m.type == kGlossy && u1 < kGlossySpecProb) {
+  const float pspec = spec_prob(m);
+  if ((m.type == kGlossy && u1 < pspec) || m.type == kConductor) {
     s.lobe = 1;
-    const float v = u1 * (1.0f / kGlossySpecProb);
+    const float v = u1 * (1.0f / pspec);
     const float a2 = m.rough * m.rough;
     const float den = 1.0f + (a2 - 1.0f) * v;
     const float ch = sqrtf((1.0f - v) / den);
@@ -265,7 +336,8 @@ DR_D void opaque_sample_dir_bwd(const MatP& m, int lobe, float3 n, float3 wo, fl
   onb(n, t, b);
   float3 gt, gb;
   if (lobe == 1) {
-    const float v = u1 * (1.0f / kGlossySpecProb);
+    const float pspec = spec_prob(m);
+    const float v = u1 * (1.0f / pspec);
     const float a2 = m.rough * m.rough;
     const float den = 1.0f + (a2 - 1.0f) * v;
     const float ch = sqrtf((1.0f - v) / den);
@@ -288,7 +360,7 @@ DR_D void opaque_sample_dir_bwd(const MatP& m, int lobe, float3 n, float3 wo, fl
     float gv = 0.0f;
     if (sh > 0.0f) gv += gsh * a2 / (2.0f * sh * den2);
     if (ch > 0.0f) gv -= gch * a2 / (2.0f * ch * den2);
-    gu1 = gv * (1.0f / kGlossySpecProb);
+    gu1 = gv * (1.0f / pspec);
     gu2 = gph * 2.0f * kPi;
   } else {
     const float dvdu = m.type == kGlossy ? 1.0f / (1.0f - kGlossySpecProb) : 1.0f;

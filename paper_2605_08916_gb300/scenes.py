@@ -22,7 +22,10 @@ are not available; the generators below are the synthetic stand-ins:
 Material record layout (float32 x 12, shared by both sides):
 ``[type, albedo_r, albedo_g, albedo_b, roughness, ior, emit_r, emit_g,
 emit_b, f0, 0, 0]`` with type 0 diffuse, 1 glossy (GGX coat over a
-Lambertian base), 2 smooth dielectric, 3 black emitter.  Any material may
+Lambertian base), 2 smooth dielectric, 3 black emitter, 4 rough conductor.
+A conductor record holds the real part eta of its complex index of
+refraction (RGB) in the albedo slots and the imaginary part k (RGB) in slots
+9..11: ``[4, eta_rgb, roughness, 0, emit_rgb, k_rgb]``.  Any material may
 carry emission; emission is one-sided along the triangle's winding normal
 ``cross(v1 - v0, v2 - v0)``.
 
@@ -39,6 +42,7 @@ MAT_DIFFUSE = 0
 MAT_GLOSSY = 1
 MAT_DIELECTRIC = 2
 MAT_EMITTER = 3
+MAT_CONDUCTOR = 4
 MAT_FLOATS = 12
 
 
@@ -51,6 +55,18 @@ def material(kind, albedo=(0.0, 0.0, 0.0), roughness=0.0, ior=1.5,
     m[5] = ior
     m[6:9] = emission
     m[9] = f0
+    return m
+
+
+def conductor(eta, k, roughness, emission=(0.0, 0.0, 0.0)):
+    """Rough conductor record: complex index eta + i k per RGB channel and
+    GGX roughness (alpha)."""
+    m = np.zeros(MAT_FLOATS, np.float32)
+    m[0] = MAT_CONDUCTOR
+    m[1:4] = eta
+    m[4] = roughness
+    m[6:9] = emission
+    m[9:12] = k
     return m
 
 
@@ -146,12 +162,13 @@ def _box_faces(lo, hi, bottomless=True, inward=False):
     return faces
 
 
-def cornell_box(seed=1, width=64, height=64, glossy=False, light_radiance=15.0):
+def cornell_box(seed=1, width=64, height=64, glossy=False, light_radiance=15.0, metal=False):
     """Closed room (6 walls, 12 triangles, camera inside), two bottomless
     axis-aligned boxes (2 x 10 triangles) and one quad area light (2 triangles)
     under the ceiling, facing down.  Wall / box albedo per face and channel is
     U[0.2, 0.8]; with ``glossy`` the boxes get a GGX coat (roughness
-    U[0.05, 0.3], F0 = 0.04)."""
+    U[0.05, 0.3], F0 = 0.04); with ``metal`` they are rough conductors
+    (eta U[0.2, 1.6], k U[2, 4] per channel, roughness U[0.05, 0.3])."""
     rng = np.random.default_rng(seed)
     b = _Builder()
     # room [-1,1] x [0,2] x [-1,3]; walls face inward
@@ -162,7 +179,9 @@ def cornell_box(seed=1, width=64, height=64, glossy=False, light_radiance=15.0):
     for lo, hi in boxes:
         for f in _box_faces(lo, hi, bottomless=True):
             alb = rng.uniform(0.2, 0.8, 3)
-            if glossy:
+            if metal:
+                m = conductor(rng.uniform(0.2, 1.6, 3), rng.uniform(2.0, 4.0, 3), rng.uniform(0.05, 0.3))
+            elif glossy:
                 m = material(MAT_GLOSSY, alb, roughness=rng.uniform(0.05, 0.3), f0=0.04)
             else:
                 m = material(MAT_DIFFUSE, alb)
@@ -172,7 +191,8 @@ def cornell_box(seed=1, width=64, height=64, glossy=False, light_radiance=15.0):
     # facing down: counter-clockwise seen from below
     b.add_quad((-0.25, y, -0.25), (0.25, y, -0.25), (0.25, y, 0.25), (-0.25, y, 0.25), lm)
     cam = [0.0, 1.0, 2.9, 0.0, 1.0, 0.0, 0.0, 1.0, 0.0, 40.0]
-    return b.build(cam, width, height, f"cornell{'-glossy' if glossy else ''}-{width}x{height}")
+    kind = '-metal' if metal else '-glossy' if glossy else ''
+    return b.build(cam, width, height, f"cornell{kind}-{width}x{height}")
 
 
 def uv_sphere(center, radius, n_theta, n_phi):

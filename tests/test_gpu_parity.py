@@ -151,6 +151,7 @@ def test_one_triangle_scene_keeps_the_binary_bvh(torch, R):
 EVAL_CASES = {
     "cornell-L4": (lambda: S.cornell_box(1, 64, 64), 4),
     "glossy-L8": (lambda: S.cornell_box(1, 256, 256, glossy=True), 8),
+    "conductor-L8": (lambda: S.cornell_box(1, 256, 256, metal=True), 8),
     "caustic-L6": (lambda: S.caustic_scene(1, 64, 64, n_theta=24, n_phi=24), 6),
 }
 
@@ -266,6 +267,20 @@ def test_chain_parity_glossy_adjoint(torch, R, oracle):
     po = oracle.make_params(L=8, drift="exact", rb=True, k0=k0)
     frac, first, n = _chain_parity(torch, R, oracle, scene, pg, po, N=65536, M=512, T=16, seed=6)
     print("glossy adjoint divergent fraction", frac, "compared", n)
+    assert frac <= 0.01
+
+
+@pytest.mark.parametrize("wavefront", [0, 1])
+def test_chain_parity_conductor_adjoint(torch, R, oracle, wavefront):
+    """Rough conductor boxes (complex-index Fresnel per channel) with the
+    adjoint drift, in both execution modes."""
+    scene = S.cornell_box(4, 128, 128, metal=True)
+    k0 = 1e6
+    pg = R.make_params(L=8, drift="adjoint", rb=True, k0=k0, steps_per_splat=16)
+    po = oracle.make_params(L=8, drift="exact", rb=True, k0=k0)
+    frac, first, n = _chain_parity_opts(torch, R, oracle, scene, pg, po, N=16384, M=512, T=16, seed=9,
+                                        opts={"wavefront": wavefront})
+    print("conductor adjoint divergent fraction", frac, "compared", n)
     assert frac <= 0.01
 
 
@@ -393,7 +408,7 @@ def test_full_size_batch_matches_oracle_on_sampled_chains(torch, R, oracle):
     assert max(fracs) <= 0.05 and np.mean(fracs) <= 0.02
 
 
-@pytest.mark.parametrize("which", ["glossy", "procedural"])
+@pytest.mark.parametrize("which", ["glossy", "conductor", "procedural"])
 def test_wavefront_matches_fused(torch, R, which):
     """The bounce-by-bounce execution performs the same operations per path
     as the fused kernel; the compiler may contract multiply-adds
@@ -401,6 +416,8 @@ def test_wavefront_matches_fused(torch, R, which):
     whose discrete choices flip on such a difference are counted)."""
     if which == "glossy":
         scene, L = S.cornell_box(1, 64, 64, glossy=True), 8
+    elif which == "conductor":
+        scene, L = S.cornell_box(1, 64, 64, metal=True), 8
     else:
         scene, L = S.procedural_scene(1, 64, 36, target_tris=60000, n_objects=40), 12
     out = []
@@ -717,6 +734,13 @@ def test_errors_are_reported_not_raised_on_device(torch, R):
     with pytest.raises(_lib.DRError) as e:
         r.upload_scene(S.Scene(scene.verts, tris, scene.tri_mat, scene.materials, scene.camera, 8, 8))
     assert e.value.code == _lib.DR_ERR_INVALID_ARG
+    metal = S.cornell_box(1, 8, 8, metal=True)
+    for slot in (2, 10):  # eta and k of a conductor must be > 0
+        mats = metal.materials.copy()
+        mats[mats[:, 0] == S.MAT_CONDUCTOR, slot] = 0.0
+        with pytest.raises(_lib.DRError) as e:
+            r.upload_scene(S.Scene(metal.verts, metal.tris, metal.tri_mat, mats, metal.camera, 8, 8))
+        assert e.value.code == _lib.DR_ERR_INVALID_ARG
     r.upload_scene(scene)
     r.init_chains(64, 1, R.make_params(L=3, drift="adjoint", k0=100.0))
     r.step(2)

@@ -10,7 +10,10 @@ P5  (i) BVH closest hit == brute force (identical triangle ids and t);
     albedo * Le * F with F the point-to-parallel-square form factor;
     (iv) BSDF sampler vs its pdf: E[g / pdf] = integral of g over the
     hemisphere for g = 1 and g = cos; sampler weight == fs cos / pdf;
-    reciprocity; energy <= 1.
+    reciprocity; energy <= 1;
+    (v) conductor Fresnel (complex index) vs the normal-incidence closed
+    form, the dielectric equations at k = 0, the grazing limit and the
+    real-variable (a, b) form of the same equations.
 P7  Philox4x32-10 (cited in Sec. 4.3) vs Triton's independent implementation
     run by its CPU interpreter.
 """
@@ -33,6 +36,7 @@ def _info_equal(a, b):
 def test_gradient_matches_central_differences(oracle):
     O = oracle
     for scene, L in [(S.cornell_box(1, 16, 16), 4), (S.cornell_box(2, 16, 16, glossy=True), 5),
+                     (S.cornell_box(3, 16, 16, metal=True), 5),
                      (S.caustic_scene(1, 16, 16, n_theta=12, n_phi=12), 6)]:
         tgt = O.target(scene)
         d = S.pss_dim(L)
@@ -130,9 +134,10 @@ def test_single_bounce_form_factor(oracle):
 
 GLOSSY = S.material(S.MAT_GLOSSY, (0.7, 0.5, 0.3), roughness=0.15, f0=0.04)
 DIFFUSE = S.material(S.MAT_DIFFUSE, (0.7, 0.5, 0.3))
+METAL = S.conductor((0.2, 1.1, 1.5), (3.0, 2.5, 2.0), roughness=0.5)
 
 
-@pytest.mark.parametrize("mat", [GLOSSY, DIFFUSE], ids=["glossy", "diffuse"])
+@pytest.mark.parametrize("mat", [GLOSSY, DIFFUSE, METAL], ids=["glossy", "diffuse", "conductor"])
 def test_bsdf_sampler_matches_pdf(oracle, mat):
     O = oracle
     n = np.array([0.0, 0.0, 1.0])
@@ -157,8 +162,9 @@ def test_bsdf_sampler_matches_pdf(oracle, mat):
             vals1.append(1.0 / pdf)
             valsc.append(wi[2] / pdf)
         v1, vc = np.array(vals1), np.array(valsc)
-        # the mixture contains the cosine lobe, so pdf > 0 on the whole
-        # hemisphere: E[1/pdf] = 2 pi and E[cos/pdf] = pi exactly
+        # pdf > 0 on the whole upper hemisphere (the cosine lobe of the
+        # mixtures; for the conductor, D(h) > 0 for every half-vector above
+        # the surface): E[1/pdf] = 2 pi and E[cos/pdf] = pi exactly
         assert abs(v1.mean() - 2 * math.pi) < 4 * v1.std() / math.sqrt(cnt)
         assert abs(vc.mean() - math.pi) < 4 * vc.std() / math.sqrt(cnt)
 
@@ -185,6 +191,55 @@ def test_ggx_lobe_white_furnace(oracle):
         # single-scattering energy loss grows with roughness
         assert acc.mean() < prev
         prev = acc.mean()
+
+
+def test_conductor_lobe_matches_ggx_coat_lobe(oracle):
+    """A conductor with a huge extinction k reflects everything (F -> 1),
+    so its single-scattering albedo equals that of the glossy material's
+    specular lobe with F0 = 1 and no base (the same D G2 / (4 cos cos)
+    integral), although the two are sampled differently (one lobe vs a
+    half/half mixture with the cosine lobe)."""
+    O = oracle
+    n = np.array([0.0, 0.0, 1.0])
+    rng = np.random.default_rng(6)
+    for rough, theta in [(0.1, 0.3), (0.4, 1.0)]:
+        metal = S.conductor((1.0, 1.0, 1.0), (1e6, 1e6, 1e6), roughness=rough)
+        coat = S.material(S.MAT_GLOSSY, (0.0, 0.0, 0.0), roughness=rough, f0=1.0)
+        wo = np.array([math.sin(theta), 0.0, math.cos(theta)])
+        est = []
+        for mat in (metal, coat):
+            acc = np.array([(lambda r: r[2][1] if r[0] else 0.0)(O.bsdf_sample(mat, n, wo, *rng.random(2)))
+                            for _ in range(30000)])
+            est.append((acc.mean(), acc.std() / math.sqrt(acc.size)))
+        (m1, s1), (m2, s2) = est
+        assert m1 <= 1.0 + 4 * s1
+        assert abs(m1 - m2) < 4 * math.hypot(s1, s2), (rough, theta, est)
+
+
+def test_fresnel_conductor_closed_forms(oracle):
+    L = oracle.lib()
+    for eta, k in [(0.2, 3.0), (1.1, 2.5), (0.05, 5.0), (2.0, 0.5)]:
+        # normal incidence: ((eta - 1)^2 + k^2) / ((eta + 1)^2 + k^2)
+        ref = ((eta - 1) ** 2 + k * k) / ((eta + 1) ** 2 + k * k)
+        assert abs(L.orc_fresnel_conductor(1.0, eta, k) - ref) < 1e-14
+        # grazing incidence reflects everything
+        assert L.orc_fresnel_conductor(1e-9, eta, k) > 1 - 1e-7
+        # the same equations in real variables (a^2 + b^2 from the complex
+        # index, then R_s and R_p as real ratios), a separate formulation
+        for ci in (0.95, 0.6, 0.25, 0.02):
+            s2 = 1 - ci * ci
+            t0 = eta * eta - k * k - s2
+            ab = math.sqrt(t0 * t0 + 4 * eta * eta * k * k)
+            a = math.sqrt(0.5 * (ab + t0))
+            rs = (ab + ci * ci - 2 * a * ci) / (ab + ci * ci + 2 * a * ci)
+            q = (ci * ci * ab + s2 * s2 - 2 * a * ci * s2) / (ci * ci * ab + s2 * s2 + 2 * a * ci * s2)
+            ref = 0.5 * (rs + rs * q)
+            assert abs(L.orc_fresnel_conductor(ci, eta, k) - ref) < 1e-13, (eta, k, ci)
+    # k = 0 is a dielectric interface: the real Fresnel equations
+    eta = 1.5
+    for ci in (0.9, 0.5, 0.1):
+        ct = math.sqrt(1 - (1 - ci * ci) / eta ** 2)
+        assert abs(L.orc_fresnel_conductor(ci, eta, 0.0) - L.orc_fresnel_dielectric(ci, ct, eta)) < 1e-15
 
 
 def test_fresnel_dielectric_closed_forms(oracle):
