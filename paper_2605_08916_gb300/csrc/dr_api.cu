@@ -32,6 +32,7 @@ struct dr_ctx {
   float4* tris4 = nullptr;
   int n_nodes4 = 0, bvh4_depth = 0, bvh4_stack = 0;
   int bvh_width = 0;  // DR_OPT_BVH_WIDTH (0 automatic)
+  bool conductors = false;  // some material is a conductor (selects the kernels that shade them)
   unsigned long long target_gen = 0;  // bumped by every scene / mixture upload
   // multi-scene batch (target 2): one sub-context per scene owns that
   // scene's BVH and surface data; the kernels see them through d_scenes
@@ -329,6 +330,7 @@ StepArgs step_args(dr_ctx* c) {
   a.tri_tests = c->counters + 3;
   a.err = c->err;
   a.refill = c->tune.refill;
+  a.conductors = c->conductors ? 1 : 0;
   if (c->target == 2) {
     a.scenes = c->d_scenes;
     a.sc = c->d_sc;
@@ -737,6 +739,8 @@ int dr_scene_upload(dr_ctx* c, const float* verts, int32_t nv, const int32_t* tr
   if (ploc_scratch) cudaFree(ploc_scratch);
   if (r != DR_OK) return r;
   c->target = 0;
+  c->conductors = false;
+  for (int i = 0; i < nm; ++i) c->conductors = c->conductors || mats[12 * i] == 4.f;
   c->W = width;
   c->H = height;
   c->nt = nt;
@@ -903,6 +907,8 @@ int dr_scenes_upload_batch(dr_ctx* c, const dr_scene_desc* sd, int32_t n) {
     return r;
   }
   c->target = 2;
+  c->conductors = false;
+  for (dr_ctx* sub : c->subs) c->conductors = c->conductors || sub->conductors;
   c->W = (int)pix;  // the shared accumulator is one row of all scenes' pixels
   c->H = 1;
   c->nt = (int)std::min<long long>(tris, 1ll << 30);

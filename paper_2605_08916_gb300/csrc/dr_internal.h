@@ -128,6 +128,7 @@ struct StepArgs {
   double* p_partial;  // [gridDim.x] init only
   uint32_t* err;
   int refill;  // persistent traversal: refill a warp below this many busy lanes
+  int conductors;  // some material is a conductor: the shading passes that handle them run
   // camera-ray order (null: chain order): wf_begin writes (key, chain) with
   // key = the pixel's Morton code (above it the scene of a batch chain)
   uint2* ray_keys;

@@ -57,7 +57,7 @@ DR_D double warp_sum_f64(double v) {
 }
 
 // Evaluates f, p and (optionally) grad log p through GW.
-template <bool TAPE, bool STATS, class XA, class GW>
+template <bool TAPE, bool STATS, bool COND = true, class XA, class GW>
 DR_D float3 evaluate(const DevScene& S, const DevMixture& M, int target, int L, float eps, const XA& xa, int* pix,
                      float* p_out, bool want_grad, const GW& gw, TraceStack<kStack> st, uint32_t* err,
                      TraceStats* stats, uint32_t* rays) {
@@ -68,16 +68,16 @@ DR_D float3 evaluate(const DevScene& S, const DevMixture& M, int target, int L, 
     return f3(g, g, g);
   }
   Tape<kMaxPathLen> tape;
-  const PathResult r = path_forward<kStack, STATS, TAPE>(S, xa, L, &tape, st, err, stats);
+  const PathResult r = path_forward<kStack, STATS, TAPE, COND>(S, xa, L, &tape, st, err, stats);
   *rays += r.rays;
   *pix = r.pix;
   const float p = lum(r.f) + eps;
   *p_out = p;
-  if (TAPE && want_grad) path_adjoint(S, xa, L, p, LocalTape<kMaxPathLen>{&tape}, r.nseg, gw);
+  if (TAPE && want_grad) path_adjoint<COND>(S, xa, L, p, LocalTape<kMaxPathLen>{&tape}, r.nseg, gw);
   return r.f;
 }
 
-template <int DRIFT, bool STATS>
+template <int DRIFT, bool STATS, bool COND>
 __global__ void __launch_bounds__(kStepThreads) step_kernel(StepArgs a) {
   extern __shared__ int smem[];
   TraceStack<kStack> st{smem + threadIdx.x, (int)blockDim.x};
@@ -104,17 +104,17 @@ __global__ void __launch_bounds__(kStepThreads) step_kernel(StepArgs a) {
     if (DRIFT == kDriftAdjoint && !a.estimate_only && a.target == 0) {
       // forward with tape; kill decision; adjoint only if the chain survives
       Tape<kMaxPathLen> tape;
-      const PathResult r = path_forward<kStack, STATS, true>(a.S, xa, a.L, &tape, st, &err, &stats);
+      const PathResult r = path_forward<kStack, STATS, true, COND>(a.S, xa, a.L, &tape, st, &err, &stats);
       rays += r.rays;
       pix = r.pix;
       f = r.f;
       if (a.plen) a.plen[j] = (uint8_t)r.nseg;
       p = lum(f) + a.eps;
       kill_clock(a.rb, u1, u2, p, a.h, k0_of(a), &killed, &wt);
-      if (!killed) path_adjoint(a.S, xa, a.L, p, LocalTape<kMaxPathLen>{&tape}, r.nseg, GSoA{a.score, a.N, j});
+      if (!killed) path_adjoint<COND>(a.S, xa, a.L, p, LocalTape<kMaxPathLen>{&tape}, r.nseg, GSoA{a.score, a.N, j});
     } else {
-      f = evaluate<false, STATS>(a.S, a.M, a.target, a.L, a.eps, xa, &pix, &p, false, GNone{}, st, &err, &stats,
-                                 &rays);
+      f = evaluate<false, STATS, COND>(a.S, a.M, a.target, a.L, a.eps, xa, &pix, &p, false, GNone{}, st, &err,
+                                       &stats, &rays);
       if (!a.estimate_only) kill_clock(a.rb, u1, u2, p, a.h, k0_of(a), &killed, &wt);
     }
     if (a.estimate_only) {
@@ -324,7 +324,9 @@ __global__ void sum_doubles_kernel(const double* __restrict__ in, int n, double*
 template <int DRIFT, bool STATS>
 void launch_step_t(const StepArgs& a, cudaStream_t s) {
   const unsigned grid = (unsigned)((a.N + kStepThreads - 1) / kStepThreads);
-  step_kernel<DRIFT, STATS><<<grid, kStepThreads, step_smem_bytes(), s>>>(a);
+  // the conductor branches are compiled in only where a scene needs them
+  if (a.conductors) step_kernel<DRIFT, STATS, true><<<grid, kStepThreads, step_smem_bytes(), s>>>(a);
+  else step_kernel<DRIFT, STATS, false><<<grid, kStepThreads, step_smem_bytes(), s>>>(a);
 }
 
 }  // namespace

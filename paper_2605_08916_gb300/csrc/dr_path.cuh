@@ -29,16 +29,21 @@ namespace dr {
 // ---------------------------------------------------------------- records
 struct MatP {
   int type;
+  bool cond;  // a conductor; constant false in code built without conductor support
   float3 albedo, emit;  // conductor: albedo = eta; k at rec[9..11]
   const float* rec;
   float rough, ior, f0;
   bool emissive;
 };
 
+// COND = false: the caller's scene has no conductor, and the conductor
+// branches are compiled out of the kernel.
+template <bool COND = true>
 DR_D MatP load_mat(const float* __restrict__ mats, int id) {
   const float* m = mats + kMatFloats * id;
   MatP r;
   r.type = (int)__ldg(m + 0);
+  r.cond = COND && r.type == kConductor;
   r.albedo = f3(__ldg(m + 1), __ldg(m + 2), __ldg(m + 3));
   r.rough = __ldg(m + 4);
   r.ior = __ldg(m + 5);
@@ -141,7 +146,8 @@ struct GlossyFwd {
   float3 h, hv;
 };
 
-DR_D float spec_prob(const MatP& m) { return m.type == kConductor ? 1.0f : kGlossySpecProb; }
+DR_D float spec_prob(const MatP& m) { return m.cond ? 1.0f : kGlossySpecProb; }
+DR_D float spec_prob_inv(const MatP& m) { return m.cond ? 1.0f : 1.0f / kGlossySpecProb; }
 
 DR_D GlossyFwd glossy_fwd(const MatP& m, float3 n, float3 wo, float3 wi) {
   GlossyFwd g;
@@ -194,7 +200,7 @@ DR_D float fresnel_conductor(float c, float eta, float k, float* dFdc) {
 
 // Per-channel Fresnel of the specular lobe at cos = ih.
 DR_D float3 lobe_fresnel(const MatP& m, float ih) {
-  if (m.type == kConductor) {
+  if (m.cond) {
     // k is read here rather than with the record: it is live only here
     float d;
     return f3(fresnel_conductor(ih, m.albedo.x, __ldg(m.rec + 9), &d),
@@ -209,7 +215,7 @@ DR_D float3 lobe_fresnel(const MatP& m, float ih) {
 // sum_c g_c F_c and sum_c g_c dF_c/d(ih) for the adjoint, one channel at a
 // time (few live registers).
 DR_D void lobe_fresnel_dots(const MatP& m, float ih, float3 g, float* gF, float* gdF) {
-  if (m.type == kConductor) {
+  if (m.cond) {
     float d0, d1, d2;
     const float F0 = fresnel_conductor(ih, m.albedo.x, __ldg(m.rec + 9), &d0);
     float sF = g.x * F0, sd = g.x * d0;
@@ -230,15 +236,14 @@ DR_D void lobe_fresnel_dots(const MatP& m, float ih, float3 g, float* gF, float*
 
 // BSDF value (RGB) and sampling pdf (solid angle) of an opaque material.
 DR_D float3 bsdf_eval(const MatP& m, float3 n, float3 wo, float3 wi, float* pdf) {
-  if (m.type == kGlossy || m.type == kConductor) {
+  if (m.type == kGlossy || m.cond) {
     const GlossyFwd g = glossy_fwd(m, n, wo, wi);
     *pdf = g.pdf;
-    const float3 F = lobe_fresnel(m, g.ih);
     const float DG = g.D * g.G, den = 4.0f * g.co * g.ci;
-    const float3 spec = f3(DG * F.x / den, DG * F.y / den, DG * F.z / den);
-    if (m.type == kConductor) return spec;
+    if (m.cond) return lobe_fresnel(m, g.ih) * (DG / den);
+    const float spec = DG * lobe_fresnel(m, g.ih).x / den;
     const float kd = (1.0f - m.f0) * kInvPi;
-    return m.albedo * kd + spec;
+    return m.albedo * kd + f3(spec, spec, spec);
   }
   *pdf = dot(n, wi) * kInvPi;
   return m.albedo * kInvPi;
@@ -248,7 +253,7 @@ DR_D float3 bsdf_eval(const MatP& m, float3 n, float3 wo, float3 wi, float* pdf)
 // d(n), d(wo), d(wi).
 DR_D void bsdf_eval_bwd(const MatP& m, float3 n, float3 wo, float3 wi, float3 gfs, float gpdf, float3& gn,
                         float3& gwo, float3& gwi) {
-  if (m.type != kGlossy && m.type != kConductor) {
+  if (m.type != kGlossy && !m.cond) {
     gn += wi * (gpdf * kInvPi);
     gwi += n * (gpdf * kInvPi);
     return;
@@ -303,10 +308,9 @@ struct SampleRec {
 DR_D bool opaque_sample(const MatP& m, float3 n, float3 ngf, float3 wo, float u1, float u2, SampleRec& s) {
   float3 t, b;
   onb(n, t, b);
-  const float pspec = spec_prob(m);
-  if ((m.type == kGlossy && u1 < pspec) || m.type == kConductor) {
+  if ((m.type == kGlossy && u1 < kGlossySpecProb) || m.cond) {
     s.lobe = 1;
-    const float v = u1 * (1.0f / pspec);
+    const float v = u1 * spec_prob_inv(m);
     const float a2 = m.rough * m.rough;
     const float den = 1.0f + (a2 - 1.0f) * v;
     const float ch = sqrtf((1.0f - v) / den);
@@ -336,8 +340,8 @@ DR_D void opaque_sample_dir_bwd(const MatP& m, int lobe, float3 n, float3 wo, fl
   onb(n, t, b);
   float3 gt, gb;
   if (lobe == 1) {
-    const float pspec = spec_prob(m);
-    const float v = u1 * (1.0f / pspec);
+    const float pinv = spec_prob_inv(m);
+    const float v = u1 * pinv;
     const float a2 = m.rough * m.rough;
     const float den = 1.0f + (a2 - 1.0f) * v;
     const float ch = sqrtf((1.0f - v) / den);
@@ -360,7 +364,7 @@ DR_D void opaque_sample_dir_bwd(const MatP& m, int lobe, float3 n, float3 wo, fl
     float gv = 0.0f;
     if (sh > 0.0f) gv += gsh * a2 / (2.0f * sh * den2);
     if (ch > 0.0f) gv -= gch * a2 / (2.0f * ch * den2);
-    gu1 = gv * (1.0f / pspec);
+    gu1 = gv * pinv;
     gu2 = gph * 2.0f * kPi;
   } else {
     const float dvdu = m.type == kGlossy ? 1.0f / (1.0f - kGlossySpecProb) : 1.0f;
@@ -539,7 +543,7 @@ DR_D int path_begin(const DevScene& S, const XA& xa, PathState& ps) {
 // direction.  Returns whether the path continues (ps then holds the next
 // ray).  The NEE contribution is added by the caller once the shadow ray
 // is found unoccluded, before the next vertex.
-template <class XA, class TP>
+template <bool COND = true, class XA, class TP>
 DR_D bool path_vertex(const DevScene& S, const XA& xa, int L, int seg, int tri, PathState& ps, const TP& tape,
                       NeeReq& nee) {
   nee.valid = false;
@@ -551,7 +555,7 @@ DR_D bool path_vertex(const DevScene& S, const XA& xa, int L, int seg, int tri, 
   int flags = ps.prev_delta ? kFPrevDelta : 0;
   tape.put(seg - 1, make_float4(ps.o.x, ps.o.y, ps.o.z, ps.ppdf), make_float4(ps.d.x, ps.d.y, ps.d.z, __int_as_float(tri)),
            make_float4(ps.beta.x, ps.beta.y, ps.beta.z, __int_as_float(flags)));
-  const MatP m = load_mat(S.mats, sf.mat);
+  const MatP m = load_mat<COND>(S.mats, sf.mat);
   const float t = dot(sf.v0 - ps.o, sf.N) / dot(ps.d, sf.N);
   const float3 P = ps.o + ps.d * t;
   if (m.emissive) {
@@ -653,7 +657,7 @@ DR_D bool path_vertex(const DevScene& S, const XA& xa, int L, int seg, int tri, 
 // Forward path evaluation in one thread (traversal inline).  XA: functor
 // x(i) -> float.  With TAPE the per-segment record for the adjoint is
 // written to *tape.
-template <int STACK, bool STATS, bool TAPE, int LMAX, class XA>
+template <int STACK, bool STATS, bool TAPE, bool COND = true, int LMAX, class XA>
 DR_D PathResult path_forward(const DevScene& S, const XA& xa, int L, Tape<LMAX>* tape, TraceStack<STACK> st,
                              uint32_t* err, TraceStats* stats) {
   PathResult res;
@@ -667,8 +671,8 @@ DR_D PathResult path_forward(const DevScene& S, const XA& xa, int L, Tape<LMAX>*
     if (tri < 0) break;
     NeeReq nee;
     bool cont;
-    if (TAPE) cont = path_vertex(S, xa, L, seg, tri, ps, LocalTape<LMAX>{tape}, nee);
-    else cont = path_vertex(S, xa, L, seg, tri, ps, NoTape{}, nee);
+    if (TAPE) cont = path_vertex<COND>(S, xa, L, seg, tri, ps, LocalTape<LMAX>{tape}, nee);
+    else cont = path_vertex<COND>(S, xa, L, seg, tri, ps, NoTape{}, nee);
     if (nee.valid) {
       ++res.rays;
       if (!trace_any<STACK, STATS>(S, make_ray(nee.o, nee.wi), nee.tmax, nee.ex0, nee.ex1, st, err, stats)) {
@@ -686,7 +690,7 @@ DR_D PathResult path_forward(const DevScene& S, const XA& xa, int L, Tape<LMAX>*
 // Reverse-mode adjoint of p = lum(f) + eps with respect to x, using the tape
 // of a forward pass with the same x.  GW: functor gw(i, value) receiving
 // d log p / d x_i = (d p / d x_i) / p; every i < d is written exactly once.
-template <class TP, class XA, class GW>
+template <bool COND = true, class TP, class XA, class GW>
 DR_D void path_adjoint(const DevScene& S, const XA& xa, int L, float p, const TP& tape, int nseg, const GW& gw) {
   const float inv_p = 1.0f / p;
   const float3 lw = lum_weights();
@@ -706,7 +710,7 @@ DR_D void path_adjoint(const DevScene& S, const XA& xa, int L, float p, const TP
     const int flags = __float_as_int(tc.w);
     const bool prev_delta = flags & kFPrevDelta;
     const Surf sf = load_surf(S, tri);
-    const MatP m = load_mat(S.mats, sf.mat);
+    const MatP m = load_mat<COND>(S.mats, sf.mat);
     const float dn = dot(d, sf.N);
     const float t = dot(sf.v0 - o, sf.N) / dn;
     const float3 P = o + d * t;

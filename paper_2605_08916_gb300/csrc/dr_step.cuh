@@ -45,20 +45,31 @@ DR_D void evolve_x(const StepArgs& a, const Rng& rng, uint32_t step, unsigned lo
     return;
   }
   const float c2 = 0.5f * a.stddev * a.stddev;
+  float* __restrict__ X = a.x;
+  const float* __restrict__ Sc = a.score;
+  const size_t N = a.N;
   // one Philox block serves two coordinate pairs: pair q uses words
-  // (q & 1) * 2 and (q & 1) * 2 + 1 of block q >> 1
+  // (q & 1) * 2 and (q & 1) * 2 + 1 of block q >> 1.  The four coordinates
+  // and scores of a block are loaded before any is stored, so each block
+  // costs one memory round trip rather than two.
   for (int blk = 0; 2 * blk < d / 2; ++blk) {
+    const bool two = 2 * blk + 1 < d / 2;
+    const size_t i0 = (size_t)(4 * blk) * N + j;
+    float xv[4], sv[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      xv[e] = e < 2 || two ? X[i0 + e * N] : 0.0f;
+      sv[e] = e < 2 || two ? Sc[i0 + e * N] : 0.0f;
+    }
     const U4 r = rng.draw(step, cj, (uint32_t)blk, kNormal);
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      const int q = 2 * blk + h;
-      if (q >= d / 2) break;
+      if (h && !two) break;
       const float ua = u01(h ? r.c : r.a), ub = u01(h ? r.d : r.b);
       const float2 xi = box_muller(ua, ub);
-      const size_t i0 = (size_t)(2 * q) * a.N + j, i1 = (size_t)(2 * q + 1) * a.N + j;
-      const float s0 = a.score[i0], s1 = a.score[i1];
-      a.x[i0] = wrap01(a.x[i0] + c2 * s0 + a.gamma_tilde * s1 + a.stddev * xi.x);
-      a.x[i1] = wrap01(a.x[i1] + c2 * s1 - a.gamma_tilde * s0 + a.stddev * xi.y);
+      const float s0 = sv[2 * h], s1 = sv[2 * h + 1];
+      X[i0 + (2 * h) * N] = wrap01(xv[2 * h] + c2 * s0 + a.gamma_tilde * s1 + a.stddev * xi.x);
+      X[i0 + (2 * h + 1) * N] = wrap01(xv[2 * h + 1] + c2 * s1 - a.gamma_tilde * s0 + a.stddev * xi.y);
     }
   }
 }

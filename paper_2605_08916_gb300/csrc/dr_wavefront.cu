@@ -310,7 +310,7 @@ __global__ void __launch_bounds__(kWfThreads, kWfTrace4MinBlocks) wf_traverse(St
   if (err) atomicOr(a.err, err);
 }
 
-template <bool BATCH>
+template <bool BATCH, bool COND>
 __global__ void __launch_bounds__(kWfThreads, kWfShadeMinBlocks) wf_shade(StepArgs a, WfBuffers w, int k) {
   const uint32_t n = w.counts[k];
   const uint32_t* q = k == 1 && !a.ray_keys ? nullptr : w.queue[k & 1];
@@ -334,7 +334,7 @@ __global__ void __launch_bounds__(kWfThreads, kWfShadeMinBlocks) wf_shade(StepAr
         PathState ps;
         int pix;
         load_slot(w.slot, j, ps, pix);
-        cont = path_vertex(scene_of<BATCH>(a, v.sid), XSoA{a.x, a.N, j}, L, k, tri, ps, GlobalTape{w.tape, a.N, j},
+        cont = path_vertex<COND>(scene_of<BATCH>(a, v.sid), XSoA{a.x, a.N, j}, L, k, tri, ps, GlobalTape{w.tape, a.N, j},
                            nee);
         store_slot(w.slot, j, ps, pix);
       }
@@ -367,7 +367,7 @@ __global__ void __launch_bounds__(kWfThreads, kWfShadeMinBlocks) wf_shade(StepAr
 // bounce-by-bounce passes, so the results are identical.
 constexpr int kWfTailMinBlocks = 4;
 
-template <bool STATS, bool BATCH>
+template <bool STATS, bool BATCH, bool COND>
 __global__ void __launch_bounds__(kWfThreads, kWfTailMinBlocks) wf_tail(StepArgs a, WfBuffers w, int k0) {
   extern __shared__ int smem[];
   TraceStack<kWfStack> st{smem + threadIdx.x, (int)blockDim.x};
@@ -421,7 +421,7 @@ __global__ void __launch_bounds__(kWfThreads, kWfTailMinBlocks) wf_tail(StepArgs
         if (hit >= 0) {
           NeeReq nee;
           nee.valid = false;
-          const bool cont = path_vertex(S, XSoA{a.x, a.N, j}, L, k, hit, ps, GlobalTape{w.tape, a.N, j}, nee);
+          const bool cont = path_vertex<COND>(S, XSoA{a.x, a.N, j}, L, k, hit, ps, GlobalTape{w.tape, a.N, j}, nee);
           next = cont && k < L;
           if (nee.valid) {
             r = make_ray(nee.o, nee.wi);
@@ -596,7 +596,7 @@ __global__ void __launch_bounds__(kWfThreads) wf_finish(StepArgs a, WfBuffers w,
   if (err) atomicOr(a.err, err);
 }
 
-template <bool BATCH>
+template <bool BATCH, bool COND>
 __global__ void __launch_bounds__(kWfThreads, 4) wf_adjoint(StepArgs a, WfBuffers w) {
   // the queue is the concatenation of the path-length buckets, longest first
   __shared__ uint32_t off[kMaxPathLen + 2];
@@ -623,7 +623,7 @@ __global__ void __launch_bounds__(kWfThreads, 4) wf_adjoint(StepArgs a, WfBuffer
     load_slot(w.slot, j, ps, pix);
     const float p = lum(ps.f) + a.eps;
     const ChainView v = chain_view<BATCH>(a, j);
-    path_adjoint(scene_of<BATCH>(a, v.sid), XSoA{a.x, a.N, j}, v.L, p, GlobalTape{w.tape, a.N, j}, ps.nseg,
+    path_adjoint<COND>(scene_of<BATCH>(a, v.sid), XSoA{a.x, a.N, j}, v.L, p, GlobalTape{w.tape, a.N, j}, ps.nseg,
                  GSoA{a.score, a.N, j});
   }
 }
@@ -645,18 +645,18 @@ int traverse_blocks_per_sm(size_t smem) {
   return cached;
 }
 
-template <bool BATCH>
+template <bool BATCH, bool COND>
 int tail_blocks_per_sm(size_t smem) {
   static int cached = 0;
   if (cached == 0) {
     int b0 = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b0, wf_tail<false, BATCH>, kWfThreads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b0, wf_tail<false, BATCH, COND>, kWfThreads, smem);
     cached = std::max(1, b0);
   }
   return cached;
 }
 
-template <bool BATCH>
+template <bool BATCH, bool COND>
 int launch_wf(const StepArgs& a, const WfBuffers& w, bool stats, int n_sm, const WfTuning& tune,
               const PhaseHook& hook, cudaStream_t s, WfMode mode, float* p_out, const RayOrder& order) {
   const int max_blocks = n_sm * 16;
@@ -701,15 +701,16 @@ int launch_wf(const StepArgs& a, const WfBuffers& w, bool stats, int n_sm, const
       if (k <= a.L && k == tune.tail_bounce) {
         // the rest of every path in one persistent pass
         hook(kPhTail, true, k);
-        if (stats) wf_tail<true, BATCH><<<n_sm * tail_blocks_per_sm<BATCH>(smem), kWfThreads, smem, s>>>(a, w, k);
-        else wf_tail<false, BATCH><<<n_sm * tail_blocks_per_sm<BATCH>(smem), kWfThreads, smem, s>>>(a, w, k);
+        const unsigned gt = (unsigned)(n_sm * tail_blocks_per_sm<BATCH, COND>(smem));
+        if (stats) wf_tail<true, BATCH, COND><<<gt, kWfThreads, smem, s>>>(a, w, k);
+        else wf_tail<false, BATCH, COND><<<gt, kWfThreads, smem, s>>>(a, w, k);
         hook(kPhTail, false, k);
         launches += 1;
         break;
       }
       if (k <= a.L) {
         hook(kPhShade, true, k);
-        wf_shade<BATCH><<<g, kWfThreads, 0, s>>>(a, w, k);
+        wf_shade<BATCH, COND><<<g, kWfThreads, 0, s>>>(a, w, k);
         hook(kPhShade, false, k);
         launches += 1;
       }
@@ -721,7 +722,7 @@ int launch_wf(const StepArgs& a, const WfBuffers& w, bool stats, int n_sm, const
       else wf_trace<false><<<g, kWfThreads, smem, s>>>(a, w, k);
       hook(kPhTrace, false, k);
       hook(kPhShade, true, k);
-      wf_shade<false><<<g, kWfThreads, 0, s>>>(a, w, k);
+      wf_shade<false, COND><<<g, kWfThreads, 0, s>>>(a, w, k);
       hook(kPhShade, false, k);
       hook(kPhShadow, true, k);
       if (stats) wf_shadow<true><<<g, kWfThreads, smem, s>>>(a, w, k);
@@ -734,7 +735,7 @@ int launch_wf(const StepArgs& a, const WfBuffers& w, bool stats, int n_sm, const
   wf_finish<BATCH><<<g, kWfThreads, 0, s>>>(a, w, mode, p_out);
   hook(kPhFinish, false);
   hook(kPhAdjoint, true);
-  wf_adjoint<BATCH><<<g, kWfThreads, 0, s>>>(a, w);
+  wf_adjoint<BATCH, COND><<<g, kWfThreads, 0, s>>>(a, w);
   hook(kPhAdjoint, false);
   return launches + 2;
 }
@@ -767,8 +768,13 @@ int launch_wavefront_step(const StepArgs& a, const WfBuffers& w, bool stats, int
   if (a.N == 0) return 0;
   StepArgs b = a;
   b.ray_keys = order.keys;
-  return a.scenes ? launch_wf<true>(b, w, stats, n_sm, tune, hook, s, mode, p_out, order)
-                  : launch_wf<false>(b, w, stats, n_sm, tune, hook, s, mode, p_out, order);
+  // kernels with the conductor branches run only for scenes that have
+  // conductors (the branches cost registers and code in every kernel)
+  if (a.conductors)
+    return a.scenes ? launch_wf<true, true>(b, w, stats, n_sm, tune, hook, s, mode, p_out, order)
+                    : launch_wf<false, true>(b, w, stats, n_sm, tune, hook, s, mode, p_out, order);
+  return a.scenes ? launch_wf<true, false>(b, w, stats, n_sm, tune, hook, s, mode, p_out, order)
+                  : launch_wf<false, false>(b, w, stats, n_sm, tune, hook, s, mode, p_out, order);
 }
 
 }  // namespace dr
