@@ -257,7 +257,8 @@ def run_ours(args, wl, rank, world, local):
     t_init = time.perf_counter() - t_init
     log(f"init (evaluation + p_lambda estimate + clock) {t_init * 1e3:.1f} ms")
     bvh4 = r.bvh4_info() if args.bvh_width != 2 else None
-    log(f"uploaded + init {N} chains; bvh {r.bvh_info()}; 4-wide {bvh4}")
+    bvh8 = r.bvh8_info() if args.bvh_width == 8 else None
+    log(f"uploaded + init {N} chains; bvh {r.bvh_info()}; 4-wide {bvh4}; 8-wide {bvh8}")
     # traversal statistics (separate kernel instantiation, untimed)
     r.set_stats(True)
     r.step(2)
@@ -270,7 +271,8 @@ def run_ours(args, wl, rank, world, local):
     # width) walks the binary one
     wf_expected = wl["drift"] == "adjoint" and (args.wavefront == 1 or (args.wavefront == -1 and N >= 1 << 17))
     wide = bool(bvh4)
-    node_bytes = 112 if wide else 64
+    # the 8-wide compressed BVH serves the bounce-by-bounce passes only
+    node_bytes = 80 if (bvh8 and wf_expected) else 112 if wide else 64
     trav_bytes = (ts["node_visits"] * node_bytes + ts["tri_tests"] * 48) / chain_steps_stats
     state_bytes = 4 * d * 4 + 1 + 1 + 4 + 16   # x and score read+write, killed r+w, logp, record
     log(f"stats pass: {ts}")
@@ -285,7 +287,8 @@ def run_ours(args, wl, rank, world, local):
     wavefront = prof["trace"][1] > 0
     assert wavefront == wf_expected, "execution mode differs from the one the roofline bytes assume"
     if wavefront:
-        k_name = ("wf_traverse (4-wide BVH traversal passes)" if wide
+        k_name = ("wf_traverse (8-wide compressed BVH traversal passes)" if bvh8
+                  else "wf_traverse (4-wide BVH traversal passes)" if wide
                   else "wf_trace + wf_shadow (binary BVH traversal passes)")
         k_ms = (prof["trace"][0] + prof["shadow"][0]) / prof_steps
         k_bytes = trav_bytes
@@ -515,6 +518,8 @@ def run_batched(args, rank, world, local):
     stream = torch.cuda.Stream(device=dev)
     r = R.Renderer(local, stream)
     r.set_option("ray_order", args.ray_order)
+    if args.bvh_width == 8:
+        r.set_option("bvh_width", 8)
     if args.tail_bounce is not None:
         r.set_option("tail_bounce", args.tail_bounce)
     r.upload_scenes(items)
@@ -529,7 +534,7 @@ def run_batched(args, rank, world, local):
     r.step(2)
     ts = r.traversal_stats()
     r.set_stats(False)
-    trav_bytes = (ts["node_visits"] * 112 + ts["tri_tests"] * 48) / (2 * N)
+    trav_bytes = (ts["node_visits"] * (80 if args.bvh_width == 8 else 112) + ts["tri_tests"] * 48) / (2 * N)
     r.set_option("profile", 1)
     r.profile()
     prof_steps = 4
@@ -636,7 +641,7 @@ def main():
                     help="run the bounces from this one on as one persistent pass (0 off; default: library's choice)")
     ap.add_argument("--ray-order", type=int, default=-1, choices=[-1, 0, 1],
                     help="sort camera rays by pixel before the first traversal (-1: by triangle count)")
-    ap.add_argument("--bvh-width", type=int, default=0, choices=[0, 2, 4],
+    ap.add_argument("--bvh-width", type=int, default=0, choices=[0, 2, 4, 8],
                     help="BVH the rays traverse: 4-wide (0, the default, or 4) or binary (2)")
     ap.add_argument("--work-order", type=int, default=0, choices=[0, 1],
                     help="fused kernel only: order chains by expected path cost (default 0)")

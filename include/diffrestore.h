@@ -277,6 +277,20 @@ int dr_bvh_info(dr_ctx* ctx, int32_t* n_nodes, int32_t* n_tris, int32_t* max_dep
  * the kernels hold; rays then use the binary BVH). */
 int dr_bvh4_info(dr_ctx* ctx, int32_t* n_nodes, int32_t* max_depth, int32_t* stack_need);
 
+/* The 8-wide compressed BVH of the uploaded scene, built at upload when
+ * DR_OPT_BVH_WIDTH is 8: the binary tree collapsed with the same leaf rule
+ * into nodes of up to 8 children, numbered breadth first (a node's inner
+ * children consecutive, its leaf triangles consecutive).  Node: 80 B = the
+ * node box origin (3 floats), three signed 8-bit exponents and the
+ * inner-child mask, the first inner child and first triangle, 8 leaf
+ * descriptors, and per child and plane an 8-bit offset (the child box is
+ * widened to the 8-bit grid, never narrowed).  Children take slots by the
+ * ray-octant heuristic (a ray visits slot k ^ octant k-th).  HOST outputs
+ * (each may be NULL): node count and depth (root = 1).  Errors: STATE (no
+ * scene, or none was built: width 8 not set before the upload, fewer than
+ * 2 triangles, or a tree deeper than the traversal stack holds). */
+int dr_bvh8_info(dr_ctx* ctx, int32_t* n_nodes, int32_t* max_depth);
+
 /* Number of kernels this context has launched since creation (a host-side
  * count kept at every launch site; HOST output). */
 int dr_get_launch_count(dr_ctx* ctx, uint64_t* launches);
@@ -326,8 +340,11 @@ int dr_pt_render(dr_ctx* ctx, int32_t max_path_len, uint32_t spp, uint64_t seed,
  *   DR_OPT_BVH_WIDTH   4: rays traverse the 4-wide BVH collapsed from the
  *                      binary one at scene upload (when it was built, see
  *                      dr_bvh4_info); 2: the binary BVH; 0 (default): the
- *                      4-wide one.  Both return the same closest hit (ties:
- *                      smaller id).
+ *                      4-wide one; 8: set before dr_scene_upload (or the
+ *                      batch upload), also builds the 8-wide compressed BVH
+ *                      (dr_bvh8_info), which the bounce-by-bounce passes
+ *                      then walk (the fused kernel keeps the 4-wide one).
+ *                      All return the same closest hit (ties: smaller id).
  * Errors: INVALID_ARG (unknown option or value). */
 enum { DR_OPT_WORK_ORDER = 1, DR_OPT_WAVEFRONT = 2, DR_OPT_PROFILE = 3, DR_OPT_BVH_WIDTH = 4,
        DR_OPT_TRAVERSE_BLOCKS = 5, DR_OPT_REFILL = 6, DR_OPT_RAY_ORDER = 7, DR_OPT_TAIL_BOUNCE = 8 };

@@ -31,6 +31,10 @@ struct dr_ctx {
   float4* nodes4 = nullptr;  // 4-wide collapse of `nodes` (null when not built)
   float4* tris4 = nullptr;
   int n_nodes4 = 0, bvh4_depth = 0, bvh4_stack = 0;
+  uint4* nodes8 = nullptr;  // 8-wide compressed collapse (built when bvh_width is 8 at upload)
+  float4* tris8 = nullptr;
+  int n_nodes8 = 0, bvh8_depth = 0;
+  bool batch_bvh8 = false;  // every scene of the batch has an 8-wide BVH
   int bvh_width = 0;  // DR_OPT_BVH_WIDTH (0 automatic)
   bool conductors = false;  // some material is a conductor (selects the kernels that shade them)
   unsigned long long target_gen = 0;  // bumped by every scene / mixture upload
@@ -242,6 +246,10 @@ DevScene dev_scene(const dr_ctx* c) {
   S.nodes4 = wide ? c->nodes4 : nullptr;
   S.tris4 = wide ? c->tris4 : nullptr;
   S.n_nodes4 = wide ? c->n_nodes4 : 0;
+  const bool w8 = wide && c->nodes8 != nullptr && c->bvh_width == 8;
+  S.nodes8 = w8 ? c->nodes8 : nullptr;
+  S.tris8 = w8 ? c->tris8 : nullptr;
+  S.n_nodes8 = w8 ? c->n_nodes8 : 0;
   S.W = c->W;
   S.H = c->H;
   S.tmin = c->tmin;
@@ -331,6 +339,7 @@ StepArgs step_args(dr_ctx* c) {
   a.err = c->err;
   a.refill = c->tune.refill;
   a.conductors = c->conductors ? 1 : 0;
+  a.bvh8 = c->target == 2 ? (c->batch_bvh8 && c->bvh_width == 8 ? 1 : 0) : (a.S.nodes8 != nullptr ? 1 : 0);
   if (c->target == 2) {
     a.scenes = c->d_scenes;
     a.sc = c->d_sc;
@@ -535,6 +544,46 @@ int build_bvh4(dr_ctx* c, int* depth2) {
   return r;
 }
 
+// The 8-wide compressed collapse (when the context asks for width 8 and the
+// 4-wide one was built); kept off when its traversal could need more stack
+// entries (two ints each) than the kernels hold.
+int build_bvh8(dr_ctx* c) {
+  dfree(&c->nodes8);
+  dfree(&c->tris8);
+  c->n_nodes8 = c->bvh8_depth = 0;
+  if (c->bvh_width != 8 || !c->nodes4 || c->nt < 2) return DR_OK;
+  const int nn = std::max(1, c->n_nodes);
+  void* scratch = nullptr;
+  if (cudaMalloc(&scratch, bvh8_scratch_bytes(nn, c->nt)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(DR_ERR_OOM, "dr_scene_upload: 8-wide BVH scratch");
+  }
+  Bvh8Plan plan{};
+  int r = DR_OK;
+  const int n8 = bvh8_plan(c->nodes, nn, c->nt, scratch, &plan, c->stream);
+  c->launches += plan.launches;
+  if (n8 < 1) {
+    r = fail(DR_ERR_DEVICE_CHECK, "dr_scene_upload: 8-wide BVH collapse failed");
+  } else if (plan.depth <= kTraversalStack / 2) {
+    r = dalloc(&c->nodes8, (size_t)kNode8U4 * n8);
+    if (r == DR_OK) r = dalloc(&c->tris8, (size_t)kTriF4 * c->nt);
+    if (r == DR_OK && bvh8_emit(c->nodes, c->tris, nn, c->nt, scratch, n8, c->nodes8, c->tris8, c->stream) < 0)
+      r = fail(DR_ERR_DEVICE_CHECK, "dr_scene_upload: 8-wide BVH emission failed");
+    c->launches += 2;
+    if (r == DR_OK) {
+      c->n_nodes8 = n8;
+      c->bvh8_depth = plan.depth;
+    } else {
+      dfree(&c->nodes8);
+      dfree(&c->tris8);
+    }
+  }
+  cudaFree(scratch);
+  const cudaError_t e = cudaGetLastError();
+  if (r == DR_OK && e != cudaSuccess) r = fail(DR_ERR_CUDA, std::string("dr_scene_upload: ") + cudaGetErrorString(e));
+  return r;
+}
+
 }  // namespace
 
 extern "C" {
@@ -576,6 +625,7 @@ int dr_destroy(dr_ctx* c) {
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
   dfree(&c->nodes4); dfree(&c->tris4);
+  dfree(&c->nodes8); dfree(&c->tris8);
   dfree(&c->nodes); dfree(&c->tris); dfree(&c->surf); dfree(&c->lights); dfree(&c->nrm); dfree(&c->mats);
   dfree(&c->mw); dfree(&c->mmu); dfree(&c->msig);
   dfree(&c->x); dfree(&c->score); dfree(&c->logp); dfree(&c->killed);
@@ -751,6 +801,7 @@ int dr_scene_upload(dr_ctx* c, const float* verts, int32_t nv, const int32_t* tr
   // traversal stack can hold
   int depth = 1;
   r = build_bvh4(c, &depth);
+  if (r == DR_OK) r = build_bvh8(c);
   if (r == DR_OK && depth - 1 > kTraversalStack)
     r = fail(DR_ERR_DEVICE_CHECK, "dr_scene_upload: BVH depth " + std::to_string(depth) +
                                       " exceeds the traversal stack (" + std::to_string(kTraversalStack + 1) + ")");
@@ -869,7 +920,7 @@ int dr_scenes_upload_batch(dr_ctx* c, const dr_scene_desc* sd, int32_t n) {
     }
     sub->builder = c->builder;
     sub->ploc_radius = c->ploc_radius;
-    sub->bvh_width = 4;
+    sub->bvh_width = c->bvh_width == 8 ? 8 : 4;
     c->subs.push_back(sub);
     r = dr_scene_upload(sub, q.verts, q.nv, q.tris, q.normals, q.nt, q.tri_mat, q.mats, q.nm, q.camera, q.width,
                         q.height);
@@ -908,7 +959,11 @@ int dr_scenes_upload_batch(dr_ctx* c, const dr_scene_desc* sd, int32_t n) {
   }
   c->target = 2;
   c->conductors = false;
-  for (dr_ctx* sub : c->subs) c->conductors = c->conductors || sub->conductors;
+  c->batch_bvh8 = !c->subs.empty();
+  for (dr_ctx* sub : c->subs) {
+    c->conductors = c->conductors || sub->conductors;
+    c->batch_bvh8 = c->batch_bvh8 && sub->nodes8 != nullptr;
+  }
   c->W = (int)pix;  // the shared accumulator is one row of all scenes' pixels
   c->H = 1;
   c->nt = (int)std::min<long long>(tris, 1ll << 30);
@@ -1416,7 +1471,7 @@ std::vector<unsigned long long> frame_key(const dr_ctx* c, uint32_t n_steps) {
   std::vector<unsigned long long> k = {n_steps, c->N, (unsigned long long)c->d, (unsigned long long)c->target,
                                        P(c->x), P(c->score), P(c->killed), P(c->logp), P(c->plen), P(c->rec),
                                        P(c->rec_alt), P(c->sort_scratch), P(c->accum), P(c->wf_mem), P(c->nodes),
-                                       P(c->nodes4), (unsigned long long)c->bvh_width, P(c->tris), P(c->surf), P(c->mats), P(c->lights), P(c->nrm), P(c->mw),
+                                       P(c->nodes4), P(c->nodes8), (unsigned long long)c->bvh_width, P(c->tris), P(c->surf), P(c->mats), P(c->lights), P(c->nrm), P(c->mw),
                                        c->rec_cap, (unsigned long long)c->wavefront,
                                        (unsigned long long)c->work_order, (unsigned long long)c->stats,
                                        (unsigned long long)c->nt, (unsigned long long)c->n_lights, P(c->stream),
@@ -1584,8 +1639,8 @@ int dr_set_option(dr_ctx* c, int32_t option, int32_t value) {
       c->ray_order = value;
       return DR_OK;
     case DR_OPT_BVH_WIDTH:
-      if (value != 0 && value != 2 && value != 4)
-        return fail(DR_ERR_INVALID_ARG, "dr_set_option: BVH width is 0, 2 or 4");
+      if (value != 0 && value != 2 && value != 4 && value != 8)
+        return fail(DR_ERR_INVALID_ARG, "dr_set_option: BVH width is 0, 2, 4 or 8");
       c->bvh_width = value;
       return DR_OK;
     default:
@@ -1625,6 +1680,15 @@ int dr_bvh4_info(dr_ctx* c, int32_t* n_nodes, int32_t* max_depth, int32_t* stack
   if (n_nodes) *n_nodes = c->n_nodes4;
   if (max_depth) *max_depth = c->bvh4_depth;
   if (stack_need) *stack_need = c->bvh4_stack;
+  return DR_OK;
+}
+
+int dr_bvh8_info(dr_ctx* c, int32_t* n_nodes, int32_t* max_depth) {
+  if (!c) return fail(DR_ERR_INVALID_ARG, "dr_bvh8_info: NULL ctx");
+  if (c->target != 0) return fail(DR_ERR_STATE, "dr_bvh8_info: no scene");
+  if (!c->nodes8) return fail(DR_ERR_STATE, "dr_bvh8_info: the scene has no 8-wide BVH");
+  if (n_nodes) *n_nodes = c->n_nodes8;
+  if (max_depth) *max_depth = c->bvh8_depth;
   return DR_OK;
 }
 

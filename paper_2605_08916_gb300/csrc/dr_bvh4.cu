@@ -24,7 +24,13 @@
 //                become 4-wide nodes, their depth and stack need
 //   scan         4-wide node slots in binary-node order
 //   emit         the 4-wide nodes and the re-laid triangles
+//
+// The 8-wide compressed collapse shares the first four passes and the leaf
+// decision, then numbers its nodes breadth first so that each node's inner
+// children are consecutive (per level: count, scan, place), lays out each
+// node's leaf triangles consecutively, and emits quantised nodes.
 #include <algorithm>
+#include <cmath>
 
 #include "dr_internal.h"
 
@@ -230,12 +236,13 @@ __global__ void first_kernel(const float4* __restrict__ n2, int nn, const int* p
 
 DR_D bool leaf_ref(const Kid& k, const uint8_t* as_leaf) { return k.code < 0 || as_leaf[k.code]; }
 
-// greedy widening of binary node n to up to four children
-DR_D int expand(const float4* __restrict__ n2, int n, const uint8_t* as_leaf, Kid kids[4]) {
+// greedy widening of binary node n to up to W children
+template <int W = 4>
+DR_D int expand(const float4* __restrict__ n2, int n, const uint8_t* as_leaf, Kid kids[W]) {
   kids[0] = kid_of(n2, n, 0);
   kids[1] = kid_of(n2, n, 1);
   int nk = 2;
-  while (nk < 4) {
+  while (nk < W) {
     int best = -1;
     float ba = -1.0f;
     for (int i = 0; i < nk; ++i) {
@@ -277,13 +284,11 @@ __global__ void mark_kernel(const float4* __restrict__ n2, const uint8_t* as_lea
   }
 }
 
-__global__ void emit_kernel(const float4* __restrict__ n2, const float4* __restrict__ t2, int nn, int nt,
-                            const uint8_t* as_leaf, const int* cnt, const int* first, const uint32_t* is4,
-                            const uint32_t* slot, float4* __restrict__ n4, float4* __restrict__ t4, uint32_t* err) {
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= nn) return;
+// copies the triangles of binary node n's leaf links to their depth-first
+// place in t4
+DR_D void relayout_links(const float4* __restrict__ n2, const float4* __restrict__ t2, int n, int nt, const int* cnt,
+                         const int* first, float4* __restrict__ t4, uint32_t* err) {
   const float4 dn = n2[4 * n + 3];
-  // triangles of this node's binary leaf links, to their depth-first place
   for (int k = 0; k < 2; ++k) {
     const int code = __float_as_int(k == 0 ? dn.x : dn.y);
     if (code >= 0) continue;
@@ -296,6 +301,28 @@ __global__ void emit_kernel(const float4* __restrict__ n2, const float4* __restr
     for (int i = 0; i < m; ++i)
       for (int q = 0; q < kTriF4; ++q) t4[(size_t)kTriF4 * (pos + i) + q] = t2[(size_t)kTriF4 * (src + i) + q];
   }
+}
+
+// depth-first position and count of the triangles of a leaf reference
+DR_D void leaf_range(const float4* __restrict__ n2, const Kid& c, const int* cnt, const int* first, int* pos,
+                     int* count) {
+  if (c.code >= 0) {
+    *pos = first[c.code];
+    *count = cnt[c.code];
+  } else {
+    const float4 d = n2[4 * c.parent + 3];
+    *pos = first[c.parent] + (c.side == 1 ? count_of(__float_as_int(d.x), cnt) : 0);
+    *count = leaf_count(c.code);
+  }
+}
+
+__global__ void emit_kernel(const float4* __restrict__ n2, const float4* __restrict__ t2, int nn, int nt,
+                            const uint8_t* as_leaf, const int* cnt, const int* first, const uint32_t* is4,
+                            const uint32_t* slot, float4* __restrict__ n4, float4* __restrict__ t4, uint32_t* err) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= nn) return;
+  // triangles of this node's binary leaf links, to their depth-first place
+  relayout_links(n2, t2, n, nt, cnt, first, t4, err);
   if (!is4[n]) return;
   Kid kids[4];
   const int nk = expand(n2, n, as_leaf, kids);
@@ -307,12 +334,10 @@ __global__ void emit_kernel(const float4* __restrict__ n2, const float4* __restr
     hi[0][k] = c.hi.x; hi[1][k] = c.hi.y; hi[2][k] = c.hi.z;
     if (!leaf_ref(c, as_leaf)) {
       links[k] = (int)slot[c.code];
-    } else if (c.code >= 0) {
-      links[k] = leaf_code(first[c.code], cnt[c.code]);
     } else {
-      const float4 d = n2[4 * c.parent + 3];
-      const int pos = first[c.parent] + (c.side == 1 ? count_of(__float_as_int(d.x), cnt) : 0);
-      links[k] = leaf_code(pos, leaf_count(c.code));
+      int pos, m;
+      leaf_range(n2, c, cnt, first, &pos, &m);
+      links[k] = leaf_code(pos, m);
     }
   }
   float4* o = n4 + (size_t)kNode4F4 * slot[n];
@@ -326,17 +351,191 @@ __global__ void emit_kernel(const float4* __restrict__ n2, const float4* __restr
                      __int_as_float(links[3]));
 }
 
+// ---------------------------------------------------------------- 8-wide
+// Slots of up to eight children by the octant heuristic: slot s is visited
+// first by rays of octant s, so it goes to the child nearest along that
+// octant's diagonal direction (smallest projection of its centre offset);
+// pairs are assigned greedily, globally smallest projection first.
+DR_D void assign_slots(const Kid* kids, int nk, int slot_of[8]) {
+  float3 lo = kids[0].lo, hi = kids[0].hi;
+  for (int k = 1; k < nk; ++k) {
+    lo = f3(fminf(lo.x, kids[k].lo.x), fminf(lo.y, kids[k].lo.y), fminf(lo.z, kids[k].lo.z));
+    hi = f3(fmaxf(hi.x, kids[k].hi.x), fmaxf(hi.y, kids[k].hi.y), fmaxf(hi.z, kids[k].hi.z));
+  }
+  const float3 c = (lo + hi) * 0.5f;
+  uint32_t used_k = 0, used_s = 0;
+  for (int round = 0; round < nk; ++round) {
+    float best = INFINITY;
+    int bk = -1, bs = -1;
+    for (int k = 0; k < nk; ++k) {
+      if (used_k >> k & 1u) continue;
+      const float3 v = (kids[k].lo + kids[k].hi) * 0.5f - c;
+      for (int sl = 0; sl < 8; ++sl) {
+        if (used_s >> sl & 1u) continue;
+        const float cost = (sl & 1 ? -v.x : v.x) + (sl & 2 ? -v.y : v.y) + (sl & 4 ? -v.z : v.z);
+        if (bk < 0 || cost < best) {
+          best = cost;
+          bk = k;
+          bs = sl;
+        }
+      }
+    }
+    slot_of[bk] = bs;
+    used_k |= 1u << bk;
+    used_s |= 1u << bs;
+  }
+}
+
+// child index per slot (-1: empty)
+DR_D void kids_by_slot(const Kid* kids, int nk, int by_slot[8]) {
+  int slot_of[8];
+  assign_slots(kids, nk, slot_of);
+  for (int sl = 0; sl < 8; ++sl) by_slot[sl] = -1;
+  for (int k = 0; k < nk; ++k) by_slot[slot_of[k]] = k;
+}
+
+// level pass 1: inner children and leaf triangles of each node of the level
+__global__ void count8_kernel(const float4* __restrict__ n2, const uint8_t* as_leaf, const int* cnt, const int* first,
+                              const uint32_t* q_in, uint32_t n_in, uint32_t base_cur, uint32_t* n_inner,
+                              uint32_t* tri_cnt, uint32_t* err) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_in) return;
+  Kid kids[8];
+  const int nk = expand<8>(n2, (int)q_in[i], as_leaf, kids);
+  uint32_t inner = 0, tris = 0;
+  for (int k = 0; k < nk; ++k) {
+    if (!leaf_ref(kids[k], as_leaf)) {
+      ++inner;
+    } else {
+      int pos, m;
+      leaf_range(n2, kids[k], cnt, first, &pos, &m);
+      if (m < 1 || m > kBvh4MaxLeaf) atomicOr(err, kErrBadIndex);
+      tris += (uint32_t)m;
+    }
+  }
+  n_inner[i] = inner;
+  tri_cnt[base_cur + i] = tris;
+}
+
+// level pass 2: node numbers (breadth first; a node's inner children
+// consecutive, in slot order) and the next level's queue
+__global__ void place8_kernel(const float4* __restrict__ n2, const uint8_t* as_leaf, const uint32_t* q_in,
+                              uint32_t n_in, const uint32_t* pos, uint32_t base_cur, uint32_t base_next,
+                              uint32_t* q_out, uint32_t* bfs, uint32_t* child_base) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_in) return;
+  const int n = (int)q_in[i];
+  bfs[base_cur + i] = (uint32_t)n;
+  child_base[base_cur + i] = base_next + pos[i];
+  Kid kids[8];
+  const int nk = expand<8>(n2, n, as_leaf, kids);
+  int by_slot[8];
+  kids_by_slot(kids, nk, by_slot);
+  uint32_t r = 0;
+  for (int sl = 0; sl < 8; ++sl) {
+    const int k = by_slot[sl];
+    if (k >= 0 && !leaf_ref(kids[k], as_leaf)) q_out[pos[i] + r++] = (uint32_t)kids[k].code;
+  }
+}
+
+__global__ void relayout_kernel(const float4* __restrict__ n2, const float4* __restrict__ t2, int nn, int nt,
+                                const int* cnt, const int* first, float4* __restrict__ tdfs, uint32_t* err) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n < nn) relayout_links(n2, t2, n, nt, cnt, first, tdfs, err);
+}
+
+// quantisation of one axis: exponent e with 255 * 2^e >= hi - lo, and the
+// conservative 8-bit planes of each child (computed in FP64, exact)
+DR_D int axis_exponent(float lo, float hi) {
+  const double ext = (double)hi - (double)lo;
+  int e = ext > 0.0 ? (int)ceil(log2(ext / 255.0)) : -100;
+  e = max(-100, min(100, e));
+  while (e < 100 && ldexp(255.0, e) < ext) ++e;
+  return e;
+}
+DR_D uint32_t q_lo(float p, int e, float v) {
+  const double sc = ldexp(1.0, e);
+  double q = floor(((double)v - (double)p) / sc);
+  q = fmin(fmax(q, 0.0), 255.0);
+  while (q > 0.0 && (double)p + q * sc > (double)v) q -= 1.0;
+  return (uint32_t)q;
+}
+DR_D uint32_t q_hi(float p, int e, float v) {
+  const double sc = ldexp(1.0, e);
+  double q = ceil(((double)v - (double)p) / sc);
+  q = fmin(fmax(q, 0.0), 255.0);
+  return (uint32_t)q;
+}
+
+__global__ void emit8_kernel(const float4* __restrict__ n2, uint32_t n_wide, const uint8_t* as_leaf, const int* cnt,
+                             const int* first, const uint32_t* bfs, const uint32_t* child_base,
+                             const uint32_t* tri_base, const float4* __restrict__ tdfs, int nt,
+                             uint4* __restrict__ n8, float4* __restrict__ t8, uint32_t* err) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_wide) return;
+  Kid kids[8];
+  const int nk = expand<8>(n2, (int)bfs[i], as_leaf, kids);
+  int by_slot[8];
+  kids_by_slot(kids, nk, by_slot);
+  float3 lo = kids[0].lo, hi = kids[0].hi;
+  for (int k = 1; k < nk; ++k) {
+    lo = f3(fminf(lo.x, kids[k].lo.x), fminf(lo.y, kids[k].lo.y), fminf(lo.z, kids[k].lo.z));
+    hi = f3(fmaxf(hi.x, kids[k].hi.x), fmaxf(hi.y, kids[k].hi.y), fmaxf(hi.z, kids[k].hi.z));
+  }
+  const int ex = axis_exponent(lo.x, hi.x), ey = axis_exponent(lo.y, hi.y), ez = axis_exponent(lo.z, hi.z);
+  uint32_t qlx[2] = {0, 0}, qly[2] = {0, 0}, qlz[2] = {0, 0}, qhx[2] = {0, 0}, qhy[2] = {0, 0}, qhz[2] = {0, 0};
+  uint32_t meta[2] = {0, 0}, imask = 0, off = 0;
+  const uint32_t tb = tri_base[i];
+  for (int sl = 0; sl < 8; ++sl) {
+    const int k = by_slot[sl];
+    if (k < 0) continue;
+    const Kid& c = kids[k];
+    const int w = sl >> 2, sh = 8 * (sl & 3);
+    qlx[w] |= q_lo(lo.x, ex, c.lo.x) << sh;
+    qly[w] |= q_lo(lo.y, ey, c.lo.y) << sh;
+    qlz[w] |= q_lo(lo.z, ez, c.lo.z) << sh;
+    qhx[w] |= q_hi(lo.x, ex, c.hi.x) << sh;
+    qhy[w] |= q_hi(lo.y, ey, c.hi.y) << sh;
+    qhz[w] |= q_hi(lo.z, ez, c.hi.z) << sh;
+    if (!leaf_ref(c, as_leaf)) {
+      imask |= 1u << sl;
+      continue;
+    }
+    int pos, m;
+    leaf_range(n2, c, cnt, first, &pos, &m);
+    if (m < 1 || m > kBvh4MaxLeaf || off + (uint32_t)m > 32u || pos < 0 || pos + m > nt ||
+        (long long)tb + off + m > nt) {
+      atomicOr(err, kErrBadIndex);
+      continue;
+    }
+    meta[w] |= (0x80u | ((uint32_t)(m - 1) << 5) | off) << sh;
+    for (int t = 0; t < m; ++t)
+      for (int q = 0; q < kTriF4; ++q)
+        t8[(size_t)kTriF4 * (tb + off + t) + q] = tdfs[(size_t)kTriF4 * (pos + t) + q];
+    off += (uint32_t)m;
+  }
+  const uint32_t eb = ((uint32_t)(ex & 0xff)) | ((uint32_t)(ey & 0xff) << 8) | ((uint32_t)(ez & 0xff) << 16) |
+                      (imask << 24);
+  uint4* o = n8 + (size_t)kNode8U4 * i;
+  o[0] = make_uint4(__float_as_uint(lo.x), __float_as_uint(lo.y), __float_as_uint(lo.z), eb);
+  o[1] = make_uint4(child_base[i], tb, meta[0], meta[1]);
+  o[2] = make_uint4(qlx[0], qlx[1], qly[0], qly[1]);
+  o[3] = make_uint4(qlz[0], qlz[1], qhx[0], qhx[1]);
+  o[4] = make_uint4(qhy[0], qhy[1], qhz[0], qhz[1]);
+}
+
 unsigned blocks(long long n) { return (unsigned)((n + kB4Threads - 1) / kB4Threads); }
 
 }  // namespace
 
 size_t bvh4_scratch_bytes(int n_inner, int n_tris) { return b4_bytes(std::max(1, n_inner), std::max(1, n_tris)); }
 
-int bvh4_plan(const float4* d_nodes2, int n_inner, int n_tris, void* scratch, Bvh4Plan* plan, cudaStream_t s) {
-  const int nn = n_inner;
-  *plan = Bvh4Plan{};
-  if (nn < 1 || n_tris < 2) return -1;
-  B4Scratch b = b4_carve(scratch, nn, n_tris);
+namespace {
+
+// The passes both collapses share: parents and reference counts, the tree
+// check, the bottom-up SAH leaf decision and the depth-first positions.
+// Returns 0, or -1 (*tree_ok = 0 for a malformed tree).
+int prepare_tree(const float4* d_nodes2, int nn, int n_tris, const B4Scratch& b, int* tree_ok, cudaStream_t s) {
   cudaMemsetAsync(b.parent, 0xff, (size_t)nn * 4, s);
   cudaMemsetAsync(b.refs, 0, (size_t)nn * 4, s);
   cudaMemsetAsync(b.tri_refs, 0, (size_t)n_tris * 4, s);
@@ -350,13 +549,25 @@ int bvh4_plan(const float4* d_nodes2, int n_inner, int n_tris, void* scratch, Bv
   cudaMemcpyAsync(&err, b.err, 4, cudaMemcpyDeviceToHost, s);
   if (cudaStreamSynchronize(s) != cudaSuccess) return -1;
   if (err != 0) {
-    plan->tree_ok = 0;
+    *tree_ok = 0;
     return -1;
   }
-  plan->tree_ok = 1;
+  *tree_ok = 1;
   bottom_up_kernel<<<blocks(nn), kB4Threads, 0, s>>>(d_nodes2, nn, b.parent, b.cnt, b.cost, b.as_leaf, b.visit,
                                                       b.err);
   first_kernel<<<blocks(nn), kB4Threads, 0, s>>>(d_nodes2, nn, b.parent, b.cnt, b.first, b.counts + 4, b.err);
+  return 0;
+}
+
+}  // namespace
+
+int bvh4_plan(const float4* d_nodes2, int n_inner, int n_tris, void* scratch, Bvh4Plan* plan, cudaStream_t s) {
+  const int nn = n_inner;
+  *plan = Bvh4Plan{};
+  if (nn < 1 || n_tris < 2) return -1;
+  B4Scratch b = b4_carve(scratch, nn, n_tris);
+  if (prepare_tree(d_nodes2, nn, n_tris, b, &plan->tree_ok, s) != 0) return -1;
+  uint32_t err = 0;
   int launches = 4;
   uint32_t n_in = 1;
   // one launch per 4-wide level; a tree has fewer levels than inner nodes
@@ -399,6 +610,108 @@ int bvh4_emit(const float4* d_nodes2, const float4* d_tris2, int n_inner, int n_
   B4Scratch b = b4_carve(scratch, n_inner, n_tris);
   emit_kernel<<<blocks(n_inner), kB4Threads, 0, s>>>(d_nodes2, d_tris2, n_inner, n_tris, b.as_leaf, b.cnt, b.first,
                                                       b.is4, b.slot, d_nodes4, d_tris4, b.err);
+  uint32_t err = 0;
+  cudaMemcpyAsync(&err, b.err, 4, cudaMemcpyDeviceToHost, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess || err != 0) return -1;
+  return 1;
+}
+
+// ---------------------------------------------------------------- 8-wide
+namespace {
+
+struct B8Extra {
+  uint32_t* bfs;         // [nn] binary node of each 8-wide node (breadth-first order)
+  uint32_t* child_base;  // [nn] first inner child of each 8-wide node
+  uint32_t* tri_cnt;     // [nn] leaf triangles of each 8-wide node
+  uint32_t* tri_base;    // [nn] their first position
+  uint32_t* n_inner;     // [nn] per level: inner children of each node
+  uint32_t* pos;         // [nn] per level: exclusive scan of n_inner
+  uint32_t* q[2];        // [nn] level queues
+  float4* tdfs;          // [nt * 3] triangles in depth-first order
+};
+
+size_t b8_extra_bytes(int nn, int nt) { return a256((size_t)nn * 4) * 8 + a256((size_t)nt * kTriF4 * 16); }
+
+B8Extra b8_carve(void* scratch, int nn, int nt) {
+  const size_t n = (size_t)nn;
+  char* p = static_cast<char*>(scratch) + b4_bytes(nn, nt);
+  B8Extra x;
+  x.bfs = reinterpret_cast<uint32_t*>(p); p += a256(n * 4);
+  x.child_base = reinterpret_cast<uint32_t*>(p); p += a256(n * 4);
+  x.tri_cnt = reinterpret_cast<uint32_t*>(p); p += a256(n * 4);
+  x.tri_base = reinterpret_cast<uint32_t*>(p); p += a256(n * 4);
+  x.n_inner = reinterpret_cast<uint32_t*>(p); p += a256(n * 4);
+  x.pos = reinterpret_cast<uint32_t*>(p); p += a256(n * 4);
+  x.q[0] = reinterpret_cast<uint32_t*>(p); p += a256(n * 4);
+  x.q[1] = reinterpret_cast<uint32_t*>(p); p += a256(n * 4);
+  x.tdfs = reinterpret_cast<float4*>(p);
+  return x;
+}
+
+}  // namespace
+
+size_t bvh8_scratch_bytes(int n_inner, int n_tris) {
+  const int nn = std::max(1, n_inner), nt = std::max(1, n_tris);
+  return b4_bytes(nn, nt) + b8_extra_bytes(nn, nt);
+}
+
+int bvh8_plan(const float4* d_nodes2, int n_inner, int n_tris, void* scratch, Bvh8Plan* plan, cudaStream_t s) {
+  const int nn = n_inner;
+  *plan = Bvh8Plan{};
+  if (nn < 1 || n_tris < 2) return -1;
+  B4Scratch b = b4_carve(scratch, nn, n_tris);
+  B8Extra x = b8_carve(scratch, nn, n_tris);
+  if (prepare_tree(d_nodes2, nn, n_tris, b, &plan->tree_ok, s) != 0) return -1;
+  int launches = 4;
+  cudaMemsetAsync(x.q[0], 0, 4, s);  // level 0: the root
+  uint32_t n_in = 1, base = 0;
+  int depth = 0;
+  // one level per round; node numbers are breadth first, so each node's
+  // inner children are consecutive
+  while (n_in > 0) {
+    if (depth > nn) return -1;
+    const uint32_t* q_in = x.q[depth & 1];
+    count8_kernel<<<blocks(n_in), kB4Threads, 0, s>>>(d_nodes2, b.as_leaf, b.cnt, b.first, q_in, n_in, base, x.n_inner,
+                                                      x.tri_cnt, b.err);
+    launch_exclusive_scan(x.n_inner, x.pos, (size_t)n_in, b.scan_tmp, s);
+    uint32_t last[2] = {0, 0};
+    cudaMemcpyAsync(&last[0], x.n_inner + n_in - 1, 4, cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(&last[1], x.pos + n_in - 1, 4, cudaMemcpyDeviceToHost, s);
+    place8_kernel<<<blocks(n_in), kB4Threads, 0, s>>>(d_nodes2, b.as_leaf, q_in, n_in, x.pos, base, base + n_in,
+                                                      x.q[(depth + 1) & 1], x.bfs, x.child_base);
+    launches += 5;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return -1;
+    base += n_in;
+    n_in = last[0] + last[1];
+    if ((size_t)base + n_in > (size_t)nn) return -1;
+    ++depth;
+  }
+  launch_exclusive_scan(x.tri_cnt, x.tri_base, (size_t)base, b.scan_tmp, s);
+  launches += 3;
+  uint32_t tl[2] = {0, 0}, err = 0;
+  cudaMemcpyAsync(&tl[0], x.tri_cnt + base - 1, 4, cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(&tl[1], x.tri_base + base - 1, 4, cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(&err, b.err, 4, cudaMemcpyDeviceToHost, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return -1;
+  if (err != 0 || tl[0] + tl[1] != (uint32_t)n_tris) {
+    plan->tree_ok = 0;
+    return -1;
+  }
+  plan->n_nodes8 = (int)base;
+  plan->depth = depth;
+  plan->launches = launches;
+  return plan->n_nodes8;
+}
+
+int bvh8_emit(const float4* d_nodes2, const float4* d_tris2, int n_inner, int n_tris, void* scratch, int n_nodes8,
+              uint4* d_nodes8, float4* d_tris8, cudaStream_t s) {
+  B4Scratch b = b4_carve(scratch, n_inner, n_tris);
+  B8Extra x = b8_carve(scratch, n_inner, n_tris);
+  relayout_kernel<<<blocks(n_inner), kB4Threads, 0, s>>>(d_nodes2, d_tris2, n_inner, n_tris, b.cnt, b.first, x.tdfs,
+                                                          b.err);
+  emit8_kernel<<<blocks(n_nodes8), kB4Threads, 0, s>>>(d_nodes2, (uint32_t)n_nodes8, b.as_leaf, b.cnt, b.first, x.bfs,
+                                                        x.child_base, x.tri_base, x.tdfs, n_tris, d_nodes8, d_tris8,
+                                                        b.err);
   uint32_t err = 0;
   cudaMemcpyAsync(&err, b.err, 4, cudaMemcpyDeviceToHost, s);
   if (cudaStreamSynchronize(s) != cudaSuccess || err != 0) return -1;

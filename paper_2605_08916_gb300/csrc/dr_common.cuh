@@ -132,6 +132,25 @@ constexpr int kNode4F4 = 7;
 constexpr int kBvh4MaxLeaf = 4;
 constexpr int kBvh4Empty = 0x7fffffff;
 
+// 8-wide compressed BVH node (80 B, 5 x uint4), child boxes quantised to
+// 8 bits per plane against the node's own box:
+//   w0 = (p.x, p.y, p.z as float bits, ex | ey << 8 | ez << 16 | imask << 24)
+//        with signed 8-bit exponents e: a child's box is
+//        [p + 2^e * qlo, p + 2^e * qhi] per axis (never smaller than the
+//        child's exact box)
+//   w1 = (child_base, tri_base, meta[0..3], meta[4..7])
+//   w2 = (qlo.x[0..3], qlo.x[4..7], qlo.y[0..3], qlo.y[4..7])
+//   w3 = (qlo.z[0..3], qlo.z[4..7], qhi.x[0..3], qhi.x[4..7])
+//   w4 = (qhi.y[0..3], qhi.y[4..7], qhi.z[0..3], qhi.z[4..7])
+// Slot s holds an inner child if bit s of imask is set: node child_base +
+// popc(imask & ((1 << s) - 1)) (a node's inner children are consecutive);
+// a leaf if bit 7 of meta[s] is set: triangles tri_base + (meta & 31) ..
+// + ((meta >> 5) & 3) (at most kBvh4MaxLeaf); else the slot is empty.
+// Children sit in slots by the octant heuristic: rays whose direction signs
+// form octant o (bit 0: x < 0, bit 1: y < 0, bit 2: z < 0) visit slot k ^ o
+// k-th, which roughly orders them near to far.
+constexpr int kNode8U4 = 5;
+
 DR_HD int leaf_code(int first, int count) { return (int)(0x80000000u | ((uint32_t)first << 3) | (uint32_t)(count - 1)); }
 DR_HD int leaf_first(int c) { return (int)(((uint32_t)c & 0x7fffffffu) >> 3); }
 DR_HD int leaf_count(int c) { return (int)((uint32_t)c & 7u) + 1; }
@@ -151,12 +170,14 @@ struct DevScene {
   const float4* __restrict__ nodes;
   const float4* __restrict__ nodes4;  // 4-wide BVH (null: use the binary one)
   const float4* __restrict__ tris4;   // triangles in the 4-wide BVH's leaf order
+  const uint4* __restrict__ nodes8;   // 8-wide compressed BVH (null: not built)
+  const float4* __restrict__ tris8;   // triangles in the 8-wide BVH's leaf order
   const float4* __restrict__ tris;
   const float4* __restrict__ surf;
   const float* __restrict__ nrm;     // 9 floats per original triangle, or null
   const float* __restrict__ mats;
   const float4* __restrict__ lights;
-  int n_lights, n_tris, n_nodes, n_nodes4, W, H;
+  int n_lights, n_tris, n_nodes, n_nodes4, n_nodes8, W, H;
   float tmin;
   Camera cam;
 };

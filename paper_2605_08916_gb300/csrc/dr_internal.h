@@ -71,6 +71,18 @@ size_t bvh4_scratch_bytes(int n_inner, int n_tris);
 int bvh4_plan(const float4* d_nodes2, int n_inner, int n_tris, void* scratch, Bvh4Plan* plan, cudaStream_t s);
 int bvh4_emit(const float4* d_nodes2, const float4* d_tris2, int n_inner, int n_tris, void* scratch,
               float4* d_nodes4, float4* d_tris4, cudaStream_t s);
+// The same collapse to the 8-wide compressed layout (kNode8U4): nodes in
+// breadth-first order (one synchronisation per level), each node's leaf
+// triangles consecutive.  bvh8_plan returns the node count (or -1);
+// bvh8_emit writes nodes8 [count * 5 uint4] and tris8 [n_tris * 3].
+struct Bvh8Plan {
+  int n_nodes8, depth, launches;
+  int tree_ok;
+};
+size_t bvh8_scratch_bytes(int n_inner, int n_tris);
+int bvh8_plan(const float4* d_nodes2, int n_inner, int n_tris, void* scratch, Bvh8Plan* plan, cudaStream_t s);
+int bvh8_emit(const float4* d_nodes2, const float4* d_tris2, int n_inner, int n_tris, void* scratch, int n_nodes8,
+              uint4* d_nodes8, float4* d_tris8, cudaStream_t s);
 
 // ---------------------------------------------------------------- chains
 enum Drift { kDriftNone = 0, kDriftFD = 1, kDriftAdjoint = 2 };
@@ -129,6 +141,7 @@ struct StepArgs {
   uint32_t* err;
   int refill;  // persistent traversal: refill a warp below this many busy lanes
   int conductors;  // some material is a conductor: the shading passes that handle them run
+  int bvh8;        // the persistent passes walk the 8-wide BVH (every scene has one)
   // camera-ray order (null: chain order): wf_begin writes (key, chain) with
   // key = the pixel's Morton code (above it the scene of a batch chain)
   uint2* ray_keys;

@@ -236,8 +236,10 @@ __global__ void __launch_bounds__(kStepThreads) trace_kernel(DevScene S, const f
   const float* r = rays + 6 * i;
   uint32_t err = 0;
   float th;
-  const int h = trace_closest<kStack, false>(S, make_ray(f3(r[0], r[1], r[2]), f3(r[3], r[4], r[5])), exclude, &th, st,
-                                             &err, nullptr);
+  const Ray ray = make_ray(f3(r[0], r[1], r[2]), f3(r[3], r[4], r[5]));
+  // the 8-wide BVH where the scene selects it (the persistent passes' walk)
+  const int h = S.nodes8 ? trace_closest<kStack, false, 8>(S, ray, exclude, &th, st, &err, nullptr)
+                         : trace_closest<kStack, false>(S, ray, exclude, &th, st, &err, nullptr);
   tri[i] = h;
   t[i] = h >= 0 ? th : __int_as_float(0x7f800000);
   if (err) atomicOr(errp, err);

@@ -475,12 +475,286 @@ DR_D bool trace_any2(const DevScene& S, const Ray& r, float tmax, int ex0, int e
   return false;
 }
 
+// ---------------------------------------------------------------- 8-wide
+// Compressed 8-wide traversal (node layout at kNode8U4).  A walk holds a
+// node group, the hit inner children of one node still to visit (a mask in
+// the ray's visit order, slot = position ^ octant), and a triangle group,
+// the hit triangles of one node still to test.  A step either tests up to
+// four triangles of the triangle group or visits the next child of the node
+// group (the rest of the group is pushed first: one stack entry per level).
+// Triangles of a node are tested before its children; children come in
+// octant order, not sorted by distance.
+struct Walk8 {
+  uint32_t gbase;  // first inner child of the group's node
+  uint32_t gbits;  // bits 0..7: pending children in visit order; bits 8..15: the node's imask
+  uint32_t tbase;  // first triangle of the triangle group's node
+  uint32_t tbits;  // pending triangles (bit i: triangle tbase + i)
+  int sp, budget;
+};
+
+DR_D int ray_octant(const Ray& r) {
+  return (r.inv.x < 0.0f ? 1 : 0) | (r.inv.y < 0.0f ? 2 : 0) | (r.inv.z < 0.0f ? 4 : 0);
+}
+
+// the root as a one-child group (slot 0, an inner child, visit position
+// 0 ^ octant); budget: every node once and every triangle step once
+DR_D Walk8 walk8_begin(const DevScene& S, const Ray& r) {
+  Walk8 w;
+  w.gbase = 0;
+  w.gbits = (1u << ray_octant(r)) | (1u << 8);
+  w.tbase = 0;
+  w.tbits = 0;
+  w.sp = 0;
+  w.budget = min(2 * S.n_nodes8 + S.n_tris / 4 + 64, kMaxNodeVisits);
+  return w;
+}
+
+DR_D bool walk8_at_tris(const Walk8& w) { return w.tbits != 0u; }
+
+DR_D float byte_f(uint32_t w, int sh) { return (float)((w >> sh) & 0xffu); }
+
+// 2^e for a signed 8-bit exponent in [-100, 100]
+DR_D float pow2_of(uint32_t eb, int sh) { return __uint_as_float((uint32_t)((int)(int8_t)(eb >> sh) + 127) << 23); }
+
+// Visits node `node`: tests its eight child boxes against [0, tmax] and
+// replaces the walk's groups by the node's hit inner children and hit
+// triangles.  Per axis, t = q * (2^e / d) + (p - o) / d: the first product
+// is exact (a power of two times 1/d), and the near (far) distances take a
+// margin of 2^-21 (|o/d| + |(p - o)/d|) off (on), more than the rounding of
+// the two fused multiply-adds, so a box is only ever widened.
+DR_D void node8_visit(const DevScene& S, uint32_t node, const Ray& r, float tmax, int oct, Walk8& w) {
+  const uint4* nb = S.nodes8 + (size_t)kNode8U4 * node;
+  const uint4 h0 = __ldg(nb), h1 = __ldg(nb + 1), qa = __ldg(nb + 2), qb = __ldg(nb + 3), qc = __ldg(nb + 4);
+  const float sx = pow2_of(h0.w, 0) * r.inv.x, sy = pow2_of(h0.w, 8) * r.inv.y, sz = pow2_of(h0.w, 16) * r.inv.z;
+  const float bx = fmaf(__uint_as_float(h0.x), r.inv.x, -r.oinv.x);
+  const float by = fmaf(__uint_as_float(h0.y), r.inv.y, -r.oinv.y);
+  const float bz = fmaf(__uint_as_float(h0.z), r.inv.z, -r.oinv.z);
+  constexpr float kM = 4.76837158203125e-07f;  // 2^-21
+  const float mx = kM * (fabsf(r.oinv.x) + fabsf(bx)), my = kM * (fabsf(r.oinv.y) + fabsf(by)),
+              mz = kM * (fabsf(r.oinv.z) + fabsf(bz));
+  const float bnx = bx - mx, bfx = bx + mx, bny = by - my, bfy = by + my, bnz = bz - mz, bfz = bz + mz;
+  // near planes: lo for a positive direction component, hi for a negative
+  const bool nxs = r.inv.x < 0.0f, nys = r.inv.y < 0.0f, nzs = r.inv.z < 0.0f;
+  const uint32_t nx0 = nxs ? qb.z : qa.x, nx1 = nxs ? qb.w : qa.y, fx0 = nxs ? qa.x : qb.z, fx1 = nxs ? qa.y : qb.w;
+  const uint32_t ny0 = nys ? qc.x : qa.z, ny1 = nys ? qc.y : qa.w, fy0 = nys ? qa.z : qc.x, fy1 = nys ? qa.w : qc.y;
+  const uint32_t nz0 = nzs ? qc.z : qb.x, nz1 = nzs ? qc.w : qb.y, fz0 = nzs ? qb.x : qc.z, fz1 = nzs ? qb.y : qc.w;
+  uint32_t hits = 0;
+#pragma unroll
+  for (int sl = 0; sl < 8; ++sl) {
+    const int sh = 8 * (sl & 3);
+    const float tnx = fmaf(byte_f(sl < 4 ? nx0 : nx1, sh), sx, bnx);
+    const float tfx = fmaf(byte_f(sl < 4 ? fx0 : fx1, sh), sx, bfx);
+    const float tny = fmaf(byte_f(sl < 4 ? ny0 : ny1, sh), sy, bny);
+    const float tfy = fmaf(byte_f(sl < 4 ? fy0 : fy1, sh), sy, bfy);
+    const float tnz = fmaf(byte_f(sl < 4 ? nz0 : nz1, sh), sz, bnz);
+    const float tfz = fmaf(byte_f(sl < 4 ? fz0 : fz1, sh), sz, bfz);
+    const float tn = fmaxf(fmaxf(tnx, tny), fmaxf(tnz, 0.0f));
+    const float tf = fminf(fminf(tfx, tfy), fminf(tfz, tmax));
+    hits |= (tn <= tf * 1.0000002f ? 1u : 0u) << sl;
+  }
+  const uint32_t im = h0.w >> 24;
+  // hit inner children in visit order: slot sl goes to bit sl ^ oct
+  uint32_t v = hits & im;
+  if (oct & 1) v = ((v & 0x55u) << 1) | ((v >> 1) & 0x55u);
+  if (oct & 2) v = ((v & 0x33u) << 2) | ((v >> 2) & 0x33u);
+  if (oct & 4) v = ((v & 0x0fu) << 4) | ((v >> 4) & 0x0fu);
+  w.gbase = h1.x;
+  w.gbits = v | (im << 8);
+  // hit leaves: their triangle ranges as one mask
+  uint32_t tb = 0;
+#pragma unroll
+  for (int sl = 0; sl < 8; ++sl) {
+    const uint32_t m = ((sl < 4 ? h1.z : h1.w) >> (8 * (sl & 3))) & 0xffu;
+    if ((hits >> sl & 1u) && (m & 0x80u)) tb |= ((1u << (((m >> 5) & 3u) + 1u)) - 1u) << (m & 31u);
+  }
+  w.tbase = h1.y;
+  w.tbits = tb;
+}
+
+// the next child of the node group: pushes the rest of the group and
+// visits the child
+template <int STACK>
+DR_D void walk8_descend(const DevScene& S, const Ray& r, float tmax, Walk8& w, TraceStack<STACK> st,
+                        uint32_t* err) {
+  const int oct = ray_octant(r);
+  const int k = __ffs(w.gbits & 0xffu) - 1;
+  const uint32_t im = w.gbits >> 8;
+  const uint32_t node = w.gbase + __popc(im & ((1u << (k ^ oct)) - 1u));
+  w.gbits &= ~(1u << k);
+  if (w.gbits & 0xffu) {
+    if (2 * w.sp + 1 < STACK) {
+      st.at(2 * w.sp) = (int)w.gbase;
+      st.at(2 * w.sp + 1) = (int)w.gbits;
+      ++w.sp;
+    } else {
+      *err |= kErrStackOverflow;
+    }
+  }
+  if (node >= (uint32_t)S.n_nodes8) {
+    *err |= kErrBadIndex;
+    w.gbits = 0;
+    w.tbits = 0;
+    return;
+  }
+  node8_visit(S, node, r, tmax, oct, w);
+}
+
+// after a step: true when the walk is over; else the walk has work
+template <int STACK>
+DR_D bool walk8_settle(Walk8& w, TraceStack<STACK> st) {
+  if (w.tbits != 0u || (w.gbits & 0xffu) != 0u) return false;
+  if (w.sp == 0) return true;
+  --w.sp;
+  w.gbase = (uint32_t)st.at(2 * w.sp);
+  w.gbits = (uint32_t)st.at(2 * w.sp + 1);
+  return false;
+}
+
+template <int STACK, bool STATS>
+DR_D bool closest8_step(const DevScene& S, const Ray& r, int exclude, Walk8& w, float& tbest, int& best,
+                        TraceStack<STACK> st, uint32_t* err, TraceStats* stats) {
+  if (--w.budget < 0) {
+    *err |= kErrBadIndex;
+    return true;
+  }
+  if (w.tbits != 0u) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (w.tbits == 0u) break;
+      const uint32_t tri = w.tbase + (uint32_t)(__ffs(w.tbits) - 1);
+      w.tbits &= w.tbits - 1u;
+      if (tri >= (uint32_t)S.n_tris) {
+        *err |= kErrBadIndex;
+        continue;
+      }
+      const float4 t0 = __ldg(S.tris8 + 3 * (size_t)tri + 0);
+      const float4 t1 = __ldg(S.tris8 + 3 * (size_t)tri + 1);
+      const float4 t2 = __ldg(S.tris8 + 3 * (size_t)tri + 2);
+      const int id = __float_as_int(t0.w);
+      if (STATS) ++stats->tris;
+      float th;
+      if (id != exclude && tri_test(xyz(t0), xyz(t1), xyz(t2), r, S.tmin, tbest * 1.0000001f + 1e-30f, &th)) {
+        if (th < tbest || (th == tbest && id < best)) {
+          tbest = th;
+          best = id;
+        }
+      }
+    }
+  } else {
+    walk8_descend<STACK>(S, r, tbest, w, st, err);
+    if (STATS) ++stats->nodes;
+  }
+  return walk8_settle<STACK>(w, st);
+}
+
+template <int STACK, bool STATS>
+DR_D bool any8_step(const DevScene& S, const Ray& r, float tmax, int ex0, int ex1, Walk8& w, bool* occluded,
+                    TraceStack<STACK> st, uint32_t* err, TraceStats* stats) {
+  *occluded = false;
+  if (--w.budget < 0) {
+    *err |= kErrBadIndex;
+    return true;
+  }
+  if (w.tbits != 0u) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (w.tbits == 0u) break;
+      const uint32_t tri = w.tbase + (uint32_t)(__ffs(w.tbits) - 1);
+      w.tbits &= w.tbits - 1u;
+      if (tri >= (uint32_t)S.n_tris) {
+        *err |= kErrBadIndex;
+        continue;
+      }
+      const float4 t0 = __ldg(S.tris8 + 3 * (size_t)tri + 0);
+      const float4 t1 = __ldg(S.tris8 + 3 * (size_t)tri + 1);
+      const float4 t2 = __ldg(S.tris8 + 3 * (size_t)tri + 2);
+      const int id = __float_as_int(t0.w);
+      if (STATS) ++stats->tris;
+      float th;
+      if (id != ex0 && id != ex1 && tri_test(xyz(t0), xyz(t1), xyz(t2), r, S.tmin, tmax, &th)) {
+        *occluded = true;
+        return true;
+      }
+    }
+  } else {
+    walk8_descend<STACK>(S, r, tmax, w, st, err);
+    if (STATS) ++stats->nodes;
+  }
+  return walk8_settle<STACK>(w, st);
+}
+
+template <int STACK, bool STATS>
+DR_D int trace_closest8(const DevScene& S, const Ray& r, int exclude, float* t_hit, TraceStack<STACK> st,
+                        uint32_t* err, TraceStats* stats) {
+  float tbest = __int_as_float(0x7f800000);
+  int best = -1;
+  if (!ray_finite(r.o, r.d)) {
+    *err |= kErrNonFinite;
+    *t_hit = tbest;
+    return -1;
+  }
+  Walk8 w = walk8_begin(S, r);
+  while (!closest8_step<STACK, STATS>(S, r, exclude, w, tbest, best, st, err, stats)) {
+  }
+  *t_hit = tbest;
+  return best;
+}
+
+template <int STACK, bool STATS>
+DR_D bool trace_any8(const DevScene& S, const Ray& r, float tmax, int ex0, int ex1, TraceStack<STACK> st,
+                     uint32_t* err, TraceStats* stats) {
+  if (!ray_finite(r.o, r.d)) {
+    *err |= kErrNonFinite;
+    return true;
+  }
+  Walk8 w = walk8_begin(S, r);
+  bool occ = false;
+  while (!any8_step<STACK, STATS>(S, r, tmax, ex0, ex1, w, &occ, st, err, stats)) {
+  }
+  return occ;
+}
+
+// Width-generic walk interface of the persistent passes.
+template <int WIDTH>
+struct WalkOf {
+  using type = Walk4;
+};
+template <>
+struct WalkOf<8> {
+  using type = Walk8;
+};
+DR_D void walk_begin(const DevScene& S, const Ray&, Walk4& w) { w = walk4_begin(S); }
+DR_D void walk_begin(const DevScene& S, const Ray& r, Walk8& w) { w = walk8_begin(S, r); }
+DR_D bool walk_at_leaf(const Walk4& w) { return w.node < 0; }
+DR_D bool walk_at_leaf(const Walk8& w) { return w.tbits != 0u; }
+template <int STACK, bool STATS>
+DR_D bool closest_step(const DevScene& S, const Ray& r, int exclude, Walk4& w, float& tbest, int& best,
+                       TraceStack<STACK> st, uint32_t* err, TraceStats* stats) {
+  return closest4_step<STACK, STATS>(S, r, exclude, w, tbest, best, st, err, stats);
+}
+template <int STACK, bool STATS>
+DR_D bool closest_step(const DevScene& S, const Ray& r, int exclude, Walk8& w, float& tbest, int& best,
+                       TraceStack<STACK> st, uint32_t* err, TraceStats* stats) {
+  return closest8_step<STACK, STATS>(S, r, exclude, w, tbest, best, st, err, stats);
+}
+template <int STACK, bool STATS>
+DR_D bool any_step(const DevScene& S, const Ray& r, float tmax, int ex0, int ex1, Walk4& w, bool* occluded,
+                   TraceStack<STACK> st, uint32_t* err, TraceStats* stats) {
+  return any4_step<STACK, STATS>(S, r, tmax, ex0, ex1, w, occluded, st, err, stats);
+}
+template <int STACK, bool STATS>
+DR_D bool any_step(const DevScene& S, const Ray& r, float tmax, int ex0, int ex1, Walk8& w, bool* occluded,
+                   TraceStack<STACK> st, uint32_t* err, TraceStats* stats) {
+  return any8_step<STACK, STATS>(S, r, tmax, ex0, ex1, w, occluded, st, err, stats);
+}
+
 // Closest hit / any hit through whichever BVH the scene selects (WIDTH 0:
-// decided per call from S.nodes4; 2 or 4: fixed at compile time, for
+// decided per call from S.nodes4; 2, 4 or 8: fixed at compile time, for
 // kernels specialised per width).
 template <int STACK, bool STATS, int WIDTH = 0>
 DR_D int trace_closest(const DevScene& S, const Ray& r, int exclude, float* t_hit, TraceStack<STACK> st,
                        uint32_t* err, TraceStats* stats) {
+  if (WIDTH == 8) return trace_closest8<STACK, STATS>(S, r, exclude, t_hit, st, err, stats);
   if (WIDTH == 4 || (WIDTH == 0 && S.nodes4 != nullptr))
     return trace_closest4<STACK, STATS>(S, r, exclude, t_hit, st, err, stats);
   return trace_closest2<STACK, STATS>(S, r, exclude, t_hit, st, err, stats);
@@ -489,6 +763,7 @@ DR_D int trace_closest(const DevScene& S, const Ray& r, int exclude, float* t_hi
 template <int STACK, bool STATS, int WIDTH = 0>
 DR_D bool trace_any(const DevScene& S, const Ray& r, float tmax, int ex0, int ex1, TraceStack<STACK> st,
                     uint32_t* err, TraceStats* stats) {
+  if (WIDTH == 8) return trace_any8<STACK, STATS>(S, r, tmax, ex0, ex1, st, err, stats);
   if (WIDTH == 4 || (WIDTH == 0 && S.nodes4 != nullptr))
     return trace_any4<STACK, STATS>(S, r, tmax, ex0, ex1, st, err, stats);
   return trace_any2<STACK, STATS>(S, r, tmax, ex0, ex1, st, err, stats);

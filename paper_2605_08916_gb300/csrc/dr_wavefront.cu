@@ -209,7 +209,7 @@ DR_D uint32_t warp_fetch(uint32_t* ctr, unsigned idle, uint32_t n, bool& drained
 // first.  The two sets touch disjoint data (hit[] and the ray state vs. the
 // path's f and the shadow-visibility tape flag), so one launch replaces two
 // and each bounce pays the latency of its slowest ray once.
-template <bool STATS, bool BATCH>
+template <bool STATS, bool BATCH, int WIDTH>
 __global__ void __launch_bounds__(kWfThreads, kWfTrace4MinBlocks) wf_traverse(StepArgs a, WfBuffers w, int k) {
   extern __shared__ int smem[];
   TraceStack<kWfStack> st{smem + threadIdx.x, (int)blockDim.x};
@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(kWfThreads, kWfTrace4MinBlocks) wf_traverse(St
   int ex0 = -1, ex1 = -1, best = -1, sid = 0;
   float tlim = 0.0f;  // closest hit so far, or the shadow ray's tmax
   Ray r;
-  Walk4 wk{0, 0, 0};
+  typename WalkOf<WIDTH>::type wk{};
   while (true) {
     if (!drained) {
       const unsigned idle = __ballot_sync(kFull, !has);
@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(kWfThreads, kWfTrace4MinBlocks) wf_traverse(St
             best = -1;
             if (BATCH) sid = a.chain_scene[j];
           }
-          wk = walk4_begin(scene_of<BATCH>(a, sid));
+          walk_begin(scene_of<BATCH>(a, sid), r, wk);
           ++rays;
           if (ray_finite(r.o, r.d)) {
             has = true;
@@ -271,19 +271,20 @@ __global__ void __launch_bounds__(kWfThreads, kWfTrace4MinBlocks) wf_traverse(St
       // inner-node steps and leaf steps are different code: a warp takes
       // the kind that more of its lanes are at, and the other lanes wait a
       // step, so each kind runs with many lanes at once
-      const unsigned at_leaf = __ballot_sync(kFull, has && wk.node < 0);
-      const unsigned at_inner = __ballot_sync(kFull, has && wk.node >= 0);
+      const bool lf = walk_at_leaf(wk);
+      const unsigned at_leaf = __ballot_sync(kFull, has && lf);
+      const unsigned at_inner = __ballot_sync(kFull, has && !lf);
       const bool leaf_phase = __popc(at_leaf) >= __popc(at_inner);
-      if (has && (wk.node < 0) == leaf_phase) {
+      if (has && lf == leaf_phase) {
         const DevScene& S = scene_of<BATCH>(a, sid);
         if (!shadow) {
-          if (closest4_step<kWfStack, STATS>(S, r, ex0, wk, tlim, best, st, &err, &stats)) {
+          if (closest_step<kWfStack, STATS>(S, r, ex0, wk, tlim, best, st, &err, &stats)) {
             w.hit[j] = best;
             has = false;
           }
         } else {
           bool occ;
-          if (any4_step<kWfStack, STATS>(S, r, tlim, ex0, ex1, wk, &occ, st, &err, &stats)) {
+          if (any_step<kWfStack, STATS>(S, r, tlim, ex0, ex1, wk, &occ, st, &err, &stats)) {
             has = false;
             if (!occ) {
               const ShadowRec& sr = w.shadow[t];
@@ -367,7 +368,7 @@ __global__ void __launch_bounds__(kWfThreads, kWfShadeMinBlocks) wf_shade(StepAr
 // bounce-by-bounce passes, so the results are identical.
 constexpr int kWfTailMinBlocks = 4;
 
-template <bool STATS, bool BATCH, bool COND>
+template <bool STATS, bool BATCH, bool COND, int WIDTH>
 __global__ void __launch_bounds__(kWfThreads, kWfTailMinBlocks) wf_tail(StepArgs a, WfBuffers w, int k0) {
   extern __shared__ int smem[];
   TraceStack<kWfStack> st{smem + threadIdx.x, (int)blockDim.x};
@@ -384,7 +385,7 @@ __global__ void __launch_bounds__(kWfThreads, kWfTailMinBlocks) wf_tail(StepArgs
   PathState ps;
   int pix = 0;
   Ray r;
-  Walk4 wk{0, 0, 0};
+  typename WalkOf<WIDTH>::type wk{};
   float tlim = 0.0f;
   float3 contrib = f3(0.f, 0.f, 0.f);
   while (true) {
@@ -430,7 +431,7 @@ __global__ void __launch_bounds__(kWfThreads, kWfTailMinBlocks) wf_tail(StepArgs
             ex1 = nee.ex1;
             contrib = nee.contrib;
             cont_after = next;
-            wk = walk4_begin(S);
+            walk_begin(S, r, wk);
             ++rays;
             if (ray_finite(r.o, r.d)) {
               state = kShadow;
@@ -446,7 +447,7 @@ __global__ void __launch_bounds__(kWfThreads, kWfTailMinBlocks) wf_tail(StepArgs
             ex0 = ps.prev_tri;
             tlim = __int_as_float(0x7f800000);
             best = -1;
-            wk = walk4_begin(S);
+            walk_begin(S, r, wk);
             ++rays;
             if (ray_finite(r.o, r.d)) {
               state = kClosest;
@@ -461,7 +462,7 @@ __global__ void __launch_bounds__(kWfThreads, kWfTailMinBlocks) wf_tail(StepArgs
         }
       } else if (state == kShadow && !do_shade) {
         bool occ;
-        if (any4_step<kWfStack, STATS>(S, r, tlim, ex0, ex1, wk, &occ, st, &err, &stats)) {
+        if (any_step<kWfStack, STATS>(S, r, tlim, ex0, ex1, wk, &occ, st, &err, &stats)) {
           if (!occ) {
             ps.f += contrib;
             GlobalTape{w.tape, a.N, j}.or_flags(k - 1, kFNeeVis);
@@ -472,7 +473,7 @@ __global__ void __launch_bounds__(kWfThreads, kWfTailMinBlocks) wf_tail(StepArgs
             ex0 = ps.prev_tri;
             tlim = __int_as_float(0x7f800000);
             best = -1;
-            wk = walk4_begin(S);
+            walk_begin(S, r, wk);
             ++rays;
             if (ray_finite(r.o, r.d)) {
               state = kClosest;
@@ -487,7 +488,7 @@ __global__ void __launch_bounds__(kWfThreads, kWfTailMinBlocks) wf_tail(StepArgs
           }
         }
       } else if (state == kClosest && !do_shade) {
-        if (closest4_step<kWfStack, STATS>(S, r, ex0, wk, tlim, best, st, &err, &stats)) {
+        if (closest_step<kWfStack, STATS>(S, r, ex0, wk, tlim, best, st, &err, &stats)) {
           hit = best;
           state = kShade;
         }
@@ -634,29 +635,29 @@ unsigned grid_for(unsigned long long n, int max_blocks) {
 }
 
 // resident blocks per SM of the persistent traversal pass, computed once
-template <bool BATCH>
+template <bool BATCH, int WIDTH>
 int traverse_blocks_per_sm(size_t smem) {
   static int cached = 0;
   if (cached == 0) {
     int b0 = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b0, wf_traverse<false, BATCH>, kWfThreads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b0, wf_traverse<false, BATCH, WIDTH>, kWfThreads, smem);
     cached = std::max(1, b0);
   }
   return cached;
 }
 
-template <bool BATCH, bool COND>
+template <bool BATCH, bool COND, int WIDTH>
 int tail_blocks_per_sm(size_t smem) {
   static int cached = 0;
   if (cached == 0) {
     int b0 = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b0, wf_tail<false, BATCH, COND>, kWfThreads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b0, wf_tail<false, BATCH, COND, WIDTH>, kWfThreads, smem);
     cached = std::max(1, b0);
   }
   return cached;
 }
 
-template <bool BATCH, bool COND>
+template <bool BATCH, bool COND, int WIDTH>
 int launch_wf(const StepArgs& a, const WfBuffers& w, bool stats, int n_sm, const WfTuning& tune,
               const PhaseHook& hook, cudaStream_t s, WfMode mode, float* p_out, const RayOrder& order) {
   const int max_blocks = n_sm * 16;
@@ -670,7 +671,7 @@ int launch_wf(const StepArgs& a, const WfBuffers& w, bool stats, int n_sm, const
   const size_t smem = (size_t)kWfStack * kWfThreads * sizeof(int);
   const bool wide = a.S.nodes4 != nullptr || BATCH;
   // persistent traversal: as many blocks as stay resident (or fewer, tuned)
-  const int resident = traverse_blocks_per_sm<BATCH>(smem);
+  const int resident = traverse_blocks_per_sm<BATCH, WIDTH>(smem);
   const int per_sm = tune.blocks_per_sm > 0 ? std::min(tune.blocks_per_sm, resident) : resident;
   const unsigned g4 = (unsigned)(n_sm * per_sm);
   int launches = 0;
@@ -694,16 +695,16 @@ int launch_wf(const StepArgs& a, const WfBuffers& w, bool stats, int n_sm, const
     // k - 1; the last launch (k = L + 1) carries the final shadow rays
     for (int k = 1; k <= a.L + 1; ++k) {
       hook(k <= a.L ? kPhTrace : kPhShadow, true, k <= a.L ? k : a.L);
-      if (stats) wf_traverse<true, BATCH><<<g4, kWfThreads, smem, s>>>(a, w, k);
-      else wf_traverse<false, BATCH><<<g4, kWfThreads, smem, s>>>(a, w, k);
+      if (stats) wf_traverse<true, BATCH, WIDTH><<<g4, kWfThreads, smem, s>>>(a, w, k);
+      else wf_traverse<false, BATCH, WIDTH><<<g4, kWfThreads, smem, s>>>(a, w, k);
       hook(k <= a.L ? kPhTrace : kPhShadow, false, k <= a.L ? k : a.L);
       launches += 1;
       if (k <= a.L && k == tune.tail_bounce) {
         // the rest of every path in one persistent pass
         hook(kPhTail, true, k);
-        const unsigned gt = (unsigned)(n_sm * tail_blocks_per_sm<BATCH, COND>(smem));
-        if (stats) wf_tail<true, BATCH, COND><<<gt, kWfThreads, smem, s>>>(a, w, k);
-        else wf_tail<false, BATCH, COND><<<gt, kWfThreads, smem, s>>>(a, w, k);
+        const unsigned gt = (unsigned)(n_sm * tail_blocks_per_sm<BATCH, COND, WIDTH>(smem));
+        if (stats) wf_tail<true, BATCH, COND, WIDTH><<<gt, kWfThreads, smem, s>>>(a, w, k);
+        else wf_tail<false, BATCH, COND, WIDTH><<<gt, kWfThreads, smem, s>>>(a, w, k);
         hook(kPhTail, false, k);
         launches += 1;
         break;
@@ -769,12 +770,20 @@ int launch_wavefront_step(const StepArgs& a, const WfBuffers& w, bool stats, int
   StepArgs b = a;
   b.ray_keys = order.keys;
   // kernels with the conductor branches run only for scenes that have
-  // conductors (the branches cost registers and code in every kernel)
+  // conductors (the branches cost registers and code in every kernel);
+  // the persistent passes walk the 8-wide BVH where it was built
+  if (a.bvh8) {
+    if (a.conductors)
+      return a.scenes ? launch_wf<true, true, 8>(b, w, stats, n_sm, tune, hook, s, mode, p_out, order)
+                      : launch_wf<false, true, 8>(b, w, stats, n_sm, tune, hook, s, mode, p_out, order);
+    return a.scenes ? launch_wf<true, false, 8>(b, w, stats, n_sm, tune, hook, s, mode, p_out, order)
+                    : launch_wf<false, false, 8>(b, w, stats, n_sm, tune, hook, s, mode, p_out, order);
+  }
   if (a.conductors)
-    return a.scenes ? launch_wf<true, true>(b, w, stats, n_sm, tune, hook, s, mode, p_out, order)
-                    : launch_wf<false, true>(b, w, stats, n_sm, tune, hook, s, mode, p_out, order);
-  return a.scenes ? launch_wf<true, false>(b, w, stats, n_sm, tune, hook, s, mode, p_out, order)
-                  : launch_wf<false, false>(b, w, stats, n_sm, tune, hook, s, mode, p_out, order);
+    return a.scenes ? launch_wf<true, true, 4>(b, w, stats, n_sm, tune, hook, s, mode, p_out, order)
+                    : launch_wf<false, true, 4>(b, w, stats, n_sm, tune, hook, s, mode, p_out, order);
+  return a.scenes ? launch_wf<true, false, 4>(b, w, stats, n_sm, tune, hook, s, mode, p_out, order)
+                  : launch_wf<false, false, 4>(b, w, stats, n_sm, tune, hook, s, mode, p_out, order);
 }
 
 }  // namespace dr

@@ -71,7 +71,7 @@ class Renderer:
     # ---------------------------------------------------------------- inputs
     def set_option(self, option, value):
         """option: "wavefront" (-1 auto / 0 / 1), "work_order" (0/1), "profile" (0/1) or
-        "bvh_width" (0 automatic / 2 / 4), "traverse_blocks" (0 = all resident),
+        "bvh_width" (0 automatic / 2 / 4 / 8; 8 before the upload), "traverse_blocks" (0 = all resident),
         "refill" (1..32), "ray_order" (-1 automatic / 0 / 1) or "tail_bounce" (-1 automatic, 0 off, k)."""
         code = {"work_order": _lib.DR_OPT_WORK_ORDER, "wavefront": _lib.DR_OPT_WAVEFRONT,
                 "profile": _lib.DR_OPT_PROFILE, "bvh_width": _lib.DR_OPT_BVH_WIDTH,
@@ -231,6 +231,15 @@ class Renderer:
             return None
         _lib.check(r, "dr_bvh4_info")
         return {"n_nodes": a.value, "max_depth": b.value, "stack_need": c.value}
+
+    def bvh8_info(self):
+        """The 8-wide compressed BVH's node count and depth, or None when the scene has none."""
+        a, b = C.c_int32(), C.c_int32()
+        r = _lib.load().dr_bvh8_info(self.h, C.byref(a), C.byref(b))
+        if r == _lib.DR_ERR_STATE:
+            return None
+        _lib.check(r, "dr_bvh8_info")
+        return {"n_nodes": a.value, "max_depth": b.value}
 
     def launch_count(self):
         n = C.c_uint64()

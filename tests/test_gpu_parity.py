@@ -70,7 +70,7 @@ def random_rays(scene, n, seed):
     return o, d
 
 
-@pytest.mark.parametrize("width", [2, 4])
+@pytest.mark.parametrize("width", [2, 4, 8])
 @pytest.mark.parametrize("builder", ["ploc", "lbvh"])
 @pytest.mark.parametrize("which", ["cornell", "caustic", "procedural"])
 def test_closest_hit_matches_oracle(torch, R, oracle, which, builder, width):
@@ -84,6 +84,11 @@ def test_closest_hit_matches_oracle(torch, R, oracle, which, builder, width):
     info4 = r.bvh4_info()
     assert info4 is not None and info4["stack_need"] <= 48
     assert info4["n_nodes"] < info["n_nodes"] and info4["max_depth"] < info["max_depth"]
+    info8 = r.bvh8_info()
+    if width == 8:
+        assert info8 is not None and info8["n_nodes"] < info4["n_nodes"] and info8["max_depth"] <= info4["max_depth"]
+    else:
+        assert info8 is None
     tgt = oracle.OracleScene(scene)
     n = 20000
     o, d = random_rays(scene, n, 2)
@@ -104,15 +109,15 @@ def test_closest_hit_matches_oracle(torch, R, oracle, which, builder, width):
 
 @pytest.mark.parametrize("which", ["cornell", "caustic", "procedural"])
 def test_bvh_widths_return_the_same_hits(torch, R, which):
-    """The 4-wide BVH is a regrouping of the binary one's boxes and
-    triangles: the closest hit (ties to the smaller id) and its distance
-    come from the same triangle test on the same data, so they agree
-    bitwise."""
+    """The 4-wide and 8-wide BVHs regroup the binary one's boxes (the 8-wide
+    widened to its 8-bit grid) and triangles: the closest hit (ties to the
+    smaller id) and its distance come from the same triangle test on the
+    same data, so they agree bitwise."""
     scene = hit_scene(which)
     o, d = random_rays(scene, 50000, 3)
     rays = torch.from_numpy(np.concatenate([o, d], 1)).cuda()
     out = []
-    for width in (2, 4):
+    for width in (2, 4, 8):
         r = R.Renderer()
         r.set_option("bvh_width", width)
         r.upload_scene(scene)
@@ -120,10 +125,11 @@ def test_bvh_widths_return_the_same_hits(torch, R, which):
         torch.cuda.synchronize()
         out.append((tri.cpu().numpy(), t.cpu().numpy()))
         r.close()
-    (a, ta), (b, tb) = out
-    assert (a == b).mean() >= 0.9999
-    same = a == b
-    assert np.array_equal(ta[same], tb[same])
+    (a, ta) = out[0]
+    for b, tb in out[1:]:
+        assert (a == b).mean() >= 0.9999
+        same = a == b
+        assert np.array_equal(ta[same], tb[same])
 
 
 def test_one_triangle_scene_keeps_the_binary_bvh(torch, R):
@@ -447,26 +453,31 @@ def test_wavefront_matches_fused(torch, R, which):
     assert abs(c_a["tour_count"] - c_b["tour_count"]) <= 1e-3 * c_a["tour_count"] + 5
 
 
-def test_bvh_widths_give_the_same_chains(torch, R):
-    """Restore steps (wavefront, adjoint drift) through the binary and the
-    4-wide BVH: both return the same hits, so the chains agree."""
+@pytest.mark.parametrize("tail", [0, 4])
+def test_bvh_widths_give_the_same_chains(torch, R, tail):
+    """Restore steps (wavefront, adjoint drift) through the binary, the
+    4-wide and the 8-wide BVH (with and without the tail pass): all return
+    the same hits, so the chains agree."""
     scene, L = S.procedural_scene(1, 64, 36, target_tris=60000, n_objects=40), 12
     out = []
-    for width in (2, 4):
+    for width in (2, 4, 8):
         r = R.Renderer()
         r.set_option("wavefront", 1)
         r.set_option("bvh_width", width)
+        r.set_option("tail_bounce", tail)
         r.upload_scene(scene)
+        assert (r.bvh8_info() is not None) == (width == 8)
         r.init_chains(16384, 35, R.make_params(L=L, drift="adjoint", k0=0.0, steps_per_splat=4))
         r.step(9)
         out.append((r.readback_state(), r.readback_accum()))
         r.close()
-    (a, acc_a), (b, acc_b) = out
-    same = (a["killed"] == b["killed"]) & (a["pix"] == b["pix"]) & np.all(a["x"] == b["x"], 1)
-    same &= a["logp"] == b["logp"]
-    print(f"bit-identical chains {same.mean():.5f}")
-    assert same.mean() >= 0.999
-    assert np.allclose(acc_a, acc_b, rtol=1e-3, atol=1e-9 * np.abs(acc_a).max())
+    (a, acc_a) = out[0]
+    for b, acc_b in out[1:]:
+        same = (a["killed"] == b["killed"]) & (a["pix"] == b["pix"]) & np.all(a["x"] == b["x"], 1)
+        same &= a["logp"] == b["logp"]
+        print(f"bit-identical chains {same.mean():.5f}")
+        assert same.mean() >= 0.999
+        assert np.allclose(acc_a, acc_b, rtol=1e-3, atol=1e-9 * np.abs(acc_a).max())
 
 
 def batch_items():
@@ -475,13 +486,15 @@ def batch_items():
             (S.procedural_scene(3, 64, 36, target_tris=20000, n_objects=20), 8, 20000)]
 
 
-def test_batch_matches_separate_contexts(torch, R):
+@pytest.mark.parametrize("width", [4, 8])
+def test_batch_matches_separate_contexts(torch, R, width):
     """A multi-scene batch advances each scene exactly as a context of its
     own with key (seed_lo, seed_hi + scene): same chain states, k0, tour
-    counts and images, bit for bit."""
+    counts and images, bit for bit (4-wide and 8-wide BVHs)."""
     items = batch_items()
     seed, T = 77, 6
     rb = R.Renderer()
+    rb.set_option("bvh_width", width)
     rb.upload_scenes(items)
     N = sum(n for _, _, n in items)
     rb.init_chains(N, seed, R.make_params(L=16, drift="adjoint", k0=0.0, steps_per_splat=4))
@@ -494,7 +507,7 @@ def test_batch_matches_separate_contexts(torch, R):
     for s, (scene, L, n) in enumerate(items):
         r = R.Renderer()
         r.set_option("wavefront", 1)
-        r.set_option("bvh_width", 4)
+        r.set_option("bvh_width", width)
         r.upload_scene(scene)
         r.init_chains(n, seed + (s << 32), R.make_params(L=L, drift="adjoint", k0=0.0, steps_per_splat=4))
         r.step(T)
