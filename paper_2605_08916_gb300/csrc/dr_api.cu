@@ -714,7 +714,8 @@ int dr_scene_upload(dr_ctx* c, const float* verts, int32_t nv, const int32_t* tr
     lrec[4 * k + 0] = make_float4(a.x, a.y, a.z, hbits_f(i));
     lrec[4 * k + 1] = make_float4(b.x, b.y, b.z, sel[i]);
     lrec[4 * k + 2] = make_float4(cc.x, cc.y, cc.z, area);
-    lrec[4 * k + 3] = make_float4(k + 1 == lt.size() ? 1.0f : (float)(acc / tot), 0.f, 0.f, 0.f);
+    const float* em = mats + 12 * tri_mat[i] + 6;
+    lrec[4 * k + 3] = make_float4(k + 1 == lt.size() ? 1.0f : (float)(acc / tot), em[0], em[1], em[2]);
   }
   {
     const double eye[3] = {camera[0], camera[1], camera[2]}, look[3] = {camera[3], camera[4], camera[5]},

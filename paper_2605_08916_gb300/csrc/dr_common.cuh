@@ -116,8 +116,8 @@ DR_D float wrap01(float v) {
 //   s0 = (v0, material id bits), s1 = (N = cross(e1, e2), area), s2 = (ng, flags),
 //   s3 = (au, -), s4 = (av, -) where barycentrics are (P - v0).au, (P - v0).av
 // Light record (64 B, 4 x float4): l0 = (v0, tri id bits), l1 = (v1, selection
-// probability), l2 = (v2, area), l3 = (cdf upper bound, -, -, -); the emission
-// comes from the triangle's material.
+// probability), l2 = (v2, area), l3 = (cdf upper bound, emission rgb of the
+// triangle's material).
 // Material: 12 floats [type, albedo rgb, roughness, ior, emission rgb, f0, -, -];
 // a conductor keeps the real part eta of its complex index (RGB) in the
 // albedo slots and the imaginary part k (RGB) in the last three.
