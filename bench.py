@@ -48,7 +48,35 @@ WORKLOADS = {
                             spp=16, cpu_chains=128),
     "cornell-64-fd": dict(scene=lambda: S.cornell_box(1, 64, 64), L=4, chains=4096, drift="fd", spp=16,
                           cpu_chains=128),
+    # the procedural layout with its 200 objects as instances of two meshes
+    # (two-level BVH); the oracle renders its flattening
+    "procedural-instanced-1m-720p": dict(scene=lambda: S.procedural_scene_instanced(1, 1280, 720), L=12,
+                                         chains=1 << 20, drift="adjoint", spp=4, cpu_chains=64),
 }
+
+
+def flat_of(scene):
+    """The flat scene the oracle takes (an instanced scene's flattening)."""
+    return scene.flatten() if isinstance(scene, S.InstancedScene) else scene
+
+
+def upload(r, scene):
+    if isinstance(scene, S.InstancedScene):
+        r.upload_instanced(scene)
+    else:
+        r.upload_scene(scene)
+
+
+def input_bytes(scene):
+    """Host bytes an upload copies (the scene arrays)."""
+    if isinstance(scene, S.InstancedScene):
+        n = sum(a.nbytes for m in scene.meshes for a in (m.verts, m.tris, m.tri_mat) if a is not None)
+        n += sum(m.normals.nbytes for m in scene.meshes if m.normals is not None)
+        return n + 56 * len(scene.instances) + scene.materials.nbytes + scene.camera.nbytes
+    n = sum(a.nbytes for a in (scene.verts, scene.tris, scene.tri_mat, scene.materials, scene.camera))
+    return n + (scene.normals.nbytes if scene.normals is not None else 0)
+
+
 DEFAULT = "procedural-1m-720p"
 SEED = 0x5EED
 
@@ -191,7 +219,7 @@ def run_reference(args, wl, rank, world):
     takes about ten seconds), after args.warmup untimed one-step runs."""
     if rank != 0:
         return 0
-    scene = wl["scene"]()
+    scene = flat_of(wl["scene"]())
     from oracle import oracle as O
     tgt = O.OracleScene(scene)
     prm = O.make_params(L=wl["L"], drift="exact" if wl["drift"] == "adjoint" else wl["drift"], rb=True, k0=1.0)
@@ -247,9 +275,10 @@ def run_ours(args, wl, rank, world, local):
     r.set_option("wavefront", args.wavefront)
     r.set_option("bvh_width", args.bvh_width)
     r.set_option("ray_order", args.ray_order)
+    r.set_option("two_level", args.two_level)
     if args.tail_bounce is not None:
         r.set_option("tail_bounce", args.tail_bounce)
-    r.upload_scene(scene)
+    upload(r, scene)
     stream.synchronize()
     t_init = time.perf_counter()
     r.init_chains(N, seed, params)
@@ -258,7 +287,8 @@ def run_ours(args, wl, rank, world, local):
     log(f"init (evaluation + p_lambda estimate + clock) {t_init * 1e3:.1f} ms")
     bvh4 = r.bvh4_info() if args.bvh_width != 2 else None
     bvh8 = r.bvh8_info() if args.bvh_width == 8 else None
-    log(f"uploaded + init {N} chains; bvh {r.bvh_info()}; 4-wide {bvh4}; 8-wide {bvh8}")
+    two_level = r.two_level_info() if isinstance(scene, S.InstancedScene) and args.two_level else None
+    log(f"uploaded + init {N} chains; bvh {r.bvh_info()}; 4-wide {bvh4}; 8-wide {bvh8}; two-level {two_level}")
     # traversal statistics (separate kernel instantiation, untimed)
     r.set_stats(True)
     r.step(2)
@@ -287,7 +317,8 @@ def run_ours(args, wl, rank, world, local):
     wavefront = prof["trace"][1] > 0
     assert wavefront == wf_expected, "execution mode differs from the one the roofline bytes assume"
     if wavefront:
-        k_name = ("wf_traverse (8-wide compressed BVH traversal passes)" if bvh8
+        k_name = ("wf_traverse (two-level BVH traversal passes)" if two_level
+                  else "wf_traverse (8-wide compressed BVH traversal passes)" if bvh8
                   else "wf_traverse (4-wide BVH traversal passes)" if wide
                   else "wf_trace + wf_shadow (binary BVH traversal passes)")
         k_ms = (prof["trace"][0] + prof["shadow"][0]) / prof_steps
@@ -353,7 +384,9 @@ def run_ours(args, wl, rank, world, local):
                            "image": [scene.width, scene.height], "chains_per_gpu": N, "max_path_len": wl["L"],
                            "pss_dim": d, "drift": wl["drift"], "rb_weight": True, "steps_per_frame": F,
                            "execution": "wavefront" if wavefront else "fused",
-                           "bvh": "4-wide" if wide else "binary",
+                           "bvh": ("two-level (4-wide TLAS over instances, 4-wide BLAS per mesh)" if two_level
+                                   else "8-wide compressed" if (bvh8 and wavefront) else "4-wide" if wide
+                                   else "binary"),
                            "frame": "CUDA graph of steps_per_frame steps + splat, replayed",
                            "l2": "inputs > L2 (BVH + chain state) and a 512 MB L2 flush between timed frames",
                            "parallelism": f"replicas{world}"},
@@ -372,7 +405,7 @@ def run_ours(args, wl, rank, world, local):
                 if wavefront else None,
                 "clocks": clocks, "gpu_launches": launches, "e2e": e2e, "relmse_33ms": rel}
         if world == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(wl, scene)
+            line["cpu_baseline"] = cpu_baseline(wl, flat_of(scene))
             log("cpu baseline done")
         print(json.dumps(line), flush=True)
     r.close()
@@ -401,7 +434,7 @@ def run_relmse33(R, scene, wl, local, seeds=16):
     import torch
     stream = torch.cuda.Stream(device=torch.device("cuda", local))
     rr = R.Renderer(local, stream)
-    rr.upload_scene(scene)
+    upload(rr, scene)
     t0 = time.perf_counter()
     rr.pt_render(wl["L"], 4, seed=99)
     stream.synchronize()
@@ -418,7 +451,7 @@ def run_relmse33(R, scene, wl, local, seeds=16):
     for form in ("plain_fd", "batched_adjoint"):
         drift = "fd" if form == "plain_fd" else "adjoint"
         r = R.Renderer(local, stream)
-        r.upload_scene(scene)
+        upload(r, scene)
         if form == "plain_fd":
             r.set_option("wavefront", 0)
         F = wl["spp"]
@@ -469,15 +502,13 @@ def run_e2e(R, scene, wl, N, steps, local, stream):
     copied host -> device (upload + BVH build), chain init with the p_lambda
     estimate, the steps, resolve, and the image copied device -> host."""
     import torch
-    h2d = sum(a.nbytes for a in (scene.verts, scene.tris, scene.tri_mat, scene.materials, scene.camera))
-    if scene.normals is not None:
-        h2d += scene.normals.nbytes
+    h2d = input_bytes(scene)
     out = torch.empty((scene.height, scene.width, 3), dtype=torch.float32, device=torch.device("cuda", local))
     host = torch.empty(out.shape, dtype=torch.float32, pin_memory=True)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     r = R.Renderer(local, stream)
-    r.upload_scene(scene)
+    upload(r, scene)
     r.init_chains(N, SEED + 1, R.make_params(L=wl["L"], drift=wl["drift"], rb=True, k0=0.0,
                                             steps_per_splat=wl["spp"]))
     F = wl["spp"]
@@ -641,6 +672,8 @@ def main():
                     help="run the bounces from this one on as one persistent pass (0 off; default: library's choice)")
     ap.add_argument("--ray-order", type=int, default=-1, choices=[-1, 0, 1],
                     help="sort camera rays by pixel before the first traversal (-1: by triangle count)")
+    ap.add_argument("--two-level", type=int, default=0, choices=[0, 1],
+                    help="instanced workloads: walk the two-level BVH (1) or the flattened one (0)")
     ap.add_argument("--bvh-width", type=int, default=0, choices=[0, 2, 4, 8],
                     help="BVH the rays traverse: 4-wide (0, the default, or 4) or binary (2)")
     ap.add_argument("--work-order", type=int, default=0, choices=[0, 1],

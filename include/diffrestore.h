@@ -156,6 +156,54 @@ typedef struct {
  * Errors: INVALID_ARG, OOM, CUDA, DEVICE_CHECK. */
 int dr_scenes_upload_batch(dr_ctx* ctx, const dr_scene_desc* scenes, int32_t n_scenes);
 
+/* A mesh of an instanced scene (object space; HOST pointers, copied):
+ * verts float [nv * 3], tris int32 [nt * 3] (counter-clockwise = front),
+ * normals float [nv * 3] per vertex or NULL (flat), tri_mat int32 [nt]. */
+typedef struct {
+  const float* verts;
+  int32_t nv;
+  const int32_t* tris;
+  int32_t nt;
+  const float* normals;
+  const int32_t* tri_mat;
+} dr_mesh_desc;
+
+/* One placement of a mesh: xform is the object-to-world affine map,
+ * row-major 3 x 4 (world = A p + t with rows (A_r0, A_r1, A_r2, t_r)), A
+ * invertible; material >= 0 replaces the mesh's per-triangle materials, -1
+ * keeps them. */
+typedef struct {
+  int32_t mesh;
+  int32_t material;
+  float xform[12];
+} dr_instance_desc;
+
+/* Uploads an instanced scene (Sec. 6 "Test scenes": objects placed in a
+ * scene; the two-level acceleration structure of RT pipelines, Sec. 4.3).
+ * The scene is by definition its flattening: instance after instance, each
+ * mesh vertex p goes to world position ((A_r0 p.x + A_r1 p.y) + A_r2 p.z) +
+ * t_r per row r in FP64, rounded to float; normals go through the inverse
+ * transpose (the inverse by cofactors over the determinant, in FP64);
+ * triangle ids are the flattened order (instance-major); a mesh without
+ * normals is flat-shaded.  Everything dr_scene_upload builds is built for
+ * the flattened scene; in addition, with at least 2 instances, a two-level
+ * BVH: a 4-wide BLAS per mesh (object space, the context's builder) and a
+ * 4-wide TLAS over the instances' world boxes with one instance per leaf.
+ * With DR_OPT_TWO_LEVEL set to 1 the bounce-by-bounce passes walk it,
+ * rays mapped into each instance's object space (see dr_two_level_info).
+ * Other arguments as in dr_scene_upload.  Synchronises.
+ * Errors: INVALID_ARG (bad index, singular or non-finite transform, sizes),
+ * OOM, CUDA, DEVICE_CHECK. */
+int dr_scene_upload_instanced(dr_ctx* ctx, const dr_mesh_desc* meshes, int32_t n_meshes,
+                              const dr_instance_desc* instances, int32_t n_instances, const float* mats, int32_t nm,
+                              const float* camera, int32_t width, int32_t height);
+
+/* The two-level BVH of an instanced scene: instances, TLAS nodes and the
+ * BLASes' total nodes (HOST outputs, each may be NULL).  Errors: STATE (no
+ * instanced scene, fewer than 2 instances, or one whose two-level walk
+ * could need more stack than the kernels hold). */
+int dr_two_level_info(dr_ctx* ctx, int32_t* n_instances, int32_t* n_tlas_nodes, int32_t* n_blas_nodes);
+
 /* Resolve (Alg. 3) of scene `scene` of a batch into the FP32 DEVICE buffer
  * out_rgb [W_s * H_s * 3] with that scene's k0 and tourCount.  Errors as
  * dr_resolve, plus STATE when no batch is uploaded, INVALID_ARG for a bad
@@ -345,9 +393,18 @@ int dr_pt_render(dr_ctx* ctx, int32_t max_path_len, uint32_t spp, uint64_t seed,
  *                      (dr_bvh8_info), which the bounce-by-bounce passes
  *                      then walk (the fused kernel keeps the 4-wide one).
  *                      All return the same closest hit (ties: smaller id).
+ *   DR_OPT_TWO_LEVEL   1: for an instanced scene with a two-level BVH, the
+ *                      bounce-by-bounce passes walk it; 0 (default): they
+ *                      walk the flattened scene's BVH (faster here: the
+ *                      object-space maps cost more than the shallower
+ *                      trees save).  The two test triangles in
+ *                      object vs world space, so a hit on an edge shared by
+ *                      two triangles can go to either (the hit point and
+ *                      shading always come from the flattened triangle).
  * Errors: INVALID_ARG (unknown option or value). */
 enum { DR_OPT_WORK_ORDER = 1, DR_OPT_WAVEFRONT = 2, DR_OPT_PROFILE = 3, DR_OPT_BVH_WIDTH = 4,
-       DR_OPT_TRAVERSE_BLOCKS = 5, DR_OPT_REFILL = 6, DR_OPT_RAY_ORDER = 7, DR_OPT_TAIL_BOUNCE = 8 };
+       DR_OPT_TRAVERSE_BLOCKS = 5, DR_OPT_REFILL = 6, DR_OPT_RAY_ORDER = 7, DR_OPT_TAIL_BOUNCE = 8,
+       DR_OPT_TWO_LEVEL = 9 };
 int dr_set_option(dr_ctx* ctx, int32_t option, int32_t value);
 
 /* Per-phase device time accumulated since the last call while DR_OPT_PROFILE

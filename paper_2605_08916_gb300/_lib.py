@@ -29,9 +29,11 @@ EXPORTS = ["dr_version", "dr_last_error", "dr_create", "dr_destroy", "dr_scene_u
            "dr_clear_image", "dr_state_save", "dr_state_load", "dr_set_stats", "dr_get_traversal_stats",
            "dr_bvh_info", "dr_get_launch_count", "dr_get_chain_shape", "dr_pt_render", "dr_set_bvh_builder",
            "dr_splat_records_noalloc", "dr_set_option", "dr_get_profile", "dr_frame", "dr_bvh4_info", "dr_bvh8_info", "dr_get_bounce_profile",
-           "dr_scenes_upload_batch", "dr_resolve_scene", "dr_get_scene_counters"]
+           "dr_scenes_upload_batch", "dr_resolve_scene", "dr_get_scene_counters", "dr_scene_upload_instanced",
+           "dr_two_level_info"]
 DR_OPT_WORK_ORDER, DR_OPT_WAVEFRONT, DR_OPT_PROFILE, DR_OPT_BVH_WIDTH = 1, 2, 3, 4
 DR_OPT_TRAVERSE_BLOCKS, DR_OPT_REFILL, DR_OPT_RAY_ORDER, DR_OPT_TAIL_BOUNCE = 5, 6, 7, 8
+DR_OPT_TWO_LEVEL = 9
 DR_PHASES = 11
 PHASE_NAMES = ["wf_begin", "trace", "shade", "shadow", "finish", "adjoint", "fused_step", "fd_score", "splat",
                "work_order", "tail"]
@@ -44,6 +46,15 @@ class dr_scene_desc(C.Structure):
                 ("nt", C.c_int32), ("tri_mat", C.c_void_p), ("mats", C.c_void_p), ("nm", C.c_int32),
                 ("camera", C.c_void_p), ("width", C.c_int32), ("height", C.c_int32),
                 ("max_path_len", C.c_int32), ("n_chains", C.c_uint64)]
+
+
+class dr_mesh_desc(C.Structure):
+    _fields_ = [("verts", C.c_void_p), ("nv", C.c_int32), ("tris", C.c_void_p), ("nt", C.c_int32),
+                ("normals", C.c_void_p), ("tri_mat", C.c_void_p)]
+
+
+class dr_instance_desc(C.Structure):
+    _fields_ = [("mesh", C.c_int32), ("material", C.c_int32), ("xform", C.c_float * 12)]
 
 
 class dr_params(C.Structure):
@@ -113,6 +124,8 @@ def load(build_if_missing=True):
         "dr_scenes_upload_batch": ([P, P, I32], C.c_int),
         "dr_resolve_scene": ([P, I32, P], C.c_int),
         "dr_get_scene_counters": ([P, I32, P, P], C.c_int),
+        "dr_scene_upload_instanced": ([P, P, I32, P, I32, P, I32, P, I32, I32], C.c_int),
+        "dr_two_level_info": ([P, P, P, P], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)

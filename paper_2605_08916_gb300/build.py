@@ -39,8 +39,11 @@ def build(force=False, verbose=False, ptxas_verbose=False):
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
-    flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
-                    "--expt-relaxed-constexpr"]
+    # host code: no contraction of a * b + c into fused multiply-adds, so the
+    # host arithmetic (e.g. the flattening of instanced scenes) rounds the
+    # same on x86_64 and aarch64 hosts and like the plain FP64 formulas
+    flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
+                    "-I", INCLUDE, "-I", CSRC, "--expt-relaxed-constexpr"]
     if ptxas_verbose:
         flags += ["-Xptxas", "-v"]
 

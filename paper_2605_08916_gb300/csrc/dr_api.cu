@@ -35,6 +35,13 @@ struct dr_ctx {
   float4* tris8 = nullptr;
   int n_nodes8 = 0, bvh8_depth = 0;
   bool batch_bvh8 = false;  // every scene of the batch has an 8-wide BVH
+  // two-level BVH of an instanced scene (null: none)
+  float4* tl_nodes = nullptr;
+  float4* bl_nodes = nullptr;
+  float4* bl_tris = nullptr;
+  float4* insts = nullptr;
+  int n_tl_nodes = 0, n_bl_nodes = 0, n_bl_tris = 0, n_insts = 0;
+  int two_level = 0;  // DR_OPT_TWO_LEVEL
   int bvh_width = 0;  // DR_OPT_BVH_WIDTH (0 automatic)
   bool conductors = false;  // some material is a conductor (selects the kernels that shade them)
   unsigned long long target_gen = 0;  // bumped by every scene / mixture upload
@@ -246,6 +253,15 @@ DevScene dev_scene(const dr_ctx* c) {
   S.nodes4 = wide ? c->nodes4 : nullptr;
   S.tris4 = wide ? c->tris4 : nullptr;
   S.n_nodes4 = wide ? c->n_nodes4 : 0;
+  const bool tl = c->tl_nodes != nullptr && c->two_level != 0;
+  S.tl_nodes = tl ? c->tl_nodes : nullptr;
+  S.bl_nodes = tl ? c->bl_nodes : nullptr;
+  S.bl_tris = tl ? c->bl_tris : nullptr;
+  S.insts = tl ? c->insts : nullptr;
+  S.n_tl_nodes = tl ? c->n_tl_nodes : 0;
+  S.n_bl_nodes = tl ? c->n_bl_nodes : 0;
+  S.n_bl_tris = tl ? c->n_bl_tris : 0;
+  S.n_insts = tl ? c->n_insts : 0;
   const bool w8 = wide && c->nodes8 != nullptr && c->bvh_width == 8;
   S.nodes8 = w8 ? c->nodes8 : nullptr;
   S.tris8 = w8 ? c->tris8 : nullptr;
@@ -340,6 +356,7 @@ StepArgs step_args(dr_ctx* c) {
   a.refill = c->tune.refill;
   a.conductors = c->conductors ? 1 : 0;
   a.bvh8 = c->target == 2 ? (c->batch_bvh8 && c->bvh_width == 8 ? 1 : 0) : (a.S.nodes8 != nullptr ? 1 : 0);
+  a.two_level = c->target == 0 && a.S.tl_nodes != nullptr ? 1 : 0;
   if (c->target == 2) {
     a.scenes = c->d_scenes;
     a.sc = c->d_sc;
@@ -584,6 +601,197 @@ int build_bvh8(dr_ctx* c) {
   return r;
 }
 
+void free_two_level(dr_ctx* c) {
+  dfree(&c->tl_nodes);
+  dfree(&c->bl_nodes);
+  dfree(&c->bl_tris);
+  dfree(&c->insts);
+  c->n_tl_nodes = c->n_bl_nodes = c->n_bl_tris = c->n_insts = 0;
+}
+
+// A 4-wide BVH over nt >= 2 triangles given on the host (binary build with
+// the context's builder, then the collapse with leaves of at most
+// max_leaf): *nodes4 [*n4 * 7] and *tris4 [nt * 3] (record id = triangle
+// index in the input), allocated here.
+int build_wide(dr_ctx* c, const float* verts, int nv, const int* tris, int nt, int max_leaf, float4** nodes4,
+               float4** tris4, int* n4, int* stack_need) {
+  cudaStream_t s = c->stream;
+  float* dv = nullptr;
+  int* dt = nullptr;
+  float4 *n2 = nullptr, *t2 = nullptr;
+  void *scratch = nullptr, *ploc = nullptr, *s4 = nullptr;
+  int r = dalloc(&dv, 3 * (size_t)nv);
+  if (r == DR_OK) r = dalloc(&dt, 3 * (size_t)nt);
+  if (r == DR_OK) r = dalloc(&n2, 4 * (size_t)(nt - 1));
+  if (r == DR_OK) r = dalloc(&t2, 3 * (size_t)nt);
+  if (r == DR_OK) {
+    cudaError_t e = cudaMalloc(&scratch, bvh_scratch_bytes(nt));
+    if (e == cudaSuccess && c->builder == DR_BVH_PLOC) e = cudaMalloc(&ploc, ploc_scratch_bytes(nt));
+    if (e == cudaSuccess) e = cudaMalloc(&s4, bvh4_scratch_bytes(nt - 1, nt));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      r = fail(DR_ERR_OOM, "dr_scene_upload_instanced: BVH scratch");
+    }
+  }
+  if (r == DR_OK) {
+    cudaMemcpyAsync(dv, verts, 12 * (size_t)nv, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(dt, tris, 12 * (size_t)nt, cudaMemcpyHostToDevice, s);
+    const int nn = c->builder == DR_BVH_PLOC ? build_ploc(dv, dt, nt, n2, t2, scratch, ploc, c->ploc_radius, s)
+                                             : build_lbvh(dv, dt, nt, n2, t2, scratch, s);
+    c->launches += 8;
+    Bvh4Plan plan{};
+    const int m = nn < 1 ? -1 : bvh4_plan(n2, nn, nt, s4, &plan, s, max_leaf);
+    c->launches += plan.launches;
+    if (m < 1) {
+      r = fail(DR_ERR_DEVICE_CHECK, "dr_scene_upload_instanced: BLAS / TLAS construction failed");
+    } else {
+      r = dalloc(nodes4, (size_t)kNode4F4 * m);
+      if (r == DR_OK) r = dalloc(tris4, (size_t)kTriF4 * nt);
+      if (r == DR_OK && bvh4_emit(n2, t2, nn, nt, s4, *nodes4, *tris4, s) < 0)
+        r = fail(DR_ERR_DEVICE_CHECK, "dr_scene_upload_instanced: BLAS / TLAS emission failed");
+      c->launches += 1;
+      *n4 = m;
+      *stack_need = plan.stack_need;
+    }
+  }
+  dfree(&dv);
+  dfree(&dt);
+  dfree(&n2);
+  dfree(&t2);
+  if (scratch) cudaFree(scratch);
+  if (ploc) cudaFree(ploc);
+  if (s4) cudaFree(s4);
+  if (r != DR_OK) {
+    dfree(nodes4);
+    dfree(tris4);
+  }
+  return r;
+}
+
+// The two-level BVH: BLAS per mesh (concatenated), TLAS over the instance
+// boxes, instance records.  Left off (DR_OK, nothing built) when its walk
+// could need more stack than the kernels hold.
+int build_two_level(dr_ctx* c, const dr_mesh_desc* meshes, int nmesh, const dr_instance_desc* inst, int ninst,
+                    const std::vector<double>& inv, const std::vector<int>& tri_base, const std::vector<float>& box) {
+  free_two_level(c);
+  cudaStream_t s = c->stream;
+  std::vector<float4*> mn(nmesh, nullptr), mt(nmesh, nullptr);
+  std::vector<int> n4(nmesh, 0), node_off(nmesh, 0), tri_off(nmesh, 0);
+  int r = DR_OK, total_nodes = 0, total_tris = 0, blas_need = 0;
+  for (int m = 0; m < nmesh && r == DR_OK; ++m) {
+    const dr_mesh_desc& q = meshes[m];
+    node_off[m] = total_nodes;
+    tri_off[m] = total_tris;
+    if (q.nt == 1) {
+      // one triangle: a root with one leaf child
+      const float* v0 = q.verts + 3 * q.tris[0];
+      const float* v1 = q.verts + 3 * q.tris[1];
+      const float* v2 = q.verts + 3 * q.tris[2];
+      float lo[3], hi[3];
+      for (int a = 0; a < 3; ++a) {
+        lo[a] = std::min(v0[a], std::min(v1[a], v2[a]));
+        hi[a] = std::max(v0[a], std::max(v1[a], v2[a]));
+      }
+      float4 nd[kNode4F4];
+      for (int a = 0; a < 3; ++a) {
+        nd[2 * a] = make_float4(lo[a], 0.f, 0.f, 0.f);
+        nd[2 * a + 1] = make_float4(hi[a], 0.f, 0.f, 0.f);
+      }
+      nd[6] = make_float4(hbits_f(leaf_code(0, 1)), hbits_f(kBvh4Empty), hbits_f(kBvh4Empty), hbits_f(kBvh4Empty));
+      const float4 tr[3] = {make_float4(v0[0], v0[1], v0[2], hbits_f(0)),
+                            make_float4(v1[0] - v0[0], v1[1] - v0[1], v1[2] - v0[2], 0.f),
+                            make_float4(v2[0] - v0[0], v2[1] - v0[1], v2[2] - v0[2], 0.f)};
+      r = dalloc(&mn[m], kNode4F4);
+      if (r == DR_OK) r = dalloc(&mt[m], 3);
+      if (r == DR_OK) {
+        cudaMemcpyAsync(mn[m], nd, sizeof(nd), cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(mt[m], tr, sizeof(tr), cudaMemcpyHostToDevice, s);
+        cudaStreamSynchronize(s);
+      }
+      n4[m] = 1;
+    } else {
+      int need = 0;
+      r = build_wide(c, q.verts, q.nv, q.tris, q.nt, kBvh4MaxLeaf, &mn[m], &mt[m], &n4[m], &need);
+      blas_need = std::max(blas_need, need);
+    }
+    total_nodes += n4[m];
+    total_tris += q.nt;
+  }
+  if (r == DR_OK) r = dalloc(&c->bl_nodes, (size_t)kNode4F4 * total_nodes);
+  if (r == DR_OK) r = dalloc(&c->bl_tris, (size_t)kTriF4 * total_tris);
+  for (int m = 0; m < nmesh && r == DR_OK; ++m) {
+    cudaMemcpyAsync(c->bl_nodes + (size_t)kNode4F4 * node_off[m], mn[m], 16 * (size_t)kNode4F4 * n4[m],
+                    cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(c->bl_tris + (size_t)kTriF4 * tri_off[m], mt[m], 16 * (size_t)kTriF4 * meshes[m].nt,
+                    cudaMemcpyDeviceToDevice, s);
+    launch_link_offset(c->bl_nodes + (size_t)kNode4F4 * node_off[m], n4[m], node_off[m], tri_off[m], s);
+    c->launches += 1;
+  }
+  if (r == DR_OK) cudaStreamSynchronize(s);
+  for (int m = 0; m < nmesh; ++m) {
+    dfree(&mn[m]);
+    dfree(&mt[m]);
+  }
+  // TLAS over the instance boxes, each given as the degenerate triangle
+  // (lo, hi, lo) whose box it is
+  float4* tl_tris = nullptr;
+  int tl_need = 0;
+  if (r == DR_OK) {
+    std::vector<float> bv(9 * (size_t)ninst);
+    std::vector<int> bt(3 * (size_t)ninst);
+    for (int i = 0; i < ninst; ++i) {
+      for (int a = 0; a < 3; ++a) {
+        bv[9 * i + a] = box[6 * i + a];
+        bv[9 * i + 3 + a] = box[6 * i + 3 + a];
+        bv[9 * i + 6 + a] = box[6 * i + a];
+      }
+      for (int k = 0; k < 3; ++k) bt[3 * i + k] = 3 * i + k;
+    }
+    r = build_wide(c, bv.data(), 3 * ninst, bt.data(), ninst, 1, &c->tl_nodes, &tl_tris, &c->n_tl_nodes, &tl_need);
+  }
+  uint32_t* derr = nullptr;
+  if (r == DR_OK) r = dalloc(&derr, 1);
+  if (r == DR_OK) {
+    cudaMemsetAsync(derr, 0, 4, s);
+    launch_tlas_leaves(c->tl_nodes, c->n_tl_nodes, tl_tris, ninst, derr, s);
+    c->launches += 1;
+    uint32_t e = 0;
+    cudaMemcpyAsync(&e, derr, 4, cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess || e != 0)
+      r = fail(DR_ERR_DEVICE_CHECK, "dr_scene_upload_instanced: TLAS leaves");
+  }
+  dfree(&derr);
+  dfree(&tl_tris);
+  // instance records
+  if (r == DR_OK) {
+    std::vector<float4> ir(kInstF4 * (size_t)ninst);
+    for (int i = 0; i < ninst; ++i) {
+      const double* M = inv.data() + 12 * (size_t)i;
+      for (int row = 0; row < 3; ++row)
+        ir[kInstF4 * i + row] = make_float4((float)M[4 * row], (float)M[4 * row + 1], (float)M[4 * row + 2],
+                                            (float)M[4 * row + 3]);
+      ir[kInstF4 * i + 3] = make_float4(hbits_f(node_off[inst[i].mesh]), hbits_f(tri_base[i]), 0.f, 0.f);
+    }
+    r = dalloc(&c->insts, ir.size());
+    if (r == DR_OK) {
+      cudaMemcpyAsync(c->insts, ir.data(), 16 * ir.size(), cudaMemcpyHostToDevice, s);
+      if (cudaStreamSynchronize(s) != cudaSuccess) r = fail(DR_ERR_CUDA, "dr_scene_upload_instanced: copy");
+    }
+  }
+  if (r == DR_OK) {
+    c->n_bl_nodes = total_nodes;
+    c->n_bl_tris = total_tris;
+    c->n_insts = ninst;
+    // the walk holds the TLAS path, one return mark and a BLAS path
+    if (tl_need + 1 + blas_need > kTraversalStackTL) free_two_level(c);
+  } else {
+    free_two_level(c);
+  }
+  const cudaError_t e = cudaGetLastError();
+  if (r == DR_OK && e != cudaSuccess) r = fail(DR_ERR_CUDA, std::string("dr_scene_upload_instanced: ") + cudaGetErrorString(e));
+  return r;
+}
+
 }  // namespace
 
 extern "C" {
@@ -626,6 +834,7 @@ int dr_destroy(dr_ctx* c) {
   cudaStreamSynchronize(c->stream);
   dfree(&c->nodes4); dfree(&c->tris4);
   dfree(&c->nodes8); dfree(&c->tris8);
+  free_two_level(c);
   dfree(&c->nodes); dfree(&c->tris); dfree(&c->surf); dfree(&c->lights); dfree(&c->nrm); dfree(&c->mats);
   dfree(&c->mw); dfree(&c->mmu); dfree(&c->msig);
   dfree(&c->x); dfree(&c->score); dfree(&c->logp); dfree(&c->killed);
@@ -657,6 +866,7 @@ int dr_scene_upload(dr_ctx* c, const float* verts, int32_t nv, const int32_t* tr
   for (int i = 0; i < 3 * nt; ++i)
     if (tris[i] < 0 || tris[i] >= nv) return fail(DR_ERR_INVALID_ARG, "dr_scene_upload: vertex index out of range");
   free_batch(c);
+  free_two_level(c);
   for (int i = 0; i < nt; ++i)
     if (tri_mat[i] < 0 || tri_mat[i] >= nm) return fail(DR_ERR_INVALID_ARG, "dr_scene_upload: material out of range");
   for (int i = 0; i < nm; ++i) {
@@ -1472,7 +1682,8 @@ std::vector<unsigned long long> frame_key(const dr_ctx* c, uint32_t n_steps) {
   std::vector<unsigned long long> k = {n_steps, c->N, (unsigned long long)c->d, (unsigned long long)c->target,
                                        P(c->x), P(c->score), P(c->killed), P(c->logp), P(c->plen), P(c->rec),
                                        P(c->rec_alt), P(c->sort_scratch), P(c->accum), P(c->wf_mem), P(c->nodes),
-                                       P(c->nodes4), P(c->nodes8), (unsigned long long)c->bvh_width, P(c->tris), P(c->surf), P(c->mats), P(c->lights), P(c->nrm), P(c->mw),
+                                       P(c->nodes4), P(c->nodes8), P(c->tl_nodes), (unsigned long long)c->two_level,
+                                       (unsigned long long)c->bvh_width, P(c->tris), P(c->surf), P(c->mats), P(c->lights), P(c->nrm), P(c->mw),
                                        c->rec_cap, (unsigned long long)c->wavefront,
                                        (unsigned long long)c->work_order, (unsigned long long)c->stats,
                                        (unsigned long long)c->nt, (unsigned long long)c->n_lights, P(c->stream),
@@ -1639,6 +1850,10 @@ int dr_set_option(dr_ctx* c, int32_t option, int32_t value) {
       if (value < -1 || value > 1) return fail(DR_ERR_INVALID_ARG, "dr_set_option: ray order is -1, 0 or 1");
       c->ray_order = value;
       return DR_OK;
+    case DR_OPT_TWO_LEVEL:
+      if (value != 0 && value != 1) return fail(DR_ERR_INVALID_ARG, "dr_set_option: two-level is 0 or 1");
+      c->two_level = value;
+      return DR_OK;
     case DR_OPT_BVH_WIDTH:
       if (value != 0 && value != 2 && value != 4 && value != 8)
         return fail(DR_ERR_INVALID_ARG, "dr_set_option: BVH width is 0, 2, 4 or 8");
@@ -1681,6 +1896,113 @@ int dr_bvh4_info(dr_ctx* c, int32_t* n_nodes, int32_t* max_depth, int32_t* stack
   if (n_nodes) *n_nodes = c->n_nodes4;
   if (max_depth) *max_depth = c->bvh4_depth;
   if (stack_need) *stack_need = c->bvh4_stack;
+  return DR_OK;
+}
+
+int dr_scene_upload_instanced(dr_ctx* c, const dr_mesh_desc* meshes, int32_t n_meshes,
+                              const dr_instance_desc* inst, int32_t n_inst, const float* mats, int32_t nm,
+                              const float* camera, int32_t width, int32_t height) {
+  const char* fn = "dr_scene_upload_instanced";
+  if (!c || !meshes || !inst || !mats || !camera) return fail(DR_ERR_INVALID_ARG, std::string(fn) + ": NULL argument");
+  if (n_meshes < 1 || n_inst < 1 || nm < 1) return fail(DR_ERR_INVALID_ARG, std::string(fn) + ": bad size");
+  bool any_normals = false;
+  for (int m = 0; m < n_meshes; ++m) {
+    const dr_mesh_desc& q = meshes[m];
+    if (!q.verts || !q.tris || !q.tri_mat || q.nv < 1 || q.nt < 1)
+      return fail(DR_ERR_INVALID_ARG, std::string(fn) + ": mesh " + std::to_string(m) + " is empty or NULL");
+    for (long long k = 0; k < 3ll * q.nt; ++k)
+      if (q.tris[k] < 0 || q.tris[k] >= q.nv)
+        return fail(DR_ERR_INVALID_ARG, std::string(fn) + ": mesh vertex index out of range");
+    for (int k = 0; k < q.nt; ++k)
+      if (q.tri_mat[k] < 0 || q.tri_mat[k] >= nm)
+        return fail(DR_ERR_INVALID_ARG, std::string(fn) + ": mesh material out of range");
+    for (long long k = 0; k < 3ll * q.nv; ++k)
+      if (!std::isfinite(q.verts[k])) return fail(DR_ERR_INVALID_ARG, std::string(fn) + ": non-finite vertex");
+    any_normals = any_normals || q.normals != nullptr;
+  }
+  long long tv = 0, tt = 0;
+  std::vector<double> inv(12 * (size_t)n_inst);
+  for (int i = 0; i < n_inst; ++i) {
+    const dr_instance_desc& d = inst[i];
+    if (d.mesh < 0 || d.mesh >= n_meshes) return fail(DR_ERR_INVALID_ARG, std::string(fn) + ": instance mesh out of range");
+    if (d.material < -1 || d.material >= nm)
+      return fail(DR_ERR_INVALID_ARG, std::string(fn) + ": instance material out of range");
+    for (int k = 0; k < 12; ++k)
+      if (!std::isfinite(d.xform[k])) return fail(DR_ERR_INVALID_ARG, std::string(fn) + ": non-finite transform");
+    // inverse of A by cofactors over the determinant; c = -A^-1 t
+    const double a00 = d.xform[0], a01 = d.xform[1], a02 = d.xform[2];
+    const double a10 = d.xform[4], a11 = d.xform[5], a12 = d.xform[6];
+    const double a20 = d.xform[8], a21 = d.xform[9], a22 = d.xform[10];
+    const double c00 = a11 * a22 - a12 * a21, c01 = a12 * a20 - a10 * a22, c02 = a10 * a21 - a11 * a20;
+    const double det = a00 * c00 + a01 * c01 + a02 * c02;
+    if (!(std::fabs(det) > 0.0) || !std::isfinite(det))
+      return fail(DR_ERR_INVALID_ARG, std::string(fn) + ": singular transform");
+    double* M = inv.data() + 12 * (size_t)i;
+    const double m[3][3] = {{c00 / det, (a02 * a21 - a01 * a22) / det, (a01 * a12 - a02 * a11) / det},
+                            {c01 / det, (a00 * a22 - a02 * a20) / det, (a02 * a10 - a00 * a12) / det},
+                            {c02 / det, (a01 * a20 - a00 * a21) / det, (a00 * a11 - a01 * a10) / det}};
+    const double t[3] = {d.xform[3], d.xform[7], d.xform[11]};
+    for (int row = 0; row < 3; ++row) {
+      M[4 * row] = m[row][0];
+      M[4 * row + 1] = m[row][1];
+      M[4 * row + 2] = m[row][2];
+      M[4 * row + 3] = -((m[row][0] * t[0] + m[row][1] * t[1]) + m[row][2] * t[2]);
+    }
+    tv += meshes[d.mesh].nv;
+    tt += meshes[d.mesh].nt;
+  }
+  if (tv >= (1ll << 31) || tt >= (1ll << 30)) return fail(DR_ERR_INVALID_ARG, std::string(fn) + ": scene too large");
+  // the flattened scene
+  std::vector<float> V(3 * (size_t)tv), N(any_normals ? 3 * (size_t)tv : 0, 0.f), box(6 * (size_t)n_inst);
+  std::vector<int> T(3 * (size_t)tt), TM((size_t)tt), tri_base(n_inst);
+  long long vb = 0, tb = 0;
+  for (int i = 0; i < n_inst; ++i) {
+    const dr_instance_desc& d = inst[i];
+    const dr_mesh_desc& q = meshes[d.mesh];
+    const double* M = inv.data() + 12 * (size_t)i;
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int v = 0; v < q.nv; ++v) {
+      const double p[3] = {q.verts[3 * v], q.verts[3 * v + 1], q.verts[3 * v + 2]};
+      for (int row = 0; row < 3; ++row) {
+        const double w = (((double)d.xform[4 * row] * p[0] + (double)d.xform[4 * row + 1] * p[1]) +
+                          (double)d.xform[4 * row + 2] * p[2]) + (double)d.xform[4 * row + 3];
+        const float f = (float)w;
+        V[3 * (vb + v) + row] = f;
+        lo[row] = std::min(lo[row], f);
+        hi[row] = std::max(hi[row], f);
+      }
+      if (q.normals) {
+        const double n[3] = {q.normals[3 * v], q.normals[3 * v + 1], q.normals[3 * v + 2]};
+        for (int row = 0; row < 3; ++row)
+          N[3 * (vb + v) + row] = (float)((M[row] * n[0] + M[4 + row] * n[1]) + M[8 + row] * n[2]);
+      }
+    }
+    for (int k = 0; k < q.nt; ++k) {
+      for (int e = 0; e < 3; ++e) T[3 * (tb + k) + e] = (int)(vb + q.tris[3 * k + e]);
+      TM[tb + k] = d.material >= 0 ? d.material : q.tri_mat[k];
+    }
+    for (int a = 0; a < 3; ++a) {
+      box[6 * i + a] = lo[a];
+      box[6 * i + 3 + a] = hi[a];
+    }
+    tri_base[i] = (int)tb;
+    vb += q.nv;
+    tb += q.nt;
+  }
+  int r = dr_scene_upload(c, V.data(), (int32_t)tv, T.data(), any_normals ? N.data() : nullptr, (int32_t)tt, TM.data(),
+                          mats, nm, camera, width, height);
+  if (r != DR_OK) return r;
+  if (n_inst >= 2) r = build_two_level(c, meshes, n_meshes, inst, n_inst, inv, tri_base, box);
+  if (r != DR_OK) c->target = -1;
+  return r;
+}
+
+int dr_two_level_info(dr_ctx* c, int32_t* n_instances, int32_t* n_tlas_nodes, int32_t* n_blas_nodes) {
+  if (!c) return fail(DR_ERR_INVALID_ARG, "dr_two_level_info: NULL ctx");
+  if (c->target != 0 || !c->tl_nodes) return fail(DR_ERR_STATE, "dr_two_level_info: no two-level BVH");
+  if (n_instances) *n_instances = c->n_insts;
+  if (n_tlas_nodes) *n_tlas_nodes = c->n_tl_nodes;
+  if (n_blas_nodes) *n_blas_nodes = c->n_bl_nodes;
   return DR_OK;
 }
 

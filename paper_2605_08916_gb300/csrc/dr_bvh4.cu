@@ -161,7 +161,7 @@ __global__ void verify_kernel(int nn, int nt, const uint32_t* refs, const uint32
 
 // settles node n (its inner children are settled): count, SAH cost, leaf
 // decision
-DR_D void settle(const float4* __restrict__ n2, int n, int* cnt, float* cost, uint8_t* as_leaf) {
+DR_D void settle(const float4* __restrict__ n2, int n, int* cnt, float* cost, uint8_t* as_leaf, int max_leaf) {
   const Kid k0 = kid_of(n2, n, 0), k1 = kid_of(n2, n, 1);
   const float an = fmaxf(box_area(f3(fminf(k0.lo.x, k1.lo.x), fminf(k0.lo.y, k1.lo.y), fminf(k0.lo.z, k1.lo.z)),
                                   f3(fmaxf(k0.hi.x, k1.hi.x), fmaxf(k0.hi.y, k1.hi.y), fmaxf(k0.hi.z, k1.hi.z))),
@@ -182,7 +182,7 @@ DR_D void settle(const float4* __restrict__ n2, int n, int* cnt, float* cost, ui
     total += cc;
     c_inner += box_area(c.lo, c.hi) / an * ccost;
   }
-  const bool leaf = total <= kBvh4MaxLeaf && (float)total <= c_inner;
+  const bool leaf = total <= max_leaf && (float)total <= c_inner;
   cnt[n] = total;
   cost[n] = leaf ? (float)total : c_inner;
   as_leaf[n] = leaf ? 1 : 0;
@@ -192,7 +192,7 @@ DR_D void settle(const float4* __restrict__ n2, int n, int* cnt, float* cost, ui
 // settled by the walk that brings its second finished child, the first
 // arrival ends its walk there.
 __global__ void bottom_up_kernel(const float4* __restrict__ n2, int nn, const int* parent, int* cnt, float* cost,
-                                 uint8_t* as_leaf, uint32_t* visit, uint32_t* err) {
+                                 uint8_t* as_leaf, uint32_t* visit, int max_leaf, uint32_t* err) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= nn) return;
   const float4 d = n2[4 * n + 3];
@@ -202,7 +202,7 @@ __global__ void bottom_up_kernel(const float4* __restrict__ n2, int nn, const in
   __threadfence();
   int cur = n;
   for (int guard = 0; guard <= nn; ++guard) {
-    settle(n2, cur, cnt, cost, as_leaf);
+    settle(n2, cur, cnt, cost, as_leaf, max_leaf);
     const int p = parent[cur];
     if (p < 0) return;
     __threadfence();  // cur's results visible before its arrival is counted
@@ -535,7 +535,8 @@ namespace {
 // The passes both collapses share: parents and reference counts, the tree
 // check, the bottom-up SAH leaf decision and the depth-first positions.
 // Returns 0, or -1 (*tree_ok = 0 for a malformed tree).
-int prepare_tree(const float4* d_nodes2, int nn, int n_tris, const B4Scratch& b, int* tree_ok, cudaStream_t s) {
+int prepare_tree(const float4* d_nodes2, int nn, int n_tris, const B4Scratch& b, int* tree_ok, int max_leaf,
+                 cudaStream_t s) {
   cudaMemsetAsync(b.parent, 0xff, (size_t)nn * 4, s);
   cudaMemsetAsync(b.refs, 0, (size_t)nn * 4, s);
   cudaMemsetAsync(b.tri_refs, 0, (size_t)n_tris * 4, s);
@@ -554,19 +555,20 @@ int prepare_tree(const float4* d_nodes2, int nn, int n_tris, const B4Scratch& b,
   }
   *tree_ok = 1;
   bottom_up_kernel<<<blocks(nn), kB4Threads, 0, s>>>(d_nodes2, nn, b.parent, b.cnt, b.cost, b.as_leaf, b.visit,
-                                                      b.err);
+                                                      max_leaf, b.err);
   first_kernel<<<blocks(nn), kB4Threads, 0, s>>>(d_nodes2, nn, b.parent, b.cnt, b.first, b.counts + 4, b.err);
   return 0;
 }
 
 }  // namespace
 
-int bvh4_plan(const float4* d_nodes2, int n_inner, int n_tris, void* scratch, Bvh4Plan* plan, cudaStream_t s) {
+int bvh4_plan(const float4* d_nodes2, int n_inner, int n_tris, void* scratch, Bvh4Plan* plan, cudaStream_t s,
+              int max_leaf) {
   const int nn = n_inner;
   *plan = Bvh4Plan{};
-  if (nn < 1 || n_tris < 2) return -1;
+  if (nn < 1 || n_tris < 2 || max_leaf < 1 || max_leaf > kBvh4MaxLeaf) return -1;
   B4Scratch b = b4_carve(scratch, nn, n_tris);
-  if (prepare_tree(d_nodes2, nn, n_tris, b, &plan->tree_ok, s) != 0) return -1;
+  if (prepare_tree(d_nodes2, nn, n_tris, b, &plan->tree_ok, max_leaf, s) != 0) return -1;
   uint32_t err = 0;
   int launches = 4;
   uint32_t n_in = 1;
@@ -661,7 +663,7 @@ int bvh8_plan(const float4* d_nodes2, int n_inner, int n_tris, void* scratch, Bv
   if (nn < 1 || n_tris < 2) return -1;
   B4Scratch b = b4_carve(scratch, nn, n_tris);
   B8Extra x = b8_carve(scratch, nn, n_tris);
-  if (prepare_tree(d_nodes2, nn, n_tris, b, &plan->tree_ok, s) != 0) return -1;
+  if (prepare_tree(d_nodes2, nn, n_tris, b, &plan->tree_ok, kBvh4MaxLeaf, s) != 0) return -1;
   int launches = 4;
   cudaMemsetAsync(x.q[0], 0, 4, s);  // level 0: the root
   uint32_t n_in = 1, base = 0;
@@ -716,6 +718,56 @@ int bvh8_emit(const float4* d_nodes2, const float4* d_tris2, int n_inner, int n_
   cudaMemcpyAsync(&err, b.err, 4, cudaMemcpyDeviceToHost, s);
   if (cudaStreamSynchronize(s) != cudaSuccess || err != 0) return -1;
   return 1;
+}
+
+// ---------------------------------------------------------------- two-level
+namespace {
+
+// links of n 4-wide nodes: inner links += node_off, leaf ranges moved by
+// tri_off (the nodes joined to a concatenation)
+__global__ void link_offset_kernel(float4* __restrict__ n4, int n, int node_off, int tri_off) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int4* l = reinterpret_cast<int4*>(n4 + (size_t)kNode4F4 * i + 6);
+  int4 v = *l;
+  int* c[4] = {&v.x, &v.y, &v.z, &v.w};
+  for (int k = 0; k < 4; ++k) {
+    if (*c[k] == kBvh4Empty) continue;
+    if (*c[k] >= 0) *c[k] += node_off;
+    else *c[k] = leaf_code(leaf_first(*c[k]) + tri_off, leaf_count(*c[k]));
+  }
+  *l = v;
+}
+
+// TLAS leaves (one record each) point at the instance itself
+__global__ void tlas_leaf_kernel(float4* __restrict__ n4, int n, const float4* __restrict__ t4, int n_inst,
+                                 uint32_t* err) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int4* l = reinterpret_cast<int4*>(n4 + (size_t)kNode4F4 * i + 6);
+  int4 v = *l;
+  int* c[4] = {&v.x, &v.y, &v.z, &v.w};
+  for (int k = 0; k < 4; ++k) {
+    if (*c[k] == kBvh4Empty || *c[k] >= 0) continue;
+    if (leaf_count(*c[k]) != 1 || leaf_first(*c[k]) >= n_inst) {
+      atomicOr(err, kErrBadIndex);
+      continue;
+    }
+    const int inst = __float_as_int(t4[(size_t)kTriF4 * leaf_first(*c[k])].w);
+    if (inst < 0 || inst >= n_inst) atomicOr(err, kErrBadIndex);
+    *c[k] = leaf_code(inst, 1);
+  }
+  *l = v;
+}
+
+}  // namespace
+
+void launch_link_offset(float4* nodes4, int n, int node_off, int tri_off, cudaStream_t s) {
+  if (n > 0) link_offset_kernel<<<blocks(n), kB4Threads, 0, s>>>(nodes4, n, node_off, tri_off);
+}
+
+void launch_tlas_leaves(float4* nodes4, int n, const float4* tris4, int n_inst, uint32_t* err, cudaStream_t s) {
+  if (n > 0) tlas_leaf_kernel<<<blocks(n), kB4Threads, 0, s>>>(nodes4, n, tris4, n_inst, err);
 }
 
 }  // namespace dr

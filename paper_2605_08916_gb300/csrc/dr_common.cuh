@@ -17,6 +17,9 @@ constexpr int kMaxPathLen = 16;               // L <= 16  ->  d <= 62
 // Entries of the per-thread traversal stack; a BVH deeper than this + 1 is
 // rejected at scene upload.
 constexpr int kTraversalStack = 48;
+// entries of the two-level walk's stack (a TLAS path, a return mark and a
+// BLAS path); its kernels get the larger shared-memory stack
+constexpr int kTraversalStackTL = 64;
 constexpr int kMaxDim = 2 + 4 * (kMaxPathLen - 1);
 
 // device error word bits (read back by the host after each call)
@@ -151,6 +154,16 @@ constexpr int kBvh4Empty = 0x7fffffff;
 // k-th, which roughly orders them near to far.
 constexpr int kNode8U4 = 5;
 
+// Two-level BVH of an instanced scene: a 4-wide TLAS over the instances'
+// world boxes whose leaves hold one instance each (leaf first = instance
+// index), and the meshes' 4-wide BLASes concatenated (inner links and leaf
+// ranges global in the concatenation; triangle records in object space,
+// t0.w = the triangle's index within its mesh).  Instance record (64 B,
+// 4 x float4): rows 0..2 of the world-to-object affine map as (m0, m1, m2,
+// c) so that p_obj = (m . p_world) + c per row, then (BLAS root node, global
+// id of the instance's first triangle, -, -) as int bits.
+constexpr int kInstF4 = 4;
+
 DR_HD int leaf_code(int first, int count) { return (int)(0x80000000u | ((uint32_t)first << 3) | (uint32_t)(count - 1)); }
 DR_HD int leaf_first(int c) { return (int)(((uint32_t)c & 0x7fffffffu) >> 3); }
 DR_HD int leaf_count(int c) { return (int)((uint32_t)c & 7u) + 1; }
@@ -172,6 +185,11 @@ struct DevScene {
   const float4* __restrict__ tris4;   // triangles in the 4-wide BVH's leaf order
   const uint4* __restrict__ nodes8;   // 8-wide compressed BVH (null: not built)
   const float4* __restrict__ tris8;   // triangles in the 8-wide BVH's leaf order
+  const float4* __restrict__ tl_nodes;  // two-level BVH (null: not built): TLAS nodes (4-wide)
+  const float4* __restrict__ bl_nodes;  // concatenated BLAS nodes (4-wide)
+  const float4* __restrict__ bl_tris;   // concatenated BLAS triangles (object space)
+  const float4* __restrict__ insts;     // instance records
+  int n_tl_nodes, n_bl_nodes, n_bl_tris, n_insts;
   const float4* __restrict__ tris;
   const float4* __restrict__ surf;
   const float* __restrict__ nrm;     // 9 floats per original triangle, or null

@@ -68,7 +68,8 @@ struct Bvh4Plan {
   int depth2;   // height of the binary tree (root = 1)
 };
 size_t bvh4_scratch_bytes(int n_inner, int n_tris);
-int bvh4_plan(const float4* d_nodes2, int n_inner, int n_tris, void* scratch, Bvh4Plan* plan, cudaStream_t s);
+int bvh4_plan(const float4* d_nodes2, int n_inner, int n_tris, void* scratch, Bvh4Plan* plan, cudaStream_t s,
+              int max_leaf = kBvh4MaxLeaf);
 int bvh4_emit(const float4* d_nodes2, const float4* d_tris2, int n_inner, int n_tris, void* scratch,
               float4* d_nodes4, float4* d_tris4, cudaStream_t s);
 // The same collapse to the 8-wide compressed layout (kNode8U4): nodes in
@@ -83,6 +84,11 @@ size_t bvh8_scratch_bytes(int n_inner, int n_tris);
 int bvh8_plan(const float4* d_nodes2, int n_inner, int n_tris, void* scratch, Bvh8Plan* plan, cudaStream_t s);
 int bvh8_emit(const float4* d_nodes2, const float4* d_tris2, int n_inner, int n_tris, void* scratch, int n_nodes8,
               uint4* d_nodes8, float4* d_tris8, cudaStream_t s);
+// Two-level BVH assembly: shift the links of n 4-wide nodes by node_off /
+// tri_off (BLAS concatenation), and turn TLAS leaves (one record each) into
+// instance indices read from the records' ids.
+void launch_link_offset(float4* nodes4, int n, int node_off, int tri_off, cudaStream_t s);
+void launch_tlas_leaves(float4* nodes4, int n, const float4* tris4, int n_inst, uint32_t* err, cudaStream_t s);
 
 // ---------------------------------------------------------------- chains
 enum Drift { kDriftNone = 0, kDriftFD = 1, kDriftAdjoint = 2 };
@@ -142,6 +148,7 @@ struct StepArgs {
   int refill;  // persistent traversal: refill a warp below this many busy lanes
   int conductors;  // some material is a conductor: the shading passes that handle them run
   int bvh8;        // the persistent passes walk the 8-wide BVH (every scene has one)
+  int two_level;   // the persistent passes walk the two-level BVH of an instanced scene
   // camera-ray order (null: chain order): wf_begin writes (key, chain) with
   // key = the pixel's Morton code (above it the scene of a batch chain)
   uint2* ray_keys;

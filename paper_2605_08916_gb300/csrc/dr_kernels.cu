@@ -226,20 +226,23 @@ __global__ void __launch_bounds__(kStepThreads) eval_kernel(EvalArgs a) {
   if (err) atomicOr(a.err, err);
 }
 
+template <int STACK>
 __global__ void __launch_bounds__(kStepThreads) trace_kernel(DevScene S, const float* __restrict__ rays, long long n,
                                                              int exclude, int* __restrict__ tri, float* __restrict__ t,
                                                              uint32_t* errp) {
   extern __shared__ int smem[];
-  TraceStack<kStack> st{smem + threadIdx.x, (int)blockDim.x};
+  TraceStack<STACK> st{smem + threadIdx.x, (int)blockDim.x};
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const float* r = rays + 6 * i;
   uint32_t err = 0;
   float th;
   const Ray ray = make_ray(f3(r[0], r[1], r[2]), f3(r[3], r[4], r[5]));
-  // the 8-wide BVH where the scene selects it (the persistent passes' walk)
-  const int h = S.nodes8 ? trace_closest<kStack, false, 8>(S, ray, exclude, &th, st, &err, nullptr)
-                         : trace_closest<kStack, false>(S, ray, exclude, &th, st, &err, nullptr);
+  // the two-level or 8-wide BVH where the scene selects it (the persistent
+  // passes' walk)
+  const int h = S.tl_nodes ? trace_closest<STACK, false, kWalkTwoLevel>(S, ray, exclude, &th, st, &err, nullptr)
+                : S.nodes8 ? trace_closest<STACK, false, 8>(S, ray, exclude, &th, st, &err, nullptr)
+                           : trace_closest<STACK, false>(S, ray, exclude, &th, st, &err, nullptr);
   tri[i] = h;
   t[i] = h >= 0 ? th : __int_as_float(0x7f800000);
   if (err) atomicOr(errp, err);
@@ -369,8 +372,12 @@ void launch_eval(const EvalArgs& a, cudaStream_t s) {
 void launch_trace(const DevScene& S, const float* rays, long long n, int exclude, int* tri, float* t, uint32_t* err,
                   cudaStream_t s) {
   if (n <= 0) return;
-  trace_kernel<<<(unsigned)((n + kStepThreads - 1) / kStepThreads), kStepThreads, step_smem_bytes(), s>>>(
-      S, rays, n, exclude, tri, t, err);
+  const unsigned g = (unsigned)((n + kStepThreads - 1) / kStepThreads);
+  if (S.tl_nodes)
+    trace_kernel<kTraversalStackTL><<<g, kStepThreads, (size_t)kTraversalStackTL * kStepThreads * sizeof(int), s>>>(
+        S, rays, n, exclude, tri, t, err);
+  else
+    trace_kernel<kStack><<<g, kStepThreads, step_smem_bytes(), s>>>(S, rays, n, exclude, tri, t, err);
 }
 
 void launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, long long n, cudaStream_t s) {

@@ -112,20 +112,22 @@ DR_D int i4c(int4 v, int k) { return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z 
 
 // Tests the triangles of one leaf against [tmin, tbest]; keeps the closest
 // (ties: smaller original id).
+// tris: the leaf-ordered triangle records of n_tris; id_base: added to each
+// record's id (the instance's first global id in a BLAS, else 0).
 template <bool STATS>
-DR_D void leaf_closest(const DevScene& S, int code, const Ray& r, int exclude, float& tbest, int& best, uint32_t* err,
-                       TraceStats* stats) {
+DR_D void leaf_closest_at(const float4* __restrict__ tris, int n_tris, int id_base, const DevScene& S, int code,
+                          const Ray& r, int exclude, float& tbest, int& best, uint32_t* err, TraceStats* stats) {
   const int first = leaf_first(code);
   int cnt = leaf_count(code);
-  if (first + cnt > S.n_tris) {
+  if (first + cnt > n_tris) {
     *err |= kErrBadIndex;
     cnt = 0;
   }
   for (int i = 0; i < cnt; ++i) {
-    const float4 t0 = __ldg(S.tris4 + 3 * (first + i) + 0);
-    const float4 t1 = __ldg(S.tris4 + 3 * (first + i) + 1);
-    const float4 t2 = __ldg(S.tris4 + 3 * (first + i) + 2);
-    const int id = __float_as_int(t0.w);
+    const float4 t0 = __ldg(tris + 3 * (first + i) + 0);
+    const float4 t1 = __ldg(tris + 3 * (first + i) + 1);
+    const float4 t2 = __ldg(tris + 3 * (first + i) + 2);
+    const int id = id_base + __float_as_int(t0.w);
     if (STATS) ++stats->tris;
     float th;
     if (id != exclude && tri_test(xyz(t0), xyz(t1), xyz(t2), r, S.tmin, tbest * 1.0000001f + 1e-30f, &th)) {
@@ -135,6 +137,34 @@ DR_D void leaf_closest(const DevScene& S, int code, const Ray& r, int exclude, f
       }
     }
   }
+}
+
+template <bool STATS>
+DR_D void leaf_closest(const DevScene& S, int code, const Ray& r, int exclude, float& tbest, int& best, uint32_t* err,
+                       TraceStats* stats) {
+  leaf_closest_at<STATS>(S.tris4, S.n_tris, 0, S, code, r, exclude, tbest, best, err, stats);
+}
+
+// Any hit among a leaf's triangles in (tmin, tmax), skipping two ids.
+template <bool STATS>
+DR_D bool leaf_any_at(const float4* __restrict__ tris, int n_tris, int id_base, const DevScene& S, int code,
+                      const Ray& r, float tmax, int ex0, int ex1, uint32_t* err, TraceStats* stats) {
+  const int first = leaf_first(code);
+  int cnt = leaf_count(code);
+  if (first + cnt > n_tris) {
+    *err |= kErrBadIndex;
+    cnt = 0;
+  }
+  for (int i = 0; i < cnt; ++i) {
+    const float4 t0 = __ldg(tris + 3 * (first + i) + 0);
+    const float4 t1 = __ldg(tris + 3 * (first + i) + 1);
+    const float4 t2 = __ldg(tris + 3 * (first + i) + 2);
+    const int id = id_base + __float_as_int(t0.w);
+    if (STATS) ++stats->tris;
+    float th;
+    if (id != ex0 && id != ex1 && tri_test(xyz(t0), xyz(t1), xyz(t2), r, S.tmin, tmax, &th)) return true;
+  }
+  return false;
 }
 
 // 4-wide traversal, one node per call so that a caller can interleave rays
@@ -157,8 +187,9 @@ DR_D Walk4 walk4_begin(const DevScene& S) { return Walk4{0, 0, min(5 * S.n_nodes
 // near distances subtract, and the far ones add, a margin of 2^-22 |o/d|
 // (more than the rounding): boxes are only ever widened, never missed, and
 // the closest hit is decided by the exact triangle tests.
-DR_D void node4_entries(const DevScene& S, int node, const Ray& r, float tmax, float e[4], int4& ch) {
-  const float4* nb = S.nodes4 + (size_t)kNode4F4 * node;
+DR_D void node4_entries_at(const float4* __restrict__ nodes, int node, const Ray& r, float tmax, float e[4],
+                           int4& ch) {
+  const float4* nb = nodes + (size_t)kNode4F4 * node;
   const int sx = r.inv.x < 0.0f, sy = r.inv.y < 0.0f, sz = r.inv.z < 0.0f;
   const float4 nx = __ldg(nb + sx), fx = __ldg(nb + 1 - sx);
   const float4 ny = __ldg(nb + 2 + sy), fy = __ldg(nb + 3 - sy);
@@ -179,27 +210,19 @@ DR_D void node4_entries(const DevScene& S, int node, const Ray& r, float tmax, f
   }
 }
 
-// One step of a closest-hit walk: an inner node (its hit children, leaves
-// and inner nodes alike, are taken nearest first: the nearest now, the
-// others pushed far-to-near) or a leaf (its triangles tested against the
-// closest hit so far).  Returns true when the walk is over (tbest / best
-// then hold the result).
+DR_D void node4_entries(const DevScene& S, int node, const Ray& r, float tmax, float e[4], int4& ch) {
+  node4_entries_at(S.nodes4, node, r, tmax, e, ch);
+}
+
+// A closest-hit walk's step at inner node w.node of `nodes`: hit children
+// (leaves and inner nodes alike) nearest first, the nearest next, the
+// others pushed far-to-near.  Returns true when the walk is over.
 template <int STACK, bool STATS>
-DR_D bool closest4_step(const DevScene& S, const Ray& r, int exclude, Walk4& w, float& tbest, int& best,
-                        TraceStack<STACK> st, uint32_t* err, TraceStats* stats) {
-  if (--w.budget < 0 || w.node >= S.n_nodes4) {
-    *err |= kErrBadIndex;
-    return true;
-  }
-  if (w.node < 0) {
-    leaf_closest<STATS>(S, w.node, r, exclude, tbest, best, err, stats);
-    if (w.sp == 0) return true;
-    w.node = st.at(--w.sp);
-    return false;
-  }
+DR_D bool closest4_inner(const float4* __restrict__ nodes, const Ray& r, Walk4& w, float tbest, TraceStack<STACK> st,
+                         uint32_t* err, TraceStats* stats) {
   int4 ch;
   float e[4];
-  node4_entries(S, w.node, r, tbest, e, ch);
+  node4_entries_at(nodes, w.node, r, tbest, e, ch);
   if (STATS) ++stats->nodes;
   bool ok[4];
   int nc = 0;
@@ -241,46 +264,15 @@ DR_D bool closest4_step(const DevScene& S, const Ray& r, int exclude, Walk4& w, 
   return false;
 }
 
-// One node of an any-hit walk in (tmin, tmax) skipping two triangle ids;
-// returns true when the walk is over, with *occluded set.
+// An any-hit walk's step at inner node w.node of `nodes`: the first hit
+// child next, the others pushed.
 template <int STACK, bool STATS>
-DR_D bool any4_step(const DevScene& S, const Ray& r, float tmax, int ex0, int ex1, Walk4& w, bool* occluded,
-                    TraceStack<STACK> st, uint32_t* err, TraceStats* stats) {
-  *occluded = false;
-  if (--w.budget < 0 || w.node >= S.n_nodes4) {
-    *err |= kErrBadIndex;
-    return true;
-  }
-  if (w.node < 0) {
-    // a leaf: any hit ends the walk
-    const int first = leaf_first(w.node);
-    int cnt = leaf_count(w.node);
-    if (first + cnt > S.n_tris) {
-      *err |= kErrBadIndex;
-      cnt = 0;
-    }
-    for (int i = 0; i < cnt; ++i) {
-      const float4 t0 = __ldg(S.tris4 + 3 * (first + i) + 0);
-      const float4 t1 = __ldg(S.tris4 + 3 * (first + i) + 1);
-      const float4 t2 = __ldg(S.tris4 + 3 * (first + i) + 2);
-      const int id = __float_as_int(t0.w);
-      if (STATS) ++stats->tris;
-      float th;
-      if (id != ex0 && id != ex1 && tri_test(xyz(t0), xyz(t1), xyz(t2), r, S.tmin, tmax, &th)) {
-        *occluded = true;
-        return true;
-      }
-    }
-    if (w.sp == 0) return true;
-    w.node = st.at(--w.sp);
-    return false;
-  }
+DR_D bool any4_inner(const float4* __restrict__ nodes, const Ray& r, float tmax, Walk4& w, TraceStack<STACK> st,
+                     uint32_t* err, TraceStats* stats) {
   int4 ch;
   float ent[4];
-  node4_entries(S, w.node, r, tmax, ent, ch);
+  node4_entries_at(nodes, w.node, r, tmax, ent, ch);
   if (STATS) ++stats->nodes;
-  // hit children, leaves and inner nodes alike: the first now, the others
-  // pushed (a step tests at most one leaf)
   int next = kBvh4Empty;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
@@ -301,6 +293,50 @@ DR_D bool any4_step(const DevScene& S, const Ray& r, float tmax, int ex0, int ex
   if (w.sp == 0) return true;
   w.node = st.at(--w.sp);
   return false;
+}
+
+// One step of a closest-hit walk: an inner node (its hit children, leaves
+// and inner nodes alike, are taken nearest first: the nearest now, the
+// others pushed far-to-near) or a leaf (its triangles tested against the
+// closest hit so far).  Returns true when the walk is over (tbest / best
+// then hold the result).
+template <int STACK, bool STATS>
+DR_D bool closest4_step(const DevScene& S, const Ray& r, int exclude, Walk4& w, float& tbest, int& best,
+                        TraceStack<STACK> st, uint32_t* err, TraceStats* stats) {
+  if (--w.budget < 0 || w.node >= S.n_nodes4) {
+    *err |= kErrBadIndex;
+    return true;
+  }
+  if (w.node < 0) {
+    leaf_closest<STATS>(S, w.node, r, exclude, tbest, best, err, stats);
+    if (w.sp == 0) return true;
+    w.node = st.at(--w.sp);
+    return false;
+  }
+  return closest4_inner<STACK, STATS>(S.nodes4, r, w, tbest, st, err, stats);
+}
+
+// One node of an any-hit walk in (tmin, tmax) skipping two triangle ids;
+// returns true when the walk is over, with *occluded set.
+template <int STACK, bool STATS>
+DR_D bool any4_step(const DevScene& S, const Ray& r, float tmax, int ex0, int ex1, Walk4& w, bool* occluded,
+                    TraceStack<STACK> st, uint32_t* err, TraceStats* stats) {
+  *occluded = false;
+  if (--w.budget < 0 || w.node >= S.n_nodes4) {
+    *err |= kErrBadIndex;
+    return true;
+  }
+  if (w.node < 0) {
+    // a leaf: any hit ends the walk
+    if (leaf_any_at<STATS>(S.tris4, S.n_tris, 0, S, w.node, r, tmax, ex0, ex1, err, stats)) {
+      *occluded = true;
+      return true;
+    }
+    if (w.sp == 0) return true;
+    w.node = st.at(--w.sp);
+    return false;
+  }
+  return any4_inner<STACK, STATS>(S.nodes4, r, tmax, w, st, err, stats);
 }
 
 template <int STACK, bool STATS>
@@ -714,6 +750,154 @@ DR_D bool trace_any8(const DevScene& S, const Ray& r, float tmax, int ex0, int e
   return occ;
 }
 
+// ---------------------------------------------------------------- two-level
+// Walk of a two-level BVH (instanced scenes): the 4-wide walk over the TLAS
+// in world space; a TLAS leaf (one instance) maps the ray into the
+// instance's object space (the parameter t is unchanged by the affine map),
+// pushes a return mark (kBvh4Empty) and continues at the instance's BLAS
+// root; popping the mark returns to the TLAS.  Hits are global triangle ids
+// (the instance's first id + the id within its mesh).
+struct WalkTL {
+  Walk4 w;    // node: a TLAS node at the top level, else a BLAS node
+  int inst;   // current instance; -1 at the top level
+  int tbase;  // global id of the instance's first triangle
+  Ray ro;     // the ray in the instance's object space
+};
+
+DR_D WalkTL walktl_begin(const DevScene&) {
+  WalkTL w;
+  w.w = Walk4{0, 0, kMaxNodeVisits};
+  w.inst = -1;
+  w.tbase = 0;
+  return w;
+}
+
+DR_D bool walktl_at_leaf(const WalkTL& w) { return w.w.node < 0; }
+
+// Enters instance `inst` from a TLAS leaf: object-space ray, return mark,
+// BLAS root.  Returns false on a bad record (the walk then ends).
+template <int STACK>
+DR_D bool walktl_enter(const DevScene& S, const Ray& r, WalkTL& w, TraceStack<STACK> st, uint32_t* err) {
+  const int inst = leaf_first(w.w.node);
+  if (inst >= S.n_insts) {
+    *err |= kErrBadIndex;
+    return false;
+  }
+  const float4* ir = S.insts + (size_t)kInstF4 * inst;
+  const float4 m0 = __ldg(ir), m1 = __ldg(ir + 1), m2 = __ldg(ir + 2);
+  const int4 i3 = __ldg(reinterpret_cast<const int4*>(ir + 3));
+  const float3 o = f3(fmaf(m0.x, r.o.x, fmaf(m0.y, r.o.y, fmaf(m0.z, r.o.z, m0.w))),
+                      fmaf(m1.x, r.o.x, fmaf(m1.y, r.o.y, fmaf(m1.z, r.o.z, m1.w))),
+                      fmaf(m2.x, r.o.x, fmaf(m2.y, r.o.y, fmaf(m2.z, r.o.z, m2.w))));
+  const float3 d = f3(fmaf(m0.x, r.d.x, fmaf(m0.y, r.d.y, m0.z * r.d.z)),
+                      fmaf(m1.x, r.d.x, fmaf(m1.y, r.d.y, m1.z * r.d.z)),
+                      fmaf(m2.x, r.d.x, fmaf(m2.y, r.d.y, m2.z * r.d.z)));
+  w.ro = make_ray(o, d);
+  w.inst = inst;
+  w.tbase = i3.y;
+  if (w.w.sp < STACK) {
+    st.at(w.w.sp++) = kBvh4Empty;
+  } else {
+    *err |= kErrStackOverflow;
+    return false;
+  }
+  w.w.node = i3.x;
+  return true;
+}
+
+// pops the next entry (a return mark switches back to the TLAS); true when
+// the walk is over
+template <int STACK>
+DR_D bool walktl_pop(WalkTL& w, TraceStack<STACK> st) {
+  while (true) {
+    if (w.w.sp == 0) return true;
+    w.w.node = st.at(--w.w.sp);
+    if (w.w.node != kBvh4Empty) return false;
+    w.inst = -1;
+  }
+}
+
+template <int STACK, bool STATS>
+DR_D bool closest_tl_step(const DevScene& S, const Ray& r, int exclude, WalkTL& w, float& tbest, int& best,
+                          TraceStack<STACK> st, uint32_t* err, TraceStats* stats) {
+  const bool top = w.inst < 0;
+  if (--w.w.budget < 0 || w.w.node >= (top ? S.n_tl_nodes : S.n_bl_nodes)) {
+    *err |= kErrBadIndex;
+    return true;
+  }
+  if (w.w.node < 0) {
+    if (top) return walktl_enter<STACK>(S, r, w, st, err) ? false : true;
+    leaf_closest_at<STATS>(S.bl_tris, S.n_bl_tris, w.tbase, S, w.w.node, w.ro, exclude, tbest, best, err, stats);
+    return walktl_pop<STACK>(w, st);
+  }
+  const int sp0 = w.w.sp;
+  const bool done = closest4_inner<STACK, STATS>(top ? S.tl_nodes : S.bl_nodes, top ? r : w.ro, w.w, tbest, st, err,
+                                                 stats);
+  // a pop inside the inner step may have taken a return mark
+  if (!done && w.w.sp < sp0 && w.w.node == kBvh4Empty) {
+    w.inst = -1;
+    return walktl_pop<STACK>(w, st);
+  }
+  return done;
+}
+
+template <int STACK, bool STATS>
+DR_D bool any_tl_step(const DevScene& S, const Ray& r, float tmax, int ex0, int ex1, WalkTL& w, bool* occluded,
+                      TraceStack<STACK> st, uint32_t* err, TraceStats* stats) {
+  *occluded = false;
+  const bool top = w.inst < 0;
+  if (--w.w.budget < 0 || w.w.node >= (top ? S.n_tl_nodes : S.n_bl_nodes)) {
+    *err |= kErrBadIndex;
+    return true;
+  }
+  if (w.w.node < 0) {
+    if (top) return walktl_enter<STACK>(S, r, w, st, err) ? false : true;
+    if (leaf_any_at<STATS>(S.bl_tris, S.n_bl_tris, w.tbase, S, w.w.node, w.ro, tmax, ex0, ex1, err, stats)) {
+      *occluded = true;
+      return true;
+    }
+    return walktl_pop<STACK>(w, st);
+  }
+  const int sp0 = w.w.sp;
+  const bool done = any4_inner<STACK, STATS>(top ? S.tl_nodes : S.bl_nodes, top ? r : w.ro, tmax, w.w, st, err, stats);
+  if (!done && w.w.sp < sp0 && w.w.node == kBvh4Empty) {
+    w.inst = -1;
+    return walktl_pop<STACK>(w, st);
+  }
+  return done;
+}
+
+template <int STACK, bool STATS>
+DR_D int trace_closest_tl(const DevScene& S, const Ray& r, int exclude, float* t_hit, TraceStack<STACK> st,
+                          uint32_t* err, TraceStats* stats) {
+  float tbest = __int_as_float(0x7f800000);
+  int best = -1;
+  if (!ray_finite(r.o, r.d)) {
+    *err |= kErrNonFinite;
+    *t_hit = tbest;
+    return -1;
+  }
+  WalkTL w = walktl_begin(S);
+  while (!closest_tl_step<STACK, STATS>(S, r, exclude, w, tbest, best, st, err, stats)) {
+  }
+  *t_hit = tbest;
+  return best;
+}
+
+template <int STACK, bool STATS>
+DR_D bool trace_any_tl(const DevScene& S, const Ray& r, float tmax, int ex0, int ex1, TraceStack<STACK> st,
+                       uint32_t* err, TraceStats* stats) {
+  if (!ray_finite(r.o, r.d)) {
+    *err |= kErrNonFinite;
+    return true;
+  }
+  WalkTL w = walktl_begin(S);
+  bool occ = false;
+  while (!any_tl_step<STACK, STATS>(S, r, tmax, ex0, ex1, w, &occ, st, err, stats)) {
+  }
+  return occ;
+}
+
 // Width-generic walk interface of the persistent passes.
 template <int WIDTH>
 struct WalkOf {
@@ -723,10 +907,27 @@ template <>
 struct WalkOf<8> {
   using type = Walk8;
 };
+constexpr int kWalkTwoLevel = 1;  // the WIDTH of the two-level walk
+template <>
+struct WalkOf<kWalkTwoLevel> {
+  using type = WalkTL;
+};
 DR_D void walk_begin(const DevScene& S, const Ray&, Walk4& w) { w = walk4_begin(S); }
 DR_D void walk_begin(const DevScene& S, const Ray& r, Walk8& w) { w = walk8_begin(S, r); }
 DR_D bool walk_at_leaf(const Walk4& w) { return w.node < 0; }
 DR_D bool walk_at_leaf(const Walk8& w) { return w.tbits != 0u; }
+DR_D void walk_begin(const DevScene& S, const Ray&, WalkTL& w) { w = walktl_begin(S); }
+DR_D bool walk_at_leaf(const WalkTL& w) { return walktl_at_leaf(w); }
+template <int STACK, bool STATS>
+DR_D bool closest_step(const DevScene& S, const Ray& r, int exclude, WalkTL& w, float& tbest, int& best,
+                       TraceStack<STACK> st, uint32_t* err, TraceStats* stats) {
+  return closest_tl_step<STACK, STATS>(S, r, exclude, w, tbest, best, st, err, stats);
+}
+template <int STACK, bool STATS>
+DR_D bool any_step(const DevScene& S, const Ray& r, float tmax, int ex0, int ex1, WalkTL& w, bool* occluded,
+                   TraceStack<STACK> st, uint32_t* err, TraceStats* stats) {
+  return any_tl_step<STACK, STATS>(S, r, tmax, ex0, ex1, w, occluded, st, err, stats);
+}
 template <int STACK, bool STATS>
 DR_D bool closest_step(const DevScene& S, const Ray& r, int exclude, Walk4& w, float& tbest, int& best,
                        TraceStack<STACK> st, uint32_t* err, TraceStats* stats) {
@@ -755,6 +956,7 @@ template <int STACK, bool STATS, int WIDTH = 0>
 DR_D int trace_closest(const DevScene& S, const Ray& r, int exclude, float* t_hit, TraceStack<STACK> st,
                        uint32_t* err, TraceStats* stats) {
   if (WIDTH == 8) return trace_closest8<STACK, STATS>(S, r, exclude, t_hit, st, err, stats);
+  if (WIDTH == kWalkTwoLevel) return trace_closest_tl<STACK, STATS>(S, r, exclude, t_hit, st, err, stats);
   if (WIDTH == 4 || (WIDTH == 0 && S.nodes4 != nullptr))
     return trace_closest4<STACK, STATS>(S, r, exclude, t_hit, st, err, stats);
   return trace_closest2<STACK, STATS>(S, r, exclude, t_hit, st, err, stats);
@@ -764,6 +966,7 @@ template <int STACK, bool STATS, int WIDTH = 0>
 DR_D bool trace_any(const DevScene& S, const Ray& r, float tmax, int ex0, int ex1, TraceStack<STACK> st,
                     uint32_t* err, TraceStats* stats) {
   if (WIDTH == 8) return trace_any8<STACK, STATS>(S, r, tmax, ex0, ex1, st, err, stats);
+  if (WIDTH == kWalkTwoLevel) return trace_any_tl<STACK, STATS>(S, r, tmax, ex0, ex1, st, err, stats);
   if (WIDTH == 4 || (WIDTH == 0 && S.nodes4 != nullptr))
     return trace_any4<STACK, STATS>(S, r, tmax, ex0, ex1, st, err, stats);
   return trace_any2<STACK, STATS>(S, r, tmax, ex0, ex1, st, err, stats);

@@ -26,6 +26,10 @@ namespace {
 
 constexpr int kWfThreads = 128;
 constexpr int kWfStack = kTraversalStack;
+// stack entries of the persistent passes per walk
+constexpr int wf_stack(int width) { return width == kWalkTwoLevel ? kTraversalStackTL : kWfStack; }
+// (the two-level traversal's larger stack leaves room for 6 blocks per SM,
+// so it is compiled for 6 and may use more registers)
 // resident blocks per SM the traversal passes are compiled for (register cap)
 constexpr int kWfTraceMinBlocks = 10;
 // the 4-wide traversal holds four child boxes at once: fewer resident
@@ -210,9 +214,11 @@ DR_D uint32_t warp_fetch(uint32_t* ctr, unsigned idle, uint32_t n, bool& drained
 // path's f and the shadow-visibility tape flag), so one launch replaces two
 // and each bounce pays the latency of its slowest ray once.
 template <bool STATS, bool BATCH, int WIDTH>
-__global__ void __launch_bounds__(kWfThreads, kWfTrace4MinBlocks) wf_traverse(StepArgs a, WfBuffers w, int k) {
+__global__ void __launch_bounds__(kWfThreads, WIDTH == kWalkTwoLevel ? 6 : kWfTrace4MinBlocks)
+    wf_traverse(StepArgs a, WfBuffers w, int k) {
   extern __shared__ int smem[];
-  TraceStack<kWfStack> st{smem + threadIdx.x, (int)blockDim.x};
+  constexpr int kS = wf_stack(WIDTH);
+  TraceStack<kS> st{smem + threadIdx.x, (int)blockDim.x};
   const uint32_t n_ray = k <= a.L ? w.counts[k] : 0u;
   const uint32_t n_shadow = k >= 2 ? w.counts[kWfShadowCount0 + k - 1] : 0u;
   const uint32_t n = n_ray + n_shadow;
@@ -278,13 +284,13 @@ __global__ void __launch_bounds__(kWfThreads, kWfTrace4MinBlocks) wf_traverse(St
       if (has && lf == leaf_phase) {
         const DevScene& S = scene_of<BATCH>(a, sid);
         if (!shadow) {
-          if (closest_step<kWfStack, STATS>(S, r, ex0, wk, tlim, best, st, &err, &stats)) {
+          if (closest_step<kS, STATS>(S, r, ex0, wk, tlim, best, st, &err, &stats)) {
             w.hit[j] = best;
             has = false;
           }
         } else {
           bool occ;
-          if (any_step<kWfStack, STATS>(S, r, tlim, ex0, ex1, wk, &occ, st, &err, &stats)) {
+          if (any_step<kS, STATS>(S, r, tlim, ex0, ex1, wk, &occ, st, &err, &stats)) {
             has = false;
             if (!occ) {
               const ShadowRec& sr = w.shadow[t];
@@ -371,7 +377,8 @@ constexpr int kWfTailMinBlocks = 4;
 template <bool STATS, bool BATCH, bool COND, int WIDTH>
 __global__ void __launch_bounds__(kWfThreads, kWfTailMinBlocks) wf_tail(StepArgs a, WfBuffers w, int k0) {
   extern __shared__ int smem[];
-  TraceStack<kWfStack> st{smem + threadIdx.x, (int)blockDim.x};
+  constexpr int kS = wf_stack(WIDTH);
+  TraceStack<kS> st{smem + threadIdx.x, (int)blockDim.x};
   enum { kIdle = 0, kShade, kClosest, kShadow };
   const uint32_t n = w.counts[k0];
   const uint32_t* q = k0 == 1 && !a.ray_keys ? nullptr : w.queue[k0 & 1];
@@ -462,7 +469,7 @@ __global__ void __launch_bounds__(kWfThreads, kWfTailMinBlocks) wf_tail(StepArgs
         }
       } else if (state == kShadow && !do_shade) {
         bool occ;
-        if (any_step<kWfStack, STATS>(S, r, tlim, ex0, ex1, wk, &occ, st, &err, &stats)) {
+        if (any_step<kS, STATS>(S, r, tlim, ex0, ex1, wk, &occ, st, &err, &stats)) {
           if (!occ) {
             ps.f += contrib;
             GlobalTape{w.tape, a.N, j}.or_flags(k - 1, kFNeeVis);
@@ -488,7 +495,7 @@ __global__ void __launch_bounds__(kWfThreads, kWfTailMinBlocks) wf_tail(StepArgs
           }
         }
       } else if (state == kClosest && !do_shade) {
-        if (closest_step<kWfStack, STATS>(S, r, ex0, wk, tlim, best, st, &err, &stats)) {
+        if (closest_step<kS, STATS>(S, r, ex0, wk, tlim, best, st, &err, &stats)) {
           hit = best;
           state = kShade;
         }
@@ -668,7 +675,7 @@ int launch_wf(const StepArgs& a, const WfBuffers& w, bool stats, int n_sm, const
     hook(kPhFinish, false);
     return 1;
   }
-  const size_t smem = (size_t)kWfStack * kWfThreads * sizeof(int);
+  const size_t smem = (size_t)wf_stack(WIDTH) * kWfThreads * sizeof(int);
   const bool wide = a.S.nodes4 != nullptr || BATCH;
   // persistent traversal: as many blocks as stay resident (or fewer, tuned)
   const int resident = traverse_blocks_per_sm<BATCH, WIDTH>(smem);
@@ -771,7 +778,12 @@ int launch_wavefront_step(const StepArgs& a, const WfBuffers& w, bool stats, int
   b.ray_keys = order.keys;
   // kernels with the conductor branches run only for scenes that have
   // conductors (the branches cost registers and code in every kernel);
-  // the persistent passes walk the 8-wide BVH where it was built
+  // the persistent passes walk the two-level or the 8-wide BVH where the
+  // scene selects it
+  if (a.two_level && !a.scenes) {
+    if (a.conductors) return launch_wf<false, true, kWalkTwoLevel>(b, w, stats, n_sm, tune, hook, s, mode, p_out, order);
+    return launch_wf<false, false, kWalkTwoLevel>(b, w, stats, n_sm, tune, hook, s, mode, p_out, order);
+  }
   if (a.bvh8) {
     if (a.conductors)
       return a.scenes ? launch_wf<true, true, 8>(b, w, stats, n_sm, tune, hook, s, mode, p_out, order)

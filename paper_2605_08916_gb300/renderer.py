@@ -72,11 +72,13 @@ class Renderer:
     def set_option(self, option, value):
         """option: "wavefront" (-1 auto / 0 / 1), "work_order" (0/1), "profile" (0/1) or
         "bvh_width" (0 automatic / 2 / 4 / 8; 8 before the upload), "traverse_blocks" (0 = all resident),
-        "refill" (1..32), "ray_order" (-1 automatic / 0 / 1) or "tail_bounce" (-1 automatic, 0 off, k)."""
+        "refill" (1..32), "ray_order" (-1 automatic / 0 / 1), "tail_bounce" (-1 automatic, 0 off, k) or
+        "two_level" (1: walk an instanced scene's two-level BVH, 0: its flattened BVH)."""
         code = {"work_order": _lib.DR_OPT_WORK_ORDER, "wavefront": _lib.DR_OPT_WAVEFRONT,
                 "profile": _lib.DR_OPT_PROFILE, "bvh_width": _lib.DR_OPT_BVH_WIDTH,
                 "traverse_blocks": _lib.DR_OPT_TRAVERSE_BLOCKS, "refill": _lib.DR_OPT_REFILL,
-                "ray_order": _lib.DR_OPT_RAY_ORDER, "tail_bounce": _lib.DR_OPT_TAIL_BOUNCE}[option]
+                "ray_order": _lib.DR_OPT_RAY_ORDER, "tail_bounce": _lib.DR_OPT_TAIL_BOUNCE,
+                "two_level": _lib.DR_OPT_TWO_LEVEL}[option]
         call("dr_set_option", self.h, code, int(value))
 
     def set_bvh_builder(self, builder="ploc", radius=16):
@@ -93,6 +95,41 @@ class Renderer:
              m.shape[0], _ptr(cam), int(scene.width), int(scene.height))
         self.width, self.height = int(scene.width), int(scene.height)
         self.kind = 0
+
+    def upload_instanced(self, iscene):
+        """An instanced scene (scenes.InstancedScene): meshes placed by affine
+        maps; the library flattens it (the scene it renders) and, with two or
+        more instances, builds a two-level BVH as well."""
+        keep = []
+        meshes = (_lib.dr_mesh_desc * len(iscene.meshes))()
+        for i, mesh in enumerate(iscene.meshes):
+            v = np.ascontiguousarray(mesh.verts, np.float32)
+            t = np.ascontiguousarray(mesh.tris, np.int32)
+            nr = None if mesh.normals is None else np.ascontiguousarray(mesh.normals, np.float32)
+            tm = np.ascontiguousarray(mesh.tri_mat, np.int32)
+            keep += [v, t, nr, tm]
+            meshes[i] = _lib.dr_mesh_desc(v.ctypes.data, v.shape[0], t.ctypes.data, t.shape[0],
+                                          None if nr is None else nr.ctypes.data, tm.ctypes.data)
+        insts = (_lib.dr_instance_desc * len(iscene.instances))()
+        for i, (mesh, mat, xf) in enumerate(iscene.instances):
+            insts[i] = _lib.dr_instance_desc(int(mesh), int(mat),
+                                             (C.c_float * 12)(*np.asarray(xf, np.float32).ravel().tolist()))
+        m = np.ascontiguousarray(iscene.materials, np.float32)
+        cam = np.ascontiguousarray(iscene.camera, np.float32)
+        call("dr_scene_upload_instanced", self.h, meshes, len(iscene.meshes), insts, len(iscene.instances),
+             _ptr(m), m.shape[0], _ptr(cam), int(iscene.width), int(iscene.height))
+        self.width, self.height = int(iscene.width), int(iscene.height)
+        self.kind = 0
+        del keep
+
+    def two_level_info(self):
+        """Instances, TLAS nodes and BLAS nodes of the two-level BVH, or None."""
+        a, b, c = C.c_int32(), C.c_int32(), C.c_int32()
+        r = _lib.load().dr_two_level_info(self.h, C.byref(a), C.byref(b), C.byref(c))
+        if r == _lib.DR_ERR_STATE:
+            return None
+        _lib.check(r, "dr_two_level_info")
+        return {"n_instances": a.value, "n_tlas_nodes": b.value, "n_blas_nodes": c.value}
 
     def upload_scenes(self, items):
         """A multi-scene batch: items = [(scene, max_path_len, n_chains), ...].

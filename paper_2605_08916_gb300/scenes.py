@@ -351,6 +351,173 @@ def procedural_scene(seed=1, width=1280, height=720, target_tris=1_000_000, n_ob
     return b.build(cam, width, height, f"procedural-{target_tris}-{width}x{height}")
 
 
+@dataclasses.dataclass
+class Mesh:
+    """Object-space triangle mesh of an instanced scene."""
+    verts: np.ndarray              # [nv, 3] float32
+    tris: np.ndarray               # [nt, 3] int32
+    tri_mat: np.ndarray            # [nt] int32
+    normals: np.ndarray = None     # [nv, 3] float32 or None (flat)
+
+
+@dataclasses.dataclass
+class InstancedScene:
+    """Meshes placed by instances (mesh index, material or -1 for the mesh's
+    own, row-major 3 x 4 object-to-world affine map).  The scene is its
+    flattening (``flatten``), which both sides render."""
+    meshes: list
+    instances: list
+    materials: np.ndarray
+    camera: np.ndarray
+    width: int
+    height: int
+    name: str = "instanced"
+
+    @property
+    def n_tris(self):
+        return sum(len(self.meshes[m].tris) for m, _, _ in self.instances)
+
+    def flatten(self):
+        """The flat scene: instance after instance, vertex p -> ((a0 p.x +
+        a1 p.y) + a2 p.z) + t per row in FP64 rounded to float32; normals by
+        the inverse transpose (the inverse by cofactors over the
+        determinant); a mesh without normals gets zero (flat) normals."""
+        V, T, M, N = [], [], [], []
+        any_n = any(self.meshes[m].normals is not None for m, _, _ in self.instances)
+        vb = 0
+        for mesh_i, mat, xf in self.instances:
+            mesh = self.meshes[mesh_i]
+            A = np.asarray(xf, np.float32).astype(np.float64).reshape(3, 4)
+            p = mesh.verts.astype(np.float64)
+            w = np.empty_like(p)
+            for r in range(3):
+                w[:, r] = A[r, 0] * p[:, 0] + A[r, 1] * p[:, 1] + A[r, 2] * p[:, 2] + A[r, 3]
+            V.append(w.astype(np.float32))
+            T.append(mesh.tris.astype(np.int64) + vb)
+            M.append(np.full(len(mesh.tris), mat) if mat >= 0 else mesh.tri_mat.astype(np.int64))
+            if any_n:
+                if mesh.normals is None:
+                    N.append(np.zeros_like(p, dtype=np.float32))
+                else:
+                    Mi = _inverse3(A[:, :3])
+                    n = mesh.normals.astype(np.float64)
+                    nw = np.empty_like(n)
+                    for r in range(3):
+                        nw[:, r] = Mi[0, r] * n[:, 0] + Mi[1, r] * n[:, 1] + Mi[2, r] * n[:, 2]
+                    N.append(nw.astype(np.float32))
+            vb += len(p)
+        return Scene(np.concatenate(V), np.concatenate(T).astype(np.int32), np.concatenate(M).astype(np.int32),
+                     np.asarray(self.materials, np.float32), np.asarray(self.camera, np.float32), self.width,
+                     self.height, np.concatenate(N) if any_n else None, self.name + "-flat").check()
+
+
+def _inverse3(a):
+    """Inverse of a 3 x 3 matrix by cofactors over the determinant (FP64)."""
+    a00, a01, a02 = a[0]
+    a10, a11, a12 = a[1]
+    a20, a21, a22 = a[2]
+    c00 = a11 * a22 - a12 * a21
+    c01 = a12 * a20 - a10 * a22
+    c02 = a10 * a21 - a11 * a20
+    det = a00 * c00 + a01 * c01 + a02 * c02
+    return np.array([[c00 / det, (a02 * a21 - a01 * a22) / det, (a01 * a12 - a02 * a11) / det],
+                     [c01 / det, (a00 * a22 - a02 * a20) / det, (a02 * a10 - a00 * a12) / det],
+                     [c02 / det, (a01 * a20 - a00 * a21) / det, (a00 * a11 - a01 * a10) / det]])
+
+
+def procedural_scene_instanced(seed=1, width=1280, height=720, target_tris=1_000_000, n_objects=200,
+                               object_res=(12, 16), terrain_chunks=4):
+    """The procedural scene's layout (same seed draws, same terrain, same
+    lights) with its objects as instances: one unit sphere mesh and one unit
+    box mesh placed by scale-and-translate maps, one material per instance;
+    the terrain (as terrain_chunks x terrain_chunks tiles, so that no one
+    mesh's hierarchy is deep) and the lights are meshes with the identity
+    map.  With terrain_chunks = 1 its flattening lists the triangles in the
+    flat generator's order."""
+    rng = np.random.default_rng(seed)
+    ext = 20.0
+    nt_th, nt_ph = object_res
+    sphere_tris = 2 * nt_ph * (nt_th - 1)
+    n_sph = n_objects // 2
+    n_box = n_objects - n_sph
+    obj_tris = n_sph * sphere_tris + n_box * 12
+    terr_tris = max(2, target_tris - obj_tris - 8)
+    g = max(2, int(round(math.sqrt(terr_tris / 2.0))))
+    xs = np.linspace(-ext, ext, g + 1)
+    X, Z = np.meshgrid(xs, xs, indexing="xy")
+    phases = [(rng.uniform(0, 2 * math.pi), rng.uniform(0, 2 * math.pi), rng.uniform(0, math.pi))
+              for _ in range(8)]
+    Y = 1.2 * _fbm(X * 0.25, Z * 0.25, phases)
+    verts = np.stack([X.ravel(), Y.ravel(), Z.ravel()], 1)
+    idx = np.arange((g + 1) * (g + 1)).reshape(g + 1, g + 1)
+    a = idx[:-1, :-1].ravel()
+    bb = idx[:-1, 1:].ravel()
+    c = idx[1:, 1:].ravel()
+    d = idx[1:, :-1].ravel()
+    mats = [material(MAT_DIFFUSE, (0.45, 0.42, 0.38))]
+    ident = [1.0, 0.0, 0.0, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0, 0.0, 1.0, 0.0]
+    meshes, instances = [], []
+    cuts = np.linspace(0, g, terrain_chunks + 1).round().astype(int)
+    for ci in range(terrain_chunks):
+        for cj in range(terrain_chunks):
+            r0, r1, c0, c1 = cuts[ci], cuts[ci + 1], cuts[cj], cuts[cj + 1]
+            sub = idx[r0:r1 + 1, c0:c1 + 1]
+            remap = sub.ravel()
+            loc = np.arange(remap.size).reshape(sub.shape)
+            la, lb, lc, ld = loc[:-1, :-1].ravel(), loc[:-1, 1:].ravel(), loc[1:, 1:].ravel(), loc[1:, :-1].ravel()
+            t = np.concatenate([np.stack([la, ld, lc], 1), np.stack([la, lc, lb], 1)])
+            meshes.append(Mesh(verts[remap].astype(np.float32), t.astype(np.int32), np.zeros(len(t), np.int32)))
+            instances.append((len(meshes) - 1, -1, ident))
+    sphere_mesh, box_mesh = len(meshes), len(meshes) + 1
+    sv, st, sn = uv_sphere((0.0, 0.0, 0.0), 1.0, nt_th, nt_ph)
+    meshes.append(Mesh(sv.astype(np.float32), st.astype(np.int32), np.zeros(len(st), np.int32),
+                       sn.astype(np.float32)))
+    bv, bt = [], []
+    for f in _box_faces((-1.0, -1.0, -1.0), (1.0, 1.0, 1.0), bottomless=False):
+        k = len(bv)
+        bv.extend(f)
+        bt.extend([[k, k + 1, k + 2], [k, k + 2, k + 3]])
+    meshes.append(Mesh(np.array(bv, np.float32), np.array(bt, np.int32), np.zeros(len(bt), np.int32)))
+
+    def height_at(x, z):
+        return float(1.2 * _fbm(np.array([x * 0.25]), np.array([z * 0.25]), phases)[0])
+
+    def obj_material():
+        r = rng.integers(0, 3)
+        if r == 0:
+            return material(MAT_DIFFUSE, rng.uniform(0.2, 0.8, 3))
+        if r == 1:
+            return material(MAT_GLOSSY, rng.uniform(0.2, 0.8, 3), roughness=rng.uniform(0.05, 0.3))
+        return material(MAT_DIELECTRIC, ior=1.5)
+
+    for k in range(n_objects):
+        x, z = rng.uniform(-0.8 * ext, 0.8 * ext, 2)
+        size = rng.uniform(0.3, 1.2)
+        y = height_at(x, z)
+        mats.append(obj_material())
+        m = len(mats) - 1
+        if k < n_sph:
+            instances.append((sphere_mesh, m, [size, 0.0, 0.0, x, 0.0, size, 0.0, y + size, 0.0, 0.0, size, z]))
+        else:
+            lo = np.array([x - size, y - 0.2, z - size])
+            hi = np.array([x + size, y + 1.6 * size, z + size])
+            cc, hh = (lo + hi) / 2, (hi - lo) / 2
+            instances.append((box_mesh, m, [hh[0], 0.0, 0.0, cc[0], 0.0, hh[1], 0.0, cc[1], 0.0, 0.0, hh[2], cc[2]]))
+    lv, lt, lm = [], [], []
+    for (cx, cz) in [(-8.0, -8.0), (8.0, -8.0), (-8.0, 8.0), (8.0, 8.0)]:
+        mats.append(material(MAT_EMITTER, emission=rng.uniform(20.0, 40.0, 3)))
+        h, sz = 14.0, 2.5
+        k = len(lv)
+        lv.extend([(cx - sz, h, cz - sz), (cx + sz, h, cz - sz), (cx + sz, h, cz + sz), (cx - sz, h, cz + sz)])
+        lt.extend([[k, k + 1, k + 2], [k, k + 2, k + 3]])
+        lm.extend([len(mats) - 1] * 2)
+    meshes.append(Mesh(np.array(lv, np.float32), np.array(lt, np.int32), np.array(lm, np.int32)))
+    instances.append((len(meshes) - 1, -1, ident))
+    cam = [0.0, 9.0, 24.0, 0.0, 0.0, 0.0, 0.0, 1.0, 0.0, 50.0]
+    return InstancedScene(meshes, instances, np.stack(mats).astype(np.float32), np.asarray(cam, np.float32),
+                          int(width), int(height), f"procedural-instanced-{target_tris}-{width}x{height}")
+
+
 def procedural_batch(n_scenes=64, total_chains=1 << 21, seed=2605, tris_range=(1_000, 200_000),
                      size_range=(128, 512), L_range=(4, 16)):
     """The multi-scene workload: ``n_scenes`` variants of the procedural

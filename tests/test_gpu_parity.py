@@ -817,3 +817,133 @@ def test_zero_steps_and_size_limits(torch, R):
     assert np.array_equal(before, r.readback_state(("x",))["x"])
     assert r.counters()["steps"] == 0
     r.close()
+
+
+def small_instanced():
+    return S.procedural_scene_instanced(1, 64, 36, target_tris=60000, n_objects=40)
+
+
+def test_instanced_upload_is_its_flattening(torch, R):
+    """The library's flattening of an instanced scene equals the one the
+    oracle takes (same FP64 formulas, no contraction): with the two-level
+    walk off, chains on the instanced upload and on the flat upload of the
+    Python flattening are bit-identical."""
+    isc = small_instanced()
+    out = []
+    for inst in (True, False):
+        r = R.Renderer()
+        r.set_option("wavefront", 1)
+        if inst:
+            r.set_option("two_level", 0)
+            r.upload_instanced(isc)
+            assert r.two_level_info() is not None  # built, not walked
+        else:
+            r.upload_scene(isc.flatten())
+        r.init_chains(16384, 41, R.make_params(L=12, drift="adjoint", k0=0.0, steps_per_splat=4))
+        r.step(6)
+        out.append(r.readback_state())
+        r.close()
+    a, b = out
+    for k in ("x", "killed", "logp", "score", "pix"):
+        assert np.array_equal(a[k], b[k]), k
+
+
+def test_two_level_hits_match_flat_and_oracle(torch, R, oracle):
+    """Rays through the two-level BVH (object-space triangle tests) hit the
+    same triangles as the flattened scene's BVH and the oracle, up to hits
+    on shared edges; distances agree to the FP32 rounding of the mapped
+    rays."""
+    isc = small_instanced()
+    flat = isc.flatten()
+    o, d = random_rays(flat, 20000, 5)
+    rays = torch.from_numpy(np.concatenate([o, d], 1)).cuda()
+    r = R.Renderer()
+    r.set_option("two_level", 1)
+    r.upload_instanced(isc)
+    info = r.two_level_info()
+    assert info is not None and info["n_instances"] == len(isc.instances)
+    tri_t, t_t = r.trace_closest(rays)
+    r.close()
+    r = R.Renderer()
+    r.upload_scene(flat)
+    tri_f, t_f = r.trace_closest(rays)
+    r.close()
+    torch.cuda.synchronize()
+    tri_t, t_t, tri_f, t_f = tri_t.cpu().numpy(), t_t.cpu().numpy(), tri_f.cpu().numpy(), t_f.cpu().numpy()
+    same = tri_t == tri_f
+    assert same.mean() >= 0.999, same.mean()
+    hit = same & (tri_f >= 0)
+    # object-space distances carry the rounding of the mapped ray origin
+    assert np.allclose(t_t[hit], t_f[hit], rtol=1e-4, atol=1e-5)
+    tri_o, t_o = oracle.OracleScene(flat).trace(o.astype(np.float64), d.astype(np.float64))
+    assert (tri_t == tri_o).mean() >= 0.999
+
+
+@pytest.mark.parametrize("tail", [0, 4])
+def test_two_level_chains_match_the_flat_walk(torch, R, tail):
+    """Restore steps walking the two-level BVH vs the flattened BVH of the
+    same instanced upload: the hit point and shading always come from the
+    flattened triangle, so chains whose hits agree are bit-identical."""
+    isc = small_instanced()
+    out = []
+    for tl in (1, 0):
+        r = R.Renderer()
+        r.set_option("wavefront", 1)
+        r.set_option("two_level", tl)
+        r.set_option("tail_bounce", tail)
+        r.upload_instanced(isc)
+        r.init_chains(16384, 43, R.make_params(L=12, drift="adjoint", k0=0.0, steps_per_splat=4))
+        r.step(9)
+        out.append((r.readback_state(), r.readback_accum()))
+        r.close()
+    (a, acc_a), (b, acc_b) = out
+    same = (a["killed"] == b["killed"]) & (a["pix"] == b["pix"]) & np.all(a["x"] == b["x"], 1)
+    same &= a["logp"] == b["logp"]
+    print(f"bit-identical chains {same.mean():.5f}")
+    assert same.mean() >= 0.999
+    assert np.allclose(acc_a, acc_b, rtol=1e-3, atol=1e-9 * np.abs(acc_a).max())
+
+
+def test_chain_parity_instanced_two_level(torch, R, oracle):
+    """An instanced scene on the two-level walk against the oracle on its
+    flattening, 16-step horizons."""
+    isc = small_instanced()
+    flat = isc.flatten()
+    k0 = 1e6
+    pg = R.make_params(L=8, drift="adjoint", rb=True, k0=k0, steps_per_splat=16)
+    po = oracle.make_params(L=8, drift="exact", rb=True, k0=k0)
+    orig = R.Renderer
+
+    class _R(orig):
+        def upload_scene(self, scene):
+            self.set_option("wavefront", 1)
+            self.set_option("two_level", 1)
+            self.upload_instanced(isc)
+
+    R.Renderer = _R
+    try:
+        frac, first, n = _chain_parity(torch, R, oracle, flat, pg, po, N=16384, M=512, T=16, seed=12)
+    finally:
+        R.Renderer = orig
+    print("instanced two-level divergent fraction", frac, "compared", n)
+    assert frac <= 0.01
+
+
+def test_instanced_upload_errors(torch, R):
+    from paper_2605_08916_gb300 import _lib
+    isc = small_instanced()
+    bad = S.InstancedScene(isc.meshes, [(0, -1, [0.0] * 12)] + isc.instances[1:], isc.materials, isc.camera,
+                           isc.width, isc.height)
+    r = R.Renderer()
+    with pytest.raises(_lib.DRError) as e:
+        r.upload_instanced(bad)  # singular map
+    assert e.value.code == _lib.DR_ERR_INVALID_ARG
+    bad = S.InstancedScene(isc.meshes, [(len(isc.meshes), -1, isc.instances[0][2])], isc.materials, isc.camera,
+                           isc.width, isc.height)
+    with pytest.raises(_lib.DRError) as e:
+        r.upload_instanced(bad)  # mesh index out of range
+    assert e.value.code == _lib.DR_ERR_INVALID_ARG
+    r.upload_instanced(isc)
+    r.init_chains(64, 1, R.make_params(L=3, drift="adjoint", k0=100.0))
+    r.step(2)
+    r.close()
