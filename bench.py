@@ -276,6 +276,8 @@ def run_ours(args, wl, rank, world, local):
     r.set_option("bvh_width", args.bvh_width)
     r.set_option("ray_order", args.ray_order)
     r.set_option("two_level", args.two_level)
+    if args.ploc_radius:
+        r.set_bvh_builder("ploc", args.ploc_radius)
     if args.tail_bounce is not None:
         r.set_option("tail_bounce", args.tail_bounce)
     upload(r, scene)
@@ -672,6 +674,8 @@ def main():
                     help="run the bounces from this one on as one persistent pass (0 off; default: library's choice)")
     ap.add_argument("--ray-order", type=int, default=-1, choices=[-1, 0, 1],
                     help="sort camera rays by pixel before the first traversal (-1: by triangle count)")
+    ap.add_argument("--ploc-radius", type=int, default=0,
+                    help="PLOC search radius of the BVH build (0: the library default, 16)")
     ap.add_argument("--two-level", type=int, default=0, choices=[0, 1],
                     help="instanced workloads: walk the two-level BVH (1) or the flattened one (0)")
     ap.add_argument("--bvh-width", type=int, default=0, choices=[0, 2, 4, 8],

@@ -186,11 +186,12 @@ typedef struct {
  * transpose (the inverse by cofactors over the determinant, in FP64);
  * triangle ids are the flattened order (instance-major); a mesh without
  * normals is flat-shaded.  Everything dr_scene_upload builds is built for
- * the flattened scene; in addition, with at least 2 instances, a two-level
- * BVH: a 4-wide BLAS per mesh (object space, the context's builder) and a
- * 4-wide TLAS over the instances' world boxes with one instance per leaf.
- * With DR_OPT_TWO_LEVEL set to 1 the bounce-by-bounce passes walk it,
- * rays mapped into each instance's object space (see dr_two_level_info).
+ * the flattened scene; in addition, when DR_OPT_TWO_LEVEL is 1 at the
+ * upload and there are at least 2 instances, a two-level BVH: a 4-wide BLAS
+ * per mesh (object space, the context's builder) and a 4-wide TLAS over the
+ * instances' world boxes with one instance per leaf, which the
+ * bounce-by-bounce passes then walk, rays mapped into each instance's object
+ * space (see dr_two_level_info).
  * Other arguments as in dr_scene_upload.  Synchronises.
  * Errors: INVALID_ARG (bad index, singular or non-finite transform, sizes),
  * OOM, CUDA, DEVICE_CHECK. */
@@ -393,11 +394,12 @@ int dr_pt_render(dr_ctx* ctx, int32_t max_path_len, uint32_t spp, uint64_t seed,
  *                      (dr_bvh8_info), which the bounce-by-bounce passes
  *                      then walk (the fused kernel keeps the 4-wide one).
  *                      All return the same closest hit (ties: smaller id).
- *   DR_OPT_TWO_LEVEL   1: for an instanced scene with a two-level BVH, the
- *                      bounce-by-bounce passes walk it; 0 (default): they
- *                      walk the flattened scene's BVH (faster here: the
- *                      object-space maps cost more than the shallower
- *                      trees save).  The two test triangles in
+ *   DR_OPT_TWO_LEVEL   1 (set before dr_scene_upload_instanced): an
+ *                      instanced scene also gets a two-level BVH, which the
+ *                      bounce-by-bounce passes walk; 0 (default, or set to
+ *                      0 later): they walk the flattened scene's BVH (faster
+ *                      here: the object-space maps cost more than the
+ *                      shallower trees save).  The two test triangles in
  *                      object vs world space, so a hit on an edge shared by
  *                      two triangles can go to either (the hit point and
  *                      shading always come from the flattened triangle).

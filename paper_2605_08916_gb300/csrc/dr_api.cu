@@ -1992,7 +1992,7 @@ int dr_scene_upload_instanced(dr_ctx* c, const dr_mesh_desc* meshes, int32_t n_m
   int r = dr_scene_upload(c, V.data(), (int32_t)tv, T.data(), any_normals ? N.data() : nullptr, (int32_t)tt, TM.data(),
                           mats, nm, camera, width, height);
   if (r != DR_OK) return r;
-  if (n_inst >= 2) r = build_two_level(c, meshes, n_meshes, inst, n_inst, inv, tri_base, box);
+  if (n_inst >= 2 && c->two_level) r = build_two_level(c, meshes, n_meshes, inst, n_inst, inv, tri_base, box);
   if (r != DR_OK) c->target = -1;
   return r;
 }

@@ -834,9 +834,10 @@ def test_instanced_upload_is_its_flattening(torch, R):
         r = R.Renderer()
         r.set_option("wavefront", 1)
         if inst:
-            r.set_option("two_level", 0)
+            r.set_option("two_level", 1)
             r.upload_instanced(isc)
-            assert r.two_level_info() is not None  # built, not walked
+            assert r.two_level_info() is not None
+            r.set_option("two_level", 0)  # built, not walked
         else:
             r.upload_scene(isc.flatten())
         r.init_chains(16384, 41, R.make_params(L=12, drift="adjoint", k0=0.0, steps_per_splat=4))
@@ -889,9 +890,10 @@ def test_two_level_chains_match_the_flat_walk(torch, R, tail):
     for tl in (1, 0):
         r = R.Renderer()
         r.set_option("wavefront", 1)
-        r.set_option("two_level", tl)
+        r.set_option("two_level", 1)
         r.set_option("tail_bounce", tail)
         r.upload_instanced(isc)
+        r.set_option("two_level", tl)  # the same upload, either walk
         r.init_chains(16384, 43, R.make_params(L=12, drift="adjoint", k0=0.0, steps_per_splat=4))
         r.step(9)
         out.append((r.readback_state(), r.readback_accum()))
@@ -944,6 +946,7 @@ def test_instanced_upload_errors(torch, R):
         r.upload_instanced(bad)  # mesh index out of range
     assert e.value.code == _lib.DR_ERR_INVALID_ARG
     r.upload_instanced(isc)
+    assert r.two_level_info() is None  # not asked for
     r.init_chains(64, 1, R.make_params(L=3, drift="adjoint", k0=100.0))
     r.step(2)
     r.close()
