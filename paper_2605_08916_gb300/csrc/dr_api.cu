@@ -1,10 +1,12 @@
 // libdiffrestore C ABI: context, device memory, scene upload and the host
 // orchestration of Alg. 1 - 3 (see include/diffrestore.h for the contract).
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/diffrestore.h"
@@ -14,6 +16,41 @@ using namespace dr;
 
 namespace {
 float hbits_f(int v) { float f; std::memcpy(&f, &v, 4); return f; }
+
+// Runs f(begin, end, part) over [0, n) in up to 16 contiguous parts on host
+// threads (one part below 2^16 items); parts are numbered in order, so
+// per-part results joined in part order are those of one sequential pass.
+template <class F>
+int parallel_parts(long long n, F f) {
+  const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+  const int parts = n < (1ll << 16) ? 1 : (int)std::min<unsigned>(16u, hw);
+  if (parts == 1) {
+    f(0ll, n, 0);
+    return 1;
+  }
+  std::vector<std::thread> th;
+  for (int p = 0; p < parts; ++p) th.emplace_back(f, n * p / parts, n * (p + 1) / parts, p);
+  for (auto& t : th) t.join();
+  return parts;
+}
+
+// Runs f(i) for i in [0, n) on up to 16 host threads taking items one at a
+// time (for few, unequal items); f must write disjoint outputs.
+template <class F>
+void parallel_items(int n, F f) {
+  const int nth = (int)std::min<unsigned>(16u, std::max(1u, std::thread::hardware_concurrency()));
+  std::atomic<int> next{0};
+  auto work = [&]() {
+    for (int i = next.fetch_add(1); i < n; i = next.fetch_add(1)) f(i);
+  };
+  if (nth == 1 || n < 2) {
+    work();
+    return;
+  }
+  std::vector<std::thread> th;
+  for (int t = 0; t < std::min(nth, n); ++t) th.emplace_back(work);
+  for (auto& t : th) t.join();
+}
 int hbits_i(float f) { int v; std::memcpy(&v, &f, 4); return v; }
 }  // namespace
 
@@ -863,12 +900,60 @@ int dr_scene_upload(dr_ctx* c, const float* verts, int32_t nv, const int32_t* tr
     return fail(DR_ERR_INVALID_ARG, "dr_scene_upload: NULL argument");
   if (nv < 1 || nt < 1 || nm < 1 || width < 1 || height < 1 || (long long)width * height >= (1ll << 31))
     return fail(DR_ERR_INVALID_ARG, "dr_scene_upload: bad size");
-  for (int i = 0; i < 3 * nt; ++i)
-    if (tris[i] < 0 || tris[i] >= nv) return fail(DR_ERR_INVALID_ARG, "dr_scene_upload: vertex index out of range");
+  // one parallel pass over the triangles (index and material checks, the
+  // emitting ones with their power) and one over the vertices (finite,
+  // extent); the light list keeps the triangle order
+  struct TriPart {
+    bool bad_index = false, bad_mat = false;
+    std::vector<int> lt;
+    std::vector<double> pw;
+  };
+  struct VertPart {
+    bool bad = false;
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  };
+  std::vector<TriPart> tp(16);
+  std::vector<VertPart> vp(16);
+  auto V = [&](int i) { return f3(verts[3 * i], verts[3 * i + 1], verts[3 * i + 2]); };
+  const int ntp = parallel_parts(nt, [&](long long b, long long e, int p) {
+    TriPart& q = tp[p];
+    for (long long i = b; i < e; ++i) {
+      const int i0 = tris[3 * i], i1 = tris[3 * i + 1], i2 = tris[3 * i + 2];
+      if (i0 < 0 || i0 >= nv || i1 < 0 || i1 >= nv || i2 < 0 || i2 >= nv) {
+        q.bad_index = true;
+        continue;
+      }
+      if (tri_mat[i] < 0 || tri_mat[i] >= nm) {
+        q.bad_mat = true;
+        continue;
+      }
+      const float* m = mats + 12 * tri_mat[i];
+      if (!(m[6] > 0.f || m[7] > 0.f || m[8] > 0.f)) continue;
+      const float3 a = V(i0), bb = V(i1), cc = V(i2);
+      const float3 N = cross(bb - a, cc - a);
+      const double area = 0.5 * std::sqrt((double)dot(N, N));
+      const double pwr = area * (0.2126 * m[6] + 0.7152 * m[7] + 0.0722 * m[8]);
+      if (!(pwr > 0.0)) continue;
+      q.lt.push_back((int)i);
+      q.pw.push_back(pwr);
+    }
+  });
+  const int nvp = parallel_parts(nv, [&](long long b, long long e, int p) {
+    VertPart& q = vp[p];
+    for (long long i = b; i < e; ++i)
+      for (int a = 0; a < 3; ++a) {
+        const float v = verts[3 * i + a];
+        if (!std::isfinite(v)) q.bad = true;
+        q.lo[a] = std::min(q.lo[a], (double)v);
+        q.hi[a] = std::max(q.hi[a], (double)v);
+      }
+  });
+  for (int p = 0; p < ntp; ++p)
+    if (tp[p].bad_index) return fail(DR_ERR_INVALID_ARG, "dr_scene_upload: vertex index out of range");
   free_batch(c);
   free_two_level(c);
-  for (int i = 0; i < nt; ++i)
-    if (tri_mat[i] < 0 || tri_mat[i] >= nm) return fail(DR_ERR_INVALID_ARG, "dr_scene_upload: material out of range");
+  for (int p = 0; p < ntp; ++p)
+    if (tp[p].bad_mat) return fail(DR_ERR_INVALID_ARG, "dr_scene_upload: material out of range");
   for (int i = 0; i < nm; ++i) {
     const float t = mats[12 * i];
     if (!(t == 0.f || t == 1.f || t == 2.f || t == 3.f || t == 4.f))
@@ -882,35 +967,26 @@ int dr_scene_upload(dr_ctx* c, const float* verts, int32_t nv, const int32_t* tr
           return fail(DR_ERR_INVALID_ARG, "dr_scene_upload: conductor eta and k must be finite and > 0");
     if (t == 2.f && !(mats[12 * i + 5] > 0.f)) return fail(DR_ERR_INVALID_ARG, "dr_scene_upload: dielectric ior must be > 0");
   }
-  for (long long i = 0; i < 3ll * nv; ++i)
-    if (!std::isfinite(verts[i])) return fail(DR_ERR_INVALID_ARG, "dr_scene_upload: non-finite vertex");
+  for (int p = 0; p < nvp; ++p)
+    if (vp[p].bad) return fail(DR_ERR_INVALID_ARG, "dr_scene_upload: non-finite vertex");
   DR_CUDA(cudaSetDevice(c->device));
   DR_CUDA(cudaStreamSynchronize(c->stream));
   // host-side scene constants: extent -> tmin, light table, camera basis
   double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
-  for (int i = 0; i < nv; ++i)
+  for (int p = 0; p < nvp; ++p)
     for (int a = 0; a < 3; ++a) {
-      lo[a] = std::min(lo[a], (double)verts[3 * i + a]);
-      hi[a] = std::max(hi[a], (double)verts[3 * i + a]);
+      lo[a] = std::min(lo[a], vp[p].lo[a]);
+      hi[a] = std::max(hi[a], vp[p].hi[a]);
     }
   const double ext = std::max(hi[0] - lo[0], std::max(hi[1] - lo[1], hi[2] - lo[2]));
-  auto V = [&](int i) { return f3(verts[3 * i], verts[3 * i + 1], verts[3 * i + 2]); };
   std::vector<int> lt;
   std::vector<double> pw;
   double tot = 0.0;
-  for (int i = 0; i < nt; ++i) {
-    const float* m = mats + 12 * tri_mat[i];
-    if (!(m[6] > 0.f || m[7] > 0.f || m[8] > 0.f)) continue;
-    const float3 a = V(tris[3 * i]), b = V(tris[3 * i + 1]), cc = V(tris[3 * i + 2]);
-    const float3 e1 = b - a, e2 = cc - a;
-    const float3 N = cross(e1, e2);
-    const double area = 0.5 * std::sqrt((double)dot(N, N));
-    const double p = area * (0.2126 * m[6] + 0.7152 * m[7] + 0.0722 * m[8]);
-    if (!(p > 0.0)) continue;
-    lt.push_back(i);
-    pw.push_back(p);
-    tot += p;
+  for (int p = 0; p < ntp; ++p) {
+    lt.insert(lt.end(), tp[p].lt.begin(), tp[p].lt.end());
+    pw.insert(pw.end(), tp[p].pw.begin(), tp[p].pw.end());
   }
+  for (double x : pw) tot += x;
   std::vector<float> sel(nt, 0.f);
   std::vector<float4> lrec(4 * lt.size());
   double acc = 0.0;
@@ -1955,40 +2031,50 @@ int dr_scene_upload_instanced(dr_ctx* c, const dr_mesh_desc* meshes, int32_t n_m
   // the flattened scene
   std::vector<float> V(3 * (size_t)tv), N(any_normals ? 3 * (size_t)tv : 0, 0.f), box(6 * (size_t)n_inst);
   std::vector<int> T(3 * (size_t)tt), TM((size_t)tt), tri_base(n_inst);
-  long long vb = 0, tb = 0;
-  for (int i = 0; i < n_inst; ++i) {
-    const dr_instance_desc& d = inst[i];
-    const dr_mesh_desc& q = meshes[d.mesh];
-    const double* M = inv.data() + 12 * (size_t)i;
-    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-    for (int v = 0; v < q.nv; ++v) {
-      const double p[3] = {q.verts[3 * v], q.verts[3 * v + 1], q.verts[3 * v + 2]};
-      for (int row = 0; row < 3; ++row) {
-        const double w = (((double)d.xform[4 * row] * p[0] + (double)d.xform[4 * row + 1] * p[1]) +
-                          (double)d.xform[4 * row + 2] * p[2]) + (double)d.xform[4 * row + 3];
-        const float f = (float)w;
-        V[3 * (vb + v) + row] = f;
-        lo[row] = std::min(lo[row], f);
-        hi[row] = std::max(hi[row], f);
-      }
-      if (q.normals) {
-        const double n[3] = {q.normals[3 * v], q.normals[3 * v + 1], q.normals[3 * v + 2]};
-        for (int row = 0; row < 3; ++row)
-          N[3 * (vb + v) + row] = (float)((M[row] * n[0] + M[4 + row] * n[1]) + M[8 + row] * n[2]);
-      }
+  std::vector<long long> vbase(n_inst);
+  {
+    long long vb = 0, tb = 0;
+    for (int i = 0; i < n_inst; ++i) {
+      vbase[i] = vb;
+      tri_base[i] = (int)tb;
+      vb += meshes[inst[i].mesh].nv;
+      tb += meshes[inst[i].mesh].nt;
     }
-    for (int k = 0; k < q.nt; ++k) {
-      for (int e = 0; e < 3; ++e) T[3 * (tb + k) + e] = (int)(vb + q.tris[3 * k + e]);
-      TM[tb + k] = d.material >= 0 ? d.material : q.tri_mat[k];
-    }
-    for (int a = 0; a < 3; ++a) {
-      box[6 * i + a] = lo[a];
-      box[6 * i + 3 + a] = hi[a];
-    }
-    tri_base[i] = (int)tb;
-    vb += q.nv;
-    tb += q.nt;
   }
+  // instances in parallel (disjoint output ranges)
+  parallel_items(n_inst, [&](int i) {
+    {
+      const dr_instance_desc& d = inst[i];
+      const dr_mesh_desc& q = meshes[d.mesh];
+      const double* M = inv.data() + 12 * (size_t)i;
+      const long long vb = vbase[i], tb = tri_base[i];
+      float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+      for (int v = 0; v < q.nv; ++v) {
+        const double p[3] = {q.verts[3 * v], q.verts[3 * v + 1], q.verts[3 * v + 2]};
+        for (int row = 0; row < 3; ++row) {
+          const double w = (((double)d.xform[4 * row] * p[0] + (double)d.xform[4 * row + 1] * p[1]) +
+                            (double)d.xform[4 * row + 2] * p[2]) + (double)d.xform[4 * row + 3];
+          const float f = (float)w;
+          V[3 * (vb + v) + row] = f;
+          lo[row] = std::min(lo[row], f);
+          hi[row] = std::max(hi[row], f);
+        }
+        if (q.normals) {
+          const double n[3] = {q.normals[3 * v], q.normals[3 * v + 1], q.normals[3 * v + 2]};
+          for (int row = 0; row < 3; ++row)
+            N[3 * (vb + v) + row] = (float)((M[row] * n[0] + M[4 + row] * n[1]) + M[8 + row] * n[2]);
+        }
+      }
+      for (int k = 0; k < q.nt; ++k) {
+        for (int e = 0; e < 3; ++e) T[3 * (tb + k) + e] = (int)(vb + q.tris[3 * k + e]);
+        TM[tb + k] = d.material >= 0 ? d.material : q.tri_mat[k];
+      }
+      for (int a = 0; a < 3; ++a) {
+        box[6 * i + a] = lo[a];
+        box[6 * i + 3 + a] = hi[a];
+      }
+    }
+  });
   int r = dr_scene_upload(c, V.data(), (int32_t)tv, T.data(), any_normals ? N.data() : nullptr, (int32_t)tt, TM.data(),
                           mats, nm, camera, width, height);
   if (r != DR_OK) return r;
