@@ -34,42 +34,38 @@ DR_D double k0_of(const StepArgs& a) { return a.fp ? a.fp->k0 : a.k0; }
 // its PSS dimension; rng: its stream key.
 DR_D void evolve_x(const StepArgs& a, const Rng& rng, uint32_t step, unsigned long long j, uint32_t cj, int d,
                    bool regen) {
-  if (regen) {
-    for (int i = 0; i < d; i += 4) {
-      const U4 r = rng.draw(step, cj, (uint32_t)(i >> 2), kRegen);
-      const uint32_t w[4] = {r.a, r.b, r.c, r.d};
-#pragma unroll
-      for (int k = 0; k < 4; ++k)
-        if (i + k < d) a.x[(size_t)(i + k) * a.N + j] = u01(w[k]);
-    }
-    return;
-  }
   const float c2 = 0.5f * a.stddev * a.stddev;
   float* __restrict__ X = a.x;
   const float* __restrict__ Sc = a.score;
   const size_t N = a.N;
-  // one Philox block serves two coordinate pairs: pair q uses words
-  // (q & 1) * 2 and (q & 1) * 2 + 1 of block q >> 1.  The four coordinates
-  // and scores of a block are loaded before any is stored, so each block
-  // costs one memory round trip rather than two.
-  for (int blk = 0; 2 * blk < d / 2; ++blk) {
-    const bool two = 2 * blk + 1 < d / 2;
+  // Philox block b covers coordinates 4b .. 4b + 3 either way: word e is
+  // the uniform of coordinate 4b + e (regeneration), or words (0, 1) and
+  // (2, 3) are the Box-Muller pairs of coordinate pairs 2b and 2b + 1
+  // (LocalDynamics; pair q moves only if both its coordinates exist).  Both
+  // run as one loop, so a warp holding a regenerating chain does not split;
+  // a block's coordinates and scores are loaded before any is stored.
+  for (int blk = 0; 4 * blk < d; ++blk) {
     const size_t i0 = (size_t)(4 * blk) * N + j;
     float xv[4], sv[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-      xv[e] = e < 2 || two ? X[i0 + e * N] : 0.0f;
-      sv[e] = e < 2 || two ? Sc[i0 + e * N] : 0.0f;
+      const bool need = !regen && 4 * blk + (e | 1) < d;
+      xv[e] = need ? X[i0 + e * N] : 0.0f;
+      sv[e] = need ? Sc[i0 + e * N] : 0.0f;
     }
-    const U4 r = rng.draw(step, cj, (uint32_t)blk, kNormal);
+    const U4 r = rng.draw(step, cj, (uint32_t)blk, regen ? kRegen : kNormal);
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      if (h && !two) break;
+      const int c0 = 4 * blk + 2 * h;
+      if (c0 >= d) break;
+      const bool pair = c0 + 1 < d;
       const float ua = u01(h ? r.c : r.a), ub = u01(h ? r.d : r.b);
       const float2 xi = box_muller(ua, ub);
       const float s0 = sv[2 * h], s1 = sv[2 * h + 1];
-      X[i0 + (2 * h) * N] = wrap01(xv[2 * h] + c2 * s0 + a.gamma_tilde * s1 + a.stddev * xi.x);
-      X[i0 + (2 * h + 1) * N] = wrap01(xv[2 * h + 1] + c2 * s1 - a.gamma_tilde * s0 + a.stddev * xi.y);
+      const float e0 = wrap01(xv[2 * h] + c2 * s0 + a.gamma_tilde * s1 + a.stddev * xi.x);
+      const float e1 = wrap01(xv[2 * h + 1] + c2 * s1 - a.gamma_tilde * s0 + a.stddev * xi.y);
+      if (regen || pair) X[i0 + (2 * h) * N] = regen ? ua : e0;
+      if (pair) X[i0 + (2 * h + 1) * N] = regen ? ub : e1;
     }
   }
 }
