@@ -290,6 +290,7 @@ def run_ours(args, wl, rank, world, local):
     bvh4 = r.bvh4_info() if args.bvh_width != 2 else None
     bvh8 = r.bvh8_info() if args.bvh_width == 8 else None
     two_level = r.two_level_info() if isinstance(scene, S.InstancedScene) and args.two_level else None
+    sah4 = r.bvh4_sah() if bvh4 else None
     log(f"uploaded + init {N} chains; bvh {r.bvh_info()}; 4-wide {bvh4}; 8-wide {bvh8}; two-level {two_level}")
     # traversal statistics (separate kernel instantiation, untimed)
     r.set_stats(True)
@@ -386,6 +387,7 @@ def run_ours(args, wl, rank, world, local):
                            "image": [scene.width, scene.height], "chains_per_gpu": N, "max_path_len": wl["L"],
                            "pss_dim": d, "drift": wl["drift"], "rb_weight": True, "steps_per_frame": F,
                            "execution": "wavefront" if wavefront else "fused",
+                           "bvh_sah": sah4,
                            "bvh": ("two-level (4-wide TLAS over instances, 4-wide BLAS per mesh)" if two_level
                                    else "8-wide compressed" if (bvh8 and wavefront) else "4-wide" if wide
                                    else "binary"),

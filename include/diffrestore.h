@@ -326,6 +326,14 @@ int dr_bvh_info(dr_ctx* ctx, int32_t* n_nodes, int32_t* n_tris, int32_t* max_dep
  * the kernels hold; rays then use the binary BVH). */
 int dr_bvh4_info(dr_ctx* ctx, int32_t* n_nodes, int32_t* max_depth, int32_t* stack_need);
 
+/* Quality of the 4-wide BVH by the surface-area heuristic (the measure its
+ * leaf decision minimises): for a ray that hits the root box, with each
+ * box entered with probability area(box) / area(root box), the expected
+ * number of node steps (the root's included; HOST output node_steps) and
+ * of triangle tests (HOST output tri_tests).  Computed at upload.  Each
+ * output may be NULL.  Errors: STATE (no 4-wide BVH). */
+int dr_bvh4_sah(dr_ctx* ctx, double* node_steps, double* tri_tests);
+
 /* The 8-wide compressed BVH of the uploaded scene, built at upload when
  * DR_OPT_BVH_WIDTH is 8: the binary tree collapsed with the same leaf rule
  * into nodes of up to 8 children, numbered breadth first (a node's inner

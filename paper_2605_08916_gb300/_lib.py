@@ -28,7 +28,7 @@ EXPORTS = ["dr_version", "dr_last_error", "dr_create", "dr_destroy", "dr_scene_u
            "dr_get_counters", "dr_eval_logp", "dr_trace_closest", "dr_philox", "dr_splat_records",
            "dr_clear_image", "dr_state_save", "dr_state_load", "dr_set_stats", "dr_get_traversal_stats",
            "dr_bvh_info", "dr_get_launch_count", "dr_get_chain_shape", "dr_pt_render", "dr_set_bvh_builder",
-           "dr_splat_records_noalloc", "dr_set_option", "dr_get_profile", "dr_frame", "dr_bvh4_info", "dr_bvh8_info", "dr_get_bounce_profile",
+           "dr_splat_records_noalloc", "dr_set_option", "dr_get_profile", "dr_frame", "dr_bvh4_info", "dr_bvh4_sah", "dr_bvh8_info", "dr_get_bounce_profile",
            "dr_scenes_upload_batch", "dr_resolve_scene", "dr_get_scene_counters", "dr_scene_upload_instanced",
            "dr_two_level_info"]
 DR_OPT_WORK_ORDER, DR_OPT_WAVEFRONT, DR_OPT_PROFILE, DR_OPT_BVH_WIDTH = 1, 2, 3, 4
@@ -120,6 +120,7 @@ def load(build_if_missing=True):
         "dr_frame": ([P, U32], C.c_int),
         "dr_bvh4_info": ([P, P, P, P], C.c_int),
         "dr_bvh8_info": ([P, P, P], C.c_int),
+        "dr_bvh4_sah": ([P, P, P], C.c_int),
         "dr_get_bounce_profile": ([P, P, I32], C.c_int),
         "dr_scenes_upload_batch": ([P, P, I32], C.c_int),
         "dr_resolve_scene": ([P, I32, P], C.c_int),

@@ -68,6 +68,7 @@ struct dr_ctx {
   float4* nodes4 = nullptr;  // 4-wide collapse of `nodes` (null when not built)
   float4* tris4 = nullptr;
   int n_nodes4 = 0, bvh4_depth = 0, bvh4_stack = 0;
+  double bvh4_sah_nodes = 0.0, bvh4_sah_tris = 0.0;  // SAH cost terms of the 4-wide BVH
   uint4* nodes8 = nullptr;  // 8-wide compressed collapse (built when bvh_width is 8 at upload)
   float4* tris8 = nullptr;
   int n_nodes8 = 0, bvh8_depth = 0;
@@ -584,6 +585,9 @@ int build_bvh4(dr_ctx* c, int* depth2) {
         c->n_nodes4 = n4;
         c->bvh4_depth = plan.depth;
         c->bvh4_stack = plan.stack_need;
+        if (bvh4_sah(c->nodes4, n4, c->stream, &c->bvh4_sah_nodes, &c->bvh4_sah_tris) < 0)
+          r = fail(DR_ERR_CUDA, "dr_scene_upload: SAH cost of the 4-wide BVH");
+        c->launches += 5;
       } else {
         dfree(&c->nodes4);
         dfree(&c->tris4);
@@ -2089,6 +2093,15 @@ int dr_two_level_info(dr_ctx* c, int32_t* n_instances, int32_t* n_tlas_nodes, in
   if (n_instances) *n_instances = c->n_insts;
   if (n_tlas_nodes) *n_tlas_nodes = c->n_tl_nodes;
   if (n_blas_nodes) *n_blas_nodes = c->n_bl_nodes;
+  return DR_OK;
+}
+
+int dr_bvh4_sah(dr_ctx* c, double* node_steps, double* tri_tests) {
+  if (!c) return fail(DR_ERR_INVALID_ARG, "dr_bvh4_sah: NULL ctx");
+  if (c->target != 0) return fail(DR_ERR_STATE, "dr_bvh4_sah: no scene");
+  if (!c->nodes4) return fail(DR_ERR_STATE, "dr_bvh4_sah: the scene has no 4-wide BVH");
+  if (node_steps) *node_steps = c->bvh4_sah_nodes;
+  if (tri_tests) *tri_tests = c->bvh4_sah_tris;
   return DR_OK;
 }
 

@@ -770,4 +770,80 @@ void launch_tlas_leaves(float4* nodes4, int n, const float4* tris4, int n_inst, 
   if (n > 0) tlas_leaf_kernel<<<blocks(n), kB4Threads, 0, s>>>(nodes4, n, tris4, n_inst, err);
 }
 
+// ---------------------------------------------------------------- SAH cost
+namespace {
+
+// per 4-wide node: the surface areas of its inner children (each a node
+// step) and of its leaves times their triangle counts (triangle tests)
+__global__ void sah4_kernel(const float4* __restrict__ n4, int n, float* __restrict__ node_a,
+                            float* __restrict__ tri_a) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float4* nb = n4 + (size_t)kNode4F4 * i;
+  const float4 lx = nb[0], hx = nb[1], ly = nb[2], hy = nb[3], lz = nb[4], hz = nb[5];
+  const int4 ch = *reinterpret_cast<const int4*>(nb + 6);
+  const float lo[3][4] = {{lx.x, lx.y, lx.z, lx.w}, {ly.x, ly.y, ly.z, ly.w}, {lz.x, lz.y, lz.z, lz.w}};
+  const float hi[3][4] = {{hx.x, hx.y, hx.z, hx.w}, {hy.x, hy.y, hy.z, hy.w}, {hz.x, hz.y, hz.z, hz.w}};
+  const int c[4] = {ch.x, ch.y, ch.z, ch.w};
+  float na = 0.0f, ta = 0.0f;
+  for (int k = 0; k < 4; ++k) {
+    if (c[k] == kBvh4Empty) continue;
+    const float a = box_area(f3(lo[0][k], lo[1][k], lo[2][k]), f3(hi[0][k], hi[1][k], hi[2][k]));
+    if (c[k] >= 0) na += a;
+    else ta += a * (float)leaf_count(c[k]);
+  }
+  node_a[i] = na;
+  tri_a[i] = ta;
+}
+
+}  // namespace
+
+int bvh4_sah(const float4* d_nodes4, int n4, cudaStream_t s, double* node_term, double* tri_term) {
+  *node_term = *tri_term = 0.0;
+  if (n4 < 1) return -1;
+  const int grid = (n4 + step_block_size() - 1) / step_block_size();  // launch_block_sums' partial sums
+  float* fa = nullptr;
+  double* da = nullptr;
+  if (cudaMalloc(&fa, 8 * (size_t)n4) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  if (cudaMalloc(&da, 8 * (size_t)(2 * grid + 2)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(fa);
+    return -1;
+  }
+  sah4_kernel<<<blocks(n4), kB4Threads, 0, s>>>(d_nodes4, n4, fa, fa + n4);
+  launch_block_sums(fa, (unsigned long long)n4, da, s);
+  launch_sum_doubles(da, grid, da + 2 * grid, s);
+  launch_block_sums(fa + n4, (unsigned long long)n4, da + grid, s);
+  launch_sum_doubles(da + grid, grid, da + 2 * grid + 1, s);
+  double sums[2] = {0.0, 0.0};
+  float4 root[kNode4F4];
+  cudaMemcpyAsync(sums, da + 2 * grid, 16, cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(root, d_nodes4, sizeof(root), cudaMemcpyDeviceToHost, s);
+  const bool ok = cudaStreamSynchronize(s) == cudaSuccess;
+  cudaFree(fa);
+  cudaFree(da);
+  if (!ok) return -1;
+  // the root box: the union of the root node's children
+  const float* lo[3] = {&root[0].x, &root[2].x, &root[4].x};
+  const float* hi[3] = {&root[1].x, &root[3].x, &root[5].x};
+  const int* links = reinterpret_cast<const int*>(&root[6]);
+  double bl[3] = {1e300, 1e300, 1e300}, bh[3] = {-1e300, -1e300, -1e300};
+  for (int k = 0; k < 4; ++k) {
+    if (links[k] == kBvh4Empty) continue;
+    for (int a = 0; a < 3; ++a) {
+      bl[a] = std::min(bl[a], (double)lo[a][k]);
+      bh[a] = std::max(bh[a], (double)hi[a][k]);
+    }
+  }
+  const double dx = bh[0] - bl[0], dy = bh[1] - bl[1], dz = bh[2] - bl[2];
+  const double a0 = 2.0 * (dx * dy + dy * dz + dz * dx);
+  if (!(a0 > 0.0)) return -1;
+  *node_term = 1.0 + sums[0] / a0;
+  *tri_term = sums[1] / a0;
+  return 1;
+}
+
 }  // namespace dr

@@ -88,6 +88,11 @@ int bvh8_emit(const float4* d_nodes2, const float4* d_tris2, int n_inner, int n_
 // tri_off (BLAS concatenation), and turn TLAS leaves (one record each) into
 // instance indices read from the records' ids.
 void launch_link_offset(float4* nodes4, int n, int node_off, int tri_off, cudaStream_t s);
+// Surface-area-heuristic cost of a 4-wide BVH for a ray that hits the root
+// box (a box is entered with probability area / root area): expected node
+// steps (*node_term, the root's included) and triangle tests (*tri_term).
+// Returns 1, or -1.  Synchronises.
+int bvh4_sah(const float4* d_nodes4, int n4, cudaStream_t s, double* node_term, double* tri_term);
 void launch_tlas_leaves(float4* nodes4, int n, const float4* tris4, int n_inst, uint32_t* err, cudaStream_t s);
 
 // ---------------------------------------------------------------- chains

@@ -269,6 +269,15 @@ class Renderer:
         _lib.check(r, "dr_bvh4_info")
         return {"n_nodes": a.value, "max_depth": b.value, "stack_need": c.value}
 
+    def bvh4_sah(self):
+        """SAH cost of the 4-wide BVH: expected node steps and triangle tests of a ray hitting the root box."""
+        a, b = C.c_double(), C.c_double()
+        r = _lib.load().dr_bvh4_sah(self.h, C.byref(a), C.byref(b))
+        if r == _lib.DR_ERR_STATE:
+            return None
+        _lib.check(r, "dr_bvh4_sah")
+        return {"node_steps": a.value, "tri_tests": b.value}
+
     def bvh8_info(self):
         """The 8-wide compressed BVH's node count and depth, or None when the scene has none."""
         a, b = C.c_int32(), C.c_int32()

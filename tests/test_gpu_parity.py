@@ -132,6 +132,27 @@ def test_bvh_widths_return_the_same_hits(torch, R, which):
         assert np.array_equal(ta[same], tb[same])
 
 
+def test_bvh4_sah_cost_closed_form(torch, R):
+    """Two unit right triangles 5 apart in the z = 0 plane: the 4-wide root
+    holds the two one-triangle leaves, so the SAH cost is one node step and
+    (2 + 2) / 12 triangle tests (leaf box areas 2 over a 6 x 1 root box).
+    A large scene's cost is finite, positive and consistent with its tree."""
+    verts = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [5, 0, 0], [6, 0, 0], [5, 1, 0]], np.float32)
+    tris = np.array([[0, 1, 2], [3, 4, 5]], np.int32)
+    mats = np.stack([S.material(S.MAT_DIFFUSE, (0.5, 0.5, 0.5))])
+    cam = np.array([3, 0.5, 5, 3, 0.5, 0, 0, 1, 0, 40], np.float32)
+    r = R.Renderer()
+    r.upload_scene(S.Scene(verts, tris, np.zeros(2, np.int32), mats, cam, 8, 8))
+    sah = r.bvh4_sah()
+    assert abs(sah["node_steps"] - 1.0) < 1e-12
+    assert abs(sah["tri_tests"] - 4.0 / 12.0) < 1e-7
+    r.upload_scene(hit_scene("procedural"))
+    sah = r.bvh4_sah()
+    info = r.bvh4_info()
+    assert 1.0 < sah["node_steps"] < info["n_nodes"] and 0.0 < sah["tri_tests"] < 4.0 * info["n_nodes"]
+    r.close()
+
+
 def test_one_triangle_scene_keeps_the_binary_bvh(torch, R):
     scene = S.cornell_box(1, 8, 8)
     keep = np.zeros(scene.n_tris, bool)
