@@ -547,6 +547,36 @@ def test_batch_matches_separate_contexts(torch, R, width):
         c0 += n
 
 
+def test_batch_with_conductors_matches_separate_contexts(torch, R):
+    """A batch holding a conductor scene runs the batch kernels compiled
+    with the conductor branches (and, with paths of 16 segments, the tail
+    pass): still bit-identical to one context per scene."""
+    items = [(S.cornell_box(3, 32, 32, metal=True), 16, 8192),
+             (S.procedural_scene(3, 64, 36, target_tris=20000, n_objects=20), 8, 8192)]
+    seed, T = 91, 5
+    rb = R.Renderer()
+    rb.upload_scenes(items)
+    rb.init_chains(sum(n for _, _, n in items), seed, R.make_params(L=16, drift="adjoint", k0=0.0, steps_per_splat=4))
+    rb.step(T)
+    stb = rb.readback_state(("x", "killed", "logp"))
+    rb.close()
+    c0 = 0
+    for s_i, (scene, L, n) in enumerate(items):
+        r = R.Renderer()
+        r.set_option("wavefront", 1)
+        r.set_option("tail_bounce", 4)
+        r.upload_scene(scene)
+        r.init_chains(n, seed + (s_i << 32), R.make_params(L=L, drift="adjoint", k0=0.0, steps_per_splat=4))
+        r.step(T)
+        st = r.readback_state(("x", "killed", "logp"))
+        r.close()
+        d = S.pss_dim(L)
+        assert np.array_equal(stb["x"][c0:c0 + n, :d], st["x"])
+        assert np.array_equal(stb["killed"][c0:c0 + n], st["killed"])
+        assert np.array_equal(stb["logp"][c0:c0 + n], st["logp"])
+        c0 += n
+
+
 def test_batch_graph_frames_and_errors(torch, R):
     from paper_2605_08916_gb300 import _lib
     items = batch_items()
