@@ -29,7 +29,13 @@ int parallel_parts(long long n, F f) {
     return 1;
   }
   std::vector<std::thread> th;
-  for (int p = 0; p < parts; ++p) th.emplace_back(f, n * p / parts, n * (p + 1) / parts, p);
+  for (int p = 0; p < parts; ++p) {
+    try {
+      th.emplace_back(f, n * p / parts, n * (p + 1) / parts, p);
+    } catch (...) {  // no thread to be had: this part on the calling thread
+      f(n * p / parts, n * (p + 1) / parts, p);
+    }
+  }
   for (auto& t : th) t.join();
   return parts;
 }
@@ -48,7 +54,14 @@ void parallel_items(int n, F f) {
     return;
   }
   std::vector<std::thread> th;
-  for (int t = 0; t < std::min(nth, n); ++t) th.emplace_back(work);
+  for (int t = 0; t < std::min(nth, n); ++t) {
+    try {
+      th.emplace_back(work);
+    } catch (...) {  // fewer threads: the others and the caller finish the items
+      break;
+    }
+  }
+  work();
   for (auto& t : th) t.join();
 }
 int hbits_i(float f) { int v; std::memcpy(&v, &f, 4); return v; }
