@@ -210,6 +210,38 @@ def test_eval_logp_and_adjoint_match_oracle(torch, R, oracle, case):
     r.close()
 
 
+def test_logp_autograd_function(torch, R, oracle):
+    """LogPFunction: x -> log p as a torch autograd node; its backward runs
+    the adjoint kernel, scaled by the incoming gradient, and matches the
+    oracle's dual-number gradient on lit points."""
+    scene, L = S.cornell_box(1, 64, 64, glossy=True), 6
+    d = S.pss_dim(L)
+    r = R.Renderer()
+    r.upload_scene(scene)
+    rng = np.random.default_rng(8)
+    M = 600
+    x0 = rng.random((M, d)).astype(np.float32)
+    x = torch.from_numpy(x0).cuda().requires_grad_(True)
+    w = torch.from_numpy(rng.normal(size=M).astype(np.float32)).cuda()
+    y = R.LogPFunction.apply(x, r, L)
+    (y * w).sum().backward()
+    # the forward is the value-only evaluation, the backward the one with the
+    # adjoint (two kernel instantiations: log p agrees to the last bits)
+    lp, _, _, _ = r.eval_logp(torch.from_numpy(x0).cuda(), L=L, grad=False)
+    lp_g, g, _, _ = r.eval_logp(torch.from_numpy(x0).cuda(), L=L, grad=True)
+    torch.cuda.synchronize()
+    assert torch.equal(y.detach(), lp)
+    assert torch.allclose(lp, lp_g, rtol=1e-5, atol=1e-5)
+    assert torch.equal(x.grad, g * w[:, None])
+    ro = oracle.evaluate(oracle.OracleScene(scene), x0.astype(np.float64), L, grad=True)
+    lit = ro["f"].sum(1) > 0
+    go = ro["grad"] * w.cpu().numpy()[:, None].astype(np.float64)
+    gg = x.grad.cpu().numpy().astype(np.float64)
+    rel = np.linalg.norm(gg - go, axis=1) / np.maximum(np.linalg.norm(go, axis=1), 1e-6)
+    assert lit.mean() > 0.05 and np.mean(rel[lit] <= 1e-3) >= 0.97
+    r.close()
+
+
 def _chain_parity(torch, R, oracle, target_obj, params_gpu, params_orc, N, M, T, seed, x_tol=1e-4):
     r = R.Renderer()
     if isinstance(target_obj, S.Scene):
