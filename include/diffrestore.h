@@ -393,7 +393,8 @@ int dr_pt_render(dr_ctx* ctx, int32_t max_path_len, uint32_t spp, uint64_t seed,
  *                      shadow rays, next rays and shading interleaved per
  *                      lane) instead of one launch per pass and bounce; the
  *                      arithmetic per path is the same.  0: no tail pass;
- *                      -1 (default): automatic.  4-wide BVH only.
+ *                      -1 (default): automatic.  Bounce-by-bounce passes
+ *                      over a 4-wide, 8-wide or two-level BVH.
  *   DR_OPT_BVH_WIDTH   4: rays traverse the 4-wide BVH collapsed from the
  *                      binary one at scene upload (when it was built, see
  *                      dr_bvh4_info); 2: the binary BVH; 0 (default): the
