@@ -44,6 +44,12 @@ def test_calls_fail_cleanly_without_a_context():
     assert "NULL" in _lib.last_error()
     assert L.dr_destroy(None) == _lib.DR_OK
     assert L.dr_create(None, 0, None) == _lib.DR_ERR_INVALID_ARG
+    # the hierarchy and instancing entry points check their context first
+    assert L.dr_scene_upload_instanced(None, None, 0, None, 0, None, 0, None, 1, 1) == _lib.DR_ERR_INVALID_ARG
+    assert L.dr_two_level_info(None, None, None, None) == _lib.DR_ERR_INVALID_ARG
+    assert L.dr_bvh8_info(None, None, None) == _lib.DR_ERR_INVALID_ARG
+    assert L.dr_bvh4_sah(None, None, None) == _lib.DR_ERR_INVALID_ARG
+    assert L.dr_set_option(None, _lib.DR_OPT_TWO_LEVEL, 1) == _lib.DR_ERR_INVALID_ARG
 
 
 def test_create_without_gpu_reports_cuda_error():
