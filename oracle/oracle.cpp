@@ -26,6 +26,15 @@
 //     (Eq. killing-rate-constant).
 //   * Analytic targets (isotropic Gaussian mixtures on the torus, constant
 //     density) used to pin the Restore/Langevin logic against closed forms.
+//   * Materials (Sec. 6 "Test scenes" names pbrt's diffuse, dielectric and
+//     conductor): Lambertian, a GGX coat over Lambertian, a smooth
+//     dielectric, and a rough GGX conductor whose Fresnel reflectance is
+//     computed from the Fresnel equations in complex arithmetic.
+// Pins (tests/test_oracle_*.py): closed-form moments, kill rates and images
+// for the chain logic; BVH vs brute force, a white furnace and a form factor
+// for f; pdf integrals, reciprocity, GGX energy and Fresnel closed forms for
+// the materials; dual gradients vs central differences; Philox vs an
+// independent implementation.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
