@@ -409,7 +409,12 @@ def run_ours(args, wl, rank, world, local):
                 if wavefront else None,
                 "clocks": clocks, "gpu_launches": launches, "e2e": e2e, "relmse_33ms": rel}
         if world == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(wl, flat_of(scene))
+            cb = cpu_baseline(wl, flat_of(scene))
+            cb["per_core"] = cb["value"] / max(1, cb["cores"])
+            # the oracle traces the same paths (same Philox streams), so its
+            # rays per chain-step are the ones counted on the GPU
+            cb["rays_per_s"] = cb["value"] * line["rays_per_chain_step"]
+            line["cpu_baseline"] = cb
             log("cpu baseline done")
         print(json.dumps(line), flush=True)
     r.close()
