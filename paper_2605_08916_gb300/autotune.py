@@ -12,8 +12,9 @@ API, the launch schedule that the hot path leaves open:
 * ``tail_bounce`` - the bounce from whose shading on each path finishes in
   one persistent pass (0: every bounce as its own launches).
 
-The traversal stack depth is fixed at build time (48 entries, checked
-against every BVH at upload), so it is not a run-time choice.
+The traversal stack depth is fixed at build time (48 entries for the flat
+hierarchies, 64 for the two-level walk; checked against every BVH at upload),
+so it is not a run-time choice.
 """
 from __future__ import annotations
 
