@@ -70,23 +70,11 @@ class DRError(RuntimeError):
         self.code = code
 
 
-_lib = None
-
-
-def load(build_if_missing=True):
-    """Loads the in-tree library (building it first if it is missing or out of
-    date when ``build_if_missing``)."""
-    global _lib
-    if _lib is not None:
-        return _lib
-    if build_if_missing:
-        from . import build as _b
-        _b.build()
-    if not os.path.exists(LIB_PATH):
-        raise RuntimeError(f"libdiffrestore.so not found at {LIB_PATH}; run paper_2605_08916_gb300.build")
-    L = C.CDLL(LIB_PATH)
+def signatures():
+    """ctypes (argtypes, restype) of every entry point, in the order and widths
+    of the prototypes in include/diffrestore.h."""
     P, I32, I64, U32, U64 = C.c_void_p, C.c_int32, C.c_int64, C.c_uint32, C.c_uint64
-    sig = {
+    return {
         "dr_version": ([], C.c_int),
         "dr_last_error": ([], C.c_char_p),
         "dr_create": ([C.POINTER(P), C.c_int, P], C.c_int),
@@ -128,7 +116,24 @@ def load(build_if_missing=True):
         "dr_scene_upload_instanced": ([P, P, I32, P, I32, P, I32, P, I32, I32], C.c_int),
         "dr_two_level_info": ([P, P, P, P], C.c_int),
     }
-    for name, (args, res) in sig.items():
+
+
+_lib = None
+
+
+def load(build_if_missing=True):
+    """Loads the in-tree library (building it first if it is missing or out of
+    date when ``build_if_missing``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing:
+        from . import build as _b
+        _b.build()
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libdiffrestore.so not found at {LIB_PATH}; run paper_2605_08916_gb300.build")
+    L = C.CDLL(LIB_PATH)
+    for name, (args, res) in signatures().items():
         f = getattr(L, name)
         f.argtypes = args
         f.restype = res
