@@ -12,6 +12,13 @@ P2  Constant target: the kill probability per step is
 P3  pi-invariance: on a 4-D Gaussian mixture the time average of g over the
     Restore process matches the target's moments (Sec. 4, Def. 1 with the
     modified killing rate; ergodic average of Sec. 3).
+P3b The discretisation bias vanishes at rate O(dt) (Sec. 5.2: the
+    continuous-time embedding of the Euler-Maruyama kernel with holding rate
+    h = 1/dt is invariant up to O(dt)).  With the diffusion coefficient
+    sigma = stddev / sqrt(dt) held at the paper's value, the relative error
+    of the Restore estimate of a Gaussian's variance at least halves with
+    each halving of dt (within 3 standard errors), so it is O(dt) and
+    vanishes as dt -> 0; at the largest dt it is far above its error bar.
 P6  Whole image: with the local moves switched off (stddev -> 0) every tour
     stays at its uniform start and the complete-tour Restore image (Alg. 3)
     is an unbiased estimate of lambda(f 1_pixel); on the 16 x 16 Cornell box
@@ -156,6 +163,36 @@ def test_mixture_invariance_moments(oracle):
     assert z2.max() < 3.5, (est2, m2, z2)
     # the check has power: the uniform distribution's moments are rejected
     assert np.max(np.abs(est2 - (np.full((d, d), 0.25) + np.eye(d) / 12.0)) / se2) > 10
+
+
+def test_discretisation_bias_vanishes_linearly_in_dt(oracle):
+    O = oracle
+    s = 0.08
+    tgt = O.target(S.single_gaussian([0.5, 0.5], s))
+    _, var_true = _wrapped_moments_1d(0.5, s)
+    var_true -= _wrapped_moments_1d(0.5, s)[0] ** 2
+    sigma = 5e-3 / np.sqrt(1e-5)          # the paper's stddev and dt
+    M = 1_000_000
+    dts = 1.6e-3 / 2.0 ** np.arange(4)
+    bias, se = [], []
+    for dt in dts:
+        prm = O.make_params(L=1, drift="exact", rb=True, stddev=sigma * np.sqrt(dt), dt=dt, m=64.0)
+        prm.k0 = 1.0 / (64.0 * dt)         # p_lambda = 1 (normalised density)
+        r = O.restore_tours(tgt, prm, seed=11, chain_ids=np.arange(M), max_steps=1 << 22)
+        assert r["truncated"].sum() == 0
+        A1, Ax, Axx = r["I1"], r["Ix"][:, 0], r["Ixx"][:, 0, 0]
+        m1, m2 = Ax.sum() / A1.sum(), Axx.sum() / A1.sum()
+        # delta method for the ratio estimators: the variance estimate's
+        # influence per tour is (Axx - m2 A1) - 2 m1 (Ax - m1 A1)
+        infl = (Axx - m2 * A1) - 2 * m1 * (Ax - m1 * A1)
+        bias.append((m2 - m1 * m1) / var_true - 1.0)
+        se.append(np.sqrt(np.var(infl) / M) / A1.mean() / var_true)
+    b, e = np.array(bias), np.array(se)
+    print("relative variance bias", b, "+-", e, "bias / dt", b / dts)
+    assert b[0] > 20 * e[0]                        # the check has power
+    for k in range(len(dts) - 1):                  # halving dt at least halves the bias
+        assert b[k + 1] <= 0.5 * b[k] + 3 * np.sqrt(e[k + 1] ** 2 + 0.25 * e[k] ** 2), (k, b, e)
+    assert b[-1] > -3 * e[-1]
 
 
 def test_cornell_restore_image_matches_path_tracing(oracle):
