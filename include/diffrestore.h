@@ -361,7 +361,9 @@ int dr_get_launch_count(dr_ctx* ctx, uint64_t* launches);
  * Errors: STATE (no scene), INVALID_ARG, OOM, CUDA, DEVICE_CHECK. */
 int dr_pt_render(dr_ctx* ctx, int32_t max_path_len, uint32_t spp, uint64_t seed, double* out_mean);
 
-/* Execution options (they change speed only, never results):
+/* Execution options.  They change speed, not the method: results are the
+ * same up to floating-point contraction order (DR_OPT_WAVEFRONT) and the
+ * triangle picked on a shared edge (DR_OPT_TWO_LEVEL), as stated below.
  *   DR_OPT_WAVEFRONT   1: adjoint-drift steps on a scene run bounce by
  *                      bounce over compacted queues of live paths (trace /
  *                      shade / shadow kernels per bounce, the per-segment
