@@ -16,8 +16,9 @@ L2 is also flushed between timed steps.
     python bench.py --impl reference ...   # the FP64 CPU oracle, timed on host cores
 
 Under torchrun each rank runs an independent replica (disjoint seeds, weak
-scaling); the per-rank FP64 images and tour counts are merged with one
-all-reduce at the end (the only exchange of the method).
+scaling).  The method's two exchanges are all-reduces outside the timed
+region: the ranks agree on p_lambda at init (so every rank splats with the
+same k0), and the per-rank FP64 images and tour counts are merged at the end.
 """
 from __future__ import annotations
 
@@ -256,7 +257,7 @@ def run_reference(args, wl, rank, world):
 def run_ours(args, wl, rank, world, local):
     import torch
     from paper_2605_08916_gb300 import renderer as R
-    from paper_2605_08916_gb300.replicas import merge_and_resolve, replica_seed
+    from paper_2605_08916_gb300.replicas import init_chains_agreed, merge_and_resolve, replica_seed
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -283,7 +284,11 @@ def run_ours(args, wl, rank, world, local):
     upload(r, scene)
     stream.synchronize()
     t_init = time.perf_counter()
-    r.init_chains(N, seed, params)
+    if world > 1:
+        # Alg. 1 with one k0 on every replica: p_lambda over all ranks' samples
+        init_chains_agreed(r, N, seed, params, device=dev)
+    else:
+        r.init_chains(N, seed, params)
     stream.synchronize()
     t_init = time.perf_counter() - t_init
     log(f"init (evaluation + p_lambda estimate + clock) {t_init * 1e3:.1f} ms")

@@ -64,3 +64,89 @@ def test_two_rank_merge_equals_union(tmp_path):
         assert int(np.load(tmp_path / f"tc{rank}.npy")[0]) == tc
         assert np.array_equal(img, union)
     assert replica_seed(77, 0) == 77 and replica_seed(77, 1) != 77
+
+
+class _OracleRank:
+    """Stands in for one rank's renderer: Alg. 1 and the following steps run
+    by the oracle on this rank's chains."""
+
+    def __init__(self, tgt):
+        self.tgt = tgt
+
+    def init_chains(self, n, seed, params, frame=0):
+        from oracle import oracle as O
+        r = O.restore_run(self.tgt, params, seed, np.arange(n), n_steps=0, record=False)
+        self.n, self.seed, self.params = n, seed, params
+        self.p_lambda = r["p_init_sum"] / n
+
+    def counters(self):
+        return {"p_lambda": self.p_lambda}
+
+    def run(self, n_steps):
+        from oracle import oracle as O
+        return O.restore_run(self.tgt, self.params, self.seed, np.arange(self.n), n_steps=n_steps, record=False)
+
+
+def _mixture():
+    from oracle import oracle as O
+    from paper_2605_08916_gb300 import scenes as S
+    return O.target(S.gaussian_mixture(seed=4, d=4, K=3, sig_range=(0.05, 0.08), width=8, height=8))
+
+
+def _run_rank_agreed(rank, world, port, out_dir):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        from oracle import oracle as O
+        from paper_2605_08916_gb300.replicas import init_chains_agreed, merge_and_resolve, replica_seed
+        r = _OracleRank(_mixture())
+        k0 = init_chains_agreed(r, 200 + 56 * rank, replica_seed(91, rank), O.make_params(L=1, drift="exact", k0=0.0))
+        out = r.run(24)
+        img, total = merge_and_resolve(torch.from_numpy(out["accum"].copy()), out["tour_count"], k0)
+        np.save(os.path.join(out_dir, f"agreed{rank}.npy"), np.concatenate([[k0, total], img.numpy().ravel()]))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_ranks_agree_on_k0_and_merge_to_the_union(tmp_path):
+    """Alg. 1 with p_lambda estimated from the union of both ranks' initial
+    samples (chain counts differ per rank), then 24 steps and the merge:
+    equals one run over the union with that k0, and both ranks use it."""
+    port = _free_port()
+    mp.start_processes(_run_rank_agreed, args=(2, port, str(tmp_path)), nprocs=2, join=True, start_method="spawn")
+    from oracle import oracle as O
+    from paper_2605_08916_gb300.replicas import replica_seed
+    tgt = _mixture()
+    ns = [200, 256]
+    est = O.make_params(L=1, drift="exact", k0=0.0)
+    sums = [O.restore_run(tgt, est, replica_seed(91, k), np.arange(ns[k]), 0, record=False)["p_init_sum"]
+            for k in range(2)]
+    local_k0 = [s / n / (est.m * est.dt) for s, n in zip(sums, ns)]
+    k0 = sum(sums) / sum(ns) / (est.m * est.dt)
+    assert abs(local_k0[0] / local_k0[1] - 1.0) > 1e-3      # the ranks' own estimates differ
+    prm = O.make_params(L=1, drift="exact", k0=k0)
+    acc, tc = 0, 0
+    for k in range(2):
+        r = O.restore_run(tgt, prm, replica_seed(91, k), np.arange(ns[k]), 24, record=False)
+        acc = acc + r["accum"]
+        tc += r["tour_count"]
+    union = (acc * (k0 / tc)).ravel()
+    for k in range(2):
+        got = np.load(tmp_path / f"agreed{k}.npy")
+        assert got[0] == pytest.approx(k0, rel=1e-15)
+        assert int(got[1]) == tc
+        np.testing.assert_allclose(got[2:], union, rtol=1e-13, atol=0)
+
+
+def test_init_agreement_without_a_process_group_is_local():
+    from oracle import oracle as O
+    from paper_2605_08916_gb300.replicas import agree_p_lambda, init_chains_agreed
+    assert agree_p_lambda(0.25, 10) == 0.25
+    assert agree_p_lambda(0.25, 0) == 0.0
+    r = _OracleRank(_mixture())
+    k0 = init_chains_agreed(r, 64, 5, O.make_params(L=1, drift="exact", k0=0.0))
+    assert k0 == pytest.approx(r.p_lambda / (64 * 1e-5), rel=1e-12)
+    assert r.params.k0 == k0
+    given = O.make_params(L=1, drift="exact", k0=123.0)
+    assert init_chains_agreed(r, 64, 5, given) == 123.0 and r.params is given
