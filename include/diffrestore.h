@@ -300,7 +300,14 @@ int dr_clear_image(dr_ctx* ctx);
 /* Checkpoint: serialises the chain state, counters, k0 and the FP64
  * accumulator into a HOST buffer.  With host_buf NULL, *bytes receives the
  * size needed.  A run resumed with dr_state_load continues bit-for-bit like
- * an uninterrupted one (the RNG is counter-based).  Synchronises. */
+ * an uninterrupted one (the RNG is counter-based).  Synchronises.
+ * dr_state_load reads `bytes` bytes of host_buf and checks them before any
+ * device work: a buffer that is not a checkpoint of this version, is
+ * truncated, was saved for another image or dimension, or holds a chain
+ * count outside [1, 2^31], invalid parameters or a k0 that is not positive
+ * and finite gives INVALID_ARG (the context is left as it was).
+ * Errors: INVALID_ARG (also NULL arguments), STATE (save: no chains; load:
+ * no target uploaded; either: a batch context), OOM, CUDA. */
 int dr_state_save(dr_ctx* ctx, void* host_buf, size_t* bytes);
 int dr_state_load(dr_ctx* ctx, const void* host_buf, size_t bytes);
 

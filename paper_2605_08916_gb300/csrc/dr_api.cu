@@ -1730,9 +1730,13 @@ int dr_state_load(dr_ctx* c, const void* host_buf, size_t bytes) {
   std::memcpy(&h, host_buf, sizeof(h));
   if (h.magic != kMagic || h.version != 1) return fail(DR_ERR_INVALID_ARG, "dr_state_load: not a checkpoint");
   if (c->target < 0) return fail(DR_ERR_STATE, "dr_state_load: upload the scene or target first");
+  // every field that sizes a buffer or a launch is checked before use, with
+  // the limits dr_chains_init applies
+  DR_TRY(validate_params(&h.prm));
+  if (h.N < 1 || h.N > (1ull << 31)) return fail(DR_ERR_INVALID_ARG, "dr_state_load: chain count out of range");
+  if (!(h.k0 > 0.0) || !std::isfinite(h.k0)) return fail(DR_ERR_INVALID_ARG, "dr_state_load: k0");
   const int d = c->target == 0 ? 2 + 4 * (h.prm.max_path_len - 1) : c->md;
   if (d != h.d || h.W != c->W || h.H != c->H) return fail(DR_ERR_INVALID_ARG, "dr_state_load: shape mismatch");
-  DR_TRY(validate_params(&h.prm));
   const size_t nd = (size_t)h.N * h.d;
   const size_t need = sizeof(SaveHeader) + nd * 8 + h.N * 5 + (size_t)h.W * h.H * 3 * 8;
   if (bytes < need) return fail(DR_ERR_INVALID_ARG, "dr_state_load: truncated checkpoint");

@@ -806,6 +806,19 @@ def test_checkpoint_resume_is_bit_identical(torch, R):
     st_a = a.readback_state(fields=("x", "killed"))
     b = R.Renderer()
     b.upload_scene(scene)
+    # damaged checkpoints are rejected on the host, before any device work,
+    # and leave the context usable (the header's magic, version and chain
+    # count are its first three 64-bit words)
+    from paper_2605_08916_gb300 import _lib
+    bad = [blob[:-1], blob[:16]]
+    for word, value in [(0, 0x1234), (1, 2), (2, 0), (2, (1 << 31) + 1)]:
+        c = blob.copy()
+        c[8 * word:8 * word + 8] = np.frombuffer(np.uint64(value).tobytes(), np.uint8)
+        bad.append(c)
+    for c in bad:
+        with pytest.raises(_lib.DRError) as e:
+            b.state_load(c)
+        assert e.value.code == _lib.DR_ERR_INVALID_ARG
     b.state_load(blob)
     b.step(9)
     img_b = b.readback_accum()
