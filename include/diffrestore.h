@@ -289,8 +289,12 @@ int dr_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int64_t n
 
 /* Splats M caller-made records (DEVICE, 16 bytes each: uint32 pixel index,
  * float r, g, b) into the accumulator with the same sort + reduce as the
- * chain records.  Pixel indices must be < W * H (checked on the host side
- * only by the caller).  Asynchronous. */
+ * chain records.  Pixel indices must be < W * H: a record at or above it
+ * is not added, and the call returns DEVICE_CHECK.  The other pixels'
+ * sums are then unspecified (the sort orders by the low key bits only), so
+ * clear the image with dr_clear_image.  The context's own device-check state
+ * is not touched.  Allocates temporary device memory and synchronises.
+ * Errors: INVALID_ARG, STATE (no image yet), OOM, CUDA, DEVICE_CHECK. */
 int dr_splat_records(dr_ctx* ctx, const void* recs, int64_t M);
 
 /* Resets the accumulator and tourCount without touching the chains (a new
@@ -475,7 +479,9 @@ int dr_set_bvh_builder(dr_ctx* ctx, int32_t builder, int32_t radius);
  *           only read.
  *   M       0 .. DR_NOALLOC_MAX_RECORDS; larger M is rejected with
  *           DR_ERR_INVALID_ARG (split the records into batches).
- *   n_pix   number of pixels; records with pixel >= n_pix are skipped.
+ *   n_pix   number of pixels; pixel indices must be < n_pix (a record at
+ *           or above it is not added, and the other pixels' sums are
+ *           then unspecified: the sort orders by the low key bits).
  *   accum   DEVICE FP64 [n_pix * 3], added to (not cleared).
  *   cuda_stream  stream to issue on (NULL: legacy default stream).
  * All pointers must belong to the current CUDA device.  The scratch is a

@@ -1640,24 +1640,36 @@ int dr_splat_records(dr_ctx* c, const void* recs, int64_t M) {
   DR_CUDA(cudaSetDevice(c->device));
   SplatRec* a = nullptr;
   SplatRec* b = nullptr;
+  uint32_t* bad = nullptr;  // this call's own check word: a bad record fails this call only
   void* scratch = nullptr;
   int r = dalloc(&a, (size_t)M);
   if (r == DR_OK) r = dalloc(&b, (size_t)M);
+  if (r == DR_OK) r = dalloc(&bad, 1);
   if (r == DR_OK && cudaMalloc(&scratch, sort_scratch_bytes((size_t)M)) != cudaSuccess) {
     cudaGetLastError();
     scratch = nullptr;
     r = fail(DR_ERR_OOM, "dr_splat_records: scratch");
   }
   if (r == DR_OK) {
-    cudaMemcpyAsync(a, recs, (size_t)M * sizeof(SplatRec), cudaMemcpyDeviceToDevice, c->stream);
-    SplatRec* sorted = sort_splat_records(a, b, (size_t)M, key_bits((long long)c->W * c->H), scratch, c->stream);
-    launch_segment_reduce(sorted, (size_t)M, c->accum, (uint32_t)((size_t)c->W * c->H), c->err, c->stream);
-    cudaError_t e = cudaStreamSynchronize(c->stream);
-    if (e == cudaSuccess) e = cudaGetLastError();
+    cudaError_t e = cudaMemcpyAsync(a, recs, (size_t)M * sizeof(SplatRec), cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(bad, 0, sizeof(uint32_t), c->stream);
+    if (e == cudaSuccess) {
+      SplatRec* sorted = sort_splat_records(a, b, (size_t)M, key_bits((long long)c->W * c->H), scratch, c->stream);
+      launch_segment_reduce(sorted, (size_t)M, c->accum, (uint32_t)((size_t)c->W * c->H), bad, c->stream);
+      e = cudaStreamSynchronize(c->stream);
+      if (e == cudaSuccess) e = cudaGetLastError();
+    } else {
+      cudaGetLastError();
+    }
+    uint32_t flags = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&flags, bad, sizeof(flags), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) r = fail(DR_ERR_CUDA, std::string("dr_splat_records: ") + cudaGetErrorString(e));
+    else if (flags) r = fail(DR_ERR_DEVICE_CHECK, "dr_splat_records: a record's pixel index is >= W * H");
   }
   dfree(&a);
   dfree(&b);
+  dfree(&bad);
   if (scratch) cudaFree(scratch);
   return r;
 }

@@ -757,6 +757,18 @@ def test_splat_is_bit_exact_sequential_sum(torch, R):
     for c in range(3):
         ref[:, c] = np.bincount(pix, weights=val[:, c].astype(np.float64), minlength=W * H)
     assert np.array_equal(acc, ref)
+    # a pixel index >= W * H fails this call only (the kernel skips the
+    # record); the context goes on stepping and splatting
+    from paper_2605_08916_gb300 import _lib
+    bad = rec[:1000].copy()
+    bad[17, 0] = W * H
+    with pytest.raises(_lib.DRError) as e:
+        r.splat_records(torch.from_numpy(bad).cuda())
+    assert e.value.code == _lib.DR_ERR_DEVICE_CHECK
+    r.clear_image()
+    r.splat_records(torch.from_numpy(rec).cuda())
+    assert np.array_equal(r.readback_accum(), ref)
+    r.step(2)
     r.close()
 
 
