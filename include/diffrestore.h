@@ -279,7 +279,8 @@ int dr_eval_logp(dr_ctx* ctx, int32_t max_path_len, const float* x, int64_t M, f
 
 /* Closest-hit queries through the BVH: rays [n * 6] (origin, direction;
  * DEVICE), tri [n] original triangle id or -1, t [n] distance (inf on miss).
- * `exclude` is a triangle id to skip (-1: none).  Asynchronous. */
+ * `exclude` is a triangle id to skip (-1: none).  Asynchronous.
+ * Errors: INVALID_ARG (NULL pointer, n < 0), STATE (no single scene), CUDA. */
 int dr_trace_closest(dr_ctx* ctx, const float* rays, int64_t n, int32_t exclude, int32_t* tri, float* t);
 
 /* Philox4x32-10 (Salmon et al. 2011, cited in Sec. 4.3) on DEVICE buffers:

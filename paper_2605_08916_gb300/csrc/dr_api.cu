@@ -1621,6 +1621,7 @@ int dr_eval_logp(dr_ctx* c, int32_t L, const float* x, int64_t M, float* logp, f
 
 int dr_trace_closest(dr_ctx* c, const float* rays, int64_t n, int32_t exclude, int32_t* tri, float* t) {
   if (!c || !rays || !tri || !t) return fail(DR_ERR_INVALID_ARG, "dr_trace_closest: NULL argument");
+  if (n < 0) return fail(DR_ERR_INVALID_ARG, "dr_trace_closest: n < 0");
   if (c->target != 0) return fail(DR_ERR_STATE, "dr_trace_closest: no scene");
   DR_CUDA(cudaSetDevice(c->device));
   launch_trace(dev_scene(c), rays, n, exclude, tri, t, c->err, c->stream);
