@@ -55,6 +55,16 @@ def test_local_dynamics_one_step_moments(oracle):
     assert np.allclose(cov, stddev ** 2 * np.eye(2), atol=4 * stddev ** 2 * np.sqrt(2.0 / n))
 
 
+def test_local_dynamics_wrap_rule(oracle):
+    """With stddev = 0 and gamma_tilde = 0 Alg. 4 only wraps x onto the torus
+    (x - floor(x)).  A tiny negative coordinate gives 1 - 2^-60, which rounds
+    to 1.0 in FP64 and must come back as 0 (the reading for results that
+    round to 1); whole periods are removed in both directions."""
+    x = np.array([-2.0 ** -60, 1.25, -0.25, 3.5, 0.0, 1.0 - 2.0 ** -53])
+    out = oracle.local_dynamics(x, np.zeros_like(x), 0.0, 0.0, seed=1, frame=0, step=1, chain=0)
+    assert out.tolist() == [0.0, 0.25, 0.75, 0.5, 0.0, 1.0 - 2.0 ** -53]
+
+
 @pytest.mark.parametrize("gt_factor", [0.0, 1.0])
 def test_stationary_covariance_closed_form(oracle, gt_factor):
     O = oracle
