@@ -1,7 +1,8 @@
 """Host-side pieces of bench.py (no GPU): the committed traffic capture is
 used only while the traversal sources hash to the recorded value and the
 chain count matches; the input byte counts of flat and instanced uploads;
-the workload table's scene sizes."""
+the workload table's scene sizes; the reference arm's line (the FP64 oracle
+on the host cores) and the bounded CPU-baseline sample."""
 import os
 import sys
 
@@ -53,3 +54,46 @@ def test_workload_table():
     assert (sc.width, sc.height, sc.n_tris) == (64, 64, 34) and wl["drift"] == "fd" and wl["L"] == 4
     for name, w in bench.WORKLOADS.items():
         assert w["chains"] > 0 and 1 <= w["L"] <= 16 and w["spp"] >= 1, name
+
+
+def _run_bench(args, env_extra=None):
+    import json
+    import subprocess
+    env = dict(os.environ)
+    env.update(env_extra or {})
+    p = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py")] + args, cwd=ROOT, env=env,
+                       capture_output=True, text=True, timeout=600)
+    assert p.returncode == 0, p.stderr[-2000:]
+    lines = [ln for ln in p.stdout.splitlines() if ln.startswith("{")]
+    return [json.loads(ln) for ln in lines]
+
+
+def test_reference_arm_line():
+    """The reference arm (the FP64 oracle on the host cores) prints one line
+    with the contract's keys, on the workload and metric of the GPU arm."""
+    (line,) = _run_bench(["--impl", "reference", "--workload", "cornell-64-fd", "--steps", "3", "--warmup", "3"])
+    for k in ["metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"]:
+        assert k in line, k
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["unit"] == bench.UNIT
+    assert line["steps"] == 3 and line["warmup"] == 3 and line["value"] > 0 and line["higher_is_better"]
+    assert line["config"]["workload"] == "cornell-64-fd"
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == line["value"] and cb["cores"] >= 1 and cb["sample"]
+    assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+
+
+def test_reference_arm_other_ranks_exit_quietly():
+    """Under torchrun only rank 0 runs the reference arm; the others exit 0
+    without work and print no line."""
+    env = {"RANK": "1", "LOCAL_RANK": "1", "WORLD_SIZE": "2", "MASTER_ADDR": "127.0.0.1", "MASTER_PORT": "29999"}
+    assert _run_bench(["--impl", "reference", "--workload", "cornell-64-fd", "--steps", "3", "--warmup", "3"],
+                      env) == []
+
+
+def test_cpu_baseline_reports_a_bounded_sample():
+    wl = bench.WORKLOADS["cornell-64-fd"]
+    cb = bench.cpu_baseline(wl, wl["scene"](), steps=2, target_s=0.2)
+    assert cb["kind"] == "oracle" and cb["unit"] == bench.UNIT and cb["value"] > 0 and cb["cores"] >= 1
+    assert cb["seconds"] < 30 and "chains x 3 steps" in cb["sample"]
