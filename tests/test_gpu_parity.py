@@ -862,6 +862,19 @@ def test_errors_are_reported_not_raised_on_device(torch, R):
         with pytest.raises(_lib.DRError) as e:
             r.upload_scene(S.Scene(metal.verts, metal.tris, metal.tri_mat, mats, metal.camera, 8, 8))
         assert e.value.code == _lib.DR_ERR_INVALID_ARG
+    # a non-finite vertex, a material index past the table, an unknown
+    # material type: all rejected on the host
+    for bad in ("vertex", "material index", "material type"):
+        v, tm, mats = scene.verts.copy(), scene.tri_mat.copy(), scene.materials.copy()
+        if bad == "vertex":
+            v[3, 1] = np.nan
+        elif bad == "material index":
+            tm[5] = mats.shape[0]
+        else:
+            mats[0, 0] = 7.0
+        with pytest.raises(_lib.DRError) as e:
+            r.upload_scene(S.Scene(v, scene.tris, tm, mats, scene.camera, 8, 8))
+        assert e.value.code == _lib.DR_ERR_INVALID_ARG, bad
     r.upload_scene(scene)
     r.init_chains(64, 1, R.make_params(L=3, drift="adjoint", k0=100.0))
     r.step(2)
