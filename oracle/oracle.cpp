@@ -31,7 +31,8 @@
 //     dielectric, and a rough GGX conductor whose Fresnel reflectance is
 //     computed from the Fresnel equations in complex arithmetic.
 // Pins (tests/test_oracle_*.py): closed-form moments, kill rates and images
-// for the chain logic; BVH vs brute force, a white furnace and a form factor
+// for the chain logic, the O(dt) decay of the discretisation bias and the
+// torus wrap; BVH vs brute force, a white furnace and a form factor
 // for f; pdf integrals, reciprocity, GGX energy and Fresnel closed forms for
 // the materials; dual gradients vs central differences; Philox vs an
 // independent implementation.
