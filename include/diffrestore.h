@@ -117,7 +117,9 @@ int dr_destroy(dr_ctx* ctx);
  *              triangles form the light set used by next-event estimation.
  *   camera     float [10]: eye xyz, look-at xyz, up xyz, vertical fov (deg)
  *   width, height  image size in pixels (>= 1; width * height < 2^31)
- * Synchronises the stream.  Errors: INVALID_ARG, OOM, CUDA. */
+ * Synchronises the stream.  Errors: INVALID_ARG, OOM, CUDA, DEVICE_CHECK.
+ * INVALID_ARG leaves the context as it was; after any other error it has no
+ * scene (and no chains) until an upload succeeds. */
 int dr_scene_upload(dr_ctx* ctx, const float* verts, int32_t nv, const int32_t* tris, const float* normals,
                     int32_t nt, const int32_t* tri_mat, const float* mats, int32_t nm, const float* camera,
                     int32_t width, int32_t height);
@@ -220,7 +222,8 @@ int dr_get_scene_counters(dr_ctx* ctx, int32_t scene, uint64_t* tour_count, doub
  * sig[k]^2 I) (differences to the nearest image), or the constant `cval`
  * when K = 0.  f = (g, g, g); the pixel comes from (x0, x1) on a
  * width x height grid.  HOST pointers w [K], mu [K * d], sig [K].
- * d must be even, 2..62.  Errors: INVALID_ARG, OOM, CUDA. */
+ * d must be even, 2..62.  Errors: INVALID_ARG, OOM, CUDA.  INVALID_ARG
+ * leaves the context as it was; after any other error it has no target. */
 int dr_target_mixture(dr_ctx* ctx, int32_t d, int32_t K, const float* w, const float* mu, const float* sig,
                       float cval, int32_t width, int32_t height);
 
@@ -231,7 +234,10 @@ int dr_target_mixture(dr_ctx* ctx, int32_t d, int32_t K, const float* w, const f
  * k0 = p_lambda / (m dt) with p_lambda estimated from the same initial
  * samples (Eq. killing-rate-constant), computed before the init clock runs.
  * prm is a HOST pointer, copied.  Synchronises when k0 is estimated.
- * Errors: STATE (no scene/target), INVALID_ARG, OOM, CUDA, DEVICE_CHECK. */
+ * Errors: STATE (no scene/target), INVALID_ARG, OOM, CUDA, DEVICE_CHECK.
+ * INVALID_ARG leaves earlier chains in place; after any other error the
+ * context has no chains (dr_step and the other chain calls give STATE)
+ * until an init succeeds. */
 int dr_chains_init(dr_ctx* ctx, uint64_t n_chains, uint64_t seed, uint32_t frame, const dr_params* prm);
 
 /* Evolve (Alg. 2 with LocalDynamics, Alg. 4) n_steps times: killed chains

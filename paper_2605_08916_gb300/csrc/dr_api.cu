@@ -967,8 +967,6 @@ int dr_scene_upload(dr_ctx* c, const float* verts, int32_t nv, const int32_t* tr
   });
   for (int p = 0; p < ntp; ++p)
     if (tp[p].bad_index) return fail(DR_ERR_INVALID_ARG, "dr_scene_upload: vertex index out of range");
-  free_batch(c);
-  free_two_level(c);
   for (int p = 0; p < ntp; ++p)
     if (tp[p].bad_mat) return fail(DR_ERR_INVALID_ARG, "dr_scene_upload: material out of range");
   for (int i = 0; i < nm; ++i) {
@@ -1041,6 +1039,14 @@ int dr_scene_upload(dr_ctx* c, const float* verts, int32_t nv, const int32_t* tr
     c->cam.ty = (float)th;
     c->cam.tx = (float)(th * width / height);
   }
+  // Every check has passed: the old scene (target or batch) is replaced from
+  // here on.  Until this upload succeeds the context has none, so no call
+  // can reach a buffer that is freed or reallocated below.
+  c->target = -1;
+  c->inited = false;
+  c->target_gen++;
+  free_batch(c);
+  free_two_level(c);
   // device arrays
   float* dverts = nullptr;
   int* dtris = nullptr;
@@ -1123,6 +1129,11 @@ int dr_target_mixture(dr_ctx* c, int32_t d, int32_t K, const float* w, const flo
   for (int k = 0; k < K; ++k)
     if (!(sig[k] > 0.f)) return fail(DR_ERR_INVALID_ARG, "dr_target_mixture: sigma must be > 0");
   DR_CUDA(cudaSetDevice(c->device));
+  // the old target is replaced from here on: until this call succeeds the
+  // context has none (no call can reach a buffer freed below)
+  c->target = -1;
+  c->inited = false;
+  c->target_gen++;
   free_batch(c);
   DR_TRY(dalloc(&c->mw, std::max(1, K)));
   DR_TRY(dalloc(&c->mmu, std::max(1, K * d)));
@@ -1156,7 +1167,7 @@ static int validate_params(const dr_params* p) {
   return DR_OK;
 }
 
-static int alloc_chains(dr_ctx* c, unsigned long long N, int d, int spp) {
+static int alloc_chains_sized(dr_ctx* c, unsigned long long N, int d, int spp) {
   const size_t nd = (size_t)N * d;
   if (nd > c->state_cap) {
     DR_TRY(dalloc(&c->x, nd));
@@ -1196,6 +1207,25 @@ static int alloc_chains(dr_ctx* c, unsigned long long N, int d, int spp) {
     c->accum_n = na;
   }
   return DR_OK;
+}
+
+// Sizes the chain buffers for an init.  The context has no chains until the
+// caller's init succeeds (a failure here or later in the init leaves
+// dr_step and the other chain calls refusing with STATE).  dalloc frees a
+// buffer before it allocates the larger one, so a failed allocation forgets
+// every capacity: the next init allocates afresh and no call can reach a
+// freed or null buffer.
+static int alloc_chains(dr_ctx* c, unsigned long long N, int d, int spp) {
+  c->inited = false;
+  const int r = alloc_chains_sized(c, N, d, spp);
+  if (r != DR_OK) {
+    c->state_cap = 0;
+    c->chains_cap = 0;
+    c->rec_cap_records = 0;
+    c->p_partial_cap = 0;
+    c->accum_n = 0;
+  }
+  return r;
 }
 
 int dr_scenes_upload_batch(dr_ctx* c, const dr_scene_desc* sd, int32_t n) {
