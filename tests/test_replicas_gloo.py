@@ -150,3 +150,13 @@ def test_init_agreement_without_a_process_group_is_local():
     assert r.params.k0 == k0
     given = O.make_params(L=1, drift="exact", k0=123.0)
     assert init_chains_agreed(r, 64, 5, given) == 123.0 and r.params is given
+
+
+def test_merge_without_tours_gives_a_zero_image():
+    """As Resolve (Alg. 3) with tourCount = 0: a zero image, not a division
+    by zero."""
+    from paper_2605_08916_gb300.replicas import merge_and_resolve
+    img, total = merge_and_resolve(torch.full((12,), 3.0, dtype=torch.float64), 0, 5.0)
+    assert total == 0 and int(torch.count_nonzero(img)) == 0
+    img, total = merge_and_resolve(torch.full((12,), 3.0, dtype=torch.float64), 4, 5.0)
+    assert total == 4 and torch.equal(img, torch.full((12,), 3.75, dtype=torch.float64))
