@@ -109,11 +109,16 @@ def traversal_traffic(workload, n_chains):
 
 
 def measured_peaks():
+    """HBM copy bandwidth (GB/s) measured on this machine's GPUs, else the
+    earlier GB300 measurement of 6.8 TB/s, marked "fallback"."""
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(p):
+    try:
         with open(p) as f:
-            d = json.load(f)
-        return float(d["hbm_gbs"]), "measured"
+            v = float(json.load(f)["hbm_gbs"])
+        if v > 0:
+            return v, "measured"
+    except (OSError, ValueError, KeyError, TypeError):
+        pass
     return 6800.0, "fallback"
 
 

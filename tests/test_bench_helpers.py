@@ -97,3 +97,14 @@ def test_cpu_baseline_reports_a_bounded_sample():
     cb = bench.cpu_baseline(wl, wl["scene"](), steps=2, target_s=0.2)
     assert cb["kind"] == "oracle" and cb["unit"] == bench.UNIT and cb["value"] > 0 and cb["cores"] >= 1
     assert cb["seconds"] < 30 and "chains x 3 steps" in cb["sample"]
+
+
+def test_measured_peaks_reads_the_file_or_falls_back(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.measured_peaks() == (6800.0, "fallback")            # absent
+    (tmp_path / "MEASURED_PEAKS.json").write_text("{not json")
+    assert bench.measured_peaks() == (6800.0, "fallback")            # malformed
+    (tmp_path / "MEASURED_PEAKS.json").write_text('{"bf16_tflops": 1800}')
+    assert bench.measured_peaks() == (6800.0, "fallback")            # no HBM figure
+    (tmp_path / "MEASURED_PEAKS.json").write_text('{"hbm_gbs": 6785.9}')
+    assert bench.measured_peaks() == (6785.9, "measured")
