@@ -230,3 +230,22 @@ def test_cornell_restore_image_matches_path_tracing(oracle):
     assert abs(mean.sum() / ref.sum() - 1.0) < 0.03
     assert np.mean(np.abs(z) < 3) >= 0.97
     assert np.mean(z ** 2) < 1.6
+
+
+def test_default_parameters_are_the_papers(oracle):
+    """The defaults of both sides are the parameters the paper prints
+    (tests/golden/paper_parameters.json, cited there): stddev, dt, m and eps;
+    gamma_tilde defaults to stddev^2 / 2 (the reading for the unspecified
+    gamma).  The Metropolis entries of the file belong to comparison systems
+    that are not built."""
+    import json
+    import os
+    from paper_2605_08916_gb300 import renderer as R
+    with open(os.path.join(os.path.dirname(__file__), "golden", "paper_parameters.json")) as f:
+        g = json.load(f)
+    po, pr = oracle.make_params(), R.make_params()
+    for key in ("stddev", "dt", "m", "eps"):
+        assert getattr(po, key) == g[key], key                        # FP64 fields
+        assert getattr(pr, key) == np.float32(g[key]), key            # FP32 fields of the C ABI
+    assert po.gamma_tilde == 0.5 * g["stddev"] ** 2
+    assert pr.gamma_tilde == np.float32(0.5 * g["stddev"] ** 2)
