@@ -34,8 +34,11 @@
 // for the chain logic, the O(dt) decay of the discretisation bias and the
 // torus wrap; BVH vs brute force, a white furnace and a form factor
 // for f; pdf integrals, reciprocity, GGX energy and Fresnel closed forms for
-// the materials; dual gradients vs central differences; Philox vs an
-// independent implementation.
+// the materials; the dielectric branch by the n^2 radiance scaling inside
+// glass in an emitting room and by where Snell's and the mirror law land
+// rays through a slab; dual gradients vs central differences; fd_score vs a
+// mixture's closed-form gradient, the dual gradient and the torus seam;
+// Philox vs an independent implementation.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>

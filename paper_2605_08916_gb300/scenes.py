@@ -554,6 +554,58 @@ def furnace_box(albedo=0.5, emission=1.0, width=8, height=8):
     return b.build(cam, width, height, "furnace")
 
 
+def glass_furnace(camera_inside=False, emission=1.0, ior=1.5, n_theta=12, n_phi=16, width=8, height=8):
+    """A glass body inside a closed room whose walls are black emitters
+    (radiance ``emission``, facing inward).  The glass is a UV sphere of
+    radius 1 at (0, 1, 0) with flat facets (no shading normals).  The camera
+    sits at the sphere's centre (``camera_inside``) or between the sphere and
+    a wall.  Every path that reaches a wall ends there, so its contribution
+    is fixed by the radiance scaling of the refractions it went through."""
+    b = _Builder()
+    wall = b.add_material(material(MAT_EMITTER, emission=(emission,) * 3))
+    for f in _box_faces((-3.0, -2.0, -3.0), (3.0, 4.0, 3.0), bottomless=False, inward=True):
+        b.add_quad(*f, wall)
+    sv, st, _ = uv_sphere((0.0, 1.0, 0.0), 1.0, n_theta, n_phi)
+    b.add_mesh(sv, st, b.add_material(material(MAT_DIELECTRIC, ior=ior)))
+    if camera_inside:
+        cam = [0.0, 1.0, 0.0, 0.3, 1.2, -1.0, 0.0, 1.0, 0.0, 70.0]
+    else:
+        cam = [0.0, 1.0, 2.7, 0.0, 1.0, 0.0, 0.0, 1.0, 0.0, 50.0]
+    return b.build(cam, width, height, "glass-furnace-" + ("inside" if camera_inside else "outside"))
+
+
+def glass_slab_stripes(thickness=1.0, stripe=0.05, ior=1.5, width=8, height=8):
+    """A camera at the origin looking down -z at a closed glass slab
+    (z in [-1 - thickness, -1], 60 x 60 wide).  Black emitter stripes of width
+    ``stripe`` along x lie behind the slab at z = -4 (facing +z) and behind
+    the camera at z = +3 (facing -z); stripe k (x in [k s, (k + 1) s]) emits
+    ``stripe_radiance(k, side)``.  Where a refracted or reflected ray lands,
+    and therefore the path's contribution, follows from Snell's law and the
+    mirror law in closed form."""
+    b = _Builder()
+    glass = b.add_material(material(MAT_DIELECTRIC, ior=ior))
+    z0, z1 = -1.0 - thickness, -1.0
+    for f in _box_faces((-30.0, -30.0, z0), (30.0, 30.0, z1), bottomless=False, inward=False):
+        b.add_quad(*f, glass)
+    n = int(round(6.0 / stripe))
+    for side, z in ((0, -4.0), (1, 3.0)):
+        for k in range(-n, n):
+            xa, xb = k * stripe, (k + 1) * stripe
+            m = b.add_material(material(MAT_EMITTER, emission=(stripe_radiance(k, side),) * 3))
+            if side == 0:   # facing +z
+                b.add_quad((xa, -6.0, z), (xb, -6.0, z), (xb, 6.0, z), (xa, 6.0, z), m)
+            else:           # facing -z
+                b.add_quad((xa, -6.0, z), (xa, 6.0, z), (xb, 6.0, z), (xb, -6.0, z), m)
+    cam = [0.0, 0.0, 0.0, 0.0, 0.0, -1.0, 0.0, 1.0, 0.0, 60.0]
+    return b.build(cam, width, height, "glass-slab-stripes")
+
+
+def stripe_radiance(k, side):
+    """Radiance of stripe k of ``glass_slab_stripes`` (side 0 behind the slab,
+    1 behind the camera): neighbouring stripes always differ."""
+    return 1.0 + (k % 7) + 10.0 * side
+
+
 def parallel_squares(half_light=0.5, height=1.0, albedo=0.5, radiance=1.0, glossy=False,
                      roughness=0.2, width=1, height_px=1):
     """A large receiving floor (y = 0) under a square emitter of half-side

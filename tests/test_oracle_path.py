@@ -300,3 +300,96 @@ def test_philox_matches_independent_implementation(oracle):
         key = np.tile(np.array([s & 0xFFFFFFFF, (s >> 32) & 0xFFFFFFFF], np.uint32), (ctr.shape[0], 1))
         mine = oracle.philox4x32_10(ctr, key)
         assert np.array_equal(mine.ravel(), np.array(r, np.uint32)), s
+
+
+def _mixture_grad_logp(mix, x, eps):
+    """Closed-form grad log(g + eps) of an isotropic Gaussian mixture on the
+    torus (nearest-image differences): grad g = -sum_k c_k delta_k / s_k^2."""
+    g = np.zeros(x.shape[0])
+    gg = np.zeros_like(x)
+    for k in range(mix.K):
+        dd = x - mix.mu[k]
+        dd -= np.round(dd)
+        s2 = mix.sig[k] ** 2
+        c = mix.w[k] * np.exp(-0.5 * (dd * dd).sum(1) / s2) / (2 * math.pi * s2) ** (0.5 * mix.d)
+        g += c
+        gg -= c[:, None] * dd / s2
+    return gg / (g + eps)[:, None]
+
+
+def test_fd_score_matches_mixture_gradient(oracle):
+    """The finite-difference drift (Alg. 4's score by central differences,
+    the plain form of the numerical study) against the mixture's closed-form
+    gradient.  Central differences with step h err by at most
+    h^2 / 6 max|d^3 log p|; with components of s >= 0.05 and points within
+    three s of a mean, |d^3 log p| < (3 / s)^3 = 2.2e5, so at h = 1e-5 the
+    truncation is below 4e-6 and FP64 rounding (1e-16 / h) below 1e-10.
+    A dropped factor 2, a sign or an index error fails by orders of
+    magnitude.  Points next to the torus seam (a coordinate within h of 0)
+    check that x +- h wraps: the nearest-image density is smooth across it."""
+    mix = S.gaussian_mixture(seed=7, d=4, K=3, sig_range=(0.05, 0.09))
+    tgt = oracle.target(mix)
+    rng = np.random.default_rng(12)
+    comp = rng.integers(0, mix.K, 400)
+    x = mix.mu[comp] + rng.normal(size=(400, mix.d)) * mix.sig[comp][:, None] * rng.uniform(0, 1, (400, 1))
+    x -= np.floor(x)
+    # points on the seam of a component moved next to it
+    seam = S.single_gaussian([0.0, 0.3, 0.6, 0.99], 0.06)
+    xs = np.array([[1e-6, 0.31, 0.58, 0.985], [0.999999, 0.29, 0.61, 0.995], [0.02, 0.3, 0.6, 1e-7]])
+    h, eps = 1e-5, 1e-8
+    for m, pts, big in ((mix, x, 10.0), (seam, xs, 2.0)):
+        t = oracle.target(m)
+        s = oracle.fd_score(t, pts, L=1, eps=eps, h=h)
+        ref = _mixture_grad_logp(m, pts, eps)
+        err = np.abs(s - ref)
+        assert np.all(err <= 4e-6 + 1e-9 * np.abs(ref)), err.max()
+        assert np.abs(ref).max() > big
+    # on a scene, a coordinate within h of the seam must be differenced
+    # across it: the neighbour of 1 - h/2 at +h is h/2 (x lives on T^d)
+    scene, L = S.cornell_box(1, 16, 16), 4
+    st = oracle.target(scene)
+    d = S.pss_dim(L)
+    xq = np.random.default_rng(14).random((64, d))
+    for i, at, hi, lo in ((4, 1.0 - h / 2, h / 2, 1.0 - 1.5 * h), (5, h / 2, 1.5 * h, 1.0 - h / 2)):
+        xs_ = xq.copy()
+        xs_[:, i] = at
+        s = oracle.fd_score(st, xs_, L=L, eps=eps, h=h)[:, i]
+        up, dn = xs_.copy(), xs_.copy()
+        up[:, i] = hi
+        dn[:, i] = lo
+        ref = (oracle.evaluate(st, up, L)["logp"] - oracle.evaluate(st, dn, L)["logp"]) / (2 * h)
+        assert np.allclose(s, ref, rtol=1e-6, atol=1e-6) and np.abs(ref).max() > 100.0, i
+    # the dual gradient of the exact drift agrees too
+    r = oracle.evaluate(tgt, x, L=1, grad=True)
+    assert np.allclose(r["grad"], _mixture_grad_logp(mix, x, eps), rtol=1e-12, atol=1e-12)
+
+
+def test_fd_score_matches_dual_gradient_on_scenes(oracle):
+    """fd_score (FP64 central differences at h = 1e-6) against the
+    forward-mode dual gradient of the same f on scene points whose discrete
+    choices (triangles, lobes, light visibility, pixel) are the same at
+    every x +- h e_i; the bound is that of P4."""
+    h = 1e-6
+    for scene, L in [(S.cornell_box(1, 16, 16), 4), (S.cornell_box(2, 16, 16, glossy=True), 5),
+                     (S.caustic_scene(1, 16, 16, n_theta=12, n_phi=12), 6)]:
+        tgt = oracle.target(scene)
+        d = S.pss_dim(L)
+        x = np.random.default_rng(13).random((800, d))
+        r = oracle.evaluate(tgt, x, L, grad=True, info=True)
+        lit = r["f"].sum(1) > 0
+        x, g, info, pix = x[lit], r["grad"][lit], r["info"][lit], r["pix"][lit]
+        M = x.shape[0]
+        xp = np.repeat(x, d, 0)
+        xm = xp.copy()
+        idx = np.tile(np.arange(d), M)
+        xp[np.arange(M * d), idx] += h
+        xm[np.arange(M * d), idx] -= h
+        same = np.ones(M, bool)
+        for xx in (xp, xm):
+            rr = oracle.evaluate(tgt, xx, L, info=True)
+            ok = np.all(rr["info"] == np.repeat(info, d, 0), 1) & (rr["pix"] == np.repeat(pix, d, 0))
+            same &= ok.reshape(M, d).all(1)
+        s = oracle.fd_score(tgt, x[same], L=L, eps=1e-8, h=h)
+        gs = g[same]
+        assert same.sum() > 50, (scene.name, same.sum())
+        assert np.all(np.abs(s - gs) <= 1e-5 * np.maximum(1.0, np.abs(gs)) + 2e-4 * np.abs(gs)), scene.name
