@@ -380,7 +380,8 @@ def run_ours(args, wl, rank, world, local):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         t_max = float(t.item())
         # the method's one exchange: merge the FP64 images and tour counts
-        merge_and_resolve(torch.from_numpy(r.readback_accum()).to(dev), c1["tour_count"], c1["k0"])
+        merge_and_resolve(torch.from_numpy(r.readback_accum()).to(dev), c1["tour_count"], c1["k0"],
+                          resolve=R.resolve_accum)
     value = N * steps * world / (t_max / 1e3)
     rays_s = rays * world / (t_max / 1e3)
     peak, peak_kind = measured_peaks()

@@ -486,22 +486,55 @@ int dr_set_bvh_builder(dr_ctx* ctx, int32_t builder, int32_t radius);
  *           only read.
  *   M       0 .. DR_NOALLOC_MAX_RECORDS; larger M is rejected with
  *           DR_ERR_INVALID_ARG (split the records into batches).
- *   n_pix   number of pixels; pixel indices must be < n_pix (a record at
- *           or above it is not added, and the other pixels' sums are
- *           then unspecified: the sort orders by the low key bits).
+ *   n_pix   number of pixels, 1 .. 2^31 - 2; pixel indices should be
+ *           < n_pix.  A record at or above it is skipped (every other
+ *           pixel's sum stays exact) and marks the call as failed, which
+ *           dr_splat_records_noalloc_status reports.
  *   accum   DEVICE FP64 [n_pix * 3], added to (not cleared).
  *   cuda_stream  stream to issue on (NULL: legacy default stream).
  * All pointers must belong to the current CUDA device.  The scratch is a
  * fixed array of about 2.1 MB in this library's device memory, present on
  * every GPU that loads the library until the process exits; it calls no
- * cudaMalloc, cudaFree or allocating routine.  The first call on a device
- * looks up the array's device address (once per device; make that first
- * call before any stream capture).  Every call on a device shares the one
- * array, so calls that overlap on the GPU (for example on two streams at
- * once) race; issue them in order on one stream, or synchronise between
- * them.  Asynchronous.  Errors: INVALID_ARG, CUDA. */
+ * cudaMalloc, cudaFree or allocating routine.  A call outside stream
+ * capture looks up the array's device address (so after a device reset the
+ * next such call finds it again); a call during capture uses the address
+ * the last call outside capture found, so make the first call on a device
+ * before any stream capture.  Every call on a device shares the one array,
+ * so calls that overlap on the GPU (for example on two streams at once)
+ * race; issue them in order on one stream, or synchronise between them.
+ * Asynchronous.  Errors: INVALID_ARG, CUDA. */
 enum { DR_NOALLOC_MAX_RECORDS = 65536 };
 int dr_splat_records_noalloc(const void* recs, int64_t M, int32_t n_pix, double* accum, void* cuda_stream);
+
+/* Outcome of the last dr_splat_records_noalloc call on the current device
+ * (its scratch array holds one error word, cleared by every call): waits
+ * for cuda_stream, then returns DR_OK, or DR_ERR_DEVICE_CHECK if a record's
+ * pixel index was >= n_pix.  Not during stream capture (STATE).
+ * Errors: STATE, CUDA, DEVICE_CHECK. */
+int dr_splat_records_noalloc_status(void* cuda_stream);
+
+/* Resolve (Alg. 3) on caller buffers, without a context: out[i] =
+ * k0 / tour_count * accum[i] for i < n, in FP64, rounded to FP32.  For
+ * replicas that summed their FP64 accumulators and tour counts (one run
+ * over the union of their chains).  accum DEVICE FP64 [n], out DEVICE FP32
+ * [n], cuda_stream may be NULL.  When tour_count = 0 it writes zeros and
+ * returns DR_ERR_STATE (as dr_resolve).  Asynchronous otherwise.
+ * Errors: INVALID_ARG (NULL pointer, n < 0, k0 not finite), STATE, CUDA. */
+int dr_resolve_accum(const double* accum, int64_t n, uint64_t tour_count, double k0, float* out, void* cuda_stream);
+
+/* The initial samples' sum of p (FP64, summed in a fixed block order) and
+ * their count, from the last dr_chains_init that estimated p_lambda
+ * (p_lambda = p_sum / n).  Replicas add these over ranks and pass the totals
+ * to dr_k0_from_p_sum, so every rank uses the k0 of the pooled samples.
+ * HOST outputs.  Errors: INVALID_ARG, STATE (no estimate: k0 was given, or
+ * the chains came from a checkpoint). */
+int dr_get_p_sum(dr_ctx* ctx, double* p_sum, uint64_t* n);
+
+/* k0 = p_lambda / (m dt) with p_lambda = p_sum / n (Eq.
+ * killing-rate-constant; m and dt from prm, a HOST pointer).  Host
+ * arithmetic only.  Errors: INVALID_ARG (n = 0, p_sum not positive and
+ * finite, m dt not positive, NULL pointer). */
+int dr_k0_from_p_sum(double p_sum, uint64_t n, const dr_params* prm, double* k0);
 
 /* Shape of the current chain state (HOST outputs, any may be NULL): number
  * of chains N, PSS dimension d and max path length L; the sizes callers of

@@ -30,7 +30,8 @@ EXPORTS = ["dr_version", "dr_last_error", "dr_create", "dr_destroy", "dr_scene_u
            "dr_bvh_info", "dr_get_launch_count", "dr_get_chain_shape", "dr_pt_render", "dr_set_bvh_builder",
            "dr_splat_records_noalloc", "dr_set_option", "dr_get_profile", "dr_frame", "dr_bvh4_info", "dr_bvh4_sah", "dr_bvh8_info", "dr_get_bounce_profile",
            "dr_scenes_upload_batch", "dr_resolve_scene", "dr_get_scene_counters", "dr_scene_upload_instanced",
-           "dr_two_level_info"]
+           "dr_two_level_info", "dr_splat_records_noalloc_status", "dr_resolve_accum", "dr_get_p_sum",
+           "dr_k0_from_p_sum"]
 DR_OPT_WORK_ORDER, DR_OPT_WAVEFRONT, DR_OPT_PROFILE, DR_OPT_BVH_WIDTH = 1, 2, 3, 4
 DR_OPT_TRAVERSE_BLOCKS, DR_OPT_REFILL, DR_OPT_RAY_ORDER, DR_OPT_TAIL_BOUNCE = 5, 6, 7, 8
 DR_OPT_TWO_LEVEL = 9
@@ -115,6 +116,10 @@ def signatures():
         "dr_get_scene_counters": ([P, I32, P, P], C.c_int),
         "dr_scene_upload_instanced": ([P, P, I32, P, I32, P, I32, P, I32, I32], C.c_int),
         "dr_two_level_info": ([P, P, P, P], C.c_int),
+        "dr_splat_records_noalloc_status": ([P], C.c_int),
+        "dr_resolve_accum": ([P, I64, U64, C.c_double, P, P], C.c_int),
+        "dr_get_p_sum": ([P, P, P], C.c_int),
+        "dr_k0_from_p_sum": ([C.c_double, U64, C.POINTER(dr_params), P], C.c_int),
     }
 
 

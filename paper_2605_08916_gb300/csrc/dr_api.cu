@@ -151,6 +151,8 @@ struct dr_ctx {
   unsigned long long launches = 0;  // kernels launched by this context
   double k0 = 0.0;
   double p_lambda = 0.0;
+  double p_init_sum = 0.0;          // sum of p over the initial samples of the last estimate
+  unsigned long long p_init_n = 0;  // their count (0: no estimate)
   bool stats = false;
   int builder = DR_BVH_PLOC;
   int ploc_radius = 16;
@@ -1471,6 +1473,7 @@ int dr_chains_init(dr_ctx* c, uint64_t n_chains, uint64_t seed, uint32_t frame, 
   DR_CUDA(cudaMemsetAsync(c->counters, 0, 4 * 8, s));
   DR_CUDA(cudaMemsetAsync(c->err, 0, 4, s));
   c->p_lambda = 0.0;
+  c->p_init_n = 0;
   if (prm->k0 <= 0.0 && use_wavefront(c)) {
     // one evaluation serves the p_lambda estimate and Init: evaluate (with
     // the adjoint for every chain), reduce p, then run the clock
@@ -1495,6 +1498,8 @@ int dr_chains_init(dr_ctx* c, uint64_t n_chains, uint64_t seed, uint32_t frame, 
     c->p_lambda = sum / (double)n_chains;
     if (!(c->p_lambda > 0.0) || !std::isfinite(c->p_lambda))
       return fail(DR_ERR_STATE, "dr_chains_init: estimated p_lambda is not positive");
+    c->p_init_sum = sum;
+    c->p_init_n = n_chains;
     c->k0 = c->p_lambda / ((double)prm->m * (double)prm->dt);
     a.k0 = c->k0;
     c->launches += launch_wavefront_step(a, w, c->stats, c->n_sm, c->tune, hook, s, kWfInitClock, p_tmp);
@@ -1523,6 +1528,8 @@ int dr_chains_init(dr_ctx* c, uint64_t n_chains, uint64_t seed, uint32_t frame, 
     c->p_lambda = sum / (double)n_chains;
     if (!(c->p_lambda > 0.0) || !std::isfinite(c->p_lambda))
       return fail(DR_ERR_STATE, "dr_chains_init: estimated p_lambda is not positive");
+    c->p_init_sum = sum;
+    c->p_init_n = n_chains;
     c->k0 = c->p_lambda / ((double)prm->m * (double)prm->dt);
     DR_CUDA(cudaMemsetAsync(c->counters, 0, 4 * 8, s));
   }
@@ -1564,6 +1571,34 @@ int dr_resolve(dr_ctx* c, float* out_rgb) {
     DR_CUDA(cudaStreamSynchronize(c->stream));
     if (tc == 0) return fail(DR_ERR_STATE, "dr_resolve: tourCount is 0 (no completed tour yet)");
   }
+  return DR_OK;
+}
+
+int dr_resolve_accum(const double* accum, int64_t n, uint64_t tour_count, double k0, float* out, void* cuda_stream) {
+  if ((!accum || !out) && n > 0) return fail(DR_ERR_INVALID_ARG, "dr_resolve_accum: NULL argument");
+  if (n < 0 || !std::isfinite(k0)) return fail(DR_ERR_INVALID_ARG, "dr_resolve_accum: n < 0 or k0 not finite");
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  launch_resolve_count(accum, (size_t)n, (unsigned long long)tour_count, k0, out, s);
+  DR_TRY(check_launch("resolve_accum"));
+  if (tour_count == 0) return fail(DR_ERR_STATE, "dr_resolve_accum: tour_count is 0 (zero image written)");
+  return DR_OK;
+}
+
+int dr_get_p_sum(dr_ctx* c, double* p_sum, uint64_t* n) {
+  if (!c || !p_sum || !n) return fail(DR_ERR_INVALID_ARG, "dr_get_p_sum: NULL argument");
+  if (!c->inited || c->p_init_n == 0)
+    return fail(DR_ERR_STATE, "dr_get_p_sum: no p_lambda estimate (k0 was given or the chains were loaded)");
+  *p_sum = c->p_init_sum;
+  *n = c->p_init_n;
+  return DR_OK;
+}
+
+int dr_k0_from_p_sum(double p_sum, uint64_t n, const dr_params* prm, double* k0) {
+  if (!prm || !k0) return fail(DR_ERR_INVALID_ARG, "dr_k0_from_p_sum: NULL argument");
+  const double mdt = (double)prm->m * (double)prm->dt;
+  if (n == 0 || !(p_sum > 0.0) || !std::isfinite(p_sum) || !(mdt > 0.0) || !std::isfinite(mdt))
+    return fail(DR_ERR_INVALID_ARG, "dr_k0_from_p_sum: n = 0, p_sum not positive, or m dt not positive");
+  *k0 = p_sum / (double)n / mdt;
   return DR_OK;
 }
 
@@ -1793,6 +1828,7 @@ int dr_state_load(dr_ctx* c, const void* host_buf, size_t bytes) {
   c->step = (uint32_t)h.step;
   c->k0 = h.k0;
   c->p_lambda = h.p_lambda;
+  c->p_init_n = 0;
   c->rec_cap = h.prm.steps_per_splat;
   c->rec_count = 0;
   const char* p = static_cast<const char*>(host_buf) + sizeof(SaveHeader);

@@ -32,6 +32,9 @@ void launch_segment_reduce(const SplatRec* sorted, size_t n, double* accum, uint
 // out[i] = k0 / tourCount * accum[i] (0 when tourCount == 0).
 void launch_resolve(const double* accum, size_t n, const unsigned long long* tour_count, double k0, float* out,
                     cudaStream_t s);
+// Resolve with the tour count given by value (replicas' merged counts).
+void launch_resolve_count(const double* accum, size_t n, unsigned long long tour_count, double k0, float* out,
+                          cudaStream_t s);
 
 // ---------------------------------------------------------------- BVH
 struct BvhBuildOut {

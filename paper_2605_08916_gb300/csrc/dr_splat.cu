@@ -229,6 +229,13 @@ __global__ void resolve_kernel(const double* __restrict__ accum, size_t n,
   out[i] = tc == 0ull ? 0.0f : (float)(k0 / (double)tc * accum[i]);
 }
 
+__global__ void resolve_count_kernel(const double* __restrict__ accum, size_t n, unsigned long long tc, double k0,
+                                     float* __restrict__ out) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  out[i] = tc == 0ull ? 0.0f : (float)(k0 / (double)tc * accum[i]);
+}
+
 }  // namespace
 
 size_t sort_scratch_bytes(size_t n) {
@@ -268,6 +275,12 @@ void launch_resolve(const double* accum, size_t n, const unsigned long long* tou
                     cudaStream_t s) {
   if (n == 0) return;
   resolve_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(accum, n, tour_count, k0, out);
+}
+
+void launch_resolve_count(const double* accum, size_t n, unsigned long long tour_count, double k0, float* out,
+                          cudaStream_t s) {
+  if (n == 0) return;
+  resolve_count_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(accum, n, tour_count, k0, out);
 }
 
 }  // namespace dr

@@ -556,6 +556,7 @@ __global__ void __launch_bounds__(kWfThreads) wf_finish(StepArgs a, WfBuffers w,
     const unsigned long long j = it * gridDim.x * blockDim.x + (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
     bool survive = false;
     int nseg = 0;
+    int kill_sid = -1;  // batch: the scene of a chain killed here
     if (j < a.N) {
       PathState ps;
       int pix;
@@ -577,7 +578,7 @@ __global__ void __launch_bounds__(kWfThreads) wf_finish(StepArgs a, WfBuffers w,
         a.killed[j] = killed ? 1 : 0;
         a.logp[j] = logf(p);
         if (BATCH) {
-          if (killed) atomicAdd(a.sc[v.sid].tour_count, 1ull);
+          if (killed) kill_sid = v.sid;
         } else {
           kills += killed ? 1ull : 0ull;
         }
@@ -591,6 +592,16 @@ __global__ void __launch_bounds__(kWfThreads) wf_finish(StepArgs a, WfBuffers w,
           a.rec[j] = rr;
         }
         survive = !killed && mode == kWfStep;
+      }
+    }
+    // a batch's tour counts: one atomic per scene present among the warp's
+    // killed chains (every lane runs the same number of iterations)
+    if (BATCH) {
+      const unsigned want = __ballot_sync(kFull, kill_sid >= 0);
+      if (kill_sid >= 0) {
+        const unsigned peers = __match_any_sync(want, kill_sid);
+        if ((int)(threadIdx.x & 31) == __ffs(peers) - 1)
+          atomicAdd(a.sc[kill_sid].tour_count, (unsigned long long)__popc(peers));
       }
     }
     // survivors queue by path length, so that the adjoint's warps run

@@ -241,6 +241,16 @@ class Renderer:
         call("dr_readback_accum", self.h, _ptr(a))
         return a
 
+    def p_sum(self):
+        """(sum of p over the initial samples, their count) of the last
+        init that estimated p_lambda."""
+        ps, n = C.c_double(), C.c_uint64()
+        call("dr_get_p_sum", self.h, C.byref(ps), C.byref(n))
+        return ps.value, n.value
+
+    def k0_from_p_sum(self, p_sum, n, params):
+        return k0_from_p_sum(p_sum, n, params)
+
     def counters(self):
         tc, st, rays = C.c_uint64(), C.c_uint64(), C.c_uint64()
         k0, pl = C.c_double(), C.c_double()
@@ -343,6 +353,27 @@ class Renderer:
         index, then float bits of r, g, b)."""
         recs = recs.contiguous()
         call("dr_splat_records", self.h, _ptr(recs), int(recs.shape[0]))
+
+
+def k0_from_p_sum(p_sum, n, params):
+    """k0 = (p_sum / n) / (m dt) computed by the library (Eq.
+    killing-rate-constant)."""
+    k0 = C.c_double()
+    call("dr_k0_from_p_sum", float(p_sum), int(n), C.byref(params), C.byref(k0))
+    return k0.value
+
+
+def resolve_accum(accum, tour_count, k0, stream=None):
+    """Resolve (Alg. 3) of an FP64 CUDA tensor by the library: k0 /
+    tour_count * accum as FP32 (zeros when tour_count is 0)."""
+    accum = accum.contiguous()
+    out = torch.empty(accum.shape, dtype=torch.float32, device=accum.device)
+    s = stream if stream is not None else torch.cuda.current_stream(accum.device)
+    code = _lib.load().dr_resolve_accum(_ptr(accum), int(accum.numel()), int(tour_count), float(k0), _ptr(out),
+                                        C.c_void_p(s.cuda_stream))
+    if not (code == _lib.DR_ERR_STATE and int(tour_count) == 0):
+        _lib.check(code, "dr_resolve_accum")
+    return out
 
 
 def philox(ctr, key, stream=None):

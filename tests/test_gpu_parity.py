@@ -12,7 +12,11 @@ Tolerances (FP32 kernels vs FP64 oracle):
   is counted as divergent from that step on; the divergent fraction is
   bounded.
 * grad log p (hand-written adjoint, FP32) vs the oracle's dual-number
-  gradient: relative L2 error <= 1e-3 on >= 97% of points with f > 0.
+  gradient: relative L2 error <= 1e-4 on >= 99% of points with f > 0 whose
+  log p agrees; vs FP64 central differences (h = 1e-6, discrete choices held
+  equal): <= 1e-4 relative on >= 99% of such points.
+* The stored score of surviving chains: 1e-4 relative for the exact drift;
+  for FP32 finite differences, plus the rounding of log p divided by h.
 """
 import math
 
@@ -204,10 +208,69 @@ def test_eval_logp_and_adjoint_match_oracle(torch, R, oracle, case):
     assert ok_lp.mean() > 0.995, ok_lp.mean()
     go = ro["grad"]
     rel = np.linalg.norm(g - go, axis=1) / np.maximum(np.linalg.norm(go, axis=1), 1e-6)
-    good = rel[lit & ok_lp] <= 1e-3
-    print(f"{case}: median rel grad err {np.median(rel[lit]):.2e}, frac<=1e-3 {good.mean():.4f}")
-    assert good.mean() >= 0.97, good.mean()
+    # the dual gradient is the derivative of the smooth piece the oracle's
+    # path lies in, which is what the adjoint differentiates wherever the
+    # FP32 path made the same discrete choices (log p agreeing)
+    good = rel[lit & ok_lp] <= 1e-4
+    q = np.quantile(rel[lit & ok_lp], [0.5, 0.99, 0.999])
+    print(f"{case}: rel grad err quantiles 50/99/99.9% {q}, frac<=1e-4 {good.mean():.4f}")
+    assert good.mean() >= 0.99, good.mean()
     r.close()
+
+
+def _fd_gradient_fp64(oracle, tgt, x, L, h=1e-6):
+    """FP64 central differences of the oracle's log p at every coordinate,
+    and whether every x +- h e_i keeps the discrete choices (triangles,
+    lobes, light visibility and pixel) of x, as Sec. 6's autodiff
+    derivative of the smooth piece requires."""
+    M, d = x.shape
+    base = oracle.evaluate(tgt, x, L, info=True)
+    idx = np.tile(np.arange(d), M)
+    rows = np.arange(M * d)
+    lp = []
+    same = np.ones(M, bool)
+    for sgn in (1.0, -1.0):
+        xx = np.repeat(x, d, 0)
+        xx[rows, idx] += sgn * h
+        rr = oracle.evaluate(tgt, xx, L, info=True)
+        ok = np.all(rr["info"] == np.repeat(base["info"], d, 0), 1) & (rr["pix"] == np.repeat(base["pix"], d, 0))
+        same &= ok.reshape(M, d).all(1)
+        lp.append(rr["logp"].reshape(M, d))
+    return (lp[0] - lp[1]) / (2 * h), same, base
+
+
+@pytest.mark.parametrize("case", list(EVAL_CASES))
+def test_adjoint_matches_fp64_central_differences(torch, R, oracle, case):
+    """The CUDA adjoint (FP32 reverse mode) against FP64 central differences
+    of the oracle's f at h = 1e-6 with every discrete choice held equal: on
+    lit points where the GPU's log p agrees with the oracle's, the gradient
+    vector agrees to 1e-4 relative (scale max(|grad|, 1)) on >= 99% of
+    them.  Points whose choices change within +-h sit on an edge of the
+    piecewise-smooth f, where the derivative of the smooth piece is not
+    what a difference measures; they are excluded and counted."""
+    make, L = EVAL_CASES[case]
+    scene = make()
+    d = S.pss_dim(L)
+    r = R.Renderer()
+    r.upload_scene(scene)
+    M = 1500
+    x = np.random.default_rng(17).random((M, d)).astype(np.float32)
+    lp, g, _, _ = r.eval_logp(torch.from_numpy(x).cuda(), L=L, grad=True)
+    torch.cuda.synchronize()
+    lp, g = lp.cpu().numpy().astype(np.float64), g.cpu().numpy().astype(np.float64)
+    r.close()
+    tgt = oracle.OracleScene(scene)
+    fd, stable, base = _fd_gradient_fp64(oracle, tgt, x.astype(np.float64), L)
+    lit = base["f"].sum(1) > 0
+    agree = np.abs(lp - base["logp"]) <= 1e-4 * np.maximum(1.0, np.abs(base["logp"]))
+    use = lit & agree & stable
+    rel = np.linalg.norm(g - fd, axis=1) / np.maximum(np.linalg.norm(fd, axis=1), 1.0)
+    q = np.quantile(rel[use], [0.5, 0.9, 0.99, 0.999]) if use.any() else []
+    print(f"{case}: lit {lit.sum()}, on an edge within h {(lit & ~stable).sum()}, log p disagreeing "
+          f"{(lit & ~agree).sum()}, compared {use.sum()}; rel err quantiles 50/90/99/99.9% {q}; "
+          f"frac <= 1e-4 {np.mean(rel[use] <= 1e-4):.4f}")
+    assert use.sum() >= 60
+    assert np.mean(rel[use] <= 1e-4) >= 0.99
 
 
 def test_logp_autograd_function(torch, R, oracle):
@@ -238,8 +301,28 @@ def test_logp_autograd_function(torch, R, oracle):
     go = ro["grad"] * w.cpu().numpy()[:, None].astype(np.float64)
     gg = x.grad.cpu().numpy().astype(np.float64)
     rel = np.linalg.norm(gg - go, axis=1) / np.maximum(np.linalg.norm(go, axis=1), 1e-6)
-    assert lit.mean() > 0.05 and np.mean(rel[lit] <= 1e-3) >= 0.97
+    print(f"LogPFunction: lit {lit.sum()}, frac rel <= 1e-4 {np.mean(rel[lit] <= 1e-4):.4f}")
+    assert lit.mean() > 0.05 and np.mean(rel[lit] <= 1e-4) >= 0.97
     r.close()
+
+
+def score_tolerance(params_orc):
+    """Per-coordinate bound on |score_gpu - score_oracle| for a chain whose
+    discrete choices agree.  Exact drift (the adjoint / the mixture's
+    gradient): 1e-4 relative to the oracle's score vector (floor 1).  Finite
+    differences in FP32: log p at x +- h carries a rounding error of about
+    1e-6 max(1, |log p|), which the difference divides by h, so the bound
+    adds 2e-6 max(1, |log p|) / h (2e-3 max(1, |log p|) at h = 1e-3)."""
+    if params_orc.drift_mode == 1:
+        h = params_orc.fd_h
+
+        def ok(sg, so, lo):
+            lim = 1e-4 * np.abs(so) + 2e-6 * np.maximum(1.0, np.abs(lo))[:, None] / h
+            return np.all(np.abs(sg - so) <= lim, axis=1)
+    else:
+        def ok(sg, so, lo):
+            return np.linalg.norm(sg - so, axis=1) <= 1e-4 * np.maximum(np.linalg.norm(so, axis=1), 1.0)
+    return ok
 
 
 def _chain_parity(torch, R, oracle, target_obj, params_gpu, params_orc, N, M, T, seed, x_tol=1e-4):
@@ -254,7 +337,9 @@ def _chain_parity(torch, R, oracle, target_obj, params_gpu, params_orc, N, M, T,
     alive = np.ones(M, bool)
     first_div = np.full(M, -1)
     n_cmp = 0
+    n_score = 0
     causes = {}
+    score_ok = score_tolerance(params_orc)
     for s in range(T + 1):
         if s > 0:
             r.step(1)
@@ -262,9 +347,14 @@ def _chain_parity(torch, R, oracle, target_obj, params_gpu, params_orc, N, M, T,
         xg, lg, kg, pg, vg = st["x"][:M], st["logp"][:M], st["killed"][:M], st["pix"][:M], st["val"][:M]
         xo, lo_, ko, po, vo = ro["x"][s], ro["logp"][s], ro["killed"][s], ro["pix"][s], ro["val"][s]
         xerr = torus_dist(xg, xo).max(1)
+        # the stored score (used by the next LocalDynamics) of surviving chains
+        survived = (kg == 0) & (ko == 0)
+        sc = ~survived | score_ok(st["score"][:M], ro["score"][s], lo_)
+        n_score += int((alive & survived).sum())
         checks = {"killed": kg == ko, "pix": pg == po, "x": xerr <= x_tol,
                   "logp": np.abs(lg - lo_) <= 1e-4 * np.maximum(1.0, np.abs(lo_)),
-                  "val": np.linalg.norm(vg - vo, axis=1) <= 1e-4 * np.linalg.norm(vo, axis=1) + 1e-12}
+                  "val": np.linalg.norm(vg - vo, axis=1) <= 1e-4 * np.linalg.norm(vo, axis=1) + 1e-12,
+                  "score": sc}
         ok = np.logical_and.reduce(list(checks.values()))
         newly = alive & ~ok
         for j in np.nonzero(newly)[0]:
@@ -277,7 +367,8 @@ def _chain_parity(torch, R, oracle, target_obj, params_gpu, params_orc, N, M, T,
         alive &= ok
         n_cmp += alive.sum()
     frac_div = 1.0 - alive.mean()
-    print("  divergence causes:", causes)
+    print("  divergence causes:", causes, "scores compared:", n_score)
+    assert n_score > M, n_score
     r.close()
     return frac_div, first_div, n_cmp
 
@@ -436,6 +527,40 @@ def test_full_size_bench_configuration_matches_oracle_on_sampled_chains(torch, R
     frac = _sampled_parity(st["x"], st["logp"], st["killed"], ro, np.arange(N)[sample])
     print(f"full-size sampled chains: divergent fraction {frac:.4f}")
     assert frac <= 0.02
+
+
+def test_full_size_caustic_matches_oracle_on_sampled_chains(torch, R, oracle):
+    """The caustic workload at full size in the bench's launch configuration
+    (19,800-triangle glass sphere, 512 x 512, L = 10, 2^18 chains,
+    bounce-by-bounce passes, one 16-step CUDA-graph frame, k0 estimated on
+    the device): 256 sampled chains followed by the oracle with the
+    device's k0 over the 16 steps; x, log p, kill flags and the stored
+    score of survivors compared at the end."""
+    scene = S.caustic_scene(1, 512, 512)
+    N, L, F, seed = 1 << 18, 10, 16, 97
+    stream = torch.cuda.Stream()
+    r = R.Renderer(0, stream)
+    r.upload_scene(scene)
+    r.init_chains(N, seed, R.make_params(L=L, drift="adjoint", rb=True, k0=0.0, steps_per_splat=F))
+    r.frame(F)
+    stream.synchronize()
+    st = r.readback_state(("x", "killed", "logp", "score"))
+    k0 = r.counters()["k0"]
+    r.close()
+    assert k0 > 0
+    sample = np.sort(np.random.default_rng(7).choice(N, 256, replace=False))
+    ro = oracle.restore_run(oracle.OracleScene(scene), oracle.make_params(L=L, drift="exact", rb=True, k0=k0),
+                            seed=seed, chain_ids=sample, n_steps=F)
+    frac = _sampled_parity(st["x"], st["logp"], st["killed"], ro, sample)
+    xo_ok = torus_dist(st["x"][sample], ro["x"][-1]).max(1) <= 1e-4
+    surv = (st["killed"][sample] == 0) & (ro["killed"][-1] == 0) & xo_ok
+    so = ro["score"][-1][surv]
+    sg = st["score"][sample][surv].astype(np.float64)
+    srel = np.linalg.norm(sg - so, axis=1) / np.maximum(np.linalg.norm(so, axis=1), 1.0)
+    print(f"caustic full size: divergent fraction {frac:.4f}; survivors compared {surv.sum()}, "
+          f"score within 1e-4: {np.mean(srel <= 1e-4):.4f}")
+    assert frac <= 0.03
+    assert surv.sum() >= 100 and np.mean(srel <= 1e-4) >= 0.97
 
 
 def test_full_size_batch_matches_oracle_on_sampled_chains(torch, R, oracle):
@@ -784,6 +909,42 @@ def test_resolve_is_k0_over_tourcount_times_accum(torch, R):
     assert c["tour_count"] > 0 and c["steps"] == 10
     ref = (acc * (c["k0"] / c["tour_count"])).astype(np.float32)
     assert np.allclose(img, ref, rtol=1e-6, atol=0)
+    r.close()
+
+
+def test_replica_calls_resolve_and_pool_like_the_context(torch, R):
+    """The context-free calls the replicas use: dr_resolve_accum on a copy of
+    the accumulator equals dr_resolve bit for bit (zero image and STATE at
+    tourCount 0), and the initial-sample sums give back the context's own
+    p_lambda and k0 through dr_k0_from_p_sum."""
+    from paper_2605_08916_gb300 import _lib
+    r = R.Renderer()
+    r.upload_scene(S.cornell_box(1, 32, 32))
+    prm = R.make_params(L=4, drift="adjoint", k0=0.0, steps_per_splat=4)
+    r.init_chains(4096, 3, prm)
+    c = r.counters()
+    p_sum, n = r.p_sum()
+    assert n == 4096 and p_sum / n == c["p_lambda"]
+    assert R.k0_from_p_sum(p_sum, n, prm) == c["k0"]
+    r.step(10)
+    img = r.resolve()
+    acc = torch.from_numpy(r.readback_accum()).cuda()
+    c = r.counters()
+    out = R.resolve_accum(acc, c["tour_count"], c["k0"])
+    torch.cuda.synchronize()
+    assert torch.equal(out.reshape(-1), img.reshape(-1))
+    zero = R.resolve_accum(acc, 0, c["k0"])
+    torch.cuda.synchronize()
+    assert int(torch.count_nonzero(zero)) == 0
+    L = _lib.load()
+    assert L.dr_resolve_accum(None, -1, 1, 1.0, None, None) == _lib.DR_ERR_INVALID_ARG
+    import ctypes
+    k0 = ctypes.c_double()
+    assert L.dr_k0_from_p_sum(1.0, 0, ctypes.byref(prm), ctypes.byref(k0)) == _lib.DR_ERR_INVALID_ARG
+    # with k0 given there is no estimate to pool
+    r.init_chains(4096, 3, R.make_params(L=4, drift="adjoint", k0=5.0, steps_per_splat=4))
+    with pytest.raises(_lib.DRError):
+        r.p_sum()
     r.close()
 
 

@@ -12,6 +12,12 @@ import torch.distributed as dist  # noqa: E402
 import torch.multiprocessing as mp  # noqa: E402
 
 
+def _oracle_resolve(accum, tour_count, k0):
+    """Stands in for the library's Resolve on a rank without a GPU."""
+    from oracle import oracle as O
+    return torch.from_numpy(O.resolve(accum.numpy(), k0, tour_count))
+
+
 def _free_port():
     s = socket.socket()
     s.bind(("127.0.0.1", 0))
@@ -35,7 +41,7 @@ def _run_rank(rank, world, port, out_dir):
         r = O.restore_run(tgt, prm, seed=replica_seed(77, rank), chain_ids=np.arange(256), n_steps=32,
                           record=False)
         acc = torch.from_numpy(r["accum"].copy())
-        img, total = merge_and_resolve(acc, r["tour_count"], k0)
+        img, total = merge_and_resolve(acc, r["tour_count"], k0, resolve=_oracle_resolve)
         np.save(os.path.join(out_dir, f"img{rank}.npy"), img.numpy())
         np.save(os.path.join(out_dir, f"tc{rank}.npy"), np.array([total]))
     finally:
@@ -77,10 +83,15 @@ class _OracleRank:
         from oracle import oracle as O
         r = O.restore_run(self.tgt, params, seed, np.arange(n), n_steps=0, record=False)
         self.n, self.seed, self.params = n, seed, params
+        self.p_init_sum = r["p_init_sum"]
         self.p_lambda = r["p_init_sum"] / n
 
-    def counters(self):
-        return {"p_lambda": self.p_lambda}
+    def p_sum(self):
+        return self.p_init_sum, self.n
+
+    @staticmethod
+    def k0_from_p_sum(p_sum, n, params):
+        return p_sum / n / (params.m * params.dt)
 
     def run(self, n_steps):
         from oracle import oracle as O
@@ -103,7 +114,8 @@ def _run_rank_agreed(rank, world, port, out_dir):
         r = _OracleRank(_mixture())
         k0 = init_chains_agreed(r, 200 + 56 * rank, replica_seed(91, rank), O.make_params(L=1, drift="exact", k0=0.0))
         out = r.run(24)
-        img, total = merge_and_resolve(torch.from_numpy(out["accum"].copy()), out["tour_count"], k0)
+        img, total = merge_and_resolve(torch.from_numpy(out["accum"].copy()), out["tour_count"], k0,
+                                       resolve=_oracle_resolve)
         np.save(os.path.join(out_dir, f"agreed{rank}.npy"), np.concatenate([[k0, total], img.numpy().ravel()]))
     finally:
         dist.destroy_process_group()
@@ -141,9 +153,10 @@ def test_ranks_agree_on_k0_and_merge_to_the_union(tmp_path):
 
 def test_init_agreement_without_a_process_group_is_local():
     from oracle import oracle as O
-    from paper_2605_08916_gb300.replicas import agree_p_lambda, init_chains_agreed
-    assert agree_p_lambda(0.25, 10) == 0.25
-    assert agree_p_lambda(0.25, 0) == 0.0
+    from paper_2605_08916_gb300.replicas import agree_p_sum, init_chains_agreed
+    assert agree_p_sum(2.5, 10) == (2.5, 10)
+    big = (1 << 62) + 3   # counts travel as 64-bit integers, exactly
+    assert agree_p_sum(1.0, big) == (1.0, big)
     r = _OracleRank(_mixture())
     k0 = init_chains_agreed(r, 64, 5, O.make_params(L=1, drift="exact", k0=0.0))
     assert k0 == pytest.approx(r.p_lambda / (64 * 1e-5), rel=1e-12)
@@ -152,11 +165,19 @@ def test_init_agreement_without_a_process_group_is_local():
     assert init_chains_agreed(r, 64, 5, given) == 123.0 and r.params is given
 
 
-def test_merge_without_tours_gives_a_zero_image():
-    """As Resolve (Alg. 3) with tourCount = 0: a zero image, not a division
-    by zero."""
+def test_merge_hands_the_summed_buffers_to_resolve():
+    """Without a process group the merge is the identity on (accum, tour
+    count), and Resolve receives them with k0 unchanged; the tour count
+    stays an exact 64-bit integer."""
     from paper_2605_08916_gb300.replicas import merge_and_resolve
-    img, total = merge_and_resolve(torch.full((12,), 3.0, dtype=torch.float64), 0, 5.0)
-    assert total == 0 and int(torch.count_nonzero(img)) == 0
-    img, total = merge_and_resolve(torch.full((12,), 3.0, dtype=torch.float64), 4, 5.0)
-    assert total == 4 and torch.equal(img, torch.full((12,), 3.75, dtype=torch.float64))
+    seen = []
+
+    def resolve(acc, tc, k0):
+        seen.append((acc.clone(), tc, k0))
+        return acc * 0 + 1
+
+    big = (1 << 62) + 1
+    img, total = merge_and_resolve(torch.full((12,), 3.0, dtype=torch.float64), big, 5.0, resolve=resolve)
+    assert total == big and seen[0][1] == big and seen[0][2] == 5.0
+    assert torch.equal(seen[0][0], torch.full((12,), 3.0, dtype=torch.float64)) and torch.equal(img, torch.ones(12,
+                                                                                                         dtype=torch.float64))
