@@ -25,7 +25,11 @@
 //     (Eq. diffusion-restore-holding-rate) and k0 = p_lambda / (m dt)
 //     (Eq. killing-rate-constant).
 //   * Analytic targets (isotropic Gaussian mixtures on the torus, constant
-//     density) used to pin the Restore/Langevin logic against closed forms.
+//     density, a density with a jump or a smoothed jump) used to pin the
+//     Restore/Langevin logic against closed forms.
+//   * The bias term L* p / p of the modified killing rate (Sec. 5.2,
+//     Eq. bias and Eq. adjoint-bias; the diagnostic of App. C) for 2-D
+//     targets, by quadrature of the Euler-Maruyama kernel of Alg. 4.
 //   * Materials (Sec. 6 "Test scenes" names pbrt's diffuse, dielectric and
 //     conductor): Lambertian, a GGX coat over Lambertian, a smooth
 //     dielectric, and a rough GGX conductor whose Fresnel reflectance is
@@ -38,7 +42,8 @@
 // glass in an emitting room and by where Snell's and the mirror law land
 // rays through a slab; dual gradients vs central differences; fd_score vs a
 // mixture's closed-form gradient, the dual gradient and the torus seam;
-// Philox vs an independent implementation.
+// L* p / p vs the Gaussian closed form, mass conservation and the O(dt) of
+// Sec. 5.2 on a smooth density; Philox vs an independent implementation.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -705,16 +710,48 @@ double mixture_eval(const Mixture& M, const double* x, double* grad) {
   return g;
 }
 
+// A density on the torus with one jump per half period along x0 (used to
+// read the bias claim of Sec. 5.2 on a discontinuous target):
+// g(x) = c2 + (c1 - c2) (1 + tanh(q(x0) / w)) / 2 with q(x0) = sin(2 pi x0) / (2 pi),
+// i.e. about c1 on x0 in (0, 1/2) and c2 on (1/2, 1), with transitions of
+// width ~w at x0 = 0 and 1/2 (q ~ +-(x0 - edge) there).  w = 0 is the sharp
+// step (the derivative of its smooth pieces is 0).  The other coordinates do
+// not enter.
+struct StepDensity {
+  int d, W, H;
+  double c1, c2, w;
+};
+
+double step_eval(const StepDensity& D, const double* x, double* grad) {
+  if (grad) std::fill(grad, grad + D.d, 0.0);
+  const double x0 = x[0] - std::floor(x[0]);
+  if (D.w <= 0.0) {
+    if (x0 == 0.0 || x0 == 0.5) return 0.5 * (D.c1 + D.c2);
+    return x0 < 0.5 ? D.c1 : D.c2;
+  }
+  const double q = std::sin(2.0 * PI * x0) / (2.0 * PI);
+  const double th = std::tanh(q / D.w);
+  if (grad) grad[0] = (D.c1 - D.c2) * 0.5 * (1.0 - th * th) / D.w * std::cos(2.0 * PI * x0);
+  return D.c2 + (D.c1 - D.c2) * 0.5 * (1.0 + th);
+}
+
 // ---------------------------------------------------------------- evaluation
 struct Target {
-  int kind;  // 0 scene, 1 mixture
+  int kind;  // 0 scene, 1 mixture, 2 step density
   Scene* S;
   Mixture* M;
   int L;
-  int d() const { return kind == 0 ? 2 + 4 * (L - 1) : M->d; }
-  int W() const { return kind == 0 ? S->W : M->W; }
-  int H() const { return kind == 0 ? S->H : M->H; }
+  StepDensity* J = nullptr;
+  int d() const { return kind == 0 ? 2 + 4 * (L - 1) : kind == 1 ? M->d : J->d; }
+  int W() const { return kind == 0 ? S->W : kind == 1 ? M->W : J->W; }
+  int H() const { return kind == 0 ? S->H : kind == 1 ? M->H : J->H; }
 };
+
+Target make_target(void* tgt, int kind, int L) {
+  Target T{kind, kind == 0 ? static_cast<Scene*>(tgt) : nullptr, kind == 1 ? static_cast<Mixture*>(tgt) : nullptr, L};
+  if (kind == 2) T.J = static_cast<StepDensity*>(tgt);
+  return T;
+}
 
 struct EvalResult {
   double f[3];
@@ -740,15 +777,16 @@ void eval_grad_scene(const Scene& S, const double* x, int L, int d, double eps, 
 // Evaluates f, p = lum(f) + eps, and (if grad) grad log p at x.
 void evaluate(const Target& T, const double* x, double eps, EvalResult& r, double* grad) {
   const int d = T.d();
-  if (T.kind == 1) {
-    const Mixture& M = *T.M;
+  if (T.kind == 1 || T.kind == 2) {
     std::vector<double> gg(d);
-    double g = mixture_eval(M, x, grad ? gg.data() : nullptr);
+    double g = T.kind == 1 ? mixture_eval(*T.M, x, grad ? gg.data() : nullptr)
+                           : step_eval(*T.J, x, grad ? gg.data() : nullptr);
     r.f[0] = r.f[1] = r.f[2] = g;
     r.p = g + eps;
-    int col = std::min(std::max((int)std::floor(x[0] * M.W), 0), M.W - 1);
-    int row = std::min(std::max((int)std::floor(x[1] * M.H), 0), M.H - 1);
-    r.pix = row * M.W + col;
+    const int W = T.W(), H = T.H();
+    int col = std::min(std::max((int)std::floor(x[0] * W), 0), W - 1);
+    int row = std::min(std::max((int)std::floor(x[1] * H), 0), H - 1);
+    r.pix = row * W + col;
     r.info = PathInfo{};
     if (grad) for (int i = 0; i < d; ++i) grad[i] = gg[i] / r.p;
     return;
@@ -990,6 +1028,58 @@ void* orc_mixture_create(int d, int K, const double* w, const double* mu, const 
 }
 void orc_mixture_destroy(void* m) { delete static_cast<Mixture*>(m); }
 
+void* orc_step_create(int d, double c1, double c2, double w, int W, int H) {
+  return new StepDensity{d, W, H, c1, c2, w};
+}
+void orc_step_destroy(void* p) { delete static_cast<StepDensity*>(p); }
+
+// The bias term of Sec. 5.2 / App. C for a target on T^2 (d = 2):
+// (L* p / p)(y) = h ((K* p)(y) / p(y) - 1), where L f = h (K f - f) is the
+// generator of the continuous-time embedding of the local dynamics with
+// holding rate h = 1 / dt (Sec. 4, Eq. diffusion-restore-holding-rate),
+// K(x, .) is the Euler-Maruyama kernel of Alg. 4 (mean
+// x + (stddev^2 / 2) s(x) + gamma_tilde J s(x), covariance stddev^2 I,
+// wrapped on the torus; s = grad log p), and
+// (K* p)(y) = int p(x) K(x, y) dx.  The integral is the trapezoid rule on
+// the square of half-width `radius` * stddev around y with `n` nodes per
+// side, each node's Gaussian summed over the nearest torus images.
+// prm: stddev, dt, gamma_tilde, eps.  y [M * 2] -> out [M].
+int orc_lstar_over_p(void* tgt, int kind, const double* prm, const double* y, int64_t M, double radius, int n,
+                     double* out) {
+  Target T = make_target(tgt, kind, 1);
+  if (T.d() != 2 || n < 2) return -1;
+  const double stddev = prm[0], dt = prm[1], gt = prm[2], eps = prm[3];
+  const double a = 0.5 * stddev * stddev, h = 1.0 / dt;
+  const double half = radius * stddev, dx = 2.0 * half / (n - 1);
+  const double norm = 1.0 / (2.0 * PI * stddev * stddev);
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int64_t m = 0; m < M; ++m) {
+    const double y0 = y[2 * m], y1 = y[2 * m + 1];
+    double acc = 0.0;
+    for (int i = 0; i < n; ++i) {
+      const double wi = (i == 0 || i == n - 1) ? 0.5 : 1.0;
+      for (int j = 0; j < n; ++j) {
+        const double wj = (j == 0 || j == n - 1) ? 0.5 : 1.0;
+        double x[2] = {y0 - half + i * dx, y1 - half + j * dx};
+        EvalResult r;
+        double s[2];
+        evaluate(T, x, eps, r, s);
+        // mean of the kernel from x, and its offset to y (nearest image)
+        double e0 = y0 - (x[0] + a * s[0] + gt * s[1]);
+        double e1 = y1 - (x[1] + a * s[1] - gt * s[0]);
+        e0 -= std::nearbyint(e0);
+        e1 -= std::nearbyint(e1);
+        acc += wi * wj * r.p * norm * std::exp(-0.5 * (e0 * e0 + e1 * e1) / (stddev * stddev));
+      }
+    }
+    EvalResult ry;
+    double yy[2] = {y0, y1};
+    evaluate(T, yy, eps, ry, nullptr);
+    out[m] = h * (acc * dx * dx / ry.p - 1.0);
+  }
+  return 0;
+}
+
 // Closest-hit queries: tri = -1 on miss.
 void orc_trace(void* s, const double* o, const double* d, int64_t n, int exclude, int* tri, double* t,
                long* tests) {
@@ -1026,7 +1116,7 @@ static void pack_info(const PathInfo& pi, int* o) {
 
 int orc_eval(void* tgt, int kind, int L, const double* x, int64_t M, double eps, double* f, double* logp,
              double* grad, int* pix, int* info) {
-  Target T{kind, kind == 0 ? static_cast<Scene*>(tgt) : nullptr, kind == 1 ? static_cast<Mixture*>(tgt) : nullptr, L};
+  Target T = make_target(tgt, kind, L);
   const int d = T.d();
 #pragma omp parallel for schedule(dynamic, 16)
   for (int64_t i = 0; i < M; ++i) {
@@ -1041,7 +1131,7 @@ int orc_eval(void* tgt, int kind, int L, const double* x, int64_t M, double eps,
 }
 
 int orc_fd_score(void* tgt, int kind, int L, const double* x, int64_t M, double eps, double h, double* score) {
-  Target T{kind, kind == 0 ? static_cast<Scene*>(tgt) : nullptr, kind == 1 ? static_cast<Mixture*>(tgt) : nullptr, L};
+  Target T = make_target(tgt, kind, L);
   const int d = T.d();
 #pragma omp parallel for schedule(dynamic, 16)
   for (int64_t i = 0; i < M; ++i) fd_score(T, x + i * d, eps, h, score + i * d);
@@ -1103,8 +1193,7 @@ int orc_restore_run(void* tgt, int kind, const Params* prm, uint64_t seed, uint3
                     const uint32_t* chain_ids, int64_t M, int n_steps, double* x_out, double* logp_out,
                     double* score_out, uint8_t* killed_out, int* pix_out, double* val_out, int* info_out,
                     double* accum, uint64_t* tour_count, double* p_init_sum) {
-  Target T{kind, kind == 0 ? static_cast<Scene*>(tgt) : nullptr, kind == 1 ? static_cast<Mixture*>(tgt) : nullptr,
-           prm->L};
+  Target T = make_target(tgt, kind, prm->L);
   const Params P = *prm;
   const int d = T.d();
   const int WH = T.W() * T.H();
@@ -1158,8 +1247,7 @@ int orc_restore_run(void* tgt, int kind, const Params* prm, uint64_t seed, uint3
 int orc_restore_tours(void* tgt, int kind, const Params* prm, uint64_t seed, uint32_t frame,
                       const uint32_t* chain_ids, int64_t M, int64_t max_steps, double* I1, double* Ix, double* Ixx,
                       int64_t* steps, uint8_t* truncated, double* accum) {
-  Target T{kind, kind == 0 ? static_cast<Scene*>(tgt) : nullptr, kind == 1 ? static_cast<Mixture*>(tgt) : nullptr,
-           prm->L};
+  Target T = make_target(tgt, kind, prm->L);
   const Params P = *prm;
   const int d = T.d();
   const size_t npix = (size_t)T.W() * T.H();

@@ -59,6 +59,11 @@ def lib():
         L.orc_mixture_create.restype = P
         L.orc_mixture_create.argtypes = [C.c_int, C.c_int, dp, dp, dp, C.c_int, C.c_int, C.c_double]
         L.orc_mixture_destroy.argtypes = [P]
+        L.orc_step_create.restype = P
+        L.orc_step_create.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, C.c_int, C.c_int]
+        L.orc_step_destroy.argtypes = [P]
+        L.orc_lstar_over_p.restype = C.c_int
+        L.orc_lstar_over_p.argtypes = [P, C.c_int, dp, dp, C.c_int64, C.c_double, C.c_int, dp]
         L.orc_trace.argtypes = [P, dp, dp, C.c_int64, C.c_int, ip, dp, P]
         L.orc_info_stride.restype = C.c_int
         L.orc_eval.argtypes = [P, C.c_int, C.c_int, dp, C.c_int64, C.c_double, P, P, P, P, P]
@@ -162,13 +167,46 @@ class OracleMixture:
             self.h = None
 
 
+class OracleStep:
+    """The jump density of ``scenes.StepDensity``."""
+    kind = 2
+
+    def __init__(self, st):
+        self.st = st
+        self.d = st.d
+        self.h = lib().orc_step_create(st.d, float(st.c1), float(st.c2), float(st.w), st.width, st.height)
+        self.width, self.height = st.width, st.height
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().orc_step_destroy(self.h)
+            self.h = None
+
+
 def target(obj, **kw):
     from paper_2605_08916_gb300 import scenes as S
     if isinstance(obj, S.Scene):
         return OracleScene(obj, **kw)
     if isinstance(obj, S.Mixture):
         return OracleMixture(obj)
+    if isinstance(obj, S.StepDensity):
+        return OracleStep(obj)
     return obj
+
+
+def lstar_over_p(tgt, y, stddev=5e-3, dt=1e-5, gamma_tilde=None, eps=1e-8, radius=8.0, n=129):
+    """(L* p / p)(y) of App. C for a 2-D target at points y [M, 2]: the bias
+    term of the modified killing rate (Sec. 5.2) for the Euler-Maruyama local
+    dynamics with holding rate 1 / dt, by quadrature."""
+    if gamma_tilde is None:
+        gamma_tilde = 0.5 * stddev * stddev
+    y = np.ascontiguousarray(y, np.float64).reshape(-1, 2)
+    out = np.zeros(y.shape[0])
+    rc = lib().orc_lstar_over_p(tgt.h, tgt.kind, np.array([stddev, dt, gamma_tilde, eps], np.float64), y.ravel(),
+                                y.shape[0], float(radius), int(n), out)
+    if rc != 0:
+        raise ValueError("lstar_over_p needs a 2-D analytic target")
+    return out
 
 
 def dim(tgt, L):

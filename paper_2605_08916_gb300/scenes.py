@@ -18,6 +18,8 @@ are not available; the generators below are the synthetic stand-ins:
 * ``procedural_scene`` fBm-displaced terrain grid + many tessellated
                        spheres/boxes with mixed materials
 * ``gaussian_mixture`` analytic target on the torus (invariance tests)
+* ``StepDensity``      a torus density with a jump (or a smoothed one),
+                       for the bias of unadjusted moves across a jump
 
 Material record layout (float32 x 12, shared by both sides):
 ``[type, albedo_r, albedo_g, albedo_b, roughness, ior, emit_r, emit_g,
@@ -659,6 +661,21 @@ def single_gaussian(center, sig, width=16, height=16):
 
 def constant_target(d=4, value=1.0, width=8, height=8):
     return Mixture(d, np.zeros(0), np.zeros((0, d)), np.zeros(0), width, height, const=float(value))
+
+
+@dataclasses.dataclass
+class StepDensity:
+    """Density on the torus T^d with one jump per half period along x0:
+    about c1 on x0 in (0, 1/2) and c2 on (1/2, 1), the jumps smoothed over a
+    width ~w (w = 0: sharp), g(x) = c2 + (c1 - c2) (1 + tanh(q(x0) / w)) / 2
+    with q(x0) = sin(2 pi x0) / (2 pi).  The pixel grid is width x height
+    over (x0, x1); the default 2 x 1 grid puts each half in its own pixel."""
+    d: int = 2
+    c1: float = 1.0
+    c2: float = 4.0
+    w: float = 0.0
+    width: int = 2
+    height: int = 1
 
 
 def pss_dim(max_path_len):
