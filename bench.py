@@ -442,15 +442,40 @@ def relmse(img, ref):
     return float(np.mean((img - ref) ** 2 / (ref ** 2 + 1e-2)))
 
 
+def bias_variance(imgs, ref):
+    """Split of the relMSE over seeds: per seed it is (I - R)^2 / (R^2 + 1e-2)
+    averaged over pixels and channels; its mean over seeds is the weighted
+    squared bias of the mean image plus the weighted variance.  Returns
+    (mean relMSE, its standard deviation over seeds, squared bias,
+    variance), the bias corrected for the variance left in the mean of the
+    seeds."""
+    imgs = np.stack(imgs).astype(np.float64)
+    w = 1.0 / (ref ** 2 + 1e-2)
+    per = [float(np.mean((im - ref) ** 2 * w)) for im in imgs]
+    n = imgs.shape[0]
+    mean = imgs.mean(0)
+    var = float(np.mean(imgs.var(0, ddof=1) * w))
+    bias2 = max(0.0, float(np.mean((mean - ref) ** 2 * w)) - var / n)
+    return statistics.mean(per), statistics.stdev(per), bias2, var
+
+
 def run_relmse33(R, scene, wl, local, seeds=16):
     """Image relMSE after one 33.3 ms frame budget, from scratch (chain init
     with the p_lambda estimate, the steps, the splat and the resolve all
-    inside the budget), for the plain form (finite-difference drift, one
-    launch sequence per step) and the batched form (adjoint drift,
-    bounce-by-bounce passes, all steps of the frame in one CUDA graph).
-    Each form takes the largest chain count (halving from the workload's)
-    that fits at least two steps; the steps are calibrated to the budget.
-    Reference: stratified path tracing of the same f."""
+    inside the budget).  Forms:
+      plain_fd         finite-difference drift, one launch sequence per step;
+      batched_adjoint  adjoint drift, bounce-by-bounce passes, all steps of
+                       the frame in one CUDA graph;
+      batched_none     the same without a drift (LocalDynamics with a zero
+                       score), the ablation of the drift at equal budget;
+      graph_fd         finite-difference drift, all steps in one CUDA graph;
+      pt               path tracing of the same f (stratified film
+                       samples), as many samples per pixel as fit the budget.
+    Each Restore form takes the largest chain count (halving from the
+    workload's) that fits at least two steps; the steps are calibrated to
+    the budget.  Each form reports the mean relMSE over seeds split into the
+    squared bias of the seeds' mean image and the variance.  Reference:
+    path tracing of the same f with a fixed large sample count."""
     import torch
     stream = torch.cuda.Stream(device=torch.device("cuda", local))
     rr = R.Renderer(local, stream)
@@ -463,16 +488,39 @@ def run_relmse33(R, scene, wl, local, seeds=16):
     t0 = time.perf_counter()
     ref = rr.pt_render(wl["L"], spp_ref, seed=12345).cpu().numpy()
     t_ref = time.perf_counter() - t0
-    rr.close()
     log(f"relmse: reference PT {spp_ref} spp in {t_ref:.1f} s")
     out = {"budget_ms": BUDGET_MS, "seeds": seeds, "reference": f"path tracing, {spp_ref} spp, same f",
-           "metric": "mean over pixels and channels of (I-R)^2/(R^2+1e-2)"}
+           "metric": "mean over pixels and channels of (I-R)^2/(R^2+1e-2)",
+           "split": "relmse_mean = bias2 (squared bias of the mean image over seeds) + variance (per seed)"}
+    # path tracing at the same budget: the render of spp samples per pixel
+    # from scratch, its result on the device
+    def pt_ms(spp, seed):
+        stream.synchronize()
+        t0 = time.perf_counter()
+        img_pt = rr.pt_render(wl["L"], spp, seed=seed)
+        stream.synchronize()
+        return (time.perf_counter() - t0) * 1e3, img_pt
+    spp = 1
+    pt_ms(1, 5)
+    while spp < 1 << 16 and min(pt_ms(2 * spp, 6 + k)[0] for k in range(2)) <= 0.97 * BUDGET_MS:
+        spp *= 2
+    imgs, times = [], []
+    for k in range(seeds):
+        ms, im = pt_ms(spp, 2000 + k)
+        times.append(ms)
+        imgs.append(im.cpu().numpy())
+    rm, sd, b2, var = bias_variance(imgs, ref)
+    out["pt"] = {"spp": spp, "frame_ms_mean": statistics.mean(times), "frame_ms_max": max(times),
+                 "relmse_mean": rm, "relmse_sd": sd, "bias2": b2, "variance": var}
+    log(f"relmse pt: {spp} spp, frame {statistics.mean(times):.1f} ms, relMSE {rm:.4g} (bias2 {b2:.3g}, var {var:.3g})")
+    rr.close()
     img = torch.empty((scene.height, scene.width, 3), dtype=torch.float32, device=torch.device("cuda", local))
-    for form in ("plain_fd", "batched_adjoint"):
-        drift = "fd" if form == "plain_fd" else "adjoint"
+    forms = {"plain_fd": ("fd", False), "batched_adjoint": ("adjoint", True), "batched_none": ("none", True),
+             "graph_fd": ("fd", True)}
+    for form, (drift, graph) in forms.items():
         r = R.Renderer(local, stream)
         upload(r, scene)
-        if form == "plain_fd":
+        if drift == "fd":
             r.set_option("wavefront", 0)
         F = wl["spp"]
         prm = R.make_params(L=wl["L"], drift=drift, rb=True, k0=0.0, steps_per_splat=F)
@@ -481,10 +529,10 @@ def run_relmse33(R, scene, wl, local, seeds=16):
             stream.synchronize()
             t0 = time.perf_counter()
             r.init_chains(n, seed, prm)
-            if form == "plain_fd":
-                r.step(steps)
-            else:
+            if graph:
                 r.frame(steps)
+            else:
+                r.step(steps)
             r.resolve(img)
             stream.synchronize()
             return (time.perf_counter() - t0) * 1e3
@@ -503,17 +551,19 @@ def run_relmse33(R, scene, wl, local, seeds=16):
             n //= 2
         steps = max(1, steps)
         run(n, steps, 9)                    # capture at the final step count
-        errs, times = [], []
+        imgs, times = [], []
         for k in range(seeds):
             times.append(run(n, steps, 1000 + k))
-            errs.append(relmse(img.cpu().numpy().astype(np.float64), ref))
+            imgs.append(img.cpu().numpy().astype(np.float64))
         r.close()
-        out[form] = {"chains": n, "steps": steps, "ms_per_step": t_step, "ms_fixed": t_fixed,
-                     "frame_ms_mean": statistics.mean(times), "frame_ms_max": max(times),
-                     "relmse_mean": statistics.mean(errs), "relmse_sd": statistics.stdev(errs)}
+        rm, sd, b2, var = bias_variance(imgs, ref)
+        out[form] = {"drift": drift, "graph": graph, "chains": n, "steps": steps, "ms_per_step": t_step,
+                     "ms_fixed": t_fixed, "frame_ms_mean": statistics.mean(times), "frame_ms_max": max(times),
+                     "relmse_mean": rm, "relmse_sd": sd, "bias2": b2, "variance": var}
         log(f"relmse {form}: {n} chains x {steps} steps, frame {statistics.mean(times):.1f} ms, "
-            f"relMSE {statistics.mean(errs):.4g} +- {statistics.stdev(errs):.2g}")
+            f"relMSE {rm:.4g} +- {sd:.2g} (bias2 {b2:.3g}, var {var:.3g})")
     out["ratio_plain_over_batched"] = out["plain_fd"]["relmse_mean"] / out["batched_adjoint"]["relmse_mean"]
+    out["ratio_pt_over_batched"] = out["pt"]["relmse_mean"] / out["batched_adjoint"]["relmse_mean"]
     return out
 
 

@@ -382,11 +382,12 @@ int dr_pt_render(dr_ctx* ctx, int32_t max_path_len, uint32_t spp, uint64_t seed,
 /* Execution options.  They change speed, not the method: results are the
  * same up to floating-point contraction order (DR_OPT_WAVEFRONT) and the
  * triangle picked on a shared edge (DR_OPT_TWO_LEVEL), as stated below.
- *   DR_OPT_WAVEFRONT   1: adjoint-drift steps on a scene run bounce by
- *                      bounce over compacted queues of live paths (trace /
- *                      shade / shadow kernels per bounce, the per-segment
- *                      tape in device memory, the adjoint pass over
- *                      surviving chains only); 0: one fused kernel, one
+ *   DR_OPT_WAVEFRONT   1: adjoint-drift (or no-drift) steps on a scene
+ *                      run bounce by bounce over compacted queues of live
+ *                      paths (trace / shade / shadow kernels per bounce,
+ *                      the per-segment tape in device memory, the adjoint
+ *                      pass over surviving chains only, skipped without a
+ *                      drift); 0: one fused kernel, one
  *                      thread per chain-step; -1 (default): wavefront from
  *                      2^17 chains up, fused below.  The two agree to
  *                      floating-point contraction order (last-bit level).

@@ -441,8 +441,9 @@ int run_fd(dr_ctx* c) {
 
 bool use_wavefront(const dr_ctx* c) {
   if (c->target == 2) return true;  // a batch runs bounce by bounce only
-  const bool adjoint_scene = c->prm.drift_mode == DR_DRIFT_ADJOINT && c->target == 0;
-  return adjoint_scene && (c->wavefront == 1 || (c->wavefront == -1 && c->N >= (1ull << 17)));
+  // the bounce-by-bounce passes compute the adjoint drift, or no drift
+  const bool wf_drift = c->prm.drift_mode == DR_DRIFT_ADJOINT || c->prm.drift_mode == DR_DRIFT_NONE;
+  return wf_drift && c->target == 0 && (c->wavefront == 1 || (c->wavefront == -1 && c->N >= (1ull << 17)));
 }
 
 int ensure_wavefront_buffers(dr_ctx* c) {

@@ -568,7 +568,7 @@ __global__ void __launch_bounds__(kWfThreads) wf_finish(StepArgs a, WfBuffers w,
       if (a.plen) a.plen[j] = (uint8_t)ps.nseg;
       if (mode == kWfInitEval) {
         p_out[j] = p;
-        survive = true;
+        survive = a.drift != 0;  // without a drift no score is computed
       } else {
         const ChainView v = chain_view<BATCH>(a, j);
         const U4 rc = chain_rng<BATCH>(a, v).draw(step_index(a), v.cj, 0u, kClock);
@@ -591,7 +591,7 @@ __global__ void __launch_bounds__(kWfThreads) wf_finish(StepArgs a, WfBuffers w,
           rr.b = f.z * s;
           a.rec[j] = rr;
         }
-        survive = !killed && mode == kWfStep;
+        survive = !killed && mode == kWfStep && a.drift != 0;
       }
     }
     // a batch's tour counts: one atomic per scene present among the warp's

@@ -108,3 +108,22 @@ def test_measured_peaks_reads_the_file_or_falls_back(tmp_path, monkeypatch):
     assert bench.measured_peaks() == (6800.0, "fallback")            # no HBM figure
     (tmp_path / "MEASURED_PEAKS.json").write_text('{"hbm_gbs": 6785.9}')
     assert bench.measured_peaks() == (6785.9, "measured")
+
+
+def test_relmse_split_into_bias_and_variance():
+    """Images I_s = R + b + noise_s (noise of variance v per pixel): the
+    split returns bias2 = mean b^2 w and variance = v mean w (w = 1 / (R^2 +
+    1e-2)), and they add up to the mean relMSE over seeds."""
+    rng = np.random.default_rng(4)
+    ref = rng.uniform(0.1, 2.0, (8, 12, 3))
+    w = 1.0 / (ref ** 2 + 1e-2)
+    bias = 0.05 * ref
+    v = 0.01
+    imgs = [ref + bias + rng.normal(size=ref.shape) * np.sqrt(v) for _ in range(400)]
+    rm, sd, b2, var = bench.bias_variance(imgs, ref)
+    assert abs(var / (v * w.mean()) - 1) < 0.05
+    assert abs(b2 / np.mean(bias ** 2 * w) - 1) < 0.05
+    assert abs(rm - (b2 + var)) < 0.02 * rm
+    # no bias: the squared bias is (up to noise) zero, all of it variance
+    rm, sd, b2, var = bench.bias_variance([ref + rng.normal(size=ref.shape) * 0.1 for _ in range(400)], ref)
+    assert b2 < 0.01 * var

@@ -432,6 +432,21 @@ def test_chain_parity_glossy_adjoint(torch, R, oracle):
 
 
 @pytest.mark.parametrize("wavefront", [0, 1])
+def test_chain_parity_without_drift(torch, R, oracle, wavefront):
+    """Drift mode none (LocalDynamics with a zero score: the drift ablation
+    of the equal-time comparison) in both execution modes: the score stays
+    zero and the chains follow the oracle's."""
+    scene = S.cornell_box(2, 64, 64, glossy=True)
+    k0 = 1e6
+    pg = R.make_params(L=6, drift="none", rb=True, k0=k0, steps_per_splat=8)
+    po = oracle.make_params(L=6, drift="none", rb=True, k0=k0)
+    frac, first, n = _chain_parity_opts(torch, R, oracle, scene, pg, po, N=1 << 17, M=512, T=12, seed=19,
+                                        opts={"wavefront": wavefront})
+    print("no-drift divergent fraction", frac, "compared", n)
+    assert frac <= 0.01
+
+
+@pytest.mark.parametrize("wavefront", [0, 1])
 def test_chain_parity_conductor_adjoint(torch, R, oracle, wavefront):
     """Rough conductor boxes (complex-index Fresnel per channel) with the
     adjoint drift, in both execution modes."""
