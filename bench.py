@@ -500,10 +500,13 @@ def run_relmse33(R, scene, wl, local, seeds=16):
         img_pt = rr.pt_render(wl["L"], spp, seed=seed)
         stream.synchronize()
         return (time.perf_counter() - t0) * 1e3, img_pt
-    spp = 1
     pt_ms(1, 5)
-    while spp < 1 << 16 and min(pt_ms(2 * spp, 6 + k)[0] for k in range(2)) <= 0.97 * BUDGET_MS:
-        spp *= 2
+    t1 = min(pt_ms(1, 6 + k)[0] for k in range(2))
+    t4 = min(pt_ms(4, 8 + k)[0] for k in range(2))
+    per = max((t4 - t1) / 3, 1e-3)
+    spp = max(1, int((0.97 * BUDGET_MS - (t1 - per)) / per))
+    while spp > 1 and min(pt_ms(spp, 10 + k)[0] for k in range(2)) > 0.97 * BUDGET_MS:
+        spp -= 1
     imgs, times = [], []
     for k in range(seeds):
         ms, im = pt_ms(spp, 2000 + k)

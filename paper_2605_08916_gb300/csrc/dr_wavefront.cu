@@ -86,6 +86,11 @@ DR_D uint32_t keyed_append(uint32_t* counters, int key, unsigned want) {
   return base + __popc(peers & ((1u << lane) - 1u));
 }
 
+// Ray queue of bounce k (the two queues alternate).  Selected with a
+// branch, not an index: a run-time index into the kernel-parameter struct
+// would make the compiler copy the whole struct to local memory.
+DR_D uint32_t* queue_of(const WfBuffers& w, int k) { return (k & 1) ? w.queue[1] : w.queue[0]; }
+
 DR_D void add_counts(unsigned long long* target, unsigned long long v) {
   const unsigned long long w = warp_sum_u64(v);
   if ((threadIdx.x & 31) == 0 && w && target) atomicAdd(target, w);
@@ -165,7 +170,7 @@ __global__ void __launch_bounds__(kWfThreads, kWfTraceMinBlocks) wf_trace(StepAr
   extern __shared__ int smem[];
   TraceStack<kWfStack> st{smem + threadIdx.x, (int)blockDim.x};
   const uint32_t n = w.counts[k];
-  const uint32_t* q = k == 1 && !a.ray_keys ? nullptr : w.queue[k & 1];
+  const uint32_t* q = k == 1 && !a.ray_keys ? nullptr : queue_of(w, k);
   uint32_t err = 0;
   TraceStats stats{0u, 0u};
   unsigned long long rays = 0;
@@ -222,7 +227,7 @@ __global__ void __launch_bounds__(kWfThreads, WIDTH == kWalkTwoLevel ? 6 : kWfTr
   const uint32_t n_ray = k <= a.L ? w.counts[k] : 0u;
   const uint32_t n_shadow = k >= 2 ? w.counts[kWfShadowCount0 + k - 1] : 0u;
   const uint32_t n = n_ray + n_shadow;
-  const uint32_t* q = k == 1 && !a.ray_keys ? nullptr : w.queue[k & 1];
+  const uint32_t* q = k == 1 && !a.ray_keys ? nullptr : queue_of(w, k);
   uint32_t* ctr = &w.counts[kWfFetch0 + k];
   uint32_t err = 0;
   TraceStats stats{0u, 0u};
@@ -320,8 +325,8 @@ __global__ void __launch_bounds__(kWfThreads, WIDTH == kWalkTwoLevel ? 6 : kWfTr
 template <bool BATCH, bool COND>
 __global__ void __launch_bounds__(kWfThreads, kWfShadeMinBlocks) wf_shade(StepArgs a, WfBuffers w, int k) {
   const uint32_t n = w.counts[k];
-  const uint32_t* q = k == 1 && !a.ray_keys ? nullptr : w.queue[k & 1];
-  uint32_t* qn = w.queue[(k + 1) & 1];
+  const uint32_t* q = k == 1 && !a.ray_keys ? nullptr : queue_of(w, k);
+  uint32_t* qn = queue_of(w, k + 1);
   const uint32_t n_iter = (n + gridDim.x * blockDim.x - 1) / (gridDim.x * blockDim.x);
   // every lane runs the same number of iterations so the queue appends see
   // whole warps
@@ -381,7 +386,7 @@ __global__ void __launch_bounds__(kWfThreads, kWfTailMinBlocks) wf_tail(StepArgs
   TraceStack<kS> st{smem + threadIdx.x, (int)blockDim.x};
   enum { kIdle = 0, kShade, kClosest, kShadow };
   const uint32_t n = w.counts[k0];
-  const uint32_t* q = k0 == 1 && !a.ray_keys ? nullptr : w.queue[k0 & 1];
+  const uint32_t* q = k0 == 1 && !a.ray_keys ? nullptr : queue_of(w, k0);
   uint32_t* ctr = &w.counts[kWfFetch0 + 0];  // the fetch counter of bounce 0 is otherwise unused
   uint32_t err = 0;
   TraceStats stats{0u, 0u};
