@@ -18,6 +18,8 @@
 //     concrete sampler below (unidirectional path tracing with next-event
 //     estimation and balance-heuristic MIS, fixed maximum length, no Russian
 //     roulette) is this project's reading, stated in the design notes.
+//   * MALA Restore (the comparison method of Sec. 6): the same chains with a
+//     Metropolis-adjusted Langevin move as local dynamics.
 //   * Restore chains: Alg. 1 (Initialize + Accumulate), Alg. 2 (Evolve),
 //     Alg. 3 (Resolve) and Alg. 4 (LocalDynamics) of Sec. 4.3 / 5.3, with the
 //     modified killing rate k = k0 / p (Eq. modified-killing-rate, uniform
@@ -43,7 +45,9 @@
 // rays through a slab; dual gradients vs central differences; fd_score vs a
 // mixture's closed-form gradient, the dual gradient and the torus seam;
 // L* p / p vs the Gaussian closed form, mass conservation and the O(dt) of
-// Sec. 5.2 on a smooth density; Philox vs an independent implementation.
+// Sec. 5.2 on a smooth density; MALA Restore exact across a jump, for a
+// mixture at a large step and on the Cornell image at the paper's stddev;
+// Philox vs an independent implementation.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -84,7 +88,7 @@ void philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]
 // 24-bit uniform in [0, 1): (r >> 8) * 2^-24 (exact in float and double).
 inline double u01(uint32_t r) { return (double)(r >> 8) * (1.0 / 16777216.0); }
 
-enum Purpose : uint32_t { P_REGEN = 0, P_NORMAL = 1, P_CLOCK = 2, P_PT = 3 };
+enum Purpose : uint32_t { P_REGEN = 0, P_NORMAL = 1, P_CLOCK = 2, P_PT = 3, P_MH = 4 };
 
 struct Stream {
   uint32_t key[2];
@@ -817,7 +821,7 @@ struct Params {
   int32_t L, drift_mode, rb_weight, pad;
   double stddev, dt, gamma_tilde, eps, fd_h, m, k0;
 };
-enum Drift { D_NONE = 0, D_FD = 1, D_EXACT = 2 };
+enum Drift { D_NONE = 0, D_FD = 1, D_EXACT = 2, D_MALA = 3 };
 
 // Central finite differences of log p on the torus with step h.
 void fd_score(const Target& T, const double* x, double eps, double h, double* s) {
@@ -849,7 +853,7 @@ void accumulate(const Target& T, const Params& P, const Stream& st, uint32_t ste
   const int d = T.d();
   EvalResult r;
   std::vector<double> g(d, 0.0);
-  const bool exact = P.drift_mode == D_EXACT;
+  const bool exact = P.drift_mode == D_EXACT || P.drift_mode == D_MALA;
   evaluate(T, x, P.eps, r, exact ? g.data() : nullptr);
   uint32_t rr[4];
   st.draw(step, chain, 0, P_CLOCK, rr);
@@ -879,6 +883,80 @@ void accumulate(const Target& T, const Params& P, const Stream& st, uint32_t ste
   } else {
     std::fill(score, score + d, 0.0);
   }
+}
+
+// The hold/kill clock of Accumulate (Alg. 1) for a state with density p:
+// killed flag and splat weight (the race, or its Rao-Blackwellised form).
+void clock(const Params& P, const Stream& st, uint32_t step, uint32_t chain, double p, bool* killed, double* wt) {
+  uint32_t rr[4];
+  st.draw(step, chain, 0, P_CLOCK, rr);
+  const double u1 = u01(rr[0]), u2 = u01(rr[1]);
+  const double h = 1.0 / P.dt;
+  if (P.rb_weight) {
+    *killed = u2 * (h * p + P.k0) < P.k0;
+    *wt = p / (h * p + P.k0);
+  } else {
+    const double t1 = -std::log(1.0 - u1) / h;
+    const double t2 = -std::log(1.0 - u2) * p / P.k0;
+    *killed = !(t1 < t2);
+    *wt = *killed ? t2 : t1;
+  }
+}
+
+// MALA Restore (the paper's comparison method of Sec. 6 and App. A: Jump
+// Restore whose local dynamics is a Metropolis-adjusted Langevin move, so the
+// local kernel is pi-invariant and the killing rate k0 / p is the invariant
+// one of Eq. invariant-killing-rate).  One move from x (current state, its
+// record in rec and its score in score): the Langevin proposal
+// y = x + (stddev^2 / 2) s(x) + stddev xi (the normals of Alg. 4, no rotation:
+// the adjusted move is reversible), wrapped; accepted with probability
+// min(1, p(y) q(x | y) / (p(x) q(y | x))),
+// q(y | x) proportional to exp(-|y - x - (stddev^2 / 2) s(x)|^2 / (2 stddev^2))
+// with torus differences to the nearest image.  Then the clock at the
+// resulting state.
+void mala_move(const Target& T, const Params& P, const Stream& st, uint32_t step, uint32_t chain, double* x,
+               double* score, ChainRec& rec) {
+  const int d = T.d();
+  const double a = 0.5 * P.stddev * P.stddev;
+  std::vector<double> y(x, x + d), sy(d, 0.0);
+  for (int q = 0; q < d / 2; ++q) {
+    uint32_t rr[4];
+    st.draw(step, chain, (uint32_t)(q >> 1), P_NORMAL, rr);
+    double ua = u01(rr[(q & 1) * 2]), ub = u01(rr[(q & 1) * 2 + 1]);
+    double rad = std::sqrt(-2.0 * std::log(1.0 - ua));
+    double th = 2.0 * PI * ub;
+    y[2 * q] = wrap01(x[2 * q] + a * score[2 * q] + P.stddev * rad * std::cos(th));
+    y[2 * q + 1] = wrap01(x[2 * q + 1] + a * score[2 * q + 1] + P.stddev * rad * std::sin(th));
+  }
+  EvalResult ry;
+  evaluate(T, y.data(), P.eps, ry, sy.data());
+  double fwd = 0.0, rev = 0.0;  // |y - x - a s(x)|^2 and |x - y - a s(y)|^2
+  for (int i = 0; i < d; ++i) {
+    double e1 = y[i] - x[i];
+    e1 -= std::nearbyint(e1);
+    e1 -= a * score[i];
+    double e2 = x[i] - y[i];
+    e2 -= std::nearbyint(e2);
+    e2 -= a * sy[i];
+    fwd += e1 * e1;
+    rev += e2 * e2;
+  }
+  const double log_alpha = std::log(ry.p) - std::log(rec.p) + (fwd - rev) / (2.0 * P.stddev * P.stddev);
+  uint32_t rr[4];
+  st.draw(step, chain, 0, P_MH, rr);
+  if (u01(rr[0]) < std::exp(log_alpha)) {
+    std::copy(y.begin(), y.end(), x);
+    std::copy(sy.begin(), sy.end(), score);
+    for (int c = 0; c < 3; ++c) rec.f[c] = ry.f[c];
+    rec.p = ry.p;
+    rec.pix = ry.pix;
+    rec.info = ry.info;
+  }
+  double wt;
+  bool killed;
+  clock(P, st, step, chain, rec.p, &killed, &wt);
+  rec.killed = killed;
+  for (int c = 0; c < 3; ++c) rec.val[c] = wt * rec.f[c] / rec.p;
 }
 
 // LocalDynamics (Alg. 4): for each coordinate pair,
@@ -1209,9 +1287,15 @@ int orc_restore_run(void* tgt, int kind, const Params* prm, uint64_t seed, uint3
       const uint32_t c = chain_ids[j];
       double* x = X.data() + j * d;
       double* sc = S.data() + j * d;
-      if (s == 0 || K[j]) regenerate(st, (uint32_t)s, c, d, x);
-      else local_dynamics(P, st, (uint32_t)s, c, d, x, sc);
-      accumulate(T, P, st, (uint32_t)s, c, x, sc, R[j]);
+      if (s == 0 || K[j]) {
+        regenerate(st, (uint32_t)s, c, d, x);
+        accumulate(T, P, st, (uint32_t)s, c, x, sc, R[j]);
+      } else if (P.drift_mode == D_MALA) {
+        mala_move(T, P, st, (uint32_t)s, c, x, sc, R[j]);
+      } else {
+        local_dynamics(P, st, (uint32_t)s, c, d, x, sc);
+        accumulate(T, P, st, (uint32_t)s, c, x, sc, R[j]);
+      }
       K[j] = R[j].killed ? 1 : 0;
     }
     for (int64_t j = 0; j < M; ++j) {
@@ -1271,9 +1355,15 @@ int orc_restore_tours(void* tgt, int kind, const Params* prm, uint64_t seed, uin
     int64_t s = 0;
     bool done = false;
     for (; s <= max_steps; ++s) {
-      if (s == 0) regenerate(st, 0, c, d, x.data());
-      else local_dynamics(P, st, (uint32_t)s, c, d, x.data(), sc.data());
-      accumulate(T, P, st, (uint32_t)s, c, x.data(), sc.data(), r);
+      if (s == 0) {
+        regenerate(st, 0, c, d, x.data());
+        accumulate(T, P, st, 0, c, x.data(), sc.data(), r);
+      } else if (P.drift_mode == D_MALA) {
+        mala_move(T, P, st, (uint32_t)s, c, x.data(), sc.data(), r);
+      } else {
+        local_dynamics(P, st, (uint32_t)s, c, d, x.data(), sc.data());
+        accumulate(T, P, st, (uint32_t)s, c, x.data(), sc.data(), r);
+      }
       // the splat weight (hold time, or its Rao-Blackwellised mean)
       uint32_t rr[4];
       st.draw((uint32_t)s, c, 0, P_CLOCK, rr);

@@ -28,7 +28,7 @@ class Params(C.Structure):
                 ("fd_h", C.c_double), ("m", C.c_double), ("k0", C.c_double)]
 
 
-DRIFT = {"none": 0, "fd": 1, "exact": 2, "adjoint": 2}
+DRIFT = {"none": 0, "fd": 1, "exact": 2, "adjoint": 2, "mala": 3}
 
 
 def make_params(L=4, drift="exact", rb=True, stddev=5e-3, dt=1e-5, gamma_tilde=None, eps=1e-8, fd_h=1e-3,
