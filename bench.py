@@ -469,6 +469,9 @@ def run_relmse33(R, scene, wl, local, seeds=16):
       batched_none     the same without a drift (LocalDynamics with a zero
                        score), the ablation of the drift at equal budget;
       graph_fd         finite-difference drift, all steps in one CUDA graph;
+      mala_restore     MALA Restore (Sec. 6's comparison method: Metropolis-
+                       adjusted Langevin moves, holding rate 1), fused
+                       kernel, all steps in one CUDA graph;
       pt               path tracing of the same f (stratified film
                        samples), as many samples per pixel as fit the budget.
     Each Restore form takes the largest chain count (halving from the
@@ -519,14 +522,16 @@ def run_relmse33(R, scene, wl, local, seeds=16):
     rr.close()
     img = torch.empty((scene.height, scene.width, 3), dtype=torch.float32, device=torch.device("cuda", local))
     forms = {"plain_fd": ("fd", False), "batched_adjoint": ("adjoint", True), "batched_none": ("none", True),
-             "graph_fd": ("fd", True)}
+             "graph_fd": ("fd", True), "mala_restore": ("mala", True)}
     for form, (drift, graph) in forms.items():
         r = R.Renderer(local, stream)
         upload(r, scene)
-        if drift == "fd":
+        if drift in ("fd", "mala"):
             r.set_option("wavefront", 0)
         F = wl["spp"]
-        prm = R.make_params(L=wl["L"], drift=drift, rb=True, k0=0.0, steps_per_splat=F)
+        # MALA Restore runs with the paper's holding rate 1 (dt = 1)
+        prm = R.make_params(L=wl["L"], drift=drift, rb=True, k0=0.0, steps_per_splat=F,
+                            dt=1.0 if drift == "mala" else 1e-5)
 
         def run(n, steps, seed):
             stream.synchronize()

@@ -40,7 +40,7 @@ enum {
   DR_ERR_TIMEOUT = -6        /* a bounded device wait gave up */
 };
 
-enum { DR_DRIFT_NONE = 0, DR_DRIFT_FD = 1, DR_DRIFT_ADJOINT = 2 };
+enum { DR_DRIFT_NONE = 0, DR_DRIFT_FD = 1, DR_DRIFT_ADJOINT = 2, DR_DRIFT_MALA = 3 };
 
 enum { DR_MAX_PATH_LEN = 16 }; /* L <= 16, so d = 2 + 4 (L - 1) <= 62 */
 
@@ -52,7 +52,18 @@ typedef struct dr_ctx dr_ctx;
  *                   the PSS dimension is d = 2 + 4 (L - 1).
  *   drift_mode      DR_DRIFT_NONE (score 0), DR_DRIFT_FD (central finite
  *                   differences of log p with step fd_h), DR_DRIFT_ADJOINT
- *                   (hand-written reverse-mode gradient of log p).
+ *                   (hand-written reverse-mode gradient of log p), or
+ *                   DR_DRIFT_MALA: MALA Restore, the comparison method of
+ *                   Sec. 6 (Jump Restore whose local move is a
+ *                   Metropolis-adjusted Langevin step: proposal
+ *                   x + (stddev^2 / 2) grad log p(x) + stddev xi with the
+ *                   normals of Alg. 4 and no rotation, accepted with the
+ *                   Metropolis-Hastings probability in FP64, torus
+ *                   differences to the nearest image; the paper runs it with
+ *                   holding rate 1, i.e. dt = 1).  MALA runs in the fused
+ *                   execution (one thread per chain-step), on a scene or a
+ *                   mixture, not in a batch; its chains cannot be
+ *                   checkpointed (dr_state_save gives STATE).
  *   rb_weight       0: the paper's exponential race of Alg. 1 (hold time
  *                   ~ Exp(h), kill time ~ Exp(k), splat weight = the smaller);
  *                   1: its Rao-Blackwellisation (weight 1 / (h + k), killed

@@ -20,7 +20,7 @@ DR_ERR_DEVICE_CHECK = -5
 DR_ERR_TIMEOUT = -6
 ERR_NAMES = {0: "DR_OK", -1: "DR_ERR_INVALID_ARG", -2: "DR_ERR_STATE", -3: "DR_ERR_CUDA", -4: "DR_ERR_OOM",
              -5: "DR_ERR_DEVICE_CHECK", -6: "DR_ERR_TIMEOUT"}
-DR_DRIFT_NONE, DR_DRIFT_FD, DR_DRIFT_ADJOINT = 0, 1, 2
+DR_DRIFT_NONE, DR_DRIFT_FD, DR_DRIFT_ADJOINT, DR_DRIFT_MALA = 0, 1, 2, 3
 
 # every entry point declared in include/diffrestore.h
 EXPORTS = ["dr_version", "dr_last_error", "dr_create", "dr_destroy", "dr_scene_upload", "dr_target_mixture",

@@ -128,6 +128,10 @@ struct dr_ctx {
   bool inited = false;
   float* x = nullptr;
   float* score = nullptr;
+  float* xp = nullptr;     // MALA: proposal [d][N]
+  float* sp = nullptr;     // MALA: score at the proposal [d][N]
+  float4* cur = nullptr;   // MALA: f and pixel of the current state [N]
+  size_t mala_cap = 0;     // chains * d the MALA buffers hold
   float* logp = nullptr;
   uint8_t* killed = nullptr;
   uint8_t* plen = nullptr;      // [N] last path length (work-order key)
@@ -388,6 +392,9 @@ StepArgs step_args(dr_ctx* c) {
   a.target = c->target;
   a.x = c->x;
   a.score = c->score;
+  a.xp = c->xp;
+  a.sp = c->sp;
+  a.cur = c->cur;
   a.killed = c->killed;
   a.logp = c->logp;
   a.N = c->N;
@@ -895,6 +902,7 @@ int dr_destroy(dr_ctx* c) {
   dfree(&c->nodes); dfree(&c->tris); dfree(&c->surf); dfree(&c->lights); dfree(&c->nrm); dfree(&c->mats);
   dfree(&c->mw); dfree(&c->mmu); dfree(&c->msig);
   dfree(&c->x); dfree(&c->score); dfree(&c->logp); dfree(&c->killed);
+  dfree(&c->xp); dfree(&c->sp); dfree(&c->cur);
   dfree(&c->plen); dfree(&c->order_a); dfree(&c->order_b);
   if (c->wf_mem) cudaFree(c->wf_mem); dfree(&c->rec); dfree(&c->rec_alt);
   if (c->sort_scratch) cudaFree(c->sort_scratch);
@@ -1161,7 +1169,7 @@ int dr_target_mixture(dr_ctx* c, int32_t d, int32_t K, const float* w, const flo
 static int validate_params(const dr_params* p) {
   if (!p) return fail(DR_ERR_INVALID_ARG, "params: NULL");
   if (p->max_path_len < 1 || p->max_path_len > DR_MAX_PATH_LEN) return fail(DR_ERR_INVALID_ARG, "params: max_path_len");
-  if (p->drift_mode < 0 || p->drift_mode > 2) return fail(DR_ERR_INVALID_ARG, "params: drift_mode");
+  if (p->drift_mode < 0 || p->drift_mode > 3) return fail(DR_ERR_INVALID_ARG, "params: drift_mode");
   if (!(p->stddev > 0.f) || !(p->dt > 0.f) || !(p->eps > 0.f) || !(p->m > 0.f))
     return fail(DR_ERR_INVALID_ARG, "params: stddev, dt, eps and m must be > 0");
   if (!std::isfinite(p->gamma_tilde)) return fail(DR_ERR_INVALID_ARG, "params: gamma_tilde");
@@ -1170,7 +1178,7 @@ static int validate_params(const dr_params* p) {
   return DR_OK;
 }
 
-static int alloc_chains_sized(dr_ctx* c, unsigned long long N, int d, int spp) {
+static int alloc_chains_sized(dr_ctx* c, unsigned long long N, int d, int spp, bool mala) {
   const size_t nd = (size_t)N * d;
   if (nd > c->state_cap) {
     DR_TRY(dalloc(&c->x, nd));
@@ -1199,6 +1207,12 @@ static int alloc_chains_sized(dr_ctx* c, unsigned long long N, int d, int spp) {
     }
     c->rec_cap_records = nrec;
   }
+  if (mala && nd > c->mala_cap) {
+    DR_TRY(dalloc(&c->xp, nd));
+    DR_TRY(dalloc(&c->sp, nd));
+    DR_TRY(dalloc(&c->cur, (size_t)N));
+    c->mala_cap = nd;
+  }
   const size_t npart = (N + step_block_size() - 1) / step_block_size();
   if (npart > c->p_partial_cap) {
     DR_TRY(dalloc(&c->p_partial, npart));
@@ -1218,11 +1232,12 @@ static int alloc_chains_sized(dr_ctx* c, unsigned long long N, int d, int spp) {
 // buffer before it allocates the larger one, so a failed allocation forgets
 // every capacity: the next init allocates afresh and no call can reach a
 // freed or null buffer.
-static int alloc_chains(dr_ctx* c, unsigned long long N, int d, int spp) {
+static int alloc_chains(dr_ctx* c, unsigned long long N, int d, int spp, bool mala = false) {
   c->inited = false;
-  const int r = alloc_chains_sized(c, N, d, spp);
+  const int r = alloc_chains_sized(c, N, d, spp, mala);
   if (r != DR_OK) {
     c->state_cap = 0;
+    c->mala_cap = 0;
     c->chains_cap = 0;
     c->rec_cap_records = 0;
     c->p_partial_cap = 0;
@@ -1457,7 +1472,7 @@ int dr_chains_init(dr_ctx* c, uint64_t n_chains, uint64_t seed, uint32_t frame, 
   if (frame >= (1u << 28)) return fail(DR_ERR_INVALID_ARG, "dr_chains_init: frame must be < 2^28");
   const int d = c->target == 0 ? 2 + 4 * (prm->max_path_len - 1) : c->md;
   DR_CUDA(cudaSetDevice(c->device));
-  DR_TRY(alloc_chains(c, n_chains, d, prm->steps_per_splat));
+  DR_TRY(alloc_chains(c, n_chains, d, prm->steps_per_splat, prm->drift_mode == DR_DRIFT_MALA));
   c->N = n_chains;
   c->d = d;
   c->prm = *prm;
@@ -1766,6 +1781,8 @@ int dr_state_save(dr_ctx* c, void* host_buf, size_t* bytes) {
   if (!c || !bytes) return fail(DR_ERR_INVALID_ARG, "dr_state_save: NULL argument");
   if (!c->inited) return fail(DR_ERR_STATE, "dr_state_save: chains not initialised");
   if (c->target == 2) return fail(DR_ERR_STATE, "dr_state_save: not available for a batch");
+  if (c->prm.drift_mode == DR_DRIFT_MALA)
+    return fail(DR_ERR_STATE, "dr_state_save: MALA chains (their current-state records) are not checkpointed");
   const size_t nd = (size_t)c->N * c->d;
   const size_t need = sizeof(SaveHeader) + nd * 8 + c->N * 5 + c->accum_n * 8;
   if (!host_buf) {

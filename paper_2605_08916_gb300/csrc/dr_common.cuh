@@ -79,7 +79,7 @@ DR_HD U4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint3
 
 // Stream identity: key = (seed_lo, seed_hi); counter = (step, chain, block,
 // frame << 4 | purpose).
-enum Purpose : uint32_t { kRegen = 0, kNormal = 1, kClock = 2, kPT = 3 };
+enum Purpose : uint32_t { kRegen = 0, kNormal = 1, kClock = 2, kPT = 3, kMH = 4 };
 
 struct Rng {
   uint32_t k0, k1, frame;

@@ -99,7 +99,7 @@ int bvh4_sah(const float4* d_nodes4, int n4, cudaStream_t s, double* node_term, 
 void launch_tlas_leaves(float4* nodes4, int n, const float4* tris4, int n_inst, uint32_t* err, cudaStream_t s);
 
 // ---------------------------------------------------------------- chains
-enum Drift { kDriftNone = 0, kDriftFD = 1, kDriftAdjoint = 2 };
+enum Drift { kDriftNone = 0, kDriftFD = 1, kDriftAdjoint = 2, kDriftMala = 3 };
 
 // What a replayed CUDA graph reads from device memory instead of its
 // captured launch arguments, so that one graph serves every step, seed,
@@ -133,6 +133,9 @@ struct StepArgs {
   int target;  // 0 scene, 1 mixture
   float* x;          // [d][N]
   float* score;      // [d][N]
+  float* xp;         // [d][N] MALA: the proposal
+  float* sp;         // [d][N] MALA: the score at the proposal
+  float4* cur;       // [N] MALA: f (rgb) and pixel of the current state
   uint8_t* killed;   // [N]
   float* logp;       // [N]
   SplatRec* rec;     // [N] slice for this step (null: no records)

@@ -77,6 +77,48 @@ DR_D float3 evaluate(const DevScene& S, const DevMixture& M, int target, int L, 
   return r.f;
 }
 
+// MALA proposal of chain j (the comparison method of Sec. 6): y = x +
+// (stddev^2 / 2) s(x) + stddev xi, wrapped, into the proposal array; the
+// normals are Alg. 4's (same Philox blocks and pairs), without the rotation.
+DR_D void mala_propose(const StepArgs& a, const Rng& rng, uint32_t step, unsigned long long j, uint32_t cj, int d) {
+  const float c2 = 0.5f * a.stddev * a.stddev;
+  const size_t N = a.N;
+  for (int blk = 0; 4 * blk < d; ++blk) {
+    const U4 r = rng.draw(step, cj, (uint32_t)blk, kNormal);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int c0 = 4 * blk + 2 * h;
+      if (c0 + 1 >= d) break;
+      const float2 xi = box_muller(u01(h ? r.c : r.a), u01(h ? r.d : r.b));
+      const size_t i0 = (size_t)c0 * N + j, i1 = i0 + N;
+      a.xp[i0] = wrap01(a.x[i0] + c2 * a.score[i0] + a.stddev * xi.x);
+      a.xp[i1] = wrap01(a.x[i1] + c2 * a.score[i1] + a.stddev * xi.y);
+    }
+  }
+}
+
+// log of the Metropolis-Hastings ratio of the MALA move x -> y in FP64:
+// log p(y) - log p(x) + (|y - x - c s(x)|^2 - |x - y - c s(y)|^2) / (2 stddev^2),
+// c = stddev^2 / 2, torus differences to the nearest image.
+DR_D double mala_log_ratio(const StepArgs& a, unsigned long long j, int d, double px, double py) {
+  const double c2 = 0.5 * (double)a.stddev * (double)a.stddev;
+  double fwd = 0.0, rev = 0.0;
+  for (int i = 0; i < d; ++i) {
+    const size_t k = (size_t)i * a.N + j;
+    const double xv = a.x[k], yv = a.xp[k];
+    double e1 = yv - xv;
+    e1 -= rint(e1);
+    e1 -= c2 * (double)a.score[k];
+    double e2 = xv - yv;
+    e2 -= rint(e2);
+    e2 -= c2 * (double)a.sp[k];
+    fwd += e1 * e1;
+    rev += e2 * e2;
+  }
+  const double s2 = (double)a.stddev * (double)a.stddev;
+  return log(py) - log(px) + (fwd - rev) / (2.0 * s2);
+}
+
 template <int DRIFT, bool STATS, bool COND>
 __global__ void __launch_bounds__(kStepThreads) step_kernel(StepArgs a) {
   extern __shared__ int smem[];
@@ -92,7 +134,10 @@ __global__ void __launch_bounds__(kStepThreads) step_kernel(StepArgs a) {
   if (active) {
     const uint32_t cj = (uint32_t)j;
     const uint32_t step = step_index(a);
-    evolve_x(a, rng_of(a), step, j, cj, a.d, a.init || a.killed[j]);
+    const bool regen = a.init || a.killed[j];
+    const bool mala_move = DRIFT == kDriftMala && !regen && !a.estimate_only;
+    if (mala_move) mala_propose(a, rng_of(a), step, j, cj, a.d);
+    else evolve_x(a, rng_of(a), step, j, cj, a.d, regen);
     const XSoA xa{a.x, a.N, j};
     int pix;
     float p;
@@ -101,7 +146,54 @@ __global__ void __launch_bounds__(kStepThreads) step_kernel(StepArgs a) {
     const float u1 = u01(rc.a), u2 = u01(rc.b);
     bool killed = false;
     float wt = 0.0f;
-    if (DRIFT == kDriftAdjoint && !a.estimate_only && a.target == 0) {
+    if (DRIFT == kDriftMala && !a.estimate_only) {
+      if (mala_move) {
+        // evaluate the proposal and its score, then accept or keep x
+        int pix_y;
+        float p_y;
+        const XSoA ya{a.xp, a.N, j};
+        const float3 f_y = evaluate<true, STATS, COND>(a.S, a.M, a.target, a.L, a.eps, ya, &pix_y, &p_y, true,
+                                                        GSoA{a.sp, a.N, j}, st, &err, &stats, &rays);
+        const float4 c = a.cur[j];
+        const float p_x = lum(f3(c.x, c.y, c.z)) + a.eps;
+        const double log_alpha = mala_log_ratio(a, j, a.d, (double)p_x, (double)p_y);
+        const U4 rm = rng_of(a).draw(step, cj, 0u, kMH);
+        if ((double)u01(rm.a) < exp(log_alpha)) {
+          for (int i = 0; i < a.d; ++i) {
+            const size_t k = (size_t)i * a.N + j;
+            a.x[k] = a.xp[k];
+            a.score[k] = a.sp[k];
+          }
+          f = f_y;
+          p = p_y;
+          pix = pix_y;
+          a.cur[j] = make_float4(f.x, f.y, f.z, __int_as_float(pix));
+        } else {
+          f = f3(c.x, c.y, c.z);
+          p = p_x;
+          pix = __float_as_int(c.w);
+        }
+        kill_clock(a.rb, u1, u2, p, a.h, k0_of(a), &killed, &wt);
+      } else if (a.target == 0) {
+        // a regenerated chain: its state and, if it survives, its score
+        // (forward with tape, clock, adjoint for survivors)
+        Tape<kMaxPathLen> tape;
+        const PathResult r = path_forward<kStack, STATS, true, COND>(a.S, xa, a.L, &tape, st, &err, &stats);
+        rays += r.rays;
+        pix = r.pix;
+        f = r.f;
+        p = lum(f) + a.eps;
+        kill_clock(a.rb, u1, u2, p, a.h, k0_of(a), &killed, &wt);
+        a.cur[j] = make_float4(f.x, f.y, f.z, __int_as_float(pix));
+        if (!killed) path_adjoint<COND>(a.S, xa, a.L, p, LocalTape<kMaxPathLen>{&tape}, r.nseg, GSoA{a.score, a.N, j});
+      } else {
+        f = evaluate<false, STATS, COND>(a.S, a.M, a.target, a.L, a.eps, xa, &pix, &p, false, GNone{}, st, &err,
+                                         &stats, &rays);
+        kill_clock(a.rb, u1, u2, p, a.h, k0_of(a), &killed, &wt);
+        a.cur[j] = make_float4(f.x, f.y, f.z, __int_as_float(pix));
+        if (!killed) mixture_eval(a.M, xa, a.eps, true, GSoA{a.score, a.N, j});
+      }
+    } else if (DRIFT == kDriftAdjoint && !a.estimate_only && a.target == 0) {
       // forward with tape; kill decision; adjoint only if the chain survives
       Tape<kMaxPathLen> tape;
       const PathResult r = path_forward<kStack, STATS, true, COND>(a.S, xa, a.L, &tape, st, &err, &stats);
@@ -351,7 +443,9 @@ void launch_order_keys(const uint8_t* killed, const uint8_t* plen, unsigned long
 
 void launch_step(const StepArgs& a, bool stats, cudaStream_t s) {
   if (a.N == 0) return;
-  if (a.drift == kDriftAdjoint) {
+  if (a.drift == kDriftMala) {
+    if (stats) launch_step_t<kDriftMala, true>(a, s); else launch_step_t<kDriftMala, false>(a, s);
+  } else if (a.drift == kDriftAdjoint) {
     if (stats) launch_step_t<kDriftAdjoint, true>(a, s); else launch_step_t<kDriftAdjoint, false>(a, s);
   } else {
     if (stats) launch_step_t<kDriftNone, true>(a, s); else launch_step_t<kDriftNone, false>(a, s);

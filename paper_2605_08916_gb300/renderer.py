@@ -14,7 +14,8 @@ import torch
 from . import _lib
 from ._lib import call, dr_params
 
-DRIFT = {"none": _lib.DR_DRIFT_NONE, "fd": _lib.DR_DRIFT_FD, "adjoint": _lib.DR_DRIFT_ADJOINT}
+DRIFT = {"none": _lib.DR_DRIFT_NONE, "fd": _lib.DR_DRIFT_FD, "adjoint": _lib.DR_DRIFT_ADJOINT,
+         "mala": _lib.DR_DRIFT_MALA}
 
 
 def make_params(L=4, drift="adjoint", rb=True, stddev=5e-3, dt=1e-5, gamma_tilde=None, eps=1e-8, fd_h=1e-3, m=64.0,

@@ -432,6 +432,60 @@ def test_chain_parity_glossy_adjoint(torch, R, oracle):
     assert frac <= 0.01
 
 
+@pytest.mark.parametrize("which", ["mixture", "glossy"])
+def test_chain_parity_mala_restore(torch, R, oracle, which):
+    """MALA Restore (the comparison method of Sec. 6: Metropolis-adjusted
+    Langevin local moves, holding rate 1, i.e. dt = 1) against the oracle's:
+    proposals, Metropolis-Hastings decisions (FP64 on both sides), clock,
+    splat values and the stored score over 16 steps.  A decision that FP32
+    inputs move across its threshold makes a chain divergent (counted)."""
+    if which == "mixture":
+        target = S.gaussian_mixture(seed=4, d=4, K=3, sig_range=(0.08, 0.12), width=16, height=16)
+        L, k0, stddev = 1, 1.0 / 64, 0.03
+    else:
+        target = S.cornell_box(1, 64, 64, glossy=True)
+        L, k0, stddev = 6, 2000.0 / 64, 5e-3
+    pg = R.make_params(L=L, drift="mala", rb=True, k0=k0, stddev=stddev, dt=1.0, steps_per_splat=8)
+    po = oracle.make_params(L=L, drift="mala", rb=True, k0=k0, stddev=stddev, dt=1.0)
+    frac, first, n = _chain_parity(torch, R, oracle, target, pg, po, N=4096, M=512, T=16, seed=31)
+    print(f"MALA Restore ({which}) divergent fraction", frac, "compared", n)
+    assert frac <= 0.01
+
+
+def test_mala_restore_graph_frames_and_refusals(torch, R):
+    """dr_frame replays MALA steps exactly as dr_step + dr_splat; MALA chains
+    are not checkpointed and a batch does not run them (both refused)."""
+    from paper_2605_08916_gb300 import _lib
+    scene = S.cornell_box(1, 32, 32, glossy=True)
+    prm = R.make_params(L=5, drift="mala", rb=True, k0=0.0, stddev=5e-3, dt=1.0, steps_per_splat=4)
+    res = []
+    for graph in (False, True):
+        s = torch.cuda.Stream()
+        r = R.Renderer(0, s)
+        r.upload_scene(scene)
+        r.init_chains(8192, 12, prm)
+        for _ in range(3):
+            if graph:
+                r.frame(4)
+            else:
+                r.step(4)
+                r.splat()
+        s.synchronize()
+        res.append((r.readback_state(fields=("x", "killed", "score")), r.readback_accum(), r.counters()))
+        if graph:
+            with pytest.raises(_lib.DRError):
+                r.state_save()
+        r.close()
+    (a, acc_a, c_a), (b, acc_b, c_b) = res
+    assert np.array_equal(a["x"], b["x"]) and np.array_equal(a["killed"], b["killed"])
+    assert np.array_equal(acc_a, acc_b) and c_a["tour_count"] == c_b["tour_count"] > 0
+    rb = R.Renderer()
+    rb.upload_scenes(batch_items())
+    with pytest.raises(_lib.DRError):
+        rb.init_chains(sum(n for _, _, n in batch_items()), 5, prm)
+    rb.close()
+
+
 @pytest.mark.parametrize("wavefront", [0, 1])
 def test_chain_parity_without_drift(torch, R, oracle, wavefront):
     """Drift mode none (LocalDynamics with a zero score: the drift ablation
