@@ -294,6 +294,23 @@ int dr_get_counters(dr_ctx* ctx, uint64_t* tour_count, double* k0, uint64_t* ste
 int dr_eval_logp(dr_ctx* ctx, int32_t max_path_len, const float* x, int64_t M, float* logp, float* grad,
                  int32_t* pix, float* f);
 
+/* The bias term of the modified killing rate (Sec. 5.2, Eq. bias and
+ * Eq. adjoint-bias; the diagnostic of App. C): (L* p / p)(y) =
+ * h ((K* p)(y) / p(y) - 1) for the mixture target on T^2 (dr_target_mixture
+ * with d = 2), where K is the Euler-Maruyama kernel of Alg. 4 with the
+ * stddev and gamma_tilde of prm, h = 1 / prm->dt, p = g + prm->eps, and
+ * (K* p)(y) = int p(x) K(x, y) dx by the trapezoid rule in FP64 over the
+ * square of half-width radius * stddev around y with n x n nodes (kernel
+ * differences to the nearest torus image).  With the modified killing rate
+ * the Restore estimate is biased by -(L* p / p).
+ *   prm   HOST, only stddev, dt, gamma_tilde and eps are read.
+ *   y     DEVICE float [M * 2] query points; out DEVICE double [M].
+ *   n     2..4097 nodes per side (e.g. 129 with radius 8: spacing
+ *         stddev / 8).
+ * Asynchronous.  Errors: INVALID_ARG, STATE (no 2-D mixture target), CUDA. */
+int dr_lstar_over_p(dr_ctx* ctx, const dr_params* prm, const float* y, int64_t M, float radius, int32_t n,
+                    double* out);
+
 /* Closest-hit queries through the BVH: rays [n * 6] (origin, direction;
  * DEVICE), tri [n] original triangle id or -1, t [n] distance (inf on miss).
  * `exclude` is a triangle id to skip (-1: none).  Asynchronous.

@@ -31,7 +31,7 @@ EXPORTS = ["dr_version", "dr_last_error", "dr_create", "dr_destroy", "dr_scene_u
            "dr_splat_records_noalloc", "dr_set_option", "dr_get_profile", "dr_frame", "dr_bvh4_info", "dr_bvh4_sah", "dr_bvh8_info", "dr_get_bounce_profile",
            "dr_scenes_upload_batch", "dr_resolve_scene", "dr_get_scene_counters", "dr_scene_upload_instanced",
            "dr_two_level_info", "dr_splat_records_noalloc_status", "dr_resolve_accum", "dr_get_p_sum",
-           "dr_k0_from_p_sum"]
+           "dr_k0_from_p_sum", "dr_lstar_over_p"]
 DR_OPT_WORK_ORDER, DR_OPT_WAVEFRONT, DR_OPT_PROFILE, DR_OPT_BVH_WIDTH = 1, 2, 3, 4
 DR_OPT_TRAVERSE_BLOCKS, DR_OPT_REFILL, DR_OPT_RAY_ORDER, DR_OPT_TAIL_BOUNCE = 5, 6, 7, 8
 DR_OPT_TWO_LEVEL = 9
@@ -120,6 +120,7 @@ def signatures():
         "dr_resolve_accum": ([P, I64, U64, C.c_double, P, P], C.c_int),
         "dr_get_p_sum": ([P, P, P], C.c_int),
         "dr_k0_from_p_sum": ([C.c_double, U64, C.POINTER(dr_params), P], C.c_int),
+        "dr_lstar_over_p": ([P, C.POINTER(dr_params), P, I64, C.c_float, I32, P], C.c_int),
     }
 
 

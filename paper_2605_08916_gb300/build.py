@@ -18,7 +18,8 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdiffrestore.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["dr_api.cu", "dr_kernels.cu", "dr_splat.cu", "dr_bvh.cu", "dr_noalloc.cu", "dr_wavefront.cu", "dr_bvh4.cu"]
+SOURCES = ["dr_api.cu", "dr_kernels.cu", "dr_splat.cu", "dr_bvh.cu", "dr_noalloc.cu", "dr_wavefront.cu", "dr_bvh4.cu",
+           "dr_bias.cu"]
 
 
 def nvcc():

@@ -1700,6 +1700,32 @@ int dr_eval_logp(dr_ctx* c, int32_t L, const float* x, int64_t M, float* logp, f
   return check_launch("eval_logp");
 }
 
+int dr_lstar_over_p(dr_ctx* c, const dr_params* prm, const float* y, int64_t M, float radius, int32_t n,
+                    double* out) {
+  if (!c || !prm || ((!y || !out) && M > 0)) return fail(DR_ERR_INVALID_ARG, "dr_lstar_over_p: NULL argument");
+  if (M < 0 || !(radius > 0.0f) || n < 2 || n > 4097)
+    return fail(DR_ERR_INVALID_ARG, "dr_lstar_over_p: M < 0, radius <= 0 or n outside 2..4097");
+  if (!(prm->stddev > 0.f) || !(prm->dt > 0.f) || !(prm->eps > 0.f) || !std::isfinite(prm->gamma_tilde))
+    return fail(DR_ERR_INVALID_ARG, "dr_lstar_over_p: stddev, dt, eps must be > 0 and gamma_tilde finite");
+  if (c->target != 1 || c->md != 2) return fail(DR_ERR_STATE, "dr_lstar_over_p: needs a mixture target on T^2");
+  if (M == 0) return DR_OK;
+  DR_CUDA(cudaSetDevice(c->device));
+  LstarArgs a{};
+  a.M = dev_mixture(c);
+  a.y = y;
+  a.n_pts = M;
+  a.stddev = prm->stddev;
+  a.h = 1.0 / (double)prm->dt;
+  a.gamma_tilde = prm->gamma_tilde;
+  a.eps = prm->eps;
+  a.radius = radius;
+  a.n = n;
+  a.out = out;
+  launch_lstar(a, c->stream);
+  c->launches += 1;
+  return check_launch("lstar_over_p");
+}
+
 int dr_trace_closest(dr_ctx* c, const float* rays, int64_t n, int32_t exclude, int32_t* tri, float* t) {
   if (!c || !rays || !tri || !t) return fail(DR_ERR_INVALID_ARG, "dr_trace_closest: NULL argument");
   if (n < 0) return fail(DR_ERR_INVALID_ARG, "dr_trace_closest: n < 0");

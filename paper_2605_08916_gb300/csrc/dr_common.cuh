@@ -11,6 +11,7 @@
 namespace dr {
 
 constexpr float kPi = 3.14159265358979323846f;
+constexpr double kPiD = 3.14159265358979323846;
 constexpr float kInvPi = 0.318309886183790671538f;
 constexpr float kLumR = 0.2126f, kLumG = 0.7152f, kLumB = 0.0722f;
 constexpr int kMaxPathLen = 16;               // L <= 16  ->  d <= 62

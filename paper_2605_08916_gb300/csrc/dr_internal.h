@@ -276,6 +276,17 @@ struct EvalArgs {
 };
 void launch_eval(const EvalArgs& a, cudaStream_t s);
 
+// L* p / p at query points of a 2-D mixture target (dr_bias.cu)
+struct LstarArgs {
+  DevMixture M;
+  const float* y;  // [n_pts][2]
+  long long n_pts;
+  double stddev, h, gamma_tilde, eps, radius;
+  int n;          // quadrature nodes per side
+  double* out;    // [n_pts]
+};
+void launch_lstar(const LstarArgs& a, cudaStream_t s);
+
 void launch_trace(const DevScene& S, const float* rays, long long n, int exclude, int* tri, float* t, uint32_t* err,
                   cudaStream_t s);
 void launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, long long n, cudaStream_t s);

@@ -334,6 +334,14 @@ class Renderer:
         call("dr_eval_logp", self.h, int(L), _ptr(x), int(M), _ptr(logp), _ptr(g), _ptr(pix), _ptr(f))
         return logp, g, pix, f
 
+    def lstar_over_p(self, y, params, radius=8.0, n=129):
+        """(L* p / p)(y) of the 2-D mixture target at query points y (float32
+        CUDA tensor [M, 2]); FP64 CUDA tensor [M]."""
+        y = y.contiguous()
+        out = torch.empty(y.shape[0], dtype=torch.float64, device=y.device)
+        call("dr_lstar_over_p", self.h, C.byref(params), _ptr(y), int(y.shape[0]), float(radius), int(n), _ptr(out))
+        return out
+
     def pt_render(self, L, spp, seed=7):
         """Stratified path-traced image [H, W, 3] (FP64 CUDA tensor) of the
         uploaded scene, in the units of resolve()."""

@@ -273,6 +273,44 @@ def test_adjoint_matches_fp64_central_differences(torch, R, oracle, case):
     assert np.mean(rel[use] <= 1e-4) >= 0.99
 
 
+def test_lstar_over_p_matches_oracle(torch, R, oracle):
+    """The App. C diagnostic L* p / p (Sec. 5.2, Eq. bias) on a 2-D mixture,
+    on the device (FP64 quadrature, one block per point) against the
+    oracle's quadrature with the same nodes: both are FP64 sums of the same
+    terms in different orders, so they agree to a relative 1e-13 of K* p / p,
+    i.e. 1e-8 after the factor h = 1 / dt; the constant density gives 0 (the
+    kernel's mass is 1)."""
+    f32 = lambda v: np.asarray(v, np.float32).astype(np.float64)
+    mix = S.Mixture(2, f32([0.3, 0.7]), f32([[0.35, 0.45], [0.62, 0.58]]), f32([0.05, 0.08]), 8, 8)
+    stddev, dt, gt, eps = (float(np.float32(v)) for v in (5e-3, 1e-5, 1.25e-5, 1e-8))
+    prm = R.make_params(L=1, drift="adjoint", stddev=stddev, dt=dt, gamma_tilde=gt, eps=eps)
+    y = np.random.default_rng(21).random((2048, 2)).astype(np.float32)
+    y[:1024] = (mix.mu[np.arange(1024) % 2] + np.random.default_rng(22).normal(size=(1024, 2)) * 0.06).astype(
+        np.float32) % 1.0
+    r = R.Renderer()
+    r.set_mixture(mix)
+    yd = torch.from_numpy(y).cuda()
+    r.lstar_over_p(yd, prm)                  # warm-up
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    got = r.lstar_over_p(yd, prm)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    got = got.cpu().numpy()
+    ref = oracle.lstar_over_p(oracle.target(mix), y.astype(np.float64), stddev=stddev, dt=dt, gamma_tilde=gt,
+                              eps=eps, radius=8.0, n=129)
+    err = np.abs(got - ref)
+    print(f"L*p/p on {len(y)} points in {ms:.2f} ms ({len(y) * 129 * 129 / ms / 1e6:.2f} G nodes/s); max |dev - "
+          f"oracle| {err.max():.2e}, range of values {np.abs(ref).max():.3g}")
+    assert np.abs(ref).max() > 1.0
+    assert np.all(err <= 1e-8 * (1.0 + np.abs(ref)) + 1e-7)
+    r.set_mixture(S.constant_target(d=2, value=2.0, width=8, height=8))
+    flat = r.lstar_over_p(yd[:64], prm).cpu().numpy()
+    assert np.all(np.abs(flat) < 1e-6), np.abs(flat).max()
+    r.close()
+
+
 def test_logp_autograd_function(torch, R, oracle):
     """LogPFunction: x -> log p as a torch autograd node; its backward runs
     the adjoint kernel, scaled by the incoming gradient, and matches the
