@@ -391,6 +391,12 @@ def run_ours(args, wl, rank, world, local):
         log(f"timed {steps} steps in {n_frames} frames: {total_ms:.1f} ms")
         e2e = None if args.no_e2e else run_e2e(R, scene, wl, N, steps, local, stream)
         rel = None if args.no_relmse else run_relmse33(R, scene, wl, local)
+        others = None
+        if not args.no_other and world == 1:
+            others = [measure_workload(R, n, local) for n in OTHER_WORKLOADS if n != args.workload]
+            for o in others:
+                log(f"other workload {o['workload']}: {o['value'] / 1e6:.1f} M chain-steps/s, "
+                    f"roofline {o['roofline']['frac']:.3f}")
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
                 "warmup": args.warmup, "ms_per_step": t_max / steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -418,7 +424,8 @@ def run_ours(args, wl, rank, world, local):
                 "phase_ms_per_step": {k: v[0] / prof_steps for k, v in prof.items() if v[1]},
                 "bounce_ms_per_step": {k: [round(x / prof_steps, 4) for x in v] for k, v in bprof.items()}
                 if wavefront else None,
-                "clocks": clocks, "gpu_launches": launches, "e2e": e2e, "relmse_33ms": rel}
+                "clocks": clocks, "gpu_launches": launches, "e2e": e2e, "relmse_33ms": rel,
+                "other_workloads": others}
         if world == 1 and not args.no_cpu_baseline:
             cb = cpu_baseline(wl, flat_of(scene))
             cb["per_core"] = cb["value"] / max(1, cb["cores"])
@@ -432,6 +439,69 @@ def run_ours(args, wl, rank, world, local):
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+OTHER_WORKLOADS = ["caustic-20k-512", "cornell-glossy-256", "cornell-64-fd"]
+
+
+def measure_workload(R, name, local, steps=16, warmup=4):
+    """A short measurement of another configuration in the same process:
+    chain-steps/s over `steps` steps in graph frames (inputs > L2 or a 512 MB
+    L2 flush between frames), the traversal roofline from the statistics
+    pass and the profiled phases, as in the main measurement."""
+    import torch
+    wl = WORKLOADS[name]
+    dev = torch.device("cuda", local)
+    scene = wl["scene"]()
+    N, F = wl["chains"], wl["spp"]
+    stream = torch.cuda.Stream(device=dev)
+    r = R.Renderer(local, stream)
+    upload(r, scene)
+    r.init_chains(N, SEED, R.make_params(L=wl["L"], drift=wl["drift"], rb=True, k0=0.0, steps_per_splat=F))
+    r.set_stats(True)
+    r.step(2)
+    ts = r.traversal_stats()
+    r.set_stats(False)
+    bvh4 = r.bvh4_info()
+    r.set_option("profile", 1)
+    r.profile()
+    r.step(4)
+    prof = r.profile()
+    r.set_option("profile", 0)
+    wavefront = prof["trace"][1] > 0
+    d = 2 + 4 * (wl["L"] - 1)
+    trav = (ts["node_visits"] * (112 if bvh4 else 64) + ts["tri_tests"] * 48) / (2 * N)
+    if wavefront:
+        k_ms, k_bytes = (prof["trace"][0] + prof["shadow"][0]) / 4, trav
+    else:
+        k_ms = (prof["fused_step"][0] + prof["fd_score"][0]) / 4
+        k_bytes = trav + 4 * d * 4 + 1 + 1 + 4 + 16
+    n_frames = max(1, steps // F)
+    for _ in range(max(1, warmup // F)):
+        r.frame(F)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    c0 = r.counters()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_frames)]
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        for k in range(n_frames):
+            flush.zero_()
+            ev[k][0].record(stream)
+            r.frame(F)
+            ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    c1 = r.counters()
+    r.close()
+    peak, peak_kind = measured_peaks()
+    achieved = k_bytes * N / (k_ms / 1e3) / 1e9
+    return {"workload": name, "triangles": scene.n_tris, "image": [scene.width, scene.height], "chains": N,
+            "max_path_len": wl["L"], "drift": wl["drift"], "execution": "wavefront" if wavefront else "fused",
+            "value": N * n_frames * F / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / (n_frames * F),
+            "steps": n_frames * F, "rays_per_s": (c1["rays"] - c0["rays"]) / (ms / 1e3),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "peak_kind": peak_kind, "kernel_ms_per_step": k_ms,
+                         "algorithmic_bytes_per_chain_step": k_bytes}}
 
 
 BUDGET_MS = 1000.0 / 30.0
@@ -742,6 +812,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end run (profiling cases)")
     ap.add_argument("--no-relmse", action="store_true", help="skip the 33 ms image relMSE comparison")
+    ap.add_argument("--no-other", action="store_true",
+                    help="skip the short measurements of the other configurations (caustic, Cornell)")
     ap.add_argument("--chains", type=int, default=0, help="override the workload's chain count (profiling cases)")
     ap.add_argument("--wavefront", type=int, default=-1, choices=[-1, 0, 1],
                     help="bounce-by-bounce execution over compacted path queues: 1 on, 0 fused kernel, "
