@@ -394,6 +394,7 @@ def run_ours(args, wl, rank, world, local):
         others = None
         if not args.no_other and world == 1:
             others = [measure_workload(R, n, local) for n in OTHER_WORKLOADS if n != args.workload]
+            others.append(measure_batch(R, local))
             for o in others:
                 log(f"other workload {o['workload']}: {o['value'] / 1e6:.1f} M chain-steps/s, "
                     f"roofline {o['roofline']['frac']:.3f}")
@@ -502,6 +503,57 @@ def measure_workload(R, name, local, steps=16, warmup=4):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "peak_kind": peak_kind, "kernel_ms_per_step": k_ms,
                          "algorithmic_bytes_per_chain_step": k_bytes}}
+
+
+def measure_batch(R, local, steps=16, F=4):
+    """A short measurement of the 64-scene batch (configuration 5) in the
+    same process, with the library's default schedule (the full run,
+    `--workload batched-64`, autotunes it and adds the per-scene baseline)."""
+    import torch
+    dev = torch.device("cuda", local)
+    items = S.procedural_batch()
+    N = sum(n for _, _, n in items)
+    stream = torch.cuda.Stream(device=dev)
+    r = R.Renderer(local, stream)
+    r.upload_scenes(items)
+    r.init_chains(N, SEED, R.make_params(L=16, drift="adjoint", rb=True, k0=0.0, steps_per_splat=F))
+    r.set_stats(True)
+    r.step(2)
+    ts = r.traversal_stats()
+    r.set_stats(False)
+    r.set_option("profile", 1)
+    r.profile()
+    r.step(4)
+    prof = r.profile()
+    r.set_option("profile", 0)
+    trav = (ts["node_visits"] * 112 + ts["tri_tests"] * 48) / (2 * N)
+    k_ms = (prof["trace"][0] + prof["shadow"][0] + prof["tail"][0]) / 4
+    for _ in range(2):
+        r.frame(F)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    n_frames = max(1, steps // F)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_frames)]
+    c0 = r.counters()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        for k in range(n_frames):
+            flush.zero_()
+            ev[k][0].record(stream)
+            r.frame(F)
+            ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    c1 = r.counters()
+    r.close()
+    peak, peak_kind = measured_peaks()
+    achieved = trav * N / (k_ms / 1e3) / 1e9
+    return {"workload": "batched-64", "scenes": len(items), "triangles": sum(sc.n_tris for sc, _, _ in items),
+            "chains": N, "schedule": "library default", "execution": "wavefront (one batch)",
+            "value": N * n_frames * F / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / (n_frames * F),
+            "steps": n_frames * F, "rays_per_s": (c1["rays"] - c0["rays"]) / (ms / 1e3),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "peak_kind": peak_kind, "kernel_ms_per_step": k_ms,
+                         "algorithmic_bytes_per_chain_step": trav}}
 
 
 BUDGET_MS = 1000.0 / 30.0

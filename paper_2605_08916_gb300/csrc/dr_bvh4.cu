@@ -1,12 +1,16 @@
 // Collapse of the binary BVH into a 4-wide BVH, on the device, at scene
 // upload.
 //
-// Leaves: a binary subtree of at most kBvh4MaxLeaf triangles becomes one
-// leaf when the surface-area heuristic rates a leaf no more expensive than
-// the subtree (unit cost per node visit and per triangle test, weighted by
-// area relative to the parent).  Inner nodes: starting from a binary node's
-// two children, the inner child of largest surface area is replaced by its
-// own two children until there are four children or only leaves are left.
+// The 4-wide tree is the one of least surface-area-heuristic cost (unit
+// cost per node visit and per triangle test, weighted by box area) that
+// regroups the binary tree's nodes, found by dynamic programming over the
+// binary tree: for every binary node n and k = 1..4 the cheapest way to
+// place n's subtree into at most k child slots of a 4-wide node (one slot:
+// n as a leaf of at most kBvh4MaxLeaf triangles, or as a 4-wide node of its
+// own; more slots: n's two children share them).  The 8-wide collapse
+// widens greedily: starting from a binary node's two children, the inner
+// child of largest surface area is replaced by its own two children until
+// there are eight children or only leaves are left.
 // Triangles are re-laid in the binary tree's depth-first order, so every
 // subtree (hence every 4-wide leaf) is one contiguous range.
 //
@@ -84,6 +88,8 @@ struct B4Scratch {
   uint32_t* tri_refs; // [nt] references to each triangle
   uint32_t* counts;   // [8]: queue sizes (2), max need, max 4-wide depth, max binary depth
   uint32_t* err;      // [1]
+  float* dp_cost;     // [nn][4]: [0] the subtree in one slot, [k - 1] in k = 2..4 slots shared by its children
+  uint8_t* dp_split;  // [nn][4]: [k - 1] slots of the left child when k = 2..4 slots are shared
   void* scan_tmp;
 };
 
@@ -91,7 +97,8 @@ size_t a256(size_t b) { return (b + 255) & ~size_t(255); }
 
 size_t b4_bytes(int nn, int nt) {
   const size_t n = (size_t)nn;
-  return a256(n * 4) * 12 + a256((size_t)nt * 4) + a256(n) + a256(32) + a256(4) + a256(scan_scratch_bytes(n));
+  return a256(n * 4) * 12 + a256((size_t)nt * 4) + a256(n) + a256(32) + a256(4) + a256(n * 16) + a256(n * 4) +
+         a256(scan_scratch_bytes(n));
 }
 
 B4Scratch b4_carve(void* base, int nn, int nt) {
@@ -114,6 +121,8 @@ B4Scratch b4_carve(void* base, int nn, int nt) {
   s.as_leaf = reinterpret_cast<uint8_t*>(p); p += a256(n);
   s.counts = reinterpret_cast<uint32_t*>(p); p += a256(32);
   s.err = reinterpret_cast<uint32_t*>(p); p += a256(4);
+  s.dp_cost = reinterpret_cast<float*>(p); p += a256(n * 16);
+  s.dp_split = reinterpret_cast<uint8_t*>(p); p += a256(n * 4);
   s.scan_tmp = p;
   return s;
 }
@@ -159,13 +168,26 @@ __global__ void verify_kernel(int nn, int nt, const uint32_t* refs, const uint32
   if (i < nt && tri_refs[i] != 1u) atomicOr(err, kErrBadIndex);
 }
 
-// settles node n (its inner children are settled): count, SAH cost, leaf
-// decision
-DR_D void settle(const float4* __restrict__ n2, int n, int* cnt, float* cost, uint8_t* as_leaf, int max_leaf) {
+// Area-weighted SAH cost of placing child reference c into at most k slots
+// (a binary leaf link takes one slot as it is).
+DR_D float slots_cost(const Kid& c, int k, const float* dp_cost) {
+  if (c.code < 0) return box_area(c.lo, c.hi) * (float)leaf_count(c.code);
+  const volatile float* d = dp_cost + 4 * (size_t)c.code;
+  float best = d[0];
+  for (int i = 2; i <= k; ++i) best = fminf(best, d[i - 1]);
+  return best;
+}
+
+// settles node n (its inner children are settled): count, binary SAH cost,
+// and the collapse's dynamic programme (see the file comment): the costs of
+// n's subtree in one slot and in 2..4 slots shared by its children, the
+// best split of those slots, and whether n in one slot is a leaf
+DR_D void settle(const float4* __restrict__ n2, int n, int* cnt, float* cost, uint8_t* as_leaf, float* dp_cost,
+                 uint8_t* dp_split, int max_leaf) {
   const Kid k0 = kid_of(n2, n, 0), k1 = kid_of(n2, n, 1);
-  const float an = fmaxf(box_area(f3(fminf(k0.lo.x, k1.lo.x), fminf(k0.lo.y, k1.lo.y), fminf(k0.lo.z, k1.lo.z)),
-                                  f3(fmaxf(k0.hi.x, k1.hi.x), fmaxf(k0.hi.y, k1.hi.y), fmaxf(k0.hi.z, k1.hi.z))),
-                         1e-30f);
+  const float an_raw = box_area(f3(fminf(k0.lo.x, k1.lo.x), fminf(k0.lo.y, k1.lo.y), fminf(k0.lo.z, k1.lo.z)),
+                                f3(fmaxf(k0.hi.x, k1.hi.x), fmaxf(k0.hi.y, k1.hi.y), fmaxf(k0.hi.z, k1.hi.z)));
+  const float an = fmaxf(an_raw, 1e-30f);
   int total = 0;
   float c_inner = 1.0f;
   for (int k = 0; k < 2; ++k) {
@@ -182,7 +204,25 @@ DR_D void settle(const float4* __restrict__ n2, int n, int* cnt, float* cost, ui
     total += cc;
     c_inner += box_area(c.lo, c.hi) / an * ccost;
   }
-  const bool leaf = total <= max_leaf && (float)total <= c_inner;
+  float* dc = dp_cost + 4 * (size_t)n;
+  uint8_t* ds = dp_split + 4 * (size_t)n;
+  for (int k = 2; k <= 4; ++k) {
+    float best = 3.0e38f;
+    int bj = 1;
+    for (int j = 1; j < k; ++j) {
+      const float c = slots_cost(k0, j, dp_cost) + slots_cost(k1, k - j, dp_cost);
+      if (c < best) {
+        best = c;
+        bj = j;
+      }
+    }
+    dc[k - 1] = best;
+    ds[k - 1] = (uint8_t)bj;
+  }
+  const float node_cost = an_raw + dc[3];
+  const bool leaf = total <= max_leaf && an_raw * (float)total <= node_cost;
+  dc[0] = leaf ? an_raw * (float)total : node_cost;
+  ds[0] = 0;
   cnt[n] = total;
   cost[n] = leaf ? (float)total : c_inner;
   as_leaf[n] = leaf ? 1 : 0;
@@ -192,7 +232,8 @@ DR_D void settle(const float4* __restrict__ n2, int n, int* cnt, float* cost, ui
 // settled by the walk that brings its second finished child, the first
 // arrival ends its walk there.
 __global__ void bottom_up_kernel(const float4* __restrict__ n2, int nn, const int* parent, int* cnt, float* cost,
-                                 uint8_t* as_leaf, uint32_t* visit, int max_leaf, uint32_t* err) {
+                                 uint8_t* as_leaf, float* dp_cost, uint8_t* dp_split, uint32_t* visit, int max_leaf,
+                                 uint32_t* err) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= nn) return;
   const float4 d = n2[4 * n + 3];
@@ -202,7 +243,7 @@ __global__ void bottom_up_kernel(const float4* __restrict__ n2, int nn, const in
   __threadfence();
   int cur = n;
   for (int guard = 0; guard <= nn; ++guard) {
-    settle(n2, cur, cnt, cost, as_leaf, max_leaf);
+    settle(n2, cur, cnt, cost, as_leaf, dp_cost, dp_split, max_leaf);
     const int p = parent[cur];
     if (p < 0) return;
     __threadfence();  // cur's results visible before its arrival is counted
@@ -263,13 +304,52 @@ DR_D int expand(const float4* __restrict__ n2, int n, const uint8_t* as_leaf, Ki
   return nk;
 }
 
-__global__ void mark_kernel(const float4* __restrict__ n2, const uint8_t* as_leaf, const uint32_t* q_in, uint32_t n_in,
-                            uint32_t* q_out, uint32_t* n_out, uint32_t* is4, int* need, int* depth, uint32_t* maxes) {
+// The children of 4-wide node n: the binary subtree distributed over four
+// slots by the dynamic programme's choices (a reference that is best in one
+// slot becomes a child, else its two children share its slots).
+DR_D int expand_dp(const float4* __restrict__ n2, int n, const float* dp_cost, const uint8_t* dp_split,
+                   Kid kids[4]) {
+  struct Item {
+    Kid c;
+    int k;
+  };
+  Item st[4];
+  int sp = 0, nk = 0;
+  const int j = dp_split[4 * (size_t)n + 3];
+  st[sp++] = Item{kid_of(n2, n, 1), 4 - j};
+  st[sp++] = Item{kid_of(n2, n, 0), j};
+  while (sp > 0 && nk < 4) {
+    const Item it = st[--sp];
+    const Kid& c = it.c;
+    int bk = 1;
+    if (c.code >= 0) {
+      const float* d = dp_cost + 4 * (size_t)c.code;
+      float best = d[0];
+      for (int i = 2; i <= it.k; ++i)
+        if (d[i - 1] < best) {
+          best = d[i - 1];
+          bk = i;
+        }
+    }
+    if (bk == 1 || sp + 2 > 4) {
+      kids[nk++] = c;
+    } else {
+      const int jj = dp_split[4 * (size_t)c.code + bk - 1];
+      st[sp++] = Item{kid_of(n2, c.code, 1), bk - jj};
+      st[sp++] = Item{kid_of(n2, c.code, 0), jj};
+    }
+  }
+  return nk;
+}
+
+__global__ void mark_kernel(const float4* __restrict__ n2, const uint8_t* as_leaf, const float* dp_cost,
+                            const uint8_t* dp_split, const uint32_t* q_in, uint32_t n_in, uint32_t* q_out,
+                            uint32_t* n_out, uint32_t* is4, int* need, int* depth, uint32_t* maxes) {
   const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n_in) return;
   const int n = (int)q_in[t];
   Kid kids[4];
-  const int nk = expand(n2, n, as_leaf, kids);
+  const int nk = expand_dp(n2, n, dp_cost, dp_split, kids);
   // a closest-hit walk pushes every hit child but the nearest (leaves too)
   const int here = need[n] + max(0, nk - 1);
   atomicMax(&maxes[0], (uint32_t)here);
@@ -317,15 +397,16 @@ DR_D void leaf_range(const float4* __restrict__ n2, const Kid& c, const int* cnt
 }
 
 __global__ void emit_kernel(const float4* __restrict__ n2, const float4* __restrict__ t2, int nn, int nt,
-                            const uint8_t* as_leaf, const int* cnt, const int* first, const uint32_t* is4,
-                            const uint32_t* slot, float4* __restrict__ n4, float4* __restrict__ t4, uint32_t* err) {
+                            const uint8_t* as_leaf, const float* dp_cost, const uint8_t* dp_split, const int* cnt,
+                            const int* first, const uint32_t* is4, const uint32_t* slot, float4* __restrict__ n4,
+                            float4* __restrict__ t4, uint32_t* err) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= nn) return;
   // triangles of this node's binary leaf links, to their depth-first place
   relayout_links(n2, t2, n, nt, cnt, first, t4, err);
   if (!is4[n]) return;
   Kid kids[4];
-  const int nk = expand(n2, n, as_leaf, kids);
+  const int nk = expand_dp(n2, n, dp_cost, dp_split, kids);
   float lo[3][4] = {}, hi[3][4] = {};  // empty slots stay zero; the traversal skips them by their link
   int links[4] = {kBvh4Empty, kBvh4Empty, kBvh4Empty, kBvh4Empty};
   for (int k = 0; k < nk; ++k) {
@@ -554,8 +635,8 @@ int prepare_tree(const float4* d_nodes2, int nn, int n_tris, const B4Scratch& b,
     return -1;
   }
   *tree_ok = 1;
-  bottom_up_kernel<<<blocks(nn), kB4Threads, 0, s>>>(d_nodes2, nn, b.parent, b.cnt, b.cost, b.as_leaf, b.visit,
-                                                      max_leaf, b.err);
+  bottom_up_kernel<<<blocks(nn), kB4Threads, 0, s>>>(d_nodes2, nn, b.parent, b.cnt, b.cost, b.as_leaf, b.dp_cost,
+                                                      b.dp_split, b.visit, max_leaf, b.err);
   first_kernel<<<blocks(nn), kB4Threads, 0, s>>>(d_nodes2, nn, b.parent, b.cnt, b.first, b.counts + 4, b.err);
   return 0;
 }
@@ -577,7 +658,7 @@ int bvh4_plan(const float4* d_nodes2, int n_inner, int n_tris, void* scratch, Bv
     if (level > nn) return -1;
     uint32_t* out_count = b.counts + ((level + 1) & 1);
     cudaMemsetAsync(out_count, 0, 4, s);
-    mark_kernel<<<blocks(n_in), kB4Threads, 0, s>>>(d_nodes2, b.as_leaf, b.queue[level & 1], n_in,
+    mark_kernel<<<blocks(n_in), kB4Threads, 0, s>>>(d_nodes2, b.as_leaf, b.dp_cost, b.dp_split, b.queue[level & 1], n_in,
                                                     b.queue[(level + 1) & 1], out_count, b.is4, b.need, b.depth,
                                                     b.counts + 2);
     ++launches;
@@ -610,8 +691,9 @@ int bvh4_plan(const float4* d_nodes2, int n_inner, int n_tris, void* scratch, Bv
 int bvh4_emit(const float4* d_nodes2, const float4* d_tris2, int n_inner, int n_tris, void* scratch,
               float4* d_nodes4, float4* d_tris4, cudaStream_t s) {
   B4Scratch b = b4_carve(scratch, n_inner, n_tris);
-  emit_kernel<<<blocks(n_inner), kB4Threads, 0, s>>>(d_nodes2, d_tris2, n_inner, n_tris, b.as_leaf, b.cnt, b.first,
-                                                      b.is4, b.slot, d_nodes4, d_tris4, b.err);
+  emit_kernel<<<blocks(n_inner), kB4Threads, 0, s>>>(d_nodes2, d_tris2, n_inner, n_tris, b.as_leaf, b.dp_cost,
+                                                      b.dp_split, b.cnt, b.first, b.is4, b.slot, d_nodes4, d_tris4,
+                                                      b.err);
   uint32_t err = 0;
   cudaMemcpyAsync(&err, b.err, 4, cudaMemcpyDeviceToHost, s);
   if (cudaStreamSynchronize(s) != cudaSuccess || err != 0) return -1;
