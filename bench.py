@@ -334,7 +334,10 @@ def run_ours(args, wl, rank, world, local):
                   else "wf_traverse (8-wide compressed BVH traversal passes)" if bvh8
                   else "wf_traverse (4-wide BVH traversal passes)" if wide
                   else "wf_trace + wf_shadow (binary BVH traversal passes)")
-        k_ms = (prof["trace"][0] + prof["shadow"][0]) / prof_steps
+        # the persistent tail pass (long paths) traverses too: its node
+        # visits are in the statistics, so its time is in the denominator
+        # (with its shading, which makes the fraction a lower bound)
+        k_ms = (prof["trace"][0] + prof["shadow"][0] + prof["tail"][0]) / prof_steps
         k_bytes = trav_bytes
     else:
         k_name = "step_kernel (fused Restore step)"
@@ -473,7 +476,7 @@ def measure_workload(R, name, local, steps=16, warmup=4):
     d = 2 + 4 * (wl["L"] - 1)
     trav = (ts["node_visits"] * (112 if bvh4 else 64) + ts["tri_tests"] * 48) / (2 * N)
     if wavefront:
-        k_ms, k_bytes = (prof["trace"][0] + prof["shadow"][0]) / 4, trav
+        k_ms, k_bytes = (prof["trace"][0] + prof["shadow"][0] + prof["tail"][0]) / 4, trav
     else:
         k_ms = (prof["fused_step"][0] + prof["fd_score"][0]) / 4
         k_bytes = trav + 4 * d * 4 + 1 + 1 + 4 + 16
@@ -772,7 +775,9 @@ def run_batched(args, rank, world, local):
     r.step(prof_steps)
     prof = r.profile()
     r.set_option("profile", 0)
-    k_ms = (prof["trace"][0] + prof["shadow"][0]) / prof_steps
+    # the tail pass's node visits are counted, so its time is too (it also
+    # shades: the fraction is a lower bound when the tail pass runs)
+    k_ms = (prof["trace"][0] + prof["shadow"][0] + prof["tail"][0]) / prof_steps
     n_frames = max(1, (args.steps + F - 1) // F)
     steps = n_frames * F
     for _ in range(max(1, (args.warmup + F - 1) // F)):

@@ -311,6 +311,32 @@ def test_lstar_over_p_matches_oracle(torch, R, oracle):
     r.close()
 
 
+@pytest.mark.parametrize("inside", [True, False], ids=["camera-in-glass", "camera-in-air"])
+def test_dielectric_radiance_scaling_on_gpu(torch, R, oracle, inside):
+    """The CUDA dielectric branch against optics directly (the oracle's pins
+    D1 and D2): in a room of black walls emitting Le every path that reaches
+    a wall carries n^2 Le from a camera inside a glass body and Le from one
+    in air (FP32: within 1e-5 relative); and path for path the device's f
+    equals the oracle's."""
+    n, Le, L = 1.5, 1.0, 8
+    scene = S.glass_furnace(camera_inside=inside, emission=Le, ior=n)
+    d = S.pss_dim(L)
+    x = np.random.default_rng(23).random((20000, d)).astype(np.float32)
+    r = R.Renderer()
+    r.upload_scene(scene)
+    _, _, _, f = r.eval_logp(torch.from_numpy(x).cuda(), L=L, want_f=True)
+    torch.cuda.synchronize()
+    f = f.cpu().numpy().astype(np.float64) / (scene.width * scene.height)
+    r.close()
+    reached = f[:, 0] > 0
+    expect = n * n * Le if inside else Le
+    assert reached.mean() > 0.9
+    assert np.allclose(f[reached], expect, rtol=1e-5, atol=0.0), np.unique(np.round(f[reached, 0], 6))[:8]
+    fo = oracle.evaluate(oracle.OracleScene(scene), x.astype(np.float64), L)["f"] / (scene.width * scene.height)
+    same = np.abs(f - fo).max(1) <= 1e-5 * np.maximum(fo.max(1), 1e-12)
+    assert same.mean() > 0.995, same.mean()
+
+
 def test_logp_autograd_function(torch, R, oracle):
     """LogPFunction: x -> log p as a torch autograd node; its backward runs
     the adjoint kernel, scaled by the incoming gradient, and matches the
