@@ -28,13 +28,14 @@ EXPORTS = ["dr_version", "dr_last_error", "dr_create", "dr_destroy", "dr_scene_u
            "dr_get_counters", "dr_eval_logp", "dr_trace_closest", "dr_philox", "dr_splat_records",
            "dr_clear_image", "dr_state_save", "dr_state_load", "dr_set_stats", "dr_get_traversal_stats",
            "dr_bvh_info", "dr_get_launch_count", "dr_get_chain_shape", "dr_pt_render", "dr_set_bvh_builder",
-           "dr_splat_records_noalloc", "dr_set_option", "dr_get_profile", "dr_frame", "dr_bvh4_info", "dr_bvh4_sah", "dr_bvh8_info", "dr_get_bounce_profile",
+           "dr_splat_records_noalloc", "dr_set_option", "dr_get_profile", "dr_frame", "dr_bvh4_info", "dr_bvh4_sah", "dr_bvh8_info", "dr_get_bounce_profile", "dr_get_bounce_rays",
            "dr_scenes_upload_batch", "dr_resolve_scene", "dr_get_scene_counters", "dr_scene_upload_instanced",
            "dr_two_level_info", "dr_splat_records_noalloc_status", "dr_resolve_accum", "dr_get_p_sum",
            "dr_k0_from_p_sum", "dr_lstar_over_p"]
 DR_OPT_WORK_ORDER, DR_OPT_WAVEFRONT, DR_OPT_PROFILE, DR_OPT_BVH_WIDTH = 1, 2, 3, 4
 DR_OPT_TRAVERSE_BLOCKS, DR_OPT_REFILL, DR_OPT_RAY_ORDER, DR_OPT_TAIL_BOUNCE = 5, 6, 7, 8
 DR_OPT_TWO_LEVEL = 9
+DR_OPT_SPLIT_BOUNCE, DR_OPT_SIDE_BLOCKS = 10, 11
 DR_PHASES = 11
 PHASE_NAMES = ["wf_begin", "trace", "shade", "shadow", "finish", "adjoint", "fused_step", "fd_score", "splat",
                "work_order", "tail"]
@@ -111,6 +112,7 @@ def signatures():
         "dr_bvh8_info": ([P, P, P], C.c_int),
         "dr_bvh4_sah": ([P, P, P], C.c_int),
         "dr_get_bounce_profile": ([P, P, I32], C.c_int),
+        "dr_get_bounce_rays": ([P, P, I32], C.c_int),
         "dr_scenes_upload_batch": ([P, P, I32], C.c_int),
         "dr_resolve_scene": ([P, I32, P], C.c_int),
         "dr_get_scene_counters": ([P, I32, P, P], C.c_int),

@@ -73,13 +73,16 @@ class Renderer:
     def set_option(self, option, value):
         """option: "wavefront" (-1 auto / 0 / 1), "work_order" (0/1), "profile" (0/1) or
         "bvh_width" (0 automatic / 2 / 4 / 8; 8 before the upload), "traverse_blocks" (0 = all resident),
-        "refill" (1..32), "ray_order" (-1 automatic / 0 / 1), "tail_bounce" (-1 automatic, 0 off, k) or
-        "two_level" (1: walk an instanced scene's two-level BVH, 0: its flattened BVH)."""
+        "refill" (1..32), "ray_order" (-1 automatic / 0 / 1), "tail_bounce" (-1 automatic, 0 off, k),
+        "two_level" (1: walk an instanced scene's two-level BVH, 0: its flattened BVH), "split_bounce"
+        (-1 automatic, 0 off, k: finish and differentiate the paths ended by bounce k on a second stream
+        while the later bounces run) or "side_blocks" (blocks per SM of that second-stream adjoint)."""
         code = {"work_order": _lib.DR_OPT_WORK_ORDER, "wavefront": _lib.DR_OPT_WAVEFRONT,
                 "profile": _lib.DR_OPT_PROFILE, "bvh_width": _lib.DR_OPT_BVH_WIDTH,
                 "traverse_blocks": _lib.DR_OPT_TRAVERSE_BLOCKS, "refill": _lib.DR_OPT_REFILL,
                 "ray_order": _lib.DR_OPT_RAY_ORDER, "tail_bounce": _lib.DR_OPT_TAIL_BOUNCE,
-                "two_level": _lib.DR_OPT_TWO_LEVEL}[option]
+                "two_level": _lib.DR_OPT_TWO_LEVEL, "split_bounce": _lib.DR_OPT_SPLIT_BOUNCE,
+                "side_blocks": _lib.DR_OPT_SIDE_BLOCKS}[option]
         call("dr_set_option", self.h, code, int(value))
 
     def set_bvh_builder(self, builder="ploc", radius=16):
@@ -197,12 +200,17 @@ class Renderer:
         call("dr_frame", self.h, int(n_steps))
 
     def bounce_profile(self, n_bounces):
-        """Per-bounce milliseconds of the trace / shade / shadow passes since the
-        last profile() call: dict of three lists of n_bounces values."""
+        """Per-bounce milliseconds of the trace / shade / shadow passes, and the
+        closest-hit and shadow rays of each bounce, since the last profile()
+        call: dict of five lists of n_bounces values."""
         ms = (C.c_double * (3 * n_bounces))()
         call("dr_get_bounce_profile", self.h, ms, int(n_bounces))
         v = list(ms)
-        return {"trace": v[:n_bounces], "shade": v[n_bounces:2 * n_bounces], "shadow": v[2 * n_bounces:]}
+        rays = (C.c_uint64 * (2 * n_bounces))()
+        call("dr_get_bounce_rays", self.h, rays, int(n_bounces))
+        n = list(rays)
+        return {"trace": v[:n_bounces], "shade": v[n_bounces:2 * n_bounces], "shadow": v[2 * n_bounces:],
+                "rays": n[:n_bounces], "shadow_rays": n[n_bounces:]}
 
     def profile(self):
         """Per-phase device milliseconds since the last call (DR_OPT_PROFILE)."""

@@ -939,6 +939,52 @@ def test_tail_pass_gives_the_same_chains(torch, R, tail):
     assert c_a["tour_count"] == c_b["tour_count"] and c_a["rays"] == c_b["rays"]
 
 
+@pytest.mark.parametrize("split,side_blocks", [(1, 0), (3, 2), (8, 0), (11, 1)])
+def test_split_step_gives_the_same_chains(torch, R, split, side_blocks):
+    """Finishing and differentiating the chains whose paths ended by bounce
+    `split` on a second stream while the later bounces run changes only
+    which thread handles which chain and when: identical chain states,
+    counters and images, in plain steps and in graph frames."""
+    scene, L = S.procedural_scene(1, 64, 36, target_tris=60000, n_objects=40), 12
+    out = []
+    for sb, graph in ((0, False), (split, False), (split, True)):
+        s = torch.cuda.Stream()
+        r = R.Renderer(0, s)
+        r.set_option("wavefront", 1)
+        r.set_option("tail_bounce", 0)
+        r.set_option("split_bounce", sb)
+        r.set_option("side_blocks", side_blocks)
+        r.upload_scene(scene)
+        r.init_chains(16384, 37, R.make_params(L=L, drift="adjoint", k0=0.0, steps_per_splat=4))
+        for _ in range(2):
+            if graph:
+                r.frame(4)
+            else:
+                r.step(4)
+                r.splat()
+        s.synchronize()
+        out.append((r.readback_state(("x", "killed", "logp", "score")), r.readback_accum(), r.counters()))
+        r.close()
+    (a, acc_a, c_a) = out[0]
+    for b, acc_b, c_b in out[1:]:
+        for key in ("x", "killed", "logp", "score"):
+            assert np.array_equal(a[key], b[key]), key
+        assert np.array_equal(acc_a, acc_b)
+        assert c_a["tour_count"] == c_b["tour_count"] and c_a["rays"] == c_b["rays"]
+    assert c_a["tour_count"] > 0 and np.abs(a["score"]).max() > 0
+
+
+def test_split_bounce_option_is_checked(torch, R):
+    from paper_2605_08916_gb300 import _lib
+    r = R.Renderer()
+    for bad in (-2, 17):
+        with pytest.raises(_lib.DRError):
+            r.set_option("split_bounce", bad)
+    with pytest.raises(_lib.DRError):
+        r.set_option("side_blocks", 17)
+    r.close()
+
+
 @pytest.mark.parametrize("chains", [8192, 1 << 17])
 def test_graph_frames_match_plain_steps(torch, R, chains):
     """dr_frame (captured once, replayed with the step index in device
