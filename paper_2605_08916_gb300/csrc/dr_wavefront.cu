@@ -239,12 +239,31 @@ __global__ void __launch_bounds__(kWfThreads, WIDTH == kWalkTwoLevel ? 6 : kWfTr
   float tlim = 0.0f;  // closest hit so far, or the shadow ray's tmax
   Ray r;
   typename WalkOf<WIDTH>::type wk{};
+  // a pass with few rays (the late bounces) spreads them over every warp of
+  // the grid: a warp then walks a few rays, and the pass, which lasts as
+  // long as its slowest warp, ends sooner
+  const uint32_t n_warps = gridDim.x * (blockDim.x / 32u);
+  const int cap = (int)min(32u, max(1u, (n + n_warps - 1u) / n_warps));
+  const int refill = cap >= 32 ? a.refill : max(1, cap / 2);
+  const int lane = threadIdx.x & 31;
   while (true) {
     if (!drained) {
       const unsigned idle = __ballot_sync(kFull, !has);
-      if (idle) {
-        const uint32_t tn = warp_fetch(ctr, idle, n, drained);
-        if (!has && tn < n) {
+      // the idle lanes that take a ray: the lowest ones, up to cap busy lanes
+      unsigned take = idle;
+      const int room = cap - (32 - __popc(idle));
+      if (room < __popc(idle)) {
+        unsigned m = idle;
+        take = 0u;
+        for (int i = 0; i < room; ++i) {
+          const unsigned low = m & (0u - m);
+          take |= low;
+          m ^= low;
+        }
+      }
+      if (take) {
+        const uint32_t tn = warp_fetch(ctr, take, n, drained);
+        if (((take >> lane) & 1u) && tn < n) {
           shadow = tn >= n_ray;
           if (shadow) {
             t = tn - n_ray;
@@ -312,7 +331,7 @@ __global__ void __launch_bounds__(kWfThreads, WIDTH == kWalkTwoLevel ? 6 : kWfTr
         }
       }
       const unsigned act = __ballot_sync(kFull, has);
-      if (act == 0 || (!drained && __popc(act) < a.refill)) break;
+      if (act == 0 || (!drained && __popc(act) < refill)) break;
     }
   }
   add_counts(a.rays, rays);
