@@ -286,10 +286,6 @@ def run_ours(args, wl, rank, world, local):
         r.set_bvh_builder("ploc", args.ploc_radius)
     if args.tail_bounce is not None:
         r.set_option("tail_bounce", args.tail_bounce)
-    if args.split_bounce is not None:
-        r.set_option("split_bounce", args.split_bounce)
-    if args.side_blocks is not None:
-        r.set_option("side_blocks", args.side_blocks)
     upload(r, scene)
     stream.synchronize()
     t_init = time.perf_counter()
@@ -763,10 +759,6 @@ def run_batched(args, rank, world, local):
         r.set_option("bvh_width", 8)
     if args.tail_bounce is not None:
         r.set_option("tail_bounce", args.tail_bounce)
-    if args.split_bounce is not None:
-        r.set_option("split_bounce", args.split_bounce)
-    if args.side_blocks is not None:
-        r.set_option("side_blocks", args.side_blocks)
     r.upload_scenes(items)
     seed = replica_seed(SEED, rank)
     prm = R.make_params(L=16, drift="adjoint", rb=True, k0=0.0, steps_per_splat=8)
@@ -888,11 +880,6 @@ def main():
                          "-1 (default) by chain count")
     ap.add_argument("--tail-bounce", type=int, default=None,
                     help="run the bounces from this one on as one persistent pass (0 off; default: library's choice)")
-    ap.add_argument("--split-bounce", type=int, default=None,
-                    help="finish and differentiate the paths ended by this bounce on a second stream while the "
-                         "later bounces run (0 off; default: library's choice)")
-    ap.add_argument("--side-blocks", type=int, default=None,
-                    help="blocks per SM of the second-stream adjoint pass (0: as for the whole queue)")
     ap.add_argument("--ray-order", type=int, default=-1, choices=[-1, 0, 1],
                     help="sort camera rays by pixel before the first traversal (-1: by triangle count)")
     ap.add_argument("--ploc-radius", type=int, default=0,

@@ -461,24 +461,10 @@ int dr_pt_render(dr_ctx* ctx, int32_t max_path_len, uint32_t spp, uint64_t seed,
  *                      object vs world space, so a hit on an edge shared by
  *                      two triangles can go to either (the hit point and
  *                      shading always come from the flattened triangle).
- *   DR_OPT_SPLIT_BOUNCE k >= 1 (single-scene bounce-by-bounce steps over
- *                      the 4-wide BVH, no tail pass): once the paths that
- *                      ended by the shading of bounce k are complete, their
- *                      chains' clock, records and adjoint run on a second
- *                      stream of the library's while the later bounces run
- *                      on the context's stream, whose late passes then
- *                      launch at the highest stream priority; each chain's
- *                      results are exactly those of the unsplit step, and
- *                      dr_step / dr_frame still return with all work
- *                      ordered on the context's stream.  0: off; -1
- *                      (default): automatic.  Off while DR_OPT_PROFILE is 1
- *                      outside dr_frame.
- *   DR_OPT_SIDE_BLOCKS blocks per SM of that second-stream adjoint pass
- *                      (1..16; 0 (default): as for the whole queue).
  * Errors: INVALID_ARG (unknown option or value). */
 enum { DR_OPT_WORK_ORDER = 1, DR_OPT_WAVEFRONT = 2, DR_OPT_PROFILE = 3, DR_OPT_BVH_WIDTH = 4,
        DR_OPT_TRAVERSE_BLOCKS = 5, DR_OPT_REFILL = 6, DR_OPT_RAY_ORDER = 7, DR_OPT_TAIL_BOUNCE = 8,
-       DR_OPT_TWO_LEVEL = 9, DR_OPT_SPLIT_BOUNCE = 10, DR_OPT_SIDE_BLOCKS = 11 };
+       DR_OPT_TWO_LEVEL = 9 };
 int dr_set_option(dr_ctx* ctx, int32_t option, int32_t value);
 
 /* Per-phase device time accumulated since the last call while DR_OPT_PROFILE

@@ -109,9 +109,6 @@ struct dr_ctx {
   WfTuning tune;                              // DR_OPT_TRAVERSE_BLOCKS, DR_OPT_REFILL
   int ray_order = -1;                         // DR_OPT_RAY_ORDER (-1 automatic)
   int tail_bounce = -1;                       // DR_OPT_TAIL_BOUNCE (-1 automatic)
-  int split_bounce = -1;                      // DR_OPT_SPLIT_BOUNCE (-1 automatic)
-  int side_blocks = 0;                        // DR_OPT_SIDE_BLOCKS
-  WfSide side;                                // second stream of split steps (created on first use)
   float4* surf = nullptr;
   float4* lights = nullptr;
   float* nrm = nullptr;
@@ -508,41 +505,6 @@ int tail_bounce(const dr_ctx* c) {
   return c->prm.max_path_len >= 14 ? 4 : 0;
 }
 
-// The bounce after whose shading the finished paths' chains are finished
-// and differentiated on a second stream (DR_OPT_SPLIT_BOUNCE; 0 none).
-// Automatic: off; profiling (outside frame capture) also turns it off, since
-// the per-phase events are recorded on the context's stream only.
-int split_bounce(const dr_ctx* c) {
-  if (c->profile && !c->capturing) return 0;
-  const int k = c->split_bounce >= 0 ? c->split_bounce : 0;
-  return k < c->prm.max_path_len ? k : 0;
-}
-
-// The second stream (lowest priority) and its events; null if they cannot
-// be made, and then steps are not split.
-const WfSide* side_of(dr_ctx* c) {
-  if (c->side.stream) return &c->side;
-  int least = 0, greatest = 0;
-  if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) {
-    cudaGetLastError();
-    return nullptr;
-  }
-  WfSide sd;
-  bool ok = cudaStreamCreateWithPriority(&sd.stream, cudaStreamNonBlocking, least) == cudaSuccess;
-  for (cudaEvent_t* e : {&sd.fork, &sd.finish_a, &sd.adjoint_a})
-    ok = ok && cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess;
-  if (!ok) {
-    cudaGetLastError();
-    for (cudaEvent_t e : {sd.fork, sd.finish_a, sd.adjoint_a})
-      if (e) cudaEventDestroy(e);
-    if (sd.stream) cudaStreamDestroy(sd.stream);
-    return nullptr;
-  }
-  sd.priority = greatest;
-  c->side = sd;
-  return &c->side;
-}
-
 int one_step(dr_ctx* c, bool init) {
   if (!init && c->rec_count >= c->rec_cap) DR_TRY(flush(c));
   StepArgs a = step_args(c);
@@ -559,11 +521,7 @@ int one_step(dr_ctx* c, bool init) {
     const RayOrder ord = ray_order(c, a);
     WfTuning tune = c->tune;
     tune.tail_bounce = tail_bounce(c);
-    tune.split_bounce = init ? 0 : split_bounce(c);
-    tune.side_blocks_per_sm = c->side_blocks;
-    const WfSide* side = tune.split_bounce > 0 ? side_of(c) : nullptr;
-    c->launches +=
-        launch_wavefront_step(a, w, c->stats, c->n_sm, tune, hook, c->stream, kWfStep, nullptr, ord, side);
+    c->launches += launch_wavefront_step(a, w, c->stats, c->n_sm, tune, hook, c->stream, kWfStep, nullptr, ord);
     DR_TRY(check_launch("wavefront step"));
     if (c->profile && !c->capturing) {
       // rays per bounce for the profile (profiling only: waits for the step)
@@ -970,9 +928,6 @@ int dr_destroy(dr_ctx* c) {
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   for (cudaEvent_t e : c->open_ev)
     if (e) cudaEventDestroy(e);
-  for (cudaEvent_t e : {c->side.fork, c->side.finish_a, c->side.adjoint_a})
-    if (e) cudaEventDestroy(e);
-  if (c->side.stream) cudaStreamDestroy(c->side.stream);
   delete c;
   return DR_OK;
 }
@@ -2138,14 +2093,6 @@ int dr_set_option(dr_ctx* c, int32_t option, int32_t value) {
     case DR_OPT_TWO_LEVEL:
       if (value != 0 && value != 1) return fail(DR_ERR_INVALID_ARG, "dr_set_option: two-level is 0 or 1");
       c->two_level = value;
-      return DR_OK;
-    case DR_OPT_SPLIT_BOUNCE:
-      if (value < -1 || value > DR_MAX_PATH_LEN) return fail(DR_ERR_INVALID_ARG, "dr_set_option: split bounce is -1..16");
-      c->split_bounce = value;
-      return DR_OK;
-    case DR_OPT_SIDE_BLOCKS:
-      if (value < 0 || value > 16) return fail(DR_ERR_INVALID_ARG, "dr_set_option: side blocks is 0..16");
-      c->side_blocks = value;
       return DR_OK;
     case DR_OPT_BVH_WIDTH:
       if (value != 0 && value != 2 && value != 4 && value != 8)

@@ -180,17 +180,14 @@ struct __align__(16) ShadowRec {
 // counters: [k] = rays of bounce k (1..16), [17 + k] = shadow rays of bounce
 // k (1..16), [34 + k] = fetch position of the traversal pass of bounce k
 // (1..17; k = 0: the tail pass), [52 + s] = surviving chains with s path
-// segments (0..16), queued for the adjoint, [69 + s] = the same counts
-// when the early part of a split step had queued its chains
+// segments (0..16), queued for the adjoint
 constexpr int kWfShadowCount0 = 17;
 constexpr int kWfFetch0 = 34;
 constexpr int kWfAdjBucket0 = 52;
-constexpr int kWfAdjSnap0 = 69;
-constexpr int kWfCounts = 86;
+constexpr int kWfCounts = 69;
 static_assert(kWfFetch0 + kMaxPathLen + 1 < kWfAdjBucket0, "fetch counters overlap the adjoint buckets");
 static_assert(kWfShadowCount0 + kMaxPathLen < kWfFetch0, "shadow counts overlap the fetch counters");
-static_assert(kWfAdjBucket0 + kMaxPathLen < kWfAdjSnap0, "adjoint buckets overlap their snapshot");
-static_assert(kWfAdjSnap0 + kMaxPathLen < kWfCounts, "adjoint snapshot exceeds the counter block");
+static_assert(kWfAdjBucket0 + kMaxPathLen < kWfCounts, "adjoint buckets exceed the counter block");
 struct WfBuffers {
   float4* slot;        // [N][4] path state
   int* hit;            // [N] closest-hit triangle of the current ray
@@ -198,7 +195,6 @@ struct WfBuffers {
   ShadowRec* shadow;   // [N] shadow queue of the current bounce
   uint32_t* adj;       // [17][N] chains for the adjoint pass, by path length
   uint32_t* counts;    // [kWfCounts]
-  uint8_t* done;       // [N] bounce whose shading ended the chain's path (0xff: not yet)
   float4* tape;        // [L][3][N]
 };
 size_t wf_bytes(unsigned long long N, int L);
@@ -229,20 +225,6 @@ struct WfTuning {
   int blocks_per_sm = 0;
   int refill = 16;
   int tail_bounce = 0;  // 0: every bounce as its own passes; k >= 1: one persistent pass from shading bounce k on
-  // 0: finish and adjoint after the last bounce; k >= 1: the paths that
-  // ended by the shading of bounce k are finished and differentiated on a
-  // second stream while the later bounces run (single scene, 4-wide walk,
-  // no tail pass)
-  int split_bounce = 0;
-  int side_blocks_per_sm = 0;  // grid of that adjoint pass (0: as for the whole queue)
-};
-// The second stream of a split step and its three events (fork after the
-// traversal that completes the early paths, early finish done, early
-// adjoint done), and the launch priority of the main stream's late passes.
-struct WfSide {
-  cudaStream_t stream = nullptr;
-  cudaEvent_t fork = nullptr, finish_a = nullptr, adjoint_a = nullptr;
-  int priority = 0;
 };
 // Sorting of the camera rays by pixel before the first traversal: the key
 // buffer (a.ray_keys), its ping-pong partner, the sort scratch and the
@@ -255,7 +237,7 @@ struct RayOrder {
 };
 int launch_wavefront_step(const StepArgs& a, const WfBuffers& w, bool stats, int n_sm, const WfTuning& tune,
                           const PhaseHook& hook, cudaStream_t s, WfMode mode = kWfStep, float* p_out = nullptr,
-                          const RayOrder& order = RayOrder{}, const WfSide* side = nullptr);
+                          const RayOrder& order = RayOrder{});
 // step index += 1 on the device (graph replay)
 void launch_advance_step(uint32_t* step, cudaStream_t s);
 

@@ -160,7 +160,6 @@ __global__ void __launch_bounds__(kWfThreads) wf_begin(StepArgs a, WfBuffers w) 
     }
     store_slot(w.slot, j, ps, pix);
     w.hit[j] = -1;
-    w.done[j] = 0xff;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) w.counts[1] = (uint32_t)a.N;  // bounce 1: every chain
 }
@@ -385,8 +384,6 @@ __global__ void __launch_bounds__(kWfThreads, kWfShadeMinBlocks) wf_shade(StepAr
     if (next) {
       qn[ni] = (uint32_t)j;
       w.hit[j] = -1;
-    } else if (t < n) {
-      w.done[j] = (uint8_t)k;  // the path ends here (its shadow ray, if any, is traced next)
     }
   }
 }
@@ -573,11 +570,8 @@ __global__ void __launch_bounds__(kWfThreads, kWfTraceMinBlocks) wf_shadow(StepA
 // Accumulate: the kill clock, the state written back and the splat record
 // (mode kWfStep / kWfInitClock); the chains that survive go to the adjoint
 // queue (kWfStep).  kWfInitEval instead stores p and queues every chain.
-// part 0: every chain; in a split step, part 1 the chains whose path ended
-// by the shading of bounce split_k, part 2 the others.
 template <bool BATCH>
-__global__ void __launch_bounds__(kWfThreads) wf_finish(StepArgs a, WfBuffers w, int mode, float* p_out, int part,
-                                                        int split_k) {
+__global__ void __launch_bounds__(kWfThreads) wf_finish(StepArgs a, WfBuffers w, int mode, float* p_out) {
   const unsigned long long n_iter = (a.N + (unsigned long long)gridDim.x * blockDim.x - 1) /
                                     ((unsigned long long)gridDim.x * blockDim.x);
   uint32_t err = 0;
@@ -587,7 +581,7 @@ __global__ void __launch_bounds__(kWfThreads) wf_finish(StepArgs a, WfBuffers w,
     bool survive = false;
     int nseg = 0;
     int kill_sid = -1;  // batch: the scene of a chain killed here
-    if (j < a.N && (part == 0 || ((int)w.done[j] <= split_k) == (part == 1))) {
+    if (j < a.N) {
       PathState ps;
       int pix;
       load_slot(w.slot, j, ps, pix);
@@ -645,21 +639,15 @@ __global__ void __launch_bounds__(kWfThreads) wf_finish(StepArgs a, WfBuffers w,
   if (err) atomicOr(a.err, err);
 }
 
-// The adjoint of the chains queued in bucket b at positions [lo[b], hi[b])
-// (lo null: from 0); hi is the bucket counters, or their snapshot.
 template <bool BATCH, bool COND>
-__global__ void __launch_bounds__(kWfThreads, 4)
-    wf_adjoint(StepArgs a, WfBuffers w, const uint32_t* lo, const uint32_t* hi) {
+__global__ void __launch_bounds__(kWfThreads, 4) wf_adjoint(StepArgs a, WfBuffers w) {
   // the queue is the concatenation of the path-length buckets, longest first
   __shared__ uint32_t off[kMaxPathLen + 2];
-  __shared__ uint32_t shift[kMaxPathLen + 1];  // queue position t of bucket b is entry t + shift[b] (mod 2^32)
   if (threadIdx.x == 0) {
     uint32_t acc = 0;
     for (int b = kMaxPathLen; b >= 0; --b) {
       off[b + 1] = acc;
-      const uint32_t l = lo ? lo[b] : 0u, h = hi[b];
-      shift[b] = l - acc;
-      acc += h > l ? h - l : 0u;
+      acc += w.counts[kWfAdjBucket0 + b];
     }
     off[0] = acc;  // total
   }
@@ -668,9 +656,8 @@ __global__ void __launch_bounds__(kWfThreads, 4)
   for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
     int b = kMaxPathLen;
     while (b > 0 && t >= off[b]) --b;  // bucket b holds positions [off[b + 1], off[b])
-    const uint32_t pos = t + shift[b];
-    const unsigned long long j = w.adj[(size_t)b * a.N + min((unsigned long long)pos, a.N - 1)];  // read in bounds
-    if (j >= a.N || pos >= a.N) {
+    const unsigned long long j = w.adj[(size_t)b * a.N + (t - off[b + 1])];
+    if (j >= a.N || t - off[b + 1] >= a.N) {
       atomicOr(a.err, kErrBadIndex);
       continue;
     }
@@ -682,30 +669,6 @@ __global__ void __launch_bounds__(kWfThreads, 4)
     path_adjoint<COND>(scene_of<BATCH>(a, v.sid), XSoA{a.x, a.N, j}, v.L, p, GlobalTape{w.tape, a.N, j}, ps.nseg,
                  GSoA{a.score, a.N, j});
   }
-}
-
-// A launch at the given stream priority (cudaLaunchAttributePriority; hp
-// false: the stream's own).  The late passes of a split step take a higher
-// priority than the second stream's work, so that their few blocks are
-// placed first whenever both wait for room on an SM.
-template <typename... KArgs, typename... Args>
-void launch_at(void (*kernel)(KArgs...), unsigned grid, size_t smem, cudaStream_t s, bool hp, int priority,
-               Args... args) {
-  if (!hp) {
-    kernel<<<grid, kWfThreads, smem, s>>>(args...);
-    return;
-  }
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(kWfThreads);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributePriority;
-  at[0].val.priority = priority;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
 unsigned grid_for(unsigned long long n, int max_blocks) {
@@ -738,13 +701,12 @@ int tail_blocks_per_sm(size_t smem) {
 
 template <bool BATCH, bool COND, int WIDTH>
 int launch_wf(const StepArgs& a, const WfBuffers& w, bool stats, int n_sm, const WfTuning& tune,
-              const PhaseHook& hook, cudaStream_t s, WfMode mode, float* p_out, const RayOrder& order,
-              const WfSide* side) {
+              const PhaseHook& hook, cudaStream_t s, WfMode mode, float* p_out, const RayOrder& order) {
   const int max_blocks = n_sm * 16;
   const unsigned g = grid_for(a.N, max_blocks);
   if (mode == kWfInitClock) {
     hook(kPhFinish, true);
-    wf_finish<BATCH><<<g, kWfThreads, 0, s>>>(a, w, mode, p_out, 0, 0);
+    wf_finish<BATCH><<<g, kWfThreads, 0, s>>>(a, w, mode, p_out);
     hook(kPhFinish, false);
     return 1;
   }
@@ -754,17 +716,6 @@ int launch_wf(const StepArgs& a, const WfBuffers& w, bool stats, int n_sm, const
   const int resident = traverse_blocks_per_sm<BATCH, WIDTH>(smem);
   const int per_sm = tune.blocks_per_sm > 0 ? std::min(tune.blocks_per_sm, resident) : resident;
   const unsigned g4 = (unsigned)(n_sm * per_sm);
-  // split step: once the traversal of bounce K + 1 (K = split_bounce) has
-  // run, every path that ended by the shading of bounce K is complete (its
-  // last shadow ray was in that pass), so its chain is finished and
-  // differentiated on the second stream while the later bounces run here.
-  // Each chain's results are those of the unsplit step; the adjoint queue
-  // holds the early chains first (their counts are snapshotted) and the
-  // late ones after them.
-  const int K = tune.split_bounce;
-  const bool split = side && side->stream && mode == kWfStep && wide && !BATCH && tune.tail_bounce == 0 && K >= 1 &&
-                     K < a.L;
-  bool forked = false;
   int launches = 0;
   cudaMemsetAsync(w.counts, 0, kWfCounts * sizeof(uint32_t), s);
   hook(kPhBegin, true);
@@ -785,25 +736,11 @@ int launch_wf(const StepArgs& a, const WfBuffers& w, bool stats, int n_sm, const
     // traverse(k) = closest-hit rays of bounce k + shadow rays of bounce
     // k - 1; the last launch (k = L + 1) carries the final shadow rays
     for (int k = 1; k <= a.L + 1; ++k) {
-      const int prio = forked ? side->priority : 0;
       hook(k <= a.L ? kPhTrace : kPhShadow, true, k <= a.L ? k : a.L);
-      if (stats) launch_at(wf_traverse<true, BATCH, WIDTH>, g4, smem, s, forked, prio, a, w, k);
-      else launch_at(wf_traverse<false, BATCH, WIDTH>, g4, smem, s, forked, prio, a, w, k);
+      if (stats) wf_traverse<true, BATCH, WIDTH><<<g4, kWfThreads, smem, s>>>(a, w, k);
+      else wf_traverse<false, BATCH, WIDTH><<<g4, kWfThreads, smem, s>>>(a, w, k);
       hook(k <= a.L ? kPhTrace : kPhShadow, false, k <= a.L ? k : a.L);
       launches += 1;
-      if (split && k == K + 1) {
-        cudaEventRecord(side->fork, s);
-        cudaStreamWaitEvent(side->stream, side->fork, 0);
-        wf_finish<BATCH><<<g, kWfThreads, 0, side->stream>>>(a, w, mode, p_out, 1, K);
-        cudaMemcpyAsync(w.counts + kWfAdjSnap0, w.counts + kWfAdjBucket0, (kMaxPathLen + 1) * sizeof(uint32_t),
-                        cudaMemcpyDeviceToDevice, side->stream);
-        cudaEventRecord(side->finish_a, side->stream);
-        const unsigned ga = tune.side_blocks_per_sm > 0 ? (unsigned)(n_sm * tune.side_blocks_per_sm) : g;
-        wf_adjoint<BATCH, COND><<<ga, kWfThreads, 0, side->stream>>>(a, w, nullptr, w.counts + kWfAdjSnap0);
-        cudaEventRecord(side->adjoint_a, side->stream);
-        launches += 3;
-        forked = true;
-      }
       if (k <= a.L && k == tune.tail_bounce) {
         // the rest of every path in one persistent pass
         hook(kPhTail, true, k);
@@ -816,7 +753,7 @@ int launch_wf(const StepArgs& a, const WfBuffers& w, bool stats, int n_sm, const
       }
       if (k <= a.L) {
         hook(kPhShade, true, k);
-        launch_at(wf_shade<BATCH, COND>, g, 0, s, forked, forked ? side->priority : 0, a, w, k);
+        wf_shade<BATCH, COND><<<g, kWfThreads, 0, s>>>(a, w, k);
         hook(kPhShade, false, k);
         launches += 1;
       }
@@ -837,24 +774,11 @@ int launch_wf(const StepArgs& a, const WfBuffers& w, bool stats, int n_sm, const
       launches += 3;
     }
   }
-  if (forked) {
-    // the late chains, queued after the early ones; the step ends when
-    // the second stream's adjoint has run too
-    cudaStreamWaitEvent(s, side->finish_a, 0);
-    hook(kPhFinish, true);
-    wf_finish<BATCH><<<g, kWfThreads, 0, s>>>(a, w, mode, p_out, 2, K);
-    hook(kPhFinish, false);
-    hook(kPhAdjoint, true);
-    wf_adjoint<BATCH, COND><<<g, kWfThreads, 0, s>>>(a, w, w.counts + kWfAdjSnap0, w.counts + kWfAdjBucket0);
-    hook(kPhAdjoint, false);
-    cudaStreamWaitEvent(s, side->adjoint_a, 0);
-    return launches + 2;
-  }
   hook(kPhFinish, true);
-  wf_finish<BATCH><<<g, kWfThreads, 0, s>>>(a, w, mode, p_out, 0, 0);
+  wf_finish<BATCH><<<g, kWfThreads, 0, s>>>(a, w, mode, p_out);
   hook(kPhFinish, false);
   hook(kPhAdjoint, true);
-  wf_adjoint<BATCH, COND><<<g, kWfThreads, 0, s>>>(a, w, nullptr, w.counts + kWfAdjBucket0);
+  wf_adjoint<BATCH, COND><<<g, kWfThreads, 0, s>>>(a, w);
   hook(kPhAdjoint, false);
   return launches + 2;
 }
@@ -864,7 +788,7 @@ int launch_wf(const StepArgs& a, const WfBuffers& w, bool stats, int n_sm, const
 size_t wf_bytes(unsigned long long N, int L) {
   auto a = [](size_t b) { return (b + 255) & ~(size_t)255; };
   return a(N * 64) + a(N * 4) + 2 * a(N * 4) + a(N * sizeof(ShadowRec)) + a((size_t)(kMaxPathLen + 1) * N * 4) +
-         a(kWfCounts * 4) + a(N) + a((size_t)L * 3 * N * 16);
+         a(kWfCounts * 4) + a((size_t)L * 3 * N * 16);
 }
 
 WfBuffers wf_carve(void* base, unsigned long long N, int L) {
@@ -878,14 +802,12 @@ WfBuffers wf_carve(void* base, unsigned long long N, int L) {
   w.shadow = reinterpret_cast<ShadowRec*>(p); p += a(N * sizeof(ShadowRec));
   w.adj = reinterpret_cast<uint32_t*>(p); p += a((size_t)(kMaxPathLen + 1) * N * 4);
   w.counts = reinterpret_cast<uint32_t*>(p); p += a(kWfCounts * 4);
-  w.done = reinterpret_cast<uint8_t*>(p); p += a(N);
   w.tape = reinterpret_cast<float4*>(p);
   return w;
 }
 
 int launch_wavefront_step(const StepArgs& a, const WfBuffers& w, bool stats, int n_sm, const WfTuning& tune,
-                          const PhaseHook& hook, cudaStream_t s, WfMode mode, float* p_out, const RayOrder& order,
-                          const WfSide* side) {
+                          const PhaseHook& hook, cudaStream_t s, WfMode mode, float* p_out, const RayOrder& order) {
   if (a.N == 0) return 0;
   StepArgs b = a;
   b.ray_keys = order.keys;
@@ -894,21 +816,21 @@ int launch_wavefront_step(const StepArgs& a, const WfBuffers& w, bool stats, int
   // the persistent passes walk the two-level or the 8-wide BVH where the
   // scene selects it
   if (a.two_level && !a.scenes) {
-    if (a.conductors) return launch_wf<false, true, kWalkTwoLevel>(b, w, stats, n_sm, tune, hook, s, mode, p_out, order, side);
-    return launch_wf<false, false, kWalkTwoLevel>(b, w, stats, n_sm, tune, hook, s, mode, p_out, order, side);
+    if (a.conductors) return launch_wf<false, true, kWalkTwoLevel>(b, w, stats, n_sm, tune, hook, s, mode, p_out, order);
+    return launch_wf<false, false, kWalkTwoLevel>(b, w, stats, n_sm, tune, hook, s, mode, p_out, order);
   }
   if (a.bvh8) {
     if (a.conductors)
-      return a.scenes ? launch_wf<true, true, 8>(b, w, stats, n_sm, tune, hook, s, mode, p_out, order, side)
-                      : launch_wf<false, true, 8>(b, w, stats, n_sm, tune, hook, s, mode, p_out, order, side);
-    return a.scenes ? launch_wf<true, false, 8>(b, w, stats, n_sm, tune, hook, s, mode, p_out, order, side)
-                    : launch_wf<false, false, 8>(b, w, stats, n_sm, tune, hook, s, mode, p_out, order, side);
+      return a.scenes ? launch_wf<true, true, 8>(b, w, stats, n_sm, tune, hook, s, mode, p_out, order)
+                      : launch_wf<false, true, 8>(b, w, stats, n_sm, tune, hook, s, mode, p_out, order);
+    return a.scenes ? launch_wf<true, false, 8>(b, w, stats, n_sm, tune, hook, s, mode, p_out, order)
+                    : launch_wf<false, false, 8>(b, w, stats, n_sm, tune, hook, s, mode, p_out, order);
   }
   if (a.conductors)
-    return a.scenes ? launch_wf<true, true, 4>(b, w, stats, n_sm, tune, hook, s, mode, p_out, order, side)
-                    : launch_wf<false, true, 4>(b, w, stats, n_sm, tune, hook, s, mode, p_out, order, side);
-  return a.scenes ? launch_wf<true, false, 4>(b, w, stats, n_sm, tune, hook, s, mode, p_out, order, side)
-                  : launch_wf<false, false, 4>(b, w, stats, n_sm, tune, hook, s, mode, p_out, order, side);
+    return a.scenes ? launch_wf<true, true, 4>(b, w, stats, n_sm, tune, hook, s, mode, p_out, order)
+                    : launch_wf<false, true, 4>(b, w, stats, n_sm, tune, hook, s, mode, p_out, order);
+  return a.scenes ? launch_wf<true, false, 4>(b, w, stats, n_sm, tune, hook, s, mode, p_out, order)
+                  : launch_wf<false, false, 4>(b, w, stats, n_sm, tune, hook, s, mode, p_out, order);
 }
 
 }  // namespace dr

@@ -73,16 +73,13 @@ class Renderer:
     def set_option(self, option, value):
         """option: "wavefront" (-1 auto / 0 / 1), "work_order" (0/1), "profile" (0/1) or
         "bvh_width" (0 automatic / 2 / 4 / 8; 8 before the upload), "traverse_blocks" (0 = all resident),
-        "refill" (1..32), "ray_order" (-1 automatic / 0 / 1), "tail_bounce" (-1 automatic, 0 off, k),
-        "two_level" (1: walk an instanced scene's two-level BVH, 0: its flattened BVH), "split_bounce"
-        (-1 automatic, 0 off, k: finish and differentiate the paths ended by bounce k on a second stream
-        while the later bounces run) or "side_blocks" (blocks per SM of that second-stream adjoint)."""
+        "refill" (1..32), "ray_order" (-1 automatic / 0 / 1), "tail_bounce" (-1 automatic, 0 off, k) or
+        "two_level" (1: walk an instanced scene's two-level BVH, 0: its flattened BVH)."""
         code = {"work_order": _lib.DR_OPT_WORK_ORDER, "wavefront": _lib.DR_OPT_WAVEFRONT,
                 "profile": _lib.DR_OPT_PROFILE, "bvh_width": _lib.DR_OPT_BVH_WIDTH,
                 "traverse_blocks": _lib.DR_OPT_TRAVERSE_BLOCKS, "refill": _lib.DR_OPT_REFILL,
                 "ray_order": _lib.DR_OPT_RAY_ORDER, "tail_bounce": _lib.DR_OPT_TAIL_BOUNCE,
-                "two_level": _lib.DR_OPT_TWO_LEVEL, "split_bounce": _lib.DR_OPT_SPLIT_BOUNCE,
-                "side_blocks": _lib.DR_OPT_SIDE_BLOCKS}[option]
+                "two_level": _lib.DR_OPT_TWO_LEVEL}[option]
         call("dr_set_option", self.h, code, int(value))
 
     def set_bvh_builder(self, builder="ploc", radius=16):

@@ -939,50 +939,26 @@ def test_tail_pass_gives_the_same_chains(torch, R, tail):
     assert c_a["tour_count"] == c_b["tour_count"] and c_a["rays"] == c_b["rays"]
 
 
-@pytest.mark.parametrize("split,side_blocks", [(1, 0), (3, 2), (8, 0), (11, 1)])
-def test_split_step_gives_the_same_chains(torch, R, split, side_blocks):
-    """Finishing and differentiating the chains whose paths ended by bounce
-    `split` on a second stream while the later bounces run changes only
-    which thread handles which chain and when: identical chain states,
-    counters and images, in plain steps and in graph frames."""
-    scene, L = S.procedural_scene(1, 64, 36, target_tris=60000, n_objects=40), 12
-    out = []
-    for sb, graph in ((0, False), (split, False), (split, True)):
-        s = torch.cuda.Stream()
-        r = R.Renderer(0, s)
-        r.set_option("wavefront", 1)
-        r.set_option("tail_bounce", 0)
-        r.set_option("split_bounce", sb)
-        r.set_option("side_blocks", side_blocks)
-        r.upload_scene(scene)
-        r.init_chains(16384, 37, R.make_params(L=L, drift="adjoint", k0=0.0, steps_per_splat=4))
-        for _ in range(2):
-            if graph:
-                r.frame(4)
-            else:
-                r.step(4)
-                r.splat()
-        s.synchronize()
-        out.append((r.readback_state(("x", "killed", "logp", "score")), r.readback_accum(), r.counters()))
-        r.close()
-    (a, acc_a, c_a) = out[0]
-    for b, acc_b, c_b in out[1:]:
-        for key in ("x", "killed", "logp", "score"):
-            assert np.array_equal(a[key], b[key]), key
-        assert np.array_equal(acc_a, acc_b)
-        assert c_a["tour_count"] == c_b["tour_count"] and c_a["rays"] == c_b["rays"]
-    assert c_a["tour_count"] > 0 and np.abs(a["score"]).max() > 0
-
-
-def test_split_bounce_option_is_checked(torch, R):
-    from paper_2605_08916_gb300 import _lib
+def test_bounce_rays_count_the_traced_rays(torch, R):
+    """The profile's rays per bounce: every chain's camera ray at bounce 1,
+    and closest-hit plus shadow rays over all bounces equal the rays the
+    traversal passes counted."""
+    scene, L, N = S.procedural_scene(2, 64, 36, target_tris=20000, n_objects=20), 8, 8192
     r = R.Renderer()
-    for bad in (-2, 17):
-        with pytest.raises(_lib.DRError):
-            r.set_option("split_bounce", bad)
-    with pytest.raises(_lib.DRError):
-        r.set_option("side_blocks", 17)
+    r.set_option("wavefront", 1)
+    r.upload_scene(scene)
+    r.init_chains(N, 3, R.make_params(L=L, drift="adjoint", k0=0.0, steps_per_splat=4))
+    r.set_option("profile", 1)
+    r.profile()
+    c0 = r.counters()["rays"]
+    r.step(2)
+    c1 = r.counters()["rays"]
+    bp = r.bounce_profile(L)
+    r.profile()
     r.close()
+    assert bp["rays"][0] == 2 * N
+    assert all(x >= y for x, y in zip(bp["rays"], bp["rays"][1:]))
+    assert sum(bp["rays"]) + sum(bp["shadow_rays"]) == c1 - c0
 
 
 @pytest.mark.parametrize("chains", [8192, 1 << 17])
