@@ -40,31 +40,44 @@ __global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(const R* __res
   hist[(size_t)threadIdx.x * ntiles + blockIdx.x] = cnt[threadIdx.x];
 }
 
+// Stable scatter of one 8-bit digit pass.  Each block ranks its tile of
+// kSortTile elements (rounds of 256: warp match-any ranks equal digits, a
+// per-digit prefix over the warps orders the warps), places the tile in
+// shared memory in (digit, input) order, and then writes it out in that
+// order: the elements of one digit leave the block as one contiguous run, so
+// the global stores are coalesced.  The output is the same stable
+// permutation as placing each element directly.
 template <class R>
 __global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(const R* __restrict__ in, R* __restrict__ out,
                                                                      size_t n, int shift,
                                                                      const uint32_t* __restrict__ offs, int ntiles) {
-  __shared__ uint32_t run[256];
+  __shared__ uint32_t run[256];     // elements of each digit ranked so far in this tile
   __shared__ uint32_t whist[kSortThreads / 32][256];
+  __shared__ uint32_t dstart[256];  // first position of each digit in the staged tile
+  __shared__ uint32_t gbase[256];   // where this tile's run of each digit goes
+  __shared__ uint32_t wsum[kSortThreads / 32];
+  __shared__ R stage[kSortTile];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  run[threadIdx.x] = offs[(size_t)threadIdx.x * ntiles + blockIdx.x];
+  run[threadIdx.x] = 0;
+  gbase[threadIdx.x] = offs[(size_t)threadIdx.x * ntiles + blockIdx.x];
   const size_t base = (size_t)blockIdx.x * kSortTile;
   const uint32_t lt_mask = (1u << lane) - 1u;
+  R v[kSortItems];
+  uint32_t dg[kSortItems], pos[kSortItems];
+#pragma unroll
   for (int r = 0; r < kSortItems; ++r) {
     const size_t i = base + (size_t)r * kSortThreads + threadIdx.x;
-    const bool valid = i < n;
-    R v;
-    uint32_t digit = 256;
-    if (valid) {
-      v = in[i];
-      digit = (rec_key(v) >> shift) & 255u;
+    dg[r] = 256;
+    if (i < n) {
+      v[r] = in[i];
+      dg[r] = (rec_key(v[r]) >> shift) & 255u;
     }
 #pragma unroll
     for (int w = 0; w < kSortThreads / 32; ++w) whist[w][threadIdx.x] = 0;
     __syncthreads();
-    const uint32_t peers = __match_any_sync(0xffffffffu, digit);
+    const uint32_t peers = __match_any_sync(0xffffffffu, dg[r]);
     const uint32_t rank = __popc(peers & lt_mask);
-    if (valid && lane == __ffs(peers) - 1) whist[warp][digit] = __popc(peers);
+    if (dg[r] < 256 && lane == __ffs(peers) - 1) whist[warp][dg[r]] = __popc(peers);
     __syncthreads();
     {
       uint32_t acc = run[threadIdx.x];
@@ -77,8 +90,35 @@ __global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(const R* __
       run[threadIdx.x] = acc;
     }
     __syncthreads();
-    if (valid) out[whist[warp][digit] + rank] = v;
+    pos[r] = dg[r] < 256 ? whist[warp][dg[r]] + rank : 0u;
     __syncthreads();
+  }
+  // dstart = exclusive prefix of the tile's digit counts
+  {
+    const uint32_t c = run[threadIdx.x];
+    uint32_t x = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    uint32_t before = 0;
+    for (int w = 0; w < warp; ++w) before += wsum[w];
+    dstart[threadIdx.x] = before + x - c;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < kSortItems; ++r)
+    if (dg[r] < 256) stage[dstart[dg[r]] + pos[r]] = v[r];
+  __syncthreads();
+  const size_t left = n - base;
+  const int cnt = left < (size_t)kSortTile ? (int)left : kSortTile;
+  for (int q = threadIdx.x; q < cnt; q += kSortThreads) {
+    const R e = stage[q];
+    const uint32_t d = (rec_key(e) >> shift) & 255u;
+    out[gbase[d] + ((uint32_t)q - dstart[d])] = e;
   }
 }
 
