@@ -317,6 +317,16 @@ int dr_lstar_over_p(dr_ctx* ctx, const dr_params* prm, const float* y, int64_t M
  * Errors: INVALID_ARG (NULL pointer, n < 0), STATE (no single scene), CUDA. */
 int dr_trace_closest(dr_ctx* ctx, const float* rays, int64_t n, int32_t exclude, int32_t* tri, float* t);
 
+/* dr_trace_closest with each ray's walk counted: node_steps [n] the inner
+ * nodes the walk visited and tri_tests [n] the triangles it tested (DEVICE
+ * uint32), the per-ray terms of the traversal statistics that give the
+ * roofline's algorithmic bytes (112 B per 4-wide node visit, 48 B per
+ * triangle test).  The walk is the one the persistent passes take (the
+ * 4-wide BVH when built).  Asynchronous.
+ * Errors: INVALID_ARG, STATE (no single scene), CUDA. */
+int dr_trace_closest_counted(dr_ctx* ctx, const float* rays, int64_t n, int32_t exclude, int32_t* tri, float* t,
+                             uint32_t* node_steps, uint32_t* tri_tests);
+
 /* Philox4x32-10 (Salmon et al. 2011, cited in Sec. 4.3) on DEVICE buffers:
  * ctr [n * 4], key [n * 2] -> out [n * 4].  cuda_stream may be NULL.
  * Asynchronous. */
@@ -371,6 +381,17 @@ int dr_bvh_info(dr_ctx* ctx, int32_t* n_nodes, int32_t* n_tris, int32_t* max_dep
  * one-triangle scene, or a tree whose traversal would need more stack than
  * the kernels hold; rays then use the binary BVH). */
 int dr_bvh4_info(dr_ctx* ctx, int32_t* n_nodes, int32_t* max_depth, int32_t* stack_need);
+
+/* Copies the 4-wide BVH to HOST buffers, for tools that walk it on the
+ * host.  nodes [n_nodes * 28] floats (dr_bvh4_info's count): per node the
+ * children's box planes as six groups of four (lo x, hi x, lo y, hi y,
+ * lo z, hi z; slot k in entry k of each group), then four int32 links: an
+ * inner child's node index (>= 0), a leaf (bit 31 set; first triangle =
+ * (link & 0x7fffffff) >> 3, count = (link & 7) + 1), or 0x7fffffff (empty).
+ * tris [n_tris * 12] floats: per triangle in leaf order v0 and the int32
+ * original id, e1 = v1 - v0 and 0, e2 = v2 - v0 and 0.  Synchronises.
+ * Errors: INVALID_ARG, STATE (no single scene or no 4-wide BVH), CUDA. */
+int dr_bvh4_download(dr_ctx* ctx, float* nodes, float* tris);
 
 /* Quality of the 4-wide BVH by the surface-area heuristic (the measure its
  * leaf decision minimises): for a ray that hits the root box, with each

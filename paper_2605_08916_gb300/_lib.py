@@ -28,7 +28,7 @@ EXPORTS = ["dr_version", "dr_last_error", "dr_create", "dr_destroy", "dr_scene_u
            "dr_get_counters", "dr_eval_logp", "dr_trace_closest", "dr_philox", "dr_splat_records",
            "dr_clear_image", "dr_state_save", "dr_state_load", "dr_set_stats", "dr_get_traversal_stats",
            "dr_bvh_info", "dr_get_launch_count", "dr_get_chain_shape", "dr_pt_render", "dr_set_bvh_builder",
-           "dr_splat_records_noalloc", "dr_set_option", "dr_get_profile", "dr_frame", "dr_bvh4_info", "dr_bvh4_sah", "dr_bvh8_info", "dr_get_bounce_profile", "dr_get_bounce_rays",
+           "dr_splat_records_noalloc", "dr_set_option", "dr_get_profile", "dr_frame", "dr_bvh4_info", "dr_bvh4_sah", "dr_bvh8_info", "dr_get_bounce_profile", "dr_get_bounce_rays", "dr_trace_closest_counted", "dr_bvh4_download",
            "dr_scenes_upload_batch", "dr_resolve_scene", "dr_get_scene_counters", "dr_scene_upload_instanced",
            "dr_two_level_info", "dr_splat_records_noalloc_status", "dr_resolve_accum", "dr_get_p_sum",
            "dr_k0_from_p_sum", "dr_lstar_over_p"]
@@ -91,6 +91,8 @@ def signatures():
         "dr_get_counters": ([P, P, P, P, P, P], C.c_int),
         "dr_eval_logp": ([P, I32, P, I64, P, P, P, P], C.c_int),
         "dr_trace_closest": ([P, P, I64, I32, P, P], C.c_int),
+        "dr_trace_closest_counted": ([P, P, I64, I32, P, P, P, P], C.c_int),
+        "dr_bvh4_download": ([P, P, P], C.c_int),
         "dr_philox": ([P, P, P, I64, P], C.c_int),
         "dr_splat_records": ([P, P, I64], C.c_int),
         "dr_clear_image": ([P], C.c_int),

@@ -1746,6 +1746,30 @@ int dr_trace_closest(dr_ctx* c, const float* rays, int64_t n, int32_t exclude, i
   return check_launch("trace_closest");
 }
 
+int dr_trace_closest_counted(dr_ctx* c, const float* rays, int64_t n, int32_t exclude, int32_t* tri, float* t,
+                             uint32_t* node_steps, uint32_t* tri_tests) {
+  if (!c || !rays || !tri || !t || !node_steps || !tri_tests)
+    return fail(DR_ERR_INVALID_ARG, "dr_trace_closest_counted: NULL argument");
+  if (n < 0) return fail(DR_ERR_INVALID_ARG, "dr_trace_closest_counted: n < 0");
+  if (c->target != 0) return fail(DR_ERR_STATE, "dr_trace_closest_counted: no scene");
+  DR_CUDA(cudaSetDevice(c->device));
+  launch_trace_stats(dev_scene(c), rays, n, exclude, tri, t, node_steps, tri_tests, c->err, c->stream);
+  return check_launch("trace_closest_counted");
+}
+
+int dr_bvh4_download(dr_ctx* c, float* nodes, float* tris) {
+  if (!c || !nodes || !tris) return fail(DR_ERR_INVALID_ARG, "dr_bvh4_download: NULL argument");
+  if (c->target != 0) return fail(DR_ERR_STATE, "dr_bvh4_download: no scene");
+  if (!c->nodes4) return fail(DR_ERR_STATE, "dr_bvh4_download: the scene has no 4-wide BVH");
+  DR_CUDA(cudaSetDevice(c->device));
+  DR_CUDA(cudaMemcpyAsync(nodes, c->nodes4, (size_t)c->n_nodes4 * kNode4F4 * sizeof(float4), cudaMemcpyDeviceToHost,
+                          c->stream));
+  DR_CUDA(cudaMemcpyAsync(tris, c->tris4, (size_t)c->nt * kTriF4 * sizeof(float4), cudaMemcpyDeviceToHost,
+                          c->stream));
+  DR_CUDA(cudaStreamSynchronize(c->stream));
+  return DR_OK;
+}
+
 int dr_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int64_t n, void* stream) {
   if (!ctr || !key || !out || n < 0) return fail(DR_ERR_INVALID_ARG, "dr_philox: bad argument");
   launch_philox(ctr, key, out, n, static_cast<cudaStream_t>(stream));

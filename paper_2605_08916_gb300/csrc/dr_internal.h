@@ -289,6 +289,9 @@ void launch_lstar(const LstarArgs& a, cudaStream_t s);
 
 void launch_trace(const DevScene& S, const float* rays, long long n, int exclude, int* tri, float* t, uint32_t* err,
                   cudaStream_t s);
+// launch_trace with each ray's node steps and triangle tests counted
+void launch_trace_stats(const DevScene& S, const float* rays, long long n, int exclude, int* tri, float* t,
+                        uint32_t* nodes, uint32_t* tests, uint32_t* err, cudaStream_t s);
 void launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, long long n, cudaStream_t s);
 void launch_sum_doubles(const double* in, int n, double* out, cudaStream_t s);
 // partial[b] = FP64 sum of p over the fused step kernel's block b, in its order

@@ -340,6 +340,32 @@ __global__ void __launch_bounds__(kStepThreads) trace_kernel(DevScene S, const f
   if (err) atomicOr(errp, err);
 }
 
+// The same queries with each ray's walk counted: node steps (inner nodes
+// visited) and triangle tests, the quantities the statistics pass sums.
+template <int STACK>
+__global__ void __launch_bounds__(kStepThreads) trace_stats_kernel(DevScene S, const float* __restrict__ rays,
+                                                                   long long n, int exclude, int* __restrict__ tri,
+                                                                   float* __restrict__ t, uint32_t* __restrict__ nodes,
+                                                                   uint32_t* __restrict__ tests, uint32_t* errp) {
+  extern __shared__ int smem[];
+  TraceStack<STACK> st{smem + threadIdx.x, (int)blockDim.x};
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float* r = rays + 6 * i;
+  uint32_t err = 0;
+  float th;
+  TraceStats stats{0u, 0u};
+  const Ray ray = make_ray(f3(r[0], r[1], r[2]), f3(r[3], r[4], r[5]));
+  const int h = S.tl_nodes ? trace_closest<STACK, true, kWalkTwoLevel>(S, ray, exclude, &th, st, &err, &stats)
+                : S.nodes8 ? trace_closest<STACK, true, 8>(S, ray, exclude, &th, st, &err, &stats)
+                           : trace_closest<STACK, true>(S, ray, exclude, &th, st, &err, &stats);
+  tri[i] = h;
+  t[i] = h >= 0 ? th : __int_as_float(0x7f800000);
+  nodes[i] = stats.nodes;
+  tests[i] = stats.tris;
+  if (err) atomicOr(errp, err);
+}
+
 __global__ void philox_kernel(const uint32_t* __restrict__ ctr, const uint32_t* __restrict__ key,
                               uint32_t* __restrict__ out, long long n) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -472,6 +498,19 @@ void launch_trace(const DevScene& S, const float* rays, long long n, int exclude
         S, rays, n, exclude, tri, t, err);
   else
     trace_kernel<kStack><<<g, kStepThreads, step_smem_bytes(), s>>>(S, rays, n, exclude, tri, t, err);
+}
+
+void launch_trace_stats(const DevScene& S, const float* rays, long long n, int exclude, int* tri, float* t,
+                        uint32_t* nodes, uint32_t* tests, uint32_t* err, cudaStream_t s) {
+  if (n <= 0) return;
+  const unsigned g = (unsigned)((n + kStepThreads - 1) / kStepThreads);
+  if (S.tl_nodes)
+    trace_stats_kernel<kTraversalStackTL>
+        <<<g, kStepThreads, (size_t)kTraversalStackTL * kStepThreads * sizeof(int), s>>>(S, rays, n, exclude, tri, t,
+                                                                                         nodes, tests, err);
+  else
+    trace_stats_kernel<kStack><<<g, kStepThreads, step_smem_bytes(), s>>>(S, rays, n, exclude, tri, t, nodes, tests,
+                                                                           err);
 }
 
 void launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, long long n, cudaStream_t s) {

@@ -362,6 +362,29 @@ class Renderer:
         call("dr_trace_closest", self.h, _ptr(rays), int(n), int(exclude), _ptr(tri), _ptr(t))
         return tri, t
 
+    def trace_closest_counted(self, rays, exclude=-1):
+        """trace_closest plus each ray's node steps and triangle tests."""
+        rays = rays.contiguous()
+        n = rays.shape[0]
+        tri = torch.empty(n, dtype=torch.int32, device=rays.device)
+        t = torch.empty(n, dtype=torch.float32, device=rays.device)
+        nodes = torch.empty(n, dtype=torch.int32, device=rays.device)
+        tests = torch.empty(n, dtype=torch.int32, device=rays.device)
+        call("dr_trace_closest_counted", self.h, _ptr(rays), int(n), int(exclude), _ptr(tri), _ptr(t), _ptr(nodes),
+             _ptr(tests))
+        return tri, t, nodes, tests
+
+    def bvh4_download(self):
+        """The 4-wide BVH on the host: nodes float32 [n, 28] and triangles
+        float32 [n_tris, 12] (layouts in the C header)."""
+        import numpy as np
+        n4 = self.bvh4_info()["n_nodes"]
+        nt = self.bvh_info()["n_tris"]
+        nodes = np.empty((n4, 28), np.float32)
+        tris = np.empty((nt, 12), np.float32)
+        call("dr_bvh4_download", self.h, nodes.ctypes.data, tris.ctypes.data)
+        return nodes, tris
+
     def splat_records(self, recs):
         """recs: CUDA tensor of 16-byte records viewed as int32 [M, 4] (pixel
         index, then float bits of r, g, b)."""

@@ -1400,3 +1400,150 @@ def test_instanced_upload_errors(torch, R):
     r.init_chains(64, 1, R.make_params(L=3, drift="adjoint", k0=100.0))
     r.step(2)
     r.close()
+
+
+# ---------------------------------------------------------------------------
+# Independent count of the traversal's work (the roofline's algorithmic
+# bytes are 112 B per node step and 48 B per triangle test, summed by the
+# library's statistics instantiation).  A host walker written from the
+# documented BVH layout and walk rules visits the downloaded 4-wide BVH:
+# hit children nearest first (ties by slot), the others pushed far-to-near,
+# leaves tested on the spot, boxes culled against the closest hit so far.
+
+_F = np.float32
+
+
+def _fma32(a, b, c):
+    # a * b is exact in float64 for float32 inputs; one rounding to float32
+    return _F(np.float64(a) * np.float64(b) + np.float64(c))
+
+
+def _cross32(a, b):
+    return [_F(a[1] * b[2] - a[2] * b[1]), _F(a[2] * b[0] - a[0] * b[2]), _F(a[0] * b[1] - a[1] * b[0])]
+
+
+def _dot32(a, b):
+    return _F(_F(a[0] * b[0]) + _F(a[1] * b[1]) + _F(a[2] * b[2]))
+
+
+def _tri_test32(v0, e1, e2, o, d, tmin, tmax):
+    p = _cross32(d, e2)
+    det = _dot32(e1, p)
+    if det == 0:
+        return None
+    sg = _F(-1.0) if det < 0 else _F(1.0)
+    adet = abs(det)
+    tv = [_F(o[i] - v0[i]) for i in range(3)]
+    du = _dot32(tv, p)
+    if du * sg < 0 or du * sg > adet:
+        return None
+    q = _cross32(tv, e1)
+    dv = _dot32(d, q)
+    if dv * sg < 0 or _F(du + dv) * sg > adet:
+        return None
+    inv = _F(1.0) / det
+    u = _F(du * inv)
+    if u < 0 or u > 1:
+        return None
+    v = _F(dv * inv)
+    if v < 0 or _F(u + v) > 1:
+        return None
+    t = _F(_dot32(e2, q) * inv)
+    return t if (t > tmin and t < tmax) else None
+
+
+def _walk4_counts(nodes, tris, links, tri_ids, o, d, tmin):
+    """Closest hit, node steps and triangle tests of one ray."""
+    o = [_F(x) for x in o]
+    d = [_F(x) for x in d]
+    inv = []
+    for v in d:
+        vv = v if abs(v) > _F(1e-20) else _F(np.copysign(_F(1e-20), v))
+        inv.append(_F(_F(1.0) / vv))
+    oinv = [_F(o[a] * inv[a]) for a in range(3)]
+    kM = _F(2.384185791015625e-07)
+    on = [_fma32(abs(oinv[a]), kM, oinv[a]) for a in range(3)]
+    of = [_fma32(-abs(oinv[a]), kM, oinv[a]) for a in range(3)]
+    sx = [1 if inv[a] < 0 else 0 for a in range(3)]
+    tbest, best = _F(np.inf), -1
+    stack, node, n_steps, n_tests = [], 0, 0, 0
+    while True:
+        if node < 0:
+            first, cnt = (node & 0x7fffffff) >> 3, (node & 7) + 1
+            tmax = _F(tbest * _F(1.0000001) + _F(1e-30))
+            for i in range(first, first + cnt):
+                n_tests += 1
+                rec = tris[i]
+                th = _tri_test32(rec[0:3], rec[4:7], rec[8:11], o, d, tmin, tmax)
+                tid = int(tri_ids[i])
+                if th is not None and (th < tbest or (th == tbest and tid < best)):
+                    tbest, best = th, tid
+            if not stack:
+                break
+            node = stack.pop()
+            continue
+        n_steps += 1
+        nb = nodes[node]
+        keys = []
+        for k in range(4):
+            tn = _F(0.0)
+            tf = tbest
+            for a in range(3):
+                near = nb[(2 * a + sx[a]) * 4 + k]
+                far = nb[(2 * a + 1 - sx[a]) * 4 + k]
+                tn = max(tn, _fma32(near, inv[a], -on[a]))
+                tf = min(tf, _fma32(far, inv[a], -of[a]))
+            e = tn if tn <= _F(tf * _F(1.0000002)) else _F(-1.0)
+            c = int(links[node, k])
+            if c != 0x7fffffff and e >= 0 and e <= tbest:
+                keys.append(((int(np.array(e, np.float32).view(np.uint32)) & ~3) | k, c))
+        if not keys:
+            if not stack:
+                break
+            node = stack.pop()
+            continue
+        keys.sort()
+        node = keys[0][1]
+        for _, c in reversed(keys[1:]):
+            stack.append(c)
+    return best, n_steps, n_tests
+
+
+def test_node_steps_match_an_independent_walk(torch, R):
+    scene = S.procedural_scene(3, 64, 36, target_tris=30000, n_objects=24)
+    r = R.Renderer()
+    r.upload_scene(scene)
+    nodes, tris = r.bvh4_download()
+    links = nodes[:, 24:28].view(np.int32)
+    tri_ids = tris[:, 3].view(np.int32)
+    lo, hi = scene.verts.min(0).astype(np.float64), scene.verts.max(0).astype(np.float64)
+    tmin = _F(1e-5 * float((hi - lo).max()))
+    rng = np.random.default_rng(4)
+    n = 1500
+    # rays leaving points on triangles (secondary-ray-like) and rays from
+    # inside the scene box, in uniformly random directions
+    k = rng.integers(0, scene.n_tris, n)
+    bu, bv = rng.random(n), rng.random(n)
+    flip = bu + bv > 1
+    bu[flip], bv[flip] = 1 - bu[flip], 1 - bv[flip]
+    v0, v1, v2 = (scene.verts[scene.tris[k, i]].astype(np.float64) for i in range(3))
+    nrm = np.cross(v1 - v0, v2 - v0)
+    nrm /= np.linalg.norm(nrm, axis=1, keepdims=True) + 1e-30
+    o = v0 + bu[:, None] * (v1 - v0) + bv[:, None] * (v2 - v0) + nrm * (2e-3 * float((hi - lo).max()))
+    o[n // 2:] = lo + rng.random((n - n // 2, 3)) * (hi - lo)
+    dr = rng.normal(size=(n, 3))
+    dr /= np.linalg.norm(dr, axis=1, keepdims=True)
+    rays = np.concatenate([o, dr], 1).astype(np.float32)
+    hit, _, steps, tests = r.trace_closest_counted(torch.from_numpy(rays).cuda())
+    hit, steps, tests = hit.cpu().numpy(), steps.cpu().numpy(), tests.cpu().numpy()
+    r.close()
+    ref = np.array([_walk4_counts(nodes, tris, links, tri_ids, rays[i, :3], rays[i, 3:], tmin) for i in range(n)])
+    same_hit = hit == ref[:, 0]
+    same_steps = (steps == ref[:, 1]) & (tests == ref[:, 2])
+    print(f"independent walk: hits {same_hit.mean():.4f}, per-ray counts {same_steps.mean():.4f}, "
+          f"node steps {steps.sum()} vs {ref[:, 1].sum()}, tests {tests.sum()} vs {ref[:, 2].sum()}")
+    assert (ref[:, 0] >= 0).mean() > 0.3 and steps.mean() > 5
+    assert same_hit.mean() >= 0.998
+    assert same_steps.mean() >= 0.99
+    assert abs(steps.sum() / ref[:, 1].sum() - 1) <= 0.005
+    assert abs(tests.sum() / ref[:, 2].sum() - 1) <= 0.005
