@@ -238,6 +238,26 @@ R* radix_sort(R* in, R* out, size_t n, int bits, void* scratch, cudaStream_t st)
   return src;
 }
 
+// A float's value as a double, built from its bits on the integer pipes
+// (the FP64 pipe is narrow on this GPU and the reduce is bound by it).
+// Exact: every float is a double.  Zero, subnormal, infinite and NaN inputs
+// take the hardware conversion.
+DR_D double float_to_double_bits(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t e = (u >> 23) & 0xffu;
+  if (e == 0u || e == 0xffu) return (double)f;
+  const unsigned long long bits = ((unsigned long long)(u >> 31) << 63) |
+                                  ((unsigned long long)(e + 896u) << 52) |  // exponent bias 1023 - 127
+                                  ((unsigned long long)(u & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)bits);
+}
+
+// r += v in FP64, skipping v == 0: adding a zero leaves an FP64 sum that
+// starts at +0 unchanged, so the result is the plain sequential sum's.
+DR_D void add_nonzero(double& r, float v) {
+  if (v != 0.0f) r += float_to_double_bits(v);
+}
+
 __global__ void segment_reduce_kernel(const SplatRec* __restrict__ s, size_t n, double* __restrict__ accum,
                                       uint32_t n_pix, uint32_t* err) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -252,9 +272,9 @@ __global__ void segment_reduce_kernel(const SplatRec* __restrict__ s, size_t n, 
   for (size_t k = i; k < n; ++k) {
     const SplatRec q = s[k];
     if (q.pix != pix) break;
-    r += (double)q.r;
-    g += (double)q.g;
-    b += (double)q.b;
+    add_nonzero(r, q.r);
+    add_nonzero(g, q.g);
+    add_nonzero(b, q.b);
   }
   accum[(size_t)pix * 3 + 0] += r;
   accum[(size_t)pix * 3 + 1] += g;
