@@ -387,7 +387,9 @@ int dr_bvh4_info(dr_ctx* ctx, int32_t* n_nodes, int32_t* max_depth, int32_t* sta
  * children's box planes as six groups of four (lo x, hi x, lo y, hi y,
  * lo z, hi z; slot k in entry k of each group), then four int32 links: an
  * inner child's node index (>= 0), a leaf (bit 31 set; first triangle =
- * (link & 0x7fffffff) >> 3, count = (link & 7) + 1), or 0x7fffffff (empty).
+ * (link & 0x7fffffff) >> 3, count = (link & 7) + 1), or 0x7fffffff (empty;
+ * an empty slot's box is inverted, lo = +inf and hi = -inf, so that every
+ * slab test misses it).
  * tris [n_tris * 12] floats: per triangle in leaf order v0 and the int32
  * original id, e1 = v1 - v0 and 0, e2 = v2 - v0 and 0.  Synchronises.
  * Errors: INVALID_ARG, STATE (no single scene or no 4-wide BVH), CUDA. */

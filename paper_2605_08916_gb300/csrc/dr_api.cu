@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <limits>
 #include <string>
 #include <thread>
 #include <vector>
@@ -768,9 +769,11 @@ int build_two_level(dr_ctx* c, const dr_mesh_desc* meshes, int nmesh, const dr_i
         hi[a] = std::max(v0[a], std::max(v1[a], v2[a]));
       }
       float4 nd[kNode4F4];
+      const float inf = std::numeric_limits<float>::infinity();
       for (int a = 0; a < 3; ++a) {
-        nd[2 * a] = make_float4(lo[a], 0.f, 0.f, 0.f);
-        nd[2 * a + 1] = make_float4(hi[a], 0.f, 0.f, 0.f);
+        // empty slots: inverted boxes, which no ray enters
+        nd[2 * a] = make_float4(lo[a], inf, inf, inf);
+        nd[2 * a + 1] = make_float4(hi[a], -inf, -inf, -inf);
       }
       nd[6] = make_float4(hbits_f(leaf_code(0, 1)), hbits_f(kBvh4Empty), hbits_f(kBvh4Empty), hbits_f(kBvh4Empty));
       const float4 tr[3] = {make_float4(v0[0], v0[1], v0[2], hbits_f(0)),

@@ -67,12 +67,23 @@ __global__ void centroid_bounds_kernel(const float* __restrict__ verts, const in
   if (threadIdx.x < 6) partial[blockIdx.x * 6 + threadIdx.x] = sh[threadIdx.x][0];
 }
 
+// One block: the union of the nblk partial boxes (min / max are exact, so
+// the order of the reduction does not matter).
 __global__ void bounds_final_kernel(const float* __restrict__ partial, int nblk, float* __restrict__ out) {
-  if (threadIdx.x >= 6) return;
-  const int a = threadIdx.x;
-  float v = a < 3 ? 3.4e38f : -3.4e38f;
-  for (int b = 0; b < nblk; ++b) v = a < 3 ? fminf(v, partial[b * 6 + a]) : fmaxf(v, partial[b * 6 + a]);
-  out[a] = v;
+  __shared__ float sh[6][kB];
+  float v[6] = {3.4e38f, 3.4e38f, 3.4e38f, -3.4e38f, -3.4e38f, -3.4e38f};
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x)
+    for (int a = 0; a < 6; ++a) v[a] = a < 3 ? fminf(v[a], partial[b * 6 + a]) : fmaxf(v[a], partial[b * 6 + a]);
+  for (int a = 0; a < 6; ++a) sh[a][threadIdx.x] = v[a];
+  __syncthreads();
+  for (int o = kB / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o)
+      for (int a = 0; a < 6; ++a)
+        sh[a][threadIdx.x] = a < 3 ? fminf(sh[a][threadIdx.x], sh[a][threadIdx.x + o])
+                                   : fmaxf(sh[a][threadIdx.x], sh[a][threadIdx.x + o]);
+    __syncthreads();
+  }
+  if (threadIdx.x < 6) out[threadIdx.x] = sh[threadIdx.x][0];
 }
 
 DR_D uint32_t expand10(uint32_t v) {
@@ -277,7 +288,17 @@ __global__ void ploc_init_kernel(int n, const float* __restrict__ box, int* __re
   for (int q = 0; q < 6; ++q) cl_box[6 * i + q] = box[(size_t)(n - 1 + i) * 6 + q];
 }
 
-__global__ void ploc_nn_kernel(int m, int r, const float* __restrict__ cl_box, int* __restrict__ nn) {
+// The clustering loop keeps its state on the device, so that the host
+// enqueues several passes between synchronisations:
+//   st[0] = m, clusters left; st[1] = inner nodes created so far;
+//   st[2] = merges of the current pass.
+// Grids are sized by the host's upper bound m_ub >= m; a pass that finds
+// m = 1 copies the single cluster and changes nothing.
+constexpr int kPlocM = 0, kPlocCreated = 1, kPlocMerges = 2, kPlocState = 4;
+
+__global__ void ploc_nn_kernel(const int* __restrict__ st, int r, const float* __restrict__ cl_box,
+                               int* __restrict__ nn) {
+  const int m = st[kPlocM];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m) return;
   float bi[6];
@@ -298,22 +319,58 @@ __global__ void ploc_nn_kernel(int m, int r, const float* __restrict__ cl_box, i
   nn[i] = bj;
 }
 
-__global__ void ploc_flag_kernel(int m, const int* __restrict__ nn, uint32_t* __restrict__ flag) {
+// flag[i] = 1 for the left cluster of each mutual nearest-neighbour pair;
+// zero from m up to m_ub, so that a scan over m_ub entries counts the pass
+__global__ void ploc_flag_kernel(const int* __restrict__ st, int m_ub, const int* __restrict__ nn,
+                                 uint32_t* __restrict__ flag) {
+  const int m = st[kPlocM];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= m) return;
+  if (i >= m_ub) return;
+  if (i >= m) {
+    flag[i] = 0u;
+    return;
+  }
   const int j = nn[i];
   flag[i] = (j >= 0 && j < m && nn[j] == i && i < j) ? 1u : 0u;
 }
 
+// The pass's merge count (scan of the flags); when no mutual pair exists
+// (degenerate ties) clusters 0 and 1 merge instead.  All flags are zero
+// then, so the scan is zero everywhere, which is what the merge of cluster
+// 0 needs.
+__global__ void ploc_count_kernel(int* __restrict__ st, int* __restrict__ nn, uint32_t* __restrict__ flag,
+                                  const uint32_t* __restrict__ pos) {
+  const int m = st[kPlocM];
+  if (m <= 1) {
+    st[kPlocMerges] = 0;
+    return;
+  }
+  int merges = (int)(pos[m - 1] + flag[m - 1]);
+  if (merges == 0) {
+    nn[0] = 1;
+    nn[1] = 0;
+    flag[0] = 1u;
+    flag[1] = 0u;
+    merges = 1;
+  }
+  st[kPlocMerges] = merges;
+}
+
 // Merges the flagged pairs: the k-th merge (k = exclusive scan of the flags)
-// creates inner node base - k.  Writes the surviving cluster list's keep
-// flags (1 = keep) into keep.
-__global__ void ploc_merge_kernel(int m, int base, const int* __restrict__ nn, const uint32_t* __restrict__ flag,
-                                  const uint32_t* __restrict__ pos, int* __restrict__ cl_node,
-                                  float* __restrict__ cl_box, int* __restrict__ child, float* __restrict__ box,
-                                  uint32_t* __restrict__ keep) {
+// creates inner node (n - 2 - created) - k.  Writes the surviving cluster
+// list's keep flags (1 = keep) into keep, zero from m up to m_ub.
+__global__ void ploc_merge_kernel(const int* __restrict__ st, int n, int m_ub, const int* __restrict__ nn,
+                                  const uint32_t* __restrict__ flag, const uint32_t* __restrict__ pos,
+                                  int* __restrict__ cl_node, float* __restrict__ cl_box, int* __restrict__ child,
+                                  float* __restrict__ box, uint32_t* __restrict__ keep) {
+  const int m = st[kPlocM];
+  const int base = (n - 2) - st[kPlocCreated];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= m) return;
+  if (i >= m_ub) return;
+  if (i >= m) {
+    keep[i] = 0u;
+    return;
+  }
   const int j = nn[i];
   const bool merging_left = flag[i] != 0u;
   const bool merged_away = j >= 0 && j < m && flag[j] != 0u && nn[j] == i;  // i is the right partner of j
@@ -335,9 +392,11 @@ __global__ void ploc_merge_kernel(int m, int base, const int* __restrict__ nn, c
   cl_node[i] = idx;
 }
 
-__global__ void ploc_compact_kernel(int m, const uint32_t* __restrict__ keep, const uint32_t* __restrict__ pos,
-                                    const int* __restrict__ cl_node, const float* __restrict__ cl_box,
-                                    int* __restrict__ out_node, float* __restrict__ out_box) {
+__global__ void ploc_compact_kernel(const int* __restrict__ st, const uint32_t* __restrict__ keep,
+                                    const uint32_t* __restrict__ pos, const int* __restrict__ cl_node,
+                                    const float* __restrict__ cl_box, int* __restrict__ out_node,
+                                    float* __restrict__ out_box) {
+  const int m = st[kPlocM];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m || !keep[i]) return;
   const int o = (int)pos[i];
@@ -345,19 +404,23 @@ __global__ void ploc_compact_kernel(int m, const uint32_t* __restrict__ keep, co
   for (int q = 0; q < 6; ++q) out_box[6 * o + q] = cl_box[6 * i + q];
 }
 
-// fallback when no mutual pair exists (degenerate ties): merge clusters 0, 1
-__global__ void ploc_force_pair_kernel(int* nn, uint32_t* flag) {
-  nn[0] = 1;
-  nn[1] = 0;
-  flag[0] = 1u;
-  flag[1] = 0u;
+// end of a pass: m -= merges, created += merges
+__global__ void ploc_advance_kernel(int* __restrict__ st) {
+  st[kPlocCreated] += st[kPlocMerges];
+  st[kPlocM] -= st[kPlocMerges];
+}
+
+__global__ void ploc_state_init_kernel(int* __restrict__ st, int n) {
+  st[kPlocM] = n;
+  st[kPlocCreated] = 0;
+  st[kPlocMerges] = 0;
 }
 
 }  // namespace
 
 size_t ploc_scratch_bytes(int nt) {
   const size_t n = (size_t)(nt < 2 ? 2 : nt);
-  return a256(n * 4) * 2 + a256(n * 24) * 2 + a256(n * 4) * 4 + scan_scratch_bytes(n) + 256;
+  return a256(n * 4) * 2 + a256(n * 24) * 2 + a256(n * 4) * 4 + a256(kPlocState * 4) + scan_scratch_bytes(n) + 256;
 }
 
 int build_ploc(const float* d_verts, const int* d_tris, int n, float4* d_nodes, float4* d_tris_out, void* scratch,
@@ -366,7 +429,7 @@ int build_ploc(const float* d_verts, const int* d_tris, int n, float4* d_nodes, 
   BvhScratch s = carve(scratch, n);
   const int nblk = (n + kB - 1) / kB;
   centroid_bounds_kernel<<<nblk, kB, 0, st>>>(d_verts, d_tris, n, s.cbox);
-  bounds_final_kernel<<<1, 32, 0, st>>>(s.cbox, nblk, s.gbox);
+  bounds_final_kernel<<<1, kB, 0, st>>>(s.cbox, nblk, s.gbox);
   morton_kernel<<<nblk, kB, 0, st>>>(d_verts, d_tris, n, s.gbox, s.keys0);
   uint2* sorted = sort_pairs(s.keys0, s.keys1, (size_t)n, 32, s.sort_scratch, st);
   leaf_boxes_kernel<<<nblk, kB, 0, st>>>(d_verts, d_tris, sorted, n, s.box, d_tris_out, s.flag);
@@ -381,36 +444,34 @@ int build_ploc(const float* d_verts, const int* d_tris, int n, float4* d_nodes, 
   uint32_t* flag = reinterpret_cast<uint32_t*>(p); p += a256(nn_ * 4);
   uint32_t* pos = reinterpret_cast<uint32_t*>(p); p += a256(nn_ * 4);
   uint32_t* keep = reinterpret_cast<uint32_t*>(p); p += a256(nn_ * 4);
+  int* state = reinterpret_cast<int*>(p); p += a256(kPlocState * 4);
   void* scan_tmp = p;
   ploc_init_kernel<<<nblk, kB, 0, st>>>(n, s.box, node_a, box_a);
-  int m = n;
-  int created = 0;
-  uint32_t host[2];
-  // every pass merges at least one pair, so at most n - 1 passes
-  for (int pass = 0; m > 1 && pass < n; ++pass) {
-    const int mb = (m + kB - 1) / kB;
-    ploc_nn_kernel<<<mb, kB, 0, st>>>(m, radius, box_a, nn);
-    ploc_flag_kernel<<<mb, kB, 0, st>>>(m, nn, flag);
-    launch_exclusive_scan(flag, pos, (size_t)m, scan_tmp, st);
-    if (cudaMemcpyAsync(host, pos + (m - 1), 4, cudaMemcpyDeviceToHost, st) != cudaSuccess) return -1;
-    if (cudaMemcpyAsync(host + 1, flag + (m - 1), 4, cudaMemcpyDeviceToHost, st) != cudaSuccess) return -1;
-    if (cudaStreamSynchronize(st) != cudaSuccess) return -1;
-    int merges = (int)(host[0] + host[1]);
-    if (merges == 0) {
-      ploc_force_pair_kernel<<<1, 1, 0, st>>>(nn, flag);
-      launch_exclusive_scan(flag, pos, (size_t)m, scan_tmp, st);
-      merges = 1;
+  ploc_state_init_kernel<<<1, 1, 0, st>>>(state, n);
+  // every pass merges at least one pair, so at most n - 1 passes; the host
+  // reads the cluster count back once per kPassesPerSync passes
+  constexpr int kPassesPerSync = 6;
+  int m_ub = n, passes = 0;
+  int host[kPlocState] = {n, 0, 0, 0};
+  while (host[kPlocM] > 1 && passes < n) {
+    for (int q = 0; q < kPassesPerSync && passes < n; ++q, ++passes) {
+      const int mb = (m_ub + kB - 1) / kB;
+      ploc_nn_kernel<<<mb, kB, 0, st>>>(state, radius, box_a, nn);
+      ploc_flag_kernel<<<mb, kB, 0, st>>>(state, m_ub, nn, flag);
+      launch_exclusive_scan(flag, pos, (size_t)m_ub, scan_tmp, st);
+      ploc_count_kernel<<<1, 1, 0, st>>>(state, nn, flag, pos);
+      ploc_merge_kernel<<<mb, kB, 0, st>>>(state, n, m_ub, nn, flag, pos, node_a, box_a, s.child, s.box, keep);
+      launch_exclusive_scan(keep, pos, (size_t)m_ub, scan_tmp, st);
+      ploc_compact_kernel<<<mb, kB, 0, st>>>(state, keep, pos, node_a, box_a, node_b, box_b);
+      ploc_advance_kernel<<<1, 1, 0, st>>>(state);
+      std::swap(node_a, node_b);
+      std::swap(box_a, box_b);
     }
-    const int base = (n - 2) - created;
-    ploc_merge_kernel<<<mb, kB, 0, st>>>(m, base, nn, flag, pos, node_a, box_a, s.child, s.box, keep);
-    launch_exclusive_scan(keep, pos, (size_t)m, scan_tmp, st);
-    ploc_compact_kernel<<<mb, kB, 0, st>>>(m, keep, pos, node_a, box_a, node_b, box_b);
-    std::swap(node_a, node_b);
-    std::swap(box_a, box_b);
-    created += merges;
-    m -= merges;
+    if (cudaMemcpyAsync(host, state, sizeof(host), cudaMemcpyDeviceToHost, st) != cudaSuccess) return -1;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return -1;
+    m_ub = std::max(host[kPlocM], 1);
   }
-  if (m != 1 || created != n - 1) return -1;
+  if (host[kPlocM] != 1 || host[kPlocCreated] != n - 1) return -1;
   emit_nodes_kernel<<<nblk, kB, 0, st>>>(n, s.child, s.box, d_nodes);
   return n - 1;
 }
@@ -432,7 +493,7 @@ int build_lbvh(const float* d_verts, const int* d_tris, int n, float4* d_nodes, 
   BvhScratch s = carve(scratch, n);
   const int nblk = (n + kB - 1) / kB;
   centroid_bounds_kernel<<<nblk, kB, 0, st>>>(d_verts, d_tris, n, s.cbox);
-  bounds_final_kernel<<<1, 32, 0, st>>>(s.cbox, nblk, s.gbox);
+  bounds_final_kernel<<<1, kB, 0, st>>>(s.cbox, nblk, s.gbox);
   morton_kernel<<<nblk, kB, 0, st>>>(d_verts, d_tris, n, s.gbox, s.keys0);
   uint2* sorted = sort_pairs(s.keys0, s.keys1, (size_t)n, 32, s.sort_scratch, st);
   hierarchy_kernel<<<nblk, kB, 0, st>>>(sorted, n, s.child, s.parent);

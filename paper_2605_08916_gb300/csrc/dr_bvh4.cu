@@ -407,7 +407,14 @@ __global__ void emit_kernel(const float4* __restrict__ n2, const float4* __restr
   if (!is4[n]) return;
   Kid kids[4];
   const int nk = expand_dp(n2, n, dp_cost, dp_split, kids);
-  float lo[3][4] = {}, hi[3][4] = {};  // empty slots stay zero; the traversal skips them by their link
+  // an empty slot holds an inverted box (lo = +inf, hi = -inf), which every
+  // slab test misses, so the walk needs no test of its link
+  float lo[3][4], hi[3][4];
+  for (int a = 0; a < 3; ++a)
+    for (int k = 0; k < 4; ++k) {
+      lo[a][k] = __int_as_float(0x7f800000);
+      hi[a][k] = __int_as_float(0xff800000);
+    }
   int links[4] = {kBvh4Empty, kBvh4Empty, kBvh4Empty, kBvh4Empty};
   for (int k = 0; k < nk; ++k) {
     const Kid& c = kids[k];

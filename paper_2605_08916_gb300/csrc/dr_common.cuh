@@ -131,7 +131,8 @@ constexpr float kGlossySpecProb = 0.5f;
 
 // 4-wide BVH node (112 B, 7 x float4): lo.x[4], hi.x[4], lo.y[4], hi.y[4],
 // lo.z[4], hi.z[4], then the four child links (inner index, leaf code, or
-// kBvh4Empty); leaves hold up to kBvh4MaxLeaf triangles.
+// kBvh4Empty, whose box is inverted: lo = +inf, hi = -inf); leaves hold up
+// to kBvh4MaxLeaf triangles.
 constexpr int kNode4F4 = 7;
 constexpr int kBvh4MaxLeaf = 4;
 constexpr int kBvh4Empty = 0x7fffffff;

@@ -228,8 +228,8 @@ DR_D bool closest4_inner(const float4* __restrict__ nodes, const Ray& r, Walk4& 
   int nc = 0;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    const int c = i4c(ch, k);
-    ok[k] = c != kBvh4Empty && e[k] >= 0.0f && e[k] <= tbest;
+    // (an empty slot's inverted box is always a miss: e[k] < 0)
+    ok[k] = e[k] >= 0.0f && e[k] <= tbest;
     nc += ok[k] ? 1 : 0;
   }
   if (nc == 0) {
@@ -277,7 +277,7 @@ DR_D bool any4_inner(const float4* __restrict__ nodes, const Ray& r, float tmax,
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     const int c = i4c(ch, k);
-    if (c == kBvh4Empty || !(ent[k] >= 0.0f)) continue;
+    if (!(ent[k] >= 0.0f)) continue;  // a miss, or an empty slot (inverted box)
     if (next == kBvh4Empty) {
       next = c;
     } else if (w.sp < STACK) {
