@@ -531,7 +531,10 @@ int dr_frame(dr_ctx* ctx, uint32_t n_steps);
  * DR_BVH_PLOC (default; parallel locally-ordered clustering of the
  * Morton-ordered triangles with search radius `radius`, 1..256, default 16)
  * or DR_BVH_LBVH (linear BVH, Karras 2012; radius ignored).  Both produce
- * the same node layout.  Errors: INVALID_ARG. */
+ * the same node layout.  A clustered tree taller than the traversal stack
+ * allows (exact ties among many triangle boxes, e.g. coincident triangles,
+ * make the clustering merge one pair per pass) is replaced by the linear
+ * BVH of the same scene.  Errors: INVALID_ARG. */
 enum { DR_BVH_LBVH = 0, DR_BVH_PLOC = 1 };
 int dr_set_bvh_builder(dr_ctx* ctx, int32_t builder, int32_t radius);
 

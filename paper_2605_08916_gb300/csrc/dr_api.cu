@@ -712,7 +712,7 @@ int build_wide(dr_ctx* c, const float* verts, int nv, const int* tris, int nt, i
   if (r == DR_OK) {
     cudaMemcpyAsync(dv, verts, 12 * (size_t)nv, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(dt, tris, 12 * (size_t)nt, cudaMemcpyHostToDevice, s);
-    const int nn = c->builder == DR_BVH_PLOC ? build_ploc(dv, dt, nt, n2, t2, scratch, ploc, c->ploc_radius, s)
+    const int nn = c->builder == DR_BVH_PLOC ? build_ploc(dv, dt, nt, n2, t2, scratch, ploc, c->ploc_radius, kTraversalStack + 1, s)
                                              : build_lbvh(dv, dt, nt, n2, t2, scratch, s);
     c->launches += 8;
     Bvh4Plan plan{};
@@ -1112,7 +1112,8 @@ int dr_scene_upload(dr_ctx* c, const float* verts, int32_t nv, const int32_t* tr
     }
     launch_surface_records(dverts, dtris, dmat, dsel, dvn, nt, c->surf, s);
     c->n_nodes = c->builder == DR_BVH_PLOC
-                     ? build_ploc(dverts, dtris, nt, c->nodes, c->tris, scratch, ploc_scratch, c->ploc_radius, s)
+                     ? build_ploc(dverts, dtris, nt, c->nodes, c->tris, scratch, ploc_scratch, c->ploc_radius,
+                                  kTraversalStack + 1, s)
                      : build_lbvh(dverts, dtris, nt, c->nodes, c->tris, scratch, s);
     cudaError_t e = cudaStreamSynchronize(s);
     if (e == cudaSuccess) e = cudaGetLastError();

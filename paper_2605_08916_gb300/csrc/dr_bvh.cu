@@ -281,20 +281,22 @@ DR_D float box_area(const float* a, const float* b) {
 }
 
 __global__ void ploc_init_kernel(int n, const float* __restrict__ box, int* __restrict__ cl_node,
-                                 float* __restrict__ cl_box) {
+                                 float* __restrict__ cl_box, int* __restrict__ height) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   cl_node[i] = n - 1 + i;
+  height[n - 1 + i] = 1;
   for (int q = 0; q < 6; ++q) cl_box[6 * i + q] = box[(size_t)(n - 1 + i) * 6 + q];
 }
 
 // The clustering loop keeps its state on the device, so that the host
 // enqueues several passes between synchronisations:
 //   st[0] = m, clusters left; st[1] = inner nodes created so far;
-//   st[2] = merges of the current pass.
+//   st[2] = merges of the current pass; st[3] = height of the tallest
+//   subtree built so far (a leaf: 1).
 // Grids are sized by the host's upper bound m_ub >= m; a pass that finds
 // m = 1 copies the single cluster and changes nothing.
-constexpr int kPlocM = 0, kPlocCreated = 1, kPlocMerges = 2, kPlocState = 4;
+constexpr int kPlocM = 0, kPlocCreated = 1, kPlocMerges = 2, kPlocMaxH = 3, kPlocState = 4;
 
 __global__ void ploc_nn_kernel(const int* __restrict__ st, int r, const float* __restrict__ cl_box,
                                int* __restrict__ nn) {
@@ -359,10 +361,10 @@ __global__ void ploc_count_kernel(int* __restrict__ st, int* __restrict__ nn, ui
 // Merges the flagged pairs: the k-th merge (k = exclusive scan of the flags)
 // creates inner node (n - 2 - created) - k.  Writes the surviving cluster
 // list's keep flags (1 = keep) into keep, zero from m up to m_ub.
-__global__ void ploc_merge_kernel(const int* __restrict__ st, int n, int m_ub, const int* __restrict__ nn,
+__global__ void ploc_merge_kernel(int* __restrict__ st, int n, int m_ub, const int* __restrict__ nn,
                                   const uint32_t* __restrict__ flag, const uint32_t* __restrict__ pos,
                                   int* __restrict__ cl_node, float* __restrict__ cl_box, int* __restrict__ child,
-                                  float* __restrict__ box, uint32_t* __restrict__ keep) {
+                                  float* __restrict__ box, uint32_t* __restrict__ keep, int* __restrict__ height) {
   const int m = st[kPlocM];
   const int base = (n - 2) - st[kPlocCreated];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -380,6 +382,9 @@ __global__ void ploc_merge_kernel(const int* __restrict__ st, int n, int m_ub, c
   const int a = cl_node[i], b = cl_node[j];
   child[2 * idx] = a;
   child[2 * idx + 1] = b;
+  const int h = max(height[a], height[b]) + 1;
+  height[idx] = h;
+  atomicMax(&st[kPlocMaxH], h);
   float u[6];
   for (int q = 0; q < 3; ++q) {
     u[q] = fminf(cl_box[6 * i + q], cl_box[6 * j + q]);
@@ -414,17 +419,19 @@ __global__ void ploc_state_init_kernel(int* __restrict__ st, int n) {
   st[kPlocM] = n;
   st[kPlocCreated] = 0;
   st[kPlocMerges] = 0;
+  st[kPlocMaxH] = 1;
 }
 
 }  // namespace
 
 size_t ploc_scratch_bytes(int nt) {
   const size_t n = (size_t)(nt < 2 ? 2 : nt);
-  return a256(n * 4) * 2 + a256(n * 24) * 2 + a256(n * 4) * 4 + a256(kPlocState * 4) + scan_scratch_bytes(n) + 256;
+  return a256(n * 4) * 2 + a256(n * 24) * 2 + a256(n * 4) * 4 + a256(kPlocState * 4) + a256(2 * n * 4) +
+         scan_scratch_bytes(n) + 256;
 }
 
 int build_ploc(const float* d_verts, const int* d_tris, int n, float4* d_nodes, float4* d_tris_out, void* scratch,
-               void* ploc_scratch, int radius, cudaStream_t st) {
+               void* ploc_scratch, int radius, int max_height, cudaStream_t st) {
   if (n <= 1) return build_lbvh(d_verts, d_tris, n, d_nodes, d_tris_out, scratch, st);
   BvhScratch s = carve(scratch, n);
   const int nblk = (n + kB - 1) / kB;
@@ -445,8 +452,9 @@ int build_ploc(const float* d_verts, const int* d_tris, int n, float4* d_nodes, 
   uint32_t* pos = reinterpret_cast<uint32_t*>(p); p += a256(nn_ * 4);
   uint32_t* keep = reinterpret_cast<uint32_t*>(p); p += a256(nn_ * 4);
   int* state = reinterpret_cast<int*>(p); p += a256(kPlocState * 4);
+  int* height = reinterpret_cast<int*>(p); p += a256(2 * nn_ * 4);  // per node id (inner, then leaves)
   void* scan_tmp = p;
-  ploc_init_kernel<<<nblk, kB, 0, st>>>(n, s.box, node_a, box_a);
+  ploc_init_kernel<<<nblk, kB, 0, st>>>(n, s.box, node_a, box_a, height);
   ploc_state_init_kernel<<<1, 1, 0, st>>>(state, n);
   // every pass merges at least one pair, so at most n - 1 passes; the host
   // reads the cluster count back once per kPassesPerSync passes
@@ -460,7 +468,8 @@ int build_ploc(const float* d_verts, const int* d_tris, int n, float4* d_nodes, 
       ploc_flag_kernel<<<mb, kB, 0, st>>>(state, m_ub, nn, flag);
       launch_exclusive_scan(flag, pos, (size_t)m_ub, scan_tmp, st);
       ploc_count_kernel<<<1, 1, 0, st>>>(state, nn, flag, pos);
-      ploc_merge_kernel<<<mb, kB, 0, st>>>(state, n, m_ub, nn, flag, pos, node_a, box_a, s.child, s.box, keep);
+      ploc_merge_kernel<<<mb, kB, 0, st>>>(state, n, m_ub, nn, flag, pos, node_a, box_a, s.child, s.box, keep,
+                                           height);
       launch_exclusive_scan(keep, pos, (size_t)m_ub, scan_tmp, st);
       ploc_compact_kernel<<<mb, kB, 0, st>>>(state, keep, pos, node_a, box_a, node_b, box_b);
       ploc_advance_kernel<<<1, 1, 0, st>>>(state);
@@ -472,6 +481,13 @@ int build_ploc(const float* d_verts, const int* d_tris, int n, float4* d_nodes, 
     m_ub = std::max(host[kPlocM], 1);
   }
   if (host[kPlocM] != 1 || host[kPlocCreated] != n - 1) return -1;
+  // exact ties among many boxes (coincident triangles, say) make every
+  // cluster's nearest neighbour the same one, so that a pass merges a single
+  // pair and the tree degenerates into a chain: too tall for the traversal
+  // stack, the linear BVH (which orders equal Morton codes by index) is
+  // built instead
+  if (max_height > 0 && host[kPlocMaxH] > max_height)
+    return build_lbvh(d_verts, d_tris, n, d_nodes, d_tris_out, scratch, st);
   emit_nodes_kernel<<<nblk, kB, 0, st>>>(n, s.child, s.box, d_nodes);
   return n - 1;
 }

@@ -47,11 +47,14 @@ size_t bvh_scratch_bytes(int nt);
 int build_lbvh(const float* d_verts, const int* d_tris, int nt, float4* d_nodes, float4* d_tris_out, void* scratch,
                cudaStream_t s);
 // Same output layout, clustered by PLOC with search radius `radius`
-// (second scratch of ploc_scratch_bytes(nt)).  Synchronises once per pass.
-// Returns the node count, or -1 on failure.
+// (second scratch of ploc_scratch_bytes(nt)).  Synchronises once per six
+// clustering passes.  When the clustered tree is taller than max_height
+// (root = 1; 0: no limit), which exact ties among many boxes can cause, the
+// linear BVH is built into the same outputs instead.  Returns the node
+// count, or -1 on failure.
 size_t ploc_scratch_bytes(int nt);
 int build_ploc(const float* d_verts, const int* d_tris, int nt, float4* d_nodes, float4* d_tris_out, void* scratch,
-               void* ploc_scratch, int radius, cudaStream_t s);
+               void* ploc_scratch, int radius, int max_height, cudaStream_t s);
 // Per-triangle surface records (5 float4) from the device arrays; sel is
 // the light-selection probability per triangle (device, may be null).
 void launch_surface_records(const float* d_verts, const int* d_tris, const int* d_tri_mat, const float* d_sel,

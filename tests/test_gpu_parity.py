@@ -179,6 +179,73 @@ def test_one_triangle_scene_keeps_the_binary_bvh(torch, R):
     r.close()
 
 
+def _soup(tri_verts, seed):
+    """A scene of the given triangles ([nt, 3, 3]) under one diffuse material."""
+    nt = len(tri_verts)
+    verts = np.ascontiguousarray(tri_verts.reshape(-1, 3), dtype=np.float32)
+    tris = np.arange(3 * nt, dtype=np.int32).reshape(nt, 3)
+    mats = np.stack([S.material(S.MAT_DIFFUSE, (0.5, 0.5, 0.5))])
+    cam = np.array([0.5, 0.5, 4, 0.5, 0.5, 0, 0, 1, 0, 40], np.float32)
+    return S.Scene(verts, tris, np.zeros(nt, np.int32), mats, cam, 8, 8, name=f"soup{seed}")
+
+
+@pytest.mark.parametrize("builder", ["ploc", "lbvh"])
+def test_bvh_builds_on_tiny_and_degenerate_scenes(torch, R, oracle, builder):
+    """Both builders make a tree over every triangle of tiny scenes (2, 3 and
+    5 triangles) and of scenes full of exact ties: 300 copies of one
+    triangle beside 20 others, and a grid of equal triangles.  On the
+    copies, clustering finds every cluster's nearest neighbour in the same
+    cluster, merges one pair per pass and would build a chain some 300
+    levels tall: the builder then falls back to the linear BVH, so the tree
+    stays within the traversal stack.  Closest hits match the oracle's brute
+    force (ties to the smaller id on both sides)."""
+    rng = np.random.default_rng(11)
+
+    def rand_tris(n):
+        c = rng.uniform(0.0, 1.0, (n, 1, 3))
+        return c + rng.uniform(-0.08, 0.08, (n, 3, 3))
+
+    one = np.array([[0.2, 0.2, 0.3], [0.8, 0.25, 0.35], [0.4, 0.8, 0.3]])
+    gx, gy = np.meshgrid(np.arange(40) / 40.0, np.arange(40) / 40.0)
+    cell = np.array([[0.0, 0.0, 0.0], [0.02, 0.0, 0.0], [0.0, 0.02, 0.0]])
+    grid = np.stack([gx.ravel(), gy.ravel(), np.full(gx.size, 0.5)], 1)[:, None, :] + cell[None]
+    cases = [rand_tris(2), rand_tris(3), rand_tris(5),
+             np.concatenate([np.repeat(one[None], 300, 0), rand_tris(20)]), grid]
+    r = R.Renderer()
+    r.set_bvh_builder(builder)
+    for k, tv in enumerate(cases):
+        scene = _soup(tv, k)
+        # 3000 rays aimed at random points of random triangles, 1000 random
+        n_aim = 3000
+        w = rng.dirichlet(np.ones(3), n_aim)
+        target = np.einsum("nk,nkc->nc", w, tv[rng.integers(0, len(tv), n_aim)])
+        o = rng.uniform(-0.5, 1.5, (n_aim + 1000, 3))
+        d = np.concatenate([target - o[:n_aim], rng.normal(size=(1000, 3))])
+        d /= np.linalg.norm(d, axis=1, keepdims=True)
+        o, d = o.astype(np.float32), d.astype(np.float32)
+        rays = torch.from_numpy(np.concatenate([o, d], 1)).cuda()
+        r.upload_scene(scene)
+        info = r.bvh_info()
+        assert info["n_tris"] == scene.n_tris and info["max_depth"] <= 49, (k, info)
+        tri_g, t_g = r.trace_closest(rays)
+        torch.cuda.synchronize()
+        tri_g, t_g = tri_g.cpu().numpy(), t_g.cpu().numpy()
+        tri_o, t_o = oracle.OracleScene(scene).trace(o.astype(np.float64), d.astype(np.float64))
+        same = tri_g == tri_o
+        assert same.mean() > 0.999, (k, same.mean())
+        assert (tri_o >= 0).sum() > 1000, k
+        # distances of hits that are not grazing (an FP32 hit distance loses
+        # relative accuracy as 1 / |cos| of the angle to the plane)
+        hit = same & (tri_o >= 0)
+        nrm = np.cross(tv[:, 1] - tv[:, 0], tv[:, 2] - tv[:, 0])
+        nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
+        steep = hit.copy()
+        steep[hit] = np.abs(np.einsum("ij,ij->i", d[hit], nrm[tri_o[hit]])) >= 0.05
+        assert steep.sum() > 0.8 * hit.sum(), k
+        assert np.allclose(t_g[steep], t_o[steep], rtol=1e-4, atol=1e-5), k
+    r.close()
+
+
 EVAL_CASES = {
     "cornell-L4": (lambda: S.cornell_box(1, 64, 64), 4),
     "glossy-L8": (lambda: S.cornell_box(1, 256, 256, glossy=True), 8),
