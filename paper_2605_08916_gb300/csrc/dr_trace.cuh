@@ -339,6 +339,56 @@ DR_D bool any4_step(const DevScene& S, const Ray& r, float tmax, int ex0, int ex
   return any4_inner<STACK, STATS>(S.nodes4, r, tmax, w, st, err, stats);
 }
 
+// One step of a 4-wide walk that serves closest-hit rays (any = false) and
+// shadow rays (any = true) with the same code, so that a warp holding both
+// kinds runs one instruction stream: inner nodes are taken nearest first
+// for both (for a shadow ray the order only changes which nodes it visits
+// before it finds an occluder, not whether it finds one), and a leaf test
+// differs only in what a hit does.  For a closest-hit ray tlim and best are
+// the closest hit so far (ex1 is -1); for a shadow ray tlim is its tmax and
+// *occluded is set when a triangle other than ex0 and ex1 lies within it.
+// The per-triangle tests are those of closest4_step and any4_step, so the
+// hits and the occlusion are theirs.  Returns true when the walk is over.
+template <int STACK, bool STATS>
+DR_D bool mixed4_step(const DevScene& S, const Ray& r, bool any, int ex0, int ex1, Walk4& w, float& tlim, int& best,
+                      bool* occluded, TraceStack<STACK> st, uint32_t* err, TraceStats* stats) {
+  if (--w.budget < 0 || w.node >= S.n_nodes4) {
+    *err |= kErrBadIndex;
+    return true;
+  }
+  if (w.node < 0) {
+    const int first = leaf_first(w.node);
+    int cnt = leaf_count(w.node);
+    if (first + cnt > S.n_tris) {
+      *err |= kErrBadIndex;
+      cnt = 0;
+    }
+    for (int i = 0; i < cnt; ++i) {
+      const float4 t0 = __ldg(S.tris4 + 3 * (first + i) + 0);
+      const float4 t1 = __ldg(S.tris4 + 3 * (first + i) + 1);
+      const float4 t2 = __ldg(S.tris4 + 3 * (first + i) + 2);
+      const int id = __float_as_int(t0.w);
+      if (STATS) ++stats->tris;
+      const float tmax = any ? tlim : tlim * 1.0000001f + 1e-30f;
+      float th;
+      if (id != ex0 && id != ex1 && tri_test(xyz(t0), xyz(t1), xyz(t2), r, S.tmin, tmax, &th)) {
+        if (any) {
+          *occluded = true;
+          return true;
+        }
+        if (th < tlim || (th == tlim && id < best)) {
+          tlim = th;
+          best = id;
+        }
+      }
+    }
+    if (w.sp == 0) return true;
+    w.node = st.at(--w.sp);
+    return false;
+  }
+  return closest4_inner<STACK, STATS>(S.nodes4, r, w, tlim, st, err, stats);
+}
+
 template <int STACK, bool STATS>
 DR_D int trace_closest4(const DevScene& S, const Ray& r, int exclude, float* t_hit, TraceStack<STACK> st,
                         uint32_t* err, TraceStats* stats) {

@@ -307,15 +307,20 @@ __global__ void __launch_bounds__(kWfThreads, WIDTH == kWalkTwoLevel ? 6 : kWfTr
       const bool leaf_phase = __popc(at_leaf) >= __popc(at_inner);
       if (has && lf == leaf_phase) {
         const DevScene& S = scene_of<BATCH>(a, sid);
-        if (!shadow) {
-          if (closest_step<kS, STATS>(S, r, ex0, wk, tlim, best, st, &err, &stats)) {
-            w.hit[j] = best;
-            has = false;
-          }
+        bool done, occ = false;
+        if constexpr (WIDTH == 4) {
+          // closest-hit and shadow rays share one step (one instruction
+          // stream for a warp that holds both)
+          done = mixed4_step<kS, STATS>(S, r, shadow, ex0, shadow ? ex1 : -1, wk, tlim, best, &occ, st, &err, &stats);
         } else {
-          bool occ;
-          if (any_step<kS, STATS>(S, r, tlim, ex0, ex1, wk, &occ, st, &err, &stats)) {
-            has = false;
+          done = !shadow ? closest_step<kS, STATS>(S, r, ex0, wk, tlim, best, st, &err, &stats)
+                         : any_step<kS, STATS>(S, r, tlim, ex0, ex1, wk, &occ, st, &err, &stats);
+        }
+        if (done) {
+          has = false;
+          if (!shadow) {
+            w.hit[j] = best;
+          } else {
             if (!occ) {
               const ShadowRec& sr = w.shadow[t];
               const unsigned long long c = (unsigned long long)__float_as_int(sr.wi_chain.w);
@@ -491,9 +496,21 @@ __global__ void __launch_bounds__(kWfThreads, kWfTailMinBlocks) wf_tail(StepArgs
             state = kIdle;
           }
         }
-      } else if (state == kShadow && !do_shade) {
-        bool occ;
-        if (any_step<kS, STATS>(S, r, tlim, ex0, ex1, wk, &occ, st, &err, &stats)) {
+      } else if ((state == kShadow || state == kClosest) && !do_shade) {
+        // closest-hit and shadow walks share one step (one instruction
+        // stream for a warp that holds both)
+        const bool sh = state == kShadow;
+        bool done, occ = false;
+        if constexpr (WIDTH == 4) {
+          done = mixed4_step<kS, STATS>(S, r, sh, ex0, sh ? ex1 : -1, wk, tlim, best, &occ, st, &err, &stats);
+        } else {
+          done = sh ? any_step<kS, STATS>(S, r, tlim, ex0, ex1, wk, &occ, st, &err, &stats)
+                    : closest_step<kS, STATS>(S, r, ex0, wk, tlim, best, st, &err, &stats);
+        }
+        if (done && !sh) {
+          hit = best;
+          state = kShade;
+        } else if (done) {
           if (!occ) {
             ps.f += contrib;
             GlobalTape{w.tape, a.N, j}.or_flags(k - 1, kFNeeVis);
@@ -517,11 +534,6 @@ __global__ void __launch_bounds__(kWfThreads, kWfTailMinBlocks) wf_tail(StepArgs
             store_slot(w.slot, j, ps, pix);
             state = kIdle;
           }
-        }
-      } else if (state == kClosest && !do_shade) {
-        if (closest_step<kS, STATS>(S, r, ex0, wk, tlim, best, st, &err, &stats)) {
-          hit = best;
-          state = kShade;
         }
       }
       const unsigned act = __ballot_sync(kFull, state != kIdle);
