@@ -12,8 +12,9 @@
 //                 that survive go to the adjoint queue
 //   wf_adjoint    reverse sweep over the tape kept in HBM
 //
-// Queues are compacted with one atomic per warp (ballot + popcount), so
-// warps never carry finished paths; the traversal passes are small kernels
+// Queues are compacted with ballots and popcounts and one atomic per block
+// iteration (shading) or per warp (the rest), so warps never carry finished
+// paths; the traversal passes are small kernels
 // with few registers.  Every path accumulates its contributions in the same
 // order as the fused kernel (emission of hit k, NEE of vertex k, emission of
 // hit k + 1, ...); the two executions differ only where the compiler
@@ -60,18 +61,6 @@ DR_D void store_slot(float4* __restrict__ slot, unsigned long long j, const Path
   slot[4 * j + 1] = make_float4(ps.d.x, ps.d.y, ps.d.z, __int_as_float(ps.prev_tri));
   slot[4 * j + 2] = make_float4(ps.beta.x, ps.beta.y, ps.beta.z, __int_as_float((ps.prev_delta & 1) | (ps.nseg << 8)));
   slot[4 * j + 3] = make_float4(ps.f.x, ps.f.y, ps.f.z, __int_as_float(pix));
-}
-
-// Warp-aggregated queue append: lanes with `take` get consecutive slots.
-DR_D uint32_t warp_append(uint32_t* count, bool take) {
-  const uint32_t mask = __activemask();
-  const uint32_t want = __ballot_sync(mask, take);
-  const int lane = threadIdx.x & 31;
-  const int leader = __ffs(mask) - 1;
-  uint32_t base = 0;
-  if (lane == leader && want) base = atomicAdd(count, (uint32_t)__popc(want));
-  base = __shfl_sync(mask, base, leader);
-  return base + __popc(want & ((1u << lane) - 1u));
 }
 
 // Appends to one of several queues (counters[key]): the lanes of `want`
@@ -352,8 +341,15 @@ __global__ void __launch_bounds__(kWfThreads, kWfShadeMinBlocks) wf_shade(StepAr
   const uint32_t* q = k == 1 && !a.ray_keys ? nullptr : queue_of(w, k);
   uint32_t* qn = queue_of(w, k + 1);
   const uint32_t n_iter = (n + gridDim.x * blockDim.x - 1) / (gridDim.x * blockDim.x);
-  // every lane runs the same number of iterations so the queue appends see
-  // whole warps
+  // the queue appends are aggregated over the block: one atomic per counter
+  // and block iteration instead of one per warp, since atomics on one address
+  // serialise (measured: shading 0.31 -> 0.26 ms per caustic step); the
+  // per-warp counts are double-buffered by iteration parity
+  __shared__ uint32_t s_cnt[2][2][kWfThreads / 32];
+  __shared__ uint32_t s_base[2][2];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  // every thread runs the same number of iterations so the queue appends see
+  // whole warps and the whole block
   for (uint32_t it = 0; it < n_iter; ++it) {
     const uint32_t t = it * gridDim.x * blockDim.x + blockIdx.x * blockDim.x + threadIdx.x;
     bool cont = false;
@@ -375,7 +371,28 @@ __global__ void __launch_bounds__(kWfThreads, kWfShadeMinBlocks) wf_shade(StepAr
         store_slot(w.slot, j, ps, pix);
       }
     }
-    const uint32_t si = warp_append(&w.counts[kWfShadowCount0 + k], nee.valid);
+    const bool next = cont && k < L;
+    const int par = it & 1;
+    const unsigned ms = __ballot_sync(kFull, nee.valid), mn = __ballot_sync(kFull, next);
+    if (lane == 0) {
+      s_cnt[par][0][wid] = __popc(ms);
+      s_cnt[par][1][wid] = __popc(mn);
+    }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+      uint32_t tot = 0;
+      for (int q2 = 0; q2 < kWfThreads / 32; ++q2) tot += s_cnt[par][threadIdx.x][q2];
+      s_base[par][threadIdx.x] =
+          tot ? atomicAdd(&w.counts[threadIdx.x == 0 ? kWfShadowCount0 + k : k + 1], tot) : 0u;
+    }
+    __syncthreads();
+    uint32_t ws = s_base[par][0], wn = s_base[par][1];
+    for (int q2 = 0; q2 < wid; ++q2) {
+      ws += s_cnt[par][0][q2];
+      wn += s_cnt[par][1][q2];
+    }
+    const unsigned below = (1u << lane) - 1u;
+    const uint32_t si = ws + __popc(ms & below), ni = wn + __popc(mn & below);
     if (nee.valid) {
       ShadowRec r;
       r.o_tmax = make_float4(nee.o.x, nee.o.y, nee.o.z, nee.tmax);
@@ -384,8 +401,6 @@ __global__ void __launch_bounds__(kWfThreads, kWfShadeMinBlocks) wf_shade(StepAr
       r.ex1 = nee.ex1;
       w.shadow[si] = r;
     }
-    const bool next = cont && k < L;
-    const uint32_t ni = warp_append(&w.counts[k + 1], next);
     if (next) {
       qn[ni] = (uint32_t)j;
       w.hit[j] = -1;
